@@ -1,0 +1,213 @@
+"""Pins of the oracle's projection (Sec. 4: Sigma' = J W Sigma W^T J^T, EWA
+splatting), SH colour and tile binning, against references that do not come
+from the oracle: scipy rotations and spherical harmonics, a finite-difference
+Jacobian of the pinhole map, numpy eigenvalues, rigid-motion invariance and a
+brute-force pixel enumeration of the tile sets."""
+import math
+
+import numpy as np
+import pytest
+from scipy.spatial.transform import Rotation
+from scipy.special import expit, sph_harm_y
+
+import scenes
+
+
+def _rotated_camera(W, H):
+    vm = scenes.look_at_viewmat(eye=(0.7, -0.4, -0.5), target=(0.05, 0.1, 3.0))
+    return scenes.pinhole_camera(W, H, viewmat=vm)
+
+
+def _pinhole(cam, pc):
+    return np.array([cam["fx"] * pc[0] / pc[2] + cam["cx"], cam["fy"] * pc[1] / pc[2] + cam["cy"]])
+
+
+def _jac_fd(cam, pc, h=1e-6):
+    J = np.zeros((2, 3))
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = h * max(1.0, abs(pc[k]))
+        J[:, k] = (_pinhole(cam, pc + e) - _pinhole(cam, pc - e)) / (2 * e[k])
+    return J
+
+
+def _world_cov(scene, i):
+    w, x, y, z = scene["quats"][i].astype(np.float64)
+    R = Rotation.from_quat([x, y, z, w]).as_matrix()
+    S = np.diag(np.exp(scene["log_scales"][i].astype(np.float64)) ** 2)
+    return R @ S @ R.T
+
+
+def test_mean_and_covariance(ora):
+    W, H = 64, 48
+    scene = scenes.random_scene(300, seed=1)
+    cam = _rotated_camera(W, H)
+    proj = ora.project(scene, cam, W, H)
+    vm = cam["viewmat"].astype(np.float64)
+    K = np.array([[cam["fx"], 0, cam["cx"]], [0, cam["fy"], cam["cy"]], [0, 0, 1.0]])
+    lim_x, lim_y = 1.3 * W / (2 * cam["fx"]), 1.3 * H / (2 * cam["fy"])
+    checked = 0
+    for i in range(300):
+        mu = scene["means"][i].astype(np.float64)
+        pc = vm[:3, :3] @ mu + vm[:3, 3]
+        if pc[2] <= cam["znear"]:
+            assert proj["radius"][i] == 0 and proj["tiles_touched"][i] == 0
+            continue
+        uvw = K @ pc
+        np.testing.assert_allclose(proj["mean2d"][i], uvw[:2] / uvw[2], rtol=1e-12)
+        if abs(pc[0] / pc[2]) > lim_x or abs(pc[1] / pc[2]) > lim_y:
+            continue
+        J = _jac_fd(cam, pc)
+        Wr = vm[:3, :3]
+        cov = J @ Wr @ _world_cov(scene, i) @ Wr.T @ J.T + 0.3 * np.eye(2)
+        got = proj["cov2d"][i]
+        np.testing.assert_allclose([got[0], got[1], got[2]], [cov[0, 0], cov[0, 1], cov[1, 1]],
+                                   rtol=1e-7, atol=1e-9 * np.abs(cov).max())
+        Q = np.linalg.inv(cov)
+        np.testing.assert_allclose(proj["conic"][i], [Q[0, 0], Q[0, 1], Q[1, 1]], rtol=1e-6,
+                                   atol=1e-9 * np.abs(Q).max())
+        lam = np.linalg.eigvalsh(cov).max()
+        assert proj["radius"][i] == math.ceil(3 * math.sqrt(lam))
+        assert proj["depth"][i] == pytest.approx(pc[2], rel=1e-14)
+        checked += 1
+    assert checked > 200
+    np.testing.assert_allclose(proj["opacity"], expit(scene["opacity_logits"].astype(np.float64)), rtol=1e-14)
+
+
+def test_jacobian_clamped_outside_frustum(ora):
+    """Outside 1.3 tan(fov/2) the Jacobian is taken at the clamped direction."""
+    W, H = 64, 64
+    cam = scenes.pinhole_camera(W, H)
+    scene = scenes.random_scene(1, seed=0)
+    scene["means"][0] = [2.5, -0.3, 2.0]       # x/z = 1.25 > 1.3 * tan(30 deg) = 0.75
+    scene["quats"][0] = [1, 0, 0, 0]
+    scene["log_scales"][0] = [-2.0, -2.5, -1.5]
+    proj = ora.project(scene, cam, W, H)
+    lim = 1.3 * W / (2 * cam["fx"])
+    pc = scene["means"][0].astype(np.float64)
+    pclamp = np.array([lim * pc[2], pc[1], pc[2]])
+    J = _jac_fd(cam, pclamp)
+    cov = J @ _world_cov(scene, 0) @ J.T + 0.3 * np.eye(2)
+    np.testing.assert_allclose(proj["cov2d"][0], [cov[0, 0], cov[0, 1], cov[1, 1]], rtol=1e-7)
+    np.testing.assert_allclose(proj["mean2d"][0], _pinhole(cam, pc), rtol=1e-13)
+
+
+def test_rigid_motion_invariance(ora):
+    """Moving the world and the camera by the same rigid motion changes nothing
+    on screen (pins the use of W inside J W Sigma W^T J^T)."""
+    W, H = 48, 40
+    scene = scenes.random_scene(200, seed=3)
+    cam = _rotated_camera(W, H)
+    base = ora.project(scene, cam, W, H)
+    G = Rotation.from_rotvec([0.3, -0.7, 0.2])
+    tr = np.array([0.4, -1.0, 2.0])
+    moved = dict(scene)
+    moved["means"] = (G.apply(scene["means"].astype(np.float64)) + tr)
+    q = scene["quats"].astype(np.float64)
+    r = G * Rotation.from_quat(np.concatenate([q[:, 1:], q[:, :1]], 1))
+    qx = r.as_quat()
+    moved["quats"] = np.concatenate([qx[:, 3:], qx[:, :3]], 1)
+    Gm = np.eye(4)
+    Gm[:3, :3] = G.as_matrix()
+    Gm[:3, 3] = tr
+    cam2 = dict(cam)
+    cam2["viewmat"] = cam["viewmat"].astype(np.float64) @ np.linalg.inv(Gm)
+    got = ora.project(moved, cam2, W, H)
+    vis = base["tiles_touched"] > 0
+    np.testing.assert_allclose(got["mean2d"][vis], base["mean2d"][vis], rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose(got["cov2d"][vis], base["cov2d"][vis], rtol=1e-9, atol=1e-12)
+
+
+def _real_sh_scipy(deg, dirs):
+    d = dirs / np.linalg.norm(dirs, axis=1, keepdims=True)
+    theta = np.arccos(np.clip(d[:, 2], -1, 1))
+    phi = np.arctan2(d[:, 1], d[:, 0])
+    out = np.zeros((len(d), (deg + 1) ** 2))
+    for l in range(deg + 1):
+        for m in range(-l, l + 1):
+            Y = sph_harm_y(l, abs(m), theta, phi)      # complex, Condon-Shortley phase
+            if m == 0:
+                v = Y.real
+            elif m > 0:
+                v = math.sqrt(2) * Y.real
+            else:
+                v = math.sqrt(2) * Y.imag
+            out[:, l * l + l + m] = v
+    return out
+
+
+def test_sh_basis_against_scipy(ora):
+    rng = np.random.default_rng(0)
+    dirs = rng.normal(0, 1, (200, 3))
+    dirs[0] = [0, 0, 1]
+    dirs[1] = [0, 0, -1]
+    got = ora.sh_basis(3, dirs)
+    want = _real_sh_scipy(3, dirs)
+    np.testing.assert_allclose(got, want, atol=1e-13)
+    # l = 1 is (-y, z, -x) times sqrt(3 / (4 pi)) in this convention
+    d = dirs[2] / np.linalg.norm(dirs[2])
+    c1 = math.sqrt(3 / (4 * math.pi))
+    np.testing.assert_allclose(got[2, 1:4], [-c1 * d[1], c1 * d[2], -c1 * d[0]], atol=1e-14)
+
+
+@pytest.mark.parametrize("deg", [0, 1, 2, 3])
+def test_colour_from_sh(ora, deg):
+    W, H = 32, 32
+    scene = scenes.random_scene(100, seed=deg, sh_degree=deg)
+    cam = _rotated_camera(W, H)
+    proj = ora.project(scene, cam, W, H)
+    campos = np.linalg.inv(cam["viewmat"].astype(np.float64))[:3, 3]
+    dirs = scene["means"].astype(np.float64) - campos
+    Y = _real_sh_scipy(deg, dirs)
+    want = np.maximum(0, np.einsum("nk,nkc->nc", Y, scene["sh"].astype(np.float64)) + 0.5)
+    vis = proj["radius"] > 0
+    # the oracle takes the camera centre as -R^T t; the float32 view matrix is
+    # orthonormal only to ~1e-8, hence the absolute tolerance
+    np.testing.assert_allclose(proj["rgb"][vis], want[vis], rtol=0, atol=2e-8)
+
+
+@pytest.mark.parametrize("W,H,seed", [(50, 37, 0), (16, 16, 1), (33, 70, 2)])
+def test_binning_brute_force(ora, W, H, seed):
+    """The pair list is exactly the set of (tile, Gaussian) with a pixel centre of
+    the tile inside the Gaussian's square of half-width r, ordered by tile, FP32
+    depth, id; ranges delimit each tile's run."""
+    scene = scenes.random_scene(40, seed=seed, xy_range=1.6)
+    cam = _rotated_camera(W, H)
+    tile = 16
+    proj = ora.project(scene, cam, W, H, tile=tile)
+    bins = ora.bin_pairs(proj)
+    tx = (W + tile - 1) // tile
+    want = []
+    for i in range(40):
+        r = int(proj["radius"][i])
+        if r == 0:
+            continue
+        mx, my = proj["mean2d"][i]
+        tiles = set()
+        for py in range(H):
+            if abs(py - my) > r:
+                continue
+            for px in range(W):
+                if abs(px - mx) <= r:
+                    tiles.add((py // tile) * tx + px // tile)
+        assert len(tiles) == proj["tiles_touched"][i]
+        d32 = np.float32(proj["depth"][i]).view(np.uint32)
+        want += [(t, int(d32), i) for t in tiles]
+    want.sort()
+    got = [(int(k >> np.uint64(32)), int(k & np.uint64(0xFFFFFFFF)), int(v))
+           for k, v in zip(bins["keys"], bins["vals"])]
+    assert got == want
+    ranges = bins["ranges"]
+    for t in range(ranges.shape[0]):
+        s, e = ranges[t]
+        run = [g for g in got if g[0] == t]
+        assert e - s == len(run)
+        if run:
+            assert got[s:e] == run
+
+
+def test_borderline_flags_are_rare(ora):
+    W, H = 64, 64
+    scene = scenes.random_scene(1000, seed=0)
+    proj = ora.project(scene, scenes.pinhole_camera(W, H), W, H)
+    assert proj["borderline"].sum() <= 2
