@@ -1,0 +1,421 @@
+#!/usr/bin/env python
+"""Throughput of the gradient-aware spline upscaling path on GB300.
+
+One step = the whole hot path over one frame of the 1.5M-Gaussian, SH degree 3
+scene: projection + depth sort + tile binning (gs_project), the blend with
+screen-space derivatives at 960x540 (gs_render_binned), and the 2x Hermite
+upscale to 1920x1080 (gs_upscale).  The metric is output megapixels per second;
+the line also carries the direct 1920x1080 render of the same scene (the
+comparator), the PSNR of the upscaled frame against it, the 4x path from
+480x270, per-stage times, the blend kernel's roofline, an end-to-end number
+through the public API from pinned host memory, and the FP64 oracle timed on
+the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gs|reference]
+
+N > 1 runs one independent replica per GPU (the path has no exchange step);
+launch with torch.distributed.run.  --impl reference times the CPU oracle.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+N_GAUSS = 1_500_000
+LOW_W, LOW_H, FACTOR = 960, 540, 2
+OUT_W, OUT_H = LOW_W * FACTOR, LOW_H * FACTOR
+WORKLOAD = "mixture scene 1.5M Gaussians SH3, 960x540 render+grads -> 2x Hermite upscale -> 1920x1080"
+METRIC = "output MPix/s render+upscale vs direct full-res render, same GB300, at PSNR"
+# Algorithmic FP32 operations per (pixel, Gaussian) pair of the blend, counted
+# from the formulas (an FMA counts 2): evaluating the exponent g = 10; blending a
+# pair with the derivative recurrences adds 52 (kernel K6).
+FLOP_EVAL = 10
+FLOP_ACC_GRADS = 52
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gs", choices=["gs", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.t0 = self.t1 = None
+        self.lines = []
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            sel = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+        except Exception:
+            sel = str(device_index)
+        self.sel = sel
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.sel, f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def mark(self, which):
+        setattr(self, which, time.time())
+
+    def stop(self):
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        rows = []
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(f[1]), smax=float(f[2]), power=float(f[3]) if f[3] not in ("[N/A]", "") else 0.0,
+                                 active=f[4], hw=f[5], hwt=f[6], swt=f[7], swp=f[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"], "samples": 0}
+        loaded = [r for r in rows if r["power"] > 150.0] or rows
+        reasons = set()
+        for r in loaded:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("swp", "sw_power_cap")):
+                if r[key].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in loaded), "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(loaded),
+                "power_w_max": max(r["power"] for r in rows)}
+
+
+def psnr(a, b):
+    a = np.clip(a, 0.0, 1.0)
+    b = np.clip(b, 0.0, 1.0)
+    mse = float(np.mean((a.astype(np.float64) - b.astype(np.float64)) ** 2))
+    return float("inf") if mse == 0 else 10.0 * math.log10(1.0 / mse)
+
+
+# --------------------------------------------------------------------------- oracle leg
+
+def oracle_sample(scene, nthreads=None):
+    """One bounded oracle pass over the same workload: projection and binning
+    of the whole scene at 960x540, the blend with derivatives for a 128x128
+    low-res crop and the 2x upscale of its 256x256 output crop.  Returns
+    (seconds for the sample, seconds extrapolated to a full frame)."""
+    import oracle
+    import scenes
+    cam = scenes.pinhole_camera(LOW_W, LOW_H)
+    t0 = time.perf_counter()
+    proj = oracle.project(scene, cam, LOW_W, LOW_H)
+    bins = oracle.bin_pairs(proj)
+    t1 = time.perf_counter()
+    cw, ch = 128, 128
+    x0, y0 = (LOW_W - cw) // 2, (LOW_H - ch) // 2
+    ys, xs = np.mgrid[y0:y0 + ch, x0:x0 + cw]
+    pix = np.stack([xs.ravel(), ys.ravel()], 1)
+    r = oracle.render(proj, bins, pixels=pix, nthreads=nthreads)
+    C = r["out"][:, 0:3].T.reshape(3, ch, cw)
+    G = r["out"][:, 3:12].T.reshape(3, 3, ch, cw)
+    oracle.upscale(C, G, cw * FACTOR, ch * FACTOR)
+    t2 = time.perf_counter()
+    per_px = (LOW_W * LOW_H) / (cw * ch)
+    return t2 - t0, (t1 - t0) + (t2 - t1) * per_px
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    import scenes
+    scene = scenes.mixture_scene(N_GAUSS, seed=0)
+    nthreads = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle_sample(scene, nthreads)
+    frames = []
+    for _ in range(args.steps):
+        frames.append(oracle_sample(scene, nthreads)[1])
+    frame_s = sum(frames) / len(frames)
+    value = OUT_W * OUT_H / 1e6 / frame_s
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MPix/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": frame_s * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSS, "low_res": [LOW_W, LOW_H], "factor": FACTOR,
+                   "out_res": [OUT_W, OUT_H]},
+        "cpu_baseline": {"value": value, "unit": "MPix/s", "cores": nthreads, "kind": "oracle",
+                         "sample": "per step: projection + binning of all 1.5M Gaussians at 960x540, blend of a "
+                                   "128x128 low-res crop, 2x upscale of its 256x256 output crop; per-pixel "
+                                   "stages scaled by frame/crop area"},
+        "e2e": {"value": value, "unit": "MPix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- GPU leg
+
+def run_gs(args):
+    import torch
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_2503_14171_gb300 as gs
+    import scenes
+
+    scene = scenes.mixture_scene(N_GAUSS, seed=0)
+    cam = scenes.pinhole_camera(LOW_W, LOW_H)
+    cam_hi = scenes.scaled_camera(cam, FACTOR)
+    cam4 = scenes.pinhole_camera(OUT_W // 4, OUT_H // 4)
+    dev = gs.DeviceScene(scene)
+    stream = torch.cuda.Stream()
+    ctx = gs.Context(stream=stream)
+    C = torch.empty(3, LOW_H, LOW_W, device="cuda")
+    G = torch.empty(3, 3, LOW_H, LOW_W, device="cuda")
+    out = torch.empty(3, OUT_H, OUT_W, device="cuda")
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def step(evs=None):
+        if evs is not None:
+            evs[0].record(stream)
+        ctx.project(dev, cam, LOW_W, LOW_H)
+        if evs is not None:
+            evs[1].record(stream)
+        ctx.render_binned(grads=True, out_C=C, out_grads=G)
+        if evs is not None:
+            evs[2].record(stream)
+        ctx.upscale(C, G, FACTOR, out=out)
+        if evs is not None:
+            evs[3].record(stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        P_low = ctx.pair_count()
+        n_eval, n_acc = ctx.blend_stats()
+
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+        clocks = ClockSampler(local)
+        clocks.start()
+        time.sleep(0.3)
+        l0 = ctx.launch_count()
+        barrier()
+        torch.cuda.synchronize()
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for k in range(args.steps):
+            step(evs[k])
+        end.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        launches = ctx.launch_count() - l0
+        clocks.stop()
+        total_ms = start.elapsed_time(end)
+        t_proj = [e[0].elapsed_time(e[1]) for e in evs]
+        t_blend = [e[1].elapsed_time(e[2]) for e in evs]
+        t_up = [e[2].elapsed_time(e[3]) for e in evs]
+
+        t_max = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        if world > 1:
+            torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t_max.item())
+        ms_step = total_ms / args.steps
+        value = world * args.steps * OUT_W * OUT_H / 1e6 / (total_ms / 1e3)
+
+        # comparator: direct 1920x1080 render of the same scene
+        def time_loop(fn, k):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(k):
+                fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / k
+
+        direct = torch.empty(3, OUT_H, OUT_W, device="cuda")
+        kd = max(10, args.steps // 3)
+        ms_direct = time_loop(lambda: ctx.render(dev, cam_hi, OUT_W, OUT_H, out_C=direct), kd)
+        P_direct = ctx.pair_count()
+        # 4x path: 480x270 -> 1920x1080
+        C4 = torch.empty(3, OUT_H // 4, OUT_W // 4, device="cuda")
+        G4 = torch.empty(3, 3, OUT_H // 4, OUT_W // 4, device="cuda")
+        out4 = torch.empty(3, OUT_H, OUT_W, device="cuda")
+
+        def step4():
+            ctx.render_with_grads(dev, cam4, OUT_W // 4, OUT_H // 4, out_C=C4, out_grads=G4)
+            ctx.upscale(C4, G4, 4, out=out4)
+
+        ms_4x = time_loop(step4, kd)
+        # quality: the timed frames' outputs vs the direct render
+        step()
+        torch.cuda.synchronize()
+        d_np = direct.cpu().numpy()
+        psnr2 = psnr(out.cpu().numpy(), d_np)
+        psnr4 = psnr(out4.cpu().numpy(), d_np)
+
+        # end to end through the public API: pinned host scene in, image out
+        host = gs.HostScene(scene)
+        out_host = torch.empty(3, OUT_H, OUT_W, pin_memory=True)
+        ke = max(5, min(50, args.steps // 4))
+
+        def e2e_step():
+            dev.copy_from(host)
+            ctx.project(dev, cam, LOW_W, LOW_H)
+            ctx.render_binned(grads=True, out_C=C, out_grads=G)
+            ctx.upscale(C, G, FACTOR, out=out)
+            out_host.copy_(out, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(ke):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = a.elapsed_time(b) / ke
+        t_e = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+        if world > 1:
+            torch.distributed.all_reduce(t_e, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t_e.item())
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    peaks, src = _peaks()
+    clk = clocks.summary()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12    # TFLOP/s
+    blend_ms = statistics.mean(t_blend)
+    flops = n_eval * FLOP_EVAL + n_acc * FLOP_ACC_GRADS
+    achieved = flops / (blend_ms * 1e-3) / 1e12
+    traffic = _traffic_from_profiles()
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        sample_s, frame_s = oracle_sample(scene, os.cpu_count())
+        cpu = {"value": OUT_W * OUT_H / 1e6 / frame_s, "unit": "MPix/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "projection + binning of all 1.5M Gaussians at 960x540, blend of a 128x128 low-res crop, "
+                         "2x upscale of its 256x256 output crop (%.1f s); per-pixel stages scaled by frame/crop "
+                         "area" % sample_s}
+
+    h2d = dev.nbytes()
+    d2h = 3 * OUT_H * OUT_W * 4
+    line = {
+        "metric": METRIC, "value": value, "unit": "MPix/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSS, "sh_degree": 3, "low_res": [LOW_W, LOW_H],
+                   "factor": FACTOR, "out_res": [OUT_W, OUT_H], "tile": 16, "mode": "3dgs",
+                   "pairs_low_res": P_low, "l2": "inputs larger than L2 (scene %.0f MB > 129 MB)" % (h2d / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "direct_render": {"mpix_s": OUT_W * OUT_H / 1e3 / ms_direct, "ms": ms_direct, "pairs": P_direct},
+        "speedup_vs_direct": (OUT_W * OUT_H / 1e3 / ms_step) / (OUT_W * OUT_H / 1e3 / ms_direct),
+        "psnr_db": {"2x_960x540": psnr2, "4x_480x270": psnr4, "vs": "direct 1920x1080 render, clipped to [0,1]"},
+        "path_4x": {"mpix_s": OUT_W * OUT_H / 1e3 / ms_4x, "ms": ms_4x},
+        "stages_ms": {"project_bin": statistics.mean(t_proj), "blend_grads": blend_ms,
+                      "upscale": statistics.mean(t_up)},
+        "roofline": {"bound": "alu", "kernel": "k_blend<grads,3dgs>", "achieved": achieved, "peak": alu_peak,
+                     "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": traffic,
+                     "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x %.0f MHz (sm_max_mhz, %s)" % (sm_mhz, src),
+                     "pairs_evaluated": n_eval, "pairs_blended": n_acc},
+        "upscale_hbm": {"achieved_gbs": (LOW_W * LOW_H * 48 + OUT_W * OUT_H * 12) / (statistics.mean(t_up) * 1e-3) / 1e9,
+                        "peak_gbs": peaks.get("hbm_gbs"), "peak_source": src},
+        "cpu_baseline": cpu,
+        "e2e": {"value": OUT_W * OUT_H / 1e3 / e2e_ms, "unit": "MPix/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "clocks": clk,
+        "gpu_launches": launches,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def _traffic_from_profiles():
+    """DRAM bytes per blend launch from the committed ncu summary, if current."""
+    p = os.path.join(ROOT, "profiles", "blend_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("dram_bytes_per_launch")
+    except Exception:
+        return None
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gs(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

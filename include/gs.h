@@ -1,0 +1,206 @@
+/*
+ * gs.h -- C ABI of libgs: tile-binned 3D Gaussian Splatting rasterisation that
+ * also emits the analytic screen-space derivatives of each pixel colour, and the
+ * gradient-aware bicubic Hermite upscale built on them (Niedermayr, Neuhauser,
+ * Westermann, "Lightweight Gradient-Aware Upscaling of 3D Gaussian Splatting
+ * Images", ICCV 2025).  Hand-written CUDA for sm_103a (GB300).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Pointers.  Unless a parameter says "host", every array pointer is a DEVICE
+ *   pointer (cudaMalloc / torch CUDA memory on the context's device) owned by the
+ *   caller.  The library never frees caller memory and never keeps a caller
+ *   pointer beyond the call that received it.  All arrays are dense, row-major,
+ *   fp32 unless stated.
+ * Context.  A gs_ctx owns only scratch memory (per-Gaussian records, sort
+ *   buffers, per-tile ranges, per-pixel blend state) and a CUDA stream handle.
+ *   One context must not be used from two host threads at once.
+ * Streams.  Work is enqueued on the context's stream and is asynchronous,
+ *   except where a call says it synchronises.  gs_project (and the render calls
+ *   that include it) read the number of (tile, Gaussian) pairs back to the host
+ *   once per call, which synchronises the context's stream.
+ * Errors.  Every call returns a gs_status; nothing throws across the ABI.
+ *   GS_ERR_INVALID_ARG: a NULL pointer where one is required, a negative count,
+ *     an image side < 1 (< 2 for the upscale input), an unsupported option.
+ *   GS_ERR_CUDA: a CUDA runtime error (gs_last_error() has the text).
+ *   GS_ERR_OOM: scratch could not be allocated.
+ *   GS_ERR_CAPACITY: the pair count exceeds gs_options.max_pairs (or 2^30 - 1);
+ *     nothing is written out of bounds.
+ *   GS_ERR_TIMEOUT / GS_ERR_DEVICE_CHECK: a kernel's bounded wait expired or a
+ *     device-side check failed; the outputs of that call are undefined, the
+ *     context stays usable.
+ * Image layout.  Planar: channel-major [3][H][W] colour, derivative stacks
+ *   [3 (d/dx, d/dy, d2/dxdy)][3][H][W].  Pixel (i, j) (column i, row j) is the
+ *   continuous image point (i, j); x grows with the column, y with the row.
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gs_status {
+    GS_OK = 0,
+    GS_ERR_INVALID_ARG = 1,
+    GS_ERR_CUDA = 2,
+    GS_ERR_OOM = 3,
+    GS_ERR_CAPACITY = 4,
+    GS_ERR_TIMEOUT = 5,
+    GS_ERR_DEVICE_CHECK = 6,
+    GS_ERR_NOT_READY = 7
+} gs_status;
+
+/* Blend modes.  GS_MODE_3DGS: alpha = min(0.99, sigma e^g), pairs with
+ * alpha < 1/255 are skipped, a pixel stops before the Gaussian that would take
+ * its transmittance below 1e-4, tile sets are the rects of radius
+ * ceil(3 sqrt(lambda_max)).  GS_MODE_EXACT: none of these cut-offs, every visible
+ * Gaussian is binned into every tile (a smooth image; meant for small scenes). */
+#define GS_MODE_3DGS 0
+#define GS_MODE_EXACT 1
+
+typedef struct gs_ctx gs_ctx;
+
+/* A set of 3D Gaussians (Sec. 4: centre mu, covariance Sigma = R S S^T R^T from a
+ * scale and a rotation, opacity sigma, spherical-harmonics colour).  Device
+ * pointers, structure-of-arrays:
+ *   means          [n][3]                world-space centre
+ *   log_scales     [n][3]                log of the per-axis standard deviation
+ *   quats          [n][4]                rotation quaternion (w, x, y, z); normalised here
+ *   opacity_logits [n]                   sigma = 1 / (1 + e^-logit)
+ *   sh             [n][(deg+1)^2][3]     real SH coefficients, index l^2 + l + m,
+ *                                        colour = max(0, sum_k sh_k Y_k(dir) + 1/2),
+ *                                        dir from the camera centre to mu; or NULL
+ *   rgb            [n][3]                direct colour, used when sh == NULL */
+typedef struct gs_gaussians {
+    int64_t n;
+    int32_t sh_degree;            /* 0..3, ignored when sh == NULL */
+    int32_t reserved;
+    const float* means;
+    const float* log_scales;
+    const float* quats;
+    const float* opacity_logits;
+    const float* sh;
+    const float* rgb;
+} gs_gaussians;
+
+/* Pinhole camera, passed by value from the host.  viewmat: row-major 4x4
+ * world->camera (x right, y down, z forward); pixel = (fx x/z + cx, fy y/z + cy);
+ * Gaussians with view depth z <= znear are culled. */
+typedef struct gs_camera {
+    float viewmat[16];
+    float fx, fy, cx, cy;
+    float znear;
+} gs_camera;
+
+typedef struct gs_options {
+    int32_t tile;        /* tile side in pixels; 16 is the only supported value */
+    int32_t mode;        /* GS_MODE_3DGS or GS_MODE_EXACT */
+    float bg[3];         /* background colour composited behind the Gaussians */
+    int32_t reserved;
+    int64_t max_pairs;   /* upper bound on (tile, Gaussian) pairs; 0 = 2^30 - 1 */
+} gs_options;
+
+/* Human-readable name of a status code (static string). */
+const char* gs_status_string(gs_status status);
+
+/* Text of the last error recorded on ctx (static per context; "" if none). */
+const char* gs_last_error(const gs_ctx* ctx);
+
+/* Create a context on the current CUDA device.  stream: a cudaStream_t (NULL =
+ * the legacy default stream).  opt may be NULL (tile 16, 3DGS mode, black
+ * background, no pair limit).  *out receives the context; free it with
+ * gs_destroy. */
+gs_status gs_create(gs_ctx** out, void* stream, const gs_options* opt);
+
+/* Release the context and its scratch memory (synchronises its stream). */
+gs_status gs_destroy(gs_ctx* ctx);
+
+/* Change the stream later calls enqueue on. */
+gs_status gs_set_stream(gs_ctx* ctx, void* stream);
+
+/* Change blend mode / background / pair limit for later calls. */
+gs_status gs_set_options(gs_ctx* ctx, const gs_options* opt);
+
+/* Projection and tile binning for a W x H image (Sec. 4: EWA projection
+ * Sigma' = J W Sigma W^T J^T + 0.3 I, front-to-back order).  Per Gaussian: view
+ * depth, 2D mean, conic Sigma'^-1, colour, opacity, radius ceil(3 sqrt(lambda_max))
+ * and the tiles whose pixel centres fall in the square of that half-width; then
+ * every (tile, Gaussian) pair is ordered by tile, FP32 depth bits, id.  Results
+ * stay in ctx for gs_render_binned / gs_read_projected / gs_read_bins.
+ * Synchronises the stream once (pair count readback). */
+gs_status gs_project(gs_ctx* ctx, const gs_gaussians* g, const gs_camera* cam, int32_t W, int32_t H);
+
+/* Blend the scene binned by the last gs_project.  Per pixel, front to back
+ * (Sec. 4 blend; Sec. 5 and supplement "Forward pass" recurrences):
+ *   C = sum_i T_i alpha_i c_i + T_N bg, with T_i = 1 - A_{i-1},
+ * and, when out_grads != NULL, dC/dx, dC/dy, d2C/dxdy accumulated through the
+ * same loop.  out_C [3][H][W] (required); out_grads [3][3][H][W] or NULL (then only
+ * the plain colour is computed).  The per-pixel final transmittance state is kept
+ * in ctx (gs_read_state). */
+gs_status gs_render_binned(gs_ctx* ctx, float* out_C, float* out_grads);
+
+/* gs_project followed by gs_render_binned with derivatives: the low-resolution
+ * render of the method (Sec. 5, pipeline figure).  out_C [3][H][W],
+ * out_grads [3][3][H][W], both required. */
+gs_status gs_render_with_grads(gs_ctx* ctx, const gs_gaussians* g, const gs_camera* cam,
+                               int32_t W, int32_t H, float* out_C, float* out_grads);
+
+/* gs_project followed by a plain blend (colour only): the direct
+ * full-resolution render the method is compared against (Table 2 "3DGS"). */
+gs_status gs_render(gs_ctx* ctx, const gs_gaussians* g, const gs_camera* cam,
+                    int32_t W, int32_t H, float* out_C);
+
+/* Gradient-aware bicubic Hermite upscale (Sec. 5 "Spline Interpolation";
+ * supplement "Spline Image Interpolation").  For every output pixel (X, Y) of
+ * the factor*W x factor*H image: x = (X + 0.5)/factor - 0.5 (likewise y), cell
+ * i = clamp(floor(x), 0, W-2), t = x - i; the patch of cell (i, j) matches the
+ * four corner values and their d/dx, d/dy, d2/dxdy; border half-cells
+ * extrapolate the edge patch.  C [3][H][W], grads [3][3][H][W] (as written by the
+ * render), out [3][factor*H][factor*W].  W, H >= 2; 1 <= factor <= 16.
+ * Asynchronous. */
+gs_status gs_upscale(gs_ctx* ctx, const float* C, const float* grads, int32_t W, int32_t H,
+                     int32_t factor, float* out);
+
+/* Number of (tile, Gaussian) pairs of the last gs_project (host int64). */
+gs_status gs_pair_count(const gs_ctx* ctx, int64_t* P);
+
+/* Copy the last gs_project's per-Gaussian results to caller device buffers (any
+ * may be NULL): mean2d [n][2], conic [n][3] (Sigma'^-1 as a, b, c), rgb [n][3],
+ * opacity [n], depth [n], radius [n] (int32, 0 = culled), tiles_touched [n]. */
+gs_status gs_read_projected(gs_ctx* ctx, float* mean2d, float* conic, float* rgb, float* opacity,
+                            float* depth, int32_t* radius, int32_t* tiles_touched);
+
+/* Copy the last gs_project's sorted pair list and per-tile ranges to caller
+ * device buffers: keys [P] (tile << 32 | FP32 depth bits), vals [P] (Gaussian id),
+ * ranges [tiles][2] ([start, end) into the list; [0, 0) for an empty tile),
+ * tiles = ceil(W/16) * ceil(H/16).  capacity: the length of keys/vals; fails
+ * with GS_ERR_CAPACITY if P > capacity.  Any pointer may be NULL. */
+gs_status gs_read_bins(gs_ctx* ctx, uint64_t* keys, uint32_t* vals, uint32_t* ranges, int64_t capacity);
+
+/* Copy the per-pixel state of the last blend: state [4][H][W] = transmittance
+ * T_N = 1 - A_N and its d/dx, d/dy, d2/dxdy; count [H][W] (int32) = 1 + the list
+ * position of the last Gaussian blended (0 = none).  Either may be NULL. */
+gs_status gs_read_state(gs_ctx* ctx, float* state, int32_t* count);
+
+/* Work counts of a blend of the last gs_project's binning (3DGS or exact mode
+ * as configured): counts[0] = (pixel, Gaussian) pairs evaluated, counts[1] =
+ * pairs blended, summed over the image (host int64[2]).  Runs a counting
+ * variant of the blend kernel that writes no image; synchronises. */
+gs_status gs_blend_stats(gs_ctx* ctx, int64_t* counts);
+
+/* Number of kernels libgs has launched on behalf of ctx since gs_create (host
+ * int64; counts every kernel of every call, e.g. for launch accounting). */
+gs_status gs_launch_count(const gs_ctx* ctx, int64_t* count);
+
+/* Wait for the context's stream and report any device-side error recorded by
+ * its kernels since the last check (GS_ERR_TIMEOUT / GS_ERR_DEVICE_CHECK). */
+gs_status gs_synchronize(gs_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_H */

@@ -1,0 +1,346 @@
+"""Python binding of libgs (include/gs.h): gradient-aware spline upscaling of
+3D Gaussian Splatting images on GB300.
+
+Argument marshalling only: every step of the path runs in the CUDA kernels of
+libgs.so; PyTorch supplies device memory and streams.  Importing this package
+loads the in-tree library and fails loudly if it has not been built
+(``python -c "import __graft_entry__ as g; g.build()"``).
+
+Low-level entry points carry the C names (``gs_create``, ``gs_project``,
+``gs_render_with_grads``, ``gs_render``, ``gs_upscale`` ...) and take raw
+pointers; :class:`Context` wraps them for torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libgs.so")
+
+GS_OK = 0
+GS_ERR_INVALID_ARG = 1
+GS_ERR_CUDA = 2
+GS_ERR_OOM = 3
+GS_ERR_CAPACITY = 4
+GS_ERR_TIMEOUT = 5
+GS_ERR_DEVICE_CHECK = 6
+GS_ERR_NOT_READY = 7
+GS_MODE_3DGS = 0
+GS_MODE_EXACT = 1
+MODES = {"3dgs": GS_MODE_3DGS, "exact": GS_MODE_EXACT}
+
+
+class GsGaussians(ct.Structure):
+    _fields_ = [("n", ct.c_int64), ("sh_degree", ct.c_int32), ("reserved", ct.c_int32),
+                ("means", ct.c_void_p), ("log_scales", ct.c_void_p), ("quats", ct.c_void_p),
+                ("opacity_logits", ct.c_void_p), ("sh", ct.c_void_p), ("rgb", ct.c_void_p)]
+
+
+class GsCamera(ct.Structure):
+    _fields_ = [("viewmat", ct.c_float * 16), ("fx", ct.c_float), ("fy", ct.c_float),
+                ("cx", ct.c_float), ("cy", ct.c_float), ("znear", ct.c_float)]
+
+
+class GsOptions(ct.Structure):
+    _fields_ = [("tile", ct.c_int32), ("mode", ct.c_int32), ("bg", ct.c_float * 3),
+                ("reserved", ct.c_int32), ("max_pairs", ct.c_int64)]
+
+
+# name -> argtypes (all return gs_status except gs_status_string / gs_last_error)
+_P = ct.c_void_p
+_SIGS = {
+    "gs_status_string": ([ct.c_int], ct.c_char_p),
+    "gs_last_error": ([_P], ct.c_char_p),
+    "gs_create": ([ct.POINTER(_P), _P, ct.POINTER(GsOptions)], ct.c_int),
+    "gs_destroy": ([_P], ct.c_int),
+    "gs_set_stream": ([_P, _P], ct.c_int),
+    "gs_set_options": ([_P, ct.POINTER(GsOptions)], ct.c_int),
+    "gs_project": ([_P, ct.POINTER(GsGaussians), ct.POINTER(GsCamera), ct.c_int32, ct.c_int32], ct.c_int),
+    "gs_render_binned": ([_P, _P, _P], ct.c_int),
+    "gs_render_with_grads": ([_P, ct.POINTER(GsGaussians), ct.POINTER(GsCamera), ct.c_int32, ct.c_int32, _P, _P],
+                             ct.c_int),
+    "gs_render": ([_P, ct.POINTER(GsGaussians), ct.POINTER(GsCamera), ct.c_int32, ct.c_int32, _P], ct.c_int),
+    "gs_upscale": ([_P, _P, _P, ct.c_int32, ct.c_int32, ct.c_int32, _P], ct.c_int),
+    "gs_pair_count": ([_P, ct.POINTER(ct.c_int64)], ct.c_int),
+    "gs_read_projected": ([_P, _P, _P, _P, _P, _P, _P, _P], ct.c_int),
+    "gs_read_bins": ([_P, _P, _P, _P, ct.c_int64], ct.c_int),
+    "gs_read_state": ([_P, _P, _P], ct.c_int),
+    "gs_launch_count": ([_P, ct.POINTER(ct.c_int64)], ct.c_int),
+    "gs_blend_stats": ([_P, _P], ct.c_int),
+    "gs_synchronize": ([_P], ct.c_int),
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libgs.so is not built ({LIB_PATH}); run paper_2503_14171_gb300.build.build() "
+                          "or __graft_entry__.build() on a machine with nvcc")
+    lib = ct.CDLL(LIB_PATH)
+    for name, (args, res) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+lib = _load()
+
+
+class GSError(RuntimeError):
+    def __init__(self, status: int, msg: str = ""):
+        self.status = status
+        name = lib.gs_status_string(status).decode()
+        super().__init__(f"{name}: {msg}" if msg else name)
+
+
+def exported_symbols():
+    return sorted(_SIGS)
+
+
+# ---- thin wrappers with the C names ----------------------------------------
+
+def gs_status_string(status: int) -> str:
+    return lib.gs_status_string(status).decode()
+
+
+def gs_last_error(ctx) -> str:
+    return lib.gs_last_error(ctx).decode()
+
+
+def gs_create(stream=None, options: GsOptions | None = None):
+    h = _P()
+    st = lib.gs_create(ct.byref(h), stream, ct.byref(options) if options is not None else None)
+    if st != GS_OK:
+        raise GSError(st, "gs_create")
+    return h
+
+
+def _chk(st, ctx, what):
+    if st != GS_OK:
+        raise GSError(st, f"{what}: {gs_last_error(ctx)}")
+
+
+def gs_destroy(ctx):
+    _chk(lib.gs_destroy(ctx), None, "gs_destroy")
+
+
+def gs_project(ctx, g: GsGaussians, cam: GsCamera, W: int, H: int):
+    _chk(lib.gs_project(ctx, ct.byref(g), ct.byref(cam), W, H), ctx, "gs_project")
+
+
+def gs_render_binned(ctx, out_C: int, out_grads: int | None):
+    _chk(lib.gs_render_binned(ctx, out_C, out_grads), ctx, "gs_render_binned")
+
+
+def gs_render_with_grads(ctx, g: GsGaussians, cam: GsCamera, W: int, H: int, out_C: int, out_grads: int):
+    _chk(lib.gs_render_with_grads(ctx, ct.byref(g), ct.byref(cam), W, H, out_C, out_grads), ctx,
+         "gs_render_with_grads")
+
+
+def gs_render(ctx, g: GsGaussians, cam: GsCamera, W: int, H: int, out_C: int):
+    _chk(lib.gs_render(ctx, ct.byref(g), ct.byref(cam), W, H, out_C), ctx, "gs_render")
+
+
+def gs_upscale(ctx, C: int, grads: int, W: int, H: int, factor: int, out: int):
+    _chk(lib.gs_upscale(ctx, C, grads, W, H, factor, out), ctx, "gs_upscale")
+
+
+def gs_synchronize(ctx):
+    _chk(lib.gs_synchronize(ctx), ctx, "gs_synchronize")
+
+
+# ---- torch-facing helpers ----------------------------------------------------
+
+def _torch():
+    import torch
+    return torch
+
+
+def make_camera(cam: dict) -> GsCamera:
+    c = GsCamera()
+    vm = np.asarray(cam["viewmat"], np.float32).reshape(16)
+    for k in range(16):
+        c.viewmat[k] = float(vm[k])
+    c.fx, c.fy, c.cx, c.cy = float(cam["fx"]), float(cam["fy"]), float(cam["cx"]), float(cam["cy"])
+    c.znear = float(cam.get("znear", 0.2))
+    return c
+
+
+class DeviceScene:
+    """A Gaussian set resident on the GPU (fp32, contiguous) and its gs_gaussians view."""
+
+    FIELDS = ("means", "log_scales", "quats", "opacity_logits", "sh", "rgb")
+
+    def __init__(self, scene: dict, device="cuda", tensors: dict | None = None):
+        torch = _torch()
+        self.t = {}
+        if tensors is not None:
+            self.t = dict(tensors)
+        else:
+            for k in self.FIELDS:
+                if k in scene and scene[k] is not None:
+                    self.t[k] = torch.as_tensor(np.ascontiguousarray(scene[k], np.float32)).to(device)
+        self.n = int(self.t["means"].shape[0])
+        self.sh_degree = int(scene.get("sh_degree", 0)) if "sh" in self.t else 0
+        self.struct = self._make()
+
+    def _make(self) -> GsGaussians:
+        g = GsGaussians()
+        g.n = self.n
+        g.sh_degree = self.sh_degree
+        for k in self.FIELDS:
+            v = self.t.get(k)
+            if v is not None:
+                assert v.is_contiguous() and v.dtype == _torch().float32
+            setattr(g, k, v.data_ptr() if v is not None and v.numel() > 0 else None)
+        return g
+
+    def copy_from(self, host: "HostScene", non_blocking=True):
+        for k, v in host.t.items():
+            self.t[k].copy_(v, non_blocking=non_blocking)
+
+    def nbytes(self) -> int:
+        return sum(v.numel() * 4 for v in self.t.values())
+
+
+class HostScene:
+    """The same fields in pinned host memory (for end-to-end timing)."""
+
+    def __init__(self, scene: dict):
+        torch = _torch()
+        self.t = {}
+        for k in DeviceScene.FIELDS:
+            if k in scene and scene[k] is not None:
+                self.t[k] = torch.as_tensor(np.ascontiguousarray(scene[k], np.float32)).pin_memory()
+
+
+class Context:
+    """Owns a gs_ctx bound to a torch CUDA stream (default: the current stream)."""
+
+    def __init__(self, mode: str | int = "3dgs", bg=(0.0, 0.0, 0.0), stream=None, max_pairs: int = 0):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("libgs needs a CUDA device")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.opt = GsOptions()
+        self.opt.tile = 16
+        self.opt.mode = MODES[mode] if isinstance(mode, str) else int(mode)
+        for k in range(3):
+            self.opt.bg[k] = float(bg[k])
+        self.opt.max_pairs = int(max_pairs)
+        self.h = gs_create(ct.c_void_p(self.stream.cuda_stream), self.opt)
+        self.W = self.H = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            gs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_options(self, mode=None, bg=None, max_pairs=None):
+        if mode is not None:
+            self.opt.mode = MODES[mode] if isinstance(mode, str) else int(mode)
+        if bg is not None:
+            for k in range(3):
+                self.opt.bg[k] = float(bg[k])
+        if max_pairs is not None:
+            self.opt.max_pairs = int(max_pairs)
+        _chk(lib.gs_set_options(self.h, ct.byref(self.opt)), self.h, "gs_set_options")
+
+    def _empty(self, *shape, dtype=None):
+        torch = _torch()
+        return torch.empty(*shape, dtype=dtype or torch.float32, device="cuda")
+
+    def project(self, scene: DeviceScene, cam: dict, W: int, H: int):
+        gs_project(self.h, scene.struct, make_camera(cam), W, H)
+        self.W, self.H, self.n = W, H, scene.n
+
+    def render_binned(self, grads: bool = True, out_C=None, out_grads=None):
+        C = out_C if out_C is not None else self._empty(3, self.H, self.W)
+        G = None
+        if grads:
+            G = out_grads if out_grads is not None else self._empty(3, 3, self.H, self.W)
+        gs_render_binned(self.h, C.data_ptr(), G.data_ptr() if G is not None else None)
+        return (C, G) if grads else C
+
+    def render_with_grads(self, scene: DeviceScene, cam: dict, W: int, H: int, out_C=None, out_grads=None):
+        C = out_C if out_C is not None else self._empty(3, H, W)
+        G = out_grads if out_grads is not None else self._empty(3, 3, H, W)
+        gs_render_with_grads(self.h, scene.struct, make_camera(cam), W, H, C.data_ptr(), G.data_ptr())
+        self.W, self.H, self.n = W, H, scene.n
+        return C, G
+
+    def render(self, scene: DeviceScene, cam: dict, W: int, H: int, out_C=None):
+        C = out_C if out_C is not None else self._empty(3, H, W)
+        gs_render(self.h, scene.struct, make_camera(cam), W, H, C.data_ptr())
+        self.W, self.H, self.n = W, H, scene.n
+        return C
+
+    def upscale(self, C, grads, factor: int, out=None):
+        H, W = int(C.shape[-2]), int(C.shape[-1])
+        assert C.is_contiguous() and grads.is_contiguous()
+        o = out if out is not None else self._empty(3, H * factor, W * factor)
+        gs_upscale(self.h, C.data_ptr(), grads.data_ptr(), W, H, factor, o.data_ptr())
+        return o
+
+    def pair_count(self) -> int:
+        P = ct.c_int64()
+        _chk(lib.gs_pair_count(self.h, ct.byref(P)), self.h, "gs_pair_count")
+        return int(P.value)
+
+    def read_projected(self) -> dict:
+        torch = _torch()
+        n = self.n
+        out = dict(mean2d=self._empty(n, 2), conic=self._empty(n, 3), rgb=self._empty(n, 3),
+                   opacity=self._empty(n), depth=self._empty(n),
+                   radius=self._empty(n, dtype=torch.int32), tiles_touched=self._empty(n, dtype=torch.int32))
+        _chk(lib.gs_read_projected(self.h, *(out[k].data_ptr() for k in
+                                             ("mean2d", "conic", "rgb", "opacity", "depth", "radius",
+                                              "tiles_touched"))), self.h, "gs_read_projected")
+        return out
+
+    def read_bins(self):
+        torch = _torch()
+        P = self.pair_count()
+        T = ((self.W + 15) // 16) * ((self.H + 15) // 16)
+        keys = self._empty(max(P, 1), dtype=torch.int64)
+        vals = self._empty(max(P, 1), dtype=torch.int32)
+        ranges = self._empty(T, 2, dtype=torch.int32)
+        _chk(lib.gs_read_bins(self.h, keys.data_ptr(), vals.data_ptr(), ranges.data_ptr(), max(P, 1)),
+             self.h, "gs_read_bins")
+        return keys[:P], vals[:P], ranges
+
+    def read_state(self):
+        torch = _torch()
+        state = self._empty(4, self.H, self.W)
+        count = self._empty(self.H, self.W, dtype=torch.int32)
+        _chk(lib.gs_read_state(self.h, state.data_ptr(), count.data_ptr()), self.h, "gs_read_state")
+        return state, count
+
+    def blend_stats(self):
+        """(pairs evaluated, pairs blended) of the current binning."""
+        counts = (ct.c_int64 * 2)()
+        _chk(lib.gs_blend_stats(self.h, ct.cast(counts, ct.c_void_p)), self.h, "gs_blend_stats")
+        return int(counts[0]), int(counts[1])
+
+    def launch_count(self) -> int:
+        n = ct.c_int64()
+        _chk(lib.gs_launch_count(self.h, ct.byref(n)), self.h, "gs_launch_count")
+        return int(n.value)
+
+    def synchronize(self):
+        gs_synchronize(self.h)

@@ -1,0 +1,489 @@
+// C ABI of libgs (declared in include/gs.h): context, scratch management and the
+// orchestration of the kernels of each call.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "gs_internal.cuh"
+
+using namespace gs;
+
+int64_t& gs::launch_counter()
+{
+    thread_local int64_t count = 0;
+    return count;
+}
+
+namespace {
+
+// Adds the kernels launched during one API call to the context's tally.
+struct LaunchTally {
+    gs_ctx* c;
+    int64_t start;
+    explicit LaunchTally(gs_ctx* ctx) : c(ctx), start(launch_counter()) {}
+    ~LaunchTally()
+    {
+        if (c) c->launches += launch_counter() - start;
+    }
+};
+
+gs_status fail(gs_ctx* c, gs_status st, const char* fmt, ...)
+{
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+gs_status cuda_fail(gs_ctx* c, cudaError_t e, const char* where)
+{
+    cudaGetLastError();   // clear a sticky-free error so the context stays usable
+    return fail(c, e == cudaErrorMemoryAllocation ? GS_ERR_OOM : GS_ERR_CUDA, "%s: %s", where,
+                cudaGetErrorString(e));
+}
+
+#define GS_CUDA(ctx, expr)                                    \
+    do {                                                      \
+        cudaError_t e_ = (expr);                              \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #expr); \
+    } while (0)
+
+// Grow a scratch buffer to at least `bytes` (1.25x headroom).  Frees only after
+// the stream has drained, so in-flight kernels never lose their memory.
+gs_status ensure(gs_ctx* c, DevBuf& b, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    if (b.cap >= bytes) return GS_OK;
+    size_t want = bytes + bytes / 4;
+    if (b.p) {
+        GS_CUDA(c, cudaStreamSynchronize(c->stream));
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.cap = 0;
+    }
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, GS_ERR_OOM, "cudaMalloc(%zu) failed: %s", want, cudaGetErrorString(e));
+    }
+    b.cap = want;
+    return GS_OK;
+}
+
+void release(DevBuf& b)
+{
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+template <typename T>
+T* as(DevBuf& b)
+{
+    return reinterpret_cast<T*>(b.p);
+}
+
+int bits_for(uint32_t v)   // number of bits to represent values < v (v >= 1)
+{
+    int b = 0;
+    while (b < 32 && (uint64_t(1) << b) < v) ++b;
+    return b;
+}
+
+gs_status check_options(gs_ctx* c, const gs_options* o)
+{
+    if (o->tile != kTile) return fail(c, GS_ERR_INVALID_ARG, "tile must be %d", kTile);
+    if (o->mode != GS_MODE_3DGS && o->mode != GS_MODE_EXACT) return fail(c, GS_ERR_INVALID_ARG, "bad mode");
+    if (o->max_pairs < 0) return fail(c, GS_ERR_INVALID_ARG, "max_pairs < 0");
+    return GS_OK;
+}
+
+gs_status check_gaussians(gs_ctx* c, const gs_gaussians* g)
+{
+    if (!g) return fail(c, GS_ERR_INVALID_ARG, "gaussians == NULL");
+    if (g->n < 0 || g->n > 0x7FFFFFFF) return fail(c, GS_ERR_INVALID_ARG, "n out of range");
+    if (g->n == 0) return GS_OK;
+    if (!g->means || !g->log_scales || !g->quats || !g->opacity_logits)
+        return fail(c, GS_ERR_INVALID_ARG, "a required Gaussian array is NULL");
+    if (!g->sh && !g->rgb) return fail(c, GS_ERR_INVALID_ARG, "both sh and rgb are NULL");
+    if (g->sh && (g->sh_degree < 0 || g->sh_degree > 3)) return fail(c, GS_ERR_INVALID_ARG, "sh_degree not in 0..3");
+    return GS_OK;
+}
+
+CameraParams make_camera(const gs_camera& cam, int W, int H)
+{
+    CameraParams p;
+    for (int r = 0; r < 3; ++r) {
+        for (int k = 0; k < 3; ++k) p.R[3 * r + k] = cam.viewmat[4 * r + k];
+        p.t[r] = cam.viewmat[4 * r + 3];
+    }
+    for (int k = 0; k < 3; ++k)
+        p.campos[k] = -(p.R[0 * 3 + k] * p.t[0] + p.R[1 * 3 + k] * p.t[1] + p.R[2 * 3 + k] * p.t[2]);
+    p.fx = cam.fx;
+    p.fy = cam.fy;
+    p.cx = cam.cx;
+    p.cy = cam.cy;
+    p.znear = cam.znear;
+    p.lim_x = 1.3f * ((float)W / (2.f * cam.fx));
+    p.lim_y = 1.3f * ((float)H / (2.f * cam.fy));
+    return p;
+}
+
+gs_status read_device_error(gs_ctx* c)
+{
+    int h = 0;
+    GS_CUDA(c, cudaMemcpyAsync(&h, c->errword.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (h != kDevOk) {
+        GS_CUDA(c, cudaMemsetAsync(c->errword.p, 0, sizeof(int), c->stream));
+        if (h == kDevTimeout) return fail(c, GS_ERR_TIMEOUT, "a bounded device wait expired");
+        return fail(c, GS_ERR_DEVICE_CHECK, "a device-side check failed (code %d)", h);
+    }
+    return GS_OK;
+}
+
+gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int W, int H)
+{
+    if (!cam) return fail(c, GS_ERR_INVALID_ARG, "camera == NULL");
+    if (W < 1 || H < 1 || W > (1 << 20) || H > (1 << 20)) return fail(c, GS_ERR_INVALID_ARG, "bad image size");
+    gs_status st = check_gaussians(c, g);
+    if (st != GS_OK) return st;
+    if (!(cam->fx > 0.f) || !(cam->fy > 0.f)) return fail(c, GS_ERR_INVALID_ARG, "fx, fy must be > 0");
+    c->have_proj = false;
+    c->have_state = false;
+    const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
+    const int64_t T = (int64_t)tiles_x * tiles_y;
+    if (T > 0x7FFFFFFF) return fail(c, GS_ERR_INVALID_ARG, "too many tiles");
+    const uint32_t n = (uint32_t)g->n;
+
+    // per-Gaussian scratch
+    if ((st = ensure(c, c->rec0, sizeof(float4) * n)) || (st = ensure(c, c->rec1, sizeof(float4) * n)) ||
+        (st = ensure(c, c->rec2, sizeof(float4) * n)) || (st = ensure(c, c->depth, sizeof(float) * n)) ||
+        (st = ensure(c, c->radius, sizeof(int) * n)) || (st = ensure(c, c->rect, sizeof(int4) * n)) ||
+        (st = ensure(c, c->tiles_touched, sizeof(uint32_t) * n)) ||
+        (st = ensure(c, c->dkey[0], sizeof(uint32_t) * n)) || (st = ensure(c, c->dkey[1], sizeof(uint32_t) * n)) ||
+        (st = ensure(c, c->did[0], sizeof(uint32_t) * n)) || (st = ensure(c, c->did[1], sizeof(uint32_t) * n)) ||
+        (st = ensure(c, c->offsets, sizeof(uint32_t) * (n + 1))) ||
+        (st = ensure(c, c->scan_partials, sizeof(unsigned long long) * scan_partials_count(n))) ||
+        (st = ensure(c, c->ranges, sizeof(uint2) * T)) || (st = ensure(c, c->sort_hist, sizeof(uint32_t) * 8 * 256)) ||
+        (st = ensure(c, c->sort_counter, sizeof(uint32_t) * 8)))
+        return st;
+
+    const Records rec{as<float4>(c->rec0), as<float4>(c->rec1), as<float4>(c->rec2)};
+    const CameraParams cp = make_camera(*cam, W, H);
+    GS_CUDA(c, launch_project(c->stream, *g, cp, W, H, tiles_x, tiles_y, c->opt.mode, rec, as<float>(c->depth),
+                              as<int>(c->radius), as<int4>(c->rect), as<uint32_t>(c->tiles_touched),
+                              as<uint32_t>(c->dkey[0]), as<uint32_t>(c->did[0])));
+
+    // depth order: stable radix sort of the FP32 depth bits (ids ascending)
+    int sorted = 0;
+    if (n > 1) {
+        if ((st = ensure(c, c->sort_status, sizeof(uint32_t) * radix_status_words(n, 0, 32)))) return st;
+        uint32_t* keys[2] = {as<uint32_t>(c->dkey[0]), as<uint32_t>(c->dkey[1])};
+        uint32_t* vals[2] = {as<uint32_t>(c->did[0]), as<uint32_t>(c->did[1])};
+        GS_CUDA(c, radix_sort_u32_pairs(c->stream, keys, vals, n, 0, 32, as<uint32_t>(c->sort_hist),
+                                        as<uint32_t>(c->sort_status), as<uint32_t>(c->sort_counter),
+                                        as<int>(c->errword), &sorted));
+    }
+    c->sorted_ids_buf = sorted;
+    const uint32_t* ids = as<uint32_t>(c->did[sorted]);
+
+    // pair offsets in depth order and the exact pair count
+    GS_CUDA(c, launch_scan_gathered(c->stream, as<uint32_t>(c->tiles_touched), ids, n, as<uint32_t>(c->offsets),
+                                    as<unsigned long long>(c->scan_partials)));
+    const size_t nb = scan_partials_count(n) - 1;
+    GS_CUDA(c, cudaMemcpyAsync(c->h_scalar, as<unsigned long long>(c->scan_partials) + (n ? nb : 0),
+                               sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    const unsigned long long P64 = *c->h_scalar;
+    const int64_t limit = c->opt.max_pairs > 0 ? std::min<int64_t>(c->opt.max_pairs, kMaxPairs) : kMaxPairs;
+    if ((int64_t)P64 > limit)
+        return fail(c, GS_ERR_CAPACITY, "pair count %llu exceeds the limit %lld", P64, (long long)limit);
+    const uint32_t P = (uint32_t)P64;
+    if ((st = read_device_error(c))) return st;
+
+    if ((st = ensure(c, c->pairs[0], sizeof(uint64_t) * P)) || (st = ensure(c, c->pairs[1], sizeof(uint64_t) * P)))
+        return st;
+    uint64_t* pairs[2] = {as<uint64_t>(c->pairs[0]), as<uint64_t>(c->pairs[1])};
+    GS_CUDA(c, launch_emit_pairs(c->stream, ids, as<uint32_t>(c->offsets), as<int4>(c->rect), n, tiles_x, pairs[0]));
+    int psorted = 0;
+    if (P > 1 && T > 1) {
+        const int tbits = bits_for((uint32_t)T);
+        if ((st = ensure(c, c->sort_status, sizeof(uint32_t) * radix_status_words(P, 32, 32 + tbits)))) return st;
+        GS_CUDA(c, radix_sort_u64_keys(c->stream, pairs, P, 32, 32 + tbits, as<uint32_t>(c->sort_hist),
+                                       as<uint32_t>(c->sort_status), as<uint32_t>(c->sort_counter),
+                                       as<int>(c->errword), &psorted));
+    }
+    c->sorted_pairs_buf = psorted;
+    GS_CUDA(c, cudaMemsetAsync(c->ranges.p, 0, sizeof(uint2) * T, c->stream));
+    GS_CUDA(c, launch_tile_ranges(c->stream, pairs[psorted], P, (uint32_t)T, as<uint2>(c->ranges)));
+
+    c->n = n;
+    c->W = W;
+    c->H = H;
+    c->tiles_x = tiles_x;
+    c->tiles_y = tiles_y;
+    c->P = P;
+    c->have_proj = true;
+    return GS_OK;
+}
+
+gs_status do_blend(gs_ctx* c, float* out_C, float* out_grads)
+{
+    if (!c->have_proj) return fail(c, GS_ERR_NOT_READY, "no projection: call gs_project first");
+    if (!out_C) return fail(c, GS_ERR_INVALID_ARG, "out_C == NULL");
+    const size_t npix = (size_t)c->W * c->H;
+    gs_status st;
+    if ((st = ensure(c, c->state, sizeof(float4) * npix)) || (st = ensure(c, c->count, sizeof(int) * npix))) return st;
+    const Records rec{as<float4>(c->rec0), as<float4>(c->rec1), as<float4>(c->rec2)};
+    GS_CUDA(c, launch_blend(c->stream, out_grads != nullptr, c->opt.mode, c->W, c->H, c->tiles_x, c->tiles_y,
+                            (uint32_t)c->n, as<uint2>(c->ranges), as<uint64_t>(c->pairs[c->sorted_pairs_buf]), rec, c->opt.bg[0],
+                            c->opt.bg[1], c->opt.bg[2], out_C, out_grads, as<float4>(c->state), as<int>(c->count)));
+    c->have_state = true;
+    return GS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gs_status_string(gs_status s)
+{
+    switch (s) {
+    case GS_OK: return "GS_OK";
+    case GS_ERR_INVALID_ARG: return "GS_ERR_INVALID_ARG";
+    case GS_ERR_CUDA: return "GS_ERR_CUDA";
+    case GS_ERR_OOM: return "GS_ERR_OOM";
+    case GS_ERR_CAPACITY: return "GS_ERR_CAPACITY";
+    case GS_ERR_TIMEOUT: return "GS_ERR_TIMEOUT";
+    case GS_ERR_DEVICE_CHECK: return "GS_ERR_DEVICE_CHECK";
+    case GS_ERR_NOT_READY: return "GS_ERR_NOT_READY";
+    }
+    return "GS_ERR_UNKNOWN";
+}
+
+const char* gs_last_error(const gs_ctx* ctx)
+{
+    return ctx ? ctx->err : "";
+}
+
+gs_status gs_create(gs_ctx** out, void* stream, const gs_options* opt)
+{
+    if (!out) return GS_ERR_INVALID_ARG;
+    *out = nullptr;
+    gs_options o{};
+    o.tile = kTile;
+    o.mode = GS_MODE_3DGS;
+    if (opt) o = *opt;
+    if (check_options(nullptr, &o) != GS_OK) return GS_ERR_INVALID_ARG;
+    gs_ctx* c = new (std::nothrow) gs_ctx();
+    if (!c) return GS_ERR_OOM;
+    c->opt = o;
+    c->stream = (cudaStream_t)stream;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return GS_ERR_CUDA;
+    }
+    if (cudaMallocHost((void**)&c->h_scalar, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return GS_ERR_OOM;
+    }
+    if (ensure(c, c->errword, sizeof(int)) != GS_OK) {
+        cudaFreeHost(c->h_scalar);
+        delete c;
+        return GS_ERR_OOM;
+    }
+    if (cudaMemsetAsync(c->errword.p, 0, sizeof(int), c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        release(c->errword);
+        cudaFreeHost(c->h_scalar);
+        delete c;
+        return GS_ERR_CUDA;
+    }
+    *out = c;
+    return GS_OK;
+}
+
+gs_status gs_destroy(gs_ctx* c)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    cudaStreamSynchronize(c->stream);
+    DevBuf* bufs[] = {&c->rec0, &c->rec1, &c->rec2, &c->depth, &c->radius, &c->rect, &c->tiles_touched,
+                      &c->dkey[0], &c->dkey[1], &c->did[0], &c->did[1], &c->offsets, &c->scan_partials,
+                      &c->pairs[0], &c->pairs[1], &c->sort_hist, &c->sort_status, &c->sort_counter,
+                      &c->ranges, &c->state, &c->count, &c->errword};
+    for (DevBuf* b : bufs) release(*b);
+    if (c->h_scalar) cudaFreeHost(c->h_scalar);
+    cudaGetLastError();
+    delete c;
+    return GS_OK;
+}
+
+gs_status gs_set_stream(gs_ctx* c, void* stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->stream = (cudaStream_t)stream;
+    return GS_OK;
+}
+
+gs_status gs_set_options(gs_ctx* c, const gs_options* opt)
+{
+    if (!c || !opt) return GS_ERR_INVALID_ARG;
+    gs_status st = check_options(c, opt);
+    if (st != GS_OK) return st;
+    c->opt = *opt;
+    c->have_proj = false;
+    c->have_state = false;
+    return GS_OK;
+}
+
+gs_status gs_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int32_t W, int32_t H)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    LaunchTally tally(c);
+    return do_project(c, g, cam, W, H);
+}
+
+gs_status gs_render_binned(gs_ctx* c, float* out_C, float* out_grads)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    LaunchTally tally(c);
+    return do_blend(c, out_C, out_grads);
+}
+
+gs_status gs_render_with_grads(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int32_t W, int32_t H,
+                               float* out_C, float* out_grads)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    LaunchTally tally(c);
+    if (!out_C || !out_grads) return fail(c, GS_ERR_INVALID_ARG, "out_C and out_grads are required");
+    gs_status st = do_project(c, g, cam, W, H);
+    if (st != GS_OK) return st;
+    return do_blend(c, out_C, out_grads);
+}
+
+gs_status gs_render(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int32_t W, int32_t H, float* out_C)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    LaunchTally tally(c);
+    if (!out_C) return fail(c, GS_ERR_INVALID_ARG, "out_C is required");
+    gs_status st = do_project(c, g, cam, W, H);
+    if (st != GS_OK) return st;
+    return do_blend(c, out_C, nullptr);
+}
+
+gs_status gs_upscale(gs_ctx* c, const float* C, const float* grads, int32_t W, int32_t H, int32_t factor,
+                     float* out)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    LaunchTally tally(c);
+    if (!C || !grads || !out) return fail(c, GS_ERR_INVALID_ARG, "NULL image pointer");
+    if (W < 2 || H < 2) return fail(c, GS_ERR_INVALID_ARG, "upscale needs W, H >= 2");
+    if (factor < 1 || factor > 16) return fail(c, GS_ERR_INVALID_ARG, "factor must be in 1..16");
+    if ((int64_t)W * factor > (1 << 24) || (int64_t)H * factor > (1 << 24))
+        return fail(c, GS_ERR_INVALID_ARG, "output too large");
+    GS_CUDA(c, launch_upscale(c->stream, C, grads, W, H, factor, out));
+    return GS_OK;
+}
+
+gs_status gs_pair_count(const gs_ctx* c, int64_t* P)
+{
+    if (!c || !P) return GS_ERR_INVALID_ARG;
+    if (!c->have_proj) return GS_ERR_NOT_READY;
+    *P = c->P;
+    return GS_OK;
+}
+
+gs_status gs_read_projected(gs_ctx* c, float* mean2d, float* conic, float* rgb, float* opacity, float* depth,
+                            int32_t* radius, int32_t* tiles_touched)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (!c->have_proj) return fail(c, GS_ERR_NOT_READY, "no projection");
+    const Records rec{as<float4>(c->rec0), as<float4>(c->rec1), as<float4>(c->rec2)};
+    GS_CUDA(c, launch_unpack_projected(c->stream, rec, as<int>(c->radius), as<uint32_t>(c->tiles_touched),
+                                       as<float>(c->depth), (uint32_t)c->n, mean2d, conic, rgb, opacity, depth,
+                                       radius, tiles_touched));
+    return GS_OK;
+}
+
+gs_status gs_read_bins(gs_ctx* c, uint64_t* keys, uint32_t* vals, uint32_t* ranges, int64_t capacity)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (!c->have_proj) return fail(c, GS_ERR_NOT_READY, "no projection");
+    if ((keys || vals) && capacity < c->P) return fail(c, GS_ERR_CAPACITY, "capacity %lld < P %lld",
+                                                       (long long)capacity, (long long)c->P);
+    if (keys || vals)
+        GS_CUDA(c, launch_finalize_bins(c->stream, as<uint64_t>(c->pairs[c->sorted_pairs_buf]), (uint32_t)c->P,
+                                        (uint32_t)c->n, as<float>(c->depth), keys, vals));
+    if (ranges)
+        GS_CUDA(c, cudaMemcpyAsync(ranges, c->ranges.p, sizeof(uint2) * (size_t)c->tiles_x * c->tiles_y,
+                                   cudaMemcpyDeviceToDevice, c->stream));
+    return GS_OK;
+}
+
+gs_status gs_read_state(gs_ctx* c, float* state, int32_t* count)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (!c->have_state) return fail(c, GS_ERR_NOT_READY, "no blend state");
+    const size_t npix = (size_t)c->W * c->H;
+    if (state) {
+        // float4 per pixel -> four planes
+        GS_CUDA(c, cudaMemcpy2DAsync(state, sizeof(float), c->state.p, sizeof(float4), sizeof(float), npix,
+                                     cudaMemcpyDeviceToDevice, c->stream));
+        for (int k = 1; k < 4; ++k)
+            GS_CUDA(c, cudaMemcpy2DAsync(state + k * npix, sizeof(float), as<float>(c->state) + k, sizeof(float4),
+                                         sizeof(float), npix, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    if (count) GS_CUDA(c, cudaMemcpyAsync(count, c->count.p, sizeof(int) * npix, cudaMemcpyDeviceToDevice, c->stream));
+    return GS_OK;
+}
+
+gs_status gs_blend_stats(gs_ctx* c, int64_t* counts)
+{
+    if (!c || !counts) return GS_ERR_INVALID_ARG;
+    if (!c->have_proj) return fail(c, GS_ERR_NOT_READY, "no projection");
+    LaunchTally tally(c);
+    DevBuf tmp;
+    gs_status st = ensure(c, tmp, 2 * sizeof(unsigned long long));
+    if (st != GS_OK) return st;
+    unsigned long long h[2] = {0, 0};
+    cudaError_t e = cudaMemsetAsync(tmp.p, 0, 2 * sizeof(unsigned long long), c->stream);
+    const Records rec{as<float4>(c->rec0), as<float4>(c->rec1), as<float4>(c->rec2)};
+    if (e == cudaSuccess)
+        e = launch_blend_stats(c->stream, c->opt.mode, c->W, c->H, c->tiles_x, c->tiles_y, (uint32_t)c->n,
+                               as<uint2>(c->ranges), as<uint64_t>(c->pairs[c->sorted_pairs_buf]), rec,
+                               as<unsigned long long>(tmp));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, tmp.p, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    release(tmp);
+    if (e != cudaSuccess) return cuda_fail(c, e, "gs_blend_stats");
+    counts[0] = (int64_t)h[0];
+    counts[1] = (int64_t)h[1];
+    return GS_OK;
+}
+
+gs_status gs_launch_count(const gs_ctx* c, int64_t* count)
+{
+    if (!c || !count) return GS_ERR_INVALID_ARG;
+    *count = c->launches;
+    return GS_OK;
+}
+
+gs_status gs_synchronize(gs_ctx* c)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    return read_device_error(c);
+}
+
+}  // extern "C"

@@ -1,0 +1,137 @@
+// Internal declarations shared by the libgs translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gs.h"
+
+namespace gs {
+
+constexpr int kTile = 16;                 // tile side in pixels (16 x 16 = 256 pixels)
+constexpr int kTilePixels = kTile * kTile;
+
+// Device error word values (written by bounded waits / device checks).
+constexpr int kDevOk = 0;
+constexpr int kDevTimeout = 1;
+constexpr int kDevCheck = 2;
+
+// Largest pair count the 30-bit look-back counters of the radix sort can hold.
+constexpr int64_t kMaxPairs = (int64_t(1) << 30) - 1;
+
+// Per-Gaussian record staged by the blend kernel (3 x 16 B):
+//   r0 = (mean_x, mean_y, conic_a, conic_b)
+//   r1 = (conic_c, opacity, log-alpha reject threshold, unused)
+//   r2 = (red, green, blue, unused)
+struct Records {
+    float4* r0;
+    float4* r1;
+    float4* r2;
+};
+
+struct CameraParams {
+    float R[9];        // world->camera rotation, row-major
+    float t[3];        // world->camera translation
+    float campos[3];   // camera centre in world coordinates, -R^T t
+    float fx, fy, cx, cy, znear;
+    float lim_x, lim_y;   // 1.3 tan(fov/2) clamp of the Jacobian's x/z, y/z
+};
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+
+}  // namespace gs
+
+struct gs_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    gs_options opt{};
+    char err[512] = {0};
+
+    // last projection
+    bool have_proj = false;
+    bool have_state = false;
+    int64_t n = 0;
+    int W = 0, H = 0, tiles_x = 0, tiles_y = 0;
+    int64_t P = 0;
+
+    // per Gaussian
+    gs::DevBuf rec0, rec1, rec2;        // float4[n]
+    gs::DevBuf depth;                   // float[n]
+    gs::DevBuf radius;                  // int32[n]
+    gs::DevBuf rect;                    // int4[n] inclusive tile rect
+    gs::DevBuf tiles_touched;           // uint32[n]
+    gs::DevBuf dkey[2], did[2];         // depth sort keys / ids, ping-pong
+    gs::DevBuf offsets;                 // uint32[n + 1]
+    gs::DevBuf scan_partials;           // uint64[blocks + 1]
+    // per pair
+    gs::DevBuf pairs[2];                // uint64[P] (tile << 32 | id), ping-pong
+    // radix sort scratch
+    gs::DevBuf sort_hist;               // uint32[passes][256]
+    gs::DevBuf sort_status;             // uint32[passes][tiles][256]
+    gs::DevBuf sort_counter;            // uint32[passes]
+    // per tile / pixel
+    gs::DevBuf ranges;                  // uint2[tiles]
+    gs::DevBuf state;                   // float4[W*H]
+    gs::DevBuf count;                   // int32[W*H]
+    gs::DevBuf errword;                 // int32
+    unsigned long long* h_scalar = nullptr;   // pinned host scalar for the pair count
+    int sorted_ids_buf = 0;             // which did[] holds the depth-sorted ids
+    int sorted_pairs_buf = 0;           // which pairs[] holds the sorted pairs
+    int64_t launches = 0;               // kernels launched on behalf of this context
+};
+
+namespace gs {
+
+// Kernel launches issued by this thread since the library was loaded (every
+// launch site calls note_launch(); the API adds the delta of each call to the
+// context's counter, exposed by gs_launch_count).
+int64_t& launch_counter();
+inline void note_launch() { ++launch_counter(); }
+
+// ---- launchers (each returns the cudaError_t of its launch) ----
+cudaError_t launch_project(cudaStream_t s, const gs_gaussians& g, const CameraParams& cam, int W, int H,
+                           int tiles_x, int tiles_y, int mode, Records rec, float* depth, int* radius,
+                           int4* rect, uint32_t* tiles_touched, uint32_t* depth_key, uint32_t* ids);
+
+// LSD radix sort of n keys (uint32 keys with uint32 values, or uint64 keys
+// alone) on bits [bit_lo, bit_hi).  Ping-pong buffers: the result lands in
+// buffer index *out_idx (0 or 1).  n is a host count.
+cudaError_t radix_sort_u32_pairs(cudaStream_t s, uint32_t* keys[2], uint32_t* vals[2], uint32_t n,
+                                 int bit_lo, int bit_hi, uint32_t* hist, uint32_t* status,
+                                 uint32_t* counters, int* err, int* out_idx);
+cudaError_t radix_sort_u64_keys(cudaStream_t s, uint64_t* keys[2], uint32_t n, int bit_lo, int bit_hi,
+                                uint32_t* hist, uint32_t* status, uint32_t* counters, int* err,
+                                int* out_idx);
+size_t radix_status_words(uint32_t n, int bit_lo, int bit_hi);
+int radix_passes(int bit_lo, int bit_hi);
+
+// exclusive scan of tiles_touched[ids[k]] over k -> offsets[k]; partials[nb]
+// (nb = scan_partials_count(n) - 1) receives the exact 64-bit total
+cudaError_t launch_scan_gathered(cudaStream_t s, const uint32_t* tiles_touched, const uint32_t* ids,
+                                 uint32_t n, uint32_t* offsets, unsigned long long* partials);
+size_t scan_partials_count(uint32_t n);
+
+cudaError_t launch_emit_pairs(cudaStream_t s, const uint32_t* ids, const uint32_t* offsets, const int4* rect,
+                              uint32_t n, int tiles_x, uint64_t* pairs);
+cudaError_t launch_tile_ranges(cudaStream_t s, const uint64_t* pairs, uint32_t P, uint32_t T, uint2* ranges);
+cudaError_t launch_finalize_bins(cudaStream_t s, const uint64_t* pairs, uint32_t P, uint32_t n, const float* depth,
+                                 uint64_t* keys, uint32_t* vals);
+cudaError_t launch_unpack_projected(cudaStream_t s, Records rec, const int* radius, const uint32_t* tiles_touched,
+                                    const float* depth_in, uint32_t n, float* mean2d, float* conic, float* rgb,
+                                    float* opacity, float* depth, int32_t* radius_out, int32_t* tiles_out);
+
+cudaError_t launch_blend(cudaStream_t s, bool grads, int mode, int W, int H, int tiles_x, int tiles_y, uint32_t n,
+                         const uint2* ranges, const uint64_t* pairs, Records rec, float bg0, float bg1,
+                         float bg2, float* out_C, float* out_grads, float4* state, int* count);
+
+cudaError_t launch_blend_stats(cudaStream_t s, int mode, int W, int H, int tiles_x, int tiles_y, uint32_t n,
+                               const uint2* ranges, const uint64_t* pairs, Records rec,
+                               unsigned long long* stats);
+
+cudaError_t launch_upscale(cudaStream_t s, const float* C, const float* grads, int W, int H, int factor,
+                           float* out);
+
+}  // namespace gs

@@ -1,0 +1,247 @@
+// Projection of 3D Gaussians to screen-space records (Sec. 4: Sigma = R S S^T R^T,
+// EWA splatting Sigma' = J W Sigma W^T J^T), view-dependent SH colour, and the
+// tile rect of each Gaussian.  One thread per Gaussian; HBM-bound (reads 60 B
+// (RGB) to 236 B (SH degree 3) per Gaussian, writes 92 B).
+#include <math.h>
+
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+// Real spherical harmonics in Cartesian form on the unit sphere (d = x, y, z),
+// index k = l^2 + l + m, Condon-Shortley phase, normalisation
+// K_l^m = sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) (times sqrt 2 for m != 0):
+//   l=0: 1/(2 sqrt(pi))
+//   l=1: sqrt(3/(4 pi)) * (-y, z, -x)
+//   l=2: (1/2)sqrt(15/pi) xy, -(1/2)sqrt(15/pi) yz, (1/4)sqrt(5/pi)(3z^2-1),
+//        -(1/2)sqrt(15/pi) xz, (1/4)sqrt(15/pi)(x^2-y^2)
+//   l=3: -(1/4)sqrt(35/(2pi)) y(3x^2-y^2), (1/2)sqrt(105/pi) xyz,
+//        -(1/4)sqrt(21/(2pi)) y(5z^2-1), (1/4)sqrt(7/pi) z(5z^2-3),
+//        -(1/4)sqrt(21/(2pi)) x(5z^2-1), (1/4)sqrt(105/pi) z(x^2-y^2),
+//        -(1/4)sqrt(35/(2pi)) x(x^2-3y^2)
+constexpr float kY00 = 0.28209479177387814f;
+constexpr float kY1 = 0.48860251190291992f;
+constexpr float kY2a = 1.0925484305920792f;
+constexpr float kY2b = 0.31539156525252005f;
+constexpr float kY2c = 0.54627421529603959f;
+constexpr float kY3a = 0.59004358992664352f;
+constexpr float kY3b = 2.8906114426405538f;
+constexpr float kY3c = 0.45704579946446572f;
+constexpr float kY3d = 0.37317633259011540f;
+constexpr float kY3e = 1.4453057213202769f;
+
+__device__ __forceinline__ void sh_colour(const float* __restrict__ sh, int deg, float x, float y, float z,
+                                          float out[3])
+{
+    float Y[16];
+    Y[0] = kY00;
+    int K = 1;
+    if (deg >= 1) {
+        Y[1] = -kY1 * y;
+        Y[2] = kY1 * z;
+        Y[3] = -kY1 * x;
+        K = 4;
+    }
+    if (deg >= 2) {
+        const float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = kY2a * x * y;
+        Y[5] = -kY2a * y * z;
+        Y[6] = kY2b * (3.f * zz - 1.f);
+        Y[7] = -kY2a * x * z;
+        Y[8] = kY2c * (xx - yy);
+        K = 9;
+        if (deg >= 3) {
+            Y[9] = -kY3a * y * (3.f * xx - yy);
+            Y[10] = kY3b * x * y * z;
+            Y[11] = -kY3c * y * (5.f * zz - 1.f);
+            Y[12] = kY3d * z * (5.f * zz - 3.f);
+            Y[13] = -kY3c * x * (5.f * zz - 1.f);
+            Y[14] = kY3e * z * (xx - yy);
+            Y[15] = -kY3a * x * (xx - 3.f * yy);
+            K = 16;
+        }
+    }
+    float r = 0.f, g = 0.f, b = 0.f;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        if (k < K) {
+            r = fmaf(sh[3 * k + 0], Y[k], r);
+            g = fmaf(sh[3 * k + 1], Y[k], g);
+            b = fmaf(sh[3 * k + 2], Y[k], b);
+        }
+    }
+    out[0] = fmaxf(0.f, r + 0.5f);
+    out[1] = fmaxf(0.f, g + 0.5f);
+    out[2] = fmaxf(0.f, b + 0.5f);
+}
+
+__global__ void __launch_bounds__(256) k_project(
+    int n, const float* __restrict__ means, const float* __restrict__ log_scales,
+    const float* __restrict__ quats, const float* __restrict__ op_logits, const float* __restrict__ sh,
+    int sh_deg, const float* __restrict__ rgb_in, CameraParams cam, int W, int H, int tiles_x, int tiles_y,
+    int mode, Records rec, float* __restrict__ depth_out, int* __restrict__ radius_out,
+    int4* __restrict__ rect_out, uint32_t* __restrict__ tiles_out, uint32_t* __restrict__ depth_key,
+    uint32_t* __restrict__ ids)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    ids[i] = (uint32_t)i;
+    const float mx3 = means[3 * i], my3 = means[3 * i + 1], mz3 = means[3 * i + 2];
+    const float px = fmaf(cam.R[0], mx3, fmaf(cam.R[1], my3, fmaf(cam.R[2], mz3, cam.t[0])));
+    const float py = fmaf(cam.R[3], mx3, fmaf(cam.R[4], my3, fmaf(cam.R[5], mz3, cam.t[1])));
+    const float pz = fmaf(cam.R[6], mx3, fmaf(cam.R[7], my3, fmaf(cam.R[8], mz3, cam.t[2])));
+
+    bool vis = pz > cam.znear;
+    // 3D covariance Sigma = M M^T with M = R diag(s), R from the unit quaternion
+    float qw = quats[4 * i], qx = quats[4 * i + 1], qy = quats[4 * i + 2], qz = quats[4 * i + 3];
+    const float qn2 = qw * qw + qx * qx + qy * qy + qz * qz;
+    vis = vis && qn2 > 0.f;
+    const float qinv = rsqrtf(qn2);
+    qw *= qinv; qx *= qinv; qy *= qinv; qz *= qinv;
+    const float s0 = expf(log_scales[3 * i]), s1 = expf(log_scales[3 * i + 1]), s2 = expf(log_scales[3 * i + 2]);
+    const float R00 = 1.f - 2.f * (qy * qy + qz * qz), R01 = 2.f * (qx * qy - qw * qz), R02 = 2.f * (qx * qz + qw * qy);
+    const float R10 = 2.f * (qx * qy + qw * qz), R11 = 1.f - 2.f * (qx * qx + qz * qz), R12 = 2.f * (qy * qz - qw * qx);
+    const float R20 = 2.f * (qx * qz - qw * qy), R21 = 2.f * (qy * qz + qw * qx), R22 = 1.f - 2.f * (qx * qx + qy * qy);
+    const float M00 = R00 * s0, M01 = R01 * s1, M02 = R02 * s2;
+    const float M10 = R10 * s0, M11 = R11 * s1, M12 = R12 * s2;
+    const float M20 = R20 * s0, M21 = R21 * s1, M22 = R22 * s2;
+    const float S00 = M00 * M00 + M01 * M01 + M02 * M02;
+    const float S01 = M00 * M10 + M01 * M11 + M02 * M12;
+    const float S02 = M00 * M20 + M01 * M21 + M02 * M22;
+    const float S11 = M10 * M10 + M11 * M11 + M12 * M12;
+    const float S12 = M10 * M20 + M11 * M21 + M12 * M22;
+    const float S22 = M20 * M20 + M21 * M21 + M22 * M22;
+
+    // Jacobian of the perspective map at the frustum-clamped mean, times W
+    const float iz = 1.f / pz;
+    const float txz = fminf(cam.lim_x, fmaxf(-cam.lim_x, px * iz));
+    const float tyz = fminf(cam.lim_y, fmaxf(-cam.lim_y, py * iz));
+    const float j00 = cam.fx * iz, j02 = -cam.fx * txz * iz;
+    const float j11 = cam.fy * iz, j12 = -cam.fy * tyz * iz;
+    // T = J W (2x3)
+    const float T00 = j00 * cam.R[0] + j02 * cam.R[6];
+    const float T01 = j00 * cam.R[1] + j02 * cam.R[7];
+    const float T02 = j00 * cam.R[2] + j02 * cam.R[8];
+    const float T10 = j11 * cam.R[3] + j12 * cam.R[6];
+    const float T11 = j11 * cam.R[4] + j12 * cam.R[7];
+    const float T12 = j11 * cam.R[5] + j12 * cam.R[8];
+    // U = T Sigma
+    const float U00 = T00 * S00 + T01 * S01 + T02 * S02;
+    const float U01 = T00 * S01 + T01 * S11 + T02 * S12;
+    const float U02 = T00 * S02 + T01 * S12 + T02 * S22;
+    const float U10 = T10 * S00 + T11 * S01 + T12 * S02;
+    const float U11 = T10 * S01 + T11 * S11 + T12 * S12;
+    const float U12 = T10 * S02 + T11 * S12 + T12 * S22;
+    const float c00 = U00 * T00 + U01 * T01 + U02 * T02 + 0.3f;
+    const float c01 = U00 * T10 + U01 * T11 + U02 * T12;
+    const float c11 = U10 * T10 + U11 * T11 + U12 * T12 + 0.3f;
+    const float det = c00 * c11 - c01 * c01;
+    vis = vis && det > 0.f;
+
+    const float idet = 1.f / det;
+    const float ca = c11 * idet, cb = -c01 * idet, cc = c00 * idet;
+    const float mid = 0.5f * (c00 + c11);
+    const float hd = 0.5f * (c00 - c11);
+    const float lam = mid + sqrtf(hd * hd + c01 * c01);   // cancellation-free largest eigenvalue
+    const float rad = ceilf(3.f * sqrtf(lam));
+    const float m2x = fmaf(cam.fx, px * iz, cam.cx);
+    const float m2y = fmaf(cam.fy, py * iz, cam.cy);
+
+    vis = vis && isfinite(m2x) && isfinite(m2y) && isfinite(rad);
+    int4 rc = make_int4(0, 0, -1, -1);
+    uint32_t ntiles = 0;
+    if (vis) {
+        if (mode == GS_MODE_EXACT) {
+            rc = make_int4(0, 0, tiles_x - 1, tiles_y - 1);
+            ntiles = (uint32_t)(tiles_x * tiles_y);
+        } else {
+            // tiles holding a pixel centre (i, j) with |i - mx| <= r, |j - my| <= r
+            const float lox = ceilf(m2x - rad), hix = floorf(m2x + rad);
+            const float loy = ceilf(m2y - rad), hiy = floorf(m2y + rad);
+            if (!(hix < 0.f || lox > (float)(W - 1) || hiy < 0.f || loy > (float)(H - 1) || lox > hix ||
+                  loy > hiy)) {
+                const int x0 = lox < 0.f ? 0 : (int)lox;
+                const int y0 = loy < 0.f ? 0 : (int)loy;
+                const int x1 = hix > (float)(W - 1) ? W - 1 : (int)hix;
+                const int y1 = hiy > (float)(H - 1) ? H - 1 : (int)hiy;
+                rc = make_int4(x0 / kTile, y0 / kTile, x1 / kTile, y1 / kTile);
+                ntiles = (uint32_t)((rc.z - rc.x + 1) * (rc.w - rc.y + 1));
+            }
+        }
+    }
+    tiles_out[i] = ntiles;
+    rect_out[i] = rc;
+    radius_out[i] = vis ? (int)rad : 0;
+    depth_out[i] = vis ? pz : 0.f;
+    depth_key[i] = ntiles > 0 ? __float_as_uint(pz) : 0xFFFFFFFFu;
+    if (!vis) {
+        rec.r0[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        rec.r1[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        rec.r2[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+
+    const float op = 1.f / (1.f + expf(-op_logits[i]));
+    float col[3];
+    if (sh != nullptr) {
+        float dx = mx3 - cam.campos[0], dy = my3 - cam.campos[1], dz = mz3 - cam.campos[2];
+        const float dn = rsqrtf(dx * dx + dy * dy + dz * dz);
+        dx *= dn; dy *= dn; dz *= dn;
+        sh_colour(sh + (size_t)i * (sh_deg + 1) * (sh_deg + 1) * 3, sh_deg, dx, dy, dz, col);
+    } else {
+        col[0] = rgb_in[3 * i];
+        col[1] = rgb_in[3 * i + 1];
+        col[2] = rgb_in[3 * i + 2];
+    }
+    // reject threshold on the exponent: g < ln(1/(255 sigma)) - 1e-4 guarantees
+    // sigma e^g < 1/255 in FP32, so the blend may skip the exponential there.
+    const float thr = (mode == GS_MODE_EXACT) ? -INFINITY : (logf(1.f / (255.f * op)) - 1e-4f);
+    rec.r0[i] = make_float4(m2x, m2y, ca, cb);
+    rec.r1[i] = make_float4(cc, op, thr, 0.f);
+    rec.r2[i] = make_float4(col[0], col[1], col[2], 0.f);
+}
+
+__global__ void k_unpack(Records rec, const int* __restrict__ radius, const uint32_t* __restrict__ tiles,
+                         const float* __restrict__ depth_in, uint32_t n, float* mean2d, float* conic, float* rgb,
+                         float* opacity, float* depth, int32_t* radius_out, int32_t* tiles_out)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 a = rec.r0[i], b = rec.r1[i], c = rec.r2[i];
+    if (mean2d) { mean2d[2 * i] = a.x; mean2d[2 * i + 1] = a.y; }
+    if (conic) { conic[3 * i] = a.z; conic[3 * i + 1] = a.w; conic[3 * i + 2] = b.x; }
+    if (rgb) { rgb[3 * i] = c.x; rgb[3 * i + 1] = c.y; rgb[3 * i + 2] = c.z; }
+    if (opacity) opacity[i] = b.y;
+    if (depth) depth[i] = depth_in[i];
+    if (radius_out) radius_out[i] = radius[i];
+    if (tiles_out) tiles_out[i] = (int32_t)tiles[i];
+}
+
+}  // namespace
+
+cudaError_t launch_project(cudaStream_t s, const gs_gaussians& g, const CameraParams& cam, int W, int H,
+                           int tiles_x, int tiles_y, int mode, Records rec, float* depth, int* radius, int4* rect,
+                           uint32_t* tiles_touched, uint32_t* depth_key, uint32_t* ids)
+{
+    const int n = (int)g.n;
+    if (n == 0) return cudaSuccess;
+    const int threads = 256;
+    const int blocks = (n + threads - 1) / threads;
+    k_project<<<blocks, threads, 0, s>>>(n, g.means, g.log_scales, g.quats, g.opacity_logits, g.sh, g.sh_degree,
+                                         g.rgb, cam, W, H, tiles_x, tiles_y, mode, rec, depth, radius, rect,
+                                         tiles_touched, depth_key, ids); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_projected(cudaStream_t s, Records rec, const int* radius, const uint32_t* tiles_touched,
+                                    const float* depth_in, uint32_t n, float* mean2d, float* conic, float* rgb,
+                                    float* opacity, float* depth, int32_t* radius_out, int32_t* tiles_out)
+{
+    if (n == 0) return cudaSuccess;
+    k_unpack<<<(n + 255) / 256, 256, 0, s>>>(rec, radius, tiles_touched, depth_in, n, mean2d, conic, rgb, opacity,
+                                             depth, radius_out, tiles_out); note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace gs
