@@ -13,6 +13,7 @@ from __future__ import annotations
 
 import ctypes as ct
 import os
+import platform
 import subprocess
 import threading
 
@@ -20,7 +21,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
-_LIBDIR = os.path.join(_HERE, "_lib")
+_LIBDIR = os.path.join(_HERE, "_lib", platform.machine())
 _LIB = os.path.join(_LIBDIR, "liboracle.so")
 _lock = threading.Lock()
 _lib = None

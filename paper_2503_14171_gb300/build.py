@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import glob
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -16,9 +17,11 @@ from concurrent.futures import ThreadPoolExecutor
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-BUILD = os.path.join(HERE, "_build")
+# objects are kept per host architecture (the library is built on x86 and on Arm)
+BUILD = os.path.join(HERE, "_build", platform.machine())
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libgs.so")
+STAMP = os.path.join(LIBDIR, "libgs.arch")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-Xptxas", "-warn-spills"]
@@ -68,7 +71,8 @@ def build(verbose: bool = False, force: bool = False, extra_flags=()) -> str:
                     sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
                 if r.returncode != 0:
                     raise RuntimeError(f"nvcc failed on {cmd[-3]}")
-    if force or jobs or _stale(LIB, objs):
+    arch_ok = os.path.exists(STAMP) and open(STAMP).read().strip() == platform.machine()
+    if force or jobs or not arch_ok or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
         cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs]
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -76,7 +80,10 @@ def build(verbose: bool = False, force: bool = False, extra_flags=()) -> str:
             sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
             raise RuntimeError("link of libgs.so failed")
         os.replace(tmp, LIB)
+        with open(STAMP, "w") as f:
+            f.write(platform.machine())
     return LIB
+
 
 
 if __name__ == "__main__":

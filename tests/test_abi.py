@@ -19,8 +19,8 @@ def declared_functions():
 
 @pytest.fixture(scope="module")
 def libpath():
-    from paper_2503_14171_gb300 import build
-    return build.build()
+    import __graft_entry__
+    return __graft_entry__._gs_build_module().build()
 
 
 def test_header_declares_the_boundary():
