@@ -54,6 +54,9 @@ def _args():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gs", choices=["gs", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", default=None, choices=["main", "direct"],
+                    help="run only warm-up + steps of the 2x path (main) or of the direct 1920x1080 "
+                         "render (direct) and print stage times; the case ncu captures use")
     return ap.parse_args()
 
 
@@ -410,10 +413,53 @@ def _traffic_from_profiles():
         return None
 
 
+def run_profile(args):
+    """The bench's own kernels on the same workload, without the extra legs, so an
+    ncu capture sees only warm-up + timed steps of one path."""
+    import torch
+    import paper_2503_14171_gb300 as gs
+    import scenes
+    scene = scenes.mixture_scene(N_GAUSS, seed=0)
+    cam = scenes.pinhole_camera(LOW_W, LOW_H)
+    cam_hi = scenes.scaled_camera(cam, FACTOR)
+    dev = gs.DeviceScene(scene)
+    stream = torch.cuda.Stream()
+    ctx = gs.Context(stream=stream)
+    C = torch.empty(3, LOW_H, LOW_W, device="cuda")
+    G = torch.empty(3, 3, LOW_H, LOW_W, device="cuda")
+    out = torch.empty(3, OUT_H, OUT_W, device="cuda")
+
+    def main_step():
+        ctx.project(dev, cam, LOW_W, LOW_H)
+        ctx.render_binned(grads=True, out_C=C, out_grads=G)
+        ctx.upscale(C, G, FACTOR, out=out)
+
+    def direct_step():
+        ctx.render(dev, cam_hi, OUT_W, OUT_H, out_C=out)
+
+    fn = main_step if args.profile == "main" else direct_step
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+    print(json.dumps({"profile": args.profile, "ms_per_step": a.elapsed_time(b) / args.steps,
+                      "pairs": ctx.pair_count(), "launches": ctx.launch_count()}), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile:
+        return run_profile(args)
     return run_gs(args)
 
 

@@ -107,7 +107,7 @@ def project(scene: dict, cam: dict, W: int, H: int, tile: int = 16, mode: int = 
         rgb=np.zeros((n, 3)), opacity=np.zeros(n), depth=np.zeros(n),
         radius=np.zeros(n, np.int32), rect=np.zeros((n, 4), np.int32),
         tiles_touched=np.zeros(n, np.int64), borderline=np.zeros(n, np.uint8),
-        envelope=np.zeros((n, 4), np.int32))
+        envelope=np.zeros((n, 4), np.int32), core=np.zeros((n, 4), np.int32))
     st = lib.ora_project(
         ct.c_int64(n), _p(means), _p(ls), _p(qs), _p(ol), _p(sh), ct.c_int(deg), _p(rgb_in),
         _p(vm), ct.c_double(cam["fx"]), ct.c_double(cam["fy"]), ct.c_double(cam["cx"]),
@@ -115,7 +115,7 @@ def project(scene: dict, cam: dict, W: int, H: int, tile: int = 16, mode: int = 
         ct.c_int(tile), ct.c_int(mode),
         _p(out["mean2d"]), _p(out["cov2d"]), _p(out["conic"]), _p(out["rgb"]),
         _p(out["opacity"]), _p(out["depth"]), _p(out["radius"]), _p(out["rect"]),
-        _p(out["tiles_touched"]), _p(out["borderline"]), _p(out["envelope"]))
+        _p(out["tiles_touched"]), _p(out["borderline"]), _p(out["envelope"]), _p(out["core"]))
     _check(st, "project")
     out.update(W=W, H=H, tile=tile, mode=mode,
                tiles_x=(W + tile - 1) // tile, tiles_y=(H + tile - 1) // tile)

@@ -146,7 +146,7 @@ int ora_project(int64_t n,
                 double znear, int W, int H, int tile, int mode,
                 double* mean2d, double* cov2d, double* conic, double* rgb,
                 double* opacity, double* depth, int32_t* radius, int32_t* rect,
-                int64_t* tiles_touched, uint8_t* borderline, int32_t* envelope)
+                int64_t* tiles_touched, uint8_t* borderline, int32_t* envelope, int32_t* core)
 {
     if (n < 0 || W < 1 || H < 1 || tile < 1 || sh_degree < 0 || sh_degree > 3) return ORA_EINVAL;
     if (sh == NULL && rgb_in == NULL && n > 0) return ORA_EINVAL;
@@ -169,7 +169,7 @@ int ora_project(int64_t n,
         for (int k = 0; k < 3; ++k) { cov2d[3 * i + k] = 0.0; conic[3 * i + k] = 0.0; rgb[3 * i + k] = 0.0; }
         opacity[i] = 0.0; depth[i] = 0.0; radius[i] = 0; tiles_touched[i] = 0; borderline[i] = 0;
         rect[4 * i + 0] = 0; rect[4 * i + 1] = 0; rect[4 * i + 2] = -1; rect[4 * i + 3] = -1;
-        for (int k = 0; k < 4; ++k) envelope[4 * i + k] = rect[4 * i + k];
+        for (int k = 0; k < 4; ++k) envelope[4 * i + k] = core[4 * i + k] = rect[4 * i + k];
 
         const double* mu = means + 3 * i;
         double p[3];
@@ -257,14 +257,15 @@ int ora_project(int64_t n,
 
         int32_t* rc = rect + 4 * i;
         int32_t* ev = envelope + 4 * i;
+        int32_t* co = core + 4 * i;
         if (mode == MODE_EXACT) {
             rc[0] = 0; rc[1] = 0; rc[2] = tiles_x - 1; rc[3] = tiles_y - 1;
             tiles_touched[i] = (int64_t)tiles_x * tiles_y;
-            for (int k = 0; k < 4; ++k) ev[k] = rc[k];
+            for (int k = 0; k < 4; ++k) ev[k] = co[k] = rc[k];
             continue;
         }
         tiles_touched[i] = rect_of(mx, my, r_nom, W, H, tile, rc);
-        for (int k = 0; k < 4; ++k) ev[k] = rc[k];
+        for (int k = 0; k < 4; ++k) ev[k] = co[k] = rc[k];
 
         /* Borderline: the rect is not stable under the rounding error an FP32
          * evaluation of the same quantities can make (mean2D within eps_pos,
@@ -279,6 +280,14 @@ int ora_project(int64_t n,
                     int64_t cnt = rect_of(mx + a * eps_pos, my + b * eps_pos, rcand[rr], W, H, tile, alt);
                     if (cnt != tiles_touched[i] || memcmp(alt, rc, sizeof(alt)) != 0) {
                         borderline[i] = 1;
+                        /* core: tiles in every perturbed rect (empty if any is empty) */
+                        if (cnt == 0) { co[0] = 0; co[1] = 0; co[2] = -1; co[3] = -1; }
+                        else if (co[2] >= co[0]) {
+                            if (alt[0] > co[0]) co[0] = alt[0];
+                            if (alt[1] > co[1]) co[1] = alt[1];
+                            if (alt[2] < co[2]) co[2] = alt[2];
+                            if (alt[3] < co[3]) co[3] = alt[3];
+                        }
                         if (cnt > 0) {
                             if (ev[2] < ev[0]) { for (int k = 0; k < 4; ++k) ev[k] = alt[k]; }
                             else {

@@ -43,12 +43,13 @@ __device__ __forceinline__ void hermite(float t, float& h0, float& h1, float& g0
 
 __device__ __forceinline__ void cell_of(int X, int s, int W, int& i, float& t)
 {
-    // x = (X + 0.5)/s - 0.5 = (2X + 1 - s) / (2s): one rounding
-    const float x = (float)(2 * X + 1 - s) / (float)(2 * s);
-    int ii = (int)floorf(x);
-    ii = ii < 0 ? 0 : (ii > W - 2 ? W - 2 : ii);
-    i = ii;
-    t = x - (float)ii;
+    // x = (X + 0.5)/s - 0.5 = num/den with num = 2X + 1 - s, den = 2s: the cell is
+    // an exact integer floor division and t = (num - den i)/den has one rounding
+    const int num = 2 * X + 1 - s, den = 2 * s;
+    int q = num >= 0 ? num / den : -((den - 1 - num) / den);
+    q = q < 0 ? 0 : (q > W - 2 ? W - 2 : q);
+    i = q;
+    t = (float)(num - den * q) / (float)den;
 }
 
 __global__ void __launch_bounds__(kOutW * kOutH) k_upscale(const float* __restrict__ Cimg,

@@ -22,15 +22,21 @@ TOL_UP = 2e-6
 
 
 def borderline_tile_mask(proj) -> np.ndarray:
-    """Pixels in any tile of a borderline Gaussian's envelope rect."""
+    """Pixels in the tiles whose membership of a borderline Gaussian can flip
+    under FP32 rounding: its envelope rect minus its core rect (the tiles in
+    every perturbed rect)."""
     W, H, tile = proj["W"], proj["H"], proj["tile"]
-    m = np.zeros((H, W), bool)
+    tx, ty = proj["tiles_x"], proj["tiles_y"]
+    mt = np.zeros((ty, tx), bool)
     for i in np.nonzero(proj["borderline"])[0]:
-        e = proj["envelope"][i]
+        e, c = proj["envelope"][i], proj["core"][i]
         if e[2] < e[0]:
             continue
-        m[e[1] * tile:(e[3] + 1) * tile, e[0] * tile:(e[2] + 1) * tile] = True
-    return m
+        sub = np.ones((e[3] - e[1] + 1, e[2] - e[0] + 1), bool)
+        if c[2] >= c[0]:
+            sub[c[1] - e[1]:c[3] - e[1] + 1, c[0] - e[0]:c[2] - e[0] + 1] = False
+        mt[e[1]:e[3] + 1, e[0]:e[2] + 1] |= sub
+    return np.repeat(np.repeat(mt, tile, 0), tile, 1)[:H, :W]
 
 
 def compare_render(C_gpu, G_gpu, ref, exclude=None, tol_c=TOL_C, tol_g=TOL_G):
