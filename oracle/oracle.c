@@ -26,7 +26,9 @@
  * renderer the paper builds on, Sec. 6.2):
  *   - Gaussian exponent g = -1/2 d^T Sigma'^-1 d, d = (x - mu_x, y - mu_y) in pixels
  *     (Sec. 4 prints the exponent without the inverse and the 1/2).
- *   - Sigma' gets +0.3 px^2 on its diagonal; radius = ceil(3 sqrt(lambda_max)).
+ *   - Sigma' gets +0.3 px^2 on its diagonal; radius = ceil(3 sqrt(lambda_max));
+ *     a Gaussian's tiles are those holding a pixel centre inside the 3-sigma
+ *     square cut to the bounding box of its alpha >= 1/255 ellipse.
  *   - near plane z <= znear culls; J uses x/z, y/z clamped to 1.3 tan(fov/2).
  *   - mode 0 ("3dgs"): alpha = min(0.99, sigma e^g), pairs with alpha < 1/255 are
  *     skipped, a pixel stops before the Gaussian that would take its
@@ -119,23 +121,57 @@ int ora_sh_basis(int deg, int64_t n, const double* dirs, double* out)
 /* Projection (Sec. 4): Sigma = R S S^T R^T, Sigma' = J W Sigma W^T J^T.       */
 /* ------------------------------------------------------------------------- */
 
-/* Tiles covered by the square of half-width r around (mx, my): the tiles that
- * contain a pixel centre (i, j) with |i - mx| <= r and |j - my| <= r.
- * rect = {tx0, ty0, tx1, ty1} inclusive; returns the tile count (0: none). */
-static int64_t rect_of(double mx, double my, double r, int W, int H, int tile, int32_t rect[4])
+/* Tile span of one axis: the tiles that contain a pixel centre i with
+ * |i - m| <= h, for pixels 0..npix-1.  Returns 0 (and t0 > t1) if none. */
+static int axis_span(double m, double h, int npix, int tile, int32_t* t0, int32_t* t1)
 {
-    double lox = ceil(mx - r), hix = floor(mx + r);
-    double loy = ceil(my - r), hiy = floor(my + r);
+    double lo = ceil(m - h), hi = floor(m + h);
+    *t0 = 0;
+    *t1 = -1;
+    if (!(h >= 0.0) || hi < 0.0 || lo > (double)(npix - 1) || lo > hi) return 0;
+    int32_t p0 = lo < 0.0 ? 0 : (int32_t)lo;
+    int32_t p1 = hi > (double)(npix - 1) ? npix - 1 : (int32_t)hi;
+    *t0 = p0 / tile;
+    *t1 = p1 / tile;
+    return 1;
+}
+
+/* rect = {tx0, ty0, tx1, ty1} inclusive from the two axis spans; returns the
+ * tile count (0: none). */
+static int64_t rect_of(double mx, double my, double hx, double hy, int W, int H, int tile, int32_t rect[4])
+{
+    int32_t a0, a1, b0, b1;
+    int okx = axis_span(mx, hx, W, tile, &a0, &a1);
+    int oky = axis_span(my, hy, H, tile, &b0, &b1);
     rect[0] = 0; rect[1] = 0; rect[2] = -1; rect[3] = -1;
-    if (hix < 0.0 || lox > (double)(W - 1) || hiy < 0.0 || loy > (double)(H - 1)) return 0;
-    if (lox > hix || loy > hiy) return 0;
-    int32_t px0 = lox < 0.0 ? 0 : (int32_t)lox;
-    int32_t py0 = loy < 0.0 ? 0 : (int32_t)loy;
-    int32_t px1 = hix > (double)(W - 1) ? W - 1 : (int32_t)hix;
-    int32_t py1 = hiy > (double)(H - 1) ? H - 1 : (int32_t)hiy;
-    rect[0] = px0 / tile; rect[1] = py0 / tile;
-    rect[2] = px1 / tile; rect[3] = py1 / tile;
-    return (int64_t)(rect[2] - rect[0] + 1) * (int64_t)(rect[3] - rect[1] + 1);
+    if (!okx || !oky) return 0;
+    rect[0] = a0; rect[1] = b0; rect[2] = a1; rect[3] = b1;
+    return (int64_t)(a1 - a0 + 1) * (int64_t)(b1 - b0 + 1);
+}
+
+/* Envelope / core of one axis span over perturbed (m, h): returns 1 if any
+ * perturbation changes the span or its emptiness. */
+static int axis_perturb(double m, double eps_m, const double* hs, int nh, int npix, int tile,
+                        int32_t nominal0, int32_t nominal1, int nominal_ok,
+                        int32_t* env0, int32_t* env1, int32_t* core0, int32_t* core1, int* core_ok)
+{
+    int changed = 0;
+    *env0 = nominal0; *env1 = nominal1; *core0 = nominal0; *core1 = nominal1;
+    *core_ok = nominal_ok;
+    for (int a = -1; a <= 1; ++a)
+        for (int k = 0; k < nh; ++k) {
+            int32_t t0, t1;
+            int ok = axis_span(m + a * eps_m, hs[k], npix, tile, &t0, &t1);
+            if (ok != nominal_ok || (ok && (t0 != nominal0 || t1 != nominal1))) changed = 1;
+            if (!ok) { *core_ok = 0; continue; }
+            if (!nominal_ok && *env1 < *env0) { *env0 = t0; *env1 = t1; }
+            if (t0 < *env0) *env0 = t0;
+            if (t1 > *env1) *env1 = t1;
+            if (t0 > *core0) *core0 = t0;
+            if (t1 < *core1) *core1 = t1;
+        }
+    if (*core1 < *core0) *core_ok = 0;
+    return changed;
 }
 
 int ora_project(int64_t n,
@@ -264,41 +300,46 @@ int ora_project(int64_t n,
             for (int k = 0; k < 4; ++k) ev[k] = co[k] = rc[k];
             continue;
         }
-        tiles_touched[i] = rect_of(mx, my, r_nom, W, H, tile, rc);
+        /* Only pixels with alpha = sigma e^g >= 1/255 can blend: g >= -L with
+         * L = ln(255 sigma), the ellipse d^T Sigma'^-1 d <= 2L, whose bounding box
+         * has half-widths sqrt(2 L Sigma'_xx), sqrt(2 L Sigma'_yy).  The tile set is
+         * the 3-sigma square of the 3DGS renderer cut to that box (no pair
+         * outside it can pass the cut-off, so the image is unchanged). */
+        const double L = log(255.0 * opacity[i]);
+        const double ex = L > 0.0 ? sqrt(2.0 * L * S2[0][0]) : -1.0;
+        const double ey = L > 0.0 ? sqrt(2.0 * L * S2[1][1]) : -1.0;
+        const double hx = fmin(r_nom, ex), hy = fmin(r_nom, ey);
+        tiles_touched[i] = rect_of(mx, my, hx, hy, W, H, tile, rc);
         for (int k = 0; k < 4; ++k) ev[k] = co[k] = rc[k];
 
         /* Borderline: the rect is not stable under the rounding error an FP32
-         * evaluation of the same quantities can make (mean2D within eps_pos,
-         * 3 sqrt(lambda) within a relative 2e-5 of an integer). */
-        double eps_pos = 3e-7 * (fabs(mx) + fabs(my) + fabs(fx) + fabs(fy)) + 1e-6;
-        double eps_r = 2e-5 * v;
-        double rcand[2] = {ceil(v - eps_r), ceil(v + eps_r)};
-        for (int a = -1; a <= 1; ++a)
-            for (int b = -1; b <= 1; ++b)
-                for (int rr = 0; rr < 2; ++rr) {
-                    int32_t alt[4];
-                    int64_t cnt = rect_of(mx + a * eps_pos, my + b * eps_pos, rcand[rr], W, H, tile, alt);
-                    if (cnt != tiles_touched[i] || memcmp(alt, rc, sizeof(alt)) != 0) {
-                        borderline[i] = 1;
-                        /* core: tiles in every perturbed rect (empty if any is empty) */
-                        if (cnt == 0) { co[0] = 0; co[1] = 0; co[2] = -1; co[3] = -1; }
-                        else if (co[2] >= co[0]) {
-                            if (alt[0] > co[0]) co[0] = alt[0];
-                            if (alt[1] > co[1]) co[1] = alt[1];
-                            if (alt[2] < co[2]) co[2] = alt[2];
-                            if (alt[3] < co[3]) co[3] = alt[3];
-                        }
-                        if (cnt > 0) {
-                            if (ev[2] < ev[0]) { for (int k = 0; k < 4; ++k) ev[k] = alt[k]; }
-                            else {
-                                if (alt[0] < ev[0]) ev[0] = alt[0];
-                                if (alt[1] < ev[1]) ev[1] = alt[1];
-                                if (alt[2] > ev[2]) ev[2] = alt[2];
-                                if (alt[3] > ev[3]) ev[3] = alt[3];
-                            }
-                        }
-                    }
-                }
+         * evaluation of the same quantities can make (mean2D within eps_pos;
+         * 3 sqrt(lambda), the box half-widths and L within a relative 2e-5). */
+        const double eps_pos = 3e-7 * (fabs(mx) + fabs(my) + fabs(fx) + fabs(fy)) + 1e-6;
+        const double eps_r = 2e-5 * v;
+        const double rc_lo = ceil(v - eps_r), rc_hi = ceil(v + eps_r);
+        double hxs[6], hys[6];
+        int nh = 0;
+        const double Lp[2] = {L * (1.0 - 2e-5) - 1e-6, L * (1.0 + 2e-5) + 1e-6};
+        for (int q = 0; q < 2; ++q) {
+            const double exq = Lp[q] > 0.0 ? sqrt(2.0 * Lp[q] * S2[0][0]) : -1.0;
+            const double eyq = Lp[q] > 0.0 ? sqrt(2.0 * Lp[q] * S2[1][1]) : -1.0;
+            hxs[nh] = fmin(rc_lo, exq); hys[nh] = fmin(rc_lo, eyq); ++nh;
+            hxs[nh] = fmin(rc_hi, exq); hys[nh] = fmin(rc_hi, eyq); ++nh;
+        }
+        int32_t nx0, nx1, ny0, ny1;
+        const int okx = axis_span(mx, hx, W, tile, &nx0, &nx1);
+        const int oky = axis_span(my, hy, H, tile, &ny0, &ny1);
+        int32_t ex0, ex1, ey0, ey1, cx0, cx1, cy0, cy1;
+        int cokx, coky;
+        const int chx = axis_perturb(mx, eps_pos, hxs, nh, W, tile, nx0, nx1, okx, &ex0, &ex1, &cx0, &cx1, &cokx);
+        const int chy = axis_perturb(my, eps_pos, hys, nh, H, tile, ny0, ny1, oky, &ey0, &ey1, &cy0, &cy1, &coky);
+        if (chx || chy) {
+            borderline[i] = 1;
+            if (ex1 >= ex0 && ey1 >= ey0) { ev[0] = ex0; ev[1] = ey0; ev[2] = ex1; ev[3] = ey1; }
+            if (cokx && coky) { co[0] = cx0; co[1] = cy0; co[2] = cx1; co[3] = cy1; }
+            else { co[0] = 0; co[1] = 0; co[2] = -1; co[3] = -1; }
+        }
     }
     return ORA_OK;
 }

@@ -159,28 +159,31 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
     c->have_proj = false;
     c->have_state = false;
     const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
+    const int stiles_x = (tiles_x + kSuper - 1) / kSuper, stiles_y = (tiles_y + kSuper - 1) / kSuper;
     const int64_t T = (int64_t)tiles_x * tiles_y;
+    const int64_t Ts = (int64_t)stiles_x * stiles_y;
     if (T > 0x7FFFFFFF) return fail(c, GS_ERR_INVALID_ARG, "too many tiles");
     const uint32_t n = (uint32_t)g->n;
 
     // per-Gaussian scratch
     if ((st = ensure(c, c->rec0, sizeof(float4) * n)) || (st = ensure(c, c->rec1, sizeof(float4) * n)) ||
         (st = ensure(c, c->rec2, sizeof(float4) * n)) || (st = ensure(c, c->depth, sizeof(float) * n)) ||
-        (st = ensure(c, c->radius, sizeof(int) * n)) || (st = ensure(c, c->rect, sizeof(int4) * n)) ||
+        (st = ensure(c, c->radius, sizeof(int) * n)) || (st = ensure(c, c->rect, sizeof(ushort4) * n)) ||
         (st = ensure(c, c->tiles_touched, sizeof(uint32_t) * n)) ||
+        (st = ensure(c, c->supers_touched, sizeof(uint32_t) * n)) ||
         (st = ensure(c, c->dkey[0], sizeof(uint32_t) * n)) || (st = ensure(c, c->dkey[1], sizeof(uint32_t) * n)) ||
         (st = ensure(c, c->did[0], sizeof(uint32_t) * n)) || (st = ensure(c, c->did[1], sizeof(uint32_t) * n)) ||
         (st = ensure(c, c->offsets, sizeof(uint32_t) * (n + 1))) ||
-        (st = ensure(c, c->scan_partials, sizeof(unsigned long long) * scan_partials_count(n))) ||
-        (st = ensure(c, c->ranges, sizeof(uint2) * T)) || (st = ensure(c, c->sort_hist, sizeof(uint32_t) * 8 * 256)) ||
+        (st = ensure(c, c->scan_partials, 2 * sizeof(unsigned long long) * scan_partials_count(n))) ||
+        (st = ensure(c, c->sranges, sizeof(uint2) * Ts)) || (st = ensure(c, c->sort_hist, sizeof(uint32_t) * 8 * 256)) ||
         (st = ensure(c, c->sort_counter, sizeof(uint32_t) * 8)))
         return st;
 
     const Records rec{as<float4>(c->rec0), as<float4>(c->rec1), as<float4>(c->rec2)};
     const CameraParams cp = make_camera(*cam, W, H);
     GS_CUDA(c, launch_project(c->stream, *g, cp, W, H, tiles_x, tiles_y, c->opt.mode, rec, as<float>(c->depth),
-                              as<int>(c->radius), as<int4>(c->rect), as<uint32_t>(c->tiles_touched),
-                              as<uint32_t>(c->dkey[0]), as<uint32_t>(c->did[0])));
+                              as<int>(c->radius), as<ushort4>(c->rect), as<uint32_t>(c->tiles_touched),
+                              as<uint32_t>(c->supers_touched), as<uint32_t>(c->dkey[0]), as<uint32_t>(c->did[0])));
 
     // depth order: stable radix sort of the FP32 depth bits (ids ascending)
     int sorted = 0;
@@ -195,44 +198,73 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
     c->sorted_ids_buf = sorted;
     const uint32_t* ids = as<uint32_t>(c->did[sorted]);
 
-    // pair offsets in depth order and the exact pair count
-    GS_CUDA(c, launch_scan_gathered(c->stream, as<uint32_t>(c->tiles_touched), ids, n, as<uint32_t>(c->offsets),
-                                    as<unsigned long long>(c->scan_partials)));
+    // super-tile pair offsets in depth order, their exact count Ps and the
+    // (tile, Gaussian) pair count P in the same pass
+    GS_CUDA(c, launch_scan_gathered(c->stream, as<uint32_t>(c->supers_touched), as<uint32_t>(c->tiles_touched), ids, n,
+                                    as<uint32_t>(c->offsets), as<unsigned long long>(c->scan_partials)));
     const size_t nb = scan_partials_count(n) - 1;
-    GS_CUDA(c, cudaMemcpyAsync(c->h_scalar, as<unsigned long long>(c->scan_partials) + (n ? nb : 0),
-                               sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+    unsigned long long* part = as<unsigned long long>(c->scan_partials);
+    GS_CUDA(c, cudaMemcpyAsync(c->h_scalar, part + nb, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+    GS_CUDA(c, cudaMemcpyAsync(c->h_scalar + 1, part + nb + 1 + nb, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                               c->stream));
     GS_CUDA(c, cudaStreamSynchronize(c->stream));
-    const unsigned long long P64 = *c->h_scalar;
+    const unsigned long long Ps64 = c->h_scalar[0], P64 = c->h_scalar[1];
     const int64_t limit = c->opt.max_pairs > 0 ? std::min<int64_t>(c->opt.max_pairs, kMaxPairs) : kMaxPairs;
     if ((int64_t)P64 > limit)
         return fail(c, GS_ERR_CAPACITY, "pair count %llu exceeds the limit %lld", P64, (long long)limit);
-    const uint32_t P = (uint32_t)P64;
+    if ((int64_t)Ps64 > kMaxPairs)
+        return fail(c, GS_ERR_CAPACITY, "super-tile pair count %llu exceeds %lld", Ps64, (long long)kMaxPairs);
+    const uint32_t Ps = (uint32_t)Ps64;
     if ((st = read_device_error(c))) return st;
 
-    if ((st = ensure(c, c->pairs[0], sizeof(uint64_t) * P)) || (st = ensure(c, c->pairs[1], sizeof(uint64_t) * P)))
+    if ((st = ensure(c, c->pairs[0], sizeof(uint64_t) * Ps)) || (st = ensure(c, c->pairs[1], sizeof(uint64_t) * Ps)))
         return st;
     uint64_t* pairs[2] = {as<uint64_t>(c->pairs[0]), as<uint64_t>(c->pairs[1])};
-    GS_CUDA(c, launch_emit_pairs(c->stream, ids, as<uint32_t>(c->offsets), as<int4>(c->rect), n, tiles_x, pairs[0]));
+    GS_CUDA(c, launch_emit_pairs(c->stream, ids, as<uint32_t>(c->offsets), as<ushort4>(c->rect), n, stiles_x, pairs[0]));
     int psorted = 0;
-    if (P > 1 && T > 1) {
-        const int tbits = bits_for((uint32_t)T);
-        if ((st = ensure(c, c->sort_status, sizeof(uint32_t) * radix_status_words(P, 32, 32 + tbits)))) return st;
-        GS_CUDA(c, radix_sort_u64_keys(c->stream, pairs, P, 32, 32 + tbits, as<uint32_t>(c->sort_hist),
+    if (Ps > 1 && Ts > 1) {
+        const int sbits = bits_for((uint32_t)Ts);
+        if ((st = ensure(c, c->sort_status, sizeof(uint32_t) * radix_status_words(Ps, 32, 32 + sbits)))) return st;
+        GS_CUDA(c, radix_sort_u64_keys(c->stream, pairs, Ps, 32, 32 + sbits, as<uint32_t>(c->sort_hist),
                                        as<uint32_t>(c->sort_status), as<uint32_t>(c->sort_counter),
                                        as<int>(c->errword), &psorted));
     }
     c->sorted_pairs_buf = psorted;
-    GS_CUDA(c, cudaMemsetAsync(c->ranges.p, 0, sizeof(uint2) * T, c->stream));
-    GS_CUDA(c, launch_tile_ranges(c->stream, pairs[psorted], P, (uint32_t)T, as<uint2>(c->ranges)));
+    GS_CUDA(c, cudaMemsetAsync(c->sranges.p, 0, sizeof(uint2) * Ts, c->stream));
+    GS_CUDA(c, launch_ranges(c->stream, pairs[psorted], Ps, (uint32_t)Ts, as<uint2>(c->sranges)));
 
     c->n = n;
     c->W = W;
     c->H = H;
     c->tiles_x = tiles_x;
     c->tiles_y = tiles_y;
-    c->P = P;
+    c->stiles_x = stiles_x;
+    c->stiles_y = stiles_y;
+    c->P = (int64_t)P64;
+    c->Ps = Ps;
     c->have_proj = true;
     return GS_OK;
+}
+
+BlendArgs blend_args(gs_ctx* c, float* out_C, float* out_grads)
+{
+    BlendArgs a;
+    a.W = c->W;
+    a.H = c->H;
+    a.tiles_x = c->tiles_x;
+    a.tiles_y = c->tiles_y;
+    a.stiles_x = c->stiles_x;
+    a.n = (uint32_t)c->n;
+    a.sranges = as<uint2>(c->sranges);
+    a.pair_words = reinterpret_cast<const uint32_t*>(c->pairs[c->sorted_pairs_buf].p);
+    a.rect = as<ushort4>(c->rect);
+    a.rec = Records{as<float4>(c->rec0), as<float4>(c->rec1), as<float4>(c->rec2)};
+    a.bg = make_float3(c->opt.bg[0], c->opt.bg[1], c->opt.bg[2]);
+    a.out_C = out_C;
+    a.out_G = out_grads;
+    a.state = as<float4>(c->state);
+    a.count = as<int>(c->count);
+    return a;
 }
 
 gs_status do_blend(gs_ctx* c, float* out_C, float* out_grads)
@@ -242,10 +274,8 @@ gs_status do_blend(gs_ctx* c, float* out_C, float* out_grads)
     const size_t npix = (size_t)c->W * c->H;
     gs_status st;
     if ((st = ensure(c, c->state, sizeof(float4) * npix)) || (st = ensure(c, c->count, sizeof(int) * npix))) return st;
-    const Records rec{as<float4>(c->rec0), as<float4>(c->rec1), as<float4>(c->rec2)};
-    GS_CUDA(c, launch_blend(c->stream, out_grads != nullptr, c->opt.mode, c->W, c->H, c->tiles_x, c->tiles_y,
-                            (uint32_t)c->n, as<uint2>(c->ranges), as<uint64_t>(c->pairs[c->sorted_pairs_buf]), rec, c->opt.bg[0],
-                            c->opt.bg[1], c->opt.bg[2], out_C, out_grads, as<float4>(c->state), as<int>(c->count)));
+    const BlendArgs a = blend_args(c, out_C, out_grads);
+    GS_CUDA(c, launch_blend(c->stream, out_grads != nullptr, c->opt.mode, a));
     c->have_state = true;
     return GS_OK;
 }
@@ -292,7 +322,7 @@ gs_status gs_create(gs_ctx** out, void* stream, const gs_options* opt)
         delete c;
         return GS_ERR_CUDA;
     }
-    if (cudaMallocHost((void**)&c->h_scalar, sizeof(unsigned long long)) != cudaSuccess) {
+    if (cudaMallocHost((void**)&c->h_scalar, 2 * sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return GS_ERR_OOM;
@@ -319,9 +349,10 @@ gs_status gs_destroy(gs_ctx* c)
     if (!c) return GS_ERR_INVALID_ARG;
     cudaStreamSynchronize(c->stream);
     DevBuf* bufs[] = {&c->rec0, &c->rec1, &c->rec2, &c->depth, &c->radius, &c->rect, &c->tiles_touched,
-                      &c->dkey[0], &c->dkey[1], &c->did[0], &c->did[1], &c->offsets, &c->scan_partials,
-                      &c->pairs[0], &c->pairs[1], &c->sort_hist, &c->sort_status, &c->sort_counter,
-                      &c->ranges, &c->state, &c->count, &c->errword};
+                      &c->supers_touched, &c->dkey[0], &c->dkey[1], &c->did[0], &c->did[1], &c->offsets,
+                      &c->scan_partials, &c->pairs[0], &c->pairs[1], &c->sort_hist, &c->sort_status,
+                      &c->sort_counter, &c->sranges, &c->tile_count, &c->tile_start, &c->state, &c->count,
+                      &c->errword};
     for (DevBuf* b : bufs) release(*b);
     if (c->h_scalar) cudaFreeHost(c->h_scalar);
     cudaGetLastError();
@@ -423,12 +454,15 @@ gs_status gs_read_bins(gs_ctx* c, uint64_t* keys, uint32_t* vals, uint32_t* rang
     if (!c->have_proj) return fail(c, GS_ERR_NOT_READY, "no projection");
     if ((keys || vals) && capacity < c->P) return fail(c, GS_ERR_CAPACITY, "capacity %lld < P %lld",
                                                        (long long)capacity, (long long)c->P);
-    if (keys || vals)
-        GS_CUDA(c, launch_finalize_bins(c->stream, as<uint64_t>(c->pairs[c->sorted_pairs_buf]), (uint32_t)c->P,
-                                        (uint32_t)c->n, as<float>(c->depth), keys, vals));
-    if (ranges)
-        GS_CUDA(c, cudaMemcpyAsync(ranges, c->ranges.p, sizeof(uint2) * (size_t)c->tiles_x * c->tiles_y,
-                                   cudaMemcpyDeviceToDevice, c->stream));
+    LaunchTally tally(c);
+    const size_t T = (size_t)c->tiles_x * c->tiles_y;
+    gs_status st;
+    if ((st = ensure(c, c->tile_count, sizeof(uint32_t) * T)) || (st = ensure(c, c->tile_start, sizeof(uint32_t) * T)))
+        return st;
+    GS_CUDA(c, launch_tile_lists(c->stream, as<uint64_t>(c->pairs[c->sorted_pairs_buf]), as<uint2>(c->sranges),
+                                 as<ushort4>(c->rect), as<float>(c->depth), (uint32_t)c->n, c->tiles_x, c->tiles_y,
+                                 c->stiles_x, as<uint32_t>(c->tile_count), as<uint32_t>(c->tile_start), keys, vals,
+                                 reinterpret_cast<uint2*>(ranges)));
     return GS_OK;
 }
 
@@ -459,11 +493,10 @@ gs_status gs_blend_stats(gs_ctx* c, int64_t* counts)
     if (st != GS_OK) return st;
     unsigned long long h[2] = {0, 0};
     cudaError_t e = cudaMemsetAsync(tmp.p, 0, 2 * sizeof(unsigned long long), c->stream);
-    const Records rec{as<float4>(c->rec0), as<float4>(c->rec1), as<float4>(c->rec2)};
-    if (e == cudaSuccess)
-        e = launch_blend_stats(c->stream, c->opt.mode, c->W, c->H, c->tiles_x, c->tiles_y, (uint32_t)c->n,
-                               as<uint2>(c->ranges), as<uint64_t>(c->pairs[c->sorted_pairs_buf]), rec,
-                               as<unsigned long long>(tmp));
+    if (e == cudaSuccess) {
+        const BlendArgs a = blend_args(c, nullptr, nullptr);
+        e = launch_blend_stats(c->stream, c->opt.mode, a, as<unsigned long long>(tmp));
+    }
     if (e == cudaSuccess) e = cudaMemcpyAsync(h, tmp.p, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     release(tmp);

@@ -1,19 +1,23 @@
 // Tile binning (the front-to-back ordering of Sec. 4, per tile).
 //
 // Gaussians are first sorted by the FP32 bits of their view depth (a stable
-// radix sort of n keys, ids ascending), then each one emits (tile << 32 | id)
-// for every tile of its rect, in depth order.  A stable radix sort on the tile
-// bits alone then yields the pairs ordered by (tile, depth, id): the per-tile
-// lists the blend walks front to back.  Sorting n depths once and only the
-// tile bits of the P pairs moves ~4x fewer bytes than sorting P 64-bit
-// (tile, depth) keys with values.
+// radix sort of n keys, ids ascending).  Each Gaussian then emits
+// (super-tile << 32 | id) for every 64x64-pixel super-tile (4x4 tiles) its tile
+// rect touches, in depth order, and a stable radix sort on the super-tile bits
+// alone yields per-super-tile lists ordered by (depth, id).  The blend filters
+// a super-tile's list by each Gaussian's tile rect, which reproduces every
+// tile's own front-to-back list exactly while sorting 3-5x fewer pairs than
+// per-tile binning (and 8 B instead of 12 B per pair and pass).
+//
+// The per-tile lists themselves (keys tile << 32 | depth bits, ids, ranges)
+// are materialised only on request (gs_read_bins), by the same filter.
 #include "gs_internal.cuh"
 
 namespace gs {
 namespace {
 
 __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ ids, const uint32_t* __restrict__ offsets,
-                                              const int4* __restrict__ rect, uint32_t n, int tiles_x,
+                                              const ushort4* __restrict__ rect, uint32_t n, int stiles_x,
                                               uint64_t* __restrict__ pairs)
 {
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -23,11 +27,12 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ ids, 
     if (off == end) return;
     const uint32_t id = ids[k];
     if (id >= n) return;   // only after an expired bounded wait in the sort
-    const int4 r = rect[id];
-    for (int ty = r.y; ty <= r.w; ++ty)
-        for (int tx = r.x; tx <= r.z && off < end; ++tx) {
-            const uint64_t t = (uint64_t)(ty * tiles_x + tx);
-            pairs[off++] = (t << 32) | id;
+    const ushort4 r = rect[id];
+    const int sx0 = r.x / kSuper, sx1 = r.z / kSuper, sy0 = r.y / kSuper, sy1 = r.w / kSuper;
+    for (int sy = sy0; sy <= sy1; ++sy)
+        for (int sx = sx0; sx <= sx1 && off < end; ++sx) {
+            const uint64_t s = (uint64_t)(sy * stiles_x + sx);
+            pairs[off++] = (s << 32) | id;
         }
 }
 
@@ -42,41 +47,115 @@ __global__ void __launch_bounds__(256) k_ranges(const uint64_t* __restrict__ pai
     if (i == P - 1 || (uint32_t)(pairs[i + 1] >> 32) != t) ranges[t].y = i + 1;
 }
 
-__global__ void __launch_bounds__(256) k_finalize(const uint64_t* __restrict__ pairs, uint32_t P, uint32_t n,
-                                                  const float* __restrict__ depth, uint64_t* __restrict__ keys,
-                                                  uint32_t* __restrict__ vals)
+__device__ __forceinline__ bool covers(ushort4 r, int tx, int ty)
 {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P) return;
-    const uint64_t p = pairs[i];
-    const uint32_t id = (uint32_t)p;
-    const uint32_t dbits = id < n ? __float_as_uint(depth[id]) : 0xFFFFFFFFu;
-    if (keys) keys[i] = (p & 0xFFFFFFFF00000000ull) | (uint64_t)dbits;
-    if (vals) vals[i] = id;
+    return (int)r.x <= tx && tx <= (int)r.z && (int)r.y <= ty && ty <= (int)r.w;
+}
+
+// Per-tile list materialisation: one block per tile walks its super-tile's list.
+// WRITE = false: count the tile's Gaussians; WRITE = true: write them, in
+// order, at tile_start[t].
+template <bool WRITE>
+__global__ void __launch_bounds__(256) k_tile_lists(const uint64_t* __restrict__ spairs, const uint2* __restrict__ sranges,
+                                                    const ushort4* __restrict__ rect, const float* __restrict__ depth,
+                                                    uint32_t n, int tiles_x, int stiles_x, uint32_t* __restrict__ count,
+                                                    const uint32_t* __restrict__ tile_start, uint64_t* __restrict__ keys,
+                                                    uint32_t* __restrict__ vals)
+{
+    __shared__ int s_wcnt[8];
+    const int t = blockIdx.x;
+    const int tx = t % tiles_x, ty = t / tiles_x;
+    const uint2 sr = sranges[(ty / kSuper) * stiles_x + tx / kSuper];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t base = WRITE ? tile_start[t] : 0u;
+    for (uint32_t c0 = sr.x; c0 < sr.y; c0 += 256) {
+        const uint32_t c = c0 + threadIdx.x;
+        uint32_t id = 0xFFFFFFFFu;
+        bool hit = false;
+        if (c < sr.y) {
+            id = (uint32_t)spairs[c];
+            hit = id < n && covers(rect[id], tx, ty);
+        }
+        const uint32_t ball = __ballot_sync(0xffffffffu, hit);
+        if (lane == 0) s_wcnt[warp] = __popc(ball);
+        __syncthreads();
+        int wbase = 0, tot = 0;
+        for (int w = 0; w < 8; ++w) {
+            wbase += w < warp ? s_wcnt[w] : 0;
+            tot += s_wcnt[w];
+        }
+        if (WRITE && hit) {
+            const uint32_t pos = base + wbase + __popc(ball & ((1u << lane) - 1u));
+            if (keys) keys[pos] = ((uint64_t)t << 32) | (uint64_t)__float_as_uint(depth[id]);
+            if (vals) vals[pos] = id;
+        }
+        base += tot;
+        __syncthreads();
+    }
+    if (!WRITE && threadIdx.x == 0) count[t] = base;
+}
+
+// single-block exclusive scan of the per-tile counts -> starts and [start, end) ranges
+__global__ void __launch_bounds__(1024) k_tile_starts(const uint32_t* __restrict__ count, uint32_t T,
+                                                      uint32_t* __restrict__ start, uint2* __restrict__ ranges)
+{
+    __shared__ uint32_t s_warp[32];
+    uint32_t carry = 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t b0 = 0; b0 < T; b0 += 1024) {
+        const uint32_t i = b0 + threadIdx.x;
+        const uint32_t v = i < T ? count[i] : 0u;
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        uint32_t wb = 0, tot = 0;
+        for (int w = 0; w < 32; ++w) {
+            wb += w < warp ? s_warp[w] : 0u;
+            tot += s_warp[w];
+        }
+        if (i < T) {
+            const uint32_t st = carry + wb + x - v;
+            start[i] = st;
+            if (ranges) ranges[i] = v ? make_uint2(st, st + v) : make_uint2(0u, 0u);
+        }
+        carry += tot;
+        __syncthreads();
+    }
 }
 
 }  // namespace
 
-cudaError_t launch_emit_pairs(cudaStream_t s, const uint32_t* ids, const uint32_t* offsets, const int4* rect,
-                              uint32_t n, int tiles_x, uint64_t* pairs)
+cudaError_t launch_emit_pairs(cudaStream_t s, const uint32_t* ids, const uint32_t* offsets, const ushort4* rect,
+                              uint32_t n, int stiles_x, uint64_t* pairs)
 {
     if (n == 0) return cudaSuccess;
-    k_emit<<<(n + 255) / 256, 256, 0, s>>>(ids, offsets, rect, n, tiles_x, pairs); note_launch();
+    k_emit<<<(n + 255) / 256, 256, 0, s>>>(ids, offsets, rect, n, stiles_x, pairs); note_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_tile_ranges(cudaStream_t s, const uint64_t* pairs, uint32_t P, uint32_t T, uint2* ranges)
+cudaError_t launch_ranges(cudaStream_t s, const uint64_t* pairs, uint32_t P, uint32_t T, uint2* ranges)
 {
     if (P == 0) return cudaSuccess;
     k_ranges<<<(P + 255) / 256, 256, 0, s>>>(pairs, P, T, ranges); note_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize_bins(cudaStream_t s, const uint64_t* pairs, uint32_t P, uint32_t n, const float* depth,
-                                 uint64_t* keys, uint32_t* vals)
+cudaError_t launch_tile_lists(cudaStream_t s, const uint64_t* spairs, const uint2* sranges, const ushort4* rect,
+                              const float* depth, uint32_t n, int tiles_x, int tiles_y, int stiles_x,
+                              uint32_t* count, uint32_t* start, uint64_t* keys, uint32_t* vals, uint2* ranges)
 {
-    if (P == 0) return cudaSuccess;
-    k_finalize<<<(P + 255) / 256, 256, 0, s>>>(pairs, P, n, depth, keys, vals); note_launch();
+    const int T = tiles_x * tiles_y;
+    k_tile_lists<false><<<T, 256, 0, s>>>(spairs, sranges, rect, depth, n, tiles_x, stiles_x, count, nullptr, nullptr,
+                                          nullptr); note_launch();
+    k_tile_starts<<<1, 1024, 0, s>>>(count, (uint32_t)T, start, ranges); note_launch();
+    if (keys || vals) {
+        k_tile_lists<true><<<T, 256, 0, s>>>(spairs, sranges, rect, depth, n, tiles_x, stiles_x, count, start, keys,
+                                             vals); note_launch();
+    }
     return cudaGetLastError();
 }
 

@@ -2,11 +2,16 @@
 // derivatives of the pixel colour (Sec. 4 blend equation; Sec. 5 "3DGS Image
 // Gradients"; supplement "Forward pass").
 //
-// One 256-thread block per 16x16 tile, one pixel per thread.  The tile's list
-// is walked in batches of 256 records staged in shared memory (one global load
-// per record per block, broadcast reads per pixel).  A pixel stops when its
-// transmittance would fall below 1e-4; a warp whose pixels have all stopped
-// skips the rest of each batch, and the block leaves once every pixel stopped.
+// One 256-thread block per 16x16 tile, one pixel per thread.  Binning is done
+// per 64x64 super-tile (4x4 tiles): the block walks its super-tile's
+// depth-ordered list 256 candidates at a time, keeps the Gaussians whose tile
+// rect covers this tile (an order-preserving block compaction, so the kept
+// sequence is exactly the tile's own front-to-back list), stages their records
+// in shared memory and blends them.  The next round's candidate ids and rects
+// are fetched before the current batch is blended, hiding their latency.  A
+// pixel stops when its transmittance would fall below 1e-4; a warp whose
+// pixels have all stopped skips the rest of each batch, and the block leaves
+// once every pixel stopped.
 //
 // The state carried per pixel is the transmittance T = 1 - A and its
 // derivatives (the paper's A-recurrences with the sign flipped): tracking T
@@ -25,29 +30,35 @@ namespace gs {
 namespace {
 
 constexpr int kBlock = kTilePixels;   // 256
+constexpr int kWarps = kBlock / 32;
+
+__device__ __forceinline__ bool covers(ushort4 r, int tx, int ty)
+{
+    return (int)r.x <= tx && tx <= (int)r.z && (int)r.y <= ty && ty <= (int)r.w;
+}
 
 // STATS: count the (pixel, Gaussian) pairs evaluated and blended instead of
 // writing images (used once, outside timed regions, to size the FLOP count).
 template <bool GRADS, int MODE, bool STATS = false>
-__global__ void __launch_bounds__(kBlock) k_blend(int W, int H, int tiles_x, uint32_t n, const uint2* __restrict__ ranges,
-                                                  const uint32_t* __restrict__ pair_words, Records rec, float3 bg,
-                                                  float* __restrict__ out_C, float* __restrict__ out_G,
-                                                  float4* __restrict__ state, int* __restrict__ count_out,
-                                                  unsigned long long* __restrict__ stats = nullptr)
+__global__ void __launch_bounds__(kBlock) k_blend(BlendArgs a, unsigned long long* __restrict__ stats = nullptr)
 {
     __shared__ float4 s_r0[kBlock];
     __shared__ float4 s_r1[kBlock];
     __shared__ float4 s_r2[kBlock];
+    __shared__ int s_wcnt[kWarps];
 
     const int tile = blockIdx.x;
-    const int tx = tile % tiles_x, ty = tile / tiles_x;
+    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
     const int x = tx * kTile + lx, y = ty * kTile + ly;
-    const bool inside = x < W && y < H;
+    const bool inside = x < a.W && y < a.H;
     const float px = (float)x, py = (float)y;
+    const uint32_t lanemask_lt = (1u << lane) - 1u;
 
-    const uint2 rg = ranges[tile];
-    const int total = (int)(rg.y - rg.x);
+    const int S = (ty / kSuper) * a.stiles_x + (tx / kSuper);
+    const uint2 sr = a.sranges[S];
+    const int total = (int)(sr.y - sr.x);
 
     float T = 1.f, Tx = 0.f, Ty = 0.f, Txy = 0.f;
     float C0 = 0.f, C1 = 0.f, C2 = 0.f;
@@ -55,36 +66,55 @@ __global__ void __launch_bounds__(kBlock) k_blend(int W, int H, int tiles_x, uin
     float Y0 = 0.f, Y1 = 0.f, Y2 = 0.f;
     float Z0 = 0.f, Z1 = 0.f, Z2 = 0.f;
     int last = 0;
+    int list_base = 0;    // position of this round's first kept Gaussian in the tile's list
     bool done = !inside;
     uint32_t n_eval = 0, n_acc = 0;
 
-    for (int b0 = 0; b0 < total; b0 += kBlock) {
+    // candidate of the first round
+    uint32_t cid = 0xFFFFFFFFu;
+    ushort4 crect = make_ushort4(1, 1, 0, 0);
+    if ((int)threadIdx.x < total) {
+        cid = a.pair_words[2 * (size_t)(sr.x + threadIdx.x)];
+        if (cid < a.n) crect = a.rect[cid];
+    }
+
+    for (int c0 = 0; c0 < total; c0 += kBlock) {
         if (__syncthreads_count(done) == kBlock) break;
-        const int j = b0 + threadIdx.x;
-        if (j < total) {
-            // low word of the (tile << 32 | id) pair
-            const uint32_t id = pair_words[2 * (size_t)(rg.x + j)];
-            if (id < n) {
-                s_r0[threadIdx.x] = rec.r0[id];
-                s_r1[threadIdx.x] = rec.r1[id];
-                s_r2[threadIdx.x] = rec.r2[id];
-            } else {   // only after an expired bounded wait in the sort: a record that never blends
-                s_r0[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
-                s_r1[threadIdx.x] = make_float4(0.f, 0.f, INFINITY, 0.f);
-                s_r2[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
+        // order-preserving compaction of the candidates that cover this tile
+        const bool hit = cid < a.n && covers(crect, tx, ty);
+        const uint32_t ball = __ballot_sync(0xffffffffu, hit);
+        if (lane == 0) s_wcnt[warp] = __popc(ball);
+        __syncthreads();
+        int wbase = 0, batch = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            const int cw = s_wcnt[w];
+            wbase += w < warp ? cw : 0;
+            batch += cw;
+        }
+        if (hit) {
+            const int pos = wbase + __popc(ball & lanemask_lt);
+            s_r0[pos] = a.rec.r0[cid];
+            s_r1[pos] = a.rec.r1[cid];
+            s_r2[pos] = a.rec.r2[cid];
+        }
+        // fetch the next round's candidate while this batch is blended
+        const int cn = c0 + kBlock + (int)threadIdx.x;
+        cid = 0xFFFFFFFFu;
+        if (cn < total) {
+            cid = a.pair_words[2 * (size_t)(sr.x + cn)];
+            if (cid < a.n) crect = a.rect[cid];
         }
         __syncthreads();
-        const int cnt = min(kBlock, total - b0);
-        for (int k = 0; !done && k < cnt; ++k) {
-            const float4 a = s_r0[k];
-            const float4 b = s_r1[k];
-            const float dx = px - a.x, dy = py - a.y;
+        for (int k = 0; !done && k < batch; ++k) {
+            const float4 r0 = s_r0[k];
+            const float4 r1 = s_r1[k];
+            const float dx = px - r0.x, dy = py - r0.y;
             if (STATS) ++n_eval;
             // g = -1/2 (a dx^2 + 2 b dx dy + c dy^2)
-            const float g = -0.5f * (a.z * dx * dx + b.x * dy * dy) - a.w * dx * dy;
-            if (MODE == GS_MODE_3DGS && g < b.z) continue;     // sigma e^g < 1/255 for sure
-            float alpha = b.y * __expf(g);
+            const float g = -0.5f * (r0.z * dx * dx + r1.x * dy * dy) - r0.w * dx * dy;
+            if (MODE == GS_MODE_3DGS && g < r1.z) continue;     // sigma e^g < 1/255 for sure
+            float alpha = r1.y * __expf(g);
             bool clamped = false;
             if (MODE == GS_MODE_3DGS) {
                 if (alpha < (1.f / 255.f)) continue;
@@ -102,9 +132,9 @@ __global__ void __launch_bounds__(kBlock) k_blend(int W, int H, int tiles_x, uin
             C1 = fmaf(c.y, w, C1);
             C2 = fmaf(c.z, w, C2);
             if (GRADS) {
-                float gx = -(a.z * dx + a.w * dy);
-                float gy = -(a.w * dx + b.x * dy);
-                float gxy = fmaf(gx, gy, -a.w);
+                float gx = -(r0.z * dx + r0.w * dy);
+                float gy = -(r0.w * dx + r1.x * dy);
+                float gxy = fmaf(gx, gy, -r0.w);
                 if (clamped) { gx = 0.f; gy = 0.f; gxy = 0.f; }
                 const float wx = alpha * fmaf(T, gx, Tx);
                 const float wy = alpha * fmaf(T, gy, Ty);
@@ -117,91 +147,71 @@ __global__ void __launch_bounds__(kBlock) k_blend(int W, int H, int tiles_x, uin
                 Txy -= wxy;
             }
             T = Tn;
-            last = b0 + k + 1;
+            last = list_base + k + 1;
             if (STATS) ++n_acc;
         }
+        list_base += batch;
     }
     if (STATS) {
-        unsigned long long e = n_eval, a = n_acc;
+        unsigned long long e = n_eval, acc = n_acc;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             e += __shfl_down_sync(0xffffffffu, e, o);
-            a += __shfl_down_sync(0xffffffffu, a, o);
+            acc += __shfl_down_sync(0xffffffffu, acc, o);
         }
-        if ((threadIdx.x & 31) == 0) {
+        if (lane == 0) {
             atomicAdd(&stats[0], e);
-            atomicAdd(&stats[1], a);
+            atomicAdd(&stats[1], acc);
         }
         return;
     }
     if (!inside) return;
-    const size_t plane = (size_t)W * H;
-    const size_t pix = (size_t)y * W + x;
-    out_C[pix] = fmaf(T, bg.x, C0);
-    out_C[plane + pix] = fmaf(T, bg.y, C1);
-    out_C[2 * plane + pix] = fmaf(T, bg.z, C2);
+    const size_t plane = (size_t)a.W * a.H;
+    const size_t pix = (size_t)y * a.W + x;
+    a.out_C[pix] = fmaf(T, a.bg.x, C0);
+    a.out_C[plane + pix] = fmaf(T, a.bg.y, C1);
+    a.out_C[2 * plane + pix] = fmaf(T, a.bg.z, C2);
     if (GRADS) {
-        out_G[pix] = fmaf(Tx, bg.x, X0);
-        out_G[plane + pix] = fmaf(Tx, bg.y, X1);
-        out_G[2 * plane + pix] = fmaf(Tx, bg.z, X2);
-        out_G[3 * plane + pix] = fmaf(Ty, bg.x, Y0);
-        out_G[4 * plane + pix] = fmaf(Ty, bg.y, Y1);
-        out_G[5 * plane + pix] = fmaf(Ty, bg.z, Y2);
-        out_G[6 * plane + pix] = fmaf(Txy, bg.x, Z0);
-        out_G[7 * plane + pix] = fmaf(Txy, bg.y, Z1);
-        out_G[8 * plane + pix] = fmaf(Txy, bg.z, Z2);
+        float* G = a.out_G;
+        G[pix] = fmaf(Tx, a.bg.x, X0);
+        G[plane + pix] = fmaf(Tx, a.bg.y, X1);
+        G[2 * plane + pix] = fmaf(Tx, a.bg.z, X2);
+        G[3 * plane + pix] = fmaf(Ty, a.bg.x, Y0);
+        G[4 * plane + pix] = fmaf(Ty, a.bg.y, Y1);
+        G[5 * plane + pix] = fmaf(Ty, a.bg.z, Y2);
+        G[6 * plane + pix] = fmaf(Txy, a.bg.x, Z0);
+        G[7 * plane + pix] = fmaf(Txy, a.bg.y, Z1);
+        G[8 * plane + pix] = fmaf(Txy, a.bg.z, Z2);
     }
-    if (state) state[pix] = make_float4(T, Tx, Ty, Txy);
-    if (count_out) count_out[pix] = last;
+    if (a.state) a.state[pix] = make_float4(T, Tx, Ty, Txy);
+    if (a.count) a.count[pix] = last;
 }
 
 template <bool GRADS, int MODE>
-cudaError_t launch_t(cudaStream_t s, int W, int H, int tiles_x, int tiles_y, uint32_t n, const uint2* ranges,
-                     const uint64_t* pairs, Records rec, float3 bg, float* out_C, float* out_G, float4* state,
-                     int* count)
+cudaError_t launch_t(cudaStream_t s, const BlendArgs& a)
 {
-    const int tiles = tiles_x * tiles_y;
-    k_blend<GRADS, MODE><<<tiles, kBlock, 0, s>>>(W, H, tiles_x, n, ranges, reinterpret_cast<const uint32_t*>(pairs),
-                                                 rec, bg, out_C, out_G, state, count); note_launch();
+    k_blend<GRADS, MODE><<<a.tiles_x * a.tiles_y, kBlock, 0, s>>>(a); note_launch();
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_blend_stats(cudaStream_t s, int mode, int W, int H, int tiles_x, int tiles_y, uint32_t n,
-                               const uint2* ranges, const uint64_t* pairs, Records rec,
-                               unsigned long long* stats)
+cudaError_t launch_blend_stats(cudaStream_t s, int mode, const BlendArgs& a, unsigned long long* stats)
 {
-    const int tiles = tiles_x * tiles_y;
-    const float3 bg = make_float3(0.f, 0.f, 0.f);
-    const uint32_t* pw = reinterpret_cast<const uint32_t*>(pairs);
+    const int tiles = a.tiles_x * a.tiles_y;
     if (mode == GS_MODE_EXACT)
-        k_blend<true, GS_MODE_EXACT, true><<<tiles, kBlock, 0, s>>>(W, H, tiles_x, n, ranges, pw, rec, bg, nullptr,
-                                                                  nullptr, nullptr, nullptr, stats);
+        k_blend<true, GS_MODE_EXACT, true><<<tiles, kBlock, 0, s>>>(a, stats);
     else
-        k_blend<true, GS_MODE_3DGS, true><<<tiles, kBlock, 0, s>>>(W, H, tiles_x, n, ranges, pw, rec, bg, nullptr,
-                                                                 nullptr, nullptr, nullptr, stats);
+        k_blend<true, GS_MODE_3DGS, true><<<tiles, kBlock, 0, s>>>(a, stats);
     note_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_blend(cudaStream_t s, bool grads, int mode, int W, int H, int tiles_x, int tiles_y, uint32_t n,
-                         const uint2* ranges, const uint64_t* pairs, Records rec, float bg0, float bg1, float bg2,
-                         float* out_C, float* out_grads, float4* state, int* count)
+cudaError_t launch_blend(cudaStream_t s, bool grads, int mode, const BlendArgs& a)
 {
-    const float3 bg = make_float3(bg0, bg1, bg2);
-    if (grads) {
-        if (mode == GS_MODE_EXACT)
-            return launch_t<true, GS_MODE_EXACT>(s, W, H, tiles_x, tiles_y, n, ranges, pairs, rec, bg, out_C,
-                                                 out_grads, state, count);
-        return launch_t<true, GS_MODE_3DGS>(s, W, H, tiles_x, tiles_y, n, ranges, pairs, rec, bg, out_C, out_grads,
-                                            state, count);
-    }
-    if (mode == GS_MODE_EXACT)
-        return launch_t<false, GS_MODE_EXACT>(s, W, H, tiles_x, tiles_y, n, ranges, pairs, rec, bg, out_C, nullptr,
-                                              state, count);
-    return launch_t<false, GS_MODE_3DGS>(s, W, H, tiles_x, tiles_y, n, ranges, pairs, rec, bg, out_C, nullptr, state,
-                                         count);
+    if (grads)
+        return mode == GS_MODE_EXACT ? launch_t<true, GS_MODE_EXACT>(s, a) : launch_t<true, GS_MODE_3DGS>(s, a);
+    return mode == GS_MODE_EXACT ? launch_t<false, GS_MODE_EXACT>(s, a) : launch_t<false, GS_MODE_3DGS>(s, a);
 }
 
 }  // namespace gs

@@ -10,6 +10,7 @@ namespace gs {
 
 constexpr int kTile = 16;                 // tile side in pixels (16 x 16 = 256 pixels)
 constexpr int kTilePixels = kTile * kTile;
+constexpr int kSuper = 4;                 // super-tile side in tiles (64 x 64 pixels)
 
 // Device error word values (written by bounded waits / device checks).
 constexpr int kDevOk = 0;
@@ -42,6 +43,21 @@ struct DevBuf {
     size_t cap = 0;
 };
 
+// Arguments of the blend kernel.
+struct BlendArgs {
+    int W, H, tiles_x, tiles_y, stiles_x;
+    uint32_t n;
+    const uint2* sranges;          // [super-tiles] list ranges
+    const uint32_t* pair_words;    // sorted (super << 32 | id) pairs viewed as 32-bit words
+    const ushort4* rect;           // [n] tile rect (x0, y0, x1, y1) inclusive
+    Records rec;
+    float3 bg;
+    float* out_C;
+    float* out_G;
+    float4* state;
+    int* count;
+};
+
 }  // namespace gs
 
 struct gs_ctx {
@@ -54,26 +70,29 @@ struct gs_ctx {
     bool have_proj = false;
     bool have_state = false;
     int64_t n = 0;
-    int W = 0, H = 0, tiles_x = 0, tiles_y = 0;
-    int64_t P = 0;
+    int W = 0, H = 0, tiles_x = 0, tiles_y = 0, stiles_x = 0, stiles_y = 0;
+    int64_t P = 0;                      // (tile, Gaussian) pairs
+    int64_t Ps = 0;                     // (super-tile, Gaussian) pairs
 
     // per Gaussian
     gs::DevBuf rec0, rec1, rec2;        // float4[n]
     gs::DevBuf depth;                   // float[n]
     gs::DevBuf radius;                  // int32[n]
-    gs::DevBuf rect;                    // int4[n] inclusive tile rect
-    gs::DevBuf tiles_touched;           // uint32[n]
+    gs::DevBuf rect;                    // ushort4[n] inclusive tile rect
+    gs::DevBuf tiles_touched;           // uint32[n] tiles of the rect
+    gs::DevBuf supers_touched;          // uint32[n] super-tiles of the rect
     gs::DevBuf dkey[2], did[2];         // depth sort keys / ids, ping-pong
     gs::DevBuf offsets;                 // uint32[n + 1]
-    gs::DevBuf scan_partials;           // uint64[blocks + 1]
-    // per pair
-    gs::DevBuf pairs[2];                // uint64[P] (tile << 32 | id), ping-pong
+    gs::DevBuf scan_partials;           // uint64[2][blocks + 1]
+    // per super-tile pair
+    gs::DevBuf pairs[2];                // uint64[Ps] (super-tile << 32 | id), ping-pong
     // radix sort scratch
     gs::DevBuf sort_hist;               // uint32[passes][256]
     gs::DevBuf sort_status;             // uint32[passes][tiles][256]
     gs::DevBuf sort_counter;            // uint32[passes]
     // per tile / pixel
-    gs::DevBuf ranges;                  // uint2[tiles]
+    gs::DevBuf sranges;                 // uint2[super-tiles]
+    gs::DevBuf tile_count, tile_start;  // uint32[tiles] (per-tile list materialisation)
     gs::DevBuf state;                   // float4[W*H]
     gs::DevBuf count;                   // int32[W*H]
     gs::DevBuf errword;                 // int32
@@ -94,7 +113,8 @@ inline void note_launch() { ++launch_counter(); }
 // ---- launchers (each returns the cudaError_t of its launch) ----
 cudaError_t launch_project(cudaStream_t s, const gs_gaussians& g, const CameraParams& cam, int W, int H,
                            int tiles_x, int tiles_y, int mode, Records rec, float* depth, int* radius,
-                           int4* rect, uint32_t* tiles_touched, uint32_t* depth_key, uint32_t* ids);
+                           ushort4* rect, uint32_t* tiles_touched, uint32_t* supers_touched, uint32_t* depth_key,
+                           uint32_t* ids);
 
 // LSD radix sort of n keys (uint32 keys with uint32 values, or uint64 keys
 // alone) on bits [bit_lo, bit_hi).  Ping-pong buffers: the result lands in
@@ -108,28 +128,27 @@ cudaError_t radix_sort_u64_keys(cudaStream_t s, uint64_t* keys[2], uint32_t n, i
 size_t radix_status_words(uint32_t n, int bit_lo, int bit_hi);
 int radix_passes(int bit_lo, int bit_hi);
 
-// exclusive scan of tiles_touched[ids[k]] over k -> offsets[k]; partials[nb]
-// (nb = scan_partials_count(n) - 1) receives the exact 64-bit total
-cudaError_t launch_scan_gathered(cudaStream_t s, const uint32_t* tiles_touched, const uint32_t* ids,
+// exclusive scan of counts[ids[k]] over k -> offsets[k]; partials[nb]
+// (nb = scan_partials_count(n) - 1) receives the exact 64-bit total, and
+// partials[nb + 1 + nb] the 64-bit total of side[ids[k]] (a second count
+// reduced in the same pass)
+cudaError_t launch_scan_gathered(cudaStream_t s, const uint32_t* counts, const uint32_t* side, const uint32_t* ids,
                                  uint32_t n, uint32_t* offsets, unsigned long long* partials);
 size_t scan_partials_count(uint32_t n);
 
-cudaError_t launch_emit_pairs(cudaStream_t s, const uint32_t* ids, const uint32_t* offsets, const int4* rect,
-                              uint32_t n, int tiles_x, uint64_t* pairs);
-cudaError_t launch_tile_ranges(cudaStream_t s, const uint64_t* pairs, uint32_t P, uint32_t T, uint2* ranges);
-cudaError_t launch_finalize_bins(cudaStream_t s, const uint64_t* pairs, uint32_t P, uint32_t n, const float* depth,
-                                 uint64_t* keys, uint32_t* vals);
+cudaError_t launch_emit_pairs(cudaStream_t s, const uint32_t* ids, const uint32_t* offsets, const ushort4* rect,
+                              uint32_t n, int stiles_x, uint64_t* pairs);
+cudaError_t launch_ranges(cudaStream_t s, const uint64_t* pairs, uint32_t P, uint32_t T, uint2* ranges);
+// per-tile lists from the super-tile lists: counts, starts, ranges and (optionally) keys/vals
+cudaError_t launch_tile_lists(cudaStream_t s, const uint64_t* spairs, const uint2* sranges, const ushort4* rect,
+                              const float* depth, uint32_t n, int tiles_x, int tiles_y, int stiles_x,
+                              uint32_t* count, uint32_t* start, uint64_t* keys, uint32_t* vals, uint2* ranges);
 cudaError_t launch_unpack_projected(cudaStream_t s, Records rec, const int* radius, const uint32_t* tiles_touched,
                                     const float* depth_in, uint32_t n, float* mean2d, float* conic, float* rgb,
                                     float* opacity, float* depth, int32_t* radius_out, int32_t* tiles_out);
 
-cudaError_t launch_blend(cudaStream_t s, bool grads, int mode, int W, int H, int tiles_x, int tiles_y, uint32_t n,
-                         const uint2* ranges, const uint64_t* pairs, Records rec, float bg0, float bg1,
-                         float bg2, float* out_C, float* out_grads, float4* state, int* count);
-
-cudaError_t launch_blend_stats(cudaStream_t s, int mode, int W, int H, int tiles_x, int tiles_y, uint32_t n,
-                               const uint2* ranges, const uint64_t* pairs, Records rec,
-                               unsigned long long* stats);
+cudaError_t launch_blend(cudaStream_t s, bool grads, int mode, const BlendArgs& a);
+cudaError_t launch_blend_stats(cudaStream_t s, int mode, const BlendArgs& a, unsigned long long* stats);
 
 cudaError_t launch_upscale(cudaStream_t s, const float* C, const float* grads, int W, int H, int factor,
                            float* out);

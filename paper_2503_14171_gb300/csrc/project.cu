@@ -76,15 +76,39 @@ __device__ __forceinline__ void sh_colour(const float* __restrict__ sh, int deg,
     out[2] = fmaxf(0.f, b + 0.5f);
 }
 
-__global__ void __launch_bounds__(256) k_project(
+constexpr int kProjThreads = 128;
+
+// DEG: SH degree 0..3, or -1 for direct RGB colours.  Each warp first copies the
+// SH coefficients of its 32 Gaussians (contiguous, (DEG+1)^2 * 3 floats each)
+// into shared memory with coalesced loads; the row pitch is padded to an odd
+// number of words so the per-thread reads are free of bank conflicts.
+template <int DEG>
+__global__ void __launch_bounds__(kProjThreads) k_project(
     int n, const float* __restrict__ means, const float* __restrict__ log_scales,
     const float* __restrict__ quats, const float* __restrict__ op_logits, const float* __restrict__ sh,
-    int sh_deg, const float* __restrict__ rgb_in, CameraParams cam, int W, int H, int tiles_x, int tiles_y,
+    const float* __restrict__ rgb_in, CameraParams cam, int W, int H, int tiles_x, int tiles_y,
     int mode, Records rec, float* __restrict__ depth_out, int* __restrict__ radius_out,
-    int4* __restrict__ rect_out, uint32_t* __restrict__ tiles_out, uint32_t* __restrict__ depth_key,
-    uint32_t* __restrict__ ids)
+    ushort4* __restrict__ rect_out, uint32_t* __restrict__ tiles_out, uint32_t* __restrict__ supers_out,
+    uint32_t* __restrict__ depth_key, uint32_t* __restrict__ ids)
 {
+    constexpr int KF = DEG >= 0 ? (DEG + 1) * (DEG + 1) * 3 : 1;   // floats per Gaussian
+    constexpr int PITCH = KF | 1;
+    __shared__ float s_sh[kProjThreads / 32][32][PITCH];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (DEG >= 0) {
+        const int wbase = blockIdx.x * blockDim.x + warp * 32;
+        const int cnt = min(32, n - wbase);
+        if (cnt > 0) {
+            const float* src = sh + (size_t)wbase * KF;
+            const int tot = cnt * KF;
+            for (int q = lane; q < tot; q += 32) {
+                const int gi = q / KF;
+                s_sh[warp][gi][q - gi * KF] = src[q];
+            }
+        }
+        __syncwarp();
+    }
     if (i >= n) return;
     ids[i] = (uint32_t)i;
     const float mx3 = means[3 * i], my3 = means[3 * i + 1], mz3 = means[3 * i + 2];
@@ -149,16 +173,22 @@ __global__ void __launch_bounds__(256) k_project(
     const float m2y = fmaf(cam.fy, py * iz, cam.cy);
 
     vis = vis && isfinite(m2x) && isfinite(m2y) && isfinite(rad);
+    const float op = 1.f / (1.f + expf(-op_logits[i]));
+    // alpha = sigma e^g >= 1/255 only inside d^T Sigma'^-1 d <= 2L, L = ln(255 sigma)
+    const float L = logf(255.f * op);
     int4 rc = make_int4(0, 0, -1, -1);
     uint32_t ntiles = 0;
     if (vis) {
         if (mode == GS_MODE_EXACT) {
             rc = make_int4(0, 0, tiles_x - 1, tiles_y - 1);
             ntiles = (uint32_t)(tiles_x * tiles_y);
-        } else {
-            // tiles holding a pixel centre (i, j) with |i - mx| <= r, |j - my| <= r
-            const float lox = ceilf(m2x - rad), hix = floorf(m2x + rad);
-            const float loy = ceilf(m2y - rad), hiy = floorf(m2y + rad);
+        } else if (L > 0.f) {
+            // tiles holding a pixel centre (i, j) with |i - mx| <= hx, |j - my| <= hy:
+            // the 3-sigma square cut to the bounding box of the alpha >= 1/255 ellipse
+            const float hx = fminf(rad, sqrtf(2.f * L * c00));
+            const float hy = fminf(rad, sqrtf(2.f * L * c11));
+            const float lox = ceilf(m2x - hx), hix = floorf(m2x + hx);
+            const float loy = ceilf(m2y - hy), hiy = floorf(m2y + hy);
             if (!(hix < 0.f || lox > (float)(W - 1) || hiy < 0.f || loy > (float)(H - 1) || lox > hix ||
                   loy > hiy)) {
                 const int x0 = lox < 0.f ? 0 : (int)lox;
@@ -171,7 +201,10 @@ __global__ void __launch_bounds__(256) k_project(
         }
     }
     tiles_out[i] = ntiles;
-    rect_out[i] = rc;
+    supers_out[i] = ntiles ? (uint32_t)((rc.z / kSuper - rc.x / kSuper + 1) * (rc.w / kSuper - rc.y / kSuper + 1)) : 0u;
+    rect_out[i] = ntiles ? make_ushort4((unsigned short)rc.x, (unsigned short)rc.y, (unsigned short)rc.z,
+                                        (unsigned short)rc.w)
+                         : make_ushort4(1, 1, 0, 0);
     radius_out[i] = vis ? (int)rad : 0;
     depth_out[i] = vis ? pz : 0.f;
     depth_key[i] = ntiles > 0 ? __float_as_uint(pz) : 0xFFFFFFFFu;
@@ -182,13 +215,12 @@ __global__ void __launch_bounds__(256) k_project(
         return;
     }
 
-    const float op = 1.f / (1.f + expf(-op_logits[i]));
     float col[3];
-    if (sh != nullptr) {
+    if (DEG >= 0) {
         float dx = mx3 - cam.campos[0], dy = my3 - cam.campos[1], dz = mz3 - cam.campos[2];
         const float dn = rsqrtf(dx * dx + dy * dy + dz * dz);
         dx *= dn; dy *= dn; dz *= dn;
-        sh_colour(sh + (size_t)i * (sh_deg + 1) * (sh_deg + 1) * 3, sh_deg, dx, dy, dz, col);
+        sh_colour(&s_sh[warp][lane][0], DEG, dx, dy, dz, col);
     } else {
         col[0] = rgb_in[3 * i];
         col[1] = rgb_in[3 * i + 1];
@@ -196,7 +228,7 @@ __global__ void __launch_bounds__(256) k_project(
     }
     // reject threshold on the exponent: g < ln(1/(255 sigma)) - 1e-4 guarantees
     // sigma e^g < 1/255 in FP32, so the blend may skip the exponential there.
-    const float thr = (mode == GS_MODE_EXACT) ? -INFINITY : (logf(1.f / (255.f * op)) - 1e-4f);
+    const float thr = (mode == GS_MODE_EXACT) ? -INFINITY : (-L - 1e-4f);
     rec.r0[i] = make_float4(m2x, m2y, ca, cb);
     rec.r1[i] = make_float4(cc, op, thr, 0.f);
     rec.r2[i] = make_float4(col[0], col[1], col[2], 0.f);
@@ -221,16 +253,26 @@ __global__ void k_unpack(Records rec, const int* __restrict__ radius, const uint
 }  // namespace
 
 cudaError_t launch_project(cudaStream_t s, const gs_gaussians& g, const CameraParams& cam, int W, int H,
-                           int tiles_x, int tiles_y, int mode, Records rec, float* depth, int* radius, int4* rect,
-                           uint32_t* tiles_touched, uint32_t* depth_key, uint32_t* ids)
+                           int tiles_x, int tiles_y, int mode, Records rec, float* depth, int* radius, ushort4* rect,
+                           uint32_t* tiles_touched, uint32_t* supers_touched, uint32_t* depth_key, uint32_t* ids)
 {
     const int n = (int)g.n;
     if (n == 0) return cudaSuccess;
-    const int threads = 256;
-    const int blocks = (n + threads - 1) / threads;
-    k_project<<<blocks, threads, 0, s>>>(n, g.means, g.log_scales, g.quats, g.opacity_logits, g.sh, g.sh_degree,
-                                         g.rgb, cam, W, H, tiles_x, tiles_y, mode, rec, depth, radius, rect,
-                                         tiles_touched, depth_key, ids); note_launch();
+    const int blocks = (n + kProjThreads - 1) / kProjThreads;
+    const int deg = g.sh ? g.sh_degree : -1;
+#define GS_PROJECT(D)                                                                                              \
+    k_project<D><<<blocks, kProjThreads, 0, s>>>(n, g.means, g.log_scales, g.quats, g.opacity_logits, g.sh, g.rgb, \
+                                                 cam, W, H, tiles_x, tiles_y, mode, rec, depth, radius, rect,      \
+                                                 tiles_touched, supers_touched, depth_key, ids)
+    switch (deg) {
+    case 0: GS_PROJECT(0); break;
+    case 1: GS_PROJECT(1); break;
+    case 2: GS_PROJECT(2); break;
+    case 3: GS_PROJECT(3); break;
+    default: GS_PROJECT(-1); break;
+    }
+#undef GS_PROJECT
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -287,40 +287,57 @@ __device__ __forceinline__ V block_exclusive_scan(V v, V* s_warp, V* total)
     return base + x - v;
 }
 
+// per block: sum of counts[ids[k]] -> partials[b], sum of side[ids[k]] -> partials2[b]
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ tt,
+                                                              const uint32_t* __restrict__ side,
                                                               const uint32_t* __restrict__ ids, uint32_t n,
-                                                              unsigned long long* __restrict__ partials)
+                                                              unsigned long long* __restrict__ partials,
+                                                              unsigned long long* __restrict__ partials2)
 {
     __shared__ unsigned long long s_warp[kScanThreads / 32];
     const uint32_t base = blockIdx.x * kScanTile;
-    unsigned long long sum = 0;
+    unsigned long long sum = 0, sum2 = 0;
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
         const uint32_t idx = base + i * kScanThreads + threadIdx.x;
         if (idx < n) {
             const uint32_t id = ids[idx];
-            if (id < n) sum += tt[id];
+            if (id < n) {
+                sum += tt[id];
+                if (side) sum2 += side[id];
+            }
         }
     }
-    unsigned long long tot;
+    unsigned long long tot, tot2;
     block_exclusive_scan<unsigned long long>(sum, s_warp, &tot);
-    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+    block_exclusive_scan<unsigned long long>(sum2, s_warp, &tot2);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = tot;
+        partials2[blockIdx.x] = tot2;
+    }
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_partials(unsigned long long* __restrict__ partials,
+                                                                unsigned long long* __restrict__ partials2,
                                                                 uint32_t nb)
 {
     __shared__ unsigned long long s_warp[kScanThreads / 32];
-    unsigned long long carry = 0;
+    unsigned long long carry = 0, carry2 = 0;
     for (uint32_t b0 = 0; b0 < nb; b0 += kScanThreads) {
         const uint32_t i = b0 + threadIdx.x;
         const unsigned long long v = i < nb ? partials[i] : 0ull;
-        unsigned long long tot;
+        const unsigned long long v2 = i < nb ? partials2[i] : 0ull;
+        unsigned long long tot, tot2;
         const unsigned long long ex = block_exclusive_scan<unsigned long long>(v, s_warp, &tot);
+        block_exclusive_scan<unsigned long long>(v2, s_warp, &tot2);
         if (i < nb) partials[i] = carry + ex;
         carry += tot;
+        carry2 += tot2;
     }
-    if (threadIdx.x == 0) partials[nb] = carry;
+    if (threadIdx.x == 0) {
+        partials[nb] = carry;
+        partials2[nb] = carry2;
+    }
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* __restrict__ tt,
@@ -384,17 +401,18 @@ size_t scan_partials_count(uint32_t n)
     return (n + kScanTile - 1) / kScanTile + 1;
 }
 
-cudaError_t launch_scan_gathered(cudaStream_t s, const uint32_t* tt, const uint32_t* ids, uint32_t n,
-                                 uint32_t* offsets, unsigned long long* partials)
+cudaError_t launch_scan_gathered(cudaStream_t s, const uint32_t* tt, const uint32_t* side, const uint32_t* ids,
+                                 uint32_t n, uint32_t* offsets, unsigned long long* partials)
 {
+    const uint32_t nb = (n + kScanTile - 1) / kScanTile;
+    unsigned long long* partials2 = partials + nb + 1;
     if (n == 0) {
         cudaError_t e = cudaMemsetAsync(offsets, 0, sizeof(uint32_t), s);
         if (e != cudaSuccess) return e;
-        return cudaMemsetAsync(partials, 0, sizeof(unsigned long long), s);
+        return cudaMemsetAsync(partials, 0, 2 * sizeof(unsigned long long), s);
     }
-    const uint32_t nb = (n + kScanTile - 1) / kScanTile;
-    k_scan_reduce<<<nb, kScanThreads, 0, s>>>(tt, ids, n, partials); note_launch();
-    k_scan_partials<<<1, kScanThreads, 0, s>>>(partials, nb); note_launch();
+    k_scan_reduce<<<nb, kScanThreads, 0, s>>>(tt, side, ids, n, partials, partials2); note_launch();
+    k_scan_partials<<<1, kScanThreads, 0, s>>>(partials, partials2, nb); note_launch();
     k_scan_apply<<<nb, kScanThreads, 0, s>>>(tt, ids, n, partials, offsets); note_launch();
     return cudaGetLastError();
 }

@@ -169,8 +169,9 @@ def test_colour_from_sh(ora, deg):
 @pytest.mark.parametrize("W,H,seed", [(50, 37, 0), (16, 16, 1), (33, 70, 2)])
 def test_binning_brute_force(ora, W, H, seed):
     """The pair list is exactly the set of (tile, Gaussian) with a pixel centre of
-    the tile inside the Gaussian's square of half-width r, ordered by tile, FP32
-    depth, id; ranges delimit each tile's run."""
+    the tile inside the Gaussian's 3-sigma square cut to the bounding box of its
+    alpha >= 1/255 ellipse, ordered by tile, FP32 depth, id; ranges delimit each
+    tile's run."""
     scene = scenes.random_scene(40, seed=seed, xy_range=1.6)
     cam = _rotated_camera(W, H)
     tile = 16
@@ -183,27 +184,66 @@ def test_binning_brute_force(ora, W, H, seed):
         if r == 0:
             continue
         mx, my = proj["mean2d"][i]
+        L = math.log(255 * proj["opacity"][i])
+        if L <= 0:
+            assert proj["tiles_touched"][i] == 0
+            continue
+        # bounding box of the ellipse {d : d^T cov^-1 d <= 2L}, measured on its
+        # boundary traced from the eigen-decomposition (sampling error < 1e-6)
+        c = proj["cov2d"][i]
+        cov = np.array([[c[0], c[1]], [c[1], c[2]]])
+        lam, vec = np.linalg.eigh(cov)
+        th = np.linspace(0, 2 * np.pi, 20001)
+        pts = vec @ (np.sqrt(2 * L * lam)[:, None] * np.stack([np.cos(th), np.sin(th)]))
+        hx = min(r, np.abs(pts[0]).max())
+        hy = min(r, np.abs(pts[1]).max())
         tiles = set()
         for py in range(H):
-            if abs(py - my) > r:
+            if abs(py - my) > hy:
                 continue
             for px in range(W):
-                if abs(px - mx) <= r:
+                if abs(px - mx) <= hx:
                     tiles.add((py // tile) * tx + px // tile)
+        if proj["borderline"][i]:
+            continue
         assert len(tiles) == proj["tiles_touched"][i]
         d32 = np.float32(proj["depth"][i]).view(np.uint32)
         want += [(t, int(d32), i) for t in tiles]
+    keep = set(np.nonzero(proj["borderline"] == 0)[0].tolist())
     want.sort()
     got = [(int(k >> np.uint64(32)), int(k & np.uint64(0xFFFFFFFF)), int(v))
-           for k, v in zip(bins["keys"], bins["vals"])]
+           for k, v in zip(bins["keys"], bins["vals"]) if int(v) in keep]
     assert got == want
     ranges = bins["ranges"]
+    allp = [(int(k >> np.uint64(32)), int(v)) for k, v in zip(bins["keys"], bins["vals"])]
     for t in range(ranges.shape[0]):
         s, e = ranges[t]
-        run = [g for g in got if g[0] == t]
+        run = [g for g in allp if g[0] == t]
         assert e - s == len(run)
         if run:
-            assert got[s:e] == run
+            assert allp[s:e] == run
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_tight_tile_sets_keep_the_image(ora, seed):
+    """Binning each Gaussian only into the tiles of its alpha >= 1/255 box drops
+    only pairs the cut-off rejects: the 3DGS-mode image (colour, derivatives,
+    state) is bit-identical to binning every Gaussian into every tile."""
+    W, H = 48, 40
+    scene = scenes.random_scene(400, seed=seed, sh_degree=1)
+    cam = _rotated_camera(W, H)
+    proj = ora.project(scene, cam, W, H)
+    full = dict(proj)
+    vis = proj["radius"] > 0
+    full["rect"] = np.where(vis[:, None], np.array([0, 0, full["tiles_x"] - 1, full["tiles_y"] - 1]),
+                            np.array([0, 0, -1, -1])).astype(np.int32)
+    full["tiles_touched"] = np.where(vis, full["tiles_x"] * full["tiles_y"], 0).astype(np.int64)
+    a = ora.render(proj, ora.bin_pairs(proj))
+    b = ora.render(full, ora.bin_pairs(full))
+    assert ora.bin_pairs(proj)["P"] < 0.5 * ora.bin_pairs(full)["P"]
+    np.testing.assert_array_equal(a["C"], b["C"])
+    np.testing.assert_array_equal(a["grads"], b["grads"])
+    np.testing.assert_array_equal(a["state"][:4], b["state"][:4])
 
 
 def test_borderline_flags_are_rare(ora):
