@@ -174,7 +174,8 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
         (st = ensure(c, c->dkey[0], sizeof(uint32_t) * n)) || (st = ensure(c, c->dkey[1], sizeof(uint32_t) * n)) ||
         (st = ensure(c, c->did[0], sizeof(uint32_t) * n)) || (st = ensure(c, c->did[1], sizeof(uint32_t) * n)) ||
         (st = ensure(c, c->offsets, sizeof(uint32_t) * (n + 1))) ||
-        (st = ensure(c, c->scan_partials, 2 * sizeof(unsigned long long) * scan_partials_count(n))) ||
+        (st = ensure(c, c->scan_partials, sizeof(unsigned long long) * scan_partials_count(n))) ||
+        (st = ensure(c, c->scan_totals, 4 * sizeof(unsigned long long))) ||
         (st = ensure(c, c->sranges, sizeof(uint2) * Ts)) || (st = ensure(c, c->sort_hist, sizeof(uint32_t) * 8 * 256)) ||
         (st = ensure(c, c->sort_counter, sizeof(uint32_t) * 8)))
         return st;
@@ -200,13 +201,11 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
 
     // super-tile pair offsets in depth order, their exact count Ps and the
     // (tile, Gaussian) pair count P in the same pass
+    unsigned long long* totals = as<unsigned long long>(c->scan_totals);
     GS_CUDA(c, launch_scan_gathered(c->stream, as<uint32_t>(c->supers_touched), as<uint32_t>(c->tiles_touched), ids, n,
-                                    as<uint32_t>(c->offsets), as<unsigned long long>(c->scan_partials)));
-    const size_t nb = scan_partials_count(n) - 1;
-    unsigned long long* part = as<unsigned long long>(c->scan_partials);
-    GS_CUDA(c, cudaMemcpyAsync(c->h_scalar, part + nb, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
-    GS_CUDA(c, cudaMemcpyAsync(c->h_scalar + 1, part + nb + 1 + nb, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                               c->stream));
+                                    as<uint32_t>(c->offsets), as<unsigned long long>(c->scan_partials),
+                                    reinterpret_cast<uint32_t*>(totals + 2), totals, as<int>(c->errword)));
+    GS_CUDA(c, cudaMemcpyAsync(c->h_scalar, totals, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
     GS_CUDA(c, cudaStreamSynchronize(c->stream));
     const unsigned long long Ps64 = c->h_scalar[0], P64 = c->h_scalar[1];
     const int64_t limit = c->opt.max_pairs > 0 ? std::min<int64_t>(c->opt.max_pairs, kMaxPairs) : kMaxPairs;
@@ -350,7 +349,7 @@ gs_status gs_destroy(gs_ctx* c)
     cudaStreamSynchronize(c->stream);
     DevBuf* bufs[] = {&c->rec0, &c->rec1, &c->rec2, &c->depth, &c->radius, &c->rect, &c->tiles_touched,
                       &c->supers_touched, &c->dkey[0], &c->dkey[1], &c->did[0], &c->did[1], &c->offsets,
-                      &c->scan_partials, &c->pairs[0], &c->pairs[1], &c->sort_hist, &c->sort_status,
+                      &c->scan_partials, &c->scan_totals, &c->pairs[0], &c->pairs[1], &c->sort_hist, &c->sort_status,
                       &c->sort_counter, &c->sranges, &c->tile_count, &c->tile_start, &c->state, &c->count,
                       &c->errword};
     for (DevBuf* b : bufs) release(*b);

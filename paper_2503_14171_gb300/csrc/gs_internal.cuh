@@ -83,7 +83,8 @@ struct gs_ctx {
     gs::DevBuf supers_touched;          // uint32[n] super-tiles of the rect
     gs::DevBuf dkey[2], did[2];         // depth sort keys / ids, ping-pong
     gs::DevBuf offsets;                 // uint32[n + 1]
-    gs::DevBuf scan_partials;           // uint64[2][blocks + 1]
+    gs::DevBuf scan_partials;           // uint64[tiles + 1] scan tile states
+    gs::DevBuf scan_totals;             // uint64[2] + uint32 tile counter
     // per super-tile pair
     gs::DevBuf pairs[2];                // uint64[Ps] (super-tile << 32 | id), ping-pong
     // radix sort scratch
@@ -128,12 +129,12 @@ cudaError_t radix_sort_u64_keys(cudaStream_t s, uint64_t* keys[2], uint32_t n, i
 size_t radix_status_words(uint32_t n, int bit_lo, int bit_hi);
 int radix_passes(int bit_lo, int bit_hi);
 
-// exclusive scan of counts[ids[k]] over k -> offsets[k]; partials[nb]
-// (nb = scan_partials_count(n) - 1) receives the exact 64-bit total, and
-// partials[nb + 1 + nb] the 64-bit total of side[ids[k]] (a second count
-// reduced in the same pass)
+// exclusive scan of counts[ids[k]] over k -> offsets[k] (offsets[n] = total);
+// totals[0] = exact 64-bit total, totals[1] = 64-bit total of side[ids[k]].
+// scratch: scan_partials_count(n) 64-bit tile states; counter: one uint32.
 cudaError_t launch_scan_gathered(cudaStream_t s, const uint32_t* counts, const uint32_t* side, const uint32_t* ids,
-                                 uint32_t n, uint32_t* offsets, unsigned long long* partials);
+                                 uint32_t n, uint32_t* offsets, unsigned long long* scratch, uint32_t* counter,
+                                 unsigned long long* totals, int* err);
 size_t scan_partials_count(uint32_t n);
 
 cudaError_t launch_emit_pairs(cudaStream_t s, const uint32_t* ids, const uint32_t* offsets, const ushort4* rect,

@@ -24,6 +24,7 @@ constexpr uint32_t kFlagAgg = 1u << 30;    // status word: 2-bit flag | 30-bit c
 constexpr uint32_t kFlagInc = 2u << 30;
 constexpr uint32_t kValueMask = (1u << 30) - 1;
 constexpr long kSpinLimit = 1L << 22;
+constexpr int kLookback = 8;               // predecessor tiles read per look-back round trip
 
 static_assert(kThreads == kRadix, "digit phases use one thread per digit");
 
@@ -40,31 +41,30 @@ __device__ __forceinline__ uint32_t digit_of(K key, int shift)
     return (uint32_t)(key >> shift) & (kRadix - 1);
 }
 
-// Histogram of every pass's digit over all keys; warp-aggregated shared-memory
-// counting (many keys share a digit, e.g. the exponent byte of depths).
+// Histogram of every pass's digit over all keys, in per-warp shared-memory
+// sub-histograms (a key shared by a whole warp, e.g. the exponent byte of a
+// depth, costs one 32-way serialised atomic instead of block-wide contention).
+constexpr int kHistPasses = 4;
 template <typename K>
 __global__ void __launch_bounds__(kThreads) k_radix_hist(const K* __restrict__ keys, uint32_t n, int bit_lo,
                                                          int passes, uint32_t* __restrict__ hist)
 {
-    __shared__ uint32_t s_hist[kMaxPasses][kRadix];
-    for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += kThreads) (&s_hist[0][0])[i] = 0;
+    __shared__ uint32_t s_hist[kWarps][kHistPasses][kRadix];
+    for (int i = threadIdx.x; i < kWarps * kHistPasses * kRadix; i += kThreads) (&s_hist[0][0][0])[i] = 0;
     __syncthreads();
+    const int warp = threadIdx.x >> 5;
     const uint32_t stride = gridDim.x * kThreads;
-    // whole warps iterate together so __match_any_sync sees all lanes
-    const uint32_t n_round = (n + 31u) & ~31u;
-    for (uint32_t i = blockIdx.x * kThreads + threadIdx.x; i < n_round; i += stride) {
-        const bool valid = i < n;
-        const K key = valid ? keys[i] : K(0);
-        for (int p = 0; p < passes; ++p) {
-            const uint32_t d = valid ? digit_of(key, bit_lo + p * kRadixBits) : kRadix;
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
-            const int leader = 31 - __clz(peers);
-            if (valid && (int)(threadIdx.x & 31) == leader) atomicAdd(&s_hist[p][d], (uint32_t)__popc(peers));
-        }
+    for (uint32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += stride) {
+        const K key = keys[i];
+#pragma unroll
+        for (int p = 0; p < kHistPasses; ++p)
+            if (p < passes) atomicAdd(&s_hist[warp][p][digit_of(key, bit_lo + p * kRadixBits)], 1u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < passes * kRadix; i += kThreads) {
-        const uint32_t v = (&s_hist[0][0])[i];
+        uint32_t v = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) v += (&s_hist[w][0][0])[i];
         if (v) atomicAdd(&hist[i], v);
     }
 }
@@ -131,12 +131,19 @@ __global__ void __launch_bounds__(kThreads) k_onesweep(const K* __restrict__ key
         if (HAS_VAL) val[i] = valid ? vals_in[idx] : 0u;
         dig[i] = valid ? digit_of(key[i], shift) : (uint32_t)kRadix;
     }
-    // warp multi-split: rank among earlier keys of the same digit in this warp
+    // warp multi-split: rank among earlier keys of the same digit in this warp;
+    // the lanes sharing a digit are found with one ballot per digit bit
     const uint32_t lt = lanemask_lt();
 #pragma unroll
     for (int i = 0; i < kItems; ++i) {
         const uint32_t d = dig[i];
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t peers = __ballot_sync(0xffffffffu, d < (uint32_t)kRadix);
+#pragma unroll
+        for (int b = 0; b < kRadixBits; ++b) {
+            const bool bit = (d >> b) & 1u;
+            const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+            peers &= bit ? bal : ~bal;
+        }
         const int leader = 31 - __clz(peers);
         uint32_t prev = 0;
         if (d < (uint32_t)kRadix) prev = S.warp_hist[warp][d];
@@ -173,24 +180,37 @@ __global__ void __launch_bounds__(kThreads) k_onesweep(const K* __restrict__ key
     const uint32_t local_start = wbase + x - total;
     S.local_start[d] = local_start;
 
-    // decoupled look-back over earlier tiles for digit d
+    // decoupled look-back over earlier tiles for digit d, kLookback tiles per
+    // round trip (tiles before 0 read as an inclusive zero)
     uint32_t excl = 0;
     if (tile > 0) {
         long spins = 0;
         int j = (int)tile - 1;
-        while (j >= 0) {
-            const uint32_t s = *(volatile const uint32_t*)(status + (size_t)j * kRadix + d);
-            const uint32_t f = s & ~kValueMask;
-            if (f == 0u) {
-                if (++spins > kSpinLimit) {
-                    atomicExch(err, kDevTimeout);
-                    break;
+        while (true) {
+            uint32_t sw[kLookback];
+#pragma unroll
+            for (int w = 0; w < kLookback; ++w)
+                sw[w] = j - w >= 0 ? *(volatile const uint32_t*)(status + (size_t)(j - w) * kRadix + d) : kFlagInc;
+            int used = 0;
+            bool inc = false, blocked = false;
+#pragma unroll
+            for (int w = 0; w < kLookback; ++w) {
+                if (inc || blocked) continue;
+                const uint32_t f = sw[w] & ~kValueMask;
+                if (f == 0u) {
+                    blocked = true;
+                    continue;
                 }
-                continue;
+                excl += sw[w] & kValueMask;
+                ++used;
+                inc = f == kFlagInc;
             }
-            excl += s & kValueMask;
-            if (f == kFlagInc) break;
-            --j;
+            if (inc) break;
+            j -= used;
+            if (blocked && ++spins > kSpinLimit) {
+                atomicExch(err, kDevTimeout);
+                break;
+            }
         }
         *st = kFlagInc | ((excl + total) & kValueMask);
     }
@@ -256,116 +276,119 @@ cudaError_t radix_sort_impl(cudaStream_t s, K* keys[2], uint32_t* vals[2], uint3
     return cudaGetLastError();
 }
 
-// ---- exclusive scan of tiles_touched gathered through the depth order ----
-// Block totals are 64-bit so that the pair count P is exact even when it would
-// not fit 32 bits (the caller then refuses the frame); per-item offsets are
-// 32-bit and valid whenever P < 2^32.
+// ---- exclusive scan of per-Gaussian counts gathered through the depth order ----
+// Single pass with decoupled look-back: each block takes the next tile of 4096
+// positions (in launch order), sums its gathered counts, publishes the sum,
+// resolves its exclusive prefix from its predecessors (one warp reads 32
+// predecessor tiles per round trip, bounded wait), and writes its offsets.
+// Tile states are 64-bit (2-bit flag | 62-bit value), so the total is exact;
+// per-position offsets are 32-bit and valid whenever the total is < 2^32.
+// A second count array is reduced alongside (one 64-bit atomic per block).
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr unsigned long long kScanAgg = 1ull << 62;
+constexpr unsigned long long kScanInc = 2ull << 62;
+constexpr unsigned long long kScanMask = (1ull << 62) - 1;
 
-template <typename V>
-__device__ __forceinline__ V block_exclusive_scan(V v, V* s_warp, V* total)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    V x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const V y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) s_warp[warp] = x;
-    __syncthreads();
-    V base = 0, tot = 0;
-    for (int w = 0; w < kScanThreads / 32; ++w) {
-        const V t = s_warp[w];
-        if (w < warp) base += t;
-        tot += t;
-    }
-    __syncthreads();
-    *total = tot;
-    return base + x - v;
-}
-
-// per block: sum of counts[ids[k]] -> partials[b], sum of side[ids[k]] -> partials2[b]
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ tt,
-                                                              const uint32_t* __restrict__ side,
-                                                              const uint32_t* __restrict__ ids, uint32_t n,
-                                                              unsigned long long* __restrict__ partials,
-                                                              unsigned long long* __restrict__ partials2)
+__global__ void __launch_bounds__(kScanThreads) k_scan_onepass(const uint32_t* __restrict__ counts,
+                                                               const uint32_t* __restrict__ side,
+                                                               const uint32_t* __restrict__ ids, uint32_t n,
+                                                               uint32_t* __restrict__ offsets,
+                                                               unsigned long long* __restrict__ status,
+                                                               uint32_t* __restrict__ tile_counter,
+                                                               unsigned long long* __restrict__ totals,
+                                                               int* __restrict__ err)
 {
     __shared__ unsigned long long s_warp[kScanThreads / 32];
-    const uint32_t base = blockIdx.x * kScanTile;
+    __shared__ unsigned long long s_prefix;
+    __shared__ uint32_t s_tile;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
+    // blocked arrangement: thread t owns positions [t*16, t*16 + 16) of the tile
+    const uint32_t base = tile * kScanTile + threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
     unsigned long long sum = 0, sum2 = 0;
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
-        const uint32_t idx = base + i * kScanThreads + threadIdx.x;
-        if (idx < n) {
-            const uint32_t id = ids[idx];
-            if (id < n) {
-                sum += tt[id];
-                if (side) sum2 += side[id];
+        const uint32_t k = base + i;
+        const uint32_t id = k < n ? ids[k] : n;
+        v[i] = id < n ? counts[id] : 0u;
+        sum += v[i];
+        if (side != nullptr && id < n) sum2 += side[id];
+    }
+    // block scan of the per-thread sums
+    unsigned long long x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    // side total: warp reduce, one atomic per warp
+    unsigned long long z = sum2;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) z += __shfl_down_sync(0xffffffffu, z, o);
+    if (lane == 0 && z) atomicAdd(&totals[1], z);
+    __syncthreads();
+    unsigned long long wbase = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < kScanThreads / 32; ++w) {
+        const unsigned long long t = s_warp[w];
+        wbase += w < warp ? t : 0ull;
+        tot += t;
+    }
+    // publish, then look back (warp 0)
+    if (warp == 0) {
+        volatile unsigned long long* st = status + tile;
+        if (lane == 0) *st = (tile == 0 ? kScanInc : kScanAgg) | tot;
+        unsigned long long excl = 0;
+        if (tile > 0) {
+            long spins = 0;
+            int j = (int)tile - 1;
+            while (true) {
+                const int jj = j - lane;
+                const unsigned long long sv =
+                    jj >= 0 ? *(volatile const unsigned long long*)(status + jj) : kScanInc;
+                const unsigned long long f = sv & ~kScanMask;
+                // lanes up to the first inclusive one count; a not-ready lane before it blocks
+                const uint32_t inc_mask = __ballot_sync(0xffffffffu, f == kScanInc);
+                const uint32_t zero_mask = __ballot_sync(0xffffffffu, f == 0ull);
+                const int first_inc = inc_mask ? __ffs(inc_mask) - 1 : 32;
+                const int first_zero = zero_mask ? __ffs(zero_mask) - 1 : 32;
+                const int upto = min(first_inc, first_zero);            // lanes [0, upto) are aggregates
+                unsigned long long add = (lane < upto || (lane == first_inc && first_inc < first_zero))
+                                             ? (sv & kScanMask) : 0ull;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) add += __shfl_down_sync(0xffffffffu, add, o);
+                add = __shfl_sync(0xffffffffu, add, 0);
+                excl += add;
+                if (first_inc < first_zero) break;
+                j -= upto;
+                if (first_zero < 32 && ++spins > (1L << 22)) {
+                    if (lane == 0) atomicExch(err, kDevTimeout);
+                    break;
+                }
             }
+            if (lane == 0) *st = kScanInc | ((excl + tot) & kScanMask);
+        }
+        if (lane == 0) {
+            s_prefix = excl;
+            if (tile == ntiles - 1) totals[0] = excl + tot;
         }
     }
-    unsigned long long tot, tot2;
-    block_exclusive_scan<unsigned long long>(sum, s_warp, &tot);
-    block_exclusive_scan<unsigned long long>(sum2, s_warp, &tot2);
-    if (threadIdx.x == 0) {
-        partials[blockIdx.x] = tot;
-        partials2[blockIdx.x] = tot2;
-    }
-}
-
-__global__ void __launch_bounds__(kScanThreads) k_scan_partials(unsigned long long* __restrict__ partials,
-                                                                unsigned long long* __restrict__ partials2,
-                                                                uint32_t nb)
-{
-    __shared__ unsigned long long s_warp[kScanThreads / 32];
-    unsigned long long carry = 0, carry2 = 0;
-    for (uint32_t b0 = 0; b0 < nb; b0 += kScanThreads) {
-        const uint32_t i = b0 + threadIdx.x;
-        const unsigned long long v = i < nb ? partials[i] : 0ull;
-        const unsigned long long v2 = i < nb ? partials2[i] : 0ull;
-        unsigned long long tot, tot2;
-        const unsigned long long ex = block_exclusive_scan<unsigned long long>(v, s_warp, &tot);
-        block_exclusive_scan<unsigned long long>(v2, s_warp, &tot2);
-        if (i < nb) partials[i] = carry + ex;
-        carry += tot;
-        carry2 += tot2;
-    }
-    if (threadIdx.x == 0) {
-        partials[nb] = carry;
-        partials2[nb] = carry2;
-    }
-}
-
-__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* __restrict__ tt,
-                                                             const uint32_t* __restrict__ ids, uint32_t n,
-                                                             const unsigned long long* __restrict__ partials,
-                                                             uint32_t* __restrict__ out)
-{
-    __shared__ uint32_t s_warp[kScanThreads / 32];
-    const uint32_t base = blockIdx.x * kScanTile;
-    // blocked arrangement: thread t owns items [t*kScanItems, (t+1)*kScanItems)
-    uint32_t v[kScanItems];
-    uint32_t sum = 0;
+    __syncthreads();
+    uint32_t run = (uint32_t)(s_prefix + wbase + x - sum);
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
-        const uint32_t idx = base + threadIdx.x * kScanItems + i;
-        const uint32_t id = idx < n ? ids[idx] : n;
-        v[i] = id < n ? tt[id] : 0u;
-        sum += v[i];
-    }
-    uint32_t tot;
-    uint32_t run = (uint32_t)partials[blockIdx.x] + block_exclusive_scan<uint32_t>(sum, s_warp, &tot);
-#pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-        const uint32_t idx = base + threadIdx.x * kScanItems + i;
-        if (idx < n) out[idx] = run;
+        const uint32_t k = base + i;
+        if (k < n) offsets[k] = run;
         run += v[i];
     }
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = (uint32_t)partials[gridDim.x];
+    if (tile == ntiles - 1 && threadIdx.x == kScanThreads - 1) offsets[n] = (uint32_t)(s_prefix + tot);
 }
 
 }  // namespace
@@ -401,19 +424,18 @@ size_t scan_partials_count(uint32_t n)
     return (n + kScanTile - 1) / kScanTile + 1;
 }
 
-cudaError_t launch_scan_gathered(cudaStream_t s, const uint32_t* tt, const uint32_t* side, const uint32_t* ids,
-                                 uint32_t n, uint32_t* offsets, unsigned long long* partials)
+cudaError_t launch_scan_gathered(cudaStream_t s, const uint32_t* counts, const uint32_t* side, const uint32_t* ids,
+                                 uint32_t n, uint32_t* offsets, unsigned long long* scratch, uint32_t* counter,
+                                 unsigned long long* totals, int* err)
 {
-    const uint32_t nb = (n + kScanTile - 1) / kScanTile;
-    unsigned long long* partials2 = partials + nb + 1;
-    if (n == 0) {
-        cudaError_t e = cudaMemsetAsync(offsets, 0, sizeof(uint32_t), s);
-        if (e != cudaSuccess) return e;
-        return cudaMemsetAsync(partials, 0, 2 * sizeof(unsigned long long), s);
-    }
-    k_scan_reduce<<<nb, kScanThreads, 0, s>>>(tt, side, ids, n, partials, partials2); note_launch();
-    k_scan_partials<<<1, kScanThreads, 0, s>>>(partials, partials2, nb); note_launch();
-    k_scan_apply<<<nb, kScanThreads, 0, s>>>(tt, ids, n, partials, offsets); note_launch();
+    const uint32_t nt = (n + kScanTile - 1) / kScanTile;
+    cudaError_t e = cudaMemsetAsync(totals, 0, 2 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    if (n == 0) return cudaMemsetAsync(offsets, 0, sizeof(uint32_t), s);
+    if ((e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * nt, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(counter, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
+    k_scan_onepass<<<nt, kScanThreads, 0, s>>>(counts, side, ids, n, offsets, scratch, counter, totals, err);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -12,34 +12,28 @@
 //
 // Output pixel X samples the low-res point x = (X + 0.5)/s - 0.5; its cell is
 // i = clamp(floor(x), 0, W - 2) and t = x - i (outside [0, 1] only in the border
-// half-cells, where the edge patch is extrapolated).
+// half-cells, where the edge patch is extrapolated).  Both come from integer
+// arithmetic: x = (2X + 1 - s) / (2s).
 //
-// Launch: one block per 32 x 8 tile of output pixels.  The block first stages
-// the low-res footprint of its tile (all 12 planes) in shared memory with
-// coalesced loads, then each thread writes its outputs; every low-res value is
-// read from HBM once per block.  HBM-bound: 48 B per low-res pixel in,
-// 12 B per output pixel out.
+// Launch: one 256-thread block per 64 x 16 tile of output pixels, 2 x 2 outputs
+// per thread.  The block computes the cell index and the four basis weights of
+// its 64 columns and 16 rows once (shared tables), stages the low-res footprint
+// of the tile -- each pixel's 12 values (C, C_x, C_y, C_xy for three channels)
+// packed as three float4 -- in shared memory with coalesced loads, and then
+// evaluates each output with 12 vector shared loads and 48 FMAs.  HBM-bound:
+// 48 B per low-res pixel in, 12 B per output pixel out.
 #include "gs_internal.cuh"
 
 namespace gs {
 namespace {
 
-constexpr int kOutW = 32;
-constexpr int kOutH = 8;
+constexpr int kThreadsX = 32, kThreadsY = 8;
+constexpr int kOutW = 2 * kThreadsX;    // 64
+constexpr int kOutH = 2 * kThreadsY;    // 16
 constexpr int kMaxFactor = 16;
-// footprint of a 32 x 8 output tile is at most ceil(32/s)+2 x ceil(8/s)+2 low-res pixels
+// footprint of a 64 x 16 output tile: at most 64 + 1 x 16 + 1 cells (s = 1)
 constexpr int kFootW = kOutW + 2;
 constexpr int kFootH = kOutH + 2;
-
-__device__ __forceinline__ void hermite(float t, float& h0, float& h1, float& g0, float& g1)
-{
-    const float t2 = t * t;
-    const float omt = 1.f - t;
-    h0 = (1.f + 2.f * t) * omt * omt;
-    h1 = t2 * (3.f - 2.f * t);
-    g0 = t * omt * omt;
-    g1 = t2 * (t - 1.f);
-}
 
 __device__ __forceinline__ void cell_of(int X, int s, int W, int& i, float& t)
 {
@@ -52,64 +46,117 @@ __device__ __forceinline__ void cell_of(int X, int s, int W, int& i, float& t)
     t = (float)(num - den * q) / (float)den;
 }
 
-__global__ void __launch_bounds__(kOutW * kOutH) k_upscale(const float* __restrict__ Cimg,
-                                                           const float* __restrict__ G, int W, int H, int s,
-                                                           float* __restrict__ out)
+__device__ __forceinline__ float4 hermite(float t)
 {
-    __shared__ float sm[12][kFootH][kFootW];
+    const float t2 = t * t;
+    const float omt = 1.f - t;
+    return make_float4((1.f + 2.f * t) * omt * omt, t2 * (3.f - 2.f * t), t * omt * omt, t2 * (t - 1.f));
+}
+
+// footprint pitch (in low-res pixels) for factor s: ceil(64 / s) + 2 columns
+__host__ __device__ inline int foot_w(int s) { return min(kFootW, (kOutW + s - 1) / s + 2); }
+__host__ __device__ inline int foot_h(int s) { return min(kFootH, (kOutH + s - 1) / s + 2); }
+
+__global__ void __launch_bounds__(kThreadsX * kThreadsY) k_upscale(const float* __restrict__ Cimg,
+                                                                   const float* __restrict__ G, int W, int H,
+                                                                   int s, float* __restrict__ out)
+{
+    // per low-res pixel of the footprint, its 12 values packed in 3 float4: [fy][fx][3]
+    extern __shared__ float4 sm[];
+    __shared__ float4 s_wx[kOutW];             // basis weights (h00, h01, h10, h11) per output column
+    __shared__ float4 s_wy[kOutH];
+    __shared__ int s_cx[kOutW], s_cy[kOutH];   // cell index relative to the footprint origin
     const int W2 = W * s, H2 = H * s;
     const int X0 = blockIdx.x * kOutW, Y0 = blockIdx.y * kOutH;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * kThreadsX + tx;
+
     int i0, j0, itmp, jtmp;
     float ttmp;
     cell_of(X0, s, W, i0, ttmp);
     cell_of(Y0, s, H, j0, ttmp);
     cell_of(min(X0 + kOutW - 1, W2 - 1), s, W, itmp, ttmp);
     cell_of(min(Y0 + kOutH - 1, H2 - 1), s, H, jtmp, ttmp);
-    const int fw = itmp + 2 - i0, fh = jtmp + 2 - j0;   // footprint size (<= kFootW x kFootH)
+    const int fw = itmp + 2 - i0, fh = jtmp + 2 - j0;   // <= foot_w(s) x foot_h(s)
+    const int pitch = foot_w(s);
+
+    if (tid < kOutW) {
+        int ci;
+        float t;
+        cell_of(min(X0 + tid, W2 - 1), s, W, ci, t);
+        s_cx[tid] = ci - i0;
+        s_wx[tid] = hermite(t);
+    } else if (tid < kOutW + kOutH) {
+        const int r = tid - kOutW;
+        int cj;
+        float u;
+        cell_of(min(Y0 + r, H2 - 1), s, H, cj, u);
+        s_cy[r] = cj - j0;
+        s_wy[r] = hermite(u);
+    }
+    // footprint: 12 planes, each a coalesced row-major fh x fw window
     const size_t plane = (size_t)W * H;
-    const int nf = fw * fh;
-    for (int q = threadIdx.x; q < 12 * nf; q += blockDim.x) {
-        const int pl = q / nf, r = q - pl * nf;
-        const int fy = r / fw, fx = r - fy * fw;
-        const float* src = pl < 3 ? Cimg + pl * plane : G + (pl - 3) * plane;
-        sm[pl][fy][fx] = src[(size_t)(j0 + fy) * W + (i0 + fx)];
+    for (int fy = ty; fy < fh; fy += kThreadsY) {
+        const size_t row = (size_t)(j0 + fy) * W + i0;
+        for (int fx = tx; fx < fw; fx += kThreadsX) {
+            const float* c = Cimg + row + fx;
+            const float* g = G + row + fx;
+            float4* d = sm + 3 * (fy * pitch + fx);
+            d[0] = make_float4(c[0], c[plane], c[2 * plane], g[0]);
+            d[1] = make_float4(g[plane], g[2 * plane], g[3 * plane], g[4 * plane]);
+            d[2] = make_float4(g[5 * plane], g[6 * plane], g[7 * plane], g[8 * plane]);
+        }
     }
     __syncthreads();
 
-    const int X = X0 + (threadIdx.x % kOutW), Y = Y0 + (threadIdx.x / kOutW);
-    if (X >= W2 || Y >= H2) return;
-    int i, j;
-    float t, u;
-    cell_of(X, s, W, i, t);
-    cell_of(Y, s, H, j, u);
-    const int li = i - i0, lj = j - j0;
-    float hx0, hx1, gx0, gx1, hy0, hy1, gy0, gy1;
-    hermite(t, hx0, hx1, gx0, gx1);
-    hermite(u, hy0, hy1, gy0, gy1);
-    const float w00 = hx0 * hy0, w10 = hx1 * hy0, w01 = hx0 * hy1, w11 = hx1 * hy1;
-    const float x00 = gx0 * hy0, x10 = gx1 * hy0, x01 = gx0 * hy1, x11 = gx1 * hy1;
-    const float y00 = hx0 * gy0, y10 = hx1 * gy0, y01 = hx0 * gy1, y11 = hx1 * gy1;
-    const float z00 = gx0 * gy0, z10 = gx1 * gy0, z01 = gx0 * gy1, z11 = gx1 * gy1;
+    const size_t oplane = (size_t)W2 * H2;
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-        const int pv = ch, px = 3 + ch, py = 6 + ch, pxy = 9 + ch;
-        float acc = w00 * sm[pv][lj][li];
-        acc = fmaf(w10, sm[pv][lj][li + 1], acc);
-        acc = fmaf(w01, sm[pv][lj + 1][li], acc);
-        acc = fmaf(w11, sm[pv][lj + 1][li + 1], acc);
-        acc = fmaf(x00, sm[px][lj][li], acc);
-        acc = fmaf(x10, sm[px][lj][li + 1], acc);
-        acc = fmaf(x01, sm[px][lj + 1][li], acc);
-        acc = fmaf(x11, sm[px][lj + 1][li + 1], acc);
-        acc = fmaf(y00, sm[py][lj][li], acc);
-        acc = fmaf(y10, sm[py][lj][li + 1], acc);
-        acc = fmaf(y01, sm[py][lj + 1][li], acc);
-        acc = fmaf(y11, sm[py][lj + 1][li + 1], acc);
-        acc = fmaf(z00, sm[pxy][lj][li], acc);
-        acc = fmaf(z10, sm[pxy][lj][li + 1], acc);
-        acc = fmaf(z01, sm[pxy][lj + 1][li], acc);
-        acc = fmaf(z11, sm[pxy][lj + 1][li + 1], acc);
-        out[(size_t)ch * W2 * H2 + (size_t)Y * W2 + X] = acc;
+    for (int b = 0; b < 2; ++b) {
+        const int oy = ty + b * kThreadsY;
+        const int Y = Y0 + oy;
+        if (Y >= H2) continue;
+        const float4 wy = s_wy[oy];
+        const int lj = s_cy[oy];
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const int ox = tx + a * kThreadsX;
+            const int X = X0 + ox;
+            if (X >= W2) continue;
+            const float4 wx = s_wx[ox];
+            const int li = s_cx[ox];
+            // corner (p, q), p, q in {0, 1}: value weight Hx_p Hy_q, d/dx weight Gx_p Hy_q,
+            // d/dy weight Hx_p Gy_q, d2/dxdy weight Gx_p Gy_q
+            float r = 0.f, gch = 0.f, bch = 0.f;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    const float hx = p ? wx.y : wx.x, gx = p ? wx.w : wx.z;
+                    const float hy = q ? wy.y : wy.x, gy = q ? wy.w : wy.z;
+                    const float wv = hx * hy, wdx = gx * hy, wdy = hx * gy, wdxy = gx * gy;
+                    const float4* v = sm + 3 * ((lj + q) * pitch + li + p);
+                    const float4 v0 = v[0];   // C r, C g, C b, Cx r
+                    const float4 v1 = v[1];   // Cx g, Cx b, Cy r, Cy g
+                    const float4 v2 = v[2];   // Cy b, Cxy r, Cxy g, Cxy b
+                    r = fmaf(wv, v0.x, r);
+                    gch = fmaf(wv, v0.y, gch);
+                    bch = fmaf(wv, v0.z, bch);
+                    r = fmaf(wdx, v0.w, r);
+                    gch = fmaf(wdx, v1.x, gch);
+                    bch = fmaf(wdx, v1.y, bch);
+                    r = fmaf(wdy, v1.z, r);
+                    gch = fmaf(wdy, v1.w, gch);
+                    bch = fmaf(wdy, v2.x, bch);
+                    r = fmaf(wdxy, v2.y, r);
+                    gch = fmaf(wdxy, v2.z, gch);
+                    bch = fmaf(wdxy, v2.w, bch);
+                }
+            }
+            const size_t o = (size_t)Y * W2 + X;
+            out[o] = r;
+            out[oplane + o] = gch;
+            out[2 * oplane + o] = bch;
+        }
     }
 }
 
@@ -120,7 +167,15 @@ cudaError_t launch_upscale(cudaStream_t s, const float* C, const float* grads, i
     if (factor < 1 || factor > kMaxFactor) return cudaErrorInvalidValue;
     const int W2 = W * factor, H2 = H * factor;
     dim3 grid((W2 + kOutW - 1) / kOutW, (H2 + kOutH - 1) / kOutH);
-    k_upscale<<<grid, kOutW * kOutH, 0, s>>>(C, grads, W, H, factor, out); note_launch();
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_upscale, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(3 * sizeof(float4) * kFootW * kFootH));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const size_t smem = 3 * sizeof(float4) * foot_w(factor) * foot_h(factor);
+    k_upscale<<<grid, dim3(kThreadsX, kThreadsY), smem, s>>>(C, grads, W, H, factor, out); note_launch();
     return cudaGetLastError();
 }
 
