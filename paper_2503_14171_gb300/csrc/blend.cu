@@ -54,6 +54,8 @@ __global__ void __launch_bounds__(kBlock) k_blend(BlendArgs a, unsigned long lon
     const int x = tx * kTile + lx, y = ty * kTile + ly;
     const bool inside = x < a.W && y < a.H;
     const float px = (float)x, py = (float)y;
+    // centre of this warp's 16 x 2 pixel strip (rows 2 warp, 2 warp + 1 of the tile)
+    const float wcx = (float)(tx * kTile) + 7.5f, wcy = (float)(ty * kTile + 2 * warp) + 0.5f;
     const uint32_t lanemask_lt = (1u << lane) - 1u;
 
     const int S = (ty / kSuper) * a.stiles_x + (tx / kSuper);
@@ -108,13 +110,16 @@ __global__ void __launch_bounds__(kBlock) k_blend(BlendArgs a, unsigned long lon
         __syncthreads();
         for (int k = 0; !done && k < batch; ++k) {
             const float4 r0 = s_r0[k];
+            if (STATS) ++n_eval;   // every list entry a pixel passes before it stops (the oracle's count)
+            // warp-uniform skip: the Gaussian's alpha >= 1/255 box misses this warp's 16 x 2 strip
+            if (fabsf(r0.x - wcx) > r0.z + 7.5f || fabsf(r0.y - wcy) > r0.w + 0.5f) continue;
             const float4 r1 = s_r1[k];
             const float dx = px - r0.x, dy = py - r0.y;
-            if (STATS) ++n_eval;
             // g = -1/2 (a dx^2 + 2 b dx dy + c dy^2)
-            const float g = -0.5f * (r0.z * dx * dx + r1.x * dy * dy) - r0.w * dx * dy;
-            if (MODE == GS_MODE_3DGS && g < r1.z) continue;     // sigma e^g < 1/255 for sure
-            float alpha = r1.y * __expf(g);
+            const float g = -0.5f * (r1.x * dx * dx + r1.z * dy * dy) - r1.y * dx * dy;
+            if (MODE == GS_MODE_3DGS && g < r1.w) continue;     // sigma e^g < 1/255 for sure
+            const float4 c = s_r2[k];
+            float alpha = c.w * __expf(g);
             bool clamped = false;
             if (MODE == GS_MODE_3DGS) {
                 if (alpha < (1.f / 255.f)) continue;
@@ -126,15 +131,14 @@ __global__ void __launch_bounds__(kBlock) k_blend(BlendArgs a, unsigned long lon
                 done = true;
                 break;
             }
-            const float4 c = s_r2[k];
             const float w = alpha * T;
             C0 = fmaf(c.x, w, C0);
             C1 = fmaf(c.y, w, C1);
             C2 = fmaf(c.z, w, C2);
             if (GRADS) {
-                float gx = -(r0.z * dx + r0.w * dy);
-                float gy = -(r0.w * dx + r1.x * dy);
-                float gxy = fmaf(gx, gy, -r0.w);
+                float gx = -(r1.x * dx + r1.y * dy);
+                float gy = -(r1.y * dx + r1.z * dy);
+                float gxy = fmaf(gx, gy, -r1.y);
                 if (clamped) { gx = 0.f; gy = 0.f; gxy = 0.f; }
                 const float wx = alpha * fmaf(T, gx, Tx);
                 const float wy = alpha * fmaf(T, gy, Ty);

@@ -21,9 +21,10 @@ constexpr int kDevCheck = 2;
 constexpr int64_t kMaxPairs = (int64_t(1) << 30) - 1;
 
 // Per-Gaussian record staged by the blend kernel (3 x 16 B):
-//   r0 = (mean_x, mean_y, conic_a, conic_b)
-//   r1 = (conic_c, opacity, log-alpha reject threshold, unused)
-//   r2 = (red, green, blue, unused)
+//   r0 = (mean_x, mean_y, bx, by): mean and the half-extents of the box outside
+//        which alpha < 1/255 with a relative margin (warp-level skip)
+//   r1 = (conic_a, conic_b, conic_c, exponent reject threshold)
+//   r2 = (red, green, blue, opacity)
 struct Records {
     float4* r0;
     float4* r1;

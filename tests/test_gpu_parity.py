@@ -254,3 +254,18 @@ def test_repeated_calls_are_deterministic(gs):
         C1, G1 = (t.clone() for t in ctx.render_with_grads(dev, cam, W, H))
         C2, G2 = ctx.render_with_grads(dev, cam, W, H)
         assert bool((C1 == C2).all()) and bool((G1 == G2).all())
+
+
+def test_blend_work_counts_match_oracle(gs, ora):
+    """The counting variant of the blend visits exactly the oracle's (pixel,
+    Gaussian) pairs: every list entry before a pixel stops, and the blended ones."""
+    W, H = 64, 64
+    scene = scenes.random_scene(1000, seed=0)
+    cam = scenes.pinhole_camera(W, H)
+    proj = ora.project(scene, cam, W, H)
+    ref = ora.render(proj, ora.bin_pairs(proj))
+    with gs.Context() as ctx:
+        ctx.project(gs.DeviceScene(scene), cam, W, H)
+        n_eval, n_acc = ctx.blend_stats()
+    assert abs(n_eval - ref["n_eval"]) <= 2e-3 * ref["n_eval"]
+    assert abs(n_acc - ref["n_acc"]) <= 2e-3 * ref["n_acc"]
