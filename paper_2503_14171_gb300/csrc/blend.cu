@@ -2,16 +2,21 @@
 // derivatives of the pixel colour (Sec. 4 blend equation; Sec. 5 "3DGS Image
 // Gradients"; supplement "Forward pass").
 //
-// One 256-thread block per 16x16 tile, one pixel per thread.  Binning is done
-// per 64x64 super-tile (4x4 tiles): the block walks its super-tile's
-// depth-ordered list 256 candidates at a time, keeps the Gaussians whose tile
-// rect covers this tile (an order-preserving block compaction, so the kept
-// sequence is exactly the tile's own front-to-back list), stages their records
-// in shared memory and blends them.  The next round's candidate ids and rects
-// are fetched before the current batch is blended, hiding their latency.  A
-// pixel stops when its transmittance would fall below 1e-4; a warp whose
-// pixels have all stopped skips the rest of each batch, and the block leaves
-// once every pixel stopped.
+// One 128-thread block per 16x16 tile; each thread owns the two pixels
+// (x, y) and (x, y + 8) of one column, so the terms of the exponent that
+// depend only on x - mu_x, the shared-memory reads and the loop overhead are
+// shared by two pixels.  Binning is done per 64x64 super-tile (4x4 tiles): the
+// block walks its super-tile's depth-ordered list 256 candidates at a time,
+// keeps the Gaussians whose tile rect covers this tile (an order-preserving
+// block compaction, so the kept sequence is exactly the tile's own
+// front-to-back list) and stages their records in shared memory until at
+// least 256 are staged (or the list ends), then blends them.  The next
+// round's candidate ids and rects are fetched before the staged records are
+// used, hiding their latency.  A pixel stops when its transmittance would fall
+// below 1e-4; the block leaves once every pixel stopped.
+//
+// The exponent is kept in base 2: the record stores the conic scaled by
+// log2(e), g2 = A2 dx^2 + B2 dx dy + C2 dy^2 = g log2(e), and alpha = sigma 2^g2.
 //
 // The state carried per pixel is the transmittance T = 1 - A and its
 // derivatives (the paper's A-recurrences with the sign flipped): tracking T
@@ -29,132 +34,215 @@
 namespace gs {
 namespace {
 
-constexpr int kBlock = kTilePixels;   // 256
-constexpr int kWarps = kBlock / 32;
+constexpr int kThreads = 128;            // 16 columns x 8 rows, 2 pixels per thread
+constexpr int kWarps = kThreads / 32;
+constexpr int kCand = 2 * kThreads;      // candidates examined per compaction round
+constexpr int kStage = 2 * kCand;        // staged records per batch (>= kCand before blending)
+constexpr float kLn2 = 0.69314718055994531f;
 
 __device__ __forceinline__ bool covers(ushort4 r, int tx, int ty)
 {
     return (int)r.x <= tx && tx <= (int)r.z && (int)r.y <= ty && ty <= (int)r.w;
 }
 
-// STATS: count the (pixel, Gaussian) pairs evaluated and blended instead of
-// writing images (used once, outside timed regions, to size the FLOP count).
-template <bool GRADS, int MODE, bool STATS = false>
-__global__ void __launch_bounds__(kBlock) k_blend(BlendArgs a, unsigned long long* __restrict__ stats = nullptr)
+struct PixelState {
+    float T, Tx, Ty, Txy;
+    float C0, C1, C2, X0, X1, X2, Y0, Y1, Y2, Z0, Z1, Z2;
+    int last;
+    bool done;
+};
+
+__device__ __forceinline__ void init(PixelState& p, bool inside)
 {
-    __shared__ float4 s_r0[kBlock];
-    __shared__ float4 s_r1[kBlock];
-    __shared__ float4 s_r2[kBlock];
-    __shared__ int s_wcnt[kWarps];
+    p.T = 1.f;
+    p.Tx = p.Ty = p.Txy = 0.f;
+    p.C0 = p.C1 = p.C2 = 0.f;
+    p.X0 = p.X1 = p.X2 = 0.f;
+    p.Y0 = p.Y1 = p.Y2 = 0.f;
+    p.Z0 = p.Z1 = p.Z2 = 0.f;
+    p.last = 0;
+    p.done = !inside;
+}
+
+// One (pixel, Gaussian) pair: g2 is the exponent in base 2, (dx, dy) the offset
+// from the mean, r0 = (mu_x, mu_y, -a, -c), r1 = (A2, B2, C2, reject threshold),
+// c = (r, g, b, sigma).  Returns true if the pair was blended.
+template <bool GRADS, int MODE>
+__device__ __forceinline__ bool blend_pair(PixelState& p, float g2, float dx, float dy, const float4& r0,
+                                           const float4& r1, const float4& c, int idx)
+{
+    if (MODE == GS_MODE_3DGS && g2 < r1.w) return false;   // sigma e^g < 1/255 for sure
+    float alpha = c.w * exp2f(g2);
+    bool clamped = false;
+    if (MODE == GS_MODE_3DGS) {
+        if (alpha < (1.f / 255.f)) return false;
+        clamped = alpha > 0.99f;
+        alpha = fminf(alpha, 0.99f);
+    }
+    const float Tn = p.T * (1.f - alpha);
+    if (MODE == GS_MODE_3DGS && Tn < 1e-4f) {
+        p.done = true;
+        return false;
+    }
+    const float w = alpha * p.T;
+    p.C0 = fmaf(c.x, w, p.C0);
+    p.C1 = fmaf(c.y, w, p.C1);
+    p.C2 = fmaf(c.z, w, p.C2);
+    if (GRADS) {
+        const float bn = r1.y * kLn2;                       // -b
+        float gx = fmaf(r0.z, dx, bn * dy);                 // -(a dx + b dy)
+        float gy = fmaf(r0.w, dy, bn * dx);                 // -(b dx + c dy)
+        float gxy = fmaf(gx, gy, bn);                       // g_x g_y + g_xy
+        if (clamped) { gx = 0.f; gy = 0.f; gxy = 0.f; }
+        const float wx = alpha * fmaf(p.T, gx, p.Tx);
+        const float wy = alpha * fmaf(p.T, gy, p.Ty);
+        const float wxy = alpha * (p.T * gxy + p.Tx * gy + p.Ty * gx + p.Txy);
+        p.X0 = fmaf(c.x, wx, p.X0); p.X1 = fmaf(c.y, wx, p.X1); p.X2 = fmaf(c.z, wx, p.X2);
+        p.Y0 = fmaf(c.x, wy, p.Y0); p.Y1 = fmaf(c.y, wy, p.Y1); p.Y2 = fmaf(c.z, wy, p.Y2);
+        p.Z0 = fmaf(c.x, wxy, p.Z0); p.Z1 = fmaf(c.y, wxy, p.Z1); p.Z2 = fmaf(c.z, wxy, p.Z2);
+        p.Tx -= wx;
+        p.Ty -= wy;
+        p.Txy -= wxy;
+    }
+    p.T = Tn;
+    p.last = idx + 1;
+    return true;
+}
+
+template <bool GRADS>
+__device__ __forceinline__ void store(const BlendArgs& a, const PixelState& p, int x, int y)
+{
+    const size_t plane = (size_t)a.W * a.H;
+    const size_t pix = (size_t)y * a.W + x;
+    a.out_C[pix] = fmaf(p.T, a.bg.x, p.C0);
+    a.out_C[plane + pix] = fmaf(p.T, a.bg.y, p.C1);
+    a.out_C[2 * plane + pix] = fmaf(p.T, a.bg.z, p.C2);
+    if (GRADS) {
+        float* G = a.out_G;
+        G[pix] = fmaf(p.Tx, a.bg.x, p.X0);
+        G[plane + pix] = fmaf(p.Tx, a.bg.y, p.X1);
+        G[2 * plane + pix] = fmaf(p.Tx, a.bg.z, p.X2);
+        G[3 * plane + pix] = fmaf(p.Ty, a.bg.x, p.Y0);
+        G[4 * plane + pix] = fmaf(p.Ty, a.bg.y, p.Y1);
+        G[5 * plane + pix] = fmaf(p.Ty, a.bg.z, p.Y2);
+        G[6 * plane + pix] = fmaf(p.Txy, a.bg.x, p.Z0);
+        G[7 * plane + pix] = fmaf(p.Txy, a.bg.y, p.Z1);
+        G[8 * plane + pix] = fmaf(p.Txy, a.bg.z, p.Z2);
+    }
+    if (a.state) a.state[pix] = make_float4(p.T, p.Tx, p.Ty, p.Txy);
+    if (a.count) a.count[pix] = p.last;
+}
+
+// STATS: count the (pixel, Gaussian) pairs evaluated (every list entry a pixel
+// passes before it stops, the oracle's count) and blended, instead of writing
+// images (used once, outside timed regions, to size the FLOP count).
+template <bool GRADS, int MODE, bool STATS = false>
+__global__ void __launch_bounds__(kThreads) k_blend(BlendArgs a, unsigned long long* __restrict__ stats = nullptr)
+{
+    __shared__ float4 s_r0[kStage];
+    __shared__ float4 s_r1[kStage];
+    __shared__ float4 s_r2[kStage];
+    __shared__ int s_wcnt[2 * kWarps];
 
     const int tile = blockIdx.x;
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
-    const int x = tx * kTile + lx, y = ty * kTile + ly;
-    const bool inside = x < a.W && y < a.H;
-    const float px = (float)x, py = (float)y;
-    // centre of this warp's 16 x 2 pixel strip (rows 2 warp, 2 warp + 1 of the tile)
-    const float wcx = (float)(tx * kTile) + 7.5f, wcy = (float)(ty * kTile + 2 * warp) + 0.5f;
+    const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;   // ly in [0, 8)
+    const int x = tx * kTile + lx, y0 = ty * kTile + ly, y1 = y0 + 8;
+    const float px = (float)x, py0 = (float)y0;
     const uint32_t lanemask_lt = (1u << lane) - 1u;
 
     const int S = (ty / kSuper) * a.stiles_x + (tx / kSuper);
     const uint2 sr = a.sranges[S];
     const int total = (int)(sr.y - sr.x);
 
-    float T = 1.f, Tx = 0.f, Ty = 0.f, Txy = 0.f;
-    float C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    float X0 = 0.f, X1 = 0.f, X2 = 0.f;
-    float Y0 = 0.f, Y1 = 0.f, Y2 = 0.f;
-    float Z0 = 0.f, Z1 = 0.f, Z2 = 0.f;
-    int last = 0;
-    int list_base = 0;    // position of this round's first kept Gaussian in the tile's list
-    bool done = !inside;
+    PixelState p0, p1;
+    init(p0, x < a.W && y0 < a.H);
+    init(p1, x < a.W && y1 < a.H);
     uint32_t n_eval = 0, n_acc = 0;
+    int list_base = 0;   // position of the batch's first record in the tile's list
 
-    // candidate of the first round
-    uint32_t cid = 0xFFFFFFFFu;
-    ushort4 crect = make_ushort4(1, 1, 0, 0);
-    if ((int)threadIdx.x < total) {
-        cid = a.pair_words[2 * (size_t)(sr.x + threadIdx.x)];
-        if (cid < a.n) crect = a.rect[cid];
+    // candidates of the first round: this thread holds positions tid and tid + 128
+    uint32_t cid[2];
+    ushort4 crect[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int c = h * kThreads + (int)threadIdx.x;
+        cid[h] = 0xFFFFFFFFu;
+        crect[h] = make_ushort4(1, 1, 0, 0);
+        if (c < total) {
+            cid[h] = a.pair_words[2 * (size_t)(sr.x + c)];
+            if (cid[h] < a.n) crect[h] = a.rect[cid[h]];
+        }
     }
 
-    for (int c0 = 0; c0 < total; c0 += kBlock) {
-        if (__syncthreads_count(done) == kBlock) break;
-        // order-preserving compaction of the candidates that cover this tile
-        const bool hit = cid < a.n && covers(crect, tx, ty);
-        const uint32_t ball = __ballot_sync(0xffffffffu, hit);
-        if (lane == 0) s_wcnt[warp] = __popc(ball);
-        __syncthreads();
-        int wbase = 0, batch = 0;
+    int c0 = 0;
+    while (c0 < total) {
+        if (__syncthreads_count(p0.done && p1.done) == kThreads) break;
+        // stage rounds of kCand candidates until >= kCand records are staged
+        int staged = 0;
+        while (c0 < total && staged < kCand) {
+            bool hit[2];
+            uint32_t ball[2];
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-            const int cw = s_wcnt[w];
-            wbase += w < warp ? cw : 0;
-            batch += cw;
+            for (int h = 0; h < 2; ++h) {
+                hit[h] = cid[h] < a.n && covers(crect[h], tx, ty);
+                ball[h] = __ballot_sync(0xffffffffu, hit[h]);
+                if (lane == 0) s_wcnt[h * kWarps + warp] = __popc(ball[h]);
+            }
+            __syncthreads();
+            // candidate order: first half (positions tid) then second half (tid + 128)
+            int base0 = 0, tot0 = 0, base1 = 0, tot1 = 0;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) {
+                const int a0 = s_wcnt[w], a1 = s_wcnt[kWarps + w];
+                base0 += w < warp ? a0 : 0;
+                base1 += w < warp ? a1 : 0;
+                tot0 += a0;
+                tot1 += a1;
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (hit[h]) {
+                    const int pos = staged + (h ? tot0 + base1 : base0) + __popc(ball[h] & lanemask_lt);
+                    s_r0[pos] = a.rec.r0[cid[h]];
+                    s_r1[pos] = a.rec.r1[cid[h]];
+                    s_r2[pos] = a.rec.r2[cid[h]];
+                }
+            }
+            staged += tot0 + tot1;
+            c0 += kCand;
+            // fetch the next round's candidates
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int c = c0 + h * kThreads + (int)threadIdx.x;
+                cid[h] = 0xFFFFFFFFu;
+                if (c < total) {
+                    cid[h] = a.pair_words[2 * (size_t)(sr.x + c)];
+                    if (cid[h] < a.n) crect[h] = a.rect[cid[h]];
+                }
+            }
+            __syncthreads();   // s_wcnt is reused by the next round
         }
-        if (hit) {
-            const int pos = wbase + __popc(ball & lanemask_lt);
-            s_r0[pos] = a.rec.r0[cid];
-            s_r1[pos] = a.rec.r1[cid];
-            s_r2[pos] = a.rec.r2[cid];
-        }
-        // fetch the next round's candidate while this batch is blended
-        const int cn = c0 + kBlock + (int)threadIdx.x;
-        cid = 0xFFFFFFFFu;
-        if (cn < total) {
-            cid = a.pair_words[2 * (size_t)(sr.x + cn)];
-            if (cid < a.n) crect = a.rect[cid];
-        }
-        __syncthreads();
-        for (int k = 0; !done && k < batch; ++k) {
+        for (int k = 0; k < staged && !(p0.done && p1.done); ++k) {
             const float4 r0 = s_r0[k];
-            if (STATS) ++n_eval;   // every list entry a pixel passes before it stops (the oracle's count)
-            // warp-uniform skip: the Gaussian's alpha >= 1/255 box misses this warp's 16 x 2 strip
-            if (fabsf(r0.x - wcx) > r0.z + 7.5f || fabsf(r0.y - wcy) > r0.w + 0.5f) continue;
             const float4 r1 = s_r1[k];
-            const float dx = px - r0.x, dy = py - r0.y;
-            // g = -1/2 (a dx^2 + 2 b dx dy + c dy^2)
-            const float g = -0.5f * (r1.x * dx * dx + r1.z * dy * dy) - r1.y * dx * dy;
-            if (MODE == GS_MODE_3DGS && g < r1.w) continue;     // sigma e^g < 1/255 for sure
-            const float4 c = s_r2[k];
-            float alpha = c.w * __expf(g);
-            bool clamped = false;
-            if (MODE == GS_MODE_3DGS) {
-                if (alpha < (1.f / 255.f)) continue;
-                clamped = alpha > 0.99f;
-                alpha = fminf(alpha, 0.99f);
+            const float dx = px - r0.x;
+            const float dy0 = py0 - r0.y, dy1 = dy0 + 8.f;
+            const float ax = r1.x * dx * dx;                 // A2 dx^2, shared by both pixels
+            const float bx = r1.y * dx;                      // B2 dx
+            const float g20 = fmaf(dy0, fmaf(r1.z, dy0, bx), ax);
+            const float g21 = fmaf(dy1, fmaf(r1.z, dy1, bx), ax);
+            const bool live0 = !p0.done && !(MODE == GS_MODE_3DGS && g20 < r1.w);
+            const bool live1 = !p1.done && !(MODE == GS_MODE_3DGS && g21 < r1.w);
+            if (STATS) n_eval += (p0.done ? 0u : 1u) + (p1.done ? 0u : 1u);
+            if (live0 || live1) {
+                const float4 c = s_r2[k];
+                if (live0 && blend_pair<GRADS, MODE>(p0, g20, dx, dy0, r0, r1, c, list_base + k)) ++n_acc;
+                if (live1 && blend_pair<GRADS, MODE>(p1, g21, dx, dy1, r0, r1, c, list_base + k)) ++n_acc;
             }
-            const float Tn = T * (1.f - alpha);
-            if (MODE == GS_MODE_3DGS && Tn < 1e-4f) {
-                done = true;
-                break;
-            }
-            const float w = alpha * T;
-            C0 = fmaf(c.x, w, C0);
-            C1 = fmaf(c.y, w, C1);
-            C2 = fmaf(c.z, w, C2);
-            if (GRADS) {
-                float gx = -(r1.x * dx + r1.y * dy);
-                float gy = -(r1.y * dx + r1.z * dy);
-                float gxy = fmaf(gx, gy, -r1.y);
-                if (clamped) { gx = 0.f; gy = 0.f; gxy = 0.f; }
-                const float wx = alpha * fmaf(T, gx, Tx);
-                const float wy = alpha * fmaf(T, gy, Ty);
-                const float wxy = alpha * (T * gxy + Tx * gy + Ty * gx + Txy);
-                X0 = fmaf(c.x, wx, X0); X1 = fmaf(c.y, wx, X1); X2 = fmaf(c.z, wx, X2);
-                Y0 = fmaf(c.x, wy, Y0); Y1 = fmaf(c.y, wy, Y1); Y2 = fmaf(c.z, wy, Y2);
-                Z0 = fmaf(c.x, wxy, Z0); Z1 = fmaf(c.y, wxy, Z1); Z2 = fmaf(c.z, wxy, Z2);
-                Tx -= wx;
-                Ty -= wy;
-                Txy -= wxy;
-            }
-            T = Tn;
-            last = list_base + k + 1;
-            if (STATS) ++n_acc;
         }
-        list_base += batch;
+        list_base += staged;
     }
     if (STATS) {
         unsigned long long e = n_eval, acc = n_acc;
@@ -169,32 +257,15 @@ __global__ void __launch_bounds__(kBlock) k_blend(BlendArgs a, unsigned long lon
         }
         return;
     }
-    if (!inside) return;
-    const size_t plane = (size_t)a.W * a.H;
-    const size_t pix = (size_t)y * a.W + x;
-    a.out_C[pix] = fmaf(T, a.bg.x, C0);
-    a.out_C[plane + pix] = fmaf(T, a.bg.y, C1);
-    a.out_C[2 * plane + pix] = fmaf(T, a.bg.z, C2);
-    if (GRADS) {
-        float* G = a.out_G;
-        G[pix] = fmaf(Tx, a.bg.x, X0);
-        G[plane + pix] = fmaf(Tx, a.bg.y, X1);
-        G[2 * plane + pix] = fmaf(Tx, a.bg.z, X2);
-        G[3 * plane + pix] = fmaf(Ty, a.bg.x, Y0);
-        G[4 * plane + pix] = fmaf(Ty, a.bg.y, Y1);
-        G[5 * plane + pix] = fmaf(Ty, a.bg.z, Y2);
-        G[6 * plane + pix] = fmaf(Txy, a.bg.x, Z0);
-        G[7 * plane + pix] = fmaf(Txy, a.bg.y, Z1);
-        G[8 * plane + pix] = fmaf(Txy, a.bg.z, Z2);
-    }
-    if (a.state) a.state[pix] = make_float4(T, Tx, Ty, Txy);
-    if (a.count) a.count[pix] = last;
+    if (x >= a.W) return;
+    if (y0 < a.H) store<GRADS>(a, p0, x, y0);
+    if (y1 < a.H) store<GRADS>(a, p1, x, y1);
 }
 
 template <bool GRADS, int MODE>
 cudaError_t launch_t(cudaStream_t s, const BlendArgs& a)
 {
-    k_blend<GRADS, MODE><<<a.tiles_x * a.tiles_y, kBlock, 0, s>>>(a); note_launch();
+    k_blend<GRADS, MODE><<<a.tiles_x * a.tiles_y, kThreads, 0, s>>>(a); note_launch();
     return cudaGetLastError();
 }
 
@@ -204,9 +275,9 @@ cudaError_t launch_blend_stats(cudaStream_t s, int mode, const BlendArgs& a, uns
 {
     const int tiles = a.tiles_x * a.tiles_y;
     if (mode == GS_MODE_EXACT)
-        k_blend<true, GS_MODE_EXACT, true><<<tiles, kBlock, 0, s>>>(a, stats);
+        k_blend<true, GS_MODE_EXACT, true><<<tiles, kThreads, 0, s>>>(a, stats);
     else
-        k_blend<true, GS_MODE_3DGS, true><<<tiles, kBlock, 0, s>>>(a, stats);
+        k_blend<true, GS_MODE_3DGS, true><<<tiles, kThreads, 0, s>>>(a, stats);
     note_launch();
     return cudaGetLastError();
 }

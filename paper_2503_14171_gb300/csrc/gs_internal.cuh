@@ -21,9 +21,9 @@ constexpr int kDevCheck = 2;
 constexpr int64_t kMaxPairs = (int64_t(1) << 30) - 1;
 
 // Per-Gaussian record staged by the blend kernel (3 x 16 B):
-//   r0 = (mean_x, mean_y, bx, by): mean and the half-extents of the box outside
-//        which alpha < 1/255 with a relative margin (warp-level skip)
-//   r1 = (conic_a, conic_b, conic_c, exponent reject threshold)
+//   r0 = (mean_x, mean_y, -conic_a, -conic_c)
+//   r1 = (A2, B2, C2, thr2): the exponent in base 2, g2 = A2 dx^2 + B2 dx dy + C2 dy^2
+//        = log2(e) * (-1/2)(a dx^2 + 2 b dx dy + c dy^2), and its reject threshold
 //   r2 = (red, green, blue, opacity)
 struct Records {
     float4* r0;

@@ -226,19 +226,14 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
         col[1] = rgb_in[3 * i + 1];
         col[2] = rgb_in[3 * i + 2];
     }
-    // reject threshold on the exponent: g < ln(1/(255 sigma)) - 1e-4 guarantees
-    // sigma e^g < 1/255 in FP32, so the blend may skip the exponential there.
-    const float thr = (mode == GS_MODE_EXACT) ? -INFINITY : (-L - 1e-4f);
-    // half-extents of the box outside which g < -(L + 1e-3), i.e. alpha is below
-    // 1/255 by a relative 1e-3 (the blend skips such a Gaussian for a whole warp)
-    float bx = INFINITY, by = INFINITY;
-    if (mode != GS_MODE_EXACT) {
-        const float Lm = fmaxf(L, 0.f) + 1e-3f;
-        bx = sqrtf(2.f * Lm * c00) * 1.0001f + 1e-3f;
-        by = sqrtf(2.f * Lm * c11) * 1.0001f + 1e-3f;
-    }
-    rec.r0[i] = make_float4(m2x, m2y, bx, by);
-    rec.r1[i] = make_float4(ca, cb, cc, thr);
+    // The blend evaluates the exponent in base 2: g2 = g log2(e) with
+    // g = -1/2 (a dx^2 + 2 b dx dy + c dy^2).  Reject threshold: g < ln(1/(255 sigma))
+    // - 1e-4 guarantees sigma e^g < 1/255 in FP32, so the blend may skip the
+    // exponential there.
+    constexpr float kLog2e = 1.4426950408889634f;
+    const float thr = (mode == GS_MODE_EXACT) ? -INFINITY : (-L - 1e-4f) * kLog2e;
+    rec.r0[i] = make_float4(m2x, m2y, -ca, -cc);
+    rec.r1[i] = make_float4(-0.5f * kLog2e * ca, -kLog2e * cb, -0.5f * kLog2e * cc, thr);
     rec.r2[i] = make_float4(col[0], col[1], col[2], op);
 }
 
@@ -250,7 +245,8 @@ __global__ void k_unpack(Records rec, const int* __restrict__ radius, const uint
     if (i >= n) return;
     const float4 a = rec.r0[i], b = rec.r1[i], c = rec.r2[i];
     if (mean2d) { mean2d[2 * i] = a.x; mean2d[2 * i + 1] = a.y; }
-    if (conic) { conic[3 * i] = b.x; conic[3 * i + 1] = b.y; conic[3 * i + 2] = b.z; }
+    // r0 = (mu, -a, -c), r1.y = -b log2(e)
+    if (conic) { conic[3 * i] = -a.z; conic[3 * i + 1] = -b.y * 0.69314718055994531f; conic[3 * i + 2] = -a.w; }
     if (rgb) { rgb[3 * i] = c.x; rgb[3 * i + 1] = c.y; rgb[3 * i + 2] = c.z; }
     if (opacity) opacity[i] = c.w;
     if (depth) depth[i] = depth_in[i];
