@@ -175,21 +175,30 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
         (st = ensure(c, c->did[0], sizeof(uint32_t) * n)) || (st = ensure(c, c->did[1], sizeof(uint32_t) * n)) ||
         (st = ensure(c, c->offsets, sizeof(uint32_t) * (n + 1))) ||
         (st = ensure(c, c->scan_partials, sizeof(unsigned long long) * scan_partials_count(n))) ||
-        (st = ensure(c, c->scan_totals, 4 * sizeof(unsigned long long))) ||
+        (st = ensure(c, c->scan_totals, 6 * sizeof(unsigned long long))) ||
+        (st = ensure(c, c->super_counts, sizeof(uint32_t) * Ts)) ||
         (st = ensure(c, c->sranges, sizeof(uint2) * Ts)) || (st = ensure(c, c->sort_hist, sizeof(uint32_t) * 8 * 256)) ||
+        (st = ensure(c, c->sort_status, sizeof(uint32_t) * radix_status_words(n, 0, 32))) ||
         (st = ensure(c, c->sort_counter, sizeof(uint32_t) * 8)))
         return st;
 
     const Records rec{as<float4>(c->rec0), as<float4>(c->rec1), as<float4>(c->rec2)};
     const CameraParams cp = make_camera(*cam, W, H);
+    // scan_totals: [0] super-tile pairs, [1] tile pairs (from the projection),
+    // [2..3] scan totals, [4] scan tile counter
+    unsigned long long* totals = as<unsigned long long>(c->scan_totals);
+    GS_CUDA(c, cudaMemsetAsync(totals, 0, 2 * sizeof(unsigned long long), c->stream));
     GS_CUDA(c, launch_project(c->stream, *g, cp, W, H, tiles_x, tiles_y, c->opt.mode, rec, as<float>(c->depth),
                               as<int>(c->radius), as<ushort4>(c->rect), as<uint32_t>(c->tiles_touched),
-                              as<uint32_t>(c->supers_touched), as<uint32_t>(c->dkey[0]), as<uint32_t>(c->did[0])));
+                              as<uint32_t>(c->supers_touched), as<uint32_t>(c->dkey[0]), as<uint32_t>(c->did[0]),
+                              totals));
+    // the pair totals travel to the host while the depth sort runs
+    GS_CUDA(c, cudaMemcpyAsync(c->h_scalar, totals, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+    GS_CUDA(c, cudaEventRecord(c->totals_ready, c->stream));
 
     // depth order: stable radix sort of the FP32 depth bits (ids ascending)
     int sorted = 0;
     if (n > 1) {
-        if ((st = ensure(c, c->sort_status, sizeof(uint32_t) * radix_status_words(n, 0, 32)))) return st;
         uint32_t* keys[2] = {as<uint32_t>(c->dkey[0]), as<uint32_t>(c->dkey[1])};
         uint32_t* vals[2] = {as<uint32_t>(c->did[0]), as<uint32_t>(c->did[1])};
         GS_CUDA(c, radix_sort_u32_pairs(c->stream, keys, vals, n, 0, 32, as<uint32_t>(c->sort_hist),
@@ -199,14 +208,12 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
     c->sorted_ids_buf = sorted;
     const uint32_t* ids = as<uint32_t>(c->did[sorted]);
 
-    // super-tile pair offsets in depth order, their exact count Ps and the
-    // (tile, Gaussian) pair count P in the same pass
-    unsigned long long* totals = as<unsigned long long>(c->scan_totals);
-    GS_CUDA(c, launch_scan_gathered(c->stream, as<uint32_t>(c->supers_touched), as<uint32_t>(c->tiles_touched), ids, n,
+    // super-tile pair offsets in depth order
+    GS_CUDA(c, launch_scan_gathered(c->stream, as<uint32_t>(c->supers_touched), nullptr, ids, n,
                                     as<uint32_t>(c->offsets), as<unsigned long long>(c->scan_partials),
-                                    reinterpret_cast<uint32_t*>(totals + 2), totals, as<int>(c->errword)));
-    GS_CUDA(c, cudaMemcpyAsync(c->h_scalar, totals, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
-    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+                                    reinterpret_cast<uint32_t*>(totals + 4), totals + 2, as<int>(c->errword)));
+
+    GS_CUDA(c, cudaEventSynchronize(c->totals_ready));
     const unsigned long long Ps64 = c->h_scalar[0], P64 = c->h_scalar[1];
     const int64_t limit = c->opt.max_pairs > 0 ? std::min<int64_t>(c->opt.max_pairs, kMaxPairs) : kMaxPairs;
     if ((int64_t)P64 > limit)
@@ -214,23 +221,38 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
     if ((int64_t)Ps64 > kMaxPairs)
         return fail(c, GS_ERR_CAPACITY, "super-tile pair count %llu exceeds %lld", Ps64, (long long)kMaxPairs);
     const uint32_t Ps = (uint32_t)Ps64;
-    if ((st = read_device_error(c))) return st;
 
     if ((st = ensure(c, c->pairs[0], sizeof(uint64_t) * Ps)) || (st = ensure(c, c->pairs[1], sizeof(uint64_t) * Ps)))
         return st;
+    const int sbits = bits_for((uint32_t)Ts);
+    const int spasses = radix_passes(32, 32 + sbits);
+    if ((st = ensure(c, c->sort_status, sizeof(uint32_t) * std::max(radix_status_words(Ps, 32, 32 + sbits),
+                                                                    radix_status_words(n, 0, 32)))))
+        return st;
     uint64_t* pairs[2] = {as<uint64_t>(c->pairs[0]), as<uint64_t>(c->pairs[1])};
-    GS_CUDA(c, launch_emit_pairs(c->stream, ids, as<uint32_t>(c->offsets), as<ushort4>(c->rect), n, stiles_x, pairs[0]));
+    const bool counted = Ts <= kMaxSupersForCounts;
+    if (counted) GS_CUDA(c, cudaMemsetAsync(c->super_counts.p, 0, sizeof(uint32_t) * Ts, c->stream));
+    GS_CUDA(c, launch_emit_pairs(c->stream, ids, as<uint32_t>(c->offsets), as<ushort4>(c->rect), n, stiles_x, pairs[0],
+                                 counted ? as<uint32_t>(c->super_counts) : nullptr, (uint32_t)Ts));
     int psorted = 0;
-    if (Ps > 1 && Ts > 1) {
-        const int sbits = bits_for((uint32_t)Ts);
-        if ((st = ensure(c, c->sort_status, sizeof(uint32_t) * radix_status_words(Ps, 32, 32 + sbits)))) return st;
-        GS_CUDA(c, radix_sort_u64_keys(c->stream, pairs, Ps, 32, 32 + sbits, as<uint32_t>(c->sort_hist),
-                                       as<uint32_t>(c->sort_status), as<uint32_t>(c->sort_counter),
-                                       as<int>(c->errword), &psorted));
+    if (counted) {
+        // digit histograms of the super-tile passes and the super-tile ranges,
+        // both from the per-super-tile counts
+        GS_CUDA(c, launch_supers_to_hist(c->stream, as<uint32_t>(c->super_counts), (uint32_t)Ts, spasses,
+                                         as<uint32_t>(c->sort_hist), as<uint2>(c->sranges)));
+        if (Ps > 1 && Ts > 1)
+            GS_CUDA(c, radix_sort_u64_keys(c->stream, pairs, Ps, 32, 32 + sbits, as<uint32_t>(c->sort_hist),
+                                           as<uint32_t>(c->sort_status), as<uint32_t>(c->sort_counter),
+                                           as<int>(c->errword), &psorted, true));
+    } else {
+        if (Ps > 1 && Ts > 1)
+            GS_CUDA(c, radix_sort_u64_keys(c->stream, pairs, Ps, 32, 32 + sbits, as<uint32_t>(c->sort_hist),
+                                           as<uint32_t>(c->sort_status), as<uint32_t>(c->sort_counter),
+                                           as<int>(c->errword), &psorted, false));
+        GS_CUDA(c, cudaMemsetAsync(c->sranges.p, 0, sizeof(uint2) * Ts, c->stream));
+        GS_CUDA(c, launch_ranges(c->stream, pairs[psorted], Ps, (uint32_t)Ts, as<uint2>(c->sranges)));
     }
     c->sorted_pairs_buf = psorted;
-    GS_CUDA(c, cudaMemsetAsync(c->sranges.p, 0, sizeof(uint2) * Ts, c->stream));
-    GS_CUDA(c, launch_ranges(c->stream, pairs[psorted], Ps, (uint32_t)Ts, as<uint2>(c->sranges)));
 
     c->n = n;
     c->W = W;
@@ -326,6 +348,12 @@ gs_status gs_create(gs_ctx** out, void* stream, const gs_options* opt)
         delete c;
         return GS_ERR_OOM;
     }
+    if (cudaEventCreateWithFlags(&c->totals_ready, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeHost(c->h_scalar);
+        delete c;
+        return GS_ERR_CUDA;
+    }
     if (ensure(c, c->errword, sizeof(int)) != GS_OK) {
         cudaFreeHost(c->h_scalar);
         delete c;
@@ -349,11 +377,13 @@ gs_status gs_destroy(gs_ctx* c)
     cudaStreamSynchronize(c->stream);
     DevBuf* bufs[] = {&c->rec0, &c->rec1, &c->rec2, &c->depth, &c->radius, &c->rect, &c->tiles_touched,
                       &c->supers_touched, &c->dkey[0], &c->dkey[1], &c->did[0], &c->did[1], &c->offsets,
-                      &c->scan_partials, &c->scan_totals, &c->pairs[0], &c->pairs[1], &c->sort_hist, &c->sort_status,
+                      &c->scan_partials, &c->scan_totals, &c->super_counts, &c->pairs[0], &c->pairs[1],
+                      &c->sort_hist, &c->sort_status,
                       &c->sort_counter, &c->sranges, &c->tile_count, &c->tile_start, &c->state, &c->count,
                       &c->errword};
     for (DevBuf* b : bufs) release(*b);
     if (c->h_scalar) cudaFreeHost(c->h_scalar);
+    if (c->totals_ready) cudaEventDestroy(c->totals_ready);
     cudaGetLastError();
     delete c;
     return GS_OK;

@@ -16,24 +16,42 @@
 namespace gs {
 namespace {
 
+// COUNT: also accumulate per-super-tile pair counts (shared memory, then one
+// atomic per touched super-tile and block).
+template <bool COUNT>
 __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ ids, const uint32_t* __restrict__ offsets,
                                               const ushort4* __restrict__ rect, uint32_t n, int stiles_x,
-                                              uint64_t* __restrict__ pairs)
+                                              uint64_t* __restrict__ pairs, uint32_t* __restrict__ counts,
+                                              uint32_t Ts)
 {
+    __shared__ uint32_t s_cnt[COUNT ? kMaxSupersForCounts : 1];
+    if (COUNT) {
+        for (uint32_t t = threadIdx.x; t < Ts; t += blockDim.x) s_cnt[t] = 0;
+        __syncthreads();
+    }
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    uint32_t off = offsets[k];
-    const uint32_t end = offsets[k + 1];
-    if (off == end) return;
-    const uint32_t id = ids[k];
-    if (id >= n) return;   // only after an expired bounded wait in the sort
-    const ushort4 r = rect[id];
-    const int sx0 = r.x / kSuper, sx1 = r.z / kSuper, sy0 = r.y / kSuper, sy1 = r.w / kSuper;
-    for (int sy = sy0; sy <= sy1; ++sy)
-        for (int sx = sx0; sx <= sx1 && off < end; ++sx) {
-            const uint64_t s = (uint64_t)(sy * stiles_x + sx);
-            pairs[off++] = (s << 32) | id;
+    if (k < n) {
+        uint32_t off = offsets[k];
+        const uint32_t end = offsets[k + 1];
+        const uint32_t id = ids[k];
+        if (off < end && id < n) {   // id >= n only after an expired bounded wait in the sort
+            const ushort4 r = rect[id];
+            const int sx0 = r.x / kSuper, sx1 = r.z / kSuper, sy0 = r.y / kSuper, sy1 = r.w / kSuper;
+            for (int sy = sy0; sy <= sy1; ++sy)
+                for (int sx = sx0; sx <= sx1 && off < end; ++sx) {
+                    const uint32_t s = (uint32_t)(sy * stiles_x + sx);
+                    pairs[off++] = ((uint64_t)s << 32) | id;
+                    if (COUNT && s < Ts) atomicAdd(&s_cnt[s], 1u);
+                }
         }
+    }
+    if (COUNT) {
+        __syncthreads();
+        for (uint32_t t = threadIdx.x; t < Ts; t += blockDim.x) {
+            const uint32_t v = s_cnt[t];
+            if (v) atomicAdd(&counts[t], v);
+        }
+    }
 }
 
 __global__ void __launch_bounds__(256) k_ranges(const uint64_t* __restrict__ pairs, uint32_t P, uint32_t T,
@@ -130,10 +148,14 @@ __global__ void __launch_bounds__(1024) k_tile_starts(const uint32_t* __restrict
 }  // namespace
 
 cudaError_t launch_emit_pairs(cudaStream_t s, const uint32_t* ids, const uint32_t* offsets, const ushort4* rect,
-                              uint32_t n, int stiles_x, uint64_t* pairs)
+                              uint32_t n, int stiles_x, uint64_t* pairs, uint32_t* counts, uint32_t Ts)
 {
     if (n == 0) return cudaSuccess;
-    k_emit<<<(n + 255) / 256, 256, 0, s>>>(ids, offsets, rect, n, stiles_x, pairs); note_launch();
+    if (counts && Ts <= (uint32_t)kMaxSupersForCounts)
+        k_emit<true><<<(n + 255) / 256, 256, 0, s>>>(ids, offsets, rect, n, stiles_x, pairs, counts, Ts);
+    else
+        k_emit<false><<<(n + 255) / 256, 256, 0, s>>>(ids, offsets, rect, n, stiles_x, pairs, nullptr, 0);
+    note_launch();
     return cudaGetLastError();
 }
 

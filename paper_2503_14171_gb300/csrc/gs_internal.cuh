@@ -92,6 +92,8 @@ struct gs_ctx {
     gs::DevBuf sort_hist;               // uint32[passes][256]
     gs::DevBuf sort_status;             // uint32[passes][tiles][256]
     gs::DevBuf sort_counter;            // uint32[passes]
+    gs::DevBuf super_counts;            // uint32[super-tiles]
+    cudaEvent_t totals_ready = nullptr; // recorded after the pair totals are copied to the host
     // per tile / pixel
     gs::DevBuf sranges;                 // uint2[super-tiles]
     gs::DevBuf tile_count, tile_start;  // uint32[tiles] (per-tile list materialisation)
@@ -116,7 +118,7 @@ inline void note_launch() { ++launch_counter(); }
 cudaError_t launch_project(cudaStream_t s, const gs_gaussians& g, const CameraParams& cam, int W, int H,
                            int tiles_x, int tiles_y, int mode, Records rec, float* depth, int* radius,
                            ushort4* rect, uint32_t* tiles_touched, uint32_t* supers_touched, uint32_t* depth_key,
-                           uint32_t* ids);
+                           uint32_t* ids, unsigned long long* totals);
 
 // LSD radix sort of n keys (uint32 keys with uint32 values, or uint64 keys
 // alone) on bits [bit_lo, bit_hi).  Ping-pong buffers: the result lands in
@@ -124,9 +126,16 @@ cudaError_t launch_project(cudaStream_t s, const gs_gaussians& g, const CameraPa
 cudaError_t radix_sort_u32_pairs(cudaStream_t s, uint32_t* keys[2], uint32_t* vals[2], uint32_t n,
                                  int bit_lo, int bit_hi, uint32_t* hist, uint32_t* status,
                                  uint32_t* counters, int* err, int* out_idx);
+// hist_ready: hist already holds the exclusive digit histograms of every pass
+// (from launch_supers_to_hist), so the sort skips its histogram kernels.
 cudaError_t radix_sort_u64_keys(cudaStream_t s, uint64_t* keys[2], uint32_t n, int bit_lo, int bit_hi,
                                 uint32_t* hist, uint32_t* status, uint32_t* counters, int* err,
-                                int* out_idx);
+                                int* out_idx, bool hist_ready);
+// Largest super-tile count whose per-super-tile counts the emission kernel
+// accumulates in shared memory (and turns into histograms + ranges).
+constexpr int kMaxSupersForCounts = 4096;
+cudaError_t launch_supers_to_hist(cudaStream_t s, const uint32_t* counts, uint32_t Ts, int passes, uint32_t* hist,
+                                  uint2* ranges);
 size_t radix_status_words(uint32_t n, int bit_lo, int bit_hi);
 int radix_passes(int bit_lo, int bit_hi);
 
@@ -138,8 +147,10 @@ cudaError_t launch_scan_gathered(cudaStream_t s, const uint32_t* counts, const u
                                  unsigned long long* totals, int* err);
 size_t scan_partials_count(uint32_t n);
 
+// counts (may be NULL): per-super-tile pair counts accumulated while emitting
+// (zeroed by the caller; Ts <= kMaxSupersForCounts)
 cudaError_t launch_emit_pairs(cudaStream_t s, const uint32_t* ids, const uint32_t* offsets, const ushort4* rect,
-                              uint32_t n, int stiles_x, uint64_t* pairs);
+                              uint32_t n, int stiles_x, uint64_t* pairs, uint32_t* counts, uint32_t Ts);
 cudaError_t launch_ranges(cudaStream_t s, const uint64_t* pairs, uint32_t P, uint32_t T, uint2* ranges);
 // per-tile lists from the super-tile lists: counts, starts, ranges and (optionally) keys/vals
 cudaError_t launch_tile_lists(cudaStream_t s, const uint64_t* spairs, const uint2* sranges, const ushort4* rect,

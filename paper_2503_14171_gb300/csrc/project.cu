@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
     const float* __restrict__ rgb_in, CameraParams cam, int W, int H, int tiles_x, int tiles_y,
     int mode, Records rec, float* __restrict__ depth_out, int* __restrict__ radius_out,
     ushort4* __restrict__ rect_out, uint32_t* __restrict__ tiles_out, uint32_t* __restrict__ supers_out,
-    uint32_t* __restrict__ depth_key, uint32_t* __restrict__ ids)
+    uint32_t* __restrict__ depth_key, uint32_t* __restrict__ ids, unsigned long long* __restrict__ totals)
 {
     constexpr int KF = DEG >= 0 ? (DEG + 1) * (DEG + 1) * 3 : 1;   // floats per Gaussian
     constexpr int PITCH = KF | 1;
@@ -109,21 +109,23 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
         }
         __syncwarp();
     }
-    if (i >= n) return;
-    ids[i] = (uint32_t)i;
-    const float mx3 = means[3 * i], my3 = means[3 * i + 1], mz3 = means[3 * i + 2];
+    // every lane runs to the warp reduction below; the tail of the last warp
+    // reads a valid Gaussian and writes nothing
+    const bool inrange = i < n;
+    const int ii = inrange ? i : n - 1;
+    const float mx3 = means[3 * ii], my3 = means[3 * ii + 1], mz3 = means[3 * ii + 2];
     const float px = fmaf(cam.R[0], mx3, fmaf(cam.R[1], my3, fmaf(cam.R[2], mz3, cam.t[0])));
     const float py = fmaf(cam.R[3], mx3, fmaf(cam.R[4], my3, fmaf(cam.R[5], mz3, cam.t[1])));
     const float pz = fmaf(cam.R[6], mx3, fmaf(cam.R[7], my3, fmaf(cam.R[8], mz3, cam.t[2])));
 
-    bool vis = pz > cam.znear;
+    bool vis = inrange && pz > cam.znear;
     // 3D covariance Sigma = M M^T with M = R diag(s), R from the unit quaternion
-    float qw = quats[4 * i], qx = quats[4 * i + 1], qy = quats[4 * i + 2], qz = quats[4 * i + 3];
+    float qw = quats[4 * ii], qx = quats[4 * ii + 1], qy = quats[4 * ii + 2], qz = quats[4 * ii + 3];
     const float qn2 = qw * qw + qx * qx + qy * qy + qz * qz;
     vis = vis && qn2 > 0.f;
     const float qinv = rsqrtf(qn2);
     qw *= qinv; qx *= qinv; qy *= qinv; qz *= qinv;
-    const float s0 = expf(log_scales[3 * i]), s1 = expf(log_scales[3 * i + 1]), s2 = expf(log_scales[3 * i + 2]);
+    const float s0 = expf(log_scales[3 * ii]), s1 = expf(log_scales[3 * ii + 1]), s2 = expf(log_scales[3 * ii + 2]);
     const float R00 = 1.f - 2.f * (qy * qy + qz * qz), R01 = 2.f * (qx * qy - qw * qz), R02 = 2.f * (qx * qz + qw * qy);
     const float R10 = 2.f * (qx * qy + qw * qz), R11 = 1.f - 2.f * (qx * qx + qz * qz), R12 = 2.f * (qy * qz - qw * qx);
     const float R20 = 2.f * (qx * qz - qw * qy), R21 = 2.f * (qy * qz + qw * qx), R22 = 1.f - 2.f * (qx * qx + qy * qy);
@@ -173,7 +175,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
     const float m2y = fmaf(cam.fy, py * iz, cam.cy);
 
     vis = vis && isfinite(m2x) && isfinite(m2y) && isfinite(rad);
-    const float op = 1.f / (1.f + expf(-op_logits[i]));
+    const float op = 1.f / (1.f + expf(-op_logits[ii]));
     // alpha = sigma e^g >= 1/255 only inside d^T Sigma'^-1 d <= 2L, L = ln(255 sigma)
     const float L = logf(255.f * op);
     int4 rc = make_int4(0, 0, -1, -1);
@@ -200,8 +202,24 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
             }
         }
     }
+    const uint32_t nsup =
+        ntiles ? (uint32_t)((rc.z / kSuper - rc.x / kSuper + 1) * (rc.w / kSuper - rc.y / kSuper + 1)) : 0u;
+    // frame totals of (super-tile, Gaussian) and (tile, Gaussian) pairs: they do
+    // not depend on the depth order, so they are summed here (one atomic per warp)
+    unsigned long long wsum = nsup, wt = ntiles;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+        wt += __shfl_xor_sync(0xffffffffu, wt, o);
+    }
+    if (lane == 0 && (wsum | wt)) {
+        atomicAdd(&totals[0], wsum);
+        atomicAdd(&totals[1], wt);
+    }
+    if (!inrange) return;
+    ids[i] = (uint32_t)i;
     tiles_out[i] = ntiles;
-    supers_out[i] = ntiles ? (uint32_t)((rc.z / kSuper - rc.x / kSuper + 1) * (rc.w / kSuper - rc.y / kSuper + 1)) : 0u;
+    supers_out[i] = nsup;
     rect_out[i] = ntiles ? make_ushort4((unsigned short)rc.x, (unsigned short)rc.y, (unsigned short)rc.z,
                                         (unsigned short)rc.w)
                          : make_ushort4(1, 1, 0, 0);
@@ -258,7 +276,8 @@ __global__ void k_unpack(Records rec, const int* __restrict__ radius, const uint
 
 cudaError_t launch_project(cudaStream_t s, const gs_gaussians& g, const CameraParams& cam, int W, int H,
                            int tiles_x, int tiles_y, int mode, Records rec, float* depth, int* radius, ushort4* rect,
-                           uint32_t* tiles_touched, uint32_t* supers_touched, uint32_t* depth_key, uint32_t* ids)
+                           uint32_t* tiles_touched, uint32_t* supers_touched, uint32_t* depth_key, uint32_t* ids,
+                           unsigned long long* totals)
 {
     const int n = (int)g.n;
     if (n == 0) return cudaSuccess;
@@ -267,7 +286,7 @@ cudaError_t launch_project(cudaStream_t s, const gs_gaussians& g, const CameraPa
 #define GS_PROJECT(D)                                                                                              \
     k_project<D><<<blocks, kProjThreads, 0, s>>>(n, g.means, g.log_scales, g.quats, g.opacity_logits, g.sh, g.rgb, \
                                                  cam, W, H, tiles_x, tiles_y, mode, rec, depth, radius, rect,      \
-                                                 tiles_touched, supers_touched, depth_key, ids)
+                                                 tiles_touched, supers_touched, depth_key, ids, totals)
     switch (deg) {
     case 0: GS_PROJECT(0); break;
     case 1: GS_PROJECT(1); break;

@@ -17,7 +17,7 @@ constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kThreads = 256;              // one thread per digit in the digit phases
 constexpr int kWarps = kThreads / 32;
-constexpr int kItems = 16;                 // keys per thread
+constexpr int kItems = 8;                  // keys per thread
 constexpr int kTileKeys = kThreads * kItems;
 constexpr int kMaxPasses = 8;
 constexpr uint32_t kFlagAgg = 1u << 30;    // status word: 2-bit flag | 30-bit count
@@ -243,20 +243,23 @@ __global__ void __launch_bounds__(kThreads) k_onesweep(const K* __restrict__ key
 
 template <typename K, bool HAS_VAL>
 cudaError_t radix_sort_impl(cudaStream_t s, K* keys[2], uint32_t* vals[2], uint32_t n, int bit_lo, int bit_hi,
-                            uint32_t* hist, uint32_t* status, uint32_t* counters, int* err, int* out_idx)
+                            uint32_t* hist, uint32_t* status, uint32_t* counters, int* err, int* out_idx,
+                            bool hist_ready)
 {
     *out_idx = 0;
     if (n <= 1 || bit_hi <= bit_lo) return cudaSuccess;
     const int passes = (bit_hi - bit_lo + kRadixBits - 1) / kRadixBits;
     const uint32_t tiles = (n + kTileKeys - 1) / kTileKeys;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * passes * kRadix, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(status, 0, sizeof(uint32_t) * (size_t)passes * tiles * kRadix, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(counters, 0, sizeof(uint32_t) * passes, s)) != cudaSuccess) return e;
-    const uint32_t hb = (n + kThreads * 8 - 1) / (kThreads * 8);
-    const int hist_blocks = (int)(hb < 152u * 8u ? hb : 152u * 8u);
-    k_radix_hist<K><<<hist_blocks, kThreads, 0, s>>>(keys[0], n, bit_lo, passes, hist); note_launch();
-    k_radix_hist_scan<<<passes, kThreads, 0, s>>>(hist); note_launch();
+    if (!hist_ready) {
+        if ((e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * passes * kRadix, s)) != cudaSuccess) return e;
+        const uint32_t hb = (n + kThreads * 8 - 1) / (kThreads * 8);
+        const int hist_blocks = (int)(hb < 152u * 8u ? hb : 152u * 8u);
+        k_radix_hist<K><<<hist_blocks, kThreads, 0, s>>>(keys[0], n, bit_lo, passes, hist); note_launch();
+        k_radix_hist_scan<<<passes, kThreads, 0, s>>>(hist); note_launch();
+    }
     const size_t smem = sizeof(OnesweepSmem<K, HAS_VAL>);
     static bool attr_set = false;
     if (!attr_set) {
@@ -408,15 +411,82 @@ cudaError_t radix_sort_u32_pairs(cudaStream_t s, uint32_t* keys[2], uint32_t* va
                                  int bit_hi, uint32_t* hist, uint32_t* status, uint32_t* counters, int* err,
                                  int* out_idx)
 {
-    return radix_sort_impl<uint32_t, true>(s, keys, vals, n, bit_lo, bit_hi, hist, status, counters, err, out_idx);
+    return radix_sort_impl<uint32_t, true>(s, keys, vals, n, bit_lo, bit_hi, hist, status, counters, err, out_idx,
+                                           false);
 }
 
 cudaError_t radix_sort_u64_keys(cudaStream_t s, uint64_t* keys[2], uint32_t n, int bit_lo, int bit_hi,
-                                uint32_t* hist, uint32_t* status, uint32_t* counters, int* err, int* out_idx)
+                                uint32_t* hist, uint32_t* status, uint32_t* counters, int* err, int* out_idx,
+                                bool hist_ready)
 {
     uint32_t* no_vals[2] = {nullptr, nullptr};
     return radix_sort_impl<uint64_t, false>(s, keys, no_vals, n, bit_lo, bit_hi, hist, status, counters, err,
-                                            out_idx);
+                                            out_idx, hist_ready);
+}
+
+// Per-super-tile counts -> (a) the exclusive digit histograms of every radix
+// pass over the super-tile bits (bits [32, 32 + 8 passes) of the pair keys) and
+// (b) the [start, end) range of every super-tile's run in the sorted list.
+// One block; Ts <= kMaxSupersForCounts.
+__global__ void __launch_bounds__(kThreads) k_supers_to_hist(const uint32_t* __restrict__ counts, uint32_t Ts,
+                                                             int passes, uint32_t* __restrict__ hist,
+                                                             uint2* __restrict__ ranges)
+{
+    __shared__ uint32_t s_hist[kHistPasses][kRadix];
+    __shared__ uint32_t s_warp[kWarps];
+    for (int i = threadIdx.x; i < kHistPasses * kRadix; i += kThreads) (&s_hist[0][0])[i] = 0;
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < Ts; t += kThreads) {
+        const uint32_t c = counts[t];
+        for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p][(t >> (p * kRadixBits)) & (kRadix - 1)], c);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int p = 0; p < passes; ++p) {
+        const uint32_t v = s_hist[p][threadIdx.x];
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        uint32_t b = 0;
+        for (int w = 0; w < warp; ++w) b += s_warp[w];
+        hist[p * kRadix + threadIdx.x] = b + x - v;
+        __syncthreads();
+    }
+    // ranges: exclusive scan of the counts in super-tile order
+    uint32_t carry = 0;
+    for (uint32_t t0 = 0; t0 < Ts; t0 += kThreads) {
+        const uint32_t t = t0 + threadIdx.x;
+        const uint32_t v = t < Ts ? counts[t] : 0u;
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        uint32_t b = 0, tot = 0;
+        for (int w = 0; w < kWarps; ++w) {
+            b += w < warp ? s_warp[w] : 0u;
+            tot += s_warp[w];
+        }
+        if (t < Ts) {
+            const uint32_t st = carry + b + x - v;
+            ranges[t] = v ? make_uint2(st, st + v) : make_uint2(0u, 0u);
+        }
+        carry += tot;
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_supers_to_hist(cudaStream_t s, const uint32_t* counts, uint32_t Ts, int passes, uint32_t* hist,
+                                  uint2* ranges)
+{
+    k_supers_to_hist<<<1, kThreads, 0, s>>>(counts, Ts, passes, hist, ranges); note_launch();
+    return cudaGetLastError();
 }
 
 size_t scan_partials_count(uint32_t n)
