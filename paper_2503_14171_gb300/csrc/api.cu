@@ -175,8 +175,8 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
         (st = ensure(c, c->did[0], sizeof(uint32_t) * n)) || (st = ensure(c, c->did[1], sizeof(uint32_t) * n)) ||
         (st = ensure(c, c->offsets, sizeof(uint32_t) * (n + 1))) ||
         (st = ensure(c, c->scan_partials, sizeof(unsigned long long) * scan_partials_count(n))) ||
-        (st = ensure(c, c->scan_totals, 6 * sizeof(unsigned long long))) ||
-        (st = ensure(c, c->super_counts, sizeof(uint32_t) * Ts)) ||
+        (st = ensure(c, c->scan_totals, (2 * kTotalSlots + 4) * sizeof(unsigned long long))) ||
+        (st = ensure(c, c->super_counts, sizeof(uint32_t) * kCountCopies * Ts)) ||
         (st = ensure(c, c->sranges, sizeof(uint2) * Ts)) || (st = ensure(c, c->sort_hist, sizeof(uint32_t) * 8 * 256)) ||
         (st = ensure(c, c->sort_status, sizeof(uint32_t) * radix_status_words(n, 0, 32))) ||
         (st = ensure(c, c->sort_counter, sizeof(uint32_t) * 8)))
@@ -184,16 +184,18 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
 
     const Records rec{as<float4>(c->rec0), as<float4>(c->rec1), as<float4>(c->rec2)};
     const CameraParams cp = make_camera(*cam, W, H);
-    // scan_totals: [0] super-tile pairs, [1] tile pairs (from the projection),
-    // [2..3] scan totals, [4] scan tile counter
+    // scan_totals: [0, 2 kTotalSlots) slot pairs (super-tile pairs, tile pairs)
+    // from the projection, then 2 scan totals and the scan tile counter
     unsigned long long* totals = as<unsigned long long>(c->scan_totals);
-    GS_CUDA(c, cudaMemsetAsync(totals, 0, 2 * sizeof(unsigned long long), c->stream));
+    unsigned long long* scan_tot = totals + 2 * kTotalSlots;
+    GS_CUDA(c, cudaMemsetAsync(totals, 0, 2 * kTotalSlots * sizeof(unsigned long long), c->stream));
     GS_CUDA(c, launch_project(c->stream, *g, cp, W, H, tiles_x, tiles_y, c->opt.mode, rec, as<float>(c->depth),
                               as<int>(c->radius), as<ushort4>(c->rect), as<uint32_t>(c->tiles_touched),
                               as<uint32_t>(c->supers_touched), as<uint32_t>(c->dkey[0]), as<uint32_t>(c->did[0]),
                               totals));
     // the pair totals travel to the host while the depth sort runs
-    GS_CUDA(c, cudaMemcpyAsync(c->h_scalar, totals, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+    GS_CUDA(c, cudaMemcpyAsync(c->h_scalar, totals, 2 * kTotalSlots * sizeof(unsigned long long),
+                               cudaMemcpyDeviceToHost, c->stream));
     GS_CUDA(c, cudaEventRecord(c->totals_ready, c->stream));
 
     // depth order: stable radix sort of the FP32 depth bits (ids ascending)
@@ -211,10 +213,14 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
     // super-tile pair offsets in depth order
     GS_CUDA(c, launch_scan_gathered(c->stream, as<uint32_t>(c->supers_touched), nullptr, ids, n,
                                     as<uint32_t>(c->offsets), as<unsigned long long>(c->scan_partials),
-                                    reinterpret_cast<uint32_t*>(totals + 4), totals + 2, as<int>(c->errword)));
+                                    reinterpret_cast<uint32_t*>(scan_tot + 2), scan_tot, as<int>(c->errword)));
 
     GS_CUDA(c, cudaEventSynchronize(c->totals_ready));
-    const unsigned long long Ps64 = c->h_scalar[0], P64 = c->h_scalar[1];
+    unsigned long long Ps64 = 0, P64 = 0;
+    for (int k = 0; k < kTotalSlots; ++k) {
+        Ps64 += c->h_scalar[2 * k];
+        P64 += c->h_scalar[2 * k + 1];
+    }
     const int64_t limit = c->opt.max_pairs > 0 ? std::min<int64_t>(c->opt.max_pairs, kMaxPairs) : kMaxPairs;
     if ((int64_t)P64 > limit)
         return fail(c, GS_ERR_CAPACITY, "pair count %llu exceeds the limit %lld", P64, (long long)limit);
@@ -231,7 +237,7 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
         return st;
     uint64_t* pairs[2] = {as<uint64_t>(c->pairs[0]), as<uint64_t>(c->pairs[1])};
     const bool counted = Ts <= kMaxSupersForCounts;
-    if (counted) GS_CUDA(c, cudaMemsetAsync(c->super_counts.p, 0, sizeof(uint32_t) * Ts, c->stream));
+    if (counted) GS_CUDA(c, cudaMemsetAsync(c->super_counts.p, 0, sizeof(uint32_t) * kCountCopies * Ts, c->stream));
     GS_CUDA(c, launch_emit_pairs(c->stream, ids, as<uint32_t>(c->offsets), as<ushort4>(c->rect), n, stiles_x, pairs[0],
                                  counted ? as<uint32_t>(c->super_counts) : nullptr, (uint32_t)Ts));
     int psorted = 0;
@@ -343,7 +349,7 @@ gs_status gs_create(gs_ctx** out, void* stream, const gs_options* opt)
         delete c;
         return GS_ERR_CUDA;
     }
-    if (cudaMallocHost((void**)&c->h_scalar, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+    if (cudaMallocHost((void**)&c->h_scalar, 2 * kTotalSlots * sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return GS_ERR_OOM;

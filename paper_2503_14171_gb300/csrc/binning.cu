@@ -47,9 +47,10 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ ids, 
     }
     if (COUNT) {
         __syncthreads();
+        uint32_t* dst = counts + (size_t)(blockIdx.x % kCountCopies) * Ts;
         for (uint32_t t = threadIdx.x; t < Ts; t += blockDim.x) {
             const uint32_t v = s_cnt[t];
-            if (v) atomicAdd(&counts[t], v);
+            if (v) atomicAdd(&dst[t], v);
         }
     }
 }

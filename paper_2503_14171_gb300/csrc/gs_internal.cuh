@@ -17,6 +17,13 @@ constexpr int kDevOk = 0;
 constexpr int kDevTimeout = 1;
 constexpr int kDevCheck = 2;
 
+// The projection sums the frame's pair totals into kTotalSlots slot pairs
+// (super-tile pairs, tile pairs) to spread its atomics; the host adds the slots.
+constexpr int kTotalSlots = 32;
+// Copies of the per-super-tile count array the emission kernel spreads its
+// atomics over (summed by launch_supers_to_hist).
+constexpr int kCountCopies = 32;
+
 // Largest pair count the 30-bit look-back counters of the radix sort can hold.
 constexpr int64_t kMaxPairs = (int64_t(1) << 30) - 1;
 
@@ -134,7 +141,7 @@ cudaError_t radix_sort_u64_keys(cudaStream_t s, uint64_t* keys[2], uint32_t n, i
 // Largest super-tile count whose per-super-tile counts the emission kernel
 // accumulates in shared memory (and turns into histograms + ranges).
 constexpr int kMaxSupersForCounts = 4096;
-cudaError_t launch_supers_to_hist(cudaStream_t s, const uint32_t* counts, uint32_t Ts, int passes, uint32_t* hist,
+cudaError_t launch_supers_to_hist(cudaStream_t s, uint32_t* counts, uint32_t Ts, int passes, uint32_t* hist,
                                   uint2* ranges);
 size_t radix_status_words(uint32_t n, int bit_lo, int bit_hi);
 int radix_passes(int bit_lo, int bit_hi);
@@ -147,8 +154,8 @@ cudaError_t launch_scan_gathered(cudaStream_t s, const uint32_t* counts, const u
                                  unsigned long long* totals, int* err);
 size_t scan_partials_count(uint32_t n);
 
-// counts (may be NULL): per-super-tile pair counts accumulated while emitting
-// (zeroed by the caller; Ts <= kMaxSupersForCounts)
+// counts (may be NULL): kCountCopies x Ts per-super-tile pair counts accumulated
+// while emitting (zeroed by the caller; Ts <= kMaxSupersForCounts)
 cudaError_t launch_emit_pairs(cudaStream_t s, const uint32_t* ids, const uint32_t* offsets, const ushort4* rect,
                               uint32_t n, int stiles_x, uint64_t* pairs, uint32_t* counts, uint32_t Ts);
 cudaError_t launch_ranges(cudaStream_t s, const uint64_t* pairs, uint32_t P, uint32_t T, uint2* ranges);

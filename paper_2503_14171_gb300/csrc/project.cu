@@ -205,16 +205,25 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
     const uint32_t nsup =
         ntiles ? (uint32_t)((rc.z / kSuper - rc.x / kSuper + 1) * (rc.w / kSuper - rc.y / kSuper + 1)) : 0u;
     // frame totals of (super-tile, Gaussian) and (tile, Gaussian) pairs: they do
-    // not depend on the depth order, so they are summed here (one atomic per warp)
+    // not depend on the depth order, so they are summed here -- per block, then
+    // into one of kTotalSlots slot pairs (spreading the atomics), summed on the host
+    __shared__ unsigned long long s_tot[2][kProjThreads / 32];
     unsigned long long wsum = nsup, wt = ntiles;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
         wt += __shfl_xor_sync(0xffffffffu, wt, o);
     }
-    if (lane == 0 && (wsum | wt)) {
-        atomicAdd(&totals[0], wsum);
-        atomicAdd(&totals[1], wt);
+    if (lane == 0) {
+        s_tot[0][warp] = wsum;
+        s_tot[1][warp] = wt;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        unsigned long long b = 0;
+#pragma unroll
+        for (int w = 0; w < kProjThreads / 32; ++w) b += s_tot[threadIdx.x][w];
+        if (b) atomicAdd(&totals[2 * (blockIdx.x % kTotalSlots) + threadIdx.x], b);
     }
     if (!inrange) return;
     ids[i] = (uint32_t)i;

@@ -428,7 +428,7 @@ cudaError_t radix_sort_u64_keys(cudaStream_t s, uint64_t* keys[2], uint32_t n, i
 // pass over the super-tile bits (bits [32, 32 + 8 passes) of the pair keys) and
 // (b) the [start, end) range of every super-tile's run in the sorted list.
 // One block; Ts <= kMaxSupersForCounts.
-__global__ void __launch_bounds__(kThreads) k_supers_to_hist(const uint32_t* __restrict__ counts, uint32_t Ts,
+__global__ void __launch_bounds__(kThreads) k_supers_to_hist(uint32_t* __restrict__ counts, uint32_t Ts,
                                                              int passes, uint32_t* __restrict__ hist,
                                                              uint2* __restrict__ ranges)
 {
@@ -436,10 +436,14 @@ __global__ void __launch_bounds__(kThreads) k_supers_to_hist(const uint32_t* __r
     __shared__ uint32_t s_warp[kWarps];
     for (int i = threadIdx.x; i < kHistPasses * kRadix; i += kThreads) (&s_hist[0][0])[i] = 0;
     __syncthreads();
+    // the counts arrive as kCountCopies partial arrays; fold them into copy 0
     for (uint32_t t = threadIdx.x; t < Ts; t += kThreads) {
-        const uint32_t c = counts[t];
+        uint32_t c = 0;
+        for (int k = 0; k < kCountCopies; ++k) c += counts[(size_t)k * Ts + t];
+        counts[t] = c;
         for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p][(t >> (p * kRadixBits)) & (kRadix - 1)], c);
     }
+    __syncthreads();
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int p = 0; p < passes; ++p) {
@@ -482,7 +486,7 @@ __global__ void __launch_bounds__(kThreads) k_supers_to_hist(const uint32_t* __r
     }
 }
 
-cudaError_t launch_supers_to_hist(cudaStream_t s, const uint32_t* counts, uint32_t Ts, int passes, uint32_t* hist,
+cudaError_t launch_supers_to_hist(cudaStream_t s, uint32_t* counts, uint32_t Ts, int passes, uint32_t* hist,
                                   uint2* ranges)
 {
     k_supers_to_hist<<<1, kThreads, 0, s>>>(counts, Ts, passes, hist, ranges); note_launch();
