@@ -2,11 +2,9 @@
 // derivatives of the pixel colour (Sec. 4 blend equation; Sec. 5 "3DGS Image
 // Gradients"; supplement "Forward pass").
 //
-// One 128-thread block per 16x16 tile; each thread owns the two pixels
-// (x, y) and (x, y + 8) of one column, so the terms of the exponent that
-// depend only on x - mu_x, the shared-memory reads and the loop overhead are
-// shared by two pixels.  Binning is done per 64x64 super-tile (4x4 tiles): the
-// block walks its super-tile's depth-ordered list 256 candidates at a time,
+// One 256-thread block per 16x16 tile, one pixel per thread.  Binning is done
+// per 64x64 super-tile (4x4 tiles): the block walks its super-tile's
+// depth-ordered list 256 candidates at a time,
 // keeps the Gaussians whose tile rect covers this tile (an order-preserving
 // block compaction, so the kept sequence is exactly the tile's own
 // front-to-back list) and stages their records in shared memory until at
@@ -34,9 +32,9 @@
 namespace gs {
 namespace {
 
-constexpr int kThreads = 128;            // 16 columns x 8 rows, 2 pixels per thread
+constexpr int kThreads = kTilePixels;    // one pixel per thread
 constexpr int kWarps = kThreads / 32;
-constexpr int kCand = 2 * kThreads;      // candidates examined per compaction round
+constexpr int kCand = kThreads;          // candidates examined per compaction round
 constexpr int kStage = 2 * kCand;        // staged records per batch (>= kCand before blending)
 constexpr float kLn2 = 0.69314718055994531f;
 
@@ -142,105 +140,76 @@ __global__ void __launch_bounds__(kThreads) k_blend(BlendArgs a, unsigned long l
     __shared__ float4 s_r0[kStage];
     __shared__ float4 s_r1[kStage];
     __shared__ float4 s_r2[kStage];
-    __shared__ int s_wcnt[2 * kWarps];
+    __shared__ int s_wcnt[kWarps];
 
     const int tile = blockIdx.x;
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;   // ly in [0, 8)
-    const int x = tx * kTile + lx, y0 = ty * kTile + ly, y1 = y0 + 8;
-    const float px = (float)x, py0 = (float)y0;
+    const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
+    const int x = tx * kTile + lx, y = ty * kTile + ly;
+    const float px = (float)x, py = (float)y;
     const uint32_t lanemask_lt = (1u << lane) - 1u;
 
     const int S = (ty / kSuper) * a.stiles_x + (tx / kSuper);
     const uint2 sr = a.sranges[S];
     const int total = (int)(sr.y - sr.x);
 
-    PixelState p0, p1;
-    init(p0, x < a.W && y0 < a.H);
-    init(p1, x < a.W && y1 < a.H);
+    PixelState p;
+    init(p, x < a.W && y < a.H);
     uint32_t n_eval = 0, n_acc = 0;
     int list_base = 0;   // position of the batch's first record in the tile's list
 
-    // candidates of the first round: this thread holds positions tid and tid + 128
-    uint32_t cid[2];
-    ushort4 crect[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int c = h * kThreads + (int)threadIdx.x;
-        cid[h] = 0xFFFFFFFFu;
-        crect[h] = make_ushort4(1, 1, 0, 0);
-        if (c < total) {
-            cid[h] = a.pair_words[2 * (size_t)(sr.x + c)];
-            if (cid[h] < a.n) crect[h] = a.rect[cid[h]];
-        }
+    // candidate of the first round
+    uint32_t cid = 0xFFFFFFFFu;
+    ushort4 crect = make_ushort4(1, 1, 0, 0);
+    if ((int)threadIdx.x < total) {
+        cid = a.pair_words[2 * (size_t)(sr.x + threadIdx.x)];
+        if (cid < a.n) crect = a.rect[cid];
     }
 
     int c0 = 0;
     while (c0 < total) {
-        if (__syncthreads_count(p0.done && p1.done) == kThreads) break;
+        if (__syncthreads_count(p.done) == kThreads) break;
         // stage rounds of kCand candidates until >= kCand records are staged
         int staged = 0;
         while (c0 < total && staged < kCand) {
-            bool hit[2];
-            uint32_t ball[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                hit[h] = cid[h] < a.n && covers(crect[h], tx, ty);
-                ball[h] = __ballot_sync(0xffffffffu, hit[h]);
-                if (lane == 0) s_wcnt[h * kWarps + warp] = __popc(ball[h]);
-            }
+            const bool hit = cid < a.n && covers(crect, tx, ty);
+            const uint32_t ball = __ballot_sync(0xffffffffu, hit);
+            if (lane == 0) s_wcnt[warp] = __popc(ball);
             __syncthreads();
-            // candidate order: first half (positions tid) then second half (tid + 128)
-            int base0 = 0, tot0 = 0, base1 = 0, tot1 = 0;
+            int wbase = 0, tot = 0;
 #pragma unroll
             for (int w = 0; w < kWarps; ++w) {
-                const int a0 = s_wcnt[w], a1 = s_wcnt[kWarps + w];
-                base0 += w < warp ? a0 : 0;
-                base1 += w < warp ? a1 : 0;
-                tot0 += a0;
-                tot1 += a1;
+                const int cw = s_wcnt[w];
+                wbase += w < warp ? cw : 0;
+                tot += cw;
             }
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                if (hit[h]) {
-                    const int pos = staged + (h ? tot0 + base1 : base0) + __popc(ball[h] & lanemask_lt);
-                    s_r0[pos] = a.rec.r0[cid[h]];
-                    s_r1[pos] = a.rec.r1[cid[h]];
-                    s_r2[pos] = a.rec.r2[cid[h]];
-                }
+            if (hit) {
+                const int pos = staged + wbase + __popc(ball & lanemask_lt);
+                s_r0[pos] = a.rec.r0[cid];
+                s_r1[pos] = a.rec.r1[cid];
+                s_r2[pos] = a.rec.r2[cid];
             }
-            staged += tot0 + tot1;
+            staged += tot;
             c0 += kCand;
-            // fetch the next round's candidates
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int c = c0 + h * kThreads + (int)threadIdx.x;
-                cid[h] = 0xFFFFFFFFu;
-                if (c < total) {
-                    cid[h] = a.pair_words[2 * (size_t)(sr.x + c)];
-                    if (cid[h] < a.n) crect[h] = a.rect[cid[h]];
-                }
+            // fetch the next round's candidate
+            const int cn = c0 + (int)threadIdx.x;
+            cid = 0xFFFFFFFFu;
+            if (cn < total) {
+                cid = a.pair_words[2 * (size_t)(sr.x + cn)];
+                if (cid < a.n) crect = a.rect[cid];
             }
-            __syncthreads();   // s_wcnt is reused by the next round
+            __syncthreads();   // s_wcnt is reused by the next round; staged records are visible
         }
-        for (int k = 0; k < staged && !(p0.done && p1.done); ++k) {
+        for (int k = 0; k < staged && !p.done; ++k) {
             const float4 r0 = s_r0[k];
             const float4 r1 = s_r1[k];
-            const float dx = px - r0.x;
-            const float dy0 = py0 - r0.y, dy1 = dy0 + 8.f;
-            const float ax = r1.x * dx * dx;                 // A2 dx^2, shared by both pixels
-            const float bx = r1.y * dx;                      // B2 dx
-            const float g20 = fmaf(dy0, fmaf(r1.z, dy0, bx), ax);
-            const float g21 = fmaf(dy1, fmaf(r1.z, dy1, bx), ax);
-            const bool live0 = !p0.done && !(MODE == GS_MODE_3DGS && g20 < r1.w);
-            const bool live1 = !p1.done && !(MODE == GS_MODE_3DGS && g21 < r1.w);
-            if (STATS) n_eval += (p0.done ? 0u : 1u) + (p1.done ? 0u : 1u);
-            if (live0 || live1) {
-                const float4 c = s_r2[k];
-                if (live0 && blend_pair<GRADS, MODE>(p0, g20, dx, dy0, r0, r1, c, list_base + k)) ++n_acc;
-                if (live1 && blend_pair<GRADS, MODE>(p1, g21, dx, dy1, r0, r1, c, list_base + k)) ++n_acc;
-            }
+            const float dx = px - r0.x, dy = py - r0.y;
+            if (STATS) ++n_eval;
+            const float g2 = fmaf(dx, fmaf(r1.x, dx, r1.y * dy), r1.z * dy * dy);
+            if (MODE == GS_MODE_3DGS && g2 < r1.w) continue;
+            const float4 c = s_r2[k];
+            if (blend_pair<GRADS, MODE>(p, g2, dx, dy, r0, r1, c, list_base + k) && STATS) ++n_acc;
         }
         list_base += staged;
     }
@@ -257,9 +226,7 @@ __global__ void __launch_bounds__(kThreads) k_blend(BlendArgs a, unsigned long l
         }
         return;
     }
-    if (x >= a.W) return;
-    if (y0 < a.H) store<GRADS>(a, p0, x, y0);
-    if (y1 < a.H) store<GRADS>(a, p1, x, y1);
+    if (x < a.W && y < a.H) store<GRADS>(a, p, x, y);
 }
 
 template <bool GRADS, int MODE>
