@@ -90,6 +90,8 @@ T* as(DevBuf& b)
     return reinterpret_cast<T*>(b.p);
 }
 
+constexpr size_t kRadixDigits = 256;
+
 int bits_for(uint32_t v)   // number of bits to represent values < v (v >= 1)
 {
     int b = 0;
@@ -198,22 +200,36 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
                                cudaMemcpyDeviceToHost, c->stream));
     GS_CUDA(c, cudaEventRecord(c->totals_ready, c->stream));
 
-    // depth order: stable radix sort of the FP32 depth bits (ids ascending)
+    // depth order (stable radix sort of the FP32 depth bits, ids ascending) and
+    // the super-tile pair offsets in that order
     int sorted = 0;
-    if (n > 1) {
+    const uint32_t ds_cap = n > 1 ? depth_sort_capacity(c->device) : 0u;
+    if (n > 1 && n <= ds_cap) {
+        const size_t G = ds_cap / kDsMaxSlice;
+        if ((st = ensure(c, c->ds_scratch, G * kRadixDigits * 4 + G * 8 + 64))) return st;
+        unsigned char* base = as<unsigned char>(c->ds_scratch);
         uint32_t* keys[2] = {as<uint32_t>(c->dkey[0]), as<uint32_t>(c->dkey[1])};
         uint32_t* vals[2] = {as<uint32_t>(c->did[0]), as<uint32_t>(c->did[1])};
-        GS_CUDA(c, radix_sort_u32_pairs(c->stream, keys, vals, n, 0, 32, as<uint32_t>(c->sort_hist),
-                                        as<uint32_t>(c->sort_status), as<uint32_t>(c->sort_counter),
-                                        as<int>(c->errword), &sorted));
+        GS_CUDA(c, launch_depth_sort_scan(c->stream, c->device, keys[0], keys, vals, as<uint32_t>(c->supers_touched), n,
+                                          as<uint32_t>(c->offsets), reinterpret_cast<uint32_t*>(base),
+                                          reinterpret_cast<unsigned long long*>(base + G * kRadixDigits * 4),
+                                          reinterpret_cast<unsigned int*>(base + G * kRadixDigits * 4 + G * 8),
+                                          as<int>(c->errword), &sorted));
+    } else {
+        if (n > 1) {
+            uint32_t* keys[2] = {as<uint32_t>(c->dkey[0]), as<uint32_t>(c->dkey[1])};
+            uint32_t* vals[2] = {as<uint32_t>(c->did[0]), as<uint32_t>(c->did[1])};
+            GS_CUDA(c, radix_sort_u32_pairs(c->stream, keys, vals, n, 0, 32, as<uint32_t>(c->sort_hist),
+                                            as<uint32_t>(c->sort_status), as<uint32_t>(c->sort_counter),
+                                            as<int>(c->errword), &sorted));
+        }
+        GS_CUDA(c, launch_scan_gathered(c->stream, as<uint32_t>(c->supers_touched), nullptr,
+                                        as<uint32_t>(c->did[sorted]), n, as<uint32_t>(c->offsets),
+                                        as<unsigned long long>(c->scan_partials),
+                                        reinterpret_cast<uint32_t*>(scan_tot + 2), scan_tot, as<int>(c->errword)));
     }
     c->sorted_ids_buf = sorted;
     const uint32_t* ids = as<uint32_t>(c->did[sorted]);
-
-    // super-tile pair offsets in depth order
-    GS_CUDA(c, launch_scan_gathered(c->stream, as<uint32_t>(c->supers_touched), nullptr, ids, n,
-                                    as<uint32_t>(c->offsets), as<unsigned long long>(c->scan_partials),
-                                    reinterpret_cast<uint32_t*>(scan_tot + 2), scan_tot, as<int>(c->errword)));
 
     GS_CUDA(c, cudaEventSynchronize(c->totals_ready));
     unsigned long long Ps64 = 0, P64 = 0;
@@ -383,7 +399,8 @@ gs_status gs_destroy(gs_ctx* c)
     cudaStreamSynchronize(c->stream);
     DevBuf* bufs[] = {&c->rec0, &c->rec1, &c->rec2, &c->depth, &c->radius, &c->rect, &c->tiles_touched,
                       &c->supers_touched, &c->dkey[0], &c->dkey[1], &c->did[0], &c->did[1], &c->offsets,
-                      &c->scan_partials, &c->scan_totals, &c->super_counts, &c->pairs[0], &c->pairs[1],
+                      &c->scan_partials, &c->scan_totals, &c->super_counts, &c->ds_scratch, &c->pairs[0],
+                      &c->pairs[1],
                       &c->sort_hist, &c->sort_status,
                       &c->sort_counter, &c->sranges, &c->tile_count, &c->tile_start, &c->state, &c->count,
                       &c->errword};

@@ -1,0 +1,286 @@
+// Front-to-back order of the Gaussians (Sec. 4: Gaussians are blended sorted
+// by depth) and the pair offsets in that order, in one persistent launch.
+//
+// For up to kDsMaxSlice Gaussians per SM the whole sort runs as a single
+// cooperative kernel, one 1024-thread block per SM, each block owning a
+// contiguous slice of the sequence:
+//   4 stable LSD passes over the 8-bit digits of the FP32 depth bits (ids in
+//   ascending order ride along): load the slice, rank it by digit with one
+//   ballot per digit bit and per-warp running counters (stable), publish the
+//   block's digit counts, grid barrier, derive the global digit offsets from
+//   all blocks' counts, scatter, grid barrier;
+//   then the exclusive scan of supers_touched[id] in the sorted order (block
+//   sums, grid barrier, block prefixes), which gives each Gaussian's first
+//   pair slot.
+// This replaces a histogram kernel, four one-sweep passes and a scan kernel
+// (seven launches whose time is dominated by latency at this size) with one.
+//
+// Grid barriers spin at most kGridSpinLimit times; on expiry the block records
+// kDevTimeout in the error word and carries on (outputs undefined, no hang).
+#include <cooperative_groups.h>
+
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+constexpr int kDsThreads = 1024;
+constexpr int kDsWarps = kDsThreads / 32;
+constexpr int kDsRadix = 256;
+constexpr int kDsPasses = 4;
+constexpr long kGridSpinLimit = 1L << 22;
+
+struct DsArgs {
+    const uint32_t* keys_in;     // [n] depth keys in id order
+    uint32_t* keys[2];           // ping-pong
+    uint32_t* ids[2];
+    const uint32_t* counts;      // [n] pair count per Gaussian (by id)
+    uint32_t* offsets;           // [n + 1] exclusive scan in depth order
+    uint32_t* cnt;               // [grid][256] per-block digit counts
+    unsigned long long* bsum;    // [grid] per-block count sums
+    unsigned int* bar;           // [2] barrier counter and generation (zeroed)
+    int* err;
+    uint32_t n;
+};
+
+// Grid-wide barrier for a cooperative launch (all blocks resident).
+__device__ __forceinline__ void grid_barrier(unsigned int* bar, int* err)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int* vgen = bar + 1;
+        const unsigned int gen = *vgen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(bar, 1u);
+        if (arrived == gridDim.x - 1) {
+            bar[0] = 0u;
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long spins = 0;
+            while (*vgen == gen) {
+                if (++spins > kGridSpinLimit) {
+                    atomicExch(err, kDevTimeout);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t n = a.n;
+    const uint32_t G = gridDim.x;
+    const uint32_t slice = (n + G - 1) / G;
+    const uint32_t lo = blockIdx.x * slice;
+    const uint32_t hi = min(n, lo + slice);
+    const uint32_t m = hi > lo ? hi - lo : 0u;
+    const uint32_t cw = (m + kDsWarps - 1) / kDsWarps;   // elements per warp chunk
+
+    uint32_t* s_key = reinterpret_cast<uint32_t*>(smem);
+    uint32_t* s_id = s_key + kDsMaxSlice;
+    uint16_t* s_rank = reinterpret_cast<uint16_t*>(s_id + kDsMaxSlice);
+    uint16_t* s_wcnt = s_rank + kDsMaxSlice;                          // [kDsWarps][256]
+    uint32_t* s_off = reinterpret_cast<uint32_t*>(s_wcnt + kDsWarps * kDsRadix);   // [256]
+    uint32_t* s_wtot = s_off + kDsRadix;                              // [kDsWarps]
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+
+    for (int pass = 0; pass < kDsPasses; ++pass) {
+        const int shift = pass * 8;
+        const uint32_t* src_key = pass == 0 ? a.keys_in : a.keys[(pass - 1) & 1];
+        const uint32_t* src_id = pass == 0 ? nullptr : a.ids[(pass - 1) & 1];
+        uint32_t* dst_key = a.keys[pass & 1];
+        uint32_t* dst_id = a.ids[pass & 1];
+        for (int i = tid; i < kDsWarps * kDsRadix; i += kDsThreads) s_wcnt[i] = 0;
+        __syncthreads();
+        // stable ranking: warp w ranks its chunk [w cw, (w+1) cw) 32 elements at a time
+        const uint32_t wlo = warp * cw, whi = min(m, wlo + cw);
+        for (uint32_t base = wlo; base < whi; base += 32) {
+            const uint32_t j = base + lane;
+            const bool valid = j < whi;
+            uint32_t key = 0, id = 0, d = 0;
+            if (valid) {
+                key = src_key[lo + j];
+                id = pass == 0 ? lo + j : src_id[lo + j];
+                d = (key >> shift) & 0xFFu;
+            }
+            uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const bool bit = (d >> b) & 1u;
+                const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+                peers &= bit ? bal : ~bal;
+            }
+            uint32_t prev = 0;
+            if (valid) prev = s_wcnt[warp * kDsRadix + d];
+            __syncwarp();
+            if (valid) {
+                s_key[j] = key;
+                s_id[j] = id;
+                s_rank[j] = (uint16_t)(prev + __popc(peers & lt));
+                if (lane == 31 - __clz(peers)) s_wcnt[warp * kDsRadix + d] = (uint16_t)(prev + __popc(peers));
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+        // per digit: exclusive prefix over warps, and the block's count
+        if (tid < kDsRadix) {
+            uint32_t run = 0;
+            for (int w = 0; w < kDsWarps; ++w) {
+                const uint32_t c = s_wcnt[w * kDsRadix + tid];
+                s_wcnt[w * kDsRadix + tid] = (uint16_t)run;
+                run += c;
+            }
+            a.cnt[(size_t)blockIdx.x * kDsRadix + tid] = run;
+        }
+        grid_barrier(a.bar, a.err);
+        // global offset of this block's first element of each digit
+        if (tid < kDsRadix) {
+            uint32_t tot = 0, pre = 0;
+            for (uint32_t b = 0; b < G; ++b) {
+                const uint32_t c = *(volatile const uint32_t*)(a.cnt + (size_t)b * kDsRadix + tid);
+                tot += c;
+                pre += b < blockIdx.x ? c : 0u;
+            }
+            // exclusive scan of the digit totals (8 warps)
+            uint32_t x = tot;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31) s_wtot[warp] = x;
+            s_off[tid] = pre + x - tot;   // completed below with the earlier warps' totals
+        }
+        __syncthreads();
+        if (tid < kDsRadix) {
+            uint32_t wb = 0;
+            for (int w = 0; w < warp; ++w) wb += s_wtot[w];
+            s_off[tid] += wb;
+        }
+        __syncthreads();
+        // scatter
+        for (uint32_t j = tid; j < m; j += kDsThreads) {
+            const uint32_t key = s_key[j];
+            const uint32_t d = (key >> shift) & 0xFFu;
+            const uint32_t w = j / cw;
+            const uint32_t pos = s_off[d] + s_wcnt[w * kDsRadix + d] + s_rank[j];
+            if (pos < n) {
+                if (pass + 1 < kDsPasses) dst_key[pos] = key;
+                dst_id[pos] = s_id[j];
+            }
+        }
+        grid_barrier(a.bar, a.err);
+    }
+
+    // exclusive scan of counts[id] over the sorted slice: thread t owns a
+    // contiguous run of E = ceil(m / 1024) positions
+    const uint32_t* sorted = a.ids[(kDsPasses - 1) & 1];
+    const uint32_t E = (m + kDsThreads - 1) / kDsThreads;
+    const uint32_t t0 = min(m, tid * E), t1 = min(m, t0 + E);
+    unsigned long long sum = 0;
+    for (uint32_t j = t0; j < t1; ++j) {
+        const uint32_t id = sorted[lo + j];
+        sum += id < n ? a.counts[id] : 0u;
+    }
+    unsigned long long x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    unsigned long long* s_w64 = reinterpret_cast<unsigned long long*>(s_key);   // reuse: [kDsWarps]
+    if (lane == 31) s_w64[warp] = x;
+    __syncthreads();
+    unsigned long long wb = 0, btot = 0;
+    for (int w = 0; w < kDsWarps; ++w) {
+        const unsigned long long t = s_w64[w];
+        wb += w < warp ? t : 0ull;
+        btot += t;
+    }
+    if (tid == 0) a.bsum[blockIdx.x] = btot;
+    grid_barrier(a.bar, a.err);
+    unsigned long long bpre = 0, all = 0;
+    for (uint32_t b = 0; b < G; ++b) {
+        const unsigned long long v = *(volatile const unsigned long long*)(a.bsum + b);
+        bpre += b < blockIdx.x ? v : 0ull;
+        all += v;
+    }
+    uint32_t run = (uint32_t)(bpre + wb + x - sum);
+    for (uint32_t j = t0; j < t1; ++j) {
+        const uint32_t id = sorted[lo + j];
+        a.offsets[lo + j] = run;
+        run += id < n ? a.counts[id] : 0u;
+    }
+    if (blockIdx.x == G - 1 && tid == 0) a.offsets[n] = (uint32_t)all;
+}
+
+int ds_grid(int device)
+{
+    static int cached_dev = -1, cached = 0;
+    if (cached_dev == device) return cached;
+    int sms = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+    const size_t smem = depth_sort_smem_bytes();
+    if (cudaFuncSetAttribute(k_depth_sort_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_depth_sort_scan, kDsThreads, smem) != cudaSuccess)
+        return 0;
+    cached_dev = device;
+    cached = per_sm >= 1 ? sms : 0;
+    return cached;
+}
+
+}  // namespace
+
+size_t depth_sort_smem_bytes()
+{
+    return (size_t)kDsMaxSlice * (4 + 4 + 2) + (size_t)kDsWarps * kDsRadix * 2 + kDsRadix * 4 + kDsWarps * 4;
+}
+
+uint32_t depth_sort_capacity(int device)
+{
+    return (uint32_t)ds_grid(device) * (uint32_t)kDsMaxSlice;
+}
+
+cudaError_t launch_depth_sort_scan(cudaStream_t s, int device, const uint32_t* keys_in, uint32_t* keys[2],
+                                   uint32_t* ids[2], const uint32_t* counts, uint32_t n, uint32_t* offsets,
+                                   uint32_t* cnt_scratch, unsigned long long* bsum_scratch, unsigned int* bar,
+                                   int* err, int* out_idx)
+{
+    const int G = ds_grid(device);
+    if (G <= 0 || n == 0 || n > (uint32_t)G * (uint32_t)kDsMaxSlice) return cudaErrorInvalidValue;
+    // fewer blocks for small inputs (at least 1024 elements per block)
+    const uint64_t want = ((uint64_t)n + 1023) / 1024;
+    const uint32_t grid = (uint32_t)(want < (uint64_t)G ? want : (uint64_t)G);
+    cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    DsArgs a;
+    a.keys_in = keys_in;
+    a.keys[0] = keys[0] == keys_in ? keys[1] : keys[0];
+    a.keys[1] = keys[0] == keys_in ? keys[0] : keys[1];
+    a.ids[0] = ids[0];
+    a.ids[1] = ids[1];
+    a.counts = counts;
+    a.offsets = offsets;
+    a.cnt = cnt_scratch;
+    a.bsum = bsum_scratch;
+    a.bar = bar;
+    a.err = err;
+    a.n = n;
+    void* args[] = {&a};
+    e = cudaLaunchCooperativeKernel((const void*)k_depth_sort_scan, dim3(grid), dim3(kDsThreads), args,
+                                    depth_sort_smem_bytes(), s);
+    note_launch();
+    *out_idx = (kDsPasses - 1) & 1;
+    return e;
+}
+
+}  // namespace gs

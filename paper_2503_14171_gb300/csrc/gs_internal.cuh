@@ -100,6 +100,7 @@ struct gs_ctx {
     gs::DevBuf sort_status;             // uint32[passes][tiles][256]
     gs::DevBuf sort_counter;            // uint32[passes]
     gs::DevBuf super_counts;            // uint32[super-tiles]
+    gs::DevBuf ds_scratch;              // persistent depth sort: per-block counts, sums, barrier
     cudaEvent_t totals_ready = nullptr; // recorded after the pair totals are copied to the host
     // per tile / pixel
     gs::DevBuf sranges;                 // uint2[super-tiles]
@@ -156,6 +157,17 @@ size_t scan_partials_count(uint32_t n);
 
 // counts (may be NULL): kCountCopies x Ts per-super-tile pair counts accumulated
 // while emitting (zeroed by the caller; Ts <= kMaxSupersForCounts)
+// Depth sort + pair-offset scan in one cooperative launch (depthsort.cu), for
+// up to depth_sort_capacity(device) Gaussians (kDsMaxSlice per SM).  keys[0]
+// holds the depth keys on entry; the sorted ids land in ids[*out_idx].
+constexpr uint32_t kDsMaxSlice = 16384;
+size_t depth_sort_smem_bytes();
+uint32_t depth_sort_capacity(int device);
+cudaError_t launch_depth_sort_scan(cudaStream_t s, int device, const uint32_t* keys_in, uint32_t* keys[2],
+                                   uint32_t* ids[2], const uint32_t* counts, uint32_t n, uint32_t* offsets,
+                                   uint32_t* cnt_scratch, unsigned long long* bsum_scratch, unsigned int* bar,
+                                   int* err, int* out_idx);
+
 cudaError_t launch_emit_pairs(cudaStream_t s, const uint32_t* ids, const uint32_t* offsets, const ushort4* rect,
                               uint32_t n, int stiles_x, uint64_t* pairs, uint32_t* counts, uint32_t Ts);
 cudaError_t launch_ranges(cudaStream_t s, const uint64_t* pairs, uint32_t P, uint32_t T, uint2* ranges);
