@@ -107,8 +107,8 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
             const bool valid = j < whi;
             uint32_t key = 0, id = 0, d = 0;
             if (valid) {
-                key = src_key[lo + j];
-                id = pass == 0 ? lo + j : src_id[lo + j];
+                key = __ldcg(src_key + lo + j);
+                id = pass == 0 ? lo + j : __ldcg(src_id + lo + j);
                 d = (key >> shift) & 0xFFu;
             }
             uint32_t peers = __ballot_sync(0xffffffffu, valid);
@@ -143,9 +143,11 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
         grid_barrier(a.bar, a.err);
         // global offset of this block's first element of each digit
         if (tid < kDsRadix) {
+            // L2 loads (other blocks wrote these this pass; L1 may hold last pass's)
             uint32_t tot = 0, pre = 0;
+#pragma unroll 8
             for (uint32_t b = 0; b < G; ++b) {
-                const uint32_t c = *(volatile const uint32_t*)(a.cnt + (size_t)b * kDsRadix + tid);
+                const uint32_t c = __ldcg(a.cnt + (size_t)b * kDsRadix + tid);
                 tot += c;
                 pre += b < blockIdx.x ? c : 0u;
             }
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
     const uint32_t t0 = min(m, tid * E), t1 = min(m, t0 + E);
     unsigned long long sum = 0;
     for (uint32_t j = t0; j < t1; ++j) {
-        const uint32_t id = sorted[lo + j];
+        const uint32_t id = __ldcg(sorted + lo + j);
         sum += id < n ? a.counts[id] : 0u;
     }
     unsigned long long x = sum;
@@ -208,14 +210,15 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
     if (tid == 0) a.bsum[blockIdx.x] = btot;
     grid_barrier(a.bar, a.err);
     unsigned long long bpre = 0, all = 0;
+#pragma unroll 8
     for (uint32_t b = 0; b < G; ++b) {
-        const unsigned long long v = *(volatile const unsigned long long*)(a.bsum + b);
+        const unsigned long long v = __ldcg(a.bsum + b);
         bpre += b < blockIdx.x ? v : 0ull;
         all += v;
     }
     uint32_t run = (uint32_t)(bpre + wb + x - sum);
     for (uint32_t j = t0; j < t1; ++j) {
-        const uint32_t id = sorted[lo + j];
+        const uint32_t id = __ldcg(sorted + lo + j);
         a.offsets[lo + j] = run;
         run += id < n ? a.counts[id] : 0u;
     }
