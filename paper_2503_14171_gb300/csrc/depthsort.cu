@@ -99,18 +99,20 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
         uint32_t* dst_key = a.keys[pass & 1];
         uint32_t* dst_id = a.ids[pass & 1];
         for (int i = tid; i < kDsWarps * kDsRadix; i += kDsThreads) s_wcnt[i] = 0;
+        // stage the slice in shared memory: independent coalesced loads (L2, the
+        // previous pass's scatter by other blocks)
+#pragma unroll 4
+        for (uint32_t j = tid; j < m; j += kDsThreads) {
+            s_key[j] = __ldcg(src_key + lo + j);
+            s_id[j] = pass == 0 ? lo + j : __ldcg(src_id + lo + j);
+        }
         __syncthreads();
         // stable ranking: warp w ranks its chunk [w cw, (w+1) cw) 32 elements at a time
         const uint32_t wlo = warp * cw, whi = min(m, wlo + cw);
         for (uint32_t base = wlo; base < whi; base += 32) {
             const uint32_t j = base + lane;
             const bool valid = j < whi;
-            uint32_t key = 0, id = 0, d = 0;
-            if (valid) {
-                key = __ldcg(src_key + lo + j);
-                id = pass == 0 ? lo + j : __ldcg(src_id + lo + j);
-                d = (key >> shift) & 0xFFu;
-            }
+            const uint32_t d = valid ? (s_key[j] >> shift) & 0xFFu : 0u;
             uint32_t peers = __ballot_sync(0xffffffffu, valid);
 #pragma unroll
             for (int b = 0; b < 8; ++b) {
@@ -122,8 +124,6 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
             if (valid) prev = s_wcnt[warp * kDsRadix + d];
             __syncwarp();
             if (valid) {
-                s_key[j] = key;
-                s_id[j] = id;
                 s_rank[j] = (uint16_t)(prev + __popc(peers & lt));
                 if (lane == 31 - __clz(peers)) s_wcnt[warp * kDsRadix + d] = (uint16_t)(prev + __popc(peers));
             }
@@ -182,23 +182,31 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
         grid_barrier(a.bar, a.err);
     }
 
-    // exclusive scan of counts[id] over the sorted slice: thread t owns a
-    // contiguous run of E = ceil(m / 1024) positions
+    // exclusive scan of counts[id] over the sorted slice.  Stage the sorted ids
+    // and their gathered counts in shared memory (independent loads), then
+    // thread t scans a contiguous run of E = ceil(m / 1024) positions.
     const uint32_t* sorted = a.ids[(kDsPasses - 1) & 1];
+    uint32_t* s_cnt = s_key;   // reuse
+#pragma unroll 4
+    for (uint32_t j = tid; j < m; j += kDsThreads) s_id[j] = __ldcg(sorted + lo + j);
+    __syncthreads();
+#pragma unroll 4
+    for (uint32_t j = tid; j < m; j += kDsThreads) {
+        const uint32_t id = s_id[j];
+        s_cnt[j] = id < n ? a.counts[id] : 0u;
+    }
+    __syncthreads();
     const uint32_t E = (m + kDsThreads - 1) / kDsThreads;
     const uint32_t t0 = min(m, tid * E), t1 = min(m, t0 + E);
     unsigned long long sum = 0;
-    for (uint32_t j = t0; j < t1; ++j) {
-        const uint32_t id = __ldcg(sorted + lo + j);
-        sum += id < n ? a.counts[id] : 0u;
-    }
+    for (uint32_t j = t0; j < t1; ++j) sum += s_cnt[j];
     unsigned long long x = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
     }
-    unsigned long long* s_w64 = reinterpret_cast<unsigned long long*>(s_key);   // reuse: [kDsWarps]
+    __shared__ unsigned long long s_w64[kDsWarps];
     if (lane == 31) s_w64[warp] = x;
     __syncthreads();
     unsigned long long wb = 0, btot = 0;
@@ -208,6 +216,13 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
         btot += t;
     }
     if (tid == 0) a.bsum[blockIdx.x] = btot;
+    // block-local exclusive prefixes, in place (s_id is free again)
+    uint32_t run = (uint32_t)(wb + x - sum);
+    for (uint32_t j = t0; j < t1; ++j) {
+        const uint32_t c = s_cnt[j];
+        s_id[j] = run;
+        run += c;
+    }
     grid_barrier(a.bar, a.err);
     unsigned long long bpre = 0, all = 0;
 #pragma unroll 8
@@ -216,12 +231,9 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
         bpre += b < blockIdx.x ? v : 0ull;
         all += v;
     }
-    uint32_t run = (uint32_t)(bpre + wb + x - sum);
-    for (uint32_t j = t0; j < t1; ++j) {
-        const uint32_t id = __ldcg(sorted + lo + j);
-        a.offsets[lo + j] = run;
-        run += id < n ? a.counts[id] : 0u;
-    }
+    const uint32_t bp = (uint32_t)bpre;
+#pragma unroll 4
+    for (uint32_t j = tid; j < m; j += kDsThreads) a.offsets[lo + j] = bp + s_id[j];
     if (blockIdx.x == G - 1 && tid == 0) a.offsets[n] = (uint32_t)all;
 }
 
