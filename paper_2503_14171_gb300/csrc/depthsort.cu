@@ -224,14 +224,28 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
         run += c;
     }
     grid_barrier(a.bar, a.err);
-    unsigned long long bpre = 0, all = 0;
-#pragma unroll 8
-    for (uint32_t b = 0; b < G; ++b) {
-        const unsigned long long v = __ldcg(a.bsum + b);
-        bpre += b < blockIdx.x ? v : 0ull;
-        all += v;
+    // one warp reads the block sums (lane-strided) and broadcasts the prefix:
+    // every thread reading them would hammer the same few L2 lines
+    if (warp == 0) {
+        unsigned long long bpre = 0, all = 0;
+        for (uint32_t b = lane; b < G; b += 32) {
+            const unsigned long long v = __ldcg(a.bsum + b);
+            bpre += b < blockIdx.x ? v : 0ull;
+            all += v;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            bpre += __shfl_xor_sync(0xffffffffu, bpre, o);
+            all += __shfl_xor_sync(0xffffffffu, all, o);
+        }
+        if (lane == 0) {
+            s_w64[0] = bpre;
+            s_w64[1] = all;
+        }
     }
-    const uint32_t bp = (uint32_t)bpre;
+    __syncthreads();
+    const uint32_t bp = (uint32_t)s_w64[0];
+    const unsigned long long all = s_w64[1];
 #pragma unroll 4
     for (uint32_t j = tid; j < m; j += kDsThreads) a.offsets[lo + j] = bp + s_id[j];
     if (blockIdx.x == G - 1 && tid == 0) a.offsets[n] = (uint32_t)all;
