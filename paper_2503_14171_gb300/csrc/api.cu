@@ -206,7 +206,7 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
     const uint32_t ds_cap = n > 1 ? depth_sort_capacity(c->device) : 0u;
     if (n > 1 && n <= ds_cap) {
         const size_t G = ds_cap / kDsMaxSlice;
-        if ((st = ensure(c, c->ds_scratch, G * kRadixDigits * 4 + G * 8 + 64))) return st;
+        if ((st = ensure(c, c->ds_scratch, G * kRadixDigits * 4 + G * 8 + 64 + 4 * kRadixDigits * 4))) return st;
         unsigned char* base = as<unsigned char>(c->ds_scratch);
         uint32_t* keys[2] = {as<uint32_t>(c->dkey[0]), as<uint32_t>(c->dkey[1])};
         uint32_t* vals[2] = {as<uint32_t>(c->did[0]), as<uint32_t>(c->did[1])};
@@ -214,6 +214,7 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
                                           as<uint32_t>(c->offsets), reinterpret_cast<uint32_t*>(base),
                                           reinterpret_cast<unsigned long long*>(base + G * kRadixDigits * 4),
                                           reinterpret_cast<unsigned int*>(base + G * kRadixDigits * 4 + G * 8),
+                                          reinterpret_cast<uint32_t*>(base + G * kRadixDigits * 4 + G * 8 + 64),
                                           as<int>(c->errword), &sorted));
     } else {
         if (n > 1) {

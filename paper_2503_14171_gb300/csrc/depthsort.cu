@@ -6,9 +6,10 @@
 // contiguous slice of the sequence:
 //   4 stable LSD passes over the 8-bit digits of the FP32 depth bits (ids in
 //   ascending order ride along): load the slice, rank it by digit with one
-//   ballot per digit bit and per-warp running counters (stable), publish the
-//   block's digit counts, grid barrier, derive the global digit offsets from
-//   all blocks' counts, scatter, grid barrier;
+//   ballot per digit bit and per-warp running counters (stable), reorder it by
+//   digit in shared memory, publish the block's digit counts (and add them to
+//   the digit totals), grid barrier, derive the global offset of each of the
+//   block's digit runs, write the runs out (coalesced), grid barrier;
 //   then the exclusive scan of supers_touched[id] in the sorted order (block
 //   sums, grid barrier, block prefixes), which gives each Gaussian's first
 //   pair slot.
@@ -37,6 +38,7 @@ struct DsArgs {
     const uint32_t* counts;      // [n] pair count per Gaussian (by id)
     uint32_t* offsets;           // [n + 1] exclusive scan in depth order
     uint32_t* cnt;               // [grid][256] per-block digit counts
+    uint32_t* tot;               // [4][256] digit totals per pass (zeroed)
     unsigned long long* bsum;    // [grid] per-block count sums
     unsigned int* bar;           // [2] barrier counter and generation (zeroed)
     int* err;
@@ -84,11 +86,13 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
 
     uint32_t* s_key = reinterpret_cast<uint32_t*>(smem);
     uint32_t* s_id = s_key + kDsMaxSlice;
-    uint16_t* s_rank = reinterpret_cast<uint16_t*>(s_id + kDsMaxSlice);
+    uint32_t* s_key2 = s_id + kDsMaxSlice;                            // slice reordered by digit
+    uint32_t* s_id2 = s_key2 + kDsMaxSlice;
+    uint16_t* s_rank = reinterpret_cast<uint16_t*>(s_id2 + kDsMaxSlice);
     uint16_t* s_wcnt = s_rank + kDsMaxSlice;                          // [kDsWarps][256]
     uint32_t* s_off = reinterpret_cast<uint32_t*>(s_wcnt + kDsWarps * kDsRadix);   // [256]
-    uint32_t* s_wtot = s_off + kDsRadix;                              // [kDsWarps]
-
+    uint32_t* s_boff = s_off + kDsRadix;                              // [256] block-local digit starts
+    uint32_t* s_wtot = s_boff + kDsRadix;                             // [kDsWarps]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt = (1u << lane) - 1u;
 
@@ -130,7 +134,8 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
             __syncwarp();
         }
         __syncthreads();
-        // per digit: exclusive prefix over warps, and the block's count
+        // per digit: exclusive prefix over warps, the block's count (published,
+        // and added to the digit total), and the block-local start of the digit
         if (tid < kDsRadix) {
             uint32_t run = 0;
             for (int w = 0; w < kDsWarps; ++w) {
@@ -139,19 +144,39 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
                 run += c;
             }
             a.cnt[(size_t)blockIdx.x * kDsRadix + tid] = run;
+            if (run) atomicAdd(&a.tot[pass * kDsRadix + tid], run);
+            uint32_t x = run;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31) s_wtot[warp] = x;
+            s_boff[tid] = x - run;
+        }
+        __syncthreads();
+        if (tid < kDsRadix) {
+            uint32_t wb = 0;
+            for (int w = 0; w < warp; ++w) wb += s_wtot[w];
+            s_boff[tid] += wb;
+        }
+        __syncthreads();
+        // reorder the slice by digit (stable) in shared memory
+        for (uint32_t j = tid; j < m; j += kDsThreads) {
+            const uint32_t key = s_key[j];
+            const uint32_t d = (key >> shift) & 0xFFu;
+            const uint32_t lp = s_boff[d] + s_wcnt[(j / cw) * kDsRadix + d] + s_rank[j];
+            s_key2[lp] = key;
+            s_id2[lp] = s_id[j];
         }
         grid_barrier(a.bar, a.err);
-        // global offset of this block's first element of each digit
+        // global start of this block's run of each digit:
+        // exclusive digit total + this digit's count in earlier blocks
         if (tid < kDsRadix) {
-            // L2 loads (other blocks wrote these this pass; L1 may hold last pass's)
-            uint32_t tot = 0, pre = 0;
+            const uint32_t tot = __ldcg(a.tot + pass * kDsRadix + tid);
+            uint32_t pre = 0;
 #pragma unroll 8
-            for (uint32_t b = 0; b < G; ++b) {
-                const uint32_t c = __ldcg(a.cnt + (size_t)b * kDsRadix + tid);
-                tot += c;
-                pre += b < blockIdx.x ? c : 0u;
-            }
-            // exclusive scan of the digit totals (8 warps)
+            for (uint32_t b = 0; b < blockIdx.x; ++b) pre += __ldcg(a.cnt + (size_t)b * kDsRadix + tid);
             uint32_t x = tot;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -159,7 +184,7 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
                 if (lane >= o) x += y;
             }
             if (lane == 31) s_wtot[warp] = x;
-            s_off[tid] = pre + x - tot;   // completed below with the earlier warps' totals
+            s_off[tid] = pre + x - tot - s_boff[tid];   // completed below with earlier warps' totals
         }
         __syncthreads();
         if (tid < kDsRadix) {
@@ -168,15 +193,13 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
             s_off[tid] += wb;
         }
         __syncthreads();
-        // scatter
+        // write the digit runs out: consecutive threads, consecutive addresses
         for (uint32_t j = tid; j < m; j += kDsThreads) {
-            const uint32_t key = s_key[j];
-            const uint32_t d = (key >> shift) & 0xFFu;
-            const uint32_t w = j / cw;
-            const uint32_t pos = s_off[d] + s_wcnt[w * kDsRadix + d] + s_rank[j];
+            const uint32_t key = s_key2[j];
+            const uint32_t pos = s_off[(key >> shift) & 0xFFu] + j;
             if (pos < n) {
                 if (pass + 1 < kDsPasses) dst_key[pos] = key;
-                dst_id[pos] = s_id[j];
+                dst_id[pos] = s_id2[j];
             }
         }
         grid_barrier(a.bar, a.err);
@@ -271,7 +294,7 @@ int ds_grid(int device)
 
 size_t depth_sort_smem_bytes()
 {
-    return (size_t)kDsMaxSlice * (4 + 4 + 2) + (size_t)kDsWarps * kDsRadix * 2 + kDsRadix * 4 + kDsWarps * 4;
+    return (size_t)kDsMaxSlice * (4 * 4 + 2) + (size_t)kDsWarps * kDsRadix * 2 + 2 * kDsRadix * 4 + kDsWarps * 4;
 }
 
 uint32_t depth_sort_capacity(int device)
@@ -282,7 +305,7 @@ uint32_t depth_sort_capacity(int device)
 cudaError_t launch_depth_sort_scan(cudaStream_t s, int device, const uint32_t* keys_in, uint32_t* keys[2],
                                    uint32_t* ids[2], const uint32_t* counts, uint32_t n, uint32_t* offsets,
                                    uint32_t* cnt_scratch, unsigned long long* bsum_scratch, unsigned int* bar,
-                                   int* err, int* out_idx)
+                                   uint32_t* tot_scratch, int* err, int* out_idx)
 {
     const int G = ds_grid(device);
     if (G <= 0 || n == 0 || n > (uint32_t)G * (uint32_t)kDsMaxSlice) return cudaErrorInvalidValue;
@@ -291,6 +314,7 @@ cudaError_t launch_depth_sort_scan(cudaStream_t s, int device, const uint32_t* k
     const uint32_t grid = (uint32_t)(want < (uint64_t)G ? want : (uint64_t)G);
     cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(tot_scratch, 0, sizeof(uint32_t) * kDsPasses * kDsRadix, s)) != cudaSuccess) return e;
     DsArgs a;
     a.keys_in = keys_in;
     a.keys[0] = keys[0] == keys_in ? keys[1] : keys[0];
@@ -300,6 +324,7 @@ cudaError_t launch_depth_sort_scan(cudaStream_t s, int device, const uint32_t* k
     a.counts = counts;
     a.offsets = offsets;
     a.cnt = cnt_scratch;
+    a.tot = tot_scratch;
     a.bsum = bsum_scratch;
     a.bar = bar;
     a.err = err;

@@ -160,13 +160,13 @@ size_t scan_partials_count(uint32_t n);
 // Depth sort + pair-offset scan in one cooperative launch (depthsort.cu), for
 // up to depth_sort_capacity(device) Gaussians (kDsMaxSlice per SM).  keys[0]
 // holds the depth keys on entry; the sorted ids land in ids[*out_idx].
-constexpr uint32_t kDsMaxSlice = 16384;
+constexpr uint32_t kDsMaxSlice = 10240;
 size_t depth_sort_smem_bytes();
 uint32_t depth_sort_capacity(int device);
 cudaError_t launch_depth_sort_scan(cudaStream_t s, int device, const uint32_t* keys_in, uint32_t* keys[2],
                                    uint32_t* ids[2], const uint32_t* counts, uint32_t n, uint32_t* offsets,
                                    uint32_t* cnt_scratch, unsigned long long* bsum_scratch, unsigned int* bar,
-                                   int* err, int* out_idx);
+                                   uint32_t* tot_scratch, int* err, int* out_idx);
 
 cudaError_t launch_emit_pairs(cudaStream_t s, const uint32_t* ids, const uint32_t* offsets, const ushort4* rect,
                               uint32_t n, int stiles_x, uint64_t* pairs, uint32_t* counts, uint32_t Ts);
