@@ -164,6 +164,32 @@ gs_status gs_render(gs_ctx* ctx, const gs_gaussians* g, const gs_camera* cam,
 gs_status gs_upscale(gs_ctx* ctx, const float* C, const float* grads, int32_t W, int32_t H,
                      int32_t factor, float* out);
 
+/* gs_render_with_grads for callers that cannot allocate device memory (an
+ * engine or compositor that owns every device byte, a plugin restricted to
+ * the buffers its host provides, a real-time loop that must not stall on an
+ * allocation).  The paper has no counterpart; it is a deployment variant of
+ * the render above and produces the same outputs.
+ *
+ * No context: every scratch buffer comes from one file-scope device array of
+ * about 6.6 MB that each GPU loading the library holds until the process
+ * exits; no cudaMalloc, cudaFree or other allocating call is made.  Limits:
+ * g->n <= 16384, W * H <= 65536 with W, H <= 4096, at most 262144
+ * (64x64-pixel super-tile, Gaussian) pairs; beyond them GS_ERR_CAPACITY and
+ * nothing is written.  opt may be NULL (3DGS mode, black background).
+ * stream: a cudaStream_t (NULL = legacy default stream).  Inputs and outputs
+ * are caller-owned device pointers as for gs_render_with_grads: out_C
+ * [3][H][W], out_grads [3][3][H][W].
+ *
+ * The first call on each device (with that device current) looks up the
+ * array's device address with cudaGetSymbolAddress; make it before any stream
+ * capture.  The call synchronises the stream (pair-count readback and a final
+ * error check).  All calls share the array and its contents persist between
+ * calls; whatever must start at zero is cleared by each call.  Calls whose
+ * work could overlap on the GPU (other streams, other host threads) race on
+ * the array and must be serialised by the caller. */
+gs_status gs_render_with_grads_noalloc(const gs_gaussians* g, const gs_camera* cam, int32_t W, int32_t H,
+                                       const gs_options* opt, void* stream, float* out_C, float* out_grads);
+
 /* Number of (tile, Gaussian) pairs of the last gs_project (host int64). */
 gs_status gs_pair_count(const gs_ctx* ctx, int64_t* P);
 

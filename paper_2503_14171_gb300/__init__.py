@@ -71,6 +71,8 @@ _SIGS = {
     "gs_launch_count": ([_P, ct.POINTER(ct.c_int64)], ct.c_int),
     "gs_blend_stats": ([_P, _P], ct.c_int),
     "gs_synchronize": ([_P], ct.c_int),
+    "gs_render_with_grads_noalloc": ([ct.POINTER(GsGaussians), ct.POINTER(GsCamera), ct.c_int32, ct.c_int32,
+                                      ct.POINTER(GsOptions), _P, _P, _P], ct.c_int),
 }
 
 
@@ -150,6 +152,16 @@ def gs_upscale(ctx, C: int, grads: int, W: int, H: int, factor: int, out: int):
 
 def gs_synchronize(ctx):
     _chk(lib.gs_synchronize(ctx), ctx, "gs_synchronize")
+
+
+def gs_render_with_grads_noalloc(g: GsGaussians, cam: GsCamera, W: int, H: int, options: GsOptions | None,
+                                 stream, out_C: int, out_grads: int):
+    """Context-free render with derivatives whose scratch is a static device array."""
+    st = lib.gs_render_with_grads_noalloc(ct.byref(g), ct.byref(cam), W, H,
+                                          ct.byref(options) if options is not None else None, stream, out_C,
+                                          out_grads)
+    if st != GS_OK:
+        raise GSError(st, "gs_render_with_grads_noalloc")
 
 
 # ---- torch-facing helpers ----------------------------------------------------
