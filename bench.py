@@ -40,7 +40,7 @@ WORKLOAD = "mixture scene 1.5M Gaussians SH3, 960x540 render+grads -> 2x Hermite
 METRIC = "output MPix/s render+upscale vs direct full-res render, same GB300, at PSNR"
 # Algorithmic FP32 operations per (pixel, Gaussian) pair of the blend, counted
 # from the formulas (an FMA counts 2): evaluating the exponent g = 10; blending a
-# pair with the derivative recurrences adds 52 (kernel K6).
+# pair with the derivative recurrences adds 52 (itemised beside the blend kernel).
 FLOP_EVAL = 10
 FLOP_ACC_GRADS = 52
 SM_COUNT = 152
@@ -65,6 +65,21 @@ def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(x: float, device, world: int) -> float:
+    """The largest of every rank's x (all ranks call it; world 1 returns x)."""
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, steps: int, units_per_step: float, slowest_ms: float) -> float:
+    """Whole-job throughput of independent replicas: every rank processes
+    units_per_step per step, the job ends with the slowest rank."""
+    return world * steps * units_per_step / (slowest_ms / 1e3)
 
 
 def _peaks():
@@ -274,12 +289,9 @@ def run_gs(args):
         t_blend = [e[1].elapsed_time(e[2]) for e in evs]
         t_up = [e[2].elapsed_time(e[3]) for e in evs]
 
-        t_max = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        if world > 1:
-            torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t_max.item())
+        total_ms = max_over_ranks(total_ms, "cuda", world)
         ms_step = total_ms / args.steps
-        value = world * args.steps * OUT_W * OUT_H / 1e6 / (total_ms / 1e3)
+        value = job_throughput(world, args.steps, OUT_W * OUT_H / 1e6, total_ms)
 
         # comparator: direct 1920x1080 render of the same scene
         def time_loop(fn, k):
@@ -338,10 +350,7 @@ def run_gs(args):
         b.record(stream)
         torch.cuda.synchronize()
         e2e_ms = a.elapsed_time(b) / ke
-        t_e = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-        if world > 1:
-            torch.distributed.all_reduce(t_e, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t_e.item())
+        e2e_ms = max_over_ranks(e2e_ms, "cuda", world)
 
     if rank != 0:
         if world > 1:
