@@ -460,16 +460,25 @@ def run_gs(args):
 
 
 def _traffic_from_profiles():
-    """DRAM bytes per blend launch from the committed ncu summary, if current."""
-    p = os.path.join(ROOT, "profiles", "blend_traffic.json")
+    """DRAM bytes per blend launch from the committed ncu summary, or None when
+    the blend's sources changed since that capture."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "k_blend_grads_traffic.txt")
     if not os.path.exists(p):
         return None
-    try:
-        with open(p) as f:
-            d = json.load(f)
-        return d.get("dram_bytes_per_launch")
-    except Exception:
+    d = {}
+    with open(p) as f:
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                d[k.strip()] = v.strip()
+    h = hashlib.sha256()
+    for name in ("blend.cu", "gs_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2503_14171_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    if h.hexdigest()[:16] != d.get("sources_sha256_16"):
         return None
+    return int(d["dram_bytes_per_launch"])
 
 
 def run_profile(args):
