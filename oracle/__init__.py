@@ -50,7 +50,8 @@ def _load():
             build()
             _lib = ct.CDLL(_LIB)
             for name in ("ora_sh_basis", "ora_project", "ora_bin", "ora_render",
-                         "ora_spline_cinv", "ora_upscale"):
+                         "ora_spline_cinv", "ora_upscale", "ora_upscale_adjoint",
+                         "ora_render_adjoint", "ora_project_adjoint"):
                 getattr(_lib, name).restype = ct.c_int
         return _lib
 
@@ -229,6 +230,91 @@ def upscale(C, grads, W2: int, H2: int, pixels=None) -> np.ndarray:
     _check(st, "upscale")
     if pixels is None:
         return np.ascontiguousarray(out.reshape(H2, W2, 3).transpose(2, 0, 1))
+    return out
+
+
+# --------------------------------------------------------------------------
+# Reverse mode (supplement "Backward Pass")
+# --------------------------------------------------------------------------
+
+G2D_FIELDS = ("mean_x", "mean_y", "conic_a", "conic_b", "conic_c", "opacity", "r", "g", "b")
+
+
+def upscale_adjoint(dout, W: int, H: int):
+    """Adjoint of ``upscale``: dout [3,H2,W2] -> (dC [3,H,W], dgrads [3,3,H,W])."""
+    lib = _load()
+    d = _f64(dout)
+    H2, W2 = d.shape[1], d.shape[2]
+    dC = np.zeros((3, H, W))
+    dG = np.zeros((3, 3, H, W))
+    _check(lib.ora_upscale_adjoint(ct.c_int(W), ct.c_int(H), ct.c_int(W2), ct.c_int(H2), _p(d), _p(dC), _p(dG)),
+           "upscale_adjoint")
+    return dC, dG
+
+
+def render_adjoint(proj: dict, bins: dict, dout, bg=(0.0, 0.0, 0.0), pixels=None,
+                   nthreads: int | None = None) -> dict:
+    """Adjoint of ``render``: upstream dL/d(C, C_x, C_y, C_xy) -> dL/d(2D parameters).
+
+    dout: planes (dC [3,H,W], dgrads [3,3,H,W]) for the whole image, or rows
+    [M, 12] (C rgb, Cx rgb, Cy rgb, Cxy rgb) for ``pixels`` [M, 2] of (x, y).
+    Returns g2d [n, 9] (columns ``G2D_FIELDS``) and ``b2f``, the image recomputed
+    back to front from the tape (same layout as dout).
+    """
+    lib = _load()
+    W, H = proj["W"], proj["H"]
+    n = proj["depth"].shape[0]
+    if pixels is None:
+        dC, dG = dout
+        rows = np.concatenate([_f64(dC).reshape(3, -1), _f64(dG).reshape(9, -1)], 0).T
+        npix, pix = W * H, None
+    else:
+        pix = np.ascontiguousarray(pixels, dtype=np.int32).reshape(-1, 2)
+        npix = pix.shape[0]
+        rows = _f64(dout).reshape(npix, 12)
+    rows = np.ascontiguousarray(rows)
+    g2d = np.zeros((n, 9))
+    b2f = np.zeros((npix, 12))
+    bgv = _f64(np.asarray(bg, np.float64).reshape(3))
+    vals = np.ascontiguousarray(bins["vals"] if bins["P"] > 0 else np.zeros(1, np.uint32))
+    st = lib.ora_render_adjoint(
+        ct.c_int(W), ct.c_int(H), ct.c_int(proj["tile"]), ct.c_int(proj["mode"]), _p(bgv),
+        _p(proj["mean2d"]), _p(proj["conic"]), _p(proj["opacity"]), _p(proj["rgb"]),
+        _p(vals), _p(np.ascontiguousarray(bins["ranges"])), ct.c_int64(n),
+        ct.c_int64(npix), _p(pix), _p(rows), _p(g2d), _p(b2f), ct.c_int(nthreads or default_threads()))
+    _check(st, "render_adjoint")
+    res = dict(g2d=g2d)
+    if pixels is None:
+        planes = b2f.reshape(H, W, 12).transpose(2, 0, 1)
+        res["b2f_C"] = np.ascontiguousarray(planes[0:3])
+        res["b2f_grads"] = np.ascontiguousarray(planes[3:12].reshape(3, 3, H, W))
+    else:
+        res["b2f"] = b2f
+    return res
+
+
+def project_adjoint(scene: dict, cam: dict, W: int, H: int, g2d) -> dict:
+    """Adjoint of ``project``: dL/d(2D parameters) [n, 9] -> dL/d(scene inputs)."""
+    lib = _load()
+    n = int(scene["means"].shape[0])
+    sh = _f64(scene.get("sh"))
+    rgb_in = _f64(scene.get("rgb")) if sh is None else None
+    deg = int(scene.get("sh_degree", 0)) if sh is not None else 0
+    vm = _f64(cam["viewmat"]).reshape(16)
+    out = dict(means=np.zeros((n, 3)), log_scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
+               opacity_logits=np.zeros(n))
+    if sh is not None:
+        out["sh"] = np.zeros(sh.shape)
+    else:
+        out["rgb"] = np.zeros((n, 3))
+    st = lib.ora_project_adjoint(
+        ct.c_int64(n), _p(_f64(scene["means"])), _p(_f64(scene["log_scales"])), _p(_f64(scene["quats"])),
+        _p(_f64(scene["opacity_logits"])), _p(sh), ct.c_int(deg), _p(rgb_in), _p(vm),
+        ct.c_double(cam["fx"]), ct.c_double(cam["fy"]), ct.c_double(cam["cx"]), ct.c_double(cam["cy"]),
+        ct.c_double(cam["znear"]), ct.c_int(W), ct.c_int(H), _p(np.ascontiguousarray(_f64(g2d))),
+        _p(out["means"]), _p(out["log_scales"]), _p(out["quats"]), _p(out["opacity_logits"]),
+        _p(out.get("sh")), _p(out.get("rgb")))
+    _check(st, "project_adjoint")
     return out
 
 

@@ -21,6 +21,11 @@
  *                    "Spline Image Interpolation")
  *   ora_upscale      bicubic patch p(x,y) = [1 x x^2 x^3] C^-1 F C^-T [1 y y^2 y^3]^T
  *                    per low-res cell (Sec. 5 "Spline Interpolation")
+ *   ora_upscale_adjoint  transpose of the (linear) upscale
+ *   ora_render_adjoint   per-pixel tape swept back to front (supplement
+ *                    "Backward Pass"): dL/d(mean2D, conic, opacity, colour)
+ *   ora_project_adjoint  forward-mode (dual number) derivatives of the
+ *                    projection, contracted with the upstream gradient
  *
  * Readings of passages the paper leaves open (all inherited from the 3DGS
  * renderer the paper builds on, Sec. 6.2):
@@ -709,6 +714,469 @@ int ora_upscale(int W, int H, int W2, int H2, const double* C, const double* G,
             for (int r = 0; r < 4; ++r)
                 for (int cc = 0; cc < 4; ++cc) acc += tv[r] * A[r][cc] * uv[cc];
             out[3 * p + ch] = acc;
+        }
+    }
+    return ORA_OK;
+}
+
+/* ========================================================================= */
+/* Reverse mode (training with differentiable upscaling; supplement          */
+/* "Backward Pass").  Upstream gradients are dL/d(output); every function     */
+/* returns the gradient of the same scalar L with respect to its inputs.      */
+/* ========================================================================= */
+
+/* ------------------------------------------------------------------------- */
+/* Adjoint of ora_upscale.  The upscale is linear in the 12 low-res planes:    */
+/* out = [1 t t^2 t^3] C^-1 F C^-T [1 u u^2 u^3]^T, so dL/dF_rc = dL/dout *     */
+/* (C^-T tv)_r (C^-T uv)_c, scattered back to the plane entries F was read     */
+/* from.  dout: [3][H2][W2]; dC: [3][H][W]; dG: [3][3][H][W] (overwritten).    */
+/* ------------------------------------------------------------------------- */
+int ora_upscale_adjoint(int W, int H, int W2, int H2, const double* dout, double* dC, double* dG)
+{
+    if (W < 2 || H < 2 || W2 < 1 || H2 < 1) return ORA_EINVAL;
+    double Ci[4][4];
+    if (invert4(SPLINE_C, Ci) != ORA_OK) return ORA_EINVAL;
+    const int64_t plane = (int64_t)W * H;
+    for (int64_t k = 0; k < 3 * plane; ++k) dC[k] = 0.0;
+    for (int64_t k = 0; k < 9 * plane; ++k) dG[k] = 0.0;
+    double* fx = dG;
+    double* fy = dG + 3 * plane;
+    double* fxy = dG + 6 * plane;
+    for (int Y = 0; Y < H2; ++Y)
+        for (int X = 0; X < W2; ++X) {
+            int i, j;
+            double t, u;
+            cell_of(X, W, W2, &i, &t);
+            cell_of(Y, H, H2, &j, &u);
+            const double tv[4] = {1.0, t, t * t, t * t * t};
+            const double uv[4] = {1.0, u, u * u, u * u * u};
+            double wt[4], wu[4];
+            for (int r = 0; r < 4; ++r) {
+                wt[r] = 0.0;
+                wu[r] = 0.0;
+                for (int k = 0; k < 4; ++k) {
+                    wt[r] += tv[k] * Ci[k][r];
+                    wu[r] += uv[k] * Ci[k][r];
+                }
+            }
+            for (int ch = 0; ch < 3; ++ch) {
+                const double d = dout[(int64_t)ch * W2 * H2 + (int64_t)Y * W2 + X];
+                double dF[4][4];
+                for (int r = 0; r < 4; ++r)
+                    for (int c = 0; c < 4; ++c) dF[r][c] = d * wt[r] * wu[c];
+#define ACC(q, a, b, v) ((q)[(int64_t)ch * plane + (int64_t)(j + (b)) * W + (i + (a))] += (v))
+                /* the layout of F in ora_upscale: rows (f(0,.), f(1,.), fx(0,.), fx(1,.)),
+                 * columns (f(.,0), f(.,1), fy(.,0), fy(.,1)) */
+                ACC(dC, 0, 0, dF[0][0]); ACC(dC, 0, 1, dF[0][1]); ACC(fy, 0, 0, dF[0][2]); ACC(fy, 0, 1, dF[0][3]);
+                ACC(dC, 1, 0, dF[1][0]); ACC(dC, 1, 1, dF[1][1]); ACC(fy, 1, 0, dF[1][2]); ACC(fy, 1, 1, dF[1][3]);
+                ACC(fx, 0, 0, dF[2][0]); ACC(fx, 0, 1, dF[2][1]); ACC(fxy, 0, 0, dF[2][2]); ACC(fxy, 0, 1, dF[2][3]);
+                ACC(fx, 1, 0, dF[3][0]); ACC(fx, 1, 1, dF[3][1]); ACC(fxy, 1, 0, dF[3][2]); ACC(fxy, 1, 1, dF[3][3]);
+#undef ACC
+            }
+        }
+    return ORA_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Adjoint of the blend (supplement "Backward Pass").  Per pixel, the forward  */
+/* pass is replayed with the same decisions as blend_pixel and every blended   */
+/* step is kept on a tape (alpha and its x/y derivatives, the state A_{k-1}    */
+/* before the step).  The tape is then swept back to front with                */
+/*   B^_k = (1 - alpha_k) B^_{k+1} + alpha_k c_k, B^_{N+1} = background,        */
+/* and its x, y, xy derivatives.  With T = 1 - A_{k-1} and D = c_k - B^_{k+1}:  */
+/*   P    = dI/dalpha_k           = T D                                         */
+/*   P_x  = d2I/(dalpha_k dx)     = T_x D - T B^_x                              */
+/*   P_xy = d3I/(dalpha_k dx dy)  = T_xy D - T_x B^_y - T_y B^_x - T B^_xy       */
+/* (the passage writes 1 - A_k; the state before step k is meant), and for a  */
+/* 2D parameter theta with Q = dalpha_k/dtheta:                                 */
+/*   dI/dtheta = P Q,  dI_x/dtheta = P_x Q + P Q_x,                            */
+/*   dI_xy/dtheta = P_xy Q + P_x Q_y + P_y Q_x + P Q_xy                         */
+/* (the passage's third term pairs d2I/(dalpha dx) with d2alpha/(dsigma dx);   */
+/* the y-derivative is meant).  Colour: dI/dc_k = T alpha_k and its x, y, xy    */
+/* derivatives.  Q for alpha = sigma e^g, g = -1/2 (a dx^2 + 2 b dx dy + c dy^2):*/
+/*   Q = alpha g_t, Q_x = alpha (g_x g_t + g_tx), Q_y = alpha (g_y g_t + g_ty),  */
+/*   Q_xy = alpha (g_y (g_x g_t + g_tx) + g_xy g_t + g_x g_ty + g_txy)           */
+/* with g_t = dg/dtheta etc.; for sigma, Q = alpha / sigma (and its x, y, xy    */
+/* derivatives alike).  A clamped alpha (0.99) is a constant: Q = 0.           */
+/* g2d layout per Gaussian: (mean_x, mean_y, conic a, conic b, conic c,        */
+/* opacity, r, g, b); b is the off-diagonal entry of the conic.               */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    uint32_t id;
+    int clamped;
+    double alpha, ax, ay, axy;
+    double A, Ax, Ay, Axy;    /* state before the step */
+    double dx, dy, gx, gy;
+} TapeStep;
+
+typedef struct {
+    const RenderCtx* c;
+    int64_t p0, p1;
+    const int32_t* pix;
+    const double* dout;    /* [npix][12] */
+    double* g2d;           /* this worker's accumulator [n][9] */
+    double* b2f;           /* [npix][12] back-to-front image, or NULL */
+    TapeStep* tape;
+    int64_t tape_cap;
+} AdjJob;
+
+static void adjoint_pixel(AdjJob* jb, int ix, int iy, const double u[12], double b2f[12])
+{
+    const RenderCtx* c = jb->c;
+    const double px = ix + c->off_x, py = iy + c->off_y;
+    const int64_t t = (int64_t)(iy / c->tile) * c->tiles_x + (ix / c->tile);
+    const uint32_t start = c->ranges[2 * t], end = c->ranges[2 * t + 1];
+    /* forward replay: the decisions of blend_pixel (no flips) */
+    double A = 0.0, Ax = 0.0, Ay = 0.0, Axy = 0.0;
+    int64_t ns = 0;
+    for (uint32_t j = 0; j < end - start; ++j) {
+        const uint32_t id = c->vals[start + j];
+        const double dx = px - c->mean2d[2 * id], dy = py - c->mean2d[2 * id + 1];
+        const double a = c->conic[3 * id], b = c->conic[3 * id + 1], cc = c->conic[3 * id + 2];
+        const double g = -0.5 * (a * dx * dx + 2.0 * b * dx * dy + cc * dy * dy);
+        const double gx = -(a * dx + b * dy), gy = -(b * dx + cc * dy), gxy = -b;
+        double alpha = c->opacity[id] * exp(g);
+        double ax = alpha * gx, ay = alpha * gy, axy = alpha * (gx * gy + gxy);
+        int clamped = 0;
+        if (c->mode == MODE_3DGS) {
+            if (alpha < 1.0 / 255.0) continue;
+            if (alpha > 0.99) { clamped = 1; alpha = 0.99; ax = 0.0; ay = 0.0; axy = 0.0; }
+            if ((1.0 - A) * (1.0 - alpha) < 1e-4) break;
+        }
+        TapeStep* s = jb->tape + ns++;
+        s->id = id; s->clamped = clamped;
+        s->alpha = alpha; s->ax = ax; s->ay = ay; s->axy = axy;
+        s->A = A; s->Ax = Ax; s->Ay = Ay; s->Axy = Axy;
+        s->dx = dx; s->dy = dy; s->gx = gx; s->gy = gy;
+        const double T = 1.0 - A;
+        const double Axy_n = Axy * (1.0 - alpha) + T * axy - Ax * ay - Ay * ax;
+        const double Ax_n = Ax * (1.0 - alpha) + T * ax;
+        const double Ay_n = Ay * (1.0 - alpha) + T * ay;
+        A = A + alpha * T; Ax = Ax_n; Ay = Ay_n; Axy = Axy_n;
+    }
+    /* back to front */
+    double Bh[3], Bx[3], By[3], Bxy[3];
+    for (int k = 0; k < 3; ++k) { Bh[k] = c->bg[k]; Bx[k] = 0.0; By[k] = 0.0; Bxy[k] = 0.0; }
+    for (int64_t k = ns - 1; k >= 0; --k) {
+        const TapeStep* s = jb->tape + k;
+        const uint32_t id = s->id;
+        const double T = 1.0 - s->A, Tx = -s->Ax, Ty = -s->Ay, Txy = -s->Axy;
+        const double al = s->alpha, ax = s->ax, ay = s->ay, axy = s->axy;
+        const double a = c->conic[3 * id], b = c->conic[3 * id + 1], cc = c->conic[3 * id + 2];
+        const double dx = s->dx, dy = s->dy, gx = s->gx, gy = s->gy, gxy = -b;
+        /* dg/dtheta, d2g/(dtheta dx), d2g/(dtheta dy), d3g/(dtheta dx dy) for
+         * theta = mean_x, mean_y, a, b, c */
+        const double gt[5] = {a * dx + b * dy, b * dx + cc * dy, -0.5 * dx * dx, -dx * dy, -0.5 * dy * dy};
+        const double gtx[5] = {a, b, -dx, -dy, 0.0};
+        const double gty[5] = {b, cc, 0.0, -dx, -dy};
+        const double gtxy[5] = {0.0, 0.0, 0.0, -1.0, 0.0};
+        double Q[6], Qx[6], Qy[6], Qxy[6];
+        for (int p = 0; p < 5; ++p) {
+            if (s->clamped) { Q[p] = Qx[p] = Qy[p] = Qxy[p] = 0.0; continue; }
+            const double hx = gx * gt[p] + gtx[p];
+            Q[p] = al * gt[p];
+            Qx[p] = al * hx;
+            Qy[p] = al * (gy * gt[p] + gty[p]);
+            Qxy[p] = al * (gy * hx + gxy * gt[p] + gx * gty[p] + gtxy[p]);
+        }
+        const double sig = c->opacity[id];
+        if (s->clamped || !(sig > 0.0)) { Q[5] = Qx[5] = Qy[5] = Qxy[5] = 0.0; }
+        else { Q[5] = al / sig; Qx[5] = ax / sig; Qy[5] = ay / sig; Qxy[5] = axy / sig; }
+        double* acc = jb->g2d + 9 * (int64_t)id;
+        for (int ch = 0; ch < 3; ++ch) {
+            const double col = c->rgb[3 * id + ch];
+            const double D = col - Bh[ch];
+            const double P = T * D;
+            const double Px = Tx * D - T * Bx[ch];
+            const double Py = Ty * D - T * By[ch];
+            const double Pxy = Txy * D - Tx * By[ch] - Ty * Bx[ch] - T * Bxy[ch];
+            const double uC = u[ch], uX = u[3 + ch], uY = u[6 + ch], uZ = u[9 + ch];
+            for (int p = 0; p < 6; ++p)
+                acc[p] += uC * P * Q[p] + uX * (Px * Q[p] + P * Qx[p]) + uY * (Py * Q[p] + P * Qy[p]) +
+                          uZ * (Pxy * Q[p] + Px * Qy[p] + Py * Qx[p] + P * Qxy[p]);
+            const double dc = T * al, dcx = Tx * al + T * ax, dcy = Ty * al + T * ay;
+            const double dcxy = Txy * al + Tx * ay + Ty * ax + T * axy;
+            acc[6 + ch] += uC * dc + uX * dcx + uY * dcy + uZ * dcxy;
+            /* B^_k from B^_{k+1} */
+            const double nBxy = (1.0 - al) * Bxy[ch] + axy * D - ay * Bx[ch] - ax * By[ch];
+            const double nBx = (1.0 - al) * Bx[ch] + ax * D;
+            const double nBy = (1.0 - al) * By[ch] + ay * D;
+            const double nB = (1.0 - al) * Bh[ch] + al * col;
+            Bh[ch] = nB; Bx[ch] = nBx; By[ch] = nBy; Bxy[ch] = nBxy;
+        }
+    }
+    if (b2f)
+        for (int k = 0; k < 3; ++k) { b2f[k] = Bh[k]; b2f[3 + k] = Bx[k]; b2f[6 + k] = By[k]; b2f[9 + k] = Bxy[k]; }
+}
+
+static void* adjoint_worker(void* arg)
+{
+    AdjJob* jb = (AdjJob*)arg;
+    const RenderCtx* c = jb->c;
+    for (int64_t p = jb->p0; p < jb->p1; ++p) {
+        int ix, iy;
+        if (jb->pix) { ix = jb->pix[2 * p]; iy = jb->pix[2 * p + 1]; }
+        else { ix = (int)(p % c->W); iy = (int)(p / c->W); }
+        adjoint_pixel(jb, ix, iy, jb->dout + 12 * p, jb->b2f ? jb->b2f + 12 * p : NULL);
+    }
+    return NULL;
+}
+
+int ora_render_adjoint(int W, int H, int tile, int mode, const double* bg,
+                       const double* mean2d, const double* conic, const double* opacity, const double* rgb,
+                       const uint32_t* vals, const uint32_t* ranges, int64_t n,
+                       int64_t npix, const int32_t* pix, const double* dout,
+                       double* g2d, double* b2f, int nthreads)
+{
+    if (W < 1 || H < 1 || tile < 1 || npix < 0 || n < 0) return ORA_EINVAL;
+    if (pix == NULL && npix != (int64_t)W * H) return ORA_EINVAL;
+    if (pix != NULL)
+        for (int64_t p = 0; p < npix; ++p)
+            if (pix[2 * p] < 0 || pix[2 * p] >= W || pix[2 * p + 1] < 0 || pix[2 * p + 1] >= H) return ORA_EINVAL;
+    RenderCtx c;
+    c.W = W; c.H = H; c.tile = tile; c.tiles_x = (W + tile - 1) / tile; c.mode = mode;
+    for (int k = 0; k < 3; ++k) c.bg[k] = bg ? bg[k] : 0.0;
+    c.off_x = 0.0; c.off_y = 0.0;
+    c.mean2d = mean2d; c.conic = conic; c.opacity = opacity; c.rgb = rgb;
+    c.vals = vals; c.ranges = ranges;
+    /* the longest tile list bounds a pixel's tape */
+    const int64_t T = (int64_t)c.tiles_x * ((H + tile - 1) / tile);
+    int64_t cap = 1;
+    for (int64_t k = 0; k < T; ++k)
+        if ((int64_t)(ranges[2 * k + 1] - ranges[2 * k]) > cap) cap = ranges[2 * k + 1] - ranges[2 * k];
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    if ((int64_t)nthreads > npix) nthreads = npix > 0 ? (int)npix : 1;
+    AdjJob jobs[256];
+    pthread_t th[256];
+    int st = ORA_OK;
+    for (int k = 0; k < nthreads; ++k) {
+        jobs[k].c = &c;
+        jobs[k].p0 = npix * k / nthreads;
+        jobs[k].p1 = npix * (k + 1) / nthreads;
+        jobs[k].pix = pix; jobs[k].dout = dout; jobs[k].b2f = b2f;
+        jobs[k].g2d = (double*)calloc((size_t)(n > 0 ? n : 1) * 9, sizeof(double));
+        jobs[k].tape = (TapeStep*)malloc(sizeof(TapeStep) * (size_t)cap);
+        jobs[k].tape_cap = cap;
+        if (!jobs[k].g2d || !jobs[k].tape) st = ORA_ENOMEM;
+    }
+    if (st == ORA_OK) {
+        for (int k = 1; k < nthreads; ++k) pthread_create(&th[k], NULL, adjoint_worker, &jobs[k]);
+        adjoint_worker(&jobs[0]);
+        for (int k = 1; k < nthreads; ++k) pthread_join(th[k], NULL);
+        for (int64_t q = 0; q < 9 * n; ++q) {
+            double s = 0.0;
+            for (int k = 0; k < nthreads; ++k) s += jobs[k].g2d[q];
+            g2d[q] = s;
+        }
+    }
+    for (int k = 0; k < nthreads; ++k) { free(jobs[k].g2d); free(jobs[k].tape); }
+    return st;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Adjoint of the projection, by forward-mode differentiation of its          */
+/* definition: every input of a Gaussian is seeded in turn with dual numbers   */
+/* (value, derivative), the projection of ora_project is evaluated in dual     */
+/* arithmetic, and the derivatives of (mean2D, conic, opacity, colour) are     */
+/* contracted with the upstream g2d row.  Piecewise functions (the frustum     */
+/* clamp of J, max(0, .) of the colour) take the derivative of the branch the  */
+/* value takes.                                                                */
+/* ------------------------------------------------------------------------- */
+
+typedef struct { double v, d; } Dual;
+
+static Dual dc(double v) { Dual r = {v, 0.0}; return r; }
+static Dual dadd(Dual a, Dual b) { Dual r = {a.v + b.v, a.d + b.d}; return r; }
+static Dual dsub(Dual a, Dual b) { Dual r = {a.v - b.v, a.d - b.d}; return r; }
+static Dual dmul(Dual a, Dual b) { Dual r = {a.v * b.v, a.d * b.v + a.v * b.d}; return r; }
+static Dual ddiv(Dual a, Dual b) { Dual r = {a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)}; return r; }
+static Dual dscale(Dual a, double s) { Dual r = {a.v * s, a.d * s}; return r; }
+static Dual dsqrt(Dual a) { double s = sqrt(a.v); Dual r = {s, a.d / (2.0 * s)}; return r; }
+static Dual dexp(Dual a) { double e = exp(a.v); Dual r = {e, a.d * e}; return r; }
+static Dual dcos(Dual a) { Dual r = {cos(a.v), -sin(a.v) * a.d}; return r; }
+static Dual dsin(Dual a) { Dual r = {sin(a.v), cos(a.v) * a.d}; return r; }
+static Dual datan2(Dual y, Dual x)
+{
+    Dual r = {atan2(y.v, x.v), (x.v * y.d - y.v * x.d) / (x.v * x.v + y.v * y.v)};
+    return r;
+}
+static Dual dclamp(Dual a, double lo, double hi)
+{
+    if (a.v < lo) return dc(lo);
+    if (a.v > hi) return dc(hi);
+    return a;
+}
+
+/* P_l^m(x) in dual arithmetic (same recurrences as legendre_p) */
+static Dual legendre_dual(int l, int m, Dual x)
+{
+    Dual s = dsqrt(dclamp(dsub(dc(1.0), dmul(x, x)), 0.0, 1.0));
+    Dual p_mm = dc(1.0);
+    for (int i = 1; i <= m; ++i) p_mm = dmul(p_mm, dscale(s, -(double)(2 * i - 1)));
+    if (l == m) return p_mm;
+    Dual p_prev = p_mm;
+    Dual p_cur = dmul(dscale(x, (double)(2 * m + 1)), p_mm);
+    for (int ll = m + 2; ll <= l; ++ll) {
+        Dual t1 = dmul(dscale(x, (double)(2 * ll - 1)), p_cur);
+        Dual t2 = dscale(p_prev, (double)(ll + m - 1));
+        Dual p_next = dscale(dsub(t1, t2), 1.0 / (double)(ll - m));
+        p_prev = p_cur;
+        p_cur = p_next;
+    }
+    return p_cur;
+}
+
+static void sh_basis_dual(int deg, const Dual dir[3], Dual* out)
+{
+    Dual nrm = dsqrt(dadd(dadd(dmul(dir[0], dir[0]), dmul(dir[1], dir[1])), dmul(dir[2], dir[2])));
+    Dual x = ddiv(dir[0], nrm), y = ddiv(dir[1], nrm), z = ddiv(dir[2], nrm);
+    Dual ct = dclamp(z, -1.0, 1.0);
+    Dual ph = datan2(y, x);
+    for (int l = 0; l <= deg; ++l)
+        for (int m = -l; m <= l; ++m) {
+            int am = m < 0 ? -m : m;
+            double K = sqrt((2.0 * l + 1.0) / (4.0 * M_PI) * fact(l - am) / fact(l + am));
+            Dual P = legendre_dual(l, am, ct);
+            Dual v;
+            if (m == 0) v = dscale(P, K);
+            else if (m > 0) v = dmul(dscale(P, sqrt(2.0) * K), dcos(dscale(ph, (double)am)));
+            else v = dmul(dscale(P, sqrt(2.0) * K), dsin(dscale(ph, (double)am)));
+            out[l * l + l + m] = v;
+        }
+}
+
+typedef struct {
+    double Rv[3][3], tv[3], campos[3];
+    double fx, fy, cx, cy, znear, lim_x, lim_y;
+} OraCam;
+
+/* out: mean_x, mean_y, conic a, b, c, opacity, r, g, b.  Returns 0 if culled. */
+static int project_one_dual(const OraCam* cam, const Dual mu[3], const Dual ls[3], const Dual q[4], Dual ol,
+                            const Dual* sh, int deg, const Dual* rgb_in, Dual out[9])
+{
+    Dual p[3];
+    for (int r = 0; r < 3; ++r)
+        p[r] = dadd(dadd(dadd(dscale(mu[0], cam->Rv[r][0]), dscale(mu[1], cam->Rv[r][1])),
+                         dscale(mu[2], cam->Rv[r][2])), dc(cam->tv[r]));
+    if (p[2].v <= cam->znear) return 0;
+    Dual qn = dsqrt(dadd(dadd(dmul(q[0], q[0]), dmul(q[1], q[1])), dadd(dmul(q[2], q[2]), dmul(q[3], q[3]))));
+    if (!(qn.v > 0.0)) return 0;
+    Dual w = ddiv(q[0], qn), x = ddiv(q[1], qn), y = ddiv(q[2], qn), z = ddiv(q[3], qn);
+    Dual two = dc(2.0), one = dc(1.0);
+    Dual R[3][3] = {
+        {dsub(one, dmul(two, dadd(dmul(y, y), dmul(z, z)))), dmul(two, dsub(dmul(x, y), dmul(w, z))),
+         dmul(two, dadd(dmul(x, z), dmul(w, y)))},
+        {dmul(two, dadd(dmul(x, y), dmul(w, z))), dsub(one, dmul(two, dadd(dmul(x, x), dmul(z, z)))),
+         dmul(two, dsub(dmul(y, z), dmul(w, x)))},
+        {dmul(two, dsub(dmul(x, z), dmul(w, y))), dmul(two, dadd(dmul(y, z), dmul(w, x))),
+         dsub(one, dmul(two, dadd(dmul(x, x), dmul(y, y))))}};
+    Dual s2[3];
+    for (int k = 0; k < 3; ++k) { Dual s = dexp(ls[k]); s2[k] = dmul(s, s); }
+    Dual Sig[3][3];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            Dual acc = dc(0.0);
+            for (int k = 0; k < 3; ++k) acc = dadd(acc, dmul(dmul(R[r][k], s2[k]), R[c][k]));
+            Sig[r][c] = acc;
+        }
+    Dual tz = p[2];
+    Dual txz = dclamp(ddiv(p[0], tz), -cam->lim_x, cam->lim_x);
+    Dual tyz = dclamp(ddiv(p[1], tz), -cam->lim_y, cam->lim_y);
+    Dual J[2][3] = {{ddiv(dc(cam->fx), tz), dc(0.0), dscale(ddiv(txz, tz), -cam->fx)},
+                    {dc(0.0), ddiv(dc(cam->fy), tz), dscale(ddiv(tyz, tz), -cam->fy)}};
+    Dual M[2][3];
+    for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 3; ++c)
+            M[r][c] = dadd(dadd(dscale(J[r][0], cam->Rv[0][c]), dscale(J[r][1], cam->Rv[1][c])),
+                           dscale(J[r][2], cam->Rv[2][c]));
+    Dual S2[2][2];
+    for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 2; ++c) {
+            Dual acc = dc(0.0);
+            for (int k = 0; k < 3; ++k)
+                for (int l = 0; l < 3; ++l) acc = dadd(acc, dmul(dmul(M[r][k], Sig[k][l]), M[c][l]));
+            S2[r][c] = acc;
+        }
+    S2[0][0] = dadd(S2[0][0], dc(0.3));
+    S2[1][1] = dadd(S2[1][1], dc(0.3));
+    Dual det = dsub(dmul(S2[0][0], S2[1][1]), dmul(S2[0][1], S2[1][0]));
+    if (!(det.v > 0.0)) return 0;
+    out[0] = dadd(dscale(ddiv(p[0], p[2]), cam->fx), dc(cam->cx));
+    out[1] = dadd(dscale(ddiv(p[1], p[2]), cam->fy), dc(cam->cy));
+    out[2] = ddiv(S2[1][1], det);
+    out[3] = dscale(ddiv(S2[0][1], det), -1.0);
+    out[4] = ddiv(S2[0][0], det);
+    out[5] = ddiv(dc(1.0), dadd(dc(1.0), dexp(dscale(ol, -1.0))));
+    if (sh) {
+        Dual dir[3];
+        for (int k = 0; k < 3; ++k) dir[k] = dsub(mu[k], dc(cam->campos[k]));
+        Dual Y[16];
+        sh_basis_dual(deg, dir, Y);
+        const int K = (deg + 1) * (deg + 1);
+        for (int ch = 0; ch < 3; ++ch) {
+            Dual acc = dc(0.0);
+            for (int k = 0; k < K; ++k) acc = dadd(acc, dmul(sh[3 * k + ch], Y[k]));
+            acc = dadd(acc, dc(0.5));
+            out[6 + ch] = acc.v > 0.0 ? acc : dc(0.0);
+        }
+    } else {
+        for (int ch = 0; ch < 3; ++ch) out[6 + ch] = rgb_in[ch];
+    }
+    return 1;
+}
+
+/* g2d: [n][9] upstream; outputs (overwritten): g_means [n][3], g_log_scales
+ * [n][3], g_quats [n][4], g_opacity_logits [n], g_sh [n][K][3] (if sh) or
+ * g_rgb [n][3] (if rgb_in). */
+int ora_project_adjoint(int64_t n, const double* means, const double* log_scales, const double* quats,
+                        const double* opacity_logits, const double* sh, int sh_degree, const double* rgb_in,
+                        const double* viewmat, double fx, double fy, double cx, double cy, double znear,
+                        int W, int H, const double* g2d,
+                        double* g_means, double* g_log_scales, double* g_quats, double* g_opacity_logits,
+                        double* g_sh, double* g_rgb)
+{
+    if (n < 0 || W < 1 || H < 1 || sh_degree < 0 || sh_degree > 3) return ORA_EINVAL;
+    if (sh == NULL && rgb_in == NULL && n > 0) return ORA_EINVAL;
+    OraCam cam;
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) cam.Rv[r][c] = viewmat[4 * r + c];
+        cam.tv[r] = viewmat[4 * r + 3];
+    }
+    for (int c = 0; c < 3; ++c)
+        cam.campos[c] = -(cam.Rv[0][c] * cam.tv[0] + cam.Rv[1][c] * cam.tv[1] + cam.Rv[2][c] * cam.tv[2]);
+    cam.fx = fx; cam.fy = fy; cam.cx = cx; cam.cy = cy; cam.znear = znear;
+    cam.lim_x = 1.3 * ((double)W / (2.0 * fx));
+    cam.lim_y = 1.3 * ((double)H / (2.0 * fy));
+    const int K = (sh_degree + 1) * (sh_degree + 1);
+    const int ncol = sh ? 3 * K : 3;
+    const int npar = 3 + 3 + 4 + 1 + ncol;
+    for (int64_t i = 0; i < n; ++i) {
+        double grad[3 + 3 + 4 + 1 + 48];
+        for (int j = 0; j < npar; ++j) {
+            Dual mu[3], ls[3], q[4], ol, col[48];
+            for (int k = 0; k < 3; ++k) { mu[k] = dc(means[3 * i + k]); ls[k] = dc(log_scales[3 * i + k]); }
+            for (int k = 0; k < 4; ++k) q[k] = dc(quats[4 * i + k]);
+            ol = dc(opacity_logits[i]);
+            for (int k = 0; k < ncol; ++k) col[k] = dc(sh ? sh[i * ncol + k] : rgb_in[3 * i + k]);
+            if (j < 3) mu[j].d = 1.0;
+            else if (j < 6) ls[j - 3].d = 1.0;
+            else if (j < 10) q[j - 6].d = 1.0;
+            else if (j == 10) ol.d = 1.0;
+            else col[j - 11].d = 1.0;
+            Dual out[9];
+            double gj = 0.0;
+            if (project_one_dual(&cam, mu, ls, q, ol, sh ? col : NULL, sh_degree, sh ? NULL : col, out))
+                for (int k = 0; k < 9; ++k) gj += g2d[9 * i + k] * out[k].d;
+            grad[j] = gj;
+        }
+        for (int k = 0; k < 3; ++k) { g_means[3 * i + k] = grad[k]; g_log_scales[3 * i + k] = grad[3 + k]; }
+        for (int k = 0; k < 4; ++k) g_quats[4 * i + k] = grad[6 + k];
+        g_opacity_logits[i] = grad[10];
+        for (int k = 0; k < ncol; ++k) {
+            if (sh && g_sh) g_sh[i * ncol + k] = grad[11 + k];
+            if (!sh && g_rgb) g_rgb[3 * i + k] = grad[11 + k];
         }
     }
     return ORA_OK;
