@@ -86,6 +86,19 @@ typedef struct gs_gaussians {
     const float* rgb;
 } gs_gaussians;
 
+/* Gradients of a scalar loss with respect to the inputs of gs_gaussians
+ * (caller-owned device fp32 arrays of the same shapes; overwritten).  sh is
+ * written when the projected Gaussians used SH, rgb when they used direct
+ * colours; either may be NULL to skip it. */
+typedef struct gs_gaussian_grads {
+    float* means;
+    float* log_scales;
+    float* quats;
+    float* opacity_logits;
+    float* sh;
+    float* rgb;
+} gs_gaussian_grads;
+
 /* Pinhole camera, passed by value from the host.  viewmat: row-major 4x4
  * world->camera (x right, y down, z forward); pixel = (fx x/z + cx, fy y/z + cy);
  * Gaussians with view depth z <= znear are culled. */
@@ -163,6 +176,39 @@ gs_status gs_render(gs_ctx* ctx, const gs_gaussians* g, const gs_camera* cam,
  * Asynchronous. */
 gs_status gs_upscale(gs_ctx* ctx, const float* C, const float* grads, int32_t W, int32_t H,
                      int32_t factor, float* out);
+
+/* ---- Reverse mode (training with differentiable upscaling; supplement
+ * "Backward Pass").  All gradients are of one scalar loss L; upstream arrays
+ * hold dL/d(output).  Asynchronous on the context's stream. */
+
+/* Adjoint of gs_upscale (a linear map): dL_dout [3][factor*H][factor*W] ->
+ * dL_dC [3][H][W] and dL_dgrads [3 (d/dx, d/dy, d2/dxdy)][3][H][W], overwritten.
+ * Each low-res value gathers the output pixels whose cell has it as a corner,
+ * weighted by the same Hermite basis; no atomics.  W, H >= 2; 1 <= factor <= 16. */
+gs_status gs_upscale_backward(gs_ctx* ctx, const float* dL_dout, int32_t W, int32_t H, int32_t factor,
+                              float* dL_dC, float* dL_dgrads);
+
+/* Adjoint of the last derivative blend (gs_render_with_grads, or
+ * gs_render_binned with out_grads, after gs_project): upstream dL_dC [3][H][W]
+ * and dL_dgrads [3][3][H][W] (dL_dgrads may be NULL: zero) -> grad2d [n][9],
+ * overwritten: dL/d(mean_x, mean_y, conic a, conic b, conic c, opacity, r, g, b)
+ * per Gaussian, with g = -1/2 (a dx^2 + 2 b dx dy + c dy^2) (b the off-diagonal
+ * entry).  Per pixel the tile list is walked back to front from the last
+ * blended Gaussian, with the blend state before each step recovered from the
+ * stored final state by inverting T -> T (1 - alpha) (the inversion trick of
+ * the supplement, written for T = 1 - A).  GS_ERR_NOT_READY without such a
+ * blend since the last projection or option change. */
+gs_status gs_render_backward(gs_ctx* ctx, const float* dL_dC, const float* dL_dgrads, float* grad2d);
+
+/* Adjoint of the last gs_project: grad2d [n][9] (the layout above) -> the
+ * gradients of the projected Gaussians' inputs.  The arrays passed to that
+ * gs_project must still hold the same values.  Culled Gaussians get zeros. */
+gs_status gs_project_backward(gs_ctx* ctx, const float* grad2d, const gs_gaussian_grads* out);
+
+/* The whole chain of the last project -> derivative blend -> upscale by
+ * factor: gs_upscale_backward into context scratch, gs_render_backward,
+ * gs_project_backward.  dL_dout [3][factor*H][factor*W]. */
+gs_status gs_backward(gs_ctx* ctx, const float* dL_dout, int32_t factor, const gs_gaussian_grads* out);
 
 /* gs_render_with_grads for callers that cannot allocate device memory (an
  * engine or compositor that owns every device byte, a plugin restricted to

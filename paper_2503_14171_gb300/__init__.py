@@ -49,6 +49,11 @@ class GsOptions(ct.Structure):
                 ("reserved", ct.c_int32), ("max_pairs", ct.c_int64)]
 
 
+class GsGaussianGrads(ct.Structure):
+    _fields_ = [("means", ct.c_void_p), ("log_scales", ct.c_void_p), ("quats", ct.c_void_p),
+                ("opacity_logits", ct.c_void_p), ("sh", ct.c_void_p), ("rgb", ct.c_void_p)]
+
+
 # name -> argtypes (all return gs_status except gs_status_string / gs_last_error)
 _P = ct.c_void_p
 _SIGS = {
@@ -71,6 +76,10 @@ _SIGS = {
     "gs_launch_count": ([_P, ct.POINTER(ct.c_int64)], ct.c_int),
     "gs_blend_stats": ([_P, _P], ct.c_int),
     "gs_synchronize": ([_P], ct.c_int),
+    "gs_upscale_backward": ([_P, _P, ct.c_int32, ct.c_int32, ct.c_int32, _P, _P], ct.c_int),
+    "gs_render_backward": ([_P, _P, _P, _P], ct.c_int),
+    "gs_project_backward": ([_P, _P, ct.POINTER(GsGaussianGrads)], ct.c_int),
+    "gs_backward": ([_P, _P, ct.c_int32, ct.POINTER(GsGaussianGrads)], ct.c_int),
     "gs_render_with_grads_noalloc": ([ct.POINTER(GsGaussians), ct.POINTER(GsCamera), ct.c_int32, ct.c_int32,
                                       ct.POINTER(GsOptions), _P, _P, _P], ct.c_int),
 }
@@ -152,6 +161,22 @@ def gs_upscale(ctx, C: int, grads: int, W: int, H: int, factor: int, out: int):
 
 def gs_synchronize(ctx):
     _chk(lib.gs_synchronize(ctx), ctx, "gs_synchronize")
+
+
+def gs_upscale_backward(ctx, dL_dout: int, W: int, H: int, factor: int, dL_dC: int, dL_dgrads: int):
+    _chk(lib.gs_upscale_backward(ctx, dL_dout, W, H, factor, dL_dC, dL_dgrads), ctx, "gs_upscale_backward")
+
+
+def gs_render_backward(ctx, dL_dC: int, dL_dgrads: int | None, grad2d: int):
+    _chk(lib.gs_render_backward(ctx, dL_dC, dL_dgrads, grad2d), ctx, "gs_render_backward")
+
+
+def gs_project_backward(ctx, grad2d: int, out: GsGaussianGrads):
+    _chk(lib.gs_project_backward(ctx, grad2d, ct.byref(out)), ctx, "gs_project_backward")
+
+
+def gs_backward(ctx, dL_dout: int, factor: int, out: GsGaussianGrads):
+    _chk(lib.gs_backward(ctx, dL_dout, factor, ct.byref(out)), ctx, "gs_backward")
 
 
 def gs_render_with_grads_noalloc(g: GsGaussians, cam: GsCamera, W: int, H: int, options: GsOptions | None,
@@ -279,7 +304,7 @@ class Context:
 
     def project(self, scene: DeviceScene, cam: dict, W: int, H: int):
         gs_project(self.h, scene.struct, make_camera(cam), W, H)
-        self.W, self.H, self.n = W, H, scene.n
+        self.W, self.H, self.n, self.scene = W, H, scene.n, scene
 
     def render_binned(self, grads: bool = True, out_C=None, out_grads=None):
         C = out_C if out_C is not None else self._empty(3, self.H, self.W)
@@ -293,13 +318,13 @@ class Context:
         C = out_C if out_C is not None else self._empty(3, H, W)
         G = out_grads if out_grads is not None else self._empty(3, 3, H, W)
         gs_render_with_grads(self.h, scene.struct, make_camera(cam), W, H, C.data_ptr(), G.data_ptr())
-        self.W, self.H, self.n = W, H, scene.n
+        self.W, self.H, self.n, self.scene = W, H, scene.n, scene
         return C, G
 
     def render(self, scene: DeviceScene, cam: dict, W: int, H: int, out_C=None):
         C = out_C if out_C is not None else self._empty(3, H, W)
         gs_render(self.h, scene.struct, make_camera(cam), W, H, C.data_ptr())
-        self.W, self.H, self.n = W, H, scene.n
+        self.W, self.H, self.n, self.scene = W, H, scene.n, scene
         return C
 
     def upscale(self, C, grads, factor: int, out=None):
@@ -356,3 +381,94 @@ class Context:
 
     def synchronize(self):
         gs_synchronize(self.h)
+
+    # ---- reverse mode ----------------------------------------------------------
+
+    def upscale_backward(self, dout, W: int, H: int, factor: int, out=None):
+        """dL/d(upscaled image) [3, sH, sW] -> (dL/dC [3, H, W], dL/dgrads [3, 3, H, W])."""
+        assert dout.is_contiguous()
+        dC, dG = out if out is not None else (self._empty(3, H, W), self._empty(3, 3, H, W))
+        gs_upscale_backward(self.h, dout.data_ptr(), W, H, factor, dC.data_ptr(), dG.data_ptr())
+        return dC, dG
+
+    def render_backward(self, dC, dG=None, out=None):
+        """Adjoint of the last derivative blend: -> grad2d [n, 9] (mean_x, mean_y,
+        conic a, b, c, opacity, r, g, b)."""
+        assert dC.is_contiguous() and (dG is None or dG.is_contiguous())
+        g2 = out if out is not None else self._empty(max(self.n, 1), 9)
+        gs_render_backward(self.h, dC.data_ptr(), dG.data_ptr() if dG is not None else None, g2.data_ptr())
+        return g2[:self.n]
+
+    def _grads_like(self, out=None):
+        out = out if out is not None else {k: _torch().empty_like(v) for k, v in self.scene.t.items()}
+        g = GsGaussianGrads()
+        for k in DeviceScene.FIELDS:
+            v = out.get(k)
+            setattr(g, k, v.data_ptr() if v is not None and v.numel() > 0 else None)
+        return out, g
+
+    def project_backward(self, grad2d, out=None) -> dict:
+        """Adjoint of the last projection: grad2d [n, 9] -> gradients of the scene's tensors."""
+        assert grad2d.is_contiguous()
+        out, g = self._grads_like(out)
+        gs_project_backward(self.h, grad2d.data_ptr(), g)
+        return out
+
+    def backward(self, dout, factor: int, out=None) -> dict:
+        """The whole chain (upscale, blend, projection) for dL/d(upscaled image)."""
+        assert dout.is_contiguous()
+        out, g = self._grads_like(out)
+        gs_backward(self.h, dout.data_ptr(), factor, g)
+        return out
+
+
+def _render_upscale_function():
+    torch = _torch()
+
+    class RenderUpscale(torch.autograd.Function):
+        """Upscaled image of the Gaussians, differentiable in their tensors.
+
+        forward(context, cam, W, H, factor, means, log_scales, quats,
+        opacity_logits, colour) renders W x H with derivatives and upscales by
+        factor; colour is the SH tensor [n, K, 3] (sh_degree from its K) or
+        direct RGB [n, 3].  backward runs gs_backward.
+        """
+
+        @staticmethod
+        def forward(actx, gctx, cam, W, H, factor, means, log_scales, quats, opacity_logits, colour):
+            t = dict(means=means.contiguous(), log_scales=log_scales.contiguous(), quats=quats.contiguous(),
+                     opacity_logits=opacity_logits.contiguous())
+            scene = {}
+            if colour.dim() == 3:
+                t["sh"] = colour.contiguous()
+                scene["sh_degree"] = int(round(colour.shape[1] ** 0.5)) - 1
+            else:
+                t["rgb"] = colour.contiguous()
+            dev = DeviceScene(scene, tensors=t)
+            dev.sh_degree = scene.get("sh_degree", 0) if "sh" in t else 0
+            dev.struct = dev._make()
+            C, G = gctx.render_with_grads(dev, cam, W, H)
+            out = gctx.upscale(C, G, factor)
+            actx.gctx, actx.factor, actx.dev = gctx, factor, dev
+            actx.colour_key = "sh" if "sh" in t else "rgb"
+            return out
+
+        @staticmethod
+        def backward(actx, dout):
+            g = actx.gctx.backward(dout.contiguous(), actx.factor)
+            return (None, None, None, None, None, g["means"], g["log_scales"], g["quats"], g["opacity_logits"],
+                    g[actx.colour_key])
+
+    return RenderUpscale
+
+
+def render_upscale(gctx: "Context", cam: dict, W: int, H: int, factor: int, means, log_scales, quats,
+                   opacity_logits, colour):
+    """Differentiable render (W x H, with derivatives) + gradient-aware upscale by factor."""
+    global _RenderUpscale
+    if _RenderUpscale is None:
+        _RenderUpscale = _render_upscale_function()
+    return _RenderUpscale.apply(gctx, cam, W, H, factor, means, log_scales, quats, opacity_logits, colour)
+
+
+_RenderUpscale = None

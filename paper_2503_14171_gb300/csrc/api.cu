@@ -186,6 +186,8 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
 
     const Records rec{as<float4>(c->rec0), as<float4>(c->rec1), as<float4>(c->rec2)};
     const CameraParams cp = make_camera(*cam, W, H);
+    c->last_g = *g;
+    c->last_cam = cp;
     // scan_totals: [0, 2 kTotalSlots) slot pairs (super-tile pairs, tile pairs)
     // from the projection, then 2 scan totals and the scan tile counter
     unsigned long long* totals = as<unsigned long long>(c->scan_totals);
@@ -321,6 +323,7 @@ gs_status do_blend(gs_ctx* c, float* out_C, float* out_grads)
     const BlendArgs a = blend_args(c, out_C, out_grads);
     GS_CUDA(c, launch_blend(c->stream, out_grads != nullptr, c->opt.mode, a));
     c->have_state = true;
+    c->state_grads = out_grads != nullptr;
     return GS_OK;
 }
 
@@ -404,7 +407,7 @@ gs_status gs_destroy(gs_ctx* c)
                       &c->pairs[1],
                       &c->sort_hist, &c->sort_status,
                       &c->sort_counter, &c->sranges, &c->tile_count, &c->tile_start, &c->state, &c->count,
-                      &c->errword};
+                      &c->errword, &c->tile_vals, &c->tile_ranges, &c->grad2d, &c->up_planes};
     for (DevBuf* b : bufs) release(*b);
     if (c->h_scalar) cudaFreeHost(c->h_scalar);
     if (c->totals_ready) cudaEventDestroy(c->totals_ready);
@@ -479,6 +482,106 @@ gs_status gs_upscale(gs_ctx* c, const float* C, const float* grads, int32_t W, i
         return fail(c, GS_ERR_INVALID_ARG, "output too large");
     GS_CUDA(c, launch_upscale(c->stream, C, grads, W, H, factor, out));
     return GS_OK;
+}
+
+gs_status gs_upscale_backward(gs_ctx* c, const float* dL_dout, int32_t W, int32_t H, int32_t factor,
+                              float* dL_dC, float* dL_dgrads)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    LaunchTally tally(c);
+    if (!dL_dout || !dL_dC || !dL_dgrads) return fail(c, GS_ERR_INVALID_ARG, "NULL image pointer");
+    if (W < 2 || H < 2) return fail(c, GS_ERR_INVALID_ARG, "upscale needs W, H >= 2");
+    if (factor < 1 || factor > 16) return fail(c, GS_ERR_INVALID_ARG, "factor must be in 1..16");
+    if ((int64_t)W * factor > (1 << 24) || (int64_t)H * factor > (1 << 24))
+        return fail(c, GS_ERR_INVALID_ARG, "output too large");
+    GS_CUDA(c, launch_upscale_backward(c->stream, dL_dout, W, H, factor, dL_dC, dL_dgrads));
+    return GS_OK;
+}
+
+namespace {
+
+gs_status do_render_backward(gs_ctx* c, const float* dC, const float* dG, float* grad2d)
+{
+    if (!dC || !grad2d) return fail(c, GS_ERR_INVALID_ARG, "dL_dC and grad2d are required");
+    if (!c->have_proj || !c->have_state || !c->state_grads)
+        return fail(c, GS_ERR_NOT_READY, "no derivative blend since the last projection");
+    const size_t T = (size_t)c->tiles_x * c->tiles_y;
+    gs_status st;
+    if ((st = ensure(c, c->tile_count, sizeof(uint32_t) * T)) ||
+        (st = ensure(c, c->tile_start, sizeof(uint32_t) * T)) ||
+        (st = ensure(c, c->tile_ranges, sizeof(uint2) * T)) ||
+        (st = ensure(c, c->tile_vals, sizeof(uint32_t) * (size_t)std::max<int64_t>(c->P, 1))))
+        return st;
+    // the tiles' own front-to-back lists, walked back to front by the adjoint
+    GS_CUDA(c, launch_tile_lists(c->stream, as<uint64_t>(c->pairs[c->sorted_pairs_buf]), as<uint2>(c->sranges),
+                                 as<ushort4>(c->rect), as<float>(c->depth), (uint32_t)c->n, c->tiles_x, c->tiles_y,
+                                 c->stiles_x, as<uint32_t>(c->tile_count), as<uint32_t>(c->tile_start), nullptr,
+                                 as<uint32_t>(c->tile_vals), as<uint2>(c->tile_ranges)));
+    if (c->n > 0) GS_CUDA(c, cudaMemsetAsync(grad2d, 0, sizeof(float) * 9 * (size_t)c->n, c->stream));
+    BlendBwdArgs a;
+    a.W = c->W;
+    a.H = c->H;
+    a.tiles_x = c->tiles_x;
+    a.n = (uint32_t)c->n;
+    a.tranges = as<uint2>(c->tile_ranges);
+    a.tvals = as<uint32_t>(c->tile_vals);
+    a.rec = Records{as<float4>(c->rec0), as<float4>(c->rec1), as<float4>(c->rec2)};
+    a.bg = make_float3(c->opt.bg[0], c->opt.bg[1], c->opt.bg[2]);
+    a.state = as<float4>(c->state);
+    a.count = as<int>(c->count);
+    a.dC = dC;
+    a.dG = dG;
+    a.grad2d = grad2d;
+    a.err = as<int>(c->errword);
+    GS_CUDA(c, launch_blend_backward(c->stream, c->opt.mode, a));
+    return GS_OK;
+}
+
+gs_status do_project_backward(gs_ctx* c, const float* grad2d, const gs_gaussian_grads* out)
+{
+    if (!grad2d || !out) return fail(c, GS_ERR_INVALID_ARG, "grad2d and out are required");
+    if (!c->have_proj) return fail(c, GS_ERR_NOT_READY, "no projection");
+    if (c->n > 0 && (!out->means || !out->log_scales || !out->quats || !out->opacity_logits))
+        return fail(c, GS_ERR_INVALID_ARG, "means, log_scales, quats and opacity_logits gradients are required");
+    GS_CUDA(c, launch_project_backward(c->stream, c->last_g, c->last_cam, grad2d, *out));
+    return GS_OK;
+}
+
+}  // namespace
+
+gs_status gs_render_backward(gs_ctx* c, const float* dL_dC, const float* dL_dgrads, float* grad2d)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    LaunchTally tally(c);
+    return do_render_backward(c, dL_dC, dL_dgrads, grad2d);
+}
+
+gs_status gs_project_backward(gs_ctx* c, const float* grad2d, const gs_gaussian_grads* out)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    LaunchTally tally(c);
+    return do_project_backward(c, grad2d, out);
+}
+
+gs_status gs_backward(gs_ctx* c, const float* dL_dout, int32_t factor, const gs_gaussian_grads* out)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    LaunchTally tally(c);
+    if (!dL_dout || !out) return fail(c, GS_ERR_INVALID_ARG, "dL_dout and out are required");
+    if (!c->have_proj || !c->have_state || !c->state_grads)
+        return fail(c, GS_ERR_NOT_READY, "no derivative blend since the last projection");
+    if (c->W < 2 || c->H < 2) return fail(c, GS_ERR_INVALID_ARG, "upscale needs W, H >= 2");
+    if (factor < 1 || factor > 16) return fail(c, GS_ERR_INVALID_ARG, "factor must be in 1..16");
+    const size_t plane = (size_t)c->W * c->H;
+    gs_status st;
+    if ((st = ensure(c, c->up_planes, sizeof(float) * 12 * plane)) ||
+        (st = ensure(c, c->grad2d, sizeof(float) * 9 * (size_t)std::max<int64_t>(c->n, 1))))
+        return st;
+    float* dC = as<float>(c->up_planes);
+    float* dG = dC + 3 * plane;
+    GS_CUDA(c, launch_upscale_backward(c->stream, dL_dout, c->W, c->H, factor, dC, dG));
+    if ((st = do_render_backward(c, dC, dG, as<float>(c->grad2d))) != GS_OK) return st;
+    return do_project_backward(c, as<float>(c->grad2d), out);
 }
 
 gs_status gs_pair_count(const gs_ctx* c, int64_t* P)

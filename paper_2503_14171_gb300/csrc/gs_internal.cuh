@@ -66,6 +66,24 @@ struct BlendArgs {
     int* count;
 };
 
+// Adjoint of the blend: per-tile lists (materialised), the forward's final
+// per-pixel state and count, the upstream planes, and the 2D gradients
+// [n][9] = (mean_x, mean_y, conic a, b, c, opacity, r, g, b), accumulated.
+struct BlendBwdArgs {
+    int W, H, tiles_x;
+    uint32_t n;
+    const uint2* tranges;          // [tiles] [start, end) into tvals
+    const uint32_t* tvals;         // per-tile front-to-back Gaussian ids
+    Records rec;
+    float3 bg;
+    const float4* state;           // [W*H] final (T, T_x, T_y, T_xy)
+    const int* count;              // [W*H] list position after the last blended Gaussian
+    const float* dC;               // [3][H][W]
+    const float* dG;               // [3 (x, y, xy)][3][H][W]
+    float* grad2d;                 // [n][9]
+    int* err;
+};
+
 }  // namespace gs
 
 struct gs_ctx {
@@ -108,6 +126,14 @@ struct gs_ctx {
     gs::DevBuf state;                   // float4[W*H]
     gs::DevBuf count;                   // int32[W*H]
     gs::DevBuf errword;                 // int32
+    // reverse mode
+    bool state_grads = false;           // the last blend carried derivatives (its state is usable)
+    gs_gaussians last_g{};              // inputs and camera of the last projection
+    gs::CameraParams last_cam{};
+    gs::DevBuf tile_vals;               // uint32[P] per-tile lists
+    gs::DevBuf tile_ranges;             // uint2[tiles]
+    gs::DevBuf grad2d;                  // float[n][9]
+    gs::DevBuf up_planes;               // float[12][H][W] upstream planes of gs_backward
     unsigned long long* h_scalar = nullptr;   // pinned host scalar for the pair count
     int sorted_ids_buf = 0;             // which did[] holds the depth-sorted ids
     int sorted_pairs_buf = 0;           // which pairs[] holds the sorted pairs
@@ -180,6 +206,14 @@ cudaError_t launch_unpack_projected(cudaStream_t s, Records rec, const int* radi
                                     float* opacity, float* depth, int32_t* radius_out, int32_t* tiles_out);
 
 cudaError_t launch_blend(cudaStream_t s, bool grads, int mode, const BlendArgs& a);
+// adjoint of the derivative blend (grad2d accumulated; zero it first)
+cudaError_t launch_blend_backward(cudaStream_t s, int mode, const BlendBwdArgs& a);
+// adjoint of the projection: grad2d [n][9] -> gradients of the inputs (overwritten)
+cudaError_t launch_project_backward(cudaStream_t s, const gs_gaussians& g, const CameraParams& cam,
+                                    const float* grad2d, const gs_gaussian_grads& out);
+// adjoint of the upscale: dout [3][sH][sW] -> dC [3][H][W], dG [9][H][W] (overwritten)
+cudaError_t launch_upscale_backward(cudaStream_t s, const float* dout, int W, int H, int factor, float* dC,
+                                    float* dG);
 cudaError_t launch_blend_stats(cudaStream_t s, int mode, const BlendArgs& a, unsigned long long* stats);
 
 cudaError_t launch_upscale(cudaStream_t s, const float* C, const float* grads, int W, int H, int factor,

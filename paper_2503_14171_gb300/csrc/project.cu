@@ -264,6 +264,268 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
     rec.r2[i] = make_float4(col[0], col[1], col[2], op);
 }
 
+// d Y_k / d(x, y, z) of the Cartesian SH polynomials above (deg <= 3); the
+// caller projects the gradient onto the sphere's tangent plane.
+__device__ __forceinline__ void sh_basis_grad(int deg, float x, float y, float z, float Y[16], float dYx[16],
+                                              float dYy[16], float dYz[16])
+{
+#pragma unroll
+    for (int k = 0; k < 16; ++k) { Y[k] = 0.f; dYx[k] = 0.f; dYy[k] = 0.f; dYz[k] = 0.f; }
+    Y[0] = kY00;
+    if (deg >= 1) {
+        Y[1] = -kY1 * y; dYy[1] = -kY1;
+        Y[2] = kY1 * z;  dYz[2] = kY1;
+        Y[3] = -kY1 * x; dYx[3] = -kY1;
+    }
+    if (deg >= 2) {
+        const float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = kY2a * x * y;            dYx[4] = kY2a * y;  dYy[4] = kY2a * x;
+        Y[5] = -kY2a * y * z;           dYy[5] = -kY2a * z; dYz[5] = -kY2a * y;
+        Y[6] = kY2b * (3.f * zz - 1.f); dYz[6] = 6.f * kY2b * z;
+        Y[7] = -kY2a * x * z;           dYx[7] = -kY2a * z; dYz[7] = -kY2a * x;
+        Y[8] = kY2c * (xx - yy);        dYx[8] = 2.f * kY2c * x; dYy[8] = -2.f * kY2c * y;
+        if (deg >= 3) {
+            Y[9] = -kY3a * y * (3.f * xx - yy);
+            dYx[9] = -6.f * kY3a * x * y;
+            dYy[9] = -3.f * kY3a * (xx - yy);
+            Y[10] = kY3b * x * y * z;
+            dYx[10] = kY3b * y * z; dYy[10] = kY3b * x * z; dYz[10] = kY3b * x * y;
+            Y[11] = -kY3c * y * (5.f * zz - 1.f);
+            dYy[11] = -kY3c * (5.f * zz - 1.f); dYz[11] = -10.f * kY3c * y * z;
+            Y[12] = kY3d * z * (5.f * zz - 3.f);
+            dYz[12] = kY3d * (15.f * zz - 3.f);
+            Y[13] = -kY3c * x * (5.f * zz - 1.f);
+            dYx[13] = -kY3c * (5.f * zz - 1.f); dYz[13] = -10.f * kY3c * x * z;
+            Y[14] = kY3e * z * (xx - yy);
+            dYx[14] = 2.f * kY3e * x * z; dYy[14] = -2.f * kY3e * y * z; dYz[14] = kY3e * (xx - yy);
+            Y[15] = -kY3a * x * (xx - 3.f * yy);
+            dYx[15] = -3.f * kY3a * (xx - yy); dYy[15] = 6.f * kY3a * x * y;
+        }
+    }
+}
+
+// Adjoint of k_project (reverse mode, hand-derived), one thread per Gaussian.
+// Upstream g2d [n][9] = dL/d(mean_x, mean_y, conic a, b, c, opacity, r, g, b).
+// The forward quantities are recomputed, then:
+//   conic Q = Sigma'^-1:   dL/dSigma' = -Q G Q, G = [[g_a, g_b/2], [g_b/2, g_c]]
+//   Sigma' = T Sigma T^T (T = J W):  dL/dSigma = T^T G' T, dL/dT = 2 G' T Sigma
+//   J at the clamped x/z, y/z:  through T = J W to the camera-space mean p
+//   mean2D = (fx x/z + cx, fy y/z + cy);  p = W mu + t
+//   Sigma = M M^T, M = R diag(s):  dL/dM = 2 dL/dSigma M -> R and s = exp(log s)
+//   R(q / |q|): the quaternion derivatives of R, projected through the
+//   normalisation;  opacity = sigmoid(logit)
+//   colour = max(0, sum_k sh_k Y_k(d/|d|) + 1/2), d = mu - campos: dL/dsh and,
+//   through the basis' gradient on the sphere, dL/dmu.
+template <int DEG>
+__global__ void __launch_bounds__(kProjThreads) k_project_bwd(
+    int n, const float* __restrict__ means, const float* __restrict__ log_scales,
+    const float* __restrict__ quats, const float* __restrict__ op_logits, const float* __restrict__ sh,
+    CameraParams cam, const float* __restrict__ g2d, float* __restrict__ g_means, float* __restrict__ g_ls,
+    float* __restrict__ g_quats, float* __restrict__ g_ol, float* __restrict__ g_sh, float* __restrict__ g_rgb)
+{
+    constexpr int KF = DEG >= 0 ? (DEG + 1) * (DEG + 1) * 3 : 1;
+    constexpr int PITCH = KF | 1;
+    __shared__ float s_sh[kProjThreads / 32][32][PITCH];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wbase = blockIdx.x * blockDim.x + warp * 32;
+    const int wcnt = min(32, n - wbase);
+    if (DEG >= 0 && wcnt > 0) {
+        const float* src = sh + (size_t)wbase * KF;
+        for (int q = lane; q < wcnt * KF; q += 32) {
+            const int gi = q / KF;
+            s_sh[warp][gi][q - gi * KF] = src[q];
+        }
+    }
+    __syncwarp();
+    const bool inrange = i < n;
+    float gshv[DEG >= 0 ? KF : 1];
+#pragma unroll
+    for (int k = 0; k < (DEG >= 0 ? KF : 1); ++k) gshv[k] = 0.f;
+    float gm[3] = {0.f, 0.f, 0.f}, gl[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, go = 0.f;
+    float gcol[3] = {0.f, 0.f, 0.f};
+    if (inrange) {
+        float g[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) g[q] = g2d[(size_t)i * 9 + q];
+        gcol[0] = g[6]; gcol[1] = g[7]; gcol[2] = g[8];
+        const float mx3 = means[3 * i], my3 = means[3 * i + 1], mz3 = means[3 * i + 2];
+        const float px = fmaf(cam.R[0], mx3, fmaf(cam.R[1], my3, fmaf(cam.R[2], mz3, cam.t[0])));
+        const float py = fmaf(cam.R[3], mx3, fmaf(cam.R[4], my3, fmaf(cam.R[5], mz3, cam.t[1])));
+        const float pz = fmaf(cam.R[6], mx3, fmaf(cam.R[7], my3, fmaf(cam.R[8], mz3, cam.t[2])));
+        float qw = quats[4 * i], qx = quats[4 * i + 1], qy = quats[4 * i + 2], qz = quats[4 * i + 3];
+        const float qn2 = qw * qw + qx * qx + qy * qy + qz * qz;
+        bool vis = pz > cam.znear && qn2 > 0.f;
+        const float qinv = rsqrtf(qn2);
+        qw *= qinv; qx *= qinv; qy *= qinv; qz *= qinv;
+        const float sc[3] = {expf(log_scales[3 * i]), expf(log_scales[3 * i + 1]), expf(log_scales[3 * i + 2])};
+        float R[3][3] = {{1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy)},
+                         {2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx)},
+                         {2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)}};
+        float M[3][3], S[3][3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) M[r][k] = R[r][k] * sc[k];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) S[r][c] = M[r][0] * M[c][0] + M[r][1] * M[c][1] + M[r][2] * M[c][2];
+        const float iz = 1.f / pz;
+        const float rx = px * iz, ry = py * iz;
+        const bool inx = rx >= -cam.lim_x && rx <= cam.lim_x;
+        const bool iny = ry >= -cam.lim_y && ry <= cam.lim_y;
+        const float txz = fminf(cam.lim_x, fmaxf(-cam.lim_x, rx));
+        const float tyz = fminf(cam.lim_y, fmaxf(-cam.lim_y, ry));
+        const float J[2][3] = {{cam.fx * iz, 0.f, -cam.fx * txz * iz}, {0.f, cam.fy * iz, -cam.fy * tyz * iz}};
+        float Tm[2][3];
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                Tm[r][c] = J[r][0] * cam.R[c] + J[r][1] * cam.R[3 + c] + J[r][2] * cam.R[6 + c];
+        float TS[2][3];   // T Sigma
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) TS[r][c] = Tm[r][0] * S[0][c] + Tm[r][1] * S[1][c] + Tm[r][2] * S[2][c];
+        const float c00 = TS[0][0] * Tm[0][0] + TS[0][1] * Tm[0][1] + TS[0][2] * Tm[0][2] + 0.3f;
+        const float c01 = TS[0][0] * Tm[1][0] + TS[0][1] * Tm[1][1] + TS[0][2] * Tm[1][2];
+        const float c11 = TS[1][0] * Tm[1][0] + TS[1][1] * Tm[1][1] + TS[1][2] * Tm[1][2] + 0.3f;
+        const float det = c00 * c11 - c01 * c01;
+        vis = vis && det > 0.f;
+        if (vis) {
+            const float idet = 1.f / det;
+            const float Qa = c11 * idet, Qb = -c01 * idet, Qc = c00 * idet;
+            // dL/dSigma' = -Q G Q
+            const float G00 = g[2], G01 = 0.5f * g[3], G11 = g[4];
+            const float QG00 = Qa * G00 + Qb * G01, QG01 = Qa * G01 + Qb * G11;
+            const float QG10 = Qb * G00 + Qc * G01, QG11 = Qb * G01 + Qc * G11;
+            const float gS00 = -(QG00 * Qa + QG01 * Qb);
+            const float gS01 = -(QG00 * Qb + QG01 * Qc);
+            const float gS11 = -(QG10 * Qb + QG11 * Qc);
+            const float gS[2][2] = {{gS00, gS01}, {gS01, gS11}};
+            // dL/dT = 2 gS T Sigma; dL/dSigma = T^T gS T
+            float gT[2][3];
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) gT[r][c] = 2.f * (gS[r][0] * TS[0][c] + gS[r][1] * TS[1][c]);
+            float gSig[3][3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float t0 = gS[0][0] * Tm[0][c] + gS[0][1] * Tm[1][c];
+                    const float t1 = gS[1][0] * Tm[0][c] + gS[1][1] * Tm[1][c];
+                    gSig[r][c] = Tm[0][r] * t0 + Tm[1][r] * t1;
+                }
+            // T = J W: dL/dJ = dL/dT W^T (only the non-zero entries of J)
+            float gJ[2][3];
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    gJ[r][c] = gT[r][0] * cam.R[3 * c] + gT[r][1] * cam.R[3 * c + 1] + gT[r][2] * cam.R[3 * c + 2];
+            // J entries as functions of p (the clamp passes no derivative)
+            float gpx = 0.f, gpy = 0.f, gpz = 0.f;
+            gpz += gJ[0][0] * (-cam.fx * iz * iz) + gJ[1][1] * (-cam.fy * iz * iz);
+            // j02 = -fx txz / z
+            gpz += gJ[0][2] * (cam.fx * txz * iz * iz);
+            if (inx) { gpx += gJ[0][2] * (-cam.fx * iz * iz); gpz += gJ[0][2] * (cam.fx * px * iz * iz * iz); }
+            gpz += gJ[1][2] * (cam.fy * tyz * iz * iz);
+            if (iny) { gpy += gJ[1][2] * (-cam.fy * iz * iz); gpz += gJ[1][2] * (cam.fy * py * iz * iz * iz); }
+            // mean2D
+            gpx += g[0] * cam.fx * iz;
+            gpy += g[1] * cam.fy * iz;
+            gpz += -(g[0] * cam.fx * px + g[1] * cam.fy * py) * iz * iz;
+            // p = W mu + t
+#pragma unroll
+            for (int c = 0; c < 3; ++c) gm[c] = cam.R[c] * gpx + cam.R[3 + c] * gpy + cam.R[6 + c] * gpz;
+            // Sigma = M M^T
+            float gR[3][3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float gM = 2.f * (gSig[r][0] * M[0][k] + gSig[r][1] * M[1][k] + gSig[r][2] * M[2][k]);
+                    gR[r][k] = gM * sc[k];
+                    gl[k] += gM * R[r][k] * sc[k];
+                }
+            // R(q^) and the normalisation q^ = q / |q|
+            const float gw = 2.f * (-qz * gR[0][1] + qy * gR[0][2] + qz * gR[1][0] - qx * gR[1][2] - qy * gR[2][0] +
+                                    qx * gR[2][1]);
+            const float gx = 2.f * (qy * gR[0][1] + qz * gR[0][2] + qy * gR[1][0] - 2.f * qx * gR[1][1] -
+                                    qw * gR[1][2] + qz * gR[2][0] + qw * gR[2][1] - 2.f * qx * gR[2][2]);
+            const float gy = 2.f * (-2.f * qy * gR[0][0] + qx * gR[0][1] + qw * gR[0][2] + qx * gR[1][0] +
+                                    qz * gR[1][2] - qw * gR[2][0] + qz * gR[2][1] - 2.f * qy * gR[2][2]);
+            const float gz = 2.f * (-2.f * qz * gR[0][0] - qw * gR[0][1] + qx * gR[0][2] + qw * gR[1][0] -
+                                    2.f * qz * gR[1][1] + qy * gR[1][2] + qx * gR[2][0] + qy * gR[2][1]);
+            const float dotq = qw * gw + qx * gx + qy * gy + qz * gz;
+            gq[0] = (gw - qw * dotq) * qinv;
+            gq[1] = (gx - qx * dotq) * qinv;
+            gq[2] = (gy - qy * dotq) * qinv;
+            gq[3] = (gz - qz * dotq) * qinv;
+            // opacity
+            const float op = 1.f / (1.f + expf(-op_logits[i]));
+            go = g[5] * op * (1.f - op);
+            // colour
+            if (DEG >= 0) {
+                float dx = mx3 - cam.campos[0], dy = my3 - cam.campos[1], dz = mz3 - cam.campos[2];
+                const float dn = rsqrtf(dx * dx + dy * dy + dz * dz);
+                dx *= dn; dy *= dn; dz *= dn;
+                float Y[16], Yx[16], Yy[16], Yz[16];
+                sh_basis_grad(DEG, dx, dy, dz, Y, Yx, Yy, Yz);
+                const float* shv = &s_sh[warp][lane][0];
+                constexpr int K = DEG >= 0 ? (DEG + 1) * (DEG + 1) : 1;
+                float gn[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) {
+                    float acc = 0.f;
+#pragma unroll
+                    for (int k = 0; k < K; ++k) acc = fmaf(shv[3 * k + ch], Y[k], acc);
+                    const float gc = acc + 0.5f > 0.f ? gcol[ch] : 0.f;
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        gshv[3 * k + ch] = gc * Y[k];
+                        gn[0] = fmaf(gc * shv[3 * k + ch], Yx[k], gn[0]);
+                        gn[1] = fmaf(gc * shv[3 * k + ch], Yy[k], gn[1]);
+                        gn[2] = fmaf(gc * shv[3 * k + ch], Yz[k], gn[2]);
+                    }
+                }
+                const float dotn = gn[0] * dx + gn[1] * dy + gn[2] * dz;
+                gm[0] += (gn[0] - dx * dotn) * dn;
+                gm[1] += (gn[1] - dy * dotn) * dn;
+                gm[2] += (gn[2] - dz * dotn) * dn;
+            }
+        } else {
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) gcol[ch] = 0.f;
+        }
+        g_means[3 * i] = gm[0]; g_means[3 * i + 1] = gm[1]; g_means[3 * i + 2] = gm[2];
+        g_ls[3 * i] = gl[0]; g_ls[3 * i + 1] = gl[1]; g_ls[3 * i + 2] = gl[2];
+        g_quats[4 * i] = gq[0]; g_quats[4 * i + 1] = gq[1]; g_quats[4 * i + 2] = gq[2]; g_quats[4 * i + 3] = gq[3];
+        g_ol[i] = go;
+        if (DEG < 0 && g_rgb) { g_rgb[3 * i] = gcol[0]; g_rgb[3 * i + 1] = gcol[1]; g_rgb[3 * i + 2] = gcol[2]; }
+    }
+    if (DEG >= 0 && g_sh) {
+        // stage the SH gradients in shared memory and write them coalesced
+        __syncwarp();
+        if (inrange) {
+#pragma unroll
+            for (int k = 0; k < (DEG >= 0 ? KF : 1); ++k) s_sh[warp][lane][k] = gshv[k];
+        }
+        __syncwarp();
+        if (wcnt > 0) {
+            float* dst = g_sh + (size_t)wbase * KF;
+            for (int q = lane; q < wcnt * KF; q += 32) {
+                const int gi = q / KF;
+                dst[q] = s_sh[warp][gi][q - gi * KF];
+            }
+        }
+    }
+}
+
 __global__ void k_unpack(Records rec, const int* __restrict__ radius, const uint32_t* __restrict__ tiles,
                          const float* __restrict__ depth_in, uint32_t n, float* mean2d, float* conic, float* rgb,
                          float* opacity, float* depth, int32_t* radius_out, int32_t* tiles_out)
@@ -304,6 +566,29 @@ cudaError_t launch_project(cudaStream_t s, const gs_gaussians& g, const CameraPa
     default: GS_PROJECT(-1); break;
     }
 #undef GS_PROJECT
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project_backward(cudaStream_t s, const gs_gaussians& g, const CameraParams& cam,
+                                    const float* grad2d, const gs_gaussian_grads& out)
+{
+    const int n = (int)g.n;
+    if (n == 0) return cudaSuccess;
+    const int blocks = (n + kProjThreads - 1) / kProjThreads;
+    const int deg = g.sh ? g.sh_degree : -1;
+#define GS_PROJECT_BWD(D)                                                                                        \
+    k_project_bwd<D><<<blocks, kProjThreads, 0, s>>>(n, g.means, g.log_scales, g.quats, g.opacity_logits, g.sh, \
+                                                     cam, grad2d, out.means, out.log_scales, out.quats,          \
+                                                     out.opacity_logits, out.sh, out.rgb)
+    switch (deg) {
+    case 0: GS_PROJECT_BWD(0); break;
+    case 1: GS_PROJECT_BWD(1); break;
+    case 2: GS_PROJECT_BWD(2); break;
+    case 3: GS_PROJECT_BWD(3); break;
+    default: GS_PROJECT_BWD(-1); break;
+    }
+#undef GS_PROJECT_BWD
     note_launch();
     return cudaGetLastError();
 }

@@ -160,7 +160,78 @@ __global__ void __launch_bounds__(kThreadsX * kThreadsY) k_upscale(const float* 
     }
 }
 
+// Adjoint of k_upscale.  The output is linear in the low-res values, so
+// dL/d(value of low-res pixel (i, j)) = sum over the output pixels whose cell
+// has (i, j) as a corner of (that corner's weight) * dL/dout.  Output pixel X
+// has (i, .) as its left corner when its cell is i (weights h00, h10 of t) and
+// as its right corner when its cell is i - 1 (weights h01, h11); the cells of
+// X lie in [(i - 1) s - 1, (i + 2) s] for those two cells (border cells
+// included).  One thread per low-res pixel gathers its 2D footprint with the
+// separable weights: no atomics, each low-res value written once.
+constexpr int kBwdX = 32, kBwdY = 8;
+
+__global__ void __launch_bounds__(kBwdX * kBwdY) k_upscale_bwd(const float* __restrict__ dout, int W, int H, int s,
+                                                               float* __restrict__ dC, float* __restrict__ dG)
+{
+    const int i = blockIdx.x * kBwdX + threadIdx.x;
+    const int j = blockIdx.y * kBwdY + threadIdx.y;
+    if (i >= W || j >= H) return;
+    const int W2 = W * s, H2 = H * s;
+    const size_t oplane = (size_t)W2 * H2;
+    const int Xa = max(0, (i - 1) * s - 1), Xb = min(W2 - 1, (i + 2) * s);
+    const int Ya = max(0, (j - 1) * s - 1), Yb = min(H2 - 1, (j + 2) * s);
+    // acc[ch][q], q: value (H H), d/dx (G H), d/dy (H G), d2/dxdy (G G)
+    float acc[3][4];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[ch][q] = 0.f;
+    for (int Y = Ya; Y <= Yb; ++Y) {
+        int cj;
+        float u;
+        cell_of(Y, s, H, cj, u);
+        if (cj != j && cj != j - 1) continue;
+        const float4 hy = hermite(u);
+        const float wyH = cj == j ? hy.x : hy.y, wyG = cj == j ? hy.z : hy.w;
+        const float* row = dout + (size_t)Y * W2;
+        for (int X = Xa; X <= Xb; ++X) {
+            int ci;
+            float t;
+            cell_of(X, s, W, ci, t);
+            if (ci != i && ci != i - 1) continue;
+            const float4 hx = hermite(t);
+            const float wxH = ci == i ? hx.x : hx.y, wxG = ci == i ? hx.z : hx.w;
+            const float wHH = wxH * wyH, wGH = wxG * wyH, wHG = wxH * wyG, wGG = wxG * wyG;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                const float d = __ldg(row + ch * oplane + X);
+                acc[ch][0] = fmaf(wHH, d, acc[ch][0]);
+                acc[ch][1] = fmaf(wGH, d, acc[ch][1]);
+                acc[ch][2] = fmaf(wHG, d, acc[ch][2]);
+                acc[ch][3] = fmaf(wGG, d, acc[ch][3]);
+            }
+        }
+    }
+    const size_t plane = (size_t)W * H, pix = (size_t)j * W + i;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        dC[ch * plane + pix] = acc[ch][0];
+        dG[(0 * 3 + ch) * plane + pix] = acc[ch][1];
+        dG[(1 * 3 + ch) * plane + pix] = acc[ch][2];
+        dG[(2 * 3 + ch) * plane + pix] = acc[ch][3];
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_upscale_backward(cudaStream_t s, const float* dout, int W, int H, int factor, float* dC,
+                                    float* dG)
+{
+    if (factor < 1 || factor > kMaxFactor || W < 2 || H < 2) return cudaErrorInvalidValue;
+    dim3 grid((W + kBwdX - 1) / kBwdX, (H + kBwdY - 1) / kBwdY);
+    k_upscale_bwd<<<grid, dim3(kBwdX, kBwdY), 0, s>>>(dout, W, H, factor, dC, dG); note_launch();
+    return cudaGetLastError();
+}
 
 cudaError_t launch_upscale(cudaStream_t s, const float* C, const float* grads, int W, int H, int factor, float* out)
 {
