@@ -54,7 +54,7 @@ def _args():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gs", choices=["gs", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile", default=None, choices=["main", "direct"],
+    ap.add_argument("--profile", default=None, choices=["main", "direct", "backward"],
                     help="run only warm-up + steps of the 2x path (main) or of the direct 1920x1080 "
                          "render (direct) and print stage times; the case ncu captures use")
     return ap.parse_args()
@@ -505,7 +505,19 @@ def run_profile(args):
     def direct_step():
         ctx.render(dev, cam_hi, OUT_W, OUT_H, out_C=out)
 
-    fn = main_step if args.profile == "main" else direct_step
+    dout = None
+    grads = None
+
+    def backward_step():
+        ctx.backward(dout, FACTOR, out=grads)
+
+    fn = {"main": main_step, "direct": direct_step, "backward": backward_step}[args.profile]
+    if args.profile == "backward":
+        with torch.cuda.stream(stream):
+            main_step()
+            dout = torch.randn(3, OUT_H, OUT_W, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+            grads = ctx.backward(dout, FACTOR)
+            torch.cuda.synchronize()
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             fn()

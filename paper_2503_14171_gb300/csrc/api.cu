@@ -407,7 +407,7 @@ gs_status gs_destroy(gs_ctx* c)
                       &c->pairs[1],
                       &c->sort_hist, &c->sort_status,
                       &c->sort_counter, &c->sranges, &c->tile_count, &c->tile_start, &c->state, &c->count,
-                      &c->errword, &c->tile_vals, &c->tile_ranges, &c->grad2d, &c->up_planes};
+                      &c->errword, &c->grad2d, &c->up_planes};
     for (DevBuf* b : bufs) release(*b);
     if (c->h_scalar) cudaFreeHost(c->h_scalar);
     if (c->totals_ready) cudaEventDestroy(c->totals_ready);
@@ -505,26 +505,16 @@ gs_status do_render_backward(gs_ctx* c, const float* dC, const float* dG, float*
     if (!dC || !grad2d) return fail(c, GS_ERR_INVALID_ARG, "dL_dC and grad2d are required");
     if (!c->have_proj || !c->have_state || !c->state_grads)
         return fail(c, GS_ERR_NOT_READY, "no derivative blend since the last projection");
-    const size_t T = (size_t)c->tiles_x * c->tiles_y;
-    gs_status st;
-    if ((st = ensure(c, c->tile_count, sizeof(uint32_t) * T)) ||
-        (st = ensure(c, c->tile_start, sizeof(uint32_t) * T)) ||
-        (st = ensure(c, c->tile_ranges, sizeof(uint2) * T)) ||
-        (st = ensure(c, c->tile_vals, sizeof(uint32_t) * (size_t)std::max<int64_t>(c->P, 1))))
-        return st;
-    // the tiles' own front-to-back lists, walked back to front by the adjoint
-    GS_CUDA(c, launch_tile_lists(c->stream, as<uint64_t>(c->pairs[c->sorted_pairs_buf]), as<uint2>(c->sranges),
-                                 as<ushort4>(c->rect), as<float>(c->depth), (uint32_t)c->n, c->tiles_x, c->tiles_y,
-                                 c->stiles_x, as<uint32_t>(c->tile_count), as<uint32_t>(c->tile_start), nullptr,
-                                 as<uint32_t>(c->tile_vals), as<uint2>(c->tile_ranges)));
     if (c->n > 0) GS_CUDA(c, cudaMemsetAsync(grad2d, 0, sizeof(float) * 9 * (size_t)c->n, c->stream));
     BlendBwdArgs a;
     a.W = c->W;
     a.H = c->H;
     a.tiles_x = c->tiles_x;
+    a.stiles_x = c->stiles_x;
     a.n = (uint32_t)c->n;
-    a.tranges = as<uint2>(c->tile_ranges);
-    a.tvals = as<uint32_t>(c->tile_vals);
+    a.sranges = as<uint2>(c->sranges);
+    a.pair_words = reinterpret_cast<const uint32_t*>(c->pairs[c->sorted_pairs_buf].p);
+    a.rect = as<ushort4>(c->rect);
     a.rec = Records{as<float4>(c->rec0), as<float4>(c->rec1), as<float4>(c->rec2)};
     a.bg = make_float3(c->opt.bg[0], c->opt.bg[1], c->opt.bg[2]);
     a.state = as<float4>(c->state);

@@ -27,28 +27,12 @@
 //   C += c w, C_x += c w_x, C_y += c w_y, C_xy += c w_xy
 //   T *= (1 - alpha), T_x -= w_x, T_y -= w_y, T_xy -= w_xy
 // (identical to B_i, A_i and their derivatives in the supplement, T = 1 - A).
-#include "gs_internal.cuh"
+#include "blend_common.cuh"
 
 namespace gs {
 namespace {
 
-constexpr int kThreads = kTilePixels;    // one pixel per thread
-constexpr int kWarps = kThreads / 32;
-constexpr int kCand = kThreads;          // candidates examined per compaction round
 constexpr int kStage = 2 * kCand;        // staged records per batch (>= kCand before blending)
-constexpr float kLn2 = 0.69314718055994531f;
-
-__device__ __forceinline__ bool covers(ushort4 r, int tx, int ty)
-{
-    return (int)r.x <= tx && tx <= (int)r.z && (int)r.y <= ty && ty <= (int)r.w;
-}
-
-// Exponent of a (pixel, Gaussian) pair in base 2 (shared by the forward and
-// the adjoint so both take every decision on the same FP32 value).
-__device__ __forceinline__ float exponent2(const float4& r1, float dx, float dy)
-{
-    return fmaf(dx, fmaf(r1.x, dx, r1.y * dy), r1.z * dy * dy);
-}
 
 struct PixelState {
     float T, Tx, Ty, Txy;
@@ -243,227 +227,7 @@ cudaError_t launch_t(cudaStream_t s, const BlendArgs& a)
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
-// Adjoint of k_blend<GRADS = true> (supplement "Backward Pass").
-//
-// Reverse mode on the forward's own recurrences.  Per blended pair, with the
-// state (T, T_x, T_y, T_xy) before the step and the weights
-//   w = alpha T, w_x = alpha (T g_x + T_x), w_y = alpha (T g_y + T_y),
-//   w_xy = alpha (T g_xy' + T_x g_y + T_y g_x + T_xy)   (g_xy' = g_x g_y + g_xy),
-// the step adds c w (and c w_x, ...) to the outputs and subtracts w (w_x, ...)
-// from the state.  Walking back to front with the adjoint lambda of the state
-// (initialised from the background term, output += bg T):
-//   G_w = u . c - lambda_T  (likewise G_wx, G_wy, G_wxy with u_x, u_y, u_xy)
-//   dL/dc = u w + u_x w_x + u_y w_y + u_xy w_xy
-//   lambda_T  += G_w alpha + G_wx alpha_x + G_wy alpha_y + G_wxy alpha_xy
-//   lambda_Tx += G_wx alpha + G_wxy alpha_y,  lambda_Ty += G_wy alpha + G_wxy alpha_x,
-//   lambda_Txy += G_wxy alpha
-//   G_alpha = G_w T + G_wx T_x + G_wy T_y + G_wxy T_xy,  G_alpha_x = G_wx T + G_wxy T_y,
-//   G_alpha_y = G_wy T + G_wxy T_x,  G_alpha_xy = G_wxy T
-// and, through alpha = sigma e^g (alpha_x = alpha g_x, ...):
-//   dL/dg = alpha (G_alpha + G_alpha_x g_x + G_alpha_y g_y + G_alpha_xy g_xy'),
-//   dL/dg_x = alpha (G_alpha_x + G_alpha_xy g_y), dL/dg_y = alpha (G_alpha_y + G_alpha_xy g_x),
-//   dL/dg_xy = alpha G_alpha_xy,  dL/dsigma = dL/dg / sigma,
-// then to the mean and the conic by differentiating g, g_x, g_y, g_xy = -b.
-// A clamped alpha (0.99) is a constant: no gradient to sigma or the geometry.
-//
-// The state before each step is recovered from the state after it (the stored
-// final state for the last one) by inverting the update: T = T'/(1 - alpha),
-// T_x = (T_x' + alpha T g_x)/(1 - alpha), ... (the supplement's inversion trick
-// written for T = 1 - A).  The Gaussian sequence is the tile's materialised
-// list, walked from the largest stored count of the block down; a pixel joins
-// at its own count, and every decision (reject, cut-off, clamp) is re-taken on
-// the same FP32 values as the forward.  Per list entry the block reduces the
-// pixels' 9 gradients (warp shuffles, then shared-memory atomics) and adds one
-// set per tile to global memory.
-constexpr int kBwdWarps = kWarps;
-
-template <int MODE>
-__global__ void __launch_bounds__(kThreads) k_blend_bwd(BlendBwdArgs a)
-{
-    __shared__ float4 s_r0[kThreads];
-    __shared__ float4 s_r1[kThreads];
-    __shared__ float4 s_r2[kThreads];
-    __shared__ uint32_t s_id[kThreads];
-    __shared__ float s_acc[kThreads][9];
-    __shared__ int s_max[kBwdWarps];
-
-    const int tile = blockIdx.x;
-    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
-    const int x = tx * kTile + lx, y = ty * kTile + ly;
-    const bool inside = x < a.W && y < a.H;
-    const float px = (float)x, py = (float)y;
-    const size_t plane = (size_t)a.W * a.H;
-    const size_t pix = inside ? (size_t)y * a.W + x : 0;
-
-    int last = 0;
-    float T = 1.f, Tx = 0.f, Ty = 0.f, Txy = 0.f;
-    float uC[3] = {0.f, 0.f, 0.f}, uX[3] = {0.f, 0.f, 0.f}, uY[3] = {0.f, 0.f, 0.f}, uZ[3] = {0.f, 0.f, 0.f};
-    if (inside) {
-        last = a.count[pix];
-        const float4 st = a.state[pix];
-        T = st.x; Tx = st.y; Ty = st.z; Txy = st.w;
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            uC[ch] = a.dC[ch * plane + pix];
-            if (a.dG) {
-                uX[ch] = a.dG[(0 * 3 + ch) * plane + pix];
-                uY[ch] = a.dG[(1 * 3 + ch) * plane + pix];
-                uZ[ch] = a.dG[(2 * 3 + ch) * plane + pix];
-            }
-        }
-    }
-    // adjoint of the state after the last step: output += bg (T, T_x, T_y, T_xy)
-    float lT = uC[0] * a.bg.x + uC[1] * a.bg.y + uC[2] * a.bg.z;
-    float lTx = uX[0] * a.bg.x + uX[1] * a.bg.y + uX[2] * a.bg.z;
-    float lTy = uY[0] * a.bg.x + uY[1] * a.bg.y + uY[2] * a.bg.z;
-    float lTxy = uZ[0] * a.bg.x + uZ[1] * a.bg.y + uZ[2] * a.bg.z;
-
-    // the block's longest prefix
-    int m = last;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) s_max[warp] = m;
-#pragma unroll
-    for (int q = 0; q < 9; ++q) s_acc[threadIdx.x][q] = 0.f;
-    __syncthreads();
-    int M = 0;
-#pragma unroll
-    for (int w = 0; w < kBwdWarps; ++w) M = max(M, s_max[w]);
-    const uint2 tr = a.tranges[tile];
-    const int len = (int)(tr.y - tr.x);
-    if (M > len) {   // the count and the list disagree: report, and stay in bounds
-        if (threadIdx.x == 0) atomicExch(a.err, kDevCheck);
-        M = len;
-    }
-
-    for (int cs = ((M - 1) / kThreads) * kThreads; M > 0 && cs >= 0; cs -= kThreads) {
-        const int cnt = min(kThreads, M - cs);
-        if ((int)threadIdx.x < cnt) {
-            const uint32_t id = a.tvals[tr.x + cs + threadIdx.x];
-            const bool ok = id < a.n;
-            s_id[threadIdx.x] = ok ? id : 0xFFFFFFFFu;
-            s_r0[threadIdx.x] = ok ? a.rec.r0[id] : make_float4(0.f, 0.f, 0.f, 0.f);
-            s_r1[threadIdx.x] = ok ? a.rec.r1[id] : make_float4(0.f, 0.f, 0.f, -INFINITY);
-            s_r2[threadIdx.x] = ok ? a.rec.r2[id] : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        __syncthreads();
-        for (int k = cnt - 1; k >= 0; --k) {
-            float v[9];
-#pragma unroll
-            for (int q = 0; q < 9; ++q) v[q] = 0.f;
-            bool contrib = false;
-            if (cs + k < last) {
-                const float4 r0 = s_r0[k];
-                const float4 r1 = s_r1[k];
-                const float4 c = s_r2[k];
-                const float dx = px - r0.x, dy = py - r0.y;
-                const float g2 = exponent2(r1, dx, dy);
-                bool blended = !(MODE == GS_MODE_3DGS && g2 < r1.w) && s_id[k] != 0xFFFFFFFFu;
-                float alpha = 0.f;
-                bool clamped = false;
-                if (blended) {
-                    alpha = c.w * exp2f(g2);
-                    if (MODE == GS_MODE_3DGS) {
-                        if (alpha < (1.f / 255.f)) blended = false;
-                        clamped = alpha > 0.99f;
-                        alpha = fminf(alpha, 0.99f);
-                    }
-                }
-                if (blended) {
-                    contrib = true;
-                    const float bn = r1.y * kLn2;   // -b
-                    float gx = fmaf(r0.z, dx, bn * dy);
-                    float gy = fmaf(r0.w, dy, bn * dx);
-                    float gxy = fmaf(gx, gy, bn);
-                    if (clamped) { gx = 0.f; gy = 0.f; gxy = 0.f; }
-                    // state before the step
-                    const float iom = 1.f / (1.f - alpha);
-                    const float T0 = T * iom;
-                    const float Tx0 = fmaf(alpha * T0, gx, Tx) * iom;
-                    const float Ty0 = fmaf(alpha * T0, gy, Ty) * iom;
-                    const float Txy0 = fmaf(alpha, T0 * gxy + Tx0 * gy + Ty0 * gx, Txy) * iom;
-                    const float w = alpha * T0;
-                    const float wx = alpha * fmaf(T0, gx, Tx0);
-                    const float wy = alpha * fmaf(T0, gy, Ty0);
-                    const float wxy = alpha * (T0 * gxy + Tx0 * gy + Ty0 * gx + Txy0);
-                    v[6] = uC[0] * w + uX[0] * wx + uY[0] * wy + uZ[0] * wxy;
-                    v[7] = uC[1] * w + uX[1] * wx + uY[1] * wy + uZ[1] * wxy;
-                    v[8] = uC[2] * w + uX[2] * wx + uY[2] * wy + uZ[2] * wxy;
-                    const float Gw = uC[0] * c.x + uC[1] * c.y + uC[2] * c.z - lT;
-                    const float Gwx = uX[0] * c.x + uX[1] * c.y + uX[2] * c.z - lTx;
-                    const float Gwy = uY[0] * c.x + uY[1] * c.y + uY[2] * c.z - lTy;
-                    const float Gwxy = uZ[0] * c.x + uZ[1] * c.y + uZ[2] * c.z - lTxy;
-                    const float ax = alpha * gx, ay = alpha * gy, axy = alpha * gxy;
-                    lT += Gw * alpha + Gwx * ax + Gwy * ay + Gwxy * axy;
-                    lTx += Gwx * alpha + Gwxy * ay;
-                    lTy += Gwy * alpha + Gwxy * ax;
-                    lTxy += Gwxy * alpha;
-                    if (!clamped) {
-                        const float Ga = Gw * T0 + Gwx * Tx0 + Gwy * Ty0 + Gwxy * Txy0;
-                        const float Gax = Gwx * T0 + Gwxy * Ty0;
-                        const float Gay = Gwy * T0 + Gwxy * Tx0;
-                        const float Gaxy = Gwxy * T0;
-                        const float dg = alpha * (Ga + Gax * gx + Gay * gy + Gaxy * gxy);
-                        const float dgx = alpha * fmaf(Gaxy, gy, Gax);
-                        const float dgy = alpha * fmaf(Gaxy, gx, Gay);
-                        const float dgxy = alpha * Gaxy;
-                        const float ca = -r0.z, cb = -bn, cc = -r0.w;
-                        v[0] = -dg * gx + ca * dgx + cb * dgy;
-                        v[1] = -dg * gy + cb * dgx + cc * dgy;
-                        v[2] = -0.5f * dx * dx * dg - dx * dgx;
-                        v[3] = -dx * dy * dg - dy * dgx - dx * dgy - dgxy;
-                        v[4] = -0.5f * dy * dy * dg - dy * dgy;
-                        v[5] = dg / c.w;
-                    }
-                    T = T0; Tx = Tx0; Ty = Ty0; Txy = Txy0;
-                }
-            }
-            if (__ballot_sync(0xffffffffu, contrib)) {
-#pragma unroll
-                for (int q = 0; q < 9; ++q) {
-                    float t = v[q];
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-                    v[q] = t;
-                }
-                if (lane == 0) {
-#pragma unroll
-                    for (int q = 0; q < 9; ++q) atomicAdd(&s_acc[k][q], v[q]);
-                }
-            }
-        }
-        __syncthreads();
-        if ((int)threadIdx.x < cnt) {
-            const uint32_t id = s_id[threadIdx.x];
-            if (id != 0xFFFFFFFFu) {
-                float* g = a.grad2d + (size_t)id * 9;
-#pragma unroll
-                for (int q = 0; q < 9; ++q) {
-                    const float val = s_acc[threadIdx.x][q];
-                    if (val != 0.f) atomicAdd(g + q, val);
-                    s_acc[threadIdx.x][q] = 0.f;
-                }
-            }
-        }
-        __syncthreads();
-    }
-}
-
 }  // namespace
-
-cudaError_t launch_blend_backward(cudaStream_t s, int mode, const BlendBwdArgs& a)
-{
-    const int tiles = a.tiles_x * ((a.H + kTile - 1) / kTile);
-    if (mode == GS_MODE_EXACT)
-        k_blend_bwd<GS_MODE_EXACT><<<tiles, kThreads, 0, s>>>(a);
-    else
-        k_blend_bwd<GS_MODE_3DGS><<<tiles, kThreads, 0, s>>>(a);
-    note_launch();
-    return cudaGetLastError();
-}
 
 cudaError_t launch_blend_stats(cudaStream_t s, int mode, const BlendArgs& a, unsigned long long* stats)
 {

@@ -1,0 +1,335 @@
+// Adjoint of the derivative blend (supplement "Backward Pass").
+//
+// Reverse mode on the forward's own recurrences.  Per blended pair, with the
+// state (T, T_x, T_y, T_xy) before the step and the weights
+//   w = alpha T, w_x = alpha (T g_x + T_x), w_y = alpha (T g_y + T_y),
+//   w_xy = alpha (T g_xy' + T_x g_y + T_y g_x + T_xy)   (g_xy' = g_x g_y + g_xy),
+// the step adds c w (and c w_x, ...) to the outputs and subtracts w (w_x, ...)
+// from the state.  Walking back to front with the adjoint lambda of the state
+// (initialised from the background term, output += bg T):
+//   G_w = u . c - lambda_T  (likewise G_wx, G_wy, G_wxy with u_x, u_y, u_xy)
+//   dL/dc = u w + u_x w_x + u_y w_y + u_xy w_xy
+//   lambda_T  += G_w alpha + G_wx alpha_x + G_wy alpha_y + G_wxy alpha_xy
+//   lambda_Tx += G_wx alpha + G_wxy alpha_y,  lambda_Ty += G_wy alpha + G_wxy alpha_x,
+//   lambda_Txy += G_wxy alpha
+//   G_alpha = G_w T + G_wx T_x + G_wy T_y + G_wxy T_xy,  G_alpha_x = G_wx T + G_wxy T_y,
+//   G_alpha_y = G_wy T + G_wxy T_x,  G_alpha_xy = G_wxy T
+// and, through alpha = sigma e^g (alpha_x = alpha g_x, ...):
+//   dL/dg = alpha (G_alpha + G_alpha_x g_x + G_alpha_y g_y + G_alpha_xy g_xy'),
+//   dL/dg_x = alpha (G_alpha_x + G_alpha_xy g_y), dL/dg_y = alpha (G_alpha_y + G_alpha_xy g_x),
+//   dL/dg_xy = alpha G_alpha_xy,  dL/dsigma = dL/dg / sigma,
+// then to the mean and the conic by differentiating g, g_x, g_y, g_xy = -b.
+// A clamped alpha (0.99) is a constant: no gradient to sigma or the geometry.
+//
+// The state before each step is recovered from the state after it (the stored
+// final state for the last one) by inverting the update: T = T'/(1 - alpha),
+// T_x = (T_x' + alpha T g_x)/(1 - alpha), ... (the supplement's inversion trick
+// written for T = 1 - A).
+//
+// List walk.  A tile's front-to-back list is its super-tile's list filtered by
+// the tile rects (as in the forward).  The block first streams the super-tile
+// list in rounds of 256 candidates, recording the tile's list position at the
+// start of each round, until the largest stored count of its pixels is
+// covered.  It then replays the rounds last to first: each round's hits are
+// compacted in order into shared memory and walked back to front; a pixel takes
+// part in the entries below its own count, and every decision (reject, cut-off,
+// clamp) is re-taken on the same FP32 values as the forward.  Round starts are
+// kept for 1024 rounds at a time; longer lists are replayed in segments of 1024
+// rounds, each recounted from a stored segment start.  Per list entry the block
+// reduces the pixels' 9 gradients (a transposed warp sum, then shared-memory
+// atomics) and adds one set per tile and Gaussian to global memory.
+#include "blend_common.cuh"
+
+namespace gs {
+namespace {
+
+constexpr int kMaxRounds = 1024;   // round starts kept in shared memory
+constexpr int kMaxSegs = 256;      // segments of kMaxRounds rounds (lists up to 2^26 candidates)
+
+struct BwdPixel {
+    float px, py;
+    int last;
+    float T, Tx, Ty, Txy;          // state after the entries not yet walked back
+    float lT, lTx, lTy, lTxy;      // its adjoint
+    float uC[3], uX[3], uY[3], uZ[3];
+};
+
+// One list entry for one pixel: returns the pixel's 9 gradient terms in v
+// (zero if the pair was not blended) and steps the state and its adjoint back.
+template <int MODE>
+__device__ __forceinline__ bool bwd_entry(BwdPixel& p, const float4& r0, const float4& r1, const float4& c,
+                                          float v[9])
+{
+    const float dx = p.px - r0.x, dy = p.py - r0.y;
+    const float g2 = exponent2(r1, dx, dy);
+    if (MODE == GS_MODE_3DGS && g2 < r1.w) return false;
+    float alpha = c.w * exp2f(g2);
+    bool clamped = false;
+    if (MODE == GS_MODE_3DGS) {
+        if (alpha < (1.f / 255.f)) return false;
+        clamped = alpha > 0.99f;
+        alpha = fminf(alpha, 0.99f);
+    }
+    const float bn = r1.y * kLn2;   // -b
+    float gx = fmaf(r0.z, dx, bn * dy);
+    float gy = fmaf(r0.w, dy, bn * dx);
+    float gxy = fmaf(gx, gy, bn);
+    if (clamped) { gx = 0.f; gy = 0.f; gxy = 0.f; }
+    // state before the step
+    const float iom = __fdividef(1.f, 1.f - alpha);
+    const float T0 = p.T * iom;
+    const float Tx0 = fmaf(alpha * T0, gx, p.Tx) * iom;
+    const float Ty0 = fmaf(alpha * T0, gy, p.Ty) * iom;
+    const float Txy0 = fmaf(alpha, T0 * gxy + Tx0 * gy + Ty0 * gx, p.Txy) * iom;
+    const float w = alpha * T0;
+    const float wx = alpha * fmaf(T0, gx, Tx0);
+    const float wy = alpha * fmaf(T0, gy, Ty0);
+    const float wxy = alpha * (T0 * gxy + Tx0 * gy + Ty0 * gx + Txy0);
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) v[6 + ch] = p.uC[ch] * w + p.uX[ch] * wx + p.uY[ch] * wy + p.uZ[ch] * wxy;
+    const float Gw = p.uC[0] * c.x + p.uC[1] * c.y + p.uC[2] * c.z - p.lT;
+    const float Gwx = p.uX[0] * c.x + p.uX[1] * c.y + p.uX[2] * c.z - p.lTx;
+    const float Gwy = p.uY[0] * c.x + p.uY[1] * c.y + p.uY[2] * c.z - p.lTy;
+    const float Gwxy = p.uZ[0] * c.x + p.uZ[1] * c.y + p.uZ[2] * c.z - p.lTxy;
+    const float ax = alpha * gx, ay = alpha * gy, axy = alpha * gxy;
+    p.lT += Gw * alpha + Gwx * ax + Gwy * ay + Gwxy * axy;
+    p.lTx += Gwx * alpha + Gwxy * ay;
+    p.lTy += Gwy * alpha + Gwxy * ax;
+    p.lTxy += Gwxy * alpha;
+    if (!clamped) {
+        const float Ga = Gw * T0 + Gwx * Tx0 + Gwy * Ty0 + Gwxy * Txy0;
+        const float Gax = Gwx * T0 + Gwxy * Ty0;
+        const float Gay = Gwy * T0 + Gwxy * Tx0;
+        const float Gaxy = Gwxy * T0;
+        const float dg = alpha * (Ga + Gax * gx + Gay * gy + Gaxy * gxy);
+        const float dgx = alpha * fmaf(Gaxy, gy, Gax);
+        const float dgy = alpha * fmaf(Gaxy, gx, Gay);
+        const float dgxy = alpha * Gaxy;
+        const float ca = -r0.z, cb = -bn, cc = -r0.w;
+        v[0] = -dg * gx + ca * dgx + cb * dgy;
+        v[1] = -dg * gy + cb * dgx + cc * dgy;
+        v[2] = -0.5f * dx * dx * dg - dx * dgx;
+        v[3] = -dx * dy * dg - dy * dgx - dx * dgy - dgxy;
+        v[4] = -0.5f * dy * dy * dg - dy * dgy;
+        v[5] = __fdividef(dg, c.w);
+    }
+    p.T = T0; p.Tx = Tx0; p.Ty = Ty0; p.Txy = Txy0;
+    return true;
+}
+
+// Sum of v[0..8] over the warp into acc[0..8] (shared memory): a transposed
+// exchange halves the values a lane carries at each of the first three steps,
+// so lane L ends with the sum of value (L >> 2) & 7 (14 shuffles for the 9
+// values instead of 45), then 2 atomic instructions.
+__device__ __forceinline__ void warp_sum9_to_shared(float v[9], int lane, float* acc)
+{
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float r = __shfl_xor_sync(0xffffffffu, b4 ? v[j] : v[j + 4], 16);
+        v[j] = (b4 ? v[j + 4] : v[j]) + r;
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const float r = __shfl_xor_sync(0xffffffffu, b3 ? v[j] : v[j + 2], 8);
+        v[j] = (b3 ? v[j + 2] : v[j]) + r;
+    }
+    {
+        const float r = __shfl_xor_sync(0xffffffffu, b2 ? v[0] : v[1], 4);
+        v[0] = (b2 ? v[1] : v[0]) + r;
+    }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+    float t8 = v[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t8 += __shfl_xor_sync(0xffffffffu, t8, o);
+    if ((lane & 3) == 0) atomicAdd(&acc[lane >> 2], v[0]);
+    if (lane == 0) atomicAdd(&acc[8], t8);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_blend_bwd(BlendBwdArgs a)
+{
+    __shared__ float4 s_r0[kCand];
+    __shared__ float4 s_r1[kCand];
+    __shared__ float4 s_r2[kCand];
+    __shared__ uint32_t s_id[kCand];
+    __shared__ float s_acc[kCand][9];
+    __shared__ int s_round[kMaxRounds];
+    __shared__ int s_seg[kMaxSegs];
+    __shared__ int s_wcnt[kWarps];
+    __shared__ int s_max[kWarps];
+
+    const int tile = blockIdx.x;
+    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lanemask_lt = (1u << lane) - 1u;
+    const int x = tx * kTile + (threadIdx.x & (kTile - 1)), y = ty * kTile + threadIdx.x / kTile;
+    const bool inside = x < a.W && y < a.H;
+    const size_t plane = (size_t)a.W * a.H;
+    const size_t pix = inside ? (size_t)y * a.W + x : 0;
+
+    BwdPixel p;
+    p.px = (float)x;
+    p.py = (float)y;
+    p.last = 0;
+    p.T = 1.f; p.Tx = 0.f; p.Ty = 0.f; p.Txy = 0.f;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) { p.uC[ch] = 0.f; p.uX[ch] = 0.f; p.uY[ch] = 0.f; p.uZ[ch] = 0.f; }
+    if (inside) {
+        p.last = a.count[pix];
+        const float4 st = a.state[pix];
+        p.T = st.x; p.Tx = st.y; p.Ty = st.z; p.Txy = st.w;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            p.uC[ch] = a.dC[ch * plane + pix];
+            if (a.dG) {
+                p.uX[ch] = a.dG[(0 * 3 + ch) * plane + pix];
+                p.uY[ch] = a.dG[(1 * 3 + ch) * plane + pix];
+                p.uZ[ch] = a.dG[(2 * 3 + ch) * plane + pix];
+            }
+        }
+    }
+    // adjoint of the state after the last step: output += bg (T, T_x, T_y, T_xy)
+    p.lT = p.uC[0] * a.bg.x + p.uC[1] * a.bg.y + p.uC[2] * a.bg.z;
+    p.lTx = p.uX[0] * a.bg.x + p.uX[1] * a.bg.y + p.uX[2] * a.bg.z;
+    p.lTy = p.uY[0] * a.bg.x + p.uY[1] * a.bg.y + p.uY[2] * a.bg.z;
+    p.lTxy = p.uZ[0] * a.bg.x + p.uZ[1] * a.bg.y + p.uZ[2] * a.bg.z;
+
+    // the block's longest prefix of the tile list
+    int m = p.last;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) s_max[warp] = m;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) s_acc[threadIdx.x][q] = 0.f;
+    __syncthreads();
+    int M = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) M = max(M, s_max[w]);
+
+    const int S = (ty / kSuper) * a.stiles_x + (tx / kSuper);
+    const uint2 sr = a.sranges[S];
+    const int total = (int)(sr.y - sr.x);
+
+    // pass 1: the tile's list position at the start of each round of candidates
+    int filt = 0, R = 0;
+    for (int c0 = 0; c0 < total && filt < M; c0 += kCand, ++R) {
+        if (R % kMaxRounds == 0) {
+            if (R / kMaxRounds >= kMaxSegs) break;
+            if (threadIdx.x == 0) s_seg[R / kMaxRounds] = filt;
+        }
+        if (threadIdx.x == 0) s_round[R % kMaxRounds] = filt;
+        const int c = c0 + (int)threadIdx.x;
+        bool hit = false;
+        if (c < total) {
+            const uint32_t id = a.pair_words[2 * (size_t)(sr.x + c)];
+            hit = id < a.n && covers(a.rect[id], tx, ty);
+        }
+        const uint32_t ball = __ballot_sync(0xffffffffu, hit);
+        if (lane == 0) s_wcnt[warp] = __popc(ball);
+        __syncthreads();
+        int tot = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) tot += s_wcnt[w];
+        __syncthreads();
+        filt += tot;
+    }
+    if (filt < M) {   // the list ended (or is too long) before the stored counts: report, walk what exists
+        if (threadIdx.x == 0) atomicExch(a.err, kDevCheck);
+        M = filt;
+    }
+
+    // pass 2: replay the rounds last to first
+    const int nseg = (R + kMaxRounds - 1) / kMaxRounds;
+    for (int seg = nseg - 1; seg >= 0; --seg) {
+        const int rb = seg * kMaxRounds, re = min(R, rb + kMaxRounds);
+        if (seg != nseg - 1) {   // pass 1 kept the round starts of the last segment only
+            __syncthreads();
+            int f = s_seg[seg];
+            for (int r = rb; r < re; ++r) {
+                if (threadIdx.x == 0) s_round[r - rb] = f;
+                const int c = r * kCand + (int)threadIdx.x;
+                bool hit = false;
+                if (c < total) {
+                    const uint32_t id = a.pair_words[2 * (size_t)(sr.x + c)];
+                    hit = id < a.n && covers(a.rect[id], tx, ty);
+                }
+                const uint32_t ball = __ballot_sync(0xffffffffu, hit);
+                if (lane == 0) s_wcnt[warp] = __popc(ball);
+                __syncthreads();
+                int tot = 0;
+#pragma unroll
+                for (int w = 0; w < kWarps; ++w) tot += s_wcnt[w];
+                __syncthreads();
+                f += tot;
+            }
+        }
+        __syncthreads();
+        for (int r = re - 1; r >= rb; --r) {
+            const int fb = s_round[r - rb];
+            const int c = r * kCand + (int)threadIdx.x;
+            uint32_t id = 0xFFFFFFFFu;
+            bool hit = false;
+            if (c < total) {
+                id = a.pair_words[2 * (size_t)(sr.x + c)];
+                hit = id < a.n && covers(a.rect[id], tx, ty);
+            }
+            const uint32_t ball = __ballot_sync(0xffffffffu, hit);
+            if (lane == 0) s_wcnt[warp] = __popc(ball);
+            __syncthreads();
+            int wbase = 0, tot = 0;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) {
+                const int cw = s_wcnt[w];
+                wbase += w < warp ? cw : 0;
+                tot += cw;
+            }
+            const int cnt = min(tot, M - fb);   // entries at list positions >= M are not needed
+            if (hit) {
+                const int k = wbase + __popc(ball & lanemask_lt);
+                if (k < cnt) {
+                    s_id[k] = id;
+                    s_r0[k] = a.rec.r0[id];
+                    s_r1[k] = a.rec.r1[id];
+                    s_r2[k] = a.rec.r2[id];
+                }
+            }
+            __syncthreads();
+            for (int k = cnt - 1; k >= 0; --k) {
+                float v[9];
+#pragma unroll
+                for (int q = 0; q < 9; ++q) v[q] = 0.f;
+                bool contrib = false;
+                if (fb + k < p.last) contrib = bwd_entry<MODE>(p, s_r0[k], s_r1[k], s_r2[k], v);
+                if (__ballot_sync(0xffffffffu, contrib)) warp_sum9_to_shared(v, lane, s_acc[k]);
+            }
+            __syncthreads();
+            if ((int)threadIdx.x < cnt) {
+                float* g = a.grad2d + (size_t)s_id[threadIdx.x] * 9;
+#pragma unroll
+                for (int q = 0; q < 9; ++q) {
+                    const float val = s_acc[threadIdx.x][q];
+                    if (val != 0.f) atomicAdd(g + q, val);
+                    s_acc[threadIdx.x][q] = 0.f;
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_blend_backward(cudaStream_t s, int mode, const BlendBwdArgs& a)
+{
+    const int tiles = a.tiles_x * ((a.H + kTile - 1) / kTile);
+    if (tiles == 0) return cudaSuccess;
+    if (mode == GS_MODE_EXACT)
+        k_blend_bwd<GS_MODE_EXACT><<<tiles, kThreads, 0, s>>>(a);
+    else
+        k_blend_bwd<GS_MODE_3DGS><<<tiles, kThreads, 0, s>>>(a);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace gs

@@ -1,0 +1,29 @@
+// Definitions shared by the blend (blend.cu) and its adjoint (blend_bwd.cu):
+// both evaluate every (pixel, Gaussian) pair with the same expressions, so the
+// adjoint re-takes each of the forward's decisions on the same FP32 values.
+#pragma once
+
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+constexpr int kThreads = kTilePixels;    // one pixel per thread
+constexpr int kWarps = kThreads / 32;
+constexpr int kCand = kThreads;          // super-tile list candidates examined per round
+constexpr float kLn2 = 0.69314718055994531f;
+
+__device__ __forceinline__ bool covers(ushort4 r, int tx, int ty)
+{
+    return (int)r.x <= tx && tx <= (int)r.z && (int)r.y <= ty && ty <= (int)r.w;
+}
+
+// Exponent of a (pixel, Gaussian) pair in base 2: r1 = (A2, B2, C2, threshold)
+// with g2 = A2 dx^2 + B2 dx dy + C2 dy^2 = g log2(e).
+__device__ __forceinline__ float exponent2(const float4& r1, float dx, float dy)
+{
+    return fmaf(dx, fmaf(r1.x, dx, r1.y * dy), r1.z * dy * dy);
+}
+
+}  // namespace
+}  // namespace gs

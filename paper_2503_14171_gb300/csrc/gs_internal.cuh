@@ -66,14 +66,16 @@ struct BlendArgs {
     int* count;
 };
 
-// Adjoint of the blend: per-tile lists (materialised), the forward's final
-// per-pixel state and count, the upstream planes, and the 2D gradients
-// [n][9] = (mean_x, mean_y, conic a, b, c, opacity, r, g, b), accumulated.
+// Adjoint of the blend: the forward's binning (super-tile lists filtered per
+// tile by the rects), its final per-pixel state and count, the upstream
+// planes, and the 2D gradients [n][9] = (mean_x, mean_y, conic a, b, c,
+// opacity, r, g, b), accumulated.
 struct BlendBwdArgs {
-    int W, H, tiles_x;
+    int W, H, tiles_x, stiles_x;
     uint32_t n;
-    const uint2* tranges;          // [tiles] [start, end) into tvals
-    const uint32_t* tvals;         // per-tile front-to-back Gaussian ids
+    const uint2* sranges;          // [super-tiles] list ranges
+    const uint32_t* pair_words;    // sorted (super << 32 | id) pairs viewed as 32-bit words
+    const ushort4* rect;           // [n] tile rect
     Records rec;
     float3 bg;
     const float4* state;           // [W*H] final (T, T_x, T_y, T_xy)
@@ -130,8 +132,6 @@ struct gs_ctx {
     bool state_grads = false;           // the last blend carried derivatives (its state is usable)
     gs_gaussians last_g{};              // inputs and camera of the last projection
     gs::CameraParams last_cam{};
-    gs::DevBuf tile_vals;               // uint32[P] per-tile lists
-    gs::DevBuf tile_ranges;             // uint2[tiles]
     gs::DevBuf grad2d;                  // float[n][9]
     gs::DevBuf up_planes;               // float[12][H][W] upstream planes of gs_backward
     unsigned long long* h_scalar = nullptr;   // pinned host scalar for the pair count

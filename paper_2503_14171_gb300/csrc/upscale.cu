@@ -164,11 +164,20 @@ __global__ void __launch_bounds__(kThreadsX * kThreadsY) k_upscale(const float* 
 // dL/d(value of low-res pixel (i, j)) = sum over the output pixels whose cell
 // has (i, j) as a corner of (that corner's weight) * dL/dout.  Output pixel X
 // has (i, .) as its left corner when its cell is i (weights h00, h10 of t) and
-// as its right corner when its cell is i - 1 (weights h01, h11); the cells of
-// X lie in [(i - 1) s - 1, (i + 2) s] for those two cells (border cells
-// included).  One thread per low-res pixel gathers its 2D footprint with the
+// as its right corner when its cell is i - 1 (weights h01, h11).  Cells are
+// monotone in X, so the pixels of cell c are [first(c), first(c + 1)) with
+// first(c) the smallest X whose clamped floor((2X + 1 - s) / (2s)) is >= c:
+// 0 for c <= 0, W s for c > W - 2, else ceil((2 s c + s - 1) / 2).  One thread
+// per low-res pixel gathers exactly its (2s)^2 output pixels with the
 // separable weights: no atomics, each low-res value written once.
 constexpr int kBwdX = 32, kBwdY = 8;
+
+__device__ __forceinline__ int first_of_cell(int c, int s, int W)
+{
+    if (c <= 0) return 0;
+    if (c > W - 2) return W * s;
+    return (2 * s * c + s) / 2;   // ceil((2 s c + s - 1) / 2)
+}
 
 __global__ void __launch_bounds__(kBwdX * kBwdY) k_upscale_bwd(const float* __restrict__ dout, int W, int H, int s,
                                                                float* __restrict__ dC, float* __restrict__ dG)
@@ -178,29 +187,26 @@ __global__ void __launch_bounds__(kBwdX * kBwdY) k_upscale_bwd(const float* __re
     if (i >= W || j >= H) return;
     const int W2 = W * s, H2 = H * s;
     const size_t oplane = (size_t)W2 * H2;
-    const int Xa = max(0, (i - 1) * s - 1), Xb = min(W2 - 1, (i + 2) * s);
-    const int Ya = max(0, (j - 1) * s - 1), Yb = min(H2 - 1, (j + 2) * s);
+    const float inv2s = 1.f / (float)(2 * s);
+    const int xa = first_of_cell(i - 1, s, W), xm = first_of_cell(i, s, W), xb = first_of_cell(i + 1, s, W);
+    const int ya = first_of_cell(j - 1, s, H), ym = first_of_cell(j, s, H), yb = first_of_cell(j + 1, s, H);
     // acc[ch][q], q: value (H H), d/dx (G H), d/dy (H G), d2/dxdy (G G)
     float acc[3][4];
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[ch][q] = 0.f;
-    for (int Y = Ya; Y <= Yb; ++Y) {
-        int cj;
-        float u;
-        cell_of(Y, s, H, cj, u);
-        if (cj != j && cj != j - 1) continue;
-        const float4 hy = hermite(u);
-        const float wyH = cj == j ? hy.x : hy.y, wyG = cj == j ? hy.z : hy.w;
+    for (int Y = ya; Y < yb; ++Y) {
+        const bool right_y = Y < ym;            // cell j - 1: (., j) is its lower corner
+        const int cj = right_y ? j - 1 : j;
+        const float4 hy = hermite((float)(2 * Y + 1 - s - 2 * s * cj) * inv2s);
+        const float wyH = right_y ? hy.y : hy.x, wyG = right_y ? hy.w : hy.z;
         const float* row = dout + (size_t)Y * W2;
-        for (int X = Xa; X <= Xb; ++X) {
-            int ci;
-            float t;
-            cell_of(X, s, W, ci, t);
-            if (ci != i && ci != i - 1) continue;
-            const float4 hx = hermite(t);
-            const float wxH = ci == i ? hx.x : hx.y, wxG = ci == i ? hx.z : hx.w;
+        for (int X = xa; X < xb; ++X) {
+            const bool right_x = X < xm;
+            const int ci = right_x ? i - 1 : i;
+            const float4 hx = hermite((float)(2 * X + 1 - s - 2 * s * ci) * inv2s);
+            const float wxH = right_x ? hx.y : hx.x, wxG = right_x ? hx.w : hx.z;
             const float wHH = wxH * wyH, wGH = wxG * wyH, wHG = wxH * wyG, wGG = wxG * wyG;
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
