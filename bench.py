@@ -43,6 +43,10 @@ METRIC = "output MPix/s render+upscale vs direct full-res render, same GB300, at
 # pair with the derivative recurrences adds 52 (itemised beside the blend kernel).
 FLOP_EVAL = 10
 FLOP_ACC_GRADS = 52
+# The blend adjoint re-evaluates each pair (10) and, per blended pair, inverts
+# the state update, forms the weights, the adjoints and the 9 gradient terms
+# and sums them over the tile's pixels: 173 (itemised beside the kernel).
+FLOP_BWD_BLEND = 173
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -401,6 +405,34 @@ def run_gs(args):
         e2e_ms = a.elapsed_time(b) / ke
         e2e_ms = max_over_ranks(e2e_ms, "cuda", world)
 
+        # reverse mode of the same step (the paper's training with differentiable
+        # upscaling): gs_backward for a seeded dL/d(1920x1080 output), per stage
+        step()
+        dout = torch.randn(3, OUT_H, OUT_W, device="cuda", generator=torch.Generator("cuda").manual_seed(1))
+        dC = torch.empty(3, LOW_H, LOW_W, device="cuda")
+        dG = torch.empty(3, 3, LOW_H, LOW_W, device="cuda")
+        g2d = torch.empty(N_GAUSS, 9, device="cuda")
+        gr = ctx.backward(dout, FACTOR)
+        for _ in range(3):
+            ctx.upscale_backward(dout, LOW_W, LOW_H, FACTOR, out=(dC, dG))
+            ctx.render_backward(dC, dG, out=g2d)
+            ctx.project_backward(g2d, out=gr)
+        torch.cuda.synchronize()
+        kb = max(5, min(100, args.steps))
+        bev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(kb)]
+        barrier()
+        for k in range(kb):
+            bev[k][0].record(stream)
+            ctx.upscale_backward(dout, LOW_W, LOW_H, FACTOR, out=(dC, dG))
+            bev[k][1].record(stream)
+            ctx.render_backward(dC, dG, out=g2d)
+            bev[k][2].record(stream)
+            ctx.project_backward(g2d, out=gr)
+            bev[k][3].record(stream)
+        torch.cuda.synchronize()
+        tb = [statistics.mean(e[q].elapsed_time(e[q + 1]) for e in bev) for q in range(3)]
+        bwd_ms = max_over_ranks(statistics.mean(e[0].elapsed_time(e[3]) for e in bev), "cuda", world)
+
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -446,6 +478,13 @@ def run_gs(args):
                      "pairs_evaluated": n_eval, "pairs_blended": n_acc},
         "upscale_hbm": {"achieved_gbs": (LOW_W * LOW_H * 48 + OUT_W * OUT_H * 12) / (statistics.mean(t_up) * 1e-3) / 1e9,
                         "peak_gbs": peaks.get("hbm_gbs"), "peak_source": src},
+        "backward": {"ms_per_step": bwd_ms, "steps": kb,
+                     "stages_ms": {"upscale_adjoint": tb[0], "blend_adjoint": tb[1], "project_adjoint": tb[2]},
+                     "roofline": {"bound": "alu", "kernel": "k_blend_bwd<3dgs>",
+                                  "achieved": (n_eval * FLOP_EVAL + n_acc * FLOP_BWD_BLEND) / (tb[1] * 1e-3) / 1e12,
+                                  "peak": alu_peak, "unit": "TFLOP/s",
+                                  "frac": (n_eval * FLOP_EVAL + n_acc * FLOP_BWD_BLEND) / (tb[1] * 1e-3) / 1e12
+                                  / alu_peak}},
         "cpu_baseline": cpu,
         "e2e": {"value": OUT_W * OUT_H / 1e3 / e2e_ms, "unit": "MPix/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},

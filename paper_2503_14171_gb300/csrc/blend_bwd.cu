@@ -26,6 +26,12 @@
 // T_x = (T_x' + alpha T g_x)/(1 - alpha), ... (the supplement's inversion trick
 // written for T = 1 - A).
 //
+// Algorithmic work (FP32 operations, FMA = 2) per blended pair: g_x, g_y, g_xy'
+// 9; the state before the step 19; the weights w.. 14; dL/dc 21; G_w.. 24;
+// alpha_x.. 3; the adjoint update 18; G_alpha.. 14; dL/dg.. 14; the six
+// geometric and opacity terms 28; the sum over the tile's pixels 9: 173.
+// Re-evaluating a pair (d, g2, alpha) is 10, as in the forward.
+//
 // List walk.  A tile's front-to-back list is its super-tile's list filtered by
 // the tile rects (as in the forward).  The block first streams the super-tile
 // list in rounds of 256 candidates, recording the tile's list position at the
