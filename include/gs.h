@@ -112,9 +112,19 @@ typedef struct gs_options {
     int32_t tile;        /* tile side in pixels; 16 is the only supported value */
     int32_t mode;        /* GS_MODE_3DGS or GS_MODE_EXACT */
     float bg[3];         /* background colour composited behind the Gaussians */
-    int32_t reserved;
+    int32_t flags;       /* GS_FLAG_* bits; 0 = default */
     int64_t max_pairs;   /* upper bound on (tile, Gaussian) pairs; 0 = 2^30 - 1 */
 } gs_options;
+
+/* gs_options.flags: frames without a host wait.  gs_project then never waits
+ * for the pair count: the pair totals stay on the device, the pair buffers are
+ * those reserved with gs_reserve (no call allocates), and a frame whose pairs
+ * exceed them (or max_pairs) renders as background only, with
+ * GS_ERR_CAPACITY reported by the next gs_synchronize (gs_pair_count then
+ * gives the pairs the frame needed).  Requires gs_reserve first.  With it the
+ * project -> render -> upscale sequence makes no host-blocking call, so it can
+ * be captured in a CUDA graph. */
+#define GS_FLAG_NO_HOST_WAIT 1
 
 /* Human-readable name of a status code (static string). */
 const char* gs_status_string(gs_status status);
@@ -134,8 +144,16 @@ gs_status gs_destroy(gs_ctx* ctx);
 /* Change the stream later calls enqueue on. */
 gs_status gs_set_stream(gs_ctx* ctx, void* stream);
 
-/* Change blend mode / background / pair limit for later calls. */
+/* Change blend mode / background / pair limit / flags for later calls. */
 gs_status gs_set_options(gs_ctx* ctx, const gs_options* opt);
+
+/* Allocate every scratch buffer for frames of up to n Gaussians, W x H pixels
+ * and super_pairs (64x64-pixel super-tile, Gaussian) pairs, and fix those
+ * capacities.  Needed before frames with GS_FLAG_NO_HOST_WAIT; afterwards no
+ * call of this context allocates: a frame beyond n, W or H returns
+ * GS_ERR_CAPACITY at once, one beyond super_pairs as described for the flag.
+ * Synchronises the stream.  W x H <= 4096 super-tiles (e.g. 4096 x 4096). */
+gs_status gs_reserve(gs_ctx* ctx, int64_t n, int32_t W, int32_t H, int64_t super_pairs);
 
 /* Projection and tile binning for a W x H image (Sec. 4: EWA projection
  * Sigma' = J W Sigma W^T J^T + 0.3 I, front-to-back order).  Per Gaussian: view
@@ -143,7 +161,8 @@ gs_status gs_set_options(gs_ctx* ctx, const gs_options* opt);
  * and the tiles whose pixel centres fall in the square of that half-width; then
  * every (tile, Gaussian) pair is ordered by tile, FP32 depth bits, id.  Results
  * stay in ctx for gs_render_binned / gs_read_projected / gs_read_bins.
- * Synchronises the stream once (pair count readback). */
+ * Waits once for the pair count (to size the pair buffers), unless
+ * GS_FLAG_NO_HOST_WAIT is set. */
 gs_status gs_project(gs_ctx* ctx, const gs_gaussians* g, const gs_camera* cam, int32_t W, int32_t H);
 
 /* Blend the scene binned by the last gs_project.  Per pixel, front to back
@@ -236,8 +255,10 @@ gs_status gs_backward(gs_ctx* ctx, const float* dL_dout, int32_t factor, const g
 gs_status gs_render_with_grads_noalloc(const gs_gaussians* g, const gs_camera* cam, int32_t W, int32_t H,
                                        const gs_options* opt, void* stream, float* out_C, float* out_grads);
 
-/* Number of (tile, Gaussian) pairs of the last gs_project (host int64). */
-gs_status gs_pair_count(const gs_ctx* ctx, int64_t* P);
+/* Number of (tile, Gaussian) pairs of the last gs_project (host int64).  After
+ * a frame with GS_FLAG_NO_HOST_WAIT it waits for the stream and reads the count
+ * the frame produced (also when it exceeded the reservation). */
+gs_status gs_pair_count(gs_ctx* ctx, int64_t* P);
 
 /* Copy the last gs_project's per-Gaussian results to caller device buffers (any
  * may be NULL): mean2d [n][2], conic [n][3] (Sigma'^-1 as a, b, c), rgb [n][3],
@@ -268,7 +289,9 @@ gs_status gs_blend_stats(gs_ctx* ctx, int64_t* counts);
 gs_status gs_launch_count(const gs_ctx* ctx, int64_t* count);
 
 /* Wait for the context's stream and report any device-side error recorded by
- * its kernels since the last check (GS_ERR_TIMEOUT / GS_ERR_DEVICE_CHECK). */
+ * its kernels since the last check (GS_ERR_TIMEOUT / GS_ERR_DEVICE_CHECK, or
+ * GS_ERR_CAPACITY for a frame beyond its reservation under
+ * GS_FLAG_NO_HOST_WAIT). */
 gs_status gs_synchronize(gs_ctx* ctx);
 
 #ifdef __cplusplus

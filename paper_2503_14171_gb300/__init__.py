@@ -31,6 +31,7 @@ GS_ERR_NOT_READY = 7
 GS_MODE_3DGS = 0
 GS_MODE_EXACT = 1
 MODES = {"3dgs": GS_MODE_3DGS, "exact": GS_MODE_EXACT}
+GS_FLAG_NO_HOST_WAIT = 1
 
 
 class GsGaussians(ct.Structure):
@@ -46,7 +47,7 @@ class GsCamera(ct.Structure):
 
 class GsOptions(ct.Structure):
     _fields_ = [("tile", ct.c_int32), ("mode", ct.c_int32), ("bg", ct.c_float * 3),
-                ("reserved", ct.c_int32), ("max_pairs", ct.c_int64)]
+                ("flags", ct.c_int32), ("max_pairs", ct.c_int64)]
 
 
 class GsGaussianGrads(ct.Structure):
@@ -63,6 +64,7 @@ _SIGS = {
     "gs_destroy": ([_P], ct.c_int),
     "gs_set_stream": ([_P, _P], ct.c_int),
     "gs_set_options": ([_P, ct.POINTER(GsOptions)], ct.c_int),
+    "gs_reserve": ([_P, ct.c_int64, ct.c_int32, ct.c_int32, ct.c_int64], ct.c_int),
     "gs_project": ([_P, ct.POINTER(GsGaussians), ct.POINTER(GsCamera), ct.c_int32, ct.c_int32], ct.c_int),
     "gs_render_binned": ([_P, _P, _P], ct.c_int),
     "gs_render_with_grads": ([_P, ct.POINTER(GsGaussians), ct.POINTER(GsCamera), ct.c_int32, ct.c_int32, _P, _P],
@@ -257,7 +259,8 @@ class HostScene:
 class Context:
     """Owns a gs_ctx bound to a torch CUDA stream (default: the current stream)."""
 
-    def __init__(self, mode: str | int = "3dgs", bg=(0.0, 0.0, 0.0), stream=None, max_pairs: int = 0):
+    def __init__(self, mode: str | int = "3dgs", bg=(0.0, 0.0, 0.0), stream=None, max_pairs: int = 0,
+                 no_host_wait: bool = False):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("libgs needs a CUDA device")
@@ -268,6 +271,7 @@ class Context:
         for k in range(3):
             self.opt.bg[k] = float(bg[k])
         self.opt.max_pairs = int(max_pairs)
+        self.opt.flags = GS_FLAG_NO_HOST_WAIT if no_host_wait else 0
         self.h = gs_create(ct.c_void_p(self.stream.cuda_stream), self.opt)
         self.W = self.H = 0
 
@@ -287,6 +291,10 @@ class Context:
 
     def __exit__(self, *a):
         self.close()
+
+    def reserve(self, n: int, W: int, H: int, super_pairs: int):
+        """Allocate every buffer for frames up to these sizes (needed for no_host_wait)."""
+        _chk(lib.gs_reserve(self.h, int(n), int(W), int(H), int(super_pairs)), self.h, "gs_reserve")
 
     def set_options(self, mode=None, bg=None, max_pairs=None):
         if mode is not None:

@@ -61,6 +61,8 @@ gs_status ensure(gs_ctx* c, DevBuf& b, size_t bytes)
 {
     if (bytes == 0) bytes = 16;
     if (b.cap >= bytes) return GS_OK;
+    if (c->reserved)   // after gs_reserve no call allocates
+        return fail(c, GS_ERR_CAPACITY, "a buffer of %zu bytes exceeds the reserved capacity", bytes);
     size_t want = bytes + bytes / 4;
     if (b.p) {
         GS_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -104,6 +106,7 @@ gs_status check_options(gs_ctx* c, const gs_options* o)
     if (o->tile != kTile) return fail(c, GS_ERR_INVALID_ARG, "tile must be %d", kTile);
     if (o->mode != GS_MODE_3DGS && o->mode != GS_MODE_EXACT) return fail(c, GS_ERR_INVALID_ARG, "bad mode");
     if (o->max_pairs < 0) return fail(c, GS_ERR_INVALID_ARG, "max_pairs < 0");
+    if (o->flags & ~GS_FLAG_NO_HOST_WAIT) return fail(c, GS_ERR_INVALID_ARG, "unknown flags 0x%x", o->flags);
     return GS_OK;
 }
 
@@ -146,6 +149,16 @@ gs_status read_device_error(gs_ctx* c)
     if (h != kDevOk) {
         GS_CUDA(c, cudaMemsetAsync(c->errword.p, 0, sizeof(int), c->stream));
         if (h == kDevTimeout) return fail(c, GS_ERR_TIMEOUT, "a bounded device wait expired");
+        if (h == kDevCapacity) {
+            PairCheckOut o{};
+            if (c->pair_check.p) {
+                GS_CUDA(c, cudaMemcpy(&o, c->pair_check.p, sizeof(o), cudaMemcpyDeviceToHost));
+            }
+            return fail(c, GS_ERR_CAPACITY,
+                        "a frame needed %llu super-tile pairs (reserved %lld) and %llu tile pairs (limit %lld); "
+                        "it was rendered without Gaussians", o.needed, (long long)c->res_pairs, o.tile_pairs,
+                        (long long)(c->opt.max_pairs > 0 ? c->opt.max_pairs : kMaxPairs));
+        }
         return fail(c, GS_ERR_DEVICE_CHECK, "a device-side check failed (code %d)", h);
     }
     return GS_OK;
@@ -166,6 +179,12 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
     const int64_t Ts = (int64_t)stiles_x * stiles_y;
     if (T > 0x7FFFFFFF) return fail(c, GS_ERR_INVALID_ARG, "too many tiles");
     const uint32_t n = (uint32_t)g->n;
+    const bool no_wait = (c->opt.flags & GS_FLAG_NO_HOST_WAIT) != 0;
+    if (no_wait) {
+        if (!c->reserved) return fail(c, GS_ERR_NOT_READY, "GS_FLAG_NO_HOST_WAIT needs gs_reserve first");
+        if ((int64_t)n > c->res_n || T > c->res_tiles || Ts > c->res_supers || (int64_t)W * H > c->res_pixels)
+            return fail(c, GS_ERR_CAPACITY, "frame (n %u, %d x %d) exceeds the reserved sizes", n, W, H);
+    }
 
     // per-Gaussian scratch
     if ((st = ensure(c, c->rec0, sizeof(float4) * n)) || (st = ensure(c, c->rec1, sizeof(float4) * n)) ||
@@ -197,10 +216,12 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
                               as<int>(c->radius), as<ushort4>(c->rect), as<uint32_t>(c->tiles_touched),
                               as<uint32_t>(c->supers_touched), as<uint32_t>(c->dkey[0]), as<uint32_t>(c->did[0]),
                               totals));
-    // the pair totals travel to the host while the depth sort runs
-    GS_CUDA(c, cudaMemcpyAsync(c->h_scalar, totals, 2 * kTotalSlots * sizeof(unsigned long long),
-                               cudaMemcpyDeviceToHost, c->stream));
-    GS_CUDA(c, cudaEventRecord(c->totals_ready, c->stream));
+    if (!no_wait) {
+        // the pair totals travel to the host while the depth sort runs
+        GS_CUDA(c, cudaMemcpyAsync(c->h_scalar, totals, 2 * kTotalSlots * sizeof(unsigned long long),
+                                   cudaMemcpyDeviceToHost, c->stream));
+        GS_CUDA(c, cudaEventRecord(c->totals_ready, c->stream));
+    }
 
     // depth order (stable radix sort of the FP32 depth bits, ids ascending) and
     // the super-tile pair offsets in that order
@@ -233,6 +254,42 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
     }
     c->sorted_ids_buf = sorted;
     const uint32_t* ids = as<uint32_t>(c->did[sorted]);
+    const int64_t limit = c->opt.max_pairs > 0 ? std::min<int64_t>(c->opt.max_pairs, kMaxPairs) : kMaxPairs;
+
+    if (no_wait) {
+        // the pair totals stay on the device: emit into the reserved buffers and
+        // let the histogram kernel check the frame against their capacity
+        const uint32_t cap = (uint32_t)c->res_pairs;
+        const int sbits = bits_for((uint32_t)Ts);
+        const int spasses = radix_passes(32, 32 + sbits);
+        uint64_t* pairs[2] = {as<uint64_t>(c->pairs[0]), as<uint64_t>(c->pairs[1])};
+        PairCheckOut* chk = as<PairCheckOut>(c->pair_check);
+        GS_CUDA(c, cudaMemsetAsync(c->super_counts.p, 0, sizeof(uint32_t) * kCountCopies * Ts, c->stream));
+        GS_CUDA(c, launch_emit_pairs(c->stream, ids, as<uint32_t>(c->offsets), as<ushort4>(c->rect), n, stiles_x,
+                                     pairs[0], as<uint32_t>(c->super_counts), (uint32_t)Ts, cap));
+        GS_CUDA(c, launch_supers_to_hist(c->stream, as<uint32_t>(c->super_counts), (uint32_t)Ts, spasses,
+                                         as<uint32_t>(c->sort_hist), as<uint2>(c->sranges),
+                                         PairCheckIn{totals, cap, (unsigned long long)limit}, chk,
+                                         as<int>(c->errword)));
+        int psorted = 0;
+        if (Ts > 1 && cap > 1)
+            GS_CUDA(c, radix_sort_u64_keys(c->stream, pairs, cap, 32, 32 + sbits, as<uint32_t>(c->sort_hist),
+                                           as<uint32_t>(c->sort_status), as<uint32_t>(c->sort_counter),
+                                           as<int>(c->errword), &psorted, true, &chk->count));
+        c->sorted_pairs_buf = psorted;
+        c->n = n;
+        c->W = W;
+        c->H = H;
+        c->tiles_x = tiles_x;
+        c->tiles_y = tiles_y;
+        c->stiles_x = stiles_x;
+        c->stiles_y = stiles_y;
+        c->P = -1;
+        c->Ps = -1;
+        c->totals_known = false;
+        c->have_proj = true;
+        return GS_OK;
+    }
 
     GS_CUDA(c, cudaEventSynchronize(c->totals_ready));
     unsigned long long Ps64 = 0, P64 = 0;
@@ -240,7 +297,6 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
         Ps64 += c->h_scalar[2 * k];
         P64 += c->h_scalar[2 * k + 1];
     }
-    const int64_t limit = c->opt.max_pairs > 0 ? std::min<int64_t>(c->opt.max_pairs, kMaxPairs) : kMaxPairs;
     if ((int64_t)P64 > limit)
         return fail(c, GS_ERR_CAPACITY, "pair count %llu exceeds the limit %lld", P64, (long long)limit);
     if ((int64_t)Ps64 > kMaxPairs)
@@ -288,6 +344,7 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
     c->stiles_y = stiles_y;
     c->P = (int64_t)P64;
     c->Ps = Ps;
+    c->totals_known = true;
     c->have_proj = true;
     return GS_OK;
 }
@@ -407,7 +464,7 @@ gs_status gs_destroy(gs_ctx* c)
                       &c->pairs[1],
                       &c->sort_hist, &c->sort_status,
                       &c->sort_counter, &c->sranges, &c->tile_count, &c->tile_start, &c->state, &c->count,
-                      &c->errword, &c->grad2d, &c->up_planes};
+                      &c->errword, &c->grad2d, &c->up_planes, &c->pair_check};
     for (DevBuf* b : bufs) release(*b);
     if (c->h_scalar) cudaFreeHost(c->h_scalar);
     if (c->totals_ready) cudaEventDestroy(c->totals_ready);
@@ -574,11 +631,82 @@ gs_status gs_backward(gs_ctx* c, const float* dL_dout, int32_t factor, const gs_
     return do_project_backward(c, as<float>(c->grad2d), out);
 }
 
-gs_status gs_pair_count(const gs_ctx* c, int64_t* P)
+namespace {
+
+// P and Ps of the last projection; after a frame without a host wait they are
+// read from the device (waiting for the stream).
+gs_status known_totals(gs_ctx* c)
+{
+    if (c->totals_known) return GS_OK;
+    PairCheckOut o{};
+    GS_CUDA(c, cudaMemcpyAsync(&o, c->pair_check.p, sizeof(o), cudaMemcpyDeviceToHost, c->stream));
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->P = (int64_t)o.tile_pairs;
+    c->Ps = (int64_t)o.needed;
+    c->totals_known = true;
+    return GS_OK;
+}
+
+}  // namespace
+
+gs_status gs_pair_count(gs_ctx* c, int64_t* P)
 {
     if (!c || !P) return GS_ERR_INVALID_ARG;
     if (!c->have_proj) return GS_ERR_NOT_READY;
+    gs_status st = known_totals(c);
+    if (st != GS_OK) return st;
     *P = c->P;
+    return GS_OK;
+}
+
+gs_status gs_reserve(gs_ctx* c, int64_t n, int32_t W, int32_t H, int64_t super_pairs)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (n < 0 || n > 0x7FFFFFFF || W < 1 || H < 1 || super_pairs < 1 || super_pairs > kMaxPairs)
+        return fail(c, GS_ERR_INVALID_ARG, "bad reserve sizes");
+    const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
+    const int stiles_x = (tiles_x + kSuper - 1) / kSuper, stiles_y = (tiles_y + kSuper - 1) / kSuper;
+    const int64_t T = (int64_t)tiles_x * tiles_y, Ts = (int64_t)stiles_x * stiles_y;
+    if (Ts > kMaxSupersForCounts)
+        return fail(c, GS_ERR_INVALID_ARG, "%lld super-tiles exceed %d", (long long)Ts, kMaxSupersForCounts);
+    const size_t un = (size_t)std::max<int64_t>(n, 1), pix = (size_t)W * H;
+    const uint32_t nn = (uint32_t)un;
+    c->reserved = false;
+    gs_status st;
+    const int sbits = bits_for((uint32_t)Ts);
+    const uint32_t ds_cap = depth_sort_capacity(c->device);
+    const size_t G = ds_cap / kDsMaxSlice;
+    if ((st = ensure(c, c->rec0, sizeof(float4) * un)) || (st = ensure(c, c->rec1, sizeof(float4) * un)) ||
+        (st = ensure(c, c->rec2, sizeof(float4) * un)) || (st = ensure(c, c->depth, sizeof(float) * un)) ||
+        (st = ensure(c, c->radius, sizeof(int) * un)) || (st = ensure(c, c->rect, sizeof(ushort4) * un)) ||
+        (st = ensure(c, c->tiles_touched, sizeof(uint32_t) * un)) ||
+        (st = ensure(c, c->supers_touched, sizeof(uint32_t) * un)) ||
+        (st = ensure(c, c->dkey[0], sizeof(uint32_t) * un)) || (st = ensure(c, c->dkey[1], sizeof(uint32_t) * un)) ||
+        (st = ensure(c, c->did[0], sizeof(uint32_t) * un)) || (st = ensure(c, c->did[1], sizeof(uint32_t) * un)) ||
+        (st = ensure(c, c->offsets, sizeof(uint32_t) * (un + 1))) ||
+        (st = ensure(c, c->scan_partials, sizeof(unsigned long long) * scan_partials_count(nn))) ||
+        (st = ensure(c, c->scan_totals, (2 * kTotalSlots + 4) * sizeof(unsigned long long))) ||
+        (st = ensure(c, c->super_counts, sizeof(uint32_t) * kCountCopies * Ts)) ||
+        (st = ensure(c, c->sranges, sizeof(uint2) * Ts)) || (st = ensure(c, c->sort_hist, sizeof(uint32_t) * 8 * 256)) ||
+        (st = ensure(c, c->sort_status,
+                     sizeof(uint32_t) * std::max(radix_status_words((uint32_t)super_pairs, 32, 32 + sbits),
+                                                 radix_status_words(nn, 0, 32)))) ||
+        (st = ensure(c, c->sort_counter, sizeof(uint32_t) * 8)) ||
+        (st = ensure(c, c->ds_scratch, G * kRadixDigits * 4 + G * 8 + 64 + 4 * kRadixDigits * 4)) ||
+        (st = ensure(c, c->pairs[0], sizeof(uint64_t) * (size_t)super_pairs)) ||
+        (st = ensure(c, c->pairs[1], sizeof(uint64_t) * (size_t)super_pairs)) ||
+        (st = ensure(c, c->state, sizeof(float4) * pix)) || (st = ensure(c, c->count, sizeof(int) * pix)) ||
+        (st = ensure(c, c->tile_count, sizeof(uint32_t) * T)) || (st = ensure(c, c->tile_start, sizeof(uint32_t) * T)) ||
+        (st = ensure(c, c->grad2d, sizeof(float) * 9 * un)) || (st = ensure(c, c->up_planes, sizeof(float) * 12 * pix)) ||
+        (st = ensure(c, c->pair_check, sizeof(PairCheckOut))))
+        return st;
+    GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->res_n = n;
+    c->res_pixels = (int64_t)pix;
+    c->res_tiles = T;
+    c->res_supers = Ts;
+    c->res_pairs = super_pairs;
+    c->reserved = true;
     return GS_OK;
 }
 
@@ -598,6 +726,8 @@ gs_status gs_read_bins(gs_ctx* c, uint64_t* keys, uint32_t* vals, uint32_t* rang
 {
     if (!c) return GS_ERR_INVALID_ARG;
     if (!c->have_proj) return fail(c, GS_ERR_NOT_READY, "no projection");
+    gs_status st0 = known_totals(c);
+    if (st0 != GS_OK) return st0;
     if ((keys || vals) && capacity < c->P) return fail(c, GS_ERR_CAPACITY, "capacity %lld < P %lld",
                                                        (long long)capacity, (long long)c->P);
     LaunchTally tally(c);
@@ -635,8 +765,11 @@ gs_status gs_blend_stats(gs_ctx* c, int64_t* counts)
     if (!c->have_proj) return fail(c, GS_ERR_NOT_READY, "no projection");
     LaunchTally tally(c);
     DevBuf tmp;
-    gs_status st = ensure(c, tmp, 2 * sizeof(unsigned long long));
-    if (st != GS_OK) return st;
+    if (cudaMalloc(&tmp.p, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, GS_ERR_OOM, "gs_blend_stats: cudaMalloc failed");
+    }
+    tmp.cap = 2 * sizeof(unsigned long long);
     unsigned long long h[2] = {0, 0};
     cudaError_t e = cudaMemsetAsync(tmp.p, 0, 2 * sizeof(unsigned long long), c->stream);
     if (e == cudaSuccess) {

@@ -22,7 +22,7 @@ template <bool COUNT>
 __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ ids, const uint32_t* __restrict__ offsets,
                                               const ushort4* __restrict__ rect, uint32_t n, int stiles_x,
                                               uint64_t* __restrict__ pairs, uint32_t* __restrict__ counts,
-                                              uint32_t Ts)
+                                              uint32_t Ts, uint32_t cap)
 {
     __shared__ uint32_t s_cnt[COUNT ? kMaxSupersForCounts : 1];
     if (COUNT) {
@@ -40,7 +40,8 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ ids, 
             for (int sy = sy0; sy <= sy1; ++sy)
                 for (int sx = sx0; sx <= sx1 && off < end; ++sx) {
                     const uint32_t s = (uint32_t)(sy * stiles_x + sx);
-                    pairs[off++] = ((uint64_t)s << 32) | id;
+                    if (off < cap) pairs[off] = ((uint64_t)s << 32) | id;
+                    ++off;
                     if (COUNT && s < Ts) atomicAdd(&s_cnt[s], 1u);
                 }
         }
@@ -149,13 +150,13 @@ __global__ void __launch_bounds__(1024) k_tile_starts(const uint32_t* __restrict
 }  // namespace
 
 cudaError_t launch_emit_pairs(cudaStream_t s, const uint32_t* ids, const uint32_t* offsets, const ushort4* rect,
-                              uint32_t n, int stiles_x, uint64_t* pairs, uint32_t* counts, uint32_t Ts)
+                              uint32_t n, int stiles_x, uint64_t* pairs, uint32_t* counts, uint32_t Ts, uint32_t cap)
 {
     if (n == 0) return cudaSuccess;
     if (counts && Ts <= (uint32_t)kMaxSupersForCounts)
-        k_emit<true><<<(n + 255) / 256, 256, 0, s>>>(ids, offsets, rect, n, stiles_x, pairs, counts, Ts);
+        k_emit<true><<<(n + 255) / 256, 256, 0, s>>>(ids, offsets, rect, n, stiles_x, pairs, counts, Ts, cap);
     else
-        k_emit<false><<<(n + 255) / 256, 256, 0, s>>>(ids, offsets, rect, n, stiles_x, pairs, nullptr, 0);
+        k_emit<false><<<(n + 255) / 256, 256, 0, s>>>(ids, offsets, rect, n, stiles_x, pairs, nullptr, 0, cap);
     note_launch();
     return cudaGetLastError();
 }

@@ -329,9 +329,20 @@ cudaError_t launch_depth_sort_scan(cudaStream_t s, int device, const uint32_t* k
     a.bar = bar;
     a.err = err;
     a.n = n;
-    void* args[] = {&a};
-    e = cudaLaunchCooperativeKernel((const void*)k_depth_sort_scan, dim3(grid), dim3(kDsThreads), args,
-                                    depth_sort_smem_bytes(), s);
+    // a cooperative launch (all blocks co-resident, checked against the
+    // occupancy above); launched through cudaLaunchKernelEx so that it can be
+    // recorded in a CUDA graph
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kDsThreads);
+    cfg.dynamicSmemBytes = depth_sort_smem_bytes();
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_depth_sort_scan, a);
     note_launch();
     *out_idx = (kDsPasses - 1) & 1;
     return e;

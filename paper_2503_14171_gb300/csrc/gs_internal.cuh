@@ -16,6 +16,7 @@ constexpr int kSuper = 4;                 // super-tile side in tiles (64 x 64 p
 constexpr int kDevOk = 0;
 constexpr int kDevTimeout = 1;
 constexpr int kDevCheck = 2;
+constexpr int kDevCapacity = 3;   // a frame's pairs exceeded the reserved pair buffers
 
 // The projection sums the frame's pair totals into kTotalSlots slot pairs
 // (super-tile pairs, tile pairs) to spread its atomics; the host adds the slots.
@@ -133,6 +134,11 @@ struct gs_ctx {
     gs_gaussians last_g{};              // inputs and camera of the last projection
     gs::CameraParams last_cam{};
     gs::DevBuf grad2d;                  // float[n][9]
+    // frames without a host wait (GS_FLAG_NO_HOST_WAIT): buffers reserved up front
+    bool reserved = false;
+    int64_t res_n = 0, res_pixels = 0, res_tiles = 0, res_supers = 0, res_pairs = 0;
+    gs::DevBuf pair_check;              // gs::PairCheckOut, device side
+    bool totals_known = true;           // P, Ps valid on the host
     gs::DevBuf up_planes;               // float[12][H][W] upstream planes of gs_backward
     unsigned long long* h_scalar = nullptr;   // pinned host scalar for the pair count
     int sorted_ids_buf = 0;             // which did[] holds the depth-sorted ids
@@ -162,14 +168,29 @@ cudaError_t radix_sort_u32_pairs(cudaStream_t s, uint32_t* keys[2], uint32_t* va
                                  uint32_t* counters, int* err, int* out_idx);
 // hist_ready: hist already holds the exclusive digit histograms of every pass
 // (from launch_supers_to_hist), so the sort skips its histogram kernels.
+// n_dev (optional, needs hist_ready): the key count is min(n, *n_dev), read on
+// the device; n is then the capacity the launch is sized for.
 cudaError_t radix_sort_u64_keys(cudaStream_t s, uint64_t* keys[2], uint32_t n, int bit_lo, int bit_hi,
                                 uint32_t* hist, uint32_t* status, uint32_t* counters, int* err,
-                                int* out_idx, bool hist_ready);
+                                int* out_idx, bool hist_ready, const uint32_t* n_dev = nullptr);
 // Largest super-tile count whose per-super-tile counts the emission kernel
 // accumulates in shared memory (and turns into histograms + ranges).
 constexpr int kMaxSupersForCounts = 4096;
+// Device-side pair-count check of a frame whose totals the host does not read
+// (see k_supers_to_hist): inputs slots (the projection's 2 x kTotalSlots pair
+// totals), cap, max_pairs; outputs count (pairs to sort, 0 on overflow),
+// needed and tile_pairs (the frame's totals).
+struct PairCheckIn {
+    const unsigned long long* slots;
+    unsigned long long cap, max_pairs;
+};
+struct PairCheckOut {
+    unsigned long long needed, tile_pairs;
+    uint32_t count;
+};
 cudaError_t launch_supers_to_hist(cudaStream_t s, uint32_t* counts, uint32_t Ts, int passes, uint32_t* hist,
-                                  uint2* ranges);
+                                  uint2* ranges, PairCheckIn in = PairCheckIn{nullptr, 0, 0},
+                                  PairCheckOut* out = nullptr, int* err = nullptr);
 size_t radix_status_words(uint32_t n, int bit_lo, int bit_hi);
 int radix_passes(int bit_lo, int bit_hi);
 
@@ -194,8 +215,11 @@ cudaError_t launch_depth_sort_scan(cudaStream_t s, int device, const uint32_t* k
                                    uint32_t* cnt_scratch, unsigned long long* bsum_scratch, unsigned int* bar,
                                    uint32_t* tot_scratch, int* err, int* out_idx);
 
+// pairs at offsets >= cap are counted but not written (the capacity check of
+// launch_supers_to_hist then rejects the frame)
 cudaError_t launch_emit_pairs(cudaStream_t s, const uint32_t* ids, const uint32_t* offsets, const ushort4* rect,
-                              uint32_t n, int stiles_x, uint64_t* pairs, uint32_t* counts, uint32_t Ts);
+                              uint32_t n, int stiles_x, uint64_t* pairs, uint32_t* counts, uint32_t Ts,
+                              uint32_t cap = 0xFFFFFFFFu);
 cudaError_t launch_ranges(cudaStream_t s, const uint64_t* pairs, uint32_t P, uint32_t T, uint2* ranges);
 // per-tile lists from the super-tile lists: counts, starts, ranges and (optionally) keys/vals
 cudaError_t launch_tile_lists(cudaStream_t s, const uint64_t* spairs, const uint2* sranges, const ushort4* rect,

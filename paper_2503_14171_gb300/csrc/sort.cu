@@ -106,11 +106,13 @@ __global__ void __launch_bounds__(kThreads) k_onesweep(const K* __restrict__ key
                                                        uint32_t* __restrict__ vals_out, uint32_t n, int shift,
                                                        const uint32_t* __restrict__ digit_base,
                                                        uint32_t* __restrict__ status,
-                                                       uint32_t* __restrict__ tile_counter, int* __restrict__ err)
+                                                       uint32_t* __restrict__ tile_counter, int* __restrict__ err,
+                                                       const uint32_t* __restrict__ n_dev)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto& S = *reinterpret_cast<OnesweepSmem<K, HAS_VAL>*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (n_dev) n = min(n, *n_dev);   // key count known on the device only; surplus tiles exit
 
     for (int i = tid; i < kWarps * kRadix; i += kThreads) (&S.warp_hist[0][0])[i] = 0;
     if (tid == 0) S.tile = atomicAdd(tile_counter, 1u);   // tiles are taken in launch order
@@ -244,7 +246,7 @@ __global__ void __launch_bounds__(kThreads) k_onesweep(const K* __restrict__ key
 template <typename K, bool HAS_VAL>
 cudaError_t radix_sort_impl(cudaStream_t s, K* keys[2], uint32_t* vals[2], uint32_t n, int bit_lo, int bit_hi,
                             uint32_t* hist, uint32_t* status, uint32_t* counters, int* err, int* out_idx,
-                            bool hist_ready)
+                            bool hist_ready, const uint32_t* n_dev = nullptr)
 {
     *out_idx = 0;
     if (n <= 1 || bit_hi <= bit_lo) return cudaSuccess;
@@ -272,7 +274,7 @@ cudaError_t radix_sort_impl(cudaStream_t s, K* keys[2], uint32_t* vals[2], uint3
         const int shift = bit_lo + p * kRadixBits;
         k_onesweep<K, HAS_VAL><<<tiles, kThreads, smem, s>>>(
             keys[cur], keys[cur ^ 1], HAS_VAL ? vals[cur] : nullptr, HAS_VAL ? vals[cur ^ 1] : nullptr, n, shift,
-            hist + p * kRadix, status + (size_t)p * tiles * kRadix, counters + p, err); note_launch();
+            hist + p * kRadix, status + (size_t)p * tiles * kRadix, counters + p, err, n_dev); note_launch();
         cur ^= 1;
     }
     *out_idx = cur;
@@ -412,40 +414,74 @@ cudaError_t radix_sort_u32_pairs(cudaStream_t s, uint32_t* keys[2], uint32_t* va
                                  int* out_idx)
 {
     return radix_sort_impl<uint32_t, true>(s, keys, vals, n, bit_lo, bit_hi, hist, status, counters, err, out_idx,
-                                           false);
+                                           false, nullptr);
 }
 
 cudaError_t radix_sort_u64_keys(cudaStream_t s, uint64_t* keys[2], uint32_t n, int bit_lo, int bit_hi,
                                 uint32_t* hist, uint32_t* status, uint32_t* counters, int* err, int* out_idx,
-                                bool hist_ready)
+                                bool hist_ready, const uint32_t* n_dev)
 {
     uint32_t* no_vals[2] = {nullptr, nullptr};
+    if (n_dev && !hist_ready) return cudaErrorInvalidValue;   // the histogram kernels need the count on the host
     return radix_sort_impl<uint64_t, false>(s, keys, no_vals, n, bit_lo, bit_hi, hist, status, counters, err,
-                                            out_idx, hist_ready);
+                                            out_idx, hist_ready, n_dev);
 }
 
 // Per-super-tile counts -> (a) the exclusive digit histograms of every radix
 // pass over the super-tile bits (bits [32, 32 + 8 passes) of the pair keys) and
 // (b) the [start, end) range of every super-tile's run in the sorted list.
 // One block; Ts <= kMaxSupersForCounts.
+//
+// With a capacity check (out != nullptr): the pair totals stay on the device.
+// If the frame's super-tile pairs exceed in.cap (the pair buffers) or its tile
+// pairs (the sum of the odd entries of in.slots) exceed in.max_pairs, every
+// range is left empty (the blend then sees no Gaussians), out->count = 0 so
+// the sort does nothing, and the error word reports the overflow;
+// out->needed / out->tile_pairs keep the frame's totals for the host.
 __global__ void __launch_bounds__(kThreads) k_supers_to_hist(uint32_t* __restrict__ counts, uint32_t Ts,
                                                              int passes, uint32_t* __restrict__ hist,
-                                                             uint2* __restrict__ ranges)
+                                                             uint2* __restrict__ ranges, PairCheckIn in,
+                                                             PairCheckOut* out, int* __restrict__ err)
 {
     __shared__ uint32_t s_hist[kHistPasses][kRadix];
     __shared__ uint32_t s_warp[kWarps];
+    __shared__ unsigned long long s_sum[kWarps];
+    __shared__ int s_ok;
     for (int i = threadIdx.x; i < kHistPasses * kRadix; i += kThreads) (&s_hist[0][0])[i] = 0;
     __syncthreads();
     // the counts arrive as kCountCopies partial arrays; fold them into copy 0
+    unsigned long long mine = 0;
     for (uint32_t t = threadIdx.x; t < Ts; t += kThreads) {
         uint32_t c = 0;
         for (int k = 0; k < kCountCopies; ++k) c += counts[(size_t)k * Ts + t];
         counts[t] = c;
+        mine += c;
         for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p][(t >> (p * kRadixBits)) & (kRadix - 1)], c);
     }
-    __syncthreads();
-    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (out) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+        if (lane == 0) s_sum[warp] = mine;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long ps = 0, p = 0;
+            for (int w = 0; w < kWarps; ++w) ps += s_sum[w];
+            for (int k = 0; k < kTotalSlots; ++k) p += in.slots[2 * k + 1];
+            const bool ok = ps <= in.cap && p <= in.max_pairs;
+            out->needed = ps;
+            out->tile_pairs = p;
+            out->count = ok ? (uint32_t)ps : 0u;
+            if (!ok) atomicExch(err, kDevCapacity);
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) {
+            for (uint32_t t = threadIdx.x; t < Ts; t += kThreads) ranges[t] = make_uint2(0u, 0u);
+            return;
+        }
+    }
+    __syncthreads();
     for (int p = 0; p < passes; ++p) {
         const uint32_t v = s_hist[p][threadIdx.x];
         uint32_t x = v;
@@ -487,9 +523,9 @@ __global__ void __launch_bounds__(kThreads) k_supers_to_hist(uint32_t* __restric
 }
 
 cudaError_t launch_supers_to_hist(cudaStream_t s, uint32_t* counts, uint32_t Ts, int passes, uint32_t* hist,
-                                  uint2* ranges)
+                                  uint2* ranges, PairCheckIn in, PairCheckOut* out, int* err)
 {
-    k_supers_to_hist<<<1, kThreads, 0, s>>>(counts, Ts, passes, hist, ranges); note_launch();
+    k_supers_to_hist<<<1, kThreads, 0, s>>>(counts, Ts, passes, hist, ranges, in, out, err); note_launch();
     return cudaGetLastError();
 }
 
