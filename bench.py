@@ -319,13 +319,11 @@ def run_gs(args):
             step()
         torch.cuda.synchronize()
         P_low = ctx.pair_count()
+        Ps_low = ctx.super_pair_count()
         n_eval, n_acc = ctx.blend_stats()
 
         evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
         clocks = ClockSampler(local)
-        clocks.start()
-        time.sleep(0.3)
-        l0 = ctx.launch_count()
         barrier()
         torch.cuda.synchronize()
         start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -335,14 +333,57 @@ def run_gs(args):
         end.record(stream)
         torch.cuda.synchronize()
         barrier()
-        launches = ctx.launch_count() - l0
-        clocks.stop()
         total_ms = start.elapsed_time(end)
         t_proj = [e[0].elapsed_time(e[1]) for e in evs]
         t_blend = [e[1].elapsed_time(e[2]) for e in evs]
         t_up = [e[2].elapsed_time(e[3]) for e in evs]
 
-        total_ms = max_over_ranks(total_ms, "cuda", world)
+        eager_ms = max_over_ranks(total_ms, "cuda", world) / args.steps
+
+        # the same step recorded once in a CUDA graph (frames without a host
+        # wait, buffers reserved up front) and replayed: the timed region
+        def graphed(Wr, Hr, pairs, body):
+            gc = gs.Context(stream=stream, no_host_wait=True)
+            gc.reserve(N_GAUSS, Wr, Hr, pairs)
+            with torch.cuda.stream(stream):
+                body(gc)
+                torch.cuda.synchronize()
+                l0g = gc.launch_count()
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=stream):
+                    body(gc)
+                nl = gc.launch_count() - l0g
+                for _ in range(3):
+                    g.replay()
+                torch.cuda.synchronize()
+            gc.synchronize()
+            return gc, g, nl
+
+        def main_body(gc):
+            gc.project(dev, cam, LOW_W, LOW_H)
+            gc.render_binned(grads=True, out_C=C, out_grads=G)
+            gc.upscale(C, G, FACTOR, out=out)
+
+        # pair buffers: the frame's super-tile pairs with 10 % headroom
+        gctx, graph, launches_per_step = graphed(LOW_W, LOW_H, Ps_low + Ps_low // 10 + 4096, main_body)
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                graph.replay()
+            torch.cuda.synchronize()
+            clocks.start()
+            time.sleep(0.3)
+            barrier()
+            torch.cuda.synchronize()
+            start.record(stream)
+            for k in range(args.steps):
+                graph.replay()
+            end.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+            clocks.stop()
+        gctx.synchronize()
+        launches = launches_per_step * args.steps
+        total_ms = max_over_ranks(start.elapsed_time(end), "cuda", world)
         ms_step = total_ms / args.steps
         value = job_throughput(world, args.steps, OUT_W * OUT_H / 1e6, total_ms)
 
@@ -361,8 +402,15 @@ def run_gs(args):
 
         direct = torch.empty(3, OUT_H, OUT_W, device="cuda")
         kd = max(10, args.steps // 3)
-        ms_direct = time_loop(lambda: ctx.render(dev, cam_hi, OUT_W, OUT_H, out_C=direct), kd)
+        ms_direct_eager = time_loop(lambda: ctx.render(dev, cam_hi, OUT_W, OUT_H, out_C=direct), kd)
         P_direct = ctx.pair_count()
+        Ps_direct = ctx.super_pair_count()
+        gctx_d, graph_d, _ = graphed(OUT_W, OUT_H, Ps_direct + Ps_direct // 10 + 4096,
+                                     lambda gc: gc.render(dev, cam_hi, OUT_W, OUT_H, out_C=direct))
+        with torch.cuda.stream(stream):
+            ms_direct = time_loop(graph_d.replay, kd)
+        gctx_d.synchronize()
+        gctx_d.close()
         # 4x path: 480x270 -> 1920x1080
         C4 = torch.empty(3, OUT_H // 4, OUT_W // 4, device="cuda")
         G4 = torch.empty(3, 3, OUT_H // 4, OUT_W // 4, device="cuda")
@@ -372,10 +420,23 @@ def run_gs(args):
             ctx.render_with_grads(dev, cam4, OUT_W // 4, OUT_H // 4, out_C=C4, out_grads=G4)
             ctx.upscale(C4, G4, 4, out=out4)
 
-        ms_4x = time_loop(step4, kd)
+        ms_4x_eager = time_loop(step4, kd)
+        Ps_4x = ctx.super_pair_count()
+
+        def body4(gc):
+            gc.render_with_grads(dev, cam4, OUT_W // 4, OUT_H // 4, out_C=C4, out_grads=G4)
+            gc.upscale(C4, G4, 4, out=out4)
+
+        gctx_4, graph_4, _ = graphed(OUT_W // 4, OUT_H // 4, Ps_4x + Ps_4x // 10 + 4096, body4)
+        with torch.cuda.stream(stream):
+            ms_4x = time_loop(graph_4.replay, kd)
+        gctx_4.synchronize()
         # quality: the timed frames' outputs vs the direct render
-        step()
+        with torch.cuda.stream(stream):
+            graph_4.replay()
+            graph.replay()
         torch.cuda.synchronize()
+        gctx_4.close()
         d_np = direct.cpu().numpy()
         psnr2 = psnr(out.cpu().numpy(), d_np)
         psnr4 = psnr(out4.cpu().numpy(), d_np)
@@ -470,6 +531,10 @@ def run_gs(args):
         "speedup_vs_direct": (OUT_W * OUT_H / 1e3 / ms_step) / (OUT_W * OUT_H / 1e3 / ms_direct),
         "psnr_db": {"2x_960x540": psnr2, "4x_480x270": psnr4, "vs": "direct 1920x1080 render, clipped to [0,1]"},
         "path_4x": {"mpix_s": OUT_W * OUT_H / 1e3 / ms_4x, "ms": ms_4x},
+        "eager": {"note": "the same steps through the API one call at a time, gs_project waiting once for the "
+                          "pair count (value, direct_render and path_4x replay each step as a CUDA graph)",
+                  "mpix_s": OUT_W * OUT_H / 1e3 / eager_ms, "ms": eager_ms,
+                  "direct_ms": ms_direct_eager, "path_4x_ms": ms_4x_eager},
         "stages_ms": {"project_bin": statistics.mean(t_proj), "blend_grads": blend_ms,
                       "upscale": statistics.mean(t_up)},
         "roofline": {"bound": "alu", "kernel": "k_blend<grads,3dgs>", "achieved": achieved, "peak": alu_peak,
@@ -492,6 +557,7 @@ def run_gs(args):
         "gpu_launches": launches,
     }
     print(json.dumps(line), flush=True)
+    gctx.close()
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()

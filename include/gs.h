@@ -260,6 +260,11 @@ gs_status gs_render_with_grads_noalloc(const gs_gaussians* g, const gs_camera* c
  * the frame produced (also when it exceeded the reservation). */
 gs_status gs_pair_count(gs_ctx* ctx, int64_t* P);
 
+/* Number of (64x64-pixel super-tile, Gaussian) pairs of the last gs_project:
+ * the pair buffers' size (and the super_pairs a gs_reserve for such frames
+ * needs).  Waits as gs_pair_count does. */
+gs_status gs_super_pair_count(gs_ctx* ctx, int64_t* Ps);
+
 /* Copy the last gs_project's per-Gaussian results to caller device buffers (any
  * may be NULL): mean2d [n][2], conic [n][3] (Sigma'^-1 as a, b, c), rgb [n][3],
  * opacity [n], depth [n], radius [n] (int32, 0 = culled), tiles_touched [n]. */

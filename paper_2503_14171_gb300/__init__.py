@@ -72,6 +72,7 @@ _SIGS = {
     "gs_render": ([_P, ct.POINTER(GsGaussians), ct.POINTER(GsCamera), ct.c_int32, ct.c_int32, _P], ct.c_int),
     "gs_upscale": ([_P, _P, _P, ct.c_int32, ct.c_int32, ct.c_int32, _P], ct.c_int),
     "gs_pair_count": ([_P, ct.POINTER(ct.c_int64)], ct.c_int),
+    "gs_super_pair_count": ([_P, ct.POINTER(ct.c_int64)], ct.c_int),
     "gs_read_projected": ([_P, _P, _P, _P, _P, _P, _P, _P], ct.c_int),
     "gs_read_bins": ([_P, _P, _P, _P, ct.c_int64], ct.c_int),
     "gs_read_state": ([_P, _P, _P], ct.c_int),
@@ -345,6 +346,11 @@ class Context:
     def pair_count(self) -> int:
         P = ct.c_int64()
         _chk(lib.gs_pair_count(self.h, ct.byref(P)), self.h, "gs_pair_count")
+        return int(P.value)
+
+    def super_pair_count(self) -> int:
+        P = ct.c_int64()
+        _chk(lib.gs_super_pair_count(self.h, ct.byref(P)), self.h, "gs_super_pair_count")
         return int(P.value)
 
     def read_projected(self) -> dict:

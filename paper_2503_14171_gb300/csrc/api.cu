@@ -211,11 +211,37 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
     // from the projection, then 2 scan totals and the scan tile counter
     unsigned long long* totals = as<unsigned long long>(c->scan_totals);
     unsigned long long* scan_tot = totals + 2 * kTotalSlots;
+    // counters of the frame's later kernels, cleared by the projection kernel
+    const uint32_t ds_cap = n > 1 ? depth_sort_capacity(c->device) : 0u;
+    const bool persistent = n > 1 && n <= ds_cap;
+    const size_t G = ds_cap / kDsMaxSlice;
+    const bool counted = Ts <= kMaxSupersForCounts;
+    const int sbits = bits_for((uint32_t)Ts);
+    const int spasses = radix_passes(32, 32 + sbits);
+    ZeroList zl{};
+    if (persistent) {
+        if ((st = ensure(c, c->ds_scratch, G * kRadixDigits * 4 + G * 8 + 64 + 4 * kRadixDigits * 4))) return st;
+        unsigned char* base = as<unsigned char>(c->ds_scratch);
+        zl.p[zl.count] = reinterpret_cast<uint32_t*>(base + G * kRadixDigits * 4 + G * 8);   // barrier
+        zl.words[zl.count++] = 2;
+        zl.p[zl.count] = reinterpret_cast<uint32_t*>(base + G * kRadixDigits * 4 + G * 8 + 64);   // digit totals
+        zl.words[zl.count++] = 4 * kRadixDigits;
+    }
+    if (counted) {
+        zl.p[zl.count] = as<uint32_t>(c->super_counts);
+        zl.words[zl.count++] = (uint32_t)(kCountCopies * Ts);
+    }
+    if (no_wait && Ts > 1) {   // the pair sort's look-back states and tile counters
+        zl.p[zl.count] = as<uint32_t>(c->sort_status);
+        zl.words[zl.count++] = (uint32_t)radix_status_words((uint32_t)c->res_pairs, 32, 32 + sbits);
+        zl.p[zl.count] = as<uint32_t>(c->sort_counter);
+        zl.words[zl.count++] = (uint32_t)spasses;
+    }
     GS_CUDA(c, cudaMemsetAsync(totals, 0, 2 * kTotalSlots * sizeof(unsigned long long), c->stream));
     GS_CUDA(c, launch_project(c->stream, *g, cp, W, H, tiles_x, tiles_y, c->opt.mode, rec, as<float>(c->depth),
                               as<int>(c->radius), as<ushort4>(c->rect), as<uint32_t>(c->tiles_touched),
                               as<uint32_t>(c->supers_touched), as<uint32_t>(c->dkey[0]), as<uint32_t>(c->did[0]),
-                              totals));
+                              totals, &zl));
     if (!no_wait) {
         // the pair totals travel to the host while the depth sort runs
         GS_CUDA(c, cudaMemcpyAsync(c->h_scalar, totals, 2 * kTotalSlots * sizeof(unsigned long long),
@@ -226,10 +252,7 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
     // depth order (stable radix sort of the FP32 depth bits, ids ascending) and
     // the super-tile pair offsets in that order
     int sorted = 0;
-    const uint32_t ds_cap = n > 1 ? depth_sort_capacity(c->device) : 0u;
-    if (n > 1 && n <= ds_cap) {
-        const size_t G = ds_cap / kDsMaxSlice;
-        if ((st = ensure(c, c->ds_scratch, G * kRadixDigits * 4 + G * 8 + 64 + 4 * kRadixDigits * 4))) return st;
+    if (persistent) {
         unsigned char* base = as<unsigned char>(c->ds_scratch);
         uint32_t* keys[2] = {as<uint32_t>(c->dkey[0]), as<uint32_t>(c->dkey[1])};
         uint32_t* vals[2] = {as<uint32_t>(c->did[0]), as<uint32_t>(c->did[1])};
@@ -238,7 +261,7 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
                                           reinterpret_cast<unsigned long long*>(base + G * kRadixDigits * 4),
                                           reinterpret_cast<unsigned int*>(base + G * kRadixDigits * 4 + G * 8),
                                           reinterpret_cast<uint32_t*>(base + G * kRadixDigits * 4 + G * 8 + 64),
-                                          as<int>(c->errword), &sorted));
+                                          as<int>(c->errword), &sorted, true));
     } else {
         if (n > 1) {
             uint32_t* keys[2] = {as<uint32_t>(c->dkey[0]), as<uint32_t>(c->dkey[1])};
@@ -260,11 +283,8 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
         // the pair totals stay on the device: emit into the reserved buffers and
         // let the histogram kernel check the frame against their capacity
         const uint32_t cap = (uint32_t)c->res_pairs;
-        const int sbits = bits_for((uint32_t)Ts);
-        const int spasses = radix_passes(32, 32 + sbits);
         uint64_t* pairs[2] = {as<uint64_t>(c->pairs[0]), as<uint64_t>(c->pairs[1])};
         PairCheckOut* chk = as<PairCheckOut>(c->pair_check);
-        GS_CUDA(c, cudaMemsetAsync(c->super_counts.p, 0, sizeof(uint32_t) * kCountCopies * Ts, c->stream));
         GS_CUDA(c, launch_emit_pairs(c->stream, ids, as<uint32_t>(c->offsets), as<ushort4>(c->rect), n, stiles_x,
                                      pairs[0], as<uint32_t>(c->super_counts), (uint32_t)Ts, cap));
         GS_CUDA(c, launch_supers_to_hist(c->stream, as<uint32_t>(c->super_counts), (uint32_t)Ts, spasses,
@@ -275,7 +295,7 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
         if (Ts > 1 && cap > 1)
             GS_CUDA(c, radix_sort_u64_keys(c->stream, pairs, cap, 32, 32 + sbits, as<uint32_t>(c->sort_hist),
                                            as<uint32_t>(c->sort_status), as<uint32_t>(c->sort_counter),
-                                           as<int>(c->errword), &psorted, true, &chk->count));
+                                           as<int>(c->errword), &psorted, true, &chk->count, true));
         c->sorted_pairs_buf = psorted;
         c->n = n;
         c->W = W;
@@ -305,14 +325,10 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
 
     if ((st = ensure(c, c->pairs[0], sizeof(uint64_t) * Ps)) || (st = ensure(c, c->pairs[1], sizeof(uint64_t) * Ps)))
         return st;
-    const int sbits = bits_for((uint32_t)Ts);
-    const int spasses = radix_passes(32, 32 + sbits);
     if ((st = ensure(c, c->sort_status, sizeof(uint32_t) * std::max(radix_status_words(Ps, 32, 32 + sbits),
                                                                     radix_status_words(n, 0, 32)))))
         return st;
     uint64_t* pairs[2] = {as<uint64_t>(c->pairs[0]), as<uint64_t>(c->pairs[1])};
-    const bool counted = Ts <= kMaxSupersForCounts;
-    if (counted) GS_CUDA(c, cudaMemsetAsync(c->super_counts.p, 0, sizeof(uint32_t) * kCountCopies * Ts, c->stream));
     GS_CUDA(c, launch_emit_pairs(c->stream, ids, as<uint32_t>(c->offsets), as<ushort4>(c->rect), n, stiles_x, pairs[0],
                                  counted ? as<uint32_t>(c->super_counts) : nullptr, (uint32_t)Ts));
     int psorted = 0;
@@ -656,6 +672,16 @@ gs_status gs_pair_count(gs_ctx* c, int64_t* P)
     gs_status st = known_totals(c);
     if (st != GS_OK) return st;
     *P = c->P;
+    return GS_OK;
+}
+
+gs_status gs_super_pair_count(gs_ctx* c, int64_t* Ps)
+{
+    if (!c || !Ps) return GS_ERR_INVALID_ARG;
+    if (!c->have_proj) return GS_ERR_NOT_READY;
+    gs_status st = known_totals(c);
+    if (st != GS_OK) return st;
+    *Ps = c->Ps;
     return GS_OK;
 }
 

@@ -305,16 +305,18 @@ uint32_t depth_sort_capacity(int device)
 cudaError_t launch_depth_sort_scan(cudaStream_t s, int device, const uint32_t* keys_in, uint32_t* keys[2],
                                    uint32_t* ids[2], const uint32_t* counts, uint32_t n, uint32_t* offsets,
                                    uint32_t* cnt_scratch, unsigned long long* bsum_scratch, unsigned int* bar,
-                                   uint32_t* tot_scratch, int* err, int* out_idx)
+                                   uint32_t* tot_scratch, int* err, int* out_idx, bool pre_zeroed)
 {
     const int G = ds_grid(device);
     if (G <= 0 || n == 0 || n > (uint32_t)G * (uint32_t)kDsMaxSlice) return cudaErrorInvalidValue;
     // fewer blocks for small inputs (at least 1024 elements per block)
     const uint64_t want = ((uint64_t)n + 1023) / 1024;
     const uint32_t grid = (uint32_t)(want < (uint64_t)G ? want : (uint64_t)G);
-    cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), s);
-    if (e != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(tot_scratch, 0, sizeof(uint32_t) * kDsPasses * kDsRadix, s)) != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    if (!pre_zeroed) {
+        if ((e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), s)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(tot_scratch, 0, sizeof(uint32_t) * kDsPasses * kDsRadix, s)) != cudaSuccess) return e;
+    }
     DsArgs a;
     a.keys_in = keys_in;
     a.keys[0] = keys[0] == keys_in ? keys[1] : keys[0];

@@ -155,10 +155,20 @@ int64_t& launch_counter();
 inline void note_launch() { ++launch_counter(); }
 
 // ---- launchers (each returns the cudaError_t of its launch) ----
+// Buffers of later kernels in the frame that must start at zero; the
+// projection kernel clears them (grid-stride) so the frame needs no memsets.
+struct ZeroList {
+    static constexpr int kMax = 6;
+    uint32_t* p[kMax];
+    uint32_t words[kMax];
+    int count;
+};
+
 cudaError_t launch_project(cudaStream_t s, const gs_gaussians& g, const CameraParams& cam, int W, int H,
                            int tiles_x, int tiles_y, int mode, Records rec, float* depth, int* radius,
                            ushort4* rect, uint32_t* tiles_touched, uint32_t* supers_touched, uint32_t* depth_key,
-                           uint32_t* ids, unsigned long long* totals);
+                           uint32_t* ids, unsigned long long* totals,
+                           const ZeroList* zero = nullptr);
 
 // LSD radix sort of n keys (uint32 keys with uint32 values, or uint64 keys
 // alone) on bits [bit_lo, bit_hi).  Ping-pong buffers: the result lands in
@@ -172,7 +182,8 @@ cudaError_t radix_sort_u32_pairs(cudaStream_t s, uint32_t* keys[2], uint32_t* va
 // the device; n is then the capacity the launch is sized for.
 cudaError_t radix_sort_u64_keys(cudaStream_t s, uint64_t* keys[2], uint32_t n, int bit_lo, int bit_hi,
                                 uint32_t* hist, uint32_t* status, uint32_t* counters, int* err,
-                                int* out_idx, bool hist_ready, const uint32_t* n_dev = nullptr);
+                                int* out_idx, bool hist_ready, const uint32_t* n_dev = nullptr,
+                                bool pre_zeroed = false);
 // Largest super-tile count whose per-super-tile counts the emission kernel
 // accumulates in shared memory (and turns into histograms + ranges).
 constexpr int kMaxSupersForCounts = 4096;
@@ -213,7 +224,7 @@ uint32_t depth_sort_capacity(int device);
 cudaError_t launch_depth_sort_scan(cudaStream_t s, int device, const uint32_t* keys_in, uint32_t* keys[2],
                                    uint32_t* ids[2], const uint32_t* counts, uint32_t n, uint32_t* offsets,
                                    uint32_t* cnt_scratch, unsigned long long* bsum_scratch, unsigned int* bar,
-                                   uint32_t* tot_scratch, int* err, int* out_idx);
+                                   uint32_t* tot_scratch, int* err, int* out_idx, bool pre_zeroed = false);
 
 // pairs at offsets >= cap are counted but not written (the capacity check of
 // launch_supers_to_hist then rejects the frame)

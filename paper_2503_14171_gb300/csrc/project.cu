@@ -89,9 +89,16 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
     const float* __restrict__ rgb_in, CameraParams cam, int W, int H, int tiles_x, int tiles_y,
     int mode, Records rec, float* __restrict__ depth_out, int* __restrict__ radius_out,
     ushort4* __restrict__ rect_out, uint32_t* __restrict__ tiles_out, uint32_t* __restrict__ supers_out,
-    uint32_t* __restrict__ depth_key, uint32_t* __restrict__ ids, unsigned long long* __restrict__ totals)
+    uint32_t* __restrict__ depth_key, uint32_t* __restrict__ ids, unsigned long long* __restrict__ totals,
+    ZeroList zero)
 {
     constexpr int KF = DEG >= 0 ? (DEG + 1) * (DEG + 1) * 3 : 1;   // floats per Gaussian
+    {
+        // clear the later kernels' counters (grid-stride over the whole grid)
+        const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+        for (int z = 0; z < zero.count; ++z)
+            for (uint32_t w = t; w < zero.words[z]; w += stride) zero.p[z][w] = 0u;
+    }
     constexpr int PITCH = KF | 1;
     __shared__ float s_sh[kProjThreads / 32][32][PITCH];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -548,16 +555,25 @@ __global__ void k_unpack(Records rec, const int* __restrict__ radius, const uint
 cudaError_t launch_project(cudaStream_t s, const gs_gaussians& g, const CameraParams& cam, int W, int H,
                            int tiles_x, int tiles_y, int mode, Records rec, float* depth, int* radius, ushort4* rect,
                            uint32_t* tiles_touched, uint32_t* supers_touched, uint32_t* depth_key, uint32_t* ids,
-                           unsigned long long* totals)
+                           unsigned long long* totals,
+                           const ZeroList* zero)
 {
     const int n = (int)g.n;
-    if (n == 0) return cudaSuccess;
+    if (n == 0) {   // no kernel to clear the later kernels' counters
+        for (int z = 0; zero && z < zero->count; ++z) {
+            cudaError_t e = cudaMemsetAsync(zero->p[z], 0, sizeof(uint32_t) * zero->words[z], s);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     const int blocks = (n + kProjThreads - 1) / kProjThreads;
     const int deg = g.sh ? g.sh_degree : -1;
+    ZeroList zl{};
+    if (zero) zl = *zero;
 #define GS_PROJECT(D)                                                                                              \
     k_project<D><<<blocks, kProjThreads, 0, s>>>(n, g.means, g.log_scales, g.quats, g.opacity_logits, g.sh, g.rgb, \
                                                  cam, W, H, tiles_x, tiles_y, mode, rec, depth, radius, rect,      \
-                                                 tiles_touched, supers_touched, depth_key, ids, totals)
+                                                 tiles_touched, supers_touched, depth_key, ids, totals, zl)
     switch (deg) {
     case 0: GS_PROJECT(0); break;
     case 1: GS_PROJECT(1); break;

@@ -246,15 +246,18 @@ __global__ void __launch_bounds__(kThreads) k_onesweep(const K* __restrict__ key
 template <typename K, bool HAS_VAL>
 cudaError_t radix_sort_impl(cudaStream_t s, K* keys[2], uint32_t* vals[2], uint32_t n, int bit_lo, int bit_hi,
                             uint32_t* hist, uint32_t* status, uint32_t* counters, int* err, int* out_idx,
-                            bool hist_ready, const uint32_t* n_dev = nullptr)
+                            bool hist_ready, const uint32_t* n_dev = nullptr, bool pre_zeroed = false)
 {
     *out_idx = 0;
     if (n <= 1 || bit_hi <= bit_lo) return cudaSuccess;
     const int passes = (bit_hi - bit_lo + kRadixBits - 1) / kRadixBits;
     const uint32_t tiles = (n + kTileKeys - 1) / kTileKeys;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(status, 0, sizeof(uint32_t) * (size_t)passes * tiles * kRadix, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(counters, 0, sizeof(uint32_t) * passes, s)) != cudaSuccess) return e;
+    if (!pre_zeroed) {
+        if ((e = cudaMemsetAsync(status, 0, sizeof(uint32_t) * (size_t)passes * tiles * kRadix, s)) != cudaSuccess)
+            return e;
+        if ((e = cudaMemsetAsync(counters, 0, sizeof(uint32_t) * passes, s)) != cudaSuccess) return e;
+    }
     if (!hist_ready) {
         if ((e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * passes * kRadix, s)) != cudaSuccess) return e;
         const uint32_t hb = (n + kThreads * 8 - 1) / (kThreads * 8);
@@ -419,12 +422,13 @@ cudaError_t radix_sort_u32_pairs(cudaStream_t s, uint32_t* keys[2], uint32_t* va
 
 cudaError_t radix_sort_u64_keys(cudaStream_t s, uint64_t* keys[2], uint32_t n, int bit_lo, int bit_hi,
                                 uint32_t* hist, uint32_t* status, uint32_t* counters, int* err, int* out_idx,
-                                bool hist_ready, const uint32_t* n_dev)
+                                bool hist_ready, const uint32_t* n_dev, bool pre_zeroed)
 {
     uint32_t* no_vals[2] = {nullptr, nullptr};
     if (n_dev && !hist_ready) return cudaErrorInvalidValue;   // the histogram kernels need the count on the host
+    if (pre_zeroed && !hist_ready) return cudaErrorInvalidValue;
     return radix_sort_impl<uint64_t, false>(s, keys, no_vals, n, bit_lo, bit_hi, hist, status, counters, err,
-                                            out_idx, hist_ready, n_dev);
+                                            out_idx, hist_ready, n_dev, pre_zeroed);
 }
 
 // Per-super-tile counts -> (a) the exclusive digit histograms of every radix
