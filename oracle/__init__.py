@@ -51,7 +51,7 @@ def _load():
             _lib = ct.CDLL(_LIB)
             for name in ("ora_sh_basis", "ora_project", "ora_bin", "ora_render",
                          "ora_spline_cinv", "ora_upscale", "ora_upscale_adjoint",
-                         "ora_render_adjoint", "ora_project_adjoint"):
+                         "ora_render_adjoint", "ora_project_adjoint", "ora_bicubic"):
                 getattr(_lib, name).restype = ct.c_int
         return _lib
 
@@ -315,6 +315,28 @@ def project_adjoint(scene: dict, cam: dict, W: int, H: int, g2d) -> dict:
         _p(out["means"]), _p(out["log_scales"]), _p(out["quats"]), _p(out["opacity_logits"]),
         _p(out.get("sh")), _p(out.get("rgb")))
     _check(st, "project_adjoint")
+    return out
+
+
+def bicubic(C, W2: int, H2: int, a: float = -0.75, pixels=None) -> np.ndarray:
+    """Classical bicubic (cubic convolution, parameter a) of C [3,H,W] to W2 x H2.
+
+    Returns [3, H2, W2] (pixels=None) or [M, 3] for hi-res pixels [M, 2] of (X, Y).
+    """
+    lib = _load()
+    C = _f64(C)
+    H, W = C.shape[1], C.shape[2]
+    if pixels is None:
+        npix, pix = W2 * H2, None
+    else:
+        pix = np.ascontiguousarray(pixels, dtype=np.int32).reshape(-1, 2)
+        npix = pix.shape[0]
+    out = np.zeros((npix, 3))
+    st = lib.ora_bicubic(ct.c_int(W), ct.c_int(H), ct.c_int(W2), ct.c_int(H2), _p(C), ct.c_double(a),
+                         ct.c_int64(npix), _p(pix), _p(out))
+    _check(st, "bicubic")
+    if pixels is None:
+        return np.ascontiguousarray(out.reshape(H2, W2, 3).transpose(2, 0, 1))
     return out
 
 

@@ -26,6 +26,7 @@
  *                    "Backward Pass"): dL/d(mean2D, conic, opacity, colour)
  *   ora_project_adjoint  forward-mode (dual number) derivatives of the
  *                    projection, contracted with the upstream gradient
+ *   ora_bicubic      classical bicubic (cubic convolution) comparator
  *
  * Readings of passages the paper leaves open (all inherited from the 3DGS
  * renderer the paper builds on, Sec. 6.2):
@@ -1177,6 +1178,59 @@ int ora_project_adjoint(int64_t n, const double* means, const double* log_scales
         for (int k = 0; k < ncol; ++k) {
             if (sh && g_sh) g_sh[i * ncol + k] = grad[11 + k];
             if (!sh && g_rgb) g_rgb[3 * i + k] = grad[11 + k];
+        }
+    }
+    return ORA_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Classical bicubic upscale, the comparator of Sec. 5 / Sec. 6: cubic         */
+/* convolution (Keys) with parameter a on the colour samples alone,           */
+/*   W(d) = (a + 2)|d|^3 - (a + 3)|d|^2 + 1            for |d| <= 1             */
+/*   W(d) = a|d|^3 - 5a|d|^2 + 8a|d| - 4a              for 1 < |d| < 2          */
+/* out(X, Y) = sum_{k,l = -1..2} W(t - k) W(u - l) f(clamp(i + k), clamp(j + l))  */
+/* with the half-pixel map x = (X + 0.5) W / W2 - 0.5, i = floor(x), t = x - i,  */
+/* sample indices clamped to the image.  a = -0.5 is the Hermite patch with    */
+/* central-difference slopes (the finite-difference gradients of Sec. 5);     */
+/* a = -0.75 is the kernel of PyTorch's bicubic interpolation used in the     */
+/* paper's experiments (Sec. 6).  C: [3][H][W]; out: [npix][3].                */
+/* ------------------------------------------------------------------------- */
+static double keys_w(double d, double a)
+{
+    d = fabs(d);
+    if (d <= 1.0) return ((a + 2.0) * d - (a + 3.0)) * d * d + 1.0;
+    if (d < 2.0) return ((a * d - 5.0 * a) * d + 8.0 * a) * d - 4.0 * a;
+    return 0.0;
+}
+
+int ora_bicubic(int W, int H, int W2, int H2, const double* C, double a, int64_t npix, const int32_t* pix,
+                double* out)
+{
+    if (W < 1 || H < 1 || W2 < 1 || H2 < 1 || npix < 0) return ORA_EINVAL;
+    if (pix == NULL && npix != (int64_t)W2 * H2) return ORA_EINVAL;
+    const int64_t plane = (int64_t)W * H;
+    for (int64_t p = 0; p < npix; ++p) {
+        int X, Y;
+        if (pix) { X = pix[2 * p]; Y = pix[2 * p + 1]; }
+        else { X = (int)(p % W2); Y = (int)(p / W2); }
+        if (X < 0 || X >= W2 || Y < 0 || Y >= H2) return ORA_EINVAL;
+        const double x = ((double)X + 0.5) * (double)W / (double)W2 - 0.5;
+        const double y = ((double)Y + 0.5) * (double)H / (double)H2 - 0.5;
+        const int i = (int)floor(x), j = (int)floor(y);
+        const double t = x - (double)i, u = y - (double)j;
+        for (int ch = 0; ch < 3; ++ch) {
+            double acc = 0.0;
+            for (int l = -1; l <= 2; ++l) {
+                int jj = j + l;
+                jj = jj < 0 ? 0 : (jj > H - 1 ? H - 1 : jj);
+                for (int k = -1; k <= 2; ++k) {
+                    int ii = i + k;
+                    ii = ii < 0 ? 0 : (ii > W - 1 ? W - 1 : ii);
+                    acc += keys_w(t - (double)k, a) * keys_w(u - (double)l, a) *
+                           C[(int64_t)ch * plane + (int64_t)jj * W + ii];
+                }
+            }
+            out[3 * p + ch] = acc;
         }
     }
     return ORA_OK;
