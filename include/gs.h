@@ -196,6 +196,24 @@ gs_status gs_render(gs_ctx* ctx, const gs_gaussians* g, const gs_camera* cam,
 gs_status gs_upscale(gs_ctx* ctx, const float* C, const float* grads, int32_t W, int32_t H,
                      int32_t factor, float* out);
 
+/* gs_upscale to any output size W2 x H2 (integer or fractional factors,
+ * supplement "Qualitative Results for Different Upsampling Rates"): output
+ * pixel X samples x = (X + 0.5) W / W2 - 0.5, likewise for Y.  W, H >= 2;
+ * W <= W2 <= 16 W, H <= H2 <= 16 H.  out [3][H2][W2].  Asynchronous.  For
+ * W2 = factor W it equals gs_upscale bit for bit. */
+gs_status gs_upscale_to(gs_ctx* ctx, const float* C, const float* grads, int32_t W, int32_t H, int32_t W2,
+                        int32_t H2, float* out);
+
+/* Classical bicubic upscale, the paper's comparator: cubic convolution of the
+ * colour samples C [3][H][W] alone with Keys' kernel of parameter a (a = -0.5:
+ * the Hermite patch with central-difference slopes, the finite-difference
+ * gradients of Sec. 5; a = -0.75: the bicubic interpolation of PyTorch used in
+ * the experiments, Sec. 6), same half-pixel map as gs_upscale_to, sample
+ * indices clamped to the image.  W, H >= 1; W <= W2 <= 16 W, H <= H2 <= 16 H;
+ * -2 <= a <= 0.  out [3][H2][W2].  Asynchronous. */
+gs_status gs_upscale_bicubic(gs_ctx* ctx, const float* C, int32_t W, int32_t H, int32_t W2, int32_t H2, float a,
+                             float* out);
+
 /* ---- Reverse mode (training with differentiable upscaling; supplement
  * "Backward Pass").  All gradients are of one scalar loss L; upstream arrays
  * hold dL/d(output).  Asynchronous on the context's stream. */
@@ -206,6 +224,10 @@ gs_status gs_upscale(gs_ctx* ctx, const float* C, const float* grads, int32_t W,
  * weighted by the same Hermite basis; no atomics.  W, H >= 2; 1 <= factor <= 16. */
 gs_status gs_upscale_backward(gs_ctx* ctx, const float* dL_dout, int32_t W, int32_t H, int32_t factor,
                               float* dL_dC, float* dL_dgrads);
+
+/* Adjoint of gs_upscale_to: dL_dout [3][H2][W2] (same size rules). */
+gs_status gs_upscale_backward_to(gs_ctx* ctx, const float* dL_dout, int32_t W, int32_t H, int32_t W2, int32_t H2,
+                                 float* dL_dC, float* dL_dgrads);
 
 /* Adjoint of the last derivative blend (gs_render_with_grads, or
  * gs_render_binned with out_grads, after gs_project): upstream dL_dC [3][H][W]

@@ -80,6 +80,9 @@ _SIGS = {
     "gs_blend_stats": ([_P, _P], ct.c_int),
     "gs_synchronize": ([_P], ct.c_int),
     "gs_upscale_backward": ([_P, _P, ct.c_int32, ct.c_int32, ct.c_int32, _P, _P], ct.c_int),
+    "gs_upscale_to": ([_P, _P, _P, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32, _P], ct.c_int),
+    "gs_upscale_backward_to": ([_P, _P, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32, _P, _P], ct.c_int),
+    "gs_upscale_bicubic": ([_P, _P, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_float, _P], ct.c_int),
     "gs_render_backward": ([_P, _P, _P, _P], ct.c_int),
     "gs_project_backward": ([_P, _P, ct.POINTER(GsGaussianGrads)], ct.c_int),
     "gs_backward": ([_P, _P, ct.c_int32, ct.POINTER(GsGaussianGrads)], ct.c_int),
@@ -342,6 +345,33 @@ class Context:
         o = out if out is not None else self._empty(3, H * factor, W * factor)
         gs_upscale(self.h, C.data_ptr(), grads.data_ptr(), W, H, factor, o.data_ptr())
         return o
+
+    def upscale_to(self, C, grads, W2: int, H2: int, out=None):
+        """Spline upscale to any size W2 x H2 (fractional factors)."""
+        H, W = int(C.shape[-2]), int(C.shape[-1])
+        assert C.is_contiguous() and grads.is_contiguous()
+        o = out if out is not None else self._empty(3, H2, W2)
+        _chk(lib.gs_upscale_to(self.h, C.data_ptr(), grads.data_ptr(), W, H, W2, H2, o.data_ptr()), self.h,
+             "gs_upscale_to")
+        return o
+
+    def upscale_bicubic(self, C, W2: int, H2: int, a: float = -0.75, out=None):
+        """Classical bicubic comparator (cubic convolution, parameter a) of the colour image."""
+        H, W = int(C.shape[-2]), int(C.shape[-1])
+        assert C.is_contiguous()
+        o = out if out is not None else self._empty(3, H2, W2)
+        _chk(lib.gs_upscale_bicubic(self.h, C.data_ptr(), W, H, W2, H2, float(a), o.data_ptr()), self.h,
+             "gs_upscale_bicubic")
+        return o
+
+    def upscale_backward_to(self, dout, W: int, H: int, out=None):
+        """Adjoint of upscale_to: dL/d(out) [3, H2, W2] -> (dL/dC, dL/dgrads)."""
+        assert dout.is_contiguous()
+        H2, W2 = int(dout.shape[-2]), int(dout.shape[-1])
+        dC, dG = out if out is not None else (self._empty(3, H, W), self._empty(3, 3, H, W))
+        _chk(lib.gs_upscale_backward_to(self.h, dout.data_ptr(), W, H, W2, H2, dC.data_ptr(), dG.data_ptr()),
+             self.h, "gs_upscale_backward_to")
+        return dC, dG
 
     def pair_count(self) -> int:
         P = ct.c_int64()

@@ -557,6 +557,56 @@ gs_status gs_upscale(gs_ctx* c, const float* C, const float* grads, int32_t W, i
     return GS_OK;
 }
 
+namespace {
+
+gs_status check_sizes(gs_ctx* c, int32_t W, int32_t H, int32_t W2, int32_t H2, int32_t min_side)
+{
+    if (W < min_side || H < min_side) return fail(c, GS_ERR_INVALID_ARG, "input must be at least %d x %d", min_side, min_side);
+    if (W2 < W || H2 < H || (int64_t)W2 > 16ll * W || (int64_t)H2 > 16ll * H)
+        return fail(c, GS_ERR_INVALID_ARG, "output %d x %d must be 1 to 16 times the input %d x %d", W2, H2, W, H);
+    if (W2 > (1 << 24) || H2 > (1 << 24)) return fail(c, GS_ERR_INVALID_ARG, "output too large");
+    return GS_OK;
+}
+
+}  // namespace
+
+gs_status gs_upscale_to(gs_ctx* c, const float* C, const float* grads, int32_t W, int32_t H, int32_t W2, int32_t H2,
+                        float* out)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    LaunchTally tally(c);
+    if (!C || !grads || !out) return fail(c, GS_ERR_INVALID_ARG, "NULL image pointer");
+    gs_status st = check_sizes(c, W, H, W2, H2, 2);
+    if (st != GS_OK) return st;
+    GS_CUDA(c, launch_upscale_to(c->stream, C, grads, W, H, W2, H2, out));
+    return GS_OK;
+}
+
+gs_status gs_upscale_backward_to(gs_ctx* c, const float* dL_dout, int32_t W, int32_t H, int32_t W2, int32_t H2,
+                                 float* dL_dC, float* dL_dgrads)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    LaunchTally tally(c);
+    if (!dL_dout || !dL_dC || !dL_dgrads) return fail(c, GS_ERR_INVALID_ARG, "NULL image pointer");
+    gs_status st = check_sizes(c, W, H, W2, H2, 2);
+    if (st != GS_OK) return st;
+    GS_CUDA(c, launch_upscale_backward_to(c->stream, dL_dout, W, H, W2, H2, dL_dC, dL_dgrads));
+    return GS_OK;
+}
+
+gs_status gs_upscale_bicubic(gs_ctx* c, const float* C, int32_t W, int32_t H, int32_t W2, int32_t H2, float a,
+                             float* out)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    LaunchTally tally(c);
+    if (!C || !out) return fail(c, GS_ERR_INVALID_ARG, "NULL image pointer");
+    if (!(a >= -2.f && a <= 0.f)) return fail(c, GS_ERR_INVALID_ARG, "a must be in [-2, 0]");
+    gs_status st = check_sizes(c, W, H, W2, H2, 1);
+    if (st != GS_OK) return st;
+    GS_CUDA(c, launch_bicubic(c->stream, C, W, H, W2, H2, a, out));
+    return GS_OK;
+}
+
 gs_status gs_upscale_backward(gs_ctx* c, const float* dL_dout, int32_t W, int32_t H, int32_t factor,
                               float* dL_dC, float* dL_dgrads)
 {

@@ -249,6 +249,13 @@ cudaError_t launch_project_backward(cudaStream_t s, const gs_gaussians& g, const
 // adjoint of the upscale: dout [3][sH][sW] -> dC [3][H][W], dG [9][H][W] (overwritten)
 cudaError_t launch_upscale_backward(cudaStream_t s, const float* dout, int W, int H, int factor, float* dC,
                                     float* dG);
+// any output size W2 x H2 with W <= W2 <= 16 W, H <= H2 <= 16 H (fractional factors)
+cudaError_t launch_upscale_to(cudaStream_t s, const float* C, const float* grads, int W, int H, int W2, int H2,
+                              float* out);
+cudaError_t launch_upscale_backward_to(cudaStream_t s, const float* dout, int W, int H, int W2, int H2, float* dC,
+                                       float* dG);
+// classical bicubic comparator (cubic convolution with Keys' parameter a) of C [3][H][W]
+cudaError_t launch_bicubic(cudaStream_t s, const float* C, int W, int H, int W2, int H2, float a, float* out);
 cudaError_t launch_blend_stats(cudaStream_t s, int mode, const BlendArgs& a, unsigned long long* stats);
 
 cudaError_t launch_upscale(cudaStream_t s, const float* C, const float* grads, int W, int H, int factor,

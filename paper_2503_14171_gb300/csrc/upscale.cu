@@ -1,5 +1,7 @@
 // Gradient-aware bicubic Hermite upscale (Sec. 5 "Spline Interpolation";
-// supplement "Spline Image Interpolation").
+// supplement "Spline Image Interpolation"), at any output size (integer or
+// fractional factors, supplement "Qualitative Results for Different Upsampling
+// Rates"), its adjoint, and the classical bicubic comparator.
 //
 // The patch of low-res cell (i, j) solves F = C A C^T, so
 // p(t, u) = [1 t t^2 t^3] C^-1 F C^-T [1 u u^2 u^3]^T, and the rows of
@@ -10,10 +12,11 @@
 //                        + H_a(t) G_b(u) f_y(a,b) + G_a(t) G_b(u) f_xy(a,b)
 // with H = (h00, h01), G = (h10, h11).
 //
-// Output pixel X samples the low-res point x = (X + 0.5)/s - 0.5; its cell is
-// i = clamp(floor(x), 0, W - 2) and t = x - i (outside [0, 1] only in the border
-// half-cells, where the edge patch is extrapolated).  Both come from integer
-// arithmetic: x = (2X + 1 - s) / (2s).
+// Output pixel X of a W2-wide output samples the low-res point
+// x = (X + 0.5) W / W2 - 0.5 = ((2X + 1) W - W2) / (2 W2); its cell is
+// i = clamp(floor(x), 0, W - 2) (an exact integer division) and t = x - i (one
+// rounding; outside [0, 1] only in the border half-cells, where the edge patch
+// is extrapolated).
 //
 // Launch: one 256-thread block per 64 x 16 tile of output pixels, 2 x 2 outputs
 // per thread.  The block computes the cell index and the four basis weights of
@@ -31,18 +34,23 @@ constexpr int kThreadsX = 32, kThreadsY = 8;
 constexpr int kOutW = 2 * kThreadsX;    // 64
 constexpr int kOutH = 2 * kThreadsY;    // 16
 constexpr int kMaxFactor = 16;
-// footprint of a 64 x 16 output tile: at most 64 + 1 x 16 + 1 cells (s = 1)
+// footprint of a 64 x 16 output tile for W2 >= W: at most 63 + 2 x 15 + 2 cells
 constexpr int kFootW = kOutW + 2;
 constexpr int kFootH = kOutH + 2;
 
-__device__ __forceinline__ void cell_of(int X, int s, int W, int& i, float& t)
+// floor(num / den) for den > 0
+__device__ __forceinline__ long long floor_div(long long num, long long den)
 {
-    // x = (X + 0.5)/s - 0.5 = num/den with num = 2X + 1 - s, den = 2s: the cell is
-    // an exact integer floor division and t = (num - den i)/den has one rounding
-    const int num = 2 * X + 1 - s, den = 2 * s;
-    int q = num >= 0 ? num / den : -((den - 1 - num) / den);
+    return num >= 0 ? num / den : -((den - 1 - num) / den);
+}
+
+// cell and local coordinate of output pixel X (clamped to [0, W - 2])
+__device__ __forceinline__ void cell_of(int X, int W, int W2, int& i, float& t)
+{
+    const long long num = (2ll * X + 1) * W - W2, den = 2ll * W2;
+    long long q = floor_div(num, den);
     q = q < 0 ? 0 : (q > W - 2 ? W - 2 : q);
-    i = q;
+    i = (int)q;
     t = (float)(num - den * q) / (float)den;
 }
 
@@ -53,44 +61,44 @@ __device__ __forceinline__ float4 hermite(float t)
     return make_float4((1.f + 2.f * t) * omt * omt, t2 * (3.f - 2.f * t), t * omt * omt, t2 * (t - 1.f));
 }
 
-// footprint pitch (in low-res pixels) for factor s: ceil(64 / s) + 2 columns
-__host__ __device__ inline int foot_w(int s) { return min(kFootW, (kOutW + s - 1) / s + 2); }
-__host__ __device__ inline int foot_h(int s) { return min(kFootH, (kOutH + s - 1) / s + 2); }
+// footprint bound of a 64 x 16 output tile: ceil(63 W / W2) + 2 columns,
+// ceil(15 H / H2) + 2 rows
+int foot_w(int W, int W2) { return std::min(kFootW, (int)((63ll * W + W2 - 1) / W2) + 2); }
+int foot_h(int H, int H2) { return std::min(kFootH, (int)((15ll * H + H2 - 1) / H2) + 2); }
 
 __global__ void __launch_bounds__(kThreadsX * kThreadsY) k_upscale(const float* __restrict__ Cimg,
                                                                    const float* __restrict__ G, int W, int H,
-                                                                   int s, float* __restrict__ out)
+                                                                   int W2, int H2, int pitch,
+                                                                   float* __restrict__ out)
 {
     // per low-res pixel of the footprint, its 12 values packed in 3 float4: [fy][fx][3]
     extern __shared__ float4 sm[];
     __shared__ float4 s_wx[kOutW];             // basis weights (h00, h01, h10, h11) per output column
     __shared__ float4 s_wy[kOutH];
     __shared__ int s_cx[kOutW], s_cy[kOutH];   // cell index relative to the footprint origin
-    const int W2 = W * s, H2 = H * s;
     const int X0 = blockIdx.x * kOutW, Y0 = blockIdx.y * kOutH;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * kThreadsX + tx;
 
     int i0, j0, itmp, jtmp;
     float ttmp;
-    cell_of(X0, s, W, i0, ttmp);
-    cell_of(Y0, s, H, j0, ttmp);
-    cell_of(min(X0 + kOutW - 1, W2 - 1), s, W, itmp, ttmp);
-    cell_of(min(Y0 + kOutH - 1, H2 - 1), s, H, jtmp, ttmp);
-    const int fw = itmp + 2 - i0, fh = jtmp + 2 - j0;   // <= foot_w(s) x foot_h(s)
-    const int pitch = foot_w(s);
+    cell_of(X0, W, W2, i0, ttmp);
+    cell_of(Y0, H, H2, j0, ttmp);
+    cell_of(min(X0 + kOutW - 1, W2 - 1), W, W2, itmp, ttmp);
+    cell_of(min(Y0 + kOutH - 1, H2 - 1), H, H2, jtmp, ttmp);
+    const int fw = itmp + 2 - i0, fh = jtmp + 2 - j0;   // <= pitch x foot_h(H, H2)
 
     if (tid < kOutW) {
         int ci;
         float t;
-        cell_of(min(X0 + tid, W2 - 1), s, W, ci, t);
+        cell_of(min(X0 + tid, W2 - 1), W, W2, ci, t);
         s_cx[tid] = ci - i0;
         s_wx[tid] = hermite(t);
     } else if (tid < kOutW + kOutH) {
         const int r = tid - kOutW;
         int cj;
         float u;
-        cell_of(min(Y0 + r, H2 - 1), s, H, cj, u);
+        cell_of(min(Y0 + r, H2 - 1), H, H2, cj, u);
         s_cy[r] = cj - j0;
         s_wy[r] = hermite(u);
     }
@@ -166,30 +174,30 @@ __global__ void __launch_bounds__(kThreadsX * kThreadsY) k_upscale(const float* 
 // has (i, .) as its left corner when its cell is i (weights h00, h10 of t) and
 // as its right corner when its cell is i - 1 (weights h01, h11).  Cells are
 // monotone in X, so the pixels of cell c are [first(c), first(c + 1)) with
-// first(c) the smallest X whose clamped floor((2X + 1 - s) / (2s)) is >= c:
-// 0 for c <= 0, W s for c > W - 2, else ceil((2 s c + s - 1) / 2).  One thread
-// per low-res pixel gathers exactly its (2s)^2 output pixels with the
-// separable weights: no atomics, each low-res value written once.
+// first(c) the smallest X whose clamped cell is >= c: 0 for c <= 0, W2 for
+// c > W - 2, else ceil((2 W2 c + W2 - W) / (2 W)).  One thread per low-res
+// pixel gathers exactly its output footprint with the separable weights: no
+// atomics, each low-res value written once.
 constexpr int kBwdX = 32, kBwdY = 8;
 
-__device__ __forceinline__ int first_of_cell(int c, int s, int W)
+__device__ __forceinline__ int first_of_cell(int c, int W, int W2)
 {
     if (c <= 0) return 0;
-    if (c > W - 2) return W * s;
-    return (2 * s * c + s) / 2;   // ceil((2 s c + s - 1) / 2)
+    if (c > W - 2) return W2;
+    const long long num = 2ll * W2 * c + W2 - W, den = 2ll * W;   // num > 0 for W2 >= W
+    return (int)((num + den - 1) / den);
 }
 
-__global__ void __launch_bounds__(kBwdX * kBwdY) k_upscale_bwd(const float* __restrict__ dout, int W, int H, int s,
-                                                               float* __restrict__ dC, float* __restrict__ dG)
+__global__ void __launch_bounds__(kBwdX * kBwdY) k_upscale_bwd(const float* __restrict__ dout, int W, int H, int W2,
+                                                               int H2, float* __restrict__ dC, float* __restrict__ dG)
 {
     const int i = blockIdx.x * kBwdX + threadIdx.x;
     const int j = blockIdx.y * kBwdY + threadIdx.y;
     if (i >= W || j >= H) return;
-    const int W2 = W * s, H2 = H * s;
     const size_t oplane = (size_t)W2 * H2;
-    const float inv2s = 1.f / (float)(2 * s);
-    const int xa = first_of_cell(i - 1, s, W), xm = first_of_cell(i, s, W), xb = first_of_cell(i + 1, s, W);
-    const int ya = first_of_cell(j - 1, s, H), ym = first_of_cell(j, s, H), yb = first_of_cell(j + 1, s, H);
+    const float inv_x = 1.f / (float)(2 * W2), inv_y = 1.f / (float)(2 * H2);
+    const int xa = first_of_cell(i - 1, W, W2), xm = first_of_cell(i, W, W2), xb = first_of_cell(i + 1, W, W2);
+    const int ya = first_of_cell(j - 1, H, H2), ym = first_of_cell(j, H, H2), yb = first_of_cell(j + 1, H, H2);
     // acc[ch][q], q: value (H H), d/dx (G H), d/dy (H G), d2/dxdy (G G)
     float acc[3][4];
 #pragma unroll
@@ -199,13 +207,13 @@ __global__ void __launch_bounds__(kBwdX * kBwdY) k_upscale_bwd(const float* __re
     for (int Y = ya; Y < yb; ++Y) {
         const bool right_y = Y < ym;            // cell j - 1: (., j) is its lower corner
         const int cj = right_y ? j - 1 : j;
-        const float4 hy = hermite((float)(2 * Y + 1 - s - 2 * s * cj) * inv2s);
+        const float4 hy = hermite((float)((2ll * Y + 1) * H - H2 - 2ll * H2 * cj) * inv_y);
         const float wyH = right_y ? hy.y : hy.x, wyG = right_y ? hy.w : hy.z;
         const float* row = dout + (size_t)Y * W2;
         for (int X = xa; X < xb; ++X) {
             const bool right_x = X < xm;
             const int ci = right_x ? i - 1 : i;
-            const float4 hx = hermite((float)(2 * X + 1 - s - 2 * s * ci) * inv2s);
+            const float4 hx = hermite((float)((2ll * X + 1) * W - W2 - 2ll * W2 * ci) * inv_x);
             const float wxH = right_x ? hx.y : hx.x, wxG = right_x ? hx.w : hx.z;
             const float wHH = wxH * wyH, wGH = wxG * wyH, wHG = wxH * wyG, wGG = wxG * wyG;
 #pragma unroll
@@ -228,21 +236,132 @@ __global__ void __launch_bounds__(kBwdX * kBwdY) k_upscale_bwd(const float* __re
     }
 }
 
-}  // namespace
-
-cudaError_t launch_upscale_backward(cudaStream_t s, const float* dout, int W, int H, int factor, float* dC,
-                                    float* dG)
+// Classical bicubic comparator (Sec. 5: slopes from finite differences; Sec.
+// 6: PyTorch's bicubic): cubic convolution of the colour samples with Keys'
+// kernel of parameter a, sample indices clamped to the image,
+//   W(d) = (a + 2)|d|^3 - (a + 3)|d|^2 + 1 (|d| <= 1), a|d|^3 - 5a|d|^2 + 8a|d| - 4a (1 < |d| < 2).
+// Same tiling as k_upscale: per 64 x 16 output tile, per-column and per-row
+// tap weights in shared tables and the clamped colour footprint staged as
+// float4; 16 vector shared loads per output.  HBM-bound: 12 B per low-res
+// pixel in, 12 B per output pixel out.
+__device__ __forceinline__ float keys(float d, float a)   // d >= 0
 {
-    if (factor < 1 || factor > kMaxFactor || W < 2 || H < 2) return cudaErrorInvalidValue;
-    dim3 grid((W + kBwdX - 1) / kBwdX, (H + kBwdY - 1) / kBwdY);
-    k_upscale_bwd<<<grid, dim3(kBwdX, kBwdY), 0, s>>>(dout, W, H, factor, dC, dG); note_launch();
-    return cudaGetLastError();
+    if (d <= 1.f) return ((a + 2.f) * d - (a + 3.f)) * d * d + 1.f;
+    if (d < 2.f) return ((a * d - 5.f * a) * d + 8.f * a) * d - 4.f * a;
+    return 0.f;
 }
 
-cudaError_t launch_upscale(cudaStream_t s, const float* C, const float* grads, int W, int H, int factor, float* out)
+// first tap index floor(x) - 1 and the four tap weights of output pixel X
+__device__ __forceinline__ void taps_of(int X, int W, int W2, float a, int& first, float4& w)
 {
-    if (factor < 1 || factor > kMaxFactor) return cudaErrorInvalidValue;
-    const int W2 = W * factor, H2 = H * factor;
+    const long long num = (2ll * X + 1) * W - W2, den = 2ll * W2;
+    const long long fl = floor_div(num, den);
+    const float t = (float)(num - den * fl) / (float)den;
+    first = (int)fl - 1;
+    w = make_float4(keys(1.f + t, a), keys(t, a), keys(1.f - t, a), keys(2.f - t, a));
+}
+
+constexpr int kBicFootW = kOutW + 3;   // 63 + 4 taps for W2 >= W
+constexpr int kBicFootH = kOutH + 3;
+
+int bic_foot_w(int W, int W2) { return std::min(kBicFootW, (int)((63ll * W + W2 - 1) / W2) + 4); }
+int bic_foot_h(int H, int H2) { return std::min(kBicFootH, (int)((15ll * H + H2 - 1) / H2) + 4); }
+
+__global__ void __launch_bounds__(kThreadsX * kThreadsY) k_bicubic(const float* __restrict__ Cimg, int W, int H,
+                                                                   int W2, int H2, float a, int pitch,
+                                                                   float* __restrict__ out)
+{
+    extern __shared__ float4 sb[];             // [fh][pitch] clamped colour (r, g, b, 0)
+    __shared__ float4 s_wx[kOutW];
+    __shared__ float4 s_wy[kOutH];
+    __shared__ int s_cx[kOutW], s_cy[kOutH];   // first tap relative to the footprint origin
+    const int X0 = blockIdx.x * kOutW, Y0 = blockIdx.y * kOutH;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * kThreadsX + tx;
+    int i0, j0, i1, j1;
+    float4 wtmp;
+    taps_of(X0, W, W2, a, i0, wtmp);
+    taps_of(Y0, H, H2, a, j0, wtmp);
+    taps_of(min(X0 + kOutW - 1, W2 - 1), W, W2, a, i1, wtmp);
+    taps_of(min(Y0 + kOutH - 1, H2 - 1), H, H2, a, j1, wtmp);
+    const int fw = i1 + 4 - i0, fh = j1 + 4 - j0;   // <= pitch x bic_foot_h(H, H2)
+    if (tid < kOutW) {
+        int f;
+        float4 w;
+        taps_of(min(X0 + tid, W2 - 1), W, W2, a, f, w);
+        s_cx[tid] = f - i0;
+        s_wx[tid] = w;
+    } else if (tid < kOutW + kOutH) {
+        const int r = tid - kOutW;
+        int f;
+        float4 w;
+        taps_of(min(Y0 + r, H2 - 1), H, H2, a, f, w);
+        s_cy[r] = f - j0;
+        s_wy[r] = w;
+    }
+    const size_t plane = (size_t)W * H;
+    for (int fy = ty; fy < fh; fy += kThreadsY) {
+        const int jj = min(max(j0 + fy, 0), H - 1);
+        for (int fx = tx; fx < fw; fx += kThreadsX) {
+            const int ii = min(max(i0 + fx, 0), W - 1);
+            const float* c = Cimg + (size_t)jj * W + ii;
+            sb[fy * pitch + fx] = make_float4(c[0], c[plane], c[2 * plane], 0.f);
+        }
+    }
+    __syncthreads();
+    const size_t oplane = (size_t)W2 * H2;
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        const int oy = ty + b * kThreadsY;
+        const int Y = Y0 + oy;
+        if (Y >= H2) continue;
+        const float4 wy = s_wy[oy];
+        const int lj = s_cy[oy];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int ox = tx + q * kThreadsX;
+            const int X = X0 + ox;
+            if (X >= W2) continue;
+            const float4 wx = s_wx[ox];
+            const int li = s_cx[ox];
+            float r = 0.f, g = 0.f, bl = 0.f;
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const float wl = l == 0 ? wy.x : (l == 1 ? wy.y : (l == 2 ? wy.z : wy.w));
+                const float4* row = sb + (lj + l) * pitch + li;
+                float hr = 0.f, hg = 0.f, hb = 0.f;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float wk = k == 0 ? wx.x : (k == 1 ? wx.y : (k == 2 ? wx.z : wx.w));
+                    const float4 v = row[k];
+                    hr = fmaf(wk, v.x, hr);
+                    hg = fmaf(wk, v.y, hg);
+                    hb = fmaf(wk, v.z, hb);
+                }
+                r = fmaf(wl, hr, r);
+                g = fmaf(wl, hg, g);
+                bl = fmaf(wl, hb, bl);
+            }
+            const size_t o = (size_t)Y * W2 + X;
+            out[o] = r;
+            out[oplane + o] = g;
+            out[2 * oplane + o] = bl;
+        }
+    }
+}
+
+bool sizes_ok(int W, int H, int W2, int H2, int min_side)
+{
+    return W >= min_side && H >= min_side && W2 >= W && H2 >= H && (long long)W2 <= (long long)kMaxFactor * W &&
+           (long long)H2 <= (long long)kMaxFactor * H;
+}
+
+}  // namespace
+
+cudaError_t launch_upscale_to(cudaStream_t s, const float* C, const float* grads, int W, int H, int W2, int H2,
+                              float* out)
+{
+    if (!sizes_ok(W, H, W2, H2, 2)) return cudaErrorInvalidValue;
     dim3 grid((W2 + kOutW - 1) / kOutW, (H2 + kOutH - 1) / kOutH);
     static bool attr = false;
     if (!attr) {
@@ -251,8 +370,41 @@ cudaError_t launch_upscale(cudaStream_t s, const float* C, const float* grads, i
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const size_t smem = 3 * sizeof(float4) * foot_w(factor) * foot_h(factor);
-    k_upscale<<<grid, dim3(kThreadsX, kThreadsY), smem, s>>>(C, grads, W, H, factor, out); note_launch();
+    const int pitch = foot_w(W, W2);
+    const size_t smem = 3 * sizeof(float4) * pitch * foot_h(H, H2);
+    k_upscale<<<grid, dim3(kThreadsX, kThreadsY), smem, s>>>(C, grads, W, H, W2, H2, pitch, out); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_upscale(cudaStream_t s, const float* C, const float* grads, int W, int H, int factor, float* out)
+{
+    if (factor < 1 || factor > kMaxFactor) return cudaErrorInvalidValue;
+    return launch_upscale_to(s, C, grads, W, H, W * factor, H * factor, out);
+}
+
+cudaError_t launch_upscale_backward_to(cudaStream_t s, const float* dout, int W, int H, int W2, int H2, float* dC,
+                                       float* dG)
+{
+    if (!sizes_ok(W, H, W2, H2, 2)) return cudaErrorInvalidValue;
+    dim3 grid((W + kBwdX - 1) / kBwdX, (H + kBwdY - 1) / kBwdY);
+    k_upscale_bwd<<<grid, dim3(kBwdX, kBwdY), 0, s>>>(dout, W, H, W2, H2, dC, dG); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_upscale_backward(cudaStream_t s, const float* dout, int W, int H, int factor, float* dC,
+                                    float* dG)
+{
+    if (factor < 1 || factor > kMaxFactor) return cudaErrorInvalidValue;
+    return launch_upscale_backward_to(s, dout, W, H, W * factor, H * factor, dC, dG);
+}
+
+cudaError_t launch_bicubic(cudaStream_t s, const float* C, int W, int H, int W2, int H2, float a, float* out)
+{
+    if (!sizes_ok(W, H, W2, H2, 1)) return cudaErrorInvalidValue;
+    dim3 grid((W2 + kOutW - 1) / kOutW, (H2 + kOutH - 1) / kOutH);
+    const int pitch = bic_foot_w(W, W2);
+    const size_t smem = sizeof(float4) * pitch * bic_foot_h(H, H2);
+    k_bicubic<<<grid, dim3(kThreadsX, kThreadsY), smem, s>>>(C, W, H, W2, H2, a, pitch, out); note_launch();
     return cudaGetLastError();
 }
 
