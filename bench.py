@@ -441,6 +441,43 @@ def run_gs(args):
         psnr2 = psnr(out.cpu().numpy(), d_np)
         psnr4 = psnr(out4.cpu().numpy(), d_np)
 
+        # the paper's comparisons: classical bicubic (PyTorch's kernel, a = -0.75)
+        # of the plain 960x540 render, and the spline at a fractional factor
+        # (1280x720 -> 1.5x), each step as a CUDA graph, PSNR vs the direct render
+        Cb = torch.empty(3, LOW_H, LOW_W, device="cuda")
+        outb = torch.empty(3, OUT_H, OUT_W, device="cuda")
+
+        def body_bic(gc):
+            gc.render(dev, cam, LOW_W, LOW_H, out_C=Cb)
+            gc.upscale_bicubic(Cb, OUT_W, OUT_H, a=-0.75, out=outb)
+
+        gctx_b, graph_b, _ = graphed(LOW_W, LOW_H, Ps_low + Ps_low // 10 + 4096, body_bic)
+        with torch.cuda.stream(stream):
+            ms_bic = time_loop(graph_b.replay, kd)
+            graph_b.replay()
+        torch.cuda.synchronize()
+        psnr_bic = psnr(outb.cpu().numpy(), d_np)
+        gctx_b.close()
+        W15, H15 = OUT_W * 2 // 3, OUT_H * 2 // 3
+        cam15 = scenes.pinhole_camera(W15, H15)
+        C15 = torch.empty(3, H15, W15, device="cuda")
+        G15 = torch.empty(3, 3, H15, W15, device="cuda")
+        out15 = torch.empty(3, OUT_H, OUT_W, device="cuda")
+        ctx.render_with_grads(dev, cam15, W15, H15, out_C=C15, out_grads=G15)
+        Ps_15 = ctx.super_pair_count()
+
+        def body15(gc):
+            gc.render_with_grads(dev, cam15, W15, H15, out_C=C15, out_grads=G15)
+            gc.upscale_to(C15, G15, OUT_W, OUT_H, out=out15)
+
+        gctx_15, graph_15, _ = graphed(W15, H15, Ps_15 + Ps_15 // 10 + 4096, body15)
+        with torch.cuda.stream(stream):
+            ms_15 = time_loop(graph_15.replay, kd)
+            graph_15.replay()
+        torch.cuda.synchronize()
+        psnr_15 = psnr(out15.cpu().numpy(), d_np)
+        gctx_15.close()
+
         # end to end through the public API: pinned host scene in, image out
         host = gs.HostScene(scene)
         out_host = torch.empty(3, OUT_H, OUT_W, pin_memory=True)
@@ -531,6 +568,11 @@ def run_gs(args):
         "speedup_vs_direct": (OUT_W * OUT_H / 1e3 / ms_step) / (OUT_W * OUT_H / 1e3 / ms_direct),
         "psnr_db": {"2x_960x540": psnr2, "4x_480x270": psnr4, "vs": "direct 1920x1080 render, clipped to [0,1]"},
         "path_4x": {"mpix_s": OUT_W * OUT_H / 1e3 / ms_4x, "ms": ms_4x},
+        "comparisons": {
+            "bicubic_2x": {"what": "plain 960x540 render + cubic convolution (a = -0.75) to 1920x1080",
+                           "mpix_s": OUT_W * OUT_H / 1e3 / ms_bic, "ms": ms_bic, "psnr_db": psnr_bic},
+            "spline_1.5x": {"what": "1280x720 render with derivatives + spline to 1920x1080",
+                            "mpix_s": OUT_W * OUT_H / 1e3 / ms_15, "ms": ms_15, "psnr_db": psnr_15}},
         "eager": {"note": "the same steps through the API one call at a time, gs_project waiting once for the "
                           "pair count (value, direct_render and path_4x replay each step as a CUDA graph)",
                   "mpix_s": OUT_W * OUT_H / 1e3 / eager_ms, "ms": eager_ms,
@@ -578,7 +620,7 @@ def _traffic_from_profiles():
                 k, v = line.split(":", 1)
                 d[k.strip()] = v.strip()
     h = hashlib.sha256()
-    for name in ("blend.cu", "gs_internal.cuh"):
+    for name in ("blend.cu", "blend_common.cuh", "gs_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2503_14171_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     if h.hexdigest()[:16] != d.get("sources_sha256_16"):

@@ -96,8 +96,10 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
     {
         // clear the later kernels' counters (grid-stride over the whole grid)
         const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-        for (int z = 0; z < zero.count; ++z)
-            for (uint32_t w = t; w < zero.words[z]; w += stride) zero.p[z][w] = 0u;
+#pragma unroll
+        for (int z = 0; z < ZeroList::kMax; ++z)   // unrolled: constant indices keep the list in registers
+            if (z < zero.count)
+                for (uint32_t w = t; w < zero.words[z]; w += stride) zero.p[z][w] = 0u;
     }
     constexpr int PITCH = KF | 1;
     __shared__ float s_sh[kProjThreads / 32][32][PITCH];
