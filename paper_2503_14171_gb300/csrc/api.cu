@@ -213,7 +213,7 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
     unsigned long long* scan_tot = totals + 2 * kTotalSlots;
     // counters of the frame's later kernels, cleared by the projection kernel
     const uint32_t ds_cap = n > 1 ? depth_sort_capacity(c->device) : 0u;
-    const bool persistent = n > 1 && n <= ds_cap;
+    const bool persistent = n > 1 && n <= ds_cap && n <= kDsMaxN;
     const size_t G = ds_cap / kDsMaxSlice;
     const bool counted = Ts <= kMaxSupersForCounts;
     const int sbits = bits_for((uint32_t)Ts);

@@ -30,6 +30,15 @@ constexpr int kDsWarps = kDsThreads / 32;
 constexpr int kDsRadix = 256;
 constexpr int kDsPasses = 4;
 constexpr long kGridSpinLimit = 1L << 22;
+constexpr int kDsPer = kDsMaxSlice / kDsThreads;   // slice elements per thread
+// The pair count of each Gaussian rides along with its id through the passes:
+// id in the low kIdBits bits, min(count, kCntEsc) above; kCntEsc means "look
+// the count up" (rare: a Gaussian over 2047 super-tiles).
+constexpr int kIdBits = 21;
+constexpr uint32_t kIdMask = (1u << kIdBits) - 1u;
+static_assert(kDsMaxN == kIdMask, "the persistent sort's size limit is the id field");
+constexpr uint32_t kCntEsc = (1u << (32 - kIdBits)) - 1u;
+static_assert(kDsPer * kDsThreads == kDsMaxSlice, "the slice is a whole number of elements per thread");
 
 struct DsArgs {
     const uint32_t* keys_in;     // [n] depth keys in id order
@@ -98,17 +107,39 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
 
     for (int pass = 0; pass < kDsPasses; ++pass) {
         const int shift = pass * 8;
-        const uint32_t* src_key = pass == 0 ? a.keys_in : a.keys[(pass - 1) & 1];
-        const uint32_t* src_id = pass == 0 ? nullptr : a.ids[(pass - 1) & 1];
-        uint32_t* dst_key = a.keys[pass & 1];
-        uint32_t* dst_id = a.ids[pass & 1];
+        // ping-pong buffers chosen by condition (a run-time index into the
+        // parameter struct would copy it to local memory)
+        const bool odd = pass & 1;
+        const uint32_t* src_key = pass == 0 ? a.keys_in : (odd ? a.keys[0] : a.keys[1]);
+        const uint32_t* src_id = pass == 0 ? nullptr : (odd ? a.ids[0] : a.ids[1]);
+        uint32_t* dst_key = odd ? a.keys[1] : a.keys[0];
+        uint32_t* dst_id = odd ? a.ids[1] : a.ids[0];
         for (int i = tid; i < kDsWarps * kDsRadix; i += kDsThreads) s_wcnt[i] = 0;
-        // stage the slice in shared memory: independent coalesced loads (L2, the
-        // previous pass's scatter by other blocks)
-#pragma unroll 4
-        for (uint32_t j = tid; j < m; j += kDsThreads) {
-            s_key[j] = __ldcg(src_key + lo + j);
-            s_id[j] = pass == 0 ? lo + j : __ldcg(src_id + lo + j);
+        // stage the slice in shared memory: coalesced loads (L2, the previous
+        // pass's scatter by other blocks), all of a thread's loads in flight at once
+        {
+            uint32_t rk[kDsPer], ri[kDsPer];
+#pragma unroll
+            for (int k = 0; k < kDsPer; ++k) {
+                const uint32_t j = tid + k * kDsThreads;
+                if (j < m) {
+                    rk[k] = __ldcg(src_key + lo + j);
+                    if (pass == 0) {
+                        const uint32_t c = a.counts[lo + j];
+                        ri[k] = (lo + j) | ((c < kCntEsc ? c : kCntEsc) << kIdBits);
+                    } else {
+                        ri[k] = __ldcg(src_id + lo + j);
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < kDsPer; ++k) {
+                const uint32_t j = tid + k * kDsThreads;
+                if (j < m) {
+                    s_key[j] = rk[k];
+                    s_id[j] = ri[k];
+                }
+            }
         }
         __syncthreads();
         // stable ranking: warp w ranks its chunk [w cw, (w+1) cw) 32 elements at a time
@@ -117,6 +148,8 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
             const uint32_t j = base + lane;
             const bool valid = j < whi;
             const uint32_t d = valid ? (s_key[j] >> shift) & 0xFFu : 0u;
+            // lanes holding the same digit: one ballot per digit bit (a match
+            // instruction's cost grows with the distinct digits in the warp)
             uint32_t peers = __ballot_sync(0xffffffffu, valid);
 #pragma unroll
             for (int b = 0; b < 8; ++b) {
@@ -171,12 +204,26 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
         }
         grid_barrier(a.bar, a.err);
         // global start of this block's run of each digit:
-        // exclusive digit total + this digit's count in earlier blocks
+        // exclusive digit total + this digit's count in earlier blocks, the
+        // latter summed by 4 groups of 256 threads (every 4th earlier block each)
+        {
+            uint32_t* s_part = reinterpret_cast<uint32_t*>(s_wcnt);   // [4][256]; s_wcnt is free here
+            const uint32_t d = tid & (kDsRadix - 1), g = tid / kDsRadix;
+            uint32_t p0 = 0, p1 = 0;
+            uint32_t b = g;
+            for (; b + 4 < blockIdx.x; b += 8) {
+                p0 += __ldcg(a.cnt + (size_t)b * kDsRadix + d);
+                p1 += __ldcg(a.cnt + (size_t)(b + 4) * kDsRadix + d);
+            }
+            if (b < blockIdx.x) p0 += __ldcg(a.cnt + (size_t)b * kDsRadix + d);
+            s_part[g * kDsRadix + d] = p0 + p1;
+        }
+        __syncthreads();
         if (tid < kDsRadix) {
+            const uint32_t* s_part = reinterpret_cast<const uint32_t*>(s_wcnt);
             const uint32_t tot = __ldcg(a.tot + pass * kDsRadix + tid);
-            uint32_t pre = 0;
-#pragma unroll 8
-            for (uint32_t b = 0; b < blockIdx.x; ++b) pre += __ldcg(a.cnt + (size_t)b * kDsRadix + tid);
+            const uint32_t pre = s_part[tid] + s_part[kDsRadix + tid] + s_part[2 * kDsRadix + tid] +
+                                 s_part[3 * kDsRadix + tid];
             uint32_t x = tot;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -198,8 +245,14 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
             const uint32_t key = s_key2[j];
             const uint32_t pos = s_off[(key >> shift) & 0xFFu] + j;
             if (pos < n) {
-                if (pass + 1 < kDsPasses) dst_key[pos] = key;
-                dst_id[pos] = s_id2[j];
+                const uint32_t v = s_id2[j];
+                if (pass + 1 < kDsPasses) {
+                    dst_key[pos] = key;
+                    dst_id[pos] = v;
+                } else {   // last pass: plain ids, and the counts in sorted order in the free key buffer
+                    dst_id[pos] = v & kIdMask;
+                    dst_key[pos] = v >> kIdBits;
+                }
             }
         }
         grid_barrier(a.bar, a.err);
@@ -208,15 +261,28 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
     // exclusive scan of counts[id] over the sorted slice.  Stage the sorted ids
     // and their gathered counts in shared memory (independent loads), then
     // thread t scans a contiguous run of E = ceil(m / 1024) positions.
-    const uint32_t* sorted = a.ids[(kDsPasses - 1) & 1];
+    const uint32_t* sorted = ((kDsPasses - 1) & 1) ? a.ids[1] : a.ids[0];
+    const uint32_t* sorted_cnt = ((kDsPasses - 1) & 1) ? a.keys[1] : a.keys[0];
     uint32_t* s_cnt = s_key;   // reuse
-#pragma unroll 4
-    for (uint32_t j = tid; j < m; j += kDsThreads) s_id[j] = __ldcg(sorted + lo + j);
-    __syncthreads();
-#pragma unroll 4
-    for (uint32_t j = tid; j < m; j += kDsThreads) {
-        const uint32_t id = s_id[j];
-        s_cnt[j] = id < n ? a.counts[id] : 0u;
+    {
+        uint32_t rc[kDsPer];
+#pragma unroll
+        for (int k = 0; k < kDsPer; ++k) {
+            const uint32_t j = tid + k * kDsThreads;
+            rc[k] = j < m ? __ldcg(sorted_cnt + lo + j) : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < kDsPer; ++k) {
+            const uint32_t j = tid + k * kDsThreads;
+            if (j < m) {
+                uint32_t c = rc[k];
+                if (c == kCntEsc) {   // escaped: look the count up
+                    const uint32_t id = __ldcg(sorted + lo + j);
+                    c = id < n ? a.counts[id] : 0u;
+                }
+                s_cnt[j] = c;
+            }
+        }
     }
     __syncthreads();
     const uint32_t E = (m + kDsThreads - 1) / kDsThreads;
@@ -308,7 +374,7 @@ cudaError_t launch_depth_sort_scan(cudaStream_t s, int device, const uint32_t* k
                                    uint32_t* tot_scratch, int* err, int* out_idx, bool pre_zeroed)
 {
     const int G = ds_grid(device);
-    if (G <= 0 || n == 0 || n > (uint32_t)G * (uint32_t)kDsMaxSlice) return cudaErrorInvalidValue;
+    if (G <= 0 || n == 0 || n > (uint32_t)G * (uint32_t)kDsMaxSlice || n > kDsMaxN) return cudaErrorInvalidValue;
     // fewer blocks for small inputs (at least 1024 elements per block)
     const uint64_t want = ((uint64_t)n + 1023) / 1024;
     const uint32_t grid = (uint32_t)(want < (uint64_t)G ? want : (uint64_t)G);

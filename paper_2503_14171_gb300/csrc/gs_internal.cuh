@@ -219,6 +219,7 @@ size_t scan_partials_count(uint32_t n);
 // up to depth_sort_capacity(device) Gaussians (kDsMaxSlice per SM).  keys[0]
 // holds the depth keys on entry; the sorted ids land in ids[*out_idx].
 constexpr uint32_t kDsMaxSlice = 10240;
+constexpr uint32_t kDsMaxN = (1u << 21) - 1u;   // ids share a 32-bit word with the pair counts
 size_t depth_sort_smem_bytes();
 uint32_t depth_sort_capacity(int device);
 cudaError_t launch_depth_sort_scan(cudaStream_t s, int device, const uint32_t* keys_in, uint32_t* keys[2],

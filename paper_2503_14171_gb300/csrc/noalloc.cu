@@ -188,7 +188,7 @@ extern "C" gs_status gs_render_with_grads_noalloc(const gs_gaussians* g, const g
 
     int sorted = 0;
     const uint32_t ds_cap = n > 1 ? depth_sort_capacity(dev) : 0u;
-    if (n > 1 && n <= ds_cap && ds_cap / kDsMaxSlice <= kNaMaxBlocks) {
+    if (n > 1 && n <= ds_cap && n <= kDsMaxN && ds_cap / kDsMaxSlice <= kNaMaxBlocks) {
         NA_CUDA(launch_depth_sort_scan(s, dev, keys[0], keys, ids, at<uint32_t>(base, kOffSupers), n, offsets,
                                        at<uint32_t>(base, kOffDsCnt), at<unsigned long long>(base, kOffDsSum),
                                        at<unsigned int>(base, kOffDsBar), at<uint32_t>(base, kOffDsTot), err,
