@@ -155,6 +155,28 @@ gs_status gs_set_options(gs_ctx* ctx, const gs_options* opt);
  * Synchronises the stream.  W x H <= 4096 super-tiles (e.g. 4096 x 4096). */
 gs_status gs_reserve(gs_ctx* ctx, int64_t n, int32_t W, int32_t H, int64_t super_pairs);
 
+/* gs_reserve plus the per-view buffers of gs_render_views for up to V views
+ * (1 <= V <= 32) of up to n Gaussians; W, H, super_pairs bound every view. */
+gs_status gs_reserve_views(gs_ctx* ctx, int64_t n, int32_t V, int32_t W, int32_t H, int64_t super_pairs);
+
+/* Several views of one Gaussian set in one batch (e.g. the stereo pairs of a
+ * VR headset, which the paper names as a use of cheap upscaling): one launch
+ * projects every view (each Gaussian's inputs, SH coefficients included, are
+ * read once for all views), then each view is depth-sorted, binned, blended
+ * with derivatives into out_C[v] [3][H_v][W_v] and out_grads[v]
+ * [3][3][H_v][W_v], and, where out_up != NULL and out_up[v] != NULL, upscaled
+ * by factors[v] into out_up[v].  View v uses cams[v], Ws[v] x Hs[v]; each view
+ * equals a single-view gs_render_with_grads of the same camera bit for bit.
+ * Requires GS_FLAG_NO_HOST_WAIT and gs_reserve_views; makes no host-blocking
+ * call (capturable in a CUDA graph); a view beyond the reserved pairs renders
+ * as background with GS_ERR_CAPACITY at the next gs_synchronize.  Host arrays
+ * of V entries (cams, Ws, Hs, factors) and of V device pointers (out_C,
+ * out_grads, out_up).  The context's single-view results (gs_render_binned,
+ * gs_read_*, gs_backward) are invalid afterwards. */
+gs_status gs_render_views(gs_ctx* ctx, const gs_gaussians* g, int32_t V, const gs_camera* cams, const int32_t* Ws,
+                          const int32_t* Hs, float* const* out_C, float* const* out_grads, const int32_t* factors,
+                          float* const* out_up);
+
 /* Projection and tile binning for a W x H image (Sec. 4: EWA projection
  * Sigma' = J W Sigma W^T J^T + 0.3 I, front-to-back order).  Per Gaussian: view
  * depth, 2D mean, conic Sigma'^-1, colour, opacity, radius ceil(3 sqrt(lambda_max))

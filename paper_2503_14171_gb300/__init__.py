@@ -65,6 +65,10 @@ _SIGS = {
     "gs_set_stream": ([_P, _P], ct.c_int),
     "gs_set_options": ([_P, ct.POINTER(GsOptions)], ct.c_int),
     "gs_reserve": ([_P, ct.c_int64, ct.c_int32, ct.c_int32, ct.c_int64], ct.c_int),
+    "gs_reserve_views": ([_P, ct.c_int64, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int64], ct.c_int),
+    "gs_render_views": ([_P, ct.POINTER(GsGaussians), ct.c_int32, ct.POINTER(GsCamera), ct.POINTER(ct.c_int32),
+                         ct.POINTER(ct.c_int32), ct.POINTER(_P), ct.POINTER(_P), ct.POINTER(ct.c_int32),
+                         ct.POINTER(_P)], ct.c_int),
     "gs_project": ([_P, ct.POINTER(GsGaussians), ct.POINTER(GsCamera), ct.c_int32, ct.c_int32], ct.c_int),
     "gs_render_binned": ([_P, _P, _P], ct.c_int),
     "gs_render_with_grads": ([_P, ct.POINTER(GsGaussians), ct.POINTER(GsCamera), ct.c_int32, ct.c_int32, _P, _P],
@@ -299,6 +303,34 @@ class Context:
     def reserve(self, n: int, W: int, H: int, super_pairs: int):
         """Allocate every buffer for frames up to these sizes (needed for no_host_wait)."""
         _chk(lib.gs_reserve(self.h, int(n), int(W), int(H), int(super_pairs)), self.h, "gs_reserve")
+
+    def reserve_views(self, n: int, V: int, W: int, H: int, super_pairs: int):
+        """Buffers for gs_render_views batches of up to V views."""
+        _chk(lib.gs_reserve_views(self.h, int(n), int(V), int(W), int(H), int(super_pairs)), self.h,
+             "gs_reserve_views")
+
+    def render_views(self, scene: DeviceScene, cams: list, sizes: list, factors=None, outs=None):
+        """Render len(cams) views (sizes: [(W, H)]) with derivatives in one batch;
+        with factors, also upscale view v by factors[v].  Returns a list of
+        (C, G) or (C, G, up) per view."""
+        V = len(cams)
+        if outs is None:
+            outs = []
+            for v, (W, H) in enumerate(sizes):
+                o = [self._empty(3, H, W), self._empty(3, 3, H, W)]
+                if factors is not None:
+                    o.append(self._empty(3, H * factors[v], W * factors[v]))
+                outs.append(o)
+        cam_arr = (GsCamera * V)(*[make_camera(c) for c in cams])
+        Ws = (ct.c_int32 * V)(*[int(w) for w, _ in sizes])
+        Hs = (ct.c_int32 * V)(*[int(h) for _, h in sizes])
+        pC = (_P * V)(*[o[0].data_ptr() for o in outs])
+        pG = (_P * V)(*[o[1].data_ptr() for o in outs])
+        fac = (ct.c_int32 * V)(*[int(f) for f in factors]) if factors is not None else None
+        pU = (_P * V)(*[o[2].data_ptr() for o in outs]) if factors is not None else None
+        _chk(lib.gs_render_views(self.h, ct.byref(scene.struct), V, cam_arr, Ws, Hs, pC, pG, fac, pU), self.h,
+             "gs_render_views")
+        return outs
 
     def set_options(self, mode=None, bg=None, max_pairs=None):
         if mode is not None:

@@ -480,7 +480,9 @@ gs_status gs_destroy(gs_ctx* c)
                       &c->pairs[1],
                       &c->sort_hist, &c->sort_status,
                       &c->sort_counter, &c->sranges, &c->tile_count, &c->tile_start, &c->state, &c->count,
-                      &c->errword, &c->grad2d, &c->up_planes, &c->pair_check};
+                      &c->errword, &c->grad2d, &c->up_planes, &c->pair_check,
+                      &c->vrec0, &c->vrec1, &c->vrec2, &c->vrect, &c->vsupers, &c->vkey, &c->vtotals,
+                      &c->views_dev};
     for (DevBuf* b : bufs) release(*b);
     if (c->h_scalar) cudaFreeHost(c->h_scalar);
     if (c->totals_ready) cudaEventDestroy(c->totals_ready);
@@ -735,10 +737,12 @@ gs_status gs_super_pair_count(gs_ctx* c, int64_t* Ps)
     return GS_OK;
 }
 
-gs_status gs_reserve(gs_ctx* c, int64_t n, int32_t W, int32_t H, int64_t super_pairs)
+namespace {
+
+gs_status reserve_impl(gs_ctx* c, int64_t n, int32_t V, int32_t W, int32_t H, int64_t super_pairs)
 {
-    if (!c) return GS_ERR_INVALID_ARG;
-    if (n < 0 || n > 0x7FFFFFFF || W < 1 || H < 1 || super_pairs < 1 || super_pairs > kMaxPairs)
+    if (n < 0 || n > 0x7FFFFFFF || W < 1 || H < 1 || super_pairs < 1 || super_pairs > kMaxPairs || V < 0 ||
+        V > kMaxViews)
         return fail(c, GS_ERR_INVALID_ARG, "bad reserve sizes");
     const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
     const int stiles_x = (tiles_x + kSuper - 1) / kSuper, stiles_y = (tiles_y + kSuper - 1) / kSuper;
@@ -776,13 +780,168 @@ gs_status gs_reserve(gs_ctx* c, int64_t n, int32_t W, int32_t H, int64_t super_p
         (st = ensure(c, c->grad2d, sizeof(float) * 9 * un)) || (st = ensure(c, c->up_planes, sizeof(float) * 12 * pix)) ||
         (st = ensure(c, c->pair_check, sizeof(PairCheckOut))))
         return st;
+    if (V > 0) {
+        const size_t vn = un * (size_t)V;
+        if ((st = ensure(c, c->vrec0, sizeof(float4) * vn)) || (st = ensure(c, c->vrec1, sizeof(float4) * vn)) ||
+            (st = ensure(c, c->vrec2, sizeof(float4) * vn)) || (st = ensure(c, c->vrect, sizeof(ushort4) * vn)) ||
+            (st = ensure(c, c->vsupers, sizeof(uint32_t) * vn)) || (st = ensure(c, c->vkey, sizeof(uint32_t) * vn)) ||
+            (st = ensure(c, c->vtotals, sizeof(unsigned long long) * 2 * kTotalSlots * (size_t)V)) ||
+            (st = ensure(c, c->views_dev, sizeof(ViewDesc) * kMaxViews)))
+            return st;
+    }
     GS_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->res_views = V;
     c->res_n = n;
     c->res_pixels = (int64_t)pix;
     c->res_tiles = T;
     c->res_supers = Ts;
     c->res_pairs = super_pairs;
     c->reserved = true;
+    return GS_OK;
+}
+
+}  // namespace
+
+gs_status gs_reserve(gs_ctx* c, int64_t n, int32_t W, int32_t H, int64_t super_pairs)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    return reserve_impl(c, n, 0, W, H, super_pairs);
+}
+
+gs_status gs_reserve_views(gs_ctx* c, int64_t n, int32_t V, int32_t W, int32_t H, int64_t super_pairs)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (V < 1) return fail(c, GS_ERR_INVALID_ARG, "V must be >= 1");
+    return reserve_impl(c, n, V, W, H, super_pairs);
+}
+
+gs_status gs_render_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_camera* cams, const int32_t* Ws,
+                          const int32_t* Hs, float* const* out_C, float* const* out_grads, const int32_t* factors,
+                          float* const* out_up)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    LaunchTally tally(c);
+    if (!(c->opt.flags & GS_FLAG_NO_HOST_WAIT) || !c->reserved || c->res_views < 1)
+        return fail(c, GS_ERR_NOT_READY, "gs_render_views needs GS_FLAG_NO_HOST_WAIT and gs_reserve_views");
+    if (V < 1 || V > c->res_views) return fail(c, GS_ERR_CAPACITY, "%d views, %d reserved", V, c->res_views);
+    if (!cams || !Ws || !Hs || !out_C || !out_grads) return fail(c, GS_ERR_INVALID_ARG, "NULL argument");
+    gs_status st = check_gaussians(c, g);
+    if (st != GS_OK) return st;
+    const uint32_t n = (uint32_t)g->n;
+    if ((int64_t)n > c->res_n) return fail(c, GS_ERR_CAPACITY, "n %u exceeds the reserved %lld", n, (long long)c->res_n);
+    ViewBatch batch{};
+    for (int v = 0; v < V; ++v) {
+        const int W = Ws[v], H = Hs[v];
+        if (W < 1 || H < 1 || !(cams[v].fx > 0.f) || !(cams[v].fy > 0.f) || !out_C[v] || !out_grads[v])
+            return fail(c, GS_ERR_INVALID_ARG, "bad view %d", v);
+        const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
+        const int64_t T = (int64_t)tiles_x * tiles_y;
+        const int64_t Ts = (int64_t)((tiles_x + kSuper - 1) / kSuper) * ((tiles_y + kSuper - 1) / kSuper);
+        if (T > c->res_tiles || Ts > c->res_supers || (int64_t)W * H > c->res_pixels)
+            return fail(c, GS_ERR_CAPACITY, "view %d (%d x %d) exceeds the reserved sizes", v, W, H);
+        if (out_up && out_up[v]) {
+            const int f = factors ? factors[v] : 0;
+            if (f < 1 || f > 16 || W < 2 || H < 2) return fail(c, GS_ERR_INVALID_ARG, "bad upscale of view %d", v);
+        }
+        batch.v[v].cam = make_camera(cams[v], W, H);
+        batch.v[v].W = W;
+        batch.v[v].H = H;
+        batch.v[v].tiles_x = tiles_x;
+        batch.v[v].tiles_y = tiles_y;
+    }
+    c->have_proj = false;
+    c->have_state = false;
+    cudaStream_t s = c->stream;
+    // all views projected in one launch
+    unsigned long long* vtot = as<unsigned long long>(c->vtotals);
+    GS_CUDA(c, cudaMemsetAsync(vtot, 0, sizeof(unsigned long long) * 2 * kTotalSlots * V, s));
+    GS_CUDA(c, launch_set_views(s, batch, V, as<ViewDesc>(c->views_dev)));
+    ViewOutputs vo;
+    vo.rec = Records{as<float4>(c->vrec0), as<float4>(c->vrec1), as<float4>(c->vrec2)};
+    vo.rect = as<ushort4>(c->vrect);
+    vo.supers = as<uint32_t>(c->vsupers);
+    vo.depth_key = as<uint32_t>(c->vkey);
+    vo.totals = vtot;
+    GS_CUDA(c, launch_project_views(s, *g, as<ViewDesc>(c->views_dev), V, c->opt.mode, vo));
+
+    // then each view: depth order, emission, pair check and sort, blend (and upscale)
+    const uint32_t ds_cap = n > 1 ? depth_sort_capacity(c->device) : 0u;
+    const bool persistent = n > 1 && n <= ds_cap && n <= kDsMaxN;
+    const size_t G = ds_cap / kDsMaxSlice;
+    const uint32_t cap = (uint32_t)c->res_pairs;
+    const int64_t limit = c->opt.max_pairs > 0 ? std::min<int64_t>(c->opt.max_pairs, kMaxPairs) : kMaxPairs;
+    uint64_t* pairs[2] = {as<uint64_t>(c->pairs[0]), as<uint64_t>(c->pairs[1])};
+    PairCheckOut* chk = as<PairCheckOut>(c->pair_check);
+    for (int v = 0; v < V; ++v) {
+        const ViewDesc& d = batch.v[v];
+        const int stiles_x = (d.tiles_x + kSuper - 1) / kSuper, stiles_y = (d.tiles_y + kSuper - 1) / kSuper;
+        const uint32_t Ts = (uint32_t)(stiles_x * stiles_y);
+        const int sbits = bits_for(Ts);
+        const int spasses = radix_passes(32, 32 + sbits);
+        const size_t off = (size_t)v * n;
+        uint32_t* keys_v = as<uint32_t>(c->vkey) + off;
+        uint32_t* supers_v = as<uint32_t>(c->vsupers) + off;
+        const ushort4* rect_v = as<ushort4>(c->vrect) + off;
+        uint32_t* keys[2] = {as<uint32_t>(c->dkey[0]), as<uint32_t>(c->dkey[1])};
+        uint32_t* ids[2] = {as<uint32_t>(c->did[0]), as<uint32_t>(c->did[1])};
+        GS_CUDA(c, cudaMemsetAsync(c->super_counts.p, 0, sizeof(uint32_t) * kCountCopies * Ts, s));
+        int sorted = 0;
+        if (persistent) {
+            unsigned char* base = as<unsigned char>(c->ds_scratch);
+            GS_CUDA(c, launch_depth_sort_scan(s, c->device, keys_v, keys, ids, supers_v, n, as<uint32_t>(c->offsets),
+                                              reinterpret_cast<uint32_t*>(base),
+                                              reinterpret_cast<unsigned long long*>(base + G * kRadixDigits * 4),
+                                              reinterpret_cast<unsigned int*>(base + G * kRadixDigits * 4 + G * 8),
+                                              reinterpret_cast<uint32_t*>(base + G * kRadixDigits * 4 + G * 8 + 64),
+                                              as<int>(c->errword), &sorted, false));
+        } else {
+            unsigned long long* scan_tot = as<unsigned long long>(c->scan_totals) + 2 * kTotalSlots;
+            if (n > 1) {
+                GS_CUDA(c, cudaMemcpyAsync(keys[0], keys_v, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+                GS_CUDA(c, launch_iota(s, ids[0], n));
+                GS_CUDA(c, radix_sort_u32_pairs(s, keys, ids, n, 0, 32, as<uint32_t>(c->sort_hist),
+                                                as<uint32_t>(c->sort_status), as<uint32_t>(c->sort_counter),
+                                                as<int>(c->errword), &sorted));
+            } else {
+                GS_CUDA(c, launch_iota(s, ids[0], n));
+            }
+            GS_CUDA(c, launch_scan_gathered(s, supers_v, nullptr, ids[sorted], n, as<uint32_t>(c->offsets),
+                                            as<unsigned long long>(c->scan_partials),
+                                            reinterpret_cast<uint32_t*>(scan_tot + 2), scan_tot, as<int>(c->errword)));
+        }
+        GS_CUDA(c, launch_emit_pairs(s, ids[sorted], as<uint32_t>(c->offsets), rect_v, n, stiles_x, pairs[0],
+                                     as<uint32_t>(c->super_counts), Ts, cap));
+        GS_CUDA(c, launch_supers_to_hist(s, as<uint32_t>(c->super_counts), Ts, spasses, as<uint32_t>(c->sort_hist),
+                                         as<uint2>(c->sranges),
+                                         PairCheckIn{vtot + (size_t)v * 2 * kTotalSlots, cap,
+                                                     (unsigned long long)limit},
+                                         chk, as<int>(c->errword)));
+        int psorted = 0;
+        if (Ts > 1 && cap > 1)
+            GS_CUDA(c, radix_sort_u64_keys(s, pairs, cap, 32, 32 + sbits, as<uint32_t>(c->sort_hist),
+                                           as<uint32_t>(c->sort_status), as<uint32_t>(c->sort_counter),
+                                           as<int>(c->errword), &psorted, true, &chk->count, false));
+        BlendArgs a;
+        a.W = d.W;
+        a.H = d.H;
+        a.tiles_x = d.tiles_x;
+        a.tiles_y = d.tiles_y;
+        a.stiles_x = stiles_x;
+        a.n = n;
+        a.sranges = as<uint2>(c->sranges);
+        a.pair_words = reinterpret_cast<const uint32_t*>(pairs[psorted]);
+        a.rect = rect_v;
+        a.rec = Records{as<float4>(c->vrec0) + off, as<float4>(c->vrec1) + off, as<float4>(c->vrec2) + off};
+        a.bg = make_float3(c->opt.bg[0], c->opt.bg[1], c->opt.bg[2]);
+        a.out_C = out_C[v];
+        a.out_G = out_grads[v];
+        a.state = nullptr;
+        a.count = nullptr;
+        GS_CUDA(c, launch_blend(s, true, c->opt.mode, a));
+        if (out_up && out_up[v])
+            GS_CUDA(c, launch_upscale(s, out_C[v], out_grads[v], d.W, d.H, factors[v], out_up[v]));
+    }
+    c->totals_known = false;
     return GS_OK;
 }
 

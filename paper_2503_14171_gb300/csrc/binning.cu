@@ -149,6 +149,19 @@ __global__ void __launch_bounds__(1024) k_tile_starts(const uint32_t* __restrict
 
 }  // namespace
 
+__global__ void k_iota(uint32_t* __restrict__ ids, uint32_t n)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) ids[i] = i;
+}
+
+cudaError_t launch_iota(cudaStream_t s, uint32_t* ids, uint32_t n)
+{
+    if (n == 0) return cudaSuccess;
+    k_iota<<<(n + 255) / 256, 256, 0, s>>>(ids, n); note_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_emit_pairs(cudaStream_t s, const uint32_t* ids, const uint32_t* offsets, const ushort4* rect,
                               uint32_t n, int stiles_x, uint64_t* pairs, uint32_t* counts, uint32_t Ts, uint32_t cap)
 {

@@ -138,6 +138,13 @@ struct gs_ctx {
     bool reserved = false;
     int64_t res_n = 0, res_pixels = 0, res_tiles = 0, res_supers = 0, res_pairs = 0;
     gs::DevBuf pair_check;              // gs::PairCheckOut, device side
+    // batched views (gs_render_views): per-view projection outputs, view v at v * n
+    int res_views = 0;
+    gs::DevBuf vrec0, vrec1, vrec2;     // float4[V][n]
+    gs::DevBuf vrect;                   // ushort4[V][n]
+    gs::DevBuf vsupers, vkey;           // uint32[V][n]
+    gs::DevBuf vtotals;                 // uint64[V][2 kTotalSlots]
+    gs::DevBuf views_dev;               // gs::ViewDesc[kMaxViews]
     bool totals_known = true;           // P, Ps valid on the host
     gs::DevBuf up_planes;               // float[12][H][W] upstream planes of gs_backward
     unsigned long long* h_scalar = nullptr;   // pinned host scalar for the pair count
@@ -155,6 +162,32 @@ int64_t& launch_counter();
 inline void note_launch() { ++launch_counter(); }
 
 // ---- launchers (each returns the cudaError_t of its launch) ----
+// One view of a batch: camera and image size.
+struct ViewDesc {
+    CameraParams cam;
+    int W, H, tiles_x, tiles_y;
+};
+// Per-view outputs of the batched projection, view v at offset v * n (totals:
+// 2 kTotalSlots per view).
+struct ViewOutputs {
+    Records rec;
+    ushort4* rect;
+    uint32_t* supers;
+    uint32_t* depth_key;
+    unsigned long long* totals;
+};
+cudaError_t launch_project_views(cudaStream_t s, const gs_gaussians& g, const ViewDesc* views, int V, int mode,
+                                 const ViewOutputs& out);
+// Copy a batch of view descriptions to device memory through kernel
+// parameters (recorded by value in a CUDA graph; no host buffer involved).
+constexpr int kMaxViews = 32;
+struct ViewBatch {
+    ViewDesc v[kMaxViews];
+};
+cudaError_t launch_set_views(cudaStream_t s, const ViewBatch& b, int V, ViewDesc* dst);
+// ids[i] = i for i < n
+cudaError_t launch_iota(cudaStream_t s, uint32_t* ids, uint32_t n);
+
 // Buffers of later kernels in the frame that must start at zero; the
 // projection kernel clears them (grid-stride) so the frame needs no memsets.
 struct ZeroList {

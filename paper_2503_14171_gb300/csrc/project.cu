@@ -76,6 +76,152 @@ __device__ __forceinline__ void sh_colour(const float* __restrict__ sh, int deg,
     out[2] = fmaxf(0.f, b + 0.5f);
 }
 
+// 3D covariance Sigma = M M^T with M = R diag(s), R from the unit quaternion:
+// S = (S00, S01, S02, S11, S12, S22); ok = false for a zero quaternion.
+__device__ __forceinline__ void cov3d(const float* __restrict__ quats, const float* __restrict__ log_scales, int ii,
+                                      float S[6], bool& ok)
+{
+    float qw = quats[4 * ii], qx = quats[4 * ii + 1], qy = quats[4 * ii + 2], qz = quats[4 * ii + 3];
+    const float qn2 = qw * qw + qx * qx + qy * qy + qz * qz;
+    ok = qn2 > 0.f;
+    const float qinv = rsqrtf(qn2);
+    qw *= qinv; qx *= qinv; qy *= qinv; qz *= qinv;
+    const float s0 = expf(log_scales[3 * ii]), s1 = expf(log_scales[3 * ii + 1]), s2 = expf(log_scales[3 * ii + 2]);
+    const float R00 = 1.f - 2.f * (qy * qy + qz * qz), R01 = 2.f * (qx * qy - qw * qz), R02 = 2.f * (qx * qz + qw * qy);
+    const float R10 = 2.f * (qx * qy + qw * qz), R11 = 1.f - 2.f * (qx * qx + qz * qz), R12 = 2.f * (qy * qz - qw * qx);
+    const float R20 = 2.f * (qx * qz - qw * qy), R21 = 2.f * (qy * qz + qw * qx), R22 = 1.f - 2.f * (qx * qx + qy * qy);
+    const float M00 = R00 * s0, M01 = R01 * s1, M02 = R02 * s2;
+    const float M10 = R10 * s0, M11 = R11 * s1, M12 = R12 * s2;
+    const float M20 = R20 * s0, M21 = R21 * s1, M22 = R22 * s2;
+    S[0] = M00 * M00 + M01 * M01 + M02 * M02;
+    S[1] = M00 * M10 + M01 * M11 + M02 * M12;
+    S[2] = M00 * M20 + M01 * M21 + M02 * M22;
+    S[3] = M10 * M10 + M11 * M11 + M12 * M12;
+    S[4] = M10 * M20 + M11 * M21 + M12 * M22;
+    S[5] = M20 * M20 + M21 * M21 + M22 * M22;
+}
+
+// One Gaussian in one view: EWA projection, conic, radius, mean and tile rect.
+struct ViewProj {
+    float pz, m2x, m2y, ca, cb, cc, rad;
+    int4 rc;
+    uint32_t ntiles, nsup;
+    bool vis;
+};
+
+__device__ __forceinline__ ViewProj project_view(float mx3, float my3, float mz3, const float S[6], bool ok, float L,
+                                                 const CameraParams& cam, int W, int H, int tiles_x, int tiles_y,
+                                                 int mode)
+{
+    ViewProj o;
+    const float S00 = S[0], S01 = S[1], S02 = S[2], S11 = S[3], S12 = S[4], S22 = S[5];
+    const float px = fmaf(cam.R[0], mx3, fmaf(cam.R[1], my3, fmaf(cam.R[2], mz3, cam.t[0])));
+    const float py = fmaf(cam.R[3], mx3, fmaf(cam.R[4], my3, fmaf(cam.R[5], mz3, cam.t[1])));
+    const float pz = fmaf(cam.R[6], mx3, fmaf(cam.R[7], my3, fmaf(cam.R[8], mz3, cam.t[2])));
+    bool vis = ok && pz > cam.znear;
+
+    // Jacobian of the perspective map at the frustum-clamped mean, times W
+    const float iz = 1.f / pz;
+    const float txz = fminf(cam.lim_x, fmaxf(-cam.lim_x, px * iz));
+    const float tyz = fminf(cam.lim_y, fmaxf(-cam.lim_y, py * iz));
+    const float j00 = cam.fx * iz, j02 = -cam.fx * txz * iz;
+    const float j11 = cam.fy * iz, j12 = -cam.fy * tyz * iz;
+    // T = J W (2x3)
+    const float T00 = j00 * cam.R[0] + j02 * cam.R[6];
+    const float T01 = j00 * cam.R[1] + j02 * cam.R[7];
+    const float T02 = j00 * cam.R[2] + j02 * cam.R[8];
+    const float T10 = j11 * cam.R[3] + j12 * cam.R[6];
+    const float T11 = j11 * cam.R[4] + j12 * cam.R[7];
+    const float T12 = j11 * cam.R[5] + j12 * cam.R[8];
+    // U = T Sigma
+    const float U00 = T00 * S00 + T01 * S01 + T02 * S02;
+    const float U01 = T00 * S01 + T01 * S11 + T02 * S12;
+    const float U02 = T00 * S02 + T01 * S12 + T02 * S22;
+    const float U10 = T10 * S00 + T11 * S01 + T12 * S02;
+    const float U11 = T10 * S01 + T11 * S11 + T12 * S12;
+    const float U12 = T10 * S02 + T11 * S12 + T12 * S22;
+    const float c00 = U00 * T00 + U01 * T01 + U02 * T02 + 0.3f;
+    const float c01 = U00 * T10 + U01 * T11 + U02 * T12;
+    const float c11 = U10 * T10 + U11 * T11 + U12 * T12 + 0.3f;
+    const float det = c00 * c11 - c01 * c01;
+    vis = vis && det > 0.f;
+
+    const float idet = 1.f / det;
+    o.ca = c11 * idet;
+    o.cb = -c01 * idet;
+    o.cc = c00 * idet;
+    const float mid = 0.5f * (c00 + c11);
+    const float hd = 0.5f * (c00 - c11);
+    const float lam = mid + sqrtf(hd * hd + c01 * c01);   // cancellation-free largest eigenvalue
+    const float rad = ceilf(3.f * sqrtf(lam));
+    const float m2x = fmaf(cam.fx, px * iz, cam.cx);
+    const float m2y = fmaf(cam.fy, py * iz, cam.cy);
+
+    vis = vis && isfinite(m2x) && isfinite(m2y) && isfinite(rad);
+    // alpha = sigma e^g >= 1/255 only inside d^T Sigma'^-1 d <= 2L, L = ln(255 sigma)
+    int4 rc = make_int4(0, 0, -1, -1);
+    uint32_t ntiles = 0;
+    if (vis) {
+        if (mode == GS_MODE_EXACT) {
+            rc = make_int4(0, 0, tiles_x - 1, tiles_y - 1);
+            ntiles = (uint32_t)(tiles_x * tiles_y);
+        } else if (L > 0.f) {
+            // tiles holding a pixel centre (i, j) with |i - mx| <= hx, |j - my| <= hy:
+            // the 3-sigma square cut to the bounding box of the alpha >= 1/255 ellipse
+            const float hx = fminf(rad, sqrtf(2.f * L * c00));
+            const float hy = fminf(rad, sqrtf(2.f * L * c11));
+            const float lox = ceilf(m2x - hx), hix = floorf(m2x + hx);
+            const float loy = ceilf(m2y - hy), hiy = floorf(m2y + hy);
+            if (!(hix < 0.f || lox > (float)(W - 1) || hiy < 0.f || loy > (float)(H - 1) || lox > hix ||
+                  loy > hiy)) {
+                const int x0 = lox < 0.f ? 0 : (int)lox;
+                const int y0 = loy < 0.f ? 0 : (int)loy;
+                const int x1 = hix > (float)(W - 1) ? W - 1 : (int)hix;
+                const int y1 = hiy > (float)(H - 1) ? H - 1 : (int)hiy;
+                rc = make_int4(x0 / kTile, y0 / kTile, x1 / kTile, y1 / kTile);
+                ntiles = (uint32_t)((rc.z - rc.x + 1) * (rc.w - rc.y + 1));
+            }
+        }
+    }
+    o.pz = pz;
+    o.m2x = m2x;
+    o.m2y = m2y;
+    o.rad = rad;
+    o.rc = rc;
+    o.ntiles = ntiles;
+    o.nsup = ntiles ? (uint32_t)((rc.z / kSuper - rc.x / kSuper + 1) * (rc.w / kSuper - rc.y / kSuper + 1)) : 0u;
+    o.vis = vis;
+    return o;
+}
+
+// The three records of a visible Gaussian in one view (colour from the SH
+// coefficients shv, or rgb).  The blend evaluates the exponent in base 2:
+// g2 = g log2(e) with g = -1/2 (a dx^2 + 2 b dx dy + c dy^2).  Reject
+// threshold: g < ln(1/(255 sigma)) - 1e-4 guarantees sigma e^g < 1/255 in FP32,
+// so the blend may skip the exponential there.
+template <int DEG>
+__device__ __forceinline__ void view_records(const ViewProj& v, float mx3, float my3, float mz3, const float* shv,
+                                             const float* rgb, float op, float L, const CameraParams& cam, int mode,
+                                             float4& r0, float4& r1, float4& r2)
+{
+    float col[3];
+    if (DEG >= 0) {
+        float dx = mx3 - cam.campos[0], dy = my3 - cam.campos[1], dz = mz3 - cam.campos[2];
+        const float dn = rsqrtf(dx * dx + dy * dy + dz * dz);
+        dx *= dn; dy *= dn; dz *= dn;
+        sh_colour(shv, DEG, dx, dy, dz, col);
+    } else {
+        col[0] = rgb[0];
+        col[1] = rgb[1];
+        col[2] = rgb[2];
+    }
+    constexpr float kLog2e = 1.4426950408889634f;
+    const float thr = (mode == GS_MODE_EXACT) ? -INFINITY : (-L - 1e-4f) * kLog2e;
+    r0 = make_float4(v.m2x, v.m2y, -v.ca, -v.cc);
+    r1 = make_float4(-0.5f * kLog2e * v.ca, -kLog2e * v.cb, -0.5f * kLog2e * v.cc, thr);
+    r2 = make_float4(col[0], col[1], col[2], op);
+}
+
 constexpr int kProjThreads = 128;
 
 // DEG: SH degree 0..3, or -1 for direct RGB colours.  Each warp first copies the
@@ -123,101 +269,17 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
     const bool inrange = i < n;
     const int ii = inrange ? i : n - 1;
     const float mx3 = means[3 * ii], my3 = means[3 * ii + 1], mz3 = means[3 * ii + 2];
-    const float px = fmaf(cam.R[0], mx3, fmaf(cam.R[1], my3, fmaf(cam.R[2], mz3, cam.t[0])));
-    const float py = fmaf(cam.R[3], mx3, fmaf(cam.R[4], my3, fmaf(cam.R[5], mz3, cam.t[1])));
-    const float pz = fmaf(cam.R[6], mx3, fmaf(cam.R[7], my3, fmaf(cam.R[8], mz3, cam.t[2])));
-
-    bool vis = inrange && pz > cam.znear;
-    // 3D covariance Sigma = M M^T with M = R diag(s), R from the unit quaternion
-    float qw = quats[4 * ii], qx = quats[4 * ii + 1], qy = quats[4 * ii + 2], qz = quats[4 * ii + 3];
-    const float qn2 = qw * qw + qx * qx + qy * qy + qz * qz;
-    vis = vis && qn2 > 0.f;
-    const float qinv = rsqrtf(qn2);
-    qw *= qinv; qx *= qinv; qy *= qinv; qz *= qinv;
-    const float s0 = expf(log_scales[3 * ii]), s1 = expf(log_scales[3 * ii + 1]), s2 = expf(log_scales[3 * ii + 2]);
-    const float R00 = 1.f - 2.f * (qy * qy + qz * qz), R01 = 2.f * (qx * qy - qw * qz), R02 = 2.f * (qx * qz + qw * qy);
-    const float R10 = 2.f * (qx * qy + qw * qz), R11 = 1.f - 2.f * (qx * qx + qz * qz), R12 = 2.f * (qy * qz - qw * qx);
-    const float R20 = 2.f * (qx * qz - qw * qy), R21 = 2.f * (qy * qz + qw * qx), R22 = 1.f - 2.f * (qx * qx + qy * qy);
-    const float M00 = R00 * s0, M01 = R01 * s1, M02 = R02 * s2;
-    const float M10 = R10 * s0, M11 = R11 * s1, M12 = R12 * s2;
-    const float M20 = R20 * s0, M21 = R21 * s1, M22 = R22 * s2;
-    const float S00 = M00 * M00 + M01 * M01 + M02 * M02;
-    const float S01 = M00 * M10 + M01 * M11 + M02 * M12;
-    const float S02 = M00 * M20 + M01 * M21 + M02 * M22;
-    const float S11 = M10 * M10 + M11 * M11 + M12 * M12;
-    const float S12 = M10 * M20 + M11 * M21 + M12 * M22;
-    const float S22 = M20 * M20 + M21 * M21 + M22 * M22;
-
-    // Jacobian of the perspective map at the frustum-clamped mean, times W
-    const float iz = 1.f / pz;
-    const float txz = fminf(cam.lim_x, fmaxf(-cam.lim_x, px * iz));
-    const float tyz = fminf(cam.lim_y, fmaxf(-cam.lim_y, py * iz));
-    const float j00 = cam.fx * iz, j02 = -cam.fx * txz * iz;
-    const float j11 = cam.fy * iz, j12 = -cam.fy * tyz * iz;
-    // T = J W (2x3)
-    const float T00 = j00 * cam.R[0] + j02 * cam.R[6];
-    const float T01 = j00 * cam.R[1] + j02 * cam.R[7];
-    const float T02 = j00 * cam.R[2] + j02 * cam.R[8];
-    const float T10 = j11 * cam.R[3] + j12 * cam.R[6];
-    const float T11 = j11 * cam.R[4] + j12 * cam.R[7];
-    const float T12 = j11 * cam.R[5] + j12 * cam.R[8];
-    // U = T Sigma
-    const float U00 = T00 * S00 + T01 * S01 + T02 * S02;
-    const float U01 = T00 * S01 + T01 * S11 + T02 * S12;
-    const float U02 = T00 * S02 + T01 * S12 + T02 * S22;
-    const float U10 = T10 * S00 + T11 * S01 + T12 * S02;
-    const float U11 = T10 * S01 + T11 * S11 + T12 * S12;
-    const float U12 = T10 * S02 + T11 * S12 + T12 * S22;
-    const float c00 = U00 * T00 + U01 * T01 + U02 * T02 + 0.3f;
-    const float c01 = U00 * T10 + U01 * T11 + U02 * T12;
-    const float c11 = U10 * T10 + U11 * T11 + U12 * T12 + 0.3f;
-    const float det = c00 * c11 - c01 * c01;
-    vis = vis && det > 0.f;
-
-    const float idet = 1.f / det;
-    const float ca = c11 * idet, cb = -c01 * idet, cc = c00 * idet;
-    const float mid = 0.5f * (c00 + c11);
-    const float hd = 0.5f * (c00 - c11);
-    const float lam = mid + sqrtf(hd * hd + c01 * c01);   // cancellation-free largest eigenvalue
-    const float rad = ceilf(3.f * sqrtf(lam));
-    const float m2x = fmaf(cam.fx, px * iz, cam.cx);
-    const float m2y = fmaf(cam.fy, py * iz, cam.cy);
-
-    vis = vis && isfinite(m2x) && isfinite(m2y) && isfinite(rad);
+    float S[6];
+    bool qok;
+    cov3d(quats, log_scales, ii, S, qok);
     const float op = 1.f / (1.f + expf(-op_logits[ii]));
-    // alpha = sigma e^g >= 1/255 only inside d^T Sigma'^-1 d <= 2L, L = ln(255 sigma)
     const float L = logf(255.f * op);
-    int4 rc = make_int4(0, 0, -1, -1);
-    uint32_t ntiles = 0;
-    if (vis) {
-        if (mode == GS_MODE_EXACT) {
-            rc = make_int4(0, 0, tiles_x - 1, tiles_y - 1);
-            ntiles = (uint32_t)(tiles_x * tiles_y);
-        } else if (L > 0.f) {
-            // tiles holding a pixel centre (i, j) with |i - mx| <= hx, |j - my| <= hy:
-            // the 3-sigma square cut to the bounding box of the alpha >= 1/255 ellipse
-            const float hx = fminf(rad, sqrtf(2.f * L * c00));
-            const float hy = fminf(rad, sqrtf(2.f * L * c11));
-            const float lox = ceilf(m2x - hx), hix = floorf(m2x + hx);
-            const float loy = ceilf(m2y - hy), hiy = floorf(m2y + hy);
-            if (!(hix < 0.f || lox > (float)(W - 1) || hiy < 0.f || loy > (float)(H - 1) || lox > hix ||
-                  loy > hiy)) {
-                const int x0 = lox < 0.f ? 0 : (int)lox;
-                const int y0 = loy < 0.f ? 0 : (int)loy;
-                const int x1 = hix > (float)(W - 1) ? W - 1 : (int)hix;
-                const int y1 = hiy > (float)(H - 1) ? H - 1 : (int)hiy;
-                rc = make_int4(x0 / kTile, y0 / kTile, x1 / kTile, y1 / kTile);
-                ntiles = (uint32_t)((rc.z - rc.x + 1) * (rc.w - rc.y + 1));
-            }
-        }
-    }
-    const uint32_t nsup =
-        ntiles ? (uint32_t)((rc.z / kSuper - rc.x / kSuper + 1) * (rc.w / kSuper - rc.y / kSuper + 1)) : 0u;
+    const ViewProj v = project_view(mx3, my3, mz3, S, qok && inrange, L, cam, W, H, tiles_x, tiles_y, mode);
     // frame totals of (super-tile, Gaussian) and (tile, Gaussian) pairs: they do
     // not depend on the depth order, so they are summed here -- per block, then
     // into one of kTotalSlots slot pairs (spreading the atomics), summed on the host
     __shared__ unsigned long long s_tot[2][kProjThreads / 32];
-    unsigned long long wsum = nsup, wt = ntiles;
+    unsigned long long wsum = v.nsup, wt = v.ntiles;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
@@ -235,42 +297,110 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
         if (b) atomicAdd(&totals[2 * (blockIdx.x % kTotalSlots) + threadIdx.x], b);
     }
     if (!inrange) return;
+    const int4 rc = v.rc;
     ids[i] = (uint32_t)i;
-    tiles_out[i] = ntiles;
-    supers_out[i] = nsup;
-    rect_out[i] = ntiles ? make_ushort4((unsigned short)rc.x, (unsigned short)rc.y, (unsigned short)rc.z,
-                                        (unsigned short)rc.w)
-                         : make_ushort4(1, 1, 0, 0);
-    radius_out[i] = vis ? (int)rad : 0;
-    depth_out[i] = vis ? pz : 0.f;
-    depth_key[i] = ntiles > 0 ? __float_as_uint(pz) : 0xFFFFFFFFu;
-    if (!vis) {
+    tiles_out[i] = v.ntiles;
+    supers_out[i] = v.nsup;
+    rect_out[i] = v.ntiles ? make_ushort4((unsigned short)rc.x, (unsigned short)rc.y, (unsigned short)rc.z,
+                                          (unsigned short)rc.w)
+                           : make_ushort4(1, 1, 0, 0);
+    radius_out[i] = v.vis ? (int)v.rad : 0;
+    depth_out[i] = v.vis ? v.pz : 0.f;
+    depth_key[i] = v.ntiles > 0 ? __float_as_uint(v.pz) : 0xFFFFFFFFu;
+    if (!v.vis) {
         rec.r0[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         rec.r1[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         rec.r2[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         return;
     }
+    float4 r0, r1, r2;
+    view_records<DEG>(v, mx3, my3, mz3, &s_sh[warp][lane][0], rgb_in + 3 * (DEG >= 0 ? 0 : i), op, L, cam, mode,
+                      r0, r1, r2);
+    rec.r0[i] = r0;
+    rec.r1[i] = r1;
+    rec.r2[i] = r2;
+}
 
-    float col[3];
+// Several views of one Gaussian set in one launch (a batch of cameras, e.g.
+// stereo pairs): each thread reads its Gaussian once -- mean, scales,
+// quaternion, opacity and the SH coefficients (staged through shared memory
+// as in k_project) -- computes the view-independent 3D covariance and opacity
+// once, then runs the per-view projection of k_project for every view (same
+// expressions, so a view here equals a single-view k_project bit for bit).
+// Per view v it writes the records, tile rect, super-tile count and depth key
+// at offset v * n of the outputs, and the view's pair totals into slot set v.
+template <int DEG>
+__global__ void __launch_bounds__(kProjThreads) k_project_views(
+    int n, const float* __restrict__ means, const float* __restrict__ log_scales,
+    const float* __restrict__ quats, const float* __restrict__ op_logits, const float* __restrict__ sh,
+    const float* __restrict__ rgb_in, const ViewDesc* __restrict__ views, int V, int mode, ViewOutputs out)
+{
+    constexpr int KF = DEG >= 0 ? (DEG + 1) * (DEG + 1) * 3 : 1;
+    constexpr int PITCH = KF | 1;
+    __shared__ float s_sh[kProjThreads / 32][32][PITCH];
+    __shared__ unsigned long long s_tot[2][kProjThreads / 32];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (DEG >= 0) {
-        float dx = mx3 - cam.campos[0], dy = my3 - cam.campos[1], dz = mz3 - cam.campos[2];
-        const float dn = rsqrtf(dx * dx + dy * dy + dz * dz);
-        dx *= dn; dy *= dn; dz *= dn;
-        sh_colour(&s_sh[warp][lane][0], DEG, dx, dy, dz, col);
-    } else {
-        col[0] = rgb_in[3 * i];
-        col[1] = rgb_in[3 * i + 1];
-        col[2] = rgb_in[3 * i + 2];
+        const int wbase = blockIdx.x * blockDim.x + warp * 32;
+        const int cnt = min(32, n - wbase);
+        if (cnt > 0) {
+            const float* src = sh + (size_t)wbase * KF;
+            const int tot = cnt * KF;
+            for (int q = lane; q < tot; q += 32) {
+                const int gi = q / KF;
+                s_sh[warp][gi][q - gi * KF] = src[q];
+            }
+        }
+        __syncwarp();
     }
-    // The blend evaluates the exponent in base 2: g2 = g log2(e) with
-    // g = -1/2 (a dx^2 + 2 b dx dy + c dy^2).  Reject threshold: g < ln(1/(255 sigma))
-    // - 1e-4 guarantees sigma e^g < 1/255 in FP32, so the blend may skip the
-    // exponential there.
-    constexpr float kLog2e = 1.4426950408889634f;
-    const float thr = (mode == GS_MODE_EXACT) ? -INFINITY : (-L - 1e-4f) * kLog2e;
-    rec.r0[i] = make_float4(m2x, m2y, -ca, -cc);
-    rec.r1[i] = make_float4(-0.5f * kLog2e * ca, -kLog2e * cb, -0.5f * kLog2e * cc, thr);
-    rec.r2[i] = make_float4(col[0], col[1], col[2], op);
+    const bool inrange = i < n;
+    const int ii = inrange ? i : n - 1;
+    const float mx3 = means[3 * ii], my3 = means[3 * ii + 1], mz3 = means[3 * ii + 2];
+    float S[6];
+    bool qok;
+    cov3d(quats, log_scales, ii, S, qok);
+    const float op = 1.f / (1.f + expf(-op_logits[ii]));
+    const float L = logf(255.f * op);
+    for (int vi = 0; vi < V; ++vi) {
+        const ViewDesc d = views[vi];
+        const ViewProj v = project_view(mx3, my3, mz3, S, qok && inrange, L, d.cam, d.W, d.H, d.tiles_x, d.tiles_y,
+                                        mode);
+        unsigned long long wsum = v.nsup, wt = v.ntiles;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+            wt += __shfl_xor_sync(0xffffffffu, wt, o);
+        }
+        if (lane == 0) {
+            s_tot[0][warp] = wsum;
+            s_tot[1][warp] = wt;
+        }
+        __syncthreads();
+        if (threadIdx.x < 2) {
+            unsigned long long b = 0;
+#pragma unroll
+            for (int w = 0; w < kProjThreads / 32; ++w) b += s_tot[threadIdx.x][w];
+            if (b)
+                atomicAdd(&out.totals[(size_t)vi * 2 * kTotalSlots + 2 * (blockIdx.x % kTotalSlots) + threadIdx.x], b);
+        }
+        __syncthreads();   // s_tot is reused by the next view
+        if (!inrange) continue;
+        const size_t o = (size_t)vi * n + i;
+        const int4 rc = v.rc;
+        out.supers[o] = v.nsup;
+        out.rect[o] = v.ntiles ? make_ushort4((unsigned short)rc.x, (unsigned short)rc.y, (unsigned short)rc.z,
+                                              (unsigned short)rc.w)
+                               : make_ushort4(1, 1, 0, 0);
+        out.depth_key[o] = v.ntiles > 0 ? __float_as_uint(v.pz) : 0xFFFFFFFFu;
+        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
+        if (v.vis)
+            view_records<DEG>(v, mx3, my3, mz3, &s_sh[warp][lane][0], rgb_in + 3 * (DEG >= 0 ? 0 : i), op, L,
+                              d.cam, mode, r0, r1, r2);
+        out.rec.r0[o] = r0;
+        out.rec.r1[o] = r1;
+        out.rec.r2[o] = r2;
+    }
 }
 
 // d Y_k / d(x, y, z) of the Cartesian SH polynomials above (deg <= 3); the
@@ -584,6 +714,40 @@ cudaError_t launch_project(cudaStream_t s, const gs_gaussians& g, const CameraPa
     default: GS_PROJECT(-1); break;
     }
 #undef GS_PROJECT
+    note_launch();
+    return cudaGetLastError();
+}
+
+__global__ void k_set_views(ViewBatch b, int V, ViewDesc* __restrict__ dst)
+{
+    if ((int)threadIdx.x < V) dst[threadIdx.x] = b.v[threadIdx.x];
+}
+
+cudaError_t launch_set_views(cudaStream_t s, const ViewBatch& b, int V, ViewDesc* dst)
+{
+    if (V < 1 || V > kMaxViews) return cudaErrorInvalidValue;
+    k_set_views<<<1, kMaxViews, 0, s>>>(b, V, dst); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project_views(cudaStream_t s, const gs_gaussians& g, const ViewDesc* views, int V, int mode,
+                                 const ViewOutputs& out)
+{
+    const int n = (int)g.n;
+    if (n == 0 || V == 0) return cudaSuccess;
+    const int blocks = (n + kProjThreads - 1) / kProjThreads;
+    const int deg = g.sh ? g.sh_degree : -1;
+#define GS_PROJECT_VIEWS(D)                                                                                        \
+    k_project_views<D><<<blocks, kProjThreads, 0, s>>>(n, g.means, g.log_scales, g.quats, g.opacity_logits, g.sh, \
+                                                       g.rgb, views, V, mode, out)
+    switch (deg) {
+    case 0: GS_PROJECT_VIEWS(0); break;
+    case 1: GS_PROJECT_VIEWS(1); break;
+    case 2: GS_PROJECT_VIEWS(2); break;
+    case 3: GS_PROJECT_VIEWS(3); break;
+    default: GS_PROJECT_VIEWS(-1); break;
+    }
+#undef GS_PROJECT_VIEWS
     note_launch();
     return cudaGetLastError();
 }
