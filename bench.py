@@ -478,6 +478,9 @@ def run_gs(args):
         psnr_15 = psnr(out15.cpu().numpy(), d_np)
         gctx_15.close()
 
+        # batched multi-view rendering (stereo pairs), batched vs one view at a time
+        views = views_leg(torch, gs, scenes, stream) if world == 1 else None
+
         # end to end through the public API: pinned host scene in, image out
         host = gs.HostScene(scene)
         out_host = torch.empty(3, OUT_H, OUT_W, pin_memory=True)
@@ -568,6 +571,7 @@ def run_gs(args):
         "speedup_vs_direct": (OUT_W * OUT_H / 1e3 / ms_step) / (OUT_W * OUT_H / 1e3 / ms_direct),
         "psnr_db": {"2x_960x540": psnr2, "4x_480x270": psnr4, "vs": "direct 1920x1080 render, clipped to [0,1]"},
         "path_4x": {"mpix_s": OUT_W * OUT_H / 1e3 / ms_4x, "ms": ms_4x},
+        "multi_view": views,
         "comparisons": {
             "bicubic_2x": {"what": "plain 960x540 render + cubic convolution (a = -0.75) to 1920x1080",
                            "mpix_s": OUT_W * OUT_H / 1e3 / ms_bic, "ms": ms_bic, "psnr_db": psnr_bic},
@@ -626,6 +630,92 @@ def _traffic_from_profiles():
     if h.hexdigest()[:16] != d.get("sources_sha256_16"):
         return None
     return int(d["dram_bytes_per_launch"])
+
+
+def stereo_views(seed=0, pairs=8, lo=(512, 512), hi=(1104, 1032), ipd=0.064):
+    """16 views = 8 stereo pairs; per-eye sizes log-uniform between lo and hi
+    (rounded to even), eyes 64 mm apart around the origin, looking down +z."""
+    import scenes
+    rng = np.random.default_rng(seed)
+    cams, eyes = [], []
+    for k in range(pairs):
+        W = int(round(np.exp(rng.uniform(np.log(lo[0]), np.log(hi[0]))) / 2)) * 2
+        H = int(round(np.exp(rng.uniform(np.log(lo[1]), np.log(hi[1]))) / 2)) * 2
+        yaw = rng.uniform(-0.05, 0.05)
+        for side in (-0.5, 0.5):
+            eye = (side * ipd, 0.0, 0.0)
+            target = (side * ipd + 6.0 * np.sin(yaw), 0.0, 6.0 * np.cos(yaw))
+            eyes.append((W, H))
+            cams.append((eye, target))
+    return cams, eyes
+
+
+def views_leg(torch, gs, scenes, stream, n_list=(300_000, 800_000, 2_000_000), reps=20):
+    """Batched multi-view rendering (16 stereo views, each eye rendered at half
+    size with derivatives and upscaled 2x) against the same views one at a
+    time; both recorded as CUDA graphs.  Output megapixels per second."""
+    camdefs, eyes = stereo_views()
+    V = len(eyes)
+    lows = [(W // 2, H // 2) for W, H in eyes]
+    cams = [scenes.pinhole_camera(w, h, viewmat=scenes.look_at_viewmat(e, t)) for (w, h), (e, t) in zip(lows, camdefs)]
+    out_mpix = sum(W * H for W, H in eyes) / 1e6
+    res = {"views": V, "eye_sizes": eyes, "scenes": {}}
+    for n in n_list:
+        scene = scenes.mixture_scene(n, seed=1)
+        dev = gs.DeviceScene(scene)
+        Wm, Hm = max(w for w, _ in lows), max(h for _, h in lows)
+        # super-tile pairs of the largest view bound the reservation (with headroom)
+        ps = 0
+        with gs.Context(stream=stream) as probe:
+            with torch.cuda.stream(stream):
+                for (w, h), cam in zip(lows, cams):
+                    probe.project(dev, cam, w, h)
+                    ps = max(ps, probe.super_pair_count())
+        cap = ps + ps // 4 + 4096
+        timings = {}
+        for mode in ("batched", "per_view"):
+            ctx = gs.Context(stream=stream, no_host_wait=True)
+            if mode == "batched":
+                ctx.reserve_views(n, V, Wm, Hm, cap)
+            else:
+                ctx.reserve(n, Wm, Hm, cap)
+            outs = [[torch.empty(3, h, w, device="cuda"), torch.empty(3, 3, h, w, device="cuda"),
+                     torch.empty(3, 2 * h, 2 * w, device="cuda")] for w, h in lows]
+
+            def body():
+                if mode == "batched":
+                    ctx.render_views(dev, cams, lows, [2] * V, outs=outs)
+                else:
+                    for (w, h), cam, o in zip(lows, cams, outs):
+                        ctx.render_with_grads(dev, cam, w, h, out_C=o[0], out_grads=o[1])
+                        ctx.upscale(o[0], o[1], 2, out=o[2])
+
+            with torch.cuda.stream(stream):
+                body()
+                torch.cuda.synchronize()
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=stream):
+                    body()
+                for _ in range(3):
+                    g.replay()
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for _ in range(reps):
+                    g.replay()
+                b.record(stream)
+                torch.cuda.synchronize()
+            ctx.synchronize()
+            timings[mode] = a.elapsed_time(b) / reps
+            del g
+            ctx.close()
+        res["scenes"][str(n)] = {"batched_ms": timings["batched"], "per_view_ms": timings["per_view"],
+                                 "batched_mpix_s": out_mpix / timings["batched"] * 1e3,
+                                 "per_view_mpix_s": out_mpix / timings["per_view"] * 1e3,
+                                 "speedup": timings["per_view"] / timings["batched"]}
+        del dev
+        torch.cuda.empty_cache()
+    return res
 
 
 def run_profile(args):

@@ -231,7 +231,11 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
         zl.p[zl.count] = as<uint32_t>(c->super_counts);
         zl.words[zl.count++] = (uint32_t)(kCountCopies * Ts);
     }
-    if (no_wait && Ts > 1) {   // the pair sort's look-back states and tile counters
+    // the pair sort's look-back states and tile counters -- only when the depth
+    // sort is the persistent kernel: the one-sweep depth sort uses the same
+    // state buffer, so the pair sort then clears it itself
+    const bool pairs_prezeroed = no_wait && Ts > 1 && persistent;
+    if (pairs_prezeroed) {
         zl.p[zl.count] = as<uint32_t>(c->sort_status);
         zl.words[zl.count++] = (uint32_t)radix_status_words((uint32_t)c->res_pairs, 32, 32 + sbits);
         zl.p[zl.count] = as<uint32_t>(c->sort_counter);
@@ -295,7 +299,7 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
         if (Ts > 1 && cap > 1)
             GS_CUDA(c, radix_sort_u64_keys(c->stream, pairs, cap, 32, 32 + sbits, as<uint32_t>(c->sort_hist),
                                            as<uint32_t>(c->sort_status), as<uint32_t>(c->sort_counter),
-                                           as<int>(c->errword), &psorted, true, &chk->count, true));
+                                           as<int>(c->errword), &psorted, true, &chk->count, pairs_prezeroed));
         c->sorted_pairs_buf = psorted;
         c->n = n;
         c->W = W;

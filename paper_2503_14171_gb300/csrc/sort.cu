@@ -237,8 +237,12 @@ __global__ void __launch_bounds__(kThreads) k_onesweep(const K* __restrict__ key
         if (p < count) {
             const K k = S.keys[p];
             const uint32_t g = S.global_base[digit_of(k, shift)] + p;
-            keys_out[g] = k;
-            if (HAS_VAL) vals_out[g] = S.vals[p];
+            if (g < n) {
+                keys_out[g] = k;
+                if (HAS_VAL) vals_out[g] = S.vals[p];
+            } else {   // inconsistent look-back state: report instead of writing out of bounds
+                atomicExch(err, kDevCheck);
+            }
         }
     }
 }

@@ -154,3 +154,25 @@ def test_backward_after_no_wait_frame(gs):
         ctx.synchronize()
     for k in want:
         np.testing.assert_allclose(got[k], want[k], rtol=1e-4, atol=1e-5 * (np.abs(want[k]).max() + 1e-12))
+
+
+def test_no_wait_beyond_persistent_sort(gs):
+    """More Gaussians than the persistent depth sort holds: the one-sweep depth
+    sort shares its look-back state buffer with the pair sort, which must then
+    start from cleared states (regression: a no-wait frame here once sorted
+    the pairs against stale states)."""
+    import torch
+    n = 152 * 10240 + 4096
+    W, H = 96, 64
+    scene = gs.DeviceScene(scenes.random_scene(n=n, seed=35, log_scale_mean=-4.5))
+    cam = scenes.pinhole_camera(W, H)
+    with gs.Context() as ref:
+        want = _render(ref, gs, scene, cam, W, H)
+        P = ref.super_pair_count()
+    with gs.Context(no_host_wait=True) as ctx:
+        ctx.reserve(n, W, H, P + P // 4 + 64)
+        for _ in range(2):
+            got = _render(ctx, gs, scene, cam, W, H)   # synchronize: no device error
+            assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+    del scene
+    torch.cuda.empty_cache()
