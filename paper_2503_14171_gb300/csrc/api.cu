@@ -387,6 +387,8 @@ BlendArgs blend_args(gs_ctx* c, float* out_C, float* out_grads)
     a.out_G = out_grads;
     a.state = as<float4>(c->state);
     a.count = as<int>(c->count);
+    a.order = nullptr;
+    a.work = nullptr;
     return a;
 }
 
@@ -397,7 +399,18 @@ gs_status do_blend(gs_ctx* c, float* out_C, float* out_grads)
     const size_t npix = (size_t)c->W * c->H;
     gs_status st;
     if ((st = ensure(c, c->state, sizeof(float4) * npix)) || (st = ensure(c, c->count, sizeof(int) * npix))) return st;
-    const BlendArgs a = blend_args(c, out_C, out_grads);
+    // tiles heaviest first, by the durations the previous frame's blocks recorded
+    const uint32_t T = (uint32_t)(c->tiles_x * c->tiles_y);
+    if ((st = ensure(c, c->tile_work, sizeof(uint32_t) * T)) || (st = ensure(c, c->tile_order, sizeof(uint32_t) * T)))
+        return st;
+    if (c->work_tiles != (int64_t)T) {   // a new tile layout: no history yet
+        GS_CUDA(c, cudaMemsetAsync(c->tile_work.p, 0, sizeof(uint32_t) * T, c->stream));
+        c->work_tiles = T;
+    }
+    GS_CUDA(c, launch_tile_order(c->stream, as<uint32_t>(c->tile_work), T, as<uint32_t>(c->tile_order)));
+    BlendArgs a = blend_args(c, out_C, out_grads);
+    a.order = as<uint32_t>(c->tile_order);
+    a.work = as<uint32_t>(c->tile_work);
     GS_CUDA(c, launch_blend(c->stream, out_grads != nullptr, c->opt.mode, a));
     c->have_state = true;
     c->state_grads = out_grads != nullptr;
@@ -484,7 +497,7 @@ gs_status gs_destroy(gs_ctx* c)
                       &c->pairs[1],
                       &c->sort_hist, &c->sort_status,
                       &c->sort_counter, &c->sranges, &c->tile_count, &c->tile_start, &c->state, &c->count,
-                      &c->errword, &c->grad2d, &c->up_planes, &c->pair_check,
+                      &c->errword, &c->grad2d, &c->up_planes, &c->pair_check, &c->tile_work, &c->tile_order,
                       &c->vrec0, &c->vrec1, &c->vrec2, &c->vrect, &c->vsupers, &c->vkey, &c->vtotals,
                       &c->views_dev};
     for (DevBuf* b : bufs) release(*b);
@@ -781,6 +794,7 @@ gs_status reserve_impl(gs_ctx* c, int64_t n, int32_t V, int32_t W, int32_t H, in
         (st = ensure(c, c->pairs[1], sizeof(uint64_t) * (size_t)super_pairs)) ||
         (st = ensure(c, c->state, sizeof(float4) * pix)) || (st = ensure(c, c->count, sizeof(int) * pix)) ||
         (st = ensure(c, c->tile_count, sizeof(uint32_t) * T)) || (st = ensure(c, c->tile_start, sizeof(uint32_t) * T)) ||
+        (st = ensure(c, c->tile_work, sizeof(uint32_t) * T)) || (st = ensure(c, c->tile_order, sizeof(uint32_t) * T)) ||
         (st = ensure(c, c->grad2d, sizeof(float) * 9 * un)) || (st = ensure(c, c->up_planes, sizeof(float) * 12 * pix)) ||
         (st = ensure(c, c->pair_check, sizeof(PairCheckOut))))
         return st;
@@ -941,6 +955,8 @@ gs_status gs_render_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_
         a.out_G = out_grads[v];
         a.state = nullptr;
         a.count = nullptr;
+        a.order = nullptr;
+        a.work = nullptr;
         GS_CUDA(c, launch_blend(s, true, c->opt.mode, a));
         if (out_up && out_up[v])
             GS_CUDA(c, launch_upscale(s, out_C[v], out_grads[v], d.W, d.H, factors[v], out_up[v]));

@@ -133,7 +133,8 @@ __global__ void __launch_bounds__(kThreads) k_blend(BlendArgs a, unsigned long l
     __shared__ float4 s_r2[kStage];
     __shared__ int s_wcnt[kWarps];
 
-    const int tile = blockIdx.x;
+    const int tile = a.order ? (int)a.order[blockIdx.x] : (int)blockIdx.x;
+    const long long t_start = clock64();
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
@@ -217,7 +218,37 @@ __global__ void __launch_bounds__(kThreads) k_blend(BlendArgs a, unsigned long l
         }
         return;
     }
+    if (a.work && threadIdx.x == 0) a.work[tile] = (uint32_t)min((clock64() - t_start) >> 4, 0xFFFFFFFFll);
     if (x < a.W && y < a.H) store<GRADS>(a, p, x, y);
+}
+
+// One block: histogram of the tiles' recorded durations in logarithmic buckets,
+// bucket starts from the heaviest bucket down, then every tile placed at its
+// bucket's next slot (the order inside a bucket does not matter).
+constexpr int kOrderBuckets = 128;
+
+__global__ void __launch_bounds__(1024) k_tile_order(const uint32_t* __restrict__ work, uint32_t T,
+                                                      uint32_t* __restrict__ order)
+{
+    __shared__ uint32_t s_cnt[kOrderBuckets];
+    for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) s_cnt[b] = 0;
+    __syncthreads();
+    auto bucket = [](uint32_t w) {   // 4 per octave, heaviest = 0
+        const int b = w ? (int)(4.f * log2f((float)w)) : 0;
+        return kOrderBuckets - 1 - min(b, kOrderBuckets - 1);
+    };
+    for (uint32_t t = threadIdx.x; t < T; t += blockDim.x) atomicAdd(&s_cnt[bucket(work[t])], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int b = 0; b < kOrderBuckets; ++b) {
+            const uint32_t c = s_cnt[b];
+            s_cnt[b] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < T; t += blockDim.x) order[atomicAdd(&s_cnt[bucket(work[t])], 1u)] = t;
 }
 
 template <bool GRADS, int MODE>
@@ -228,6 +259,13 @@ cudaError_t launch_t(cudaStream_t s, const BlendArgs& a)
 }
 
 }  // namespace
+
+cudaError_t launch_tile_order(cudaStream_t s, const uint32_t* work, uint32_t T, uint32_t* order)
+{
+    if (T == 0) return cudaSuccess;
+    k_tile_order<<<1, 1024, 0, s>>>(work, T, order); note_launch();
+    return cudaGetLastError();
+}
 
 cudaError_t launch_blend_stats(cudaStream_t s, int mode, const BlendArgs& a, unsigned long long* stats)
 {

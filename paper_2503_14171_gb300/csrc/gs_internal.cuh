@@ -65,7 +65,15 @@ struct BlendArgs {
     float* out_G;
     float4* state;
     int* count;
+    // tile scheduling (optional): blocks take tiles in the order order[] (the
+    // heaviest of the previous frame first) and record their duration in work[]
+    const uint32_t* order;
+    uint32_t* work;
 };
+
+// Order tiles by the recorded work of the previous frame, heaviest first
+// (coarse: 4 buckets per octave of the recorded duration).
+cudaError_t launch_tile_order(cudaStream_t s, const uint32_t* work, uint32_t T, uint32_t* order);
 
 // Adjoint of the blend: the forward's binning (super-tile lists filtered per
 // tile by the rects), its final per-pixel state and count, the upstream
@@ -126,6 +134,8 @@ struct gs_ctx {
     // per tile / pixel
     gs::DevBuf sranges;                 // uint2[super-tiles]
     gs::DevBuf tile_count, tile_start;  // uint32[tiles] (per-tile list materialisation)
+    gs::DevBuf tile_work, tile_order;   // uint32[tiles]: last frame's block durations, this frame's order
+    int64_t work_tiles = -1;            // tile count the recorded durations belong to
     gs::DevBuf state;                   // float4[W*H]
     gs::DevBuf count;                   // int32[W*H]
     gs::DevBuf errword;                 // int32

@@ -233,6 +233,8 @@ extern "C" gs_status gs_render_with_grads_noalloc(const gs_gaussians* g, const g
     a.out_G = out_grads;
     a.state = nullptr;
     a.count = nullptr;
+    a.order = nullptr;
+    a.work = nullptr;
     NA_CUDA(launch_blend(s, true, o.mode, a));
 
     // report a bounded device wait that expired (outputs are then undefined)
