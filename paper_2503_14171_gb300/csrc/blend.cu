@@ -2,7 +2,8 @@
 // derivatives of the pixel colour (Sec. 4 blend equation; Sec. 5 "3DGS Image
 // Gradients"; supplement "Forward pass").
 //
-// One 256-thread block per 16x16 tile, one pixel per thread.  Binning is done
+// One 256-thread block per 16x16 tile, one pixel per thread (each warp an 8x4
+// block of pixels).  Binning is done
 // per 64x64 super-tile (4x4 tiles): the block walks its super-tile's
 // depth-ordered list 256 candidates at a time,
 // keeps the Gaussians whose tile rect covers this tile (an order-preserving
@@ -137,7 +138,10 @@ __global__ void __launch_bounds__(kThreads) k_blend(BlendArgs a, unsigned long l
     const long long t_start = clock64();
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
+    // each warp covers an 8 x 4 block of the tile (two blocks across, four
+    // down): a compact block makes the lanes of a warp agree more often on
+    // whether a Gaussian reaches them
+    const int lx = ((warp & 1) << 3) | (lane & 7), ly = ((warp >> 1) << 2) | (lane >> 3);
     const int x = tx * kTile + lx, y = ty * kTile + ly;
     const float px = (float)x, py = (float)y;
     const uint32_t lanemask_lt = (1u << lane) - 1u;
@@ -222,35 +226,6 @@ __global__ void __launch_bounds__(kThreads) k_blend(BlendArgs a, unsigned long l
     if (x < a.W && y < a.H) store<GRADS>(a, p, x, y);
 }
 
-// One block: histogram of the tiles' recorded durations in logarithmic buckets,
-// bucket starts from the heaviest bucket down, then every tile placed at its
-// bucket's next slot (the order inside a bucket does not matter).
-constexpr int kOrderBuckets = 128;
-
-__global__ void __launch_bounds__(1024) k_tile_order(const uint32_t* __restrict__ work, uint32_t T,
-                                                      uint32_t* __restrict__ order)
-{
-    __shared__ uint32_t s_cnt[kOrderBuckets];
-    for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) s_cnt[b] = 0;
-    __syncthreads();
-    auto bucket = [](uint32_t w) {   // 4 per octave, heaviest = 0
-        const int b = w ? (int)(4.f * log2f((float)w)) : 0;
-        return kOrderBuckets - 1 - min(b, kOrderBuckets - 1);
-    };
-    for (uint32_t t = threadIdx.x; t < T; t += blockDim.x) atomicAdd(&s_cnt[bucket(work[t])], 1u);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t run = 0;
-        for (int b = 0; b < kOrderBuckets; ++b) {
-            const uint32_t c = s_cnt[b];
-            s_cnt[b] = run;
-            run += c;
-        }
-    }
-    __syncthreads();
-    for (uint32_t t = threadIdx.x; t < T; t += blockDim.x) order[atomicAdd(&s_cnt[bucket(work[t])], 1u)] = t;
-}
-
 template <bool GRADS, int MODE>
 cudaError_t launch_t(cudaStream_t s, const BlendArgs& a)
 {
@@ -259,13 +234,6 @@ cudaError_t launch_t(cudaStream_t s, const BlendArgs& a)
 }
 
 }  // namespace
-
-cudaError_t launch_tile_order(cudaStream_t s, const uint32_t* work, uint32_t T, uint32_t* order)
-{
-    if (T == 0) return cudaSuccess;
-    k_tile_order<<<1, 1024, 0, s>>>(work, T, order); note_launch();
-    return cudaGetLastError();
-}
 
 cudaError_t launch_blend_stats(cudaStream_t s, int mode, const BlendArgs& a, unsigned long long* stats)
 {
