@@ -665,6 +665,9 @@ gs_status do_render_backward(gs_ctx* c, const float* dC, const float* dG, float*
     a.dG = dG;
     a.grad2d = grad2d;
     a.err = as<int>(c->errword);
+    // the forward blend's tile order of this frame (heaviest first)
+    a.order = c->work_tiles == (int64_t)c->tiles_x * c->tiles_y && c->tile_order.p ? as<uint32_t>(c->tile_order)
+                                                                                   : nullptr;
     GS_CUDA(c, launch_blend_backward(c->stream, c->opt.mode, a));
     return GS_OK;
 }

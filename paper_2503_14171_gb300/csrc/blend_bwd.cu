@@ -166,11 +166,13 @@ __global__ void __launch_bounds__(kThreads) k_blend_bwd(BlendBwdArgs a)
     __shared__ int s_wcnt[kWarps];
     __shared__ int s_max[kWarps];
 
-    const int tile = blockIdx.x;
+    const int tile = a.order ? (int)a.order[blockIdx.x] : (int)blockIdx.x;
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lanemask_lt = (1u << lane) - 1u;
-    const int x = tx * kTile + (threadIdx.x & (kTile - 1)), y = ty * kTile + threadIdx.x / kTile;
+    // each warp an 8 x 4 block of pixels, as in the forward blend
+    const int x = tx * kTile + (((warp & 1) << 3) | (lane & 7));
+    const int y = ty * kTile + (((warp >> 1) << 2) | (lane >> 3));
     const bool inside = x < a.W && y < a.H;
     const size_t plane = (size_t)a.W * a.H;
     const size_t pix = inside ? (size_t)y * a.W + x : 0;

@@ -93,6 +93,7 @@ struct BlendBwdArgs {
     const float* dG;               // [3 (x, y, xy)][3][H][W]
     float* grad2d;                 // [n][9]
     int* err;
+    const uint32_t* order;         // optional: tiles in this order (the forward's, heaviest first)
 };
 
 }  // namespace gs
