@@ -204,16 +204,21 @@ __global__ void __launch_bounds__(kBwdX * kBwdY) k_upscale_bwd(const float* __re
     for (int ch = 0; ch < 3; ++ch)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[ch][q] = 0.f;
-    for (int Y = ya; Y < yb; ++Y) {
+    // numerators of t = ((2X + 1) W - W2 - 2 W2 c) / (2 W2), stepped by 2W per
+    // output pixel (|num| <= 3 W2 inside the footprint: 32-bit)
+    const int nx0 = (int)((2ll * xa + 1) * W - W2 - 2ll * W2 * (i - 1));
+    int ny = (int)((2ll * ya + 1) * H - H2 - 2ll * H2 * (j - 1));
+    for (int Y = ya; Y < yb; ++Y, ny += 2 * H) {
         const bool right_y = Y < ym;            // cell j - 1: (., j) is its lower corner
-        const int cj = right_y ? j - 1 : j;
-        const float4 hy = hermite((float)((2ll * Y + 1) * H - H2 - 2ll * H2 * cj) * inv_y);
+        if (Y == ym) ny -= 2 * H2;              // now in cell j
+        const float4 hy = hermite((float)ny * inv_y);
         const float wyH = right_y ? hy.y : hy.x, wyG = right_y ? hy.w : hy.z;
         const float* row = dout + (size_t)Y * W2;
-        for (int X = xa; X < xb; ++X) {
+        int nx = nx0;
+        for (int X = xa; X < xb; ++X, nx += 2 * W) {
             const bool right_x = X < xm;
-            const int ci = right_x ? i - 1 : i;
-            const float4 hx = hermite((float)((2ll * X + 1) * W - W2 - 2ll * W2 * ci) * inv_x);
+            if (X == xm) nx -= 2 * W2;
+            const float4 hx = hermite((float)nx * inv_x);
             const float wxH = right_x ? hx.y : hx.x, wxG = right_x ? hx.w : hx.z;
             const float wHH = wxH * wyH, wGH = wxG * wyH, wHG = wxH * wyG, wGG = wxG * wyG;
 #pragma unroll
