@@ -178,6 +178,7 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
     const int64_t T = (int64_t)tiles_x * tiles_y;
     const int64_t Ts = (int64_t)stiles_x * stiles_y;
     if (T > 0x7FFFFFFF) return fail(c, GS_ERR_INVALID_ARG, "too many tiles");
+    if (Ts > 65536) return fail(c, GS_ERR_INVALID_ARG, "more than 65536 super-tiles (image over 16384 x 16384)");
     const uint32_t n = (uint32_t)g->n;
     const bool no_wait = (c->opt.flags & GS_FLAG_NO_HOST_WAIT) != 0;
     if (no_wait) {

@@ -6,7 +6,7 @@
 // block of pixels).  Binning is done
 // per 64x64 super-tile (4x4 tiles): the block walks its super-tile's
 // depth-ordered list 256 candidates at a time,
-// keeps the Gaussians whose tile rect covers this tile (an order-preserving
+// keeps the Gaussians whose pair marks this tile (an order-preserving
 // block compaction, so the kept sequence is exactly the tile's own
 // front-to-back list) and stages their records in shared memory until at
 // least 256 are staged (or the list ends), then blends them.  The next
@@ -156,12 +156,10 @@ __global__ void __launch_bounds__(kThreads) k_blend(BlendArgs a, unsigned long l
     int list_base = 0;   // position of the batch's first record in the tile's list
 
     // candidate of the first round
+    const int tbit = (ty & (kSuper - 1)) * kSuper + (tx & (kSuper - 1));   // this tile in the pair masks
     uint32_t cid = 0xFFFFFFFFu;
-    ushort4 crect = make_ushort4(1, 1, 0, 0);
-    if ((int)threadIdx.x < total) {
-        cid = a.pair_words[2 * (size_t)(sr.x + threadIdx.x)];
-        if (cid < a.n) crect = a.rect[cid];
-    }
+    bool chit = false;
+    if ((int)threadIdx.x < total) chit = pair_hit(a.pair_words, sr.x + threadIdx.x, a.n, tbit, cid);
 
     int c0 = 0;
     while (c0 < total) {
@@ -169,7 +167,7 @@ __global__ void __launch_bounds__(kThreads) k_blend(BlendArgs a, unsigned long l
         // stage rounds of kCand candidates until >= kCand records are staged
         int staged = 0;
         while (c0 < total && staged < kCand) {
-            const bool hit = cid < a.n && covers(crect, tx, ty);
+            const bool hit = chit;
             const uint32_t ball = __ballot_sync(0xffffffffu, hit);
             if (lane == 0) s_wcnt[warp] = __popc(ball);
             __syncthreads();
@@ -191,10 +189,8 @@ __global__ void __launch_bounds__(kThreads) k_blend(BlendArgs a, unsigned long l
             // fetch the next round's candidate
             const int cn = c0 + (int)threadIdx.x;
             cid = 0xFFFFFFFFu;
-            if (cn < total) {
-                cid = a.pair_words[2 * (size_t)(sr.x + cn)];
-                if (cid < a.n) crect = a.rect[cid];
-            }
+            chit = false;
+            if (cn < total) chit = pair_hit(a.pair_words, sr.x + cn, a.n, tbit, cid);
             __syncthreads();   // s_wcnt is reused by the next round; staged records are visible
         }
         for (int k = 0; k < staged && !p.done; ++k) {

@@ -219,6 +219,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_bwd(BlendBwdArgs a)
     const int S = (ty / kSuper) * a.stiles_x + (tx / kSuper);
     const uint2 sr = a.sranges[S];
     const int total = (int)(sr.y - sr.x);
+    const int tbit = (ty & (kSuper - 1)) * kSuper + (tx & (kSuper - 1));   // this tile in the pair masks
 
     // pass 1: the tile's list position at the start of each round of candidates
     int filt = 0, R = 0;
@@ -231,8 +232,8 @@ __global__ void __launch_bounds__(kThreads) k_blend_bwd(BlendBwdArgs a)
         const int c = c0 + (int)threadIdx.x;
         bool hit = false;
         if (c < total) {
-            const uint32_t id = a.pair_words[2 * (size_t)(sr.x + c)];
-            hit = id < a.n && covers(a.rect[id], tx, ty);
+            uint32_t id;
+            hit = pair_hit(a.pair_words, sr.x + c, a.n, tbit, id);
         }
         const uint32_t ball = __ballot_sync(0xffffffffu, hit);
         if (lane == 0) s_wcnt[warp] = __popc(ball);
@@ -260,8 +261,8 @@ __global__ void __launch_bounds__(kThreads) k_blend_bwd(BlendBwdArgs a)
                 const int c = r * kCand + (int)threadIdx.x;
                 bool hit = false;
                 if (c < total) {
-                    const uint32_t id = a.pair_words[2 * (size_t)(sr.x + c)];
-                    hit = id < a.n && covers(a.rect[id], tx, ty);
+                    uint32_t id;
+                    hit = pair_hit(a.pair_words, sr.x + c, a.n, tbit, id);
                 }
                 const uint32_t ball = __ballot_sync(0xffffffffu, hit);
                 if (lane == 0) s_wcnt[warp] = __popc(ball);
@@ -279,10 +280,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_bwd(BlendBwdArgs a)
             const int c = r * kCand + (int)threadIdx.x;
             uint32_t id = 0xFFFFFFFFu;
             bool hit = false;
-            if (c < total) {
-                id = a.pair_words[2 * (size_t)(sr.x + c)];
-                hit = id < a.n && covers(a.rect[id], tx, ty);
-            }
+            if (c < total) hit = pair_hit(a.pair_words, sr.x + c, a.n, tbit, id);
             const uint32_t ball = __ballot_sync(0xffffffffu, hit);
             if (lane == 0) s_wcnt[warp] = __popc(ball);
             __syncthreads();

@@ -18,6 +18,18 @@ __device__ __forceinline__ bool covers(ushort4 r, int tx, int ty)
     return (int)r.x <= tx && tx <= (int)r.z && (int)r.y <= ty && ty <= (int)r.w;
 }
 
+// A (super-tile, Gaussian) pair is mask << 48 | super-tile << 32 | id, with
+// bit 4 ly + lx of the 16-bit mask set when the Gaussian's tile rect covers
+// tile (lx, ly) of the super-tile's 4 x 4 tiles.  pair_hit reads pair k (one
+// coalesced 8-byte load) and tests the calling tile's bit.
+__device__ __forceinline__ bool pair_hit(const uint32_t* __restrict__ pair_words, size_t k, uint32_t n, int bit,
+                                         uint32_t& id)
+{
+    const uint2 w = reinterpret_cast<const uint2*>(pair_words)[k];
+    id = w.x;
+    return id < n && ((w.y >> (16 + bit)) & 1u);
+}
+
 // Exponent of a (pixel, Gaussian) pair in base 2: r1 = (A2, B2, C2, threshold)
 // with g2 = A2 dx^2 + B2 dx dy + C2 dy^2 = g log2(e).
 __device__ __forceinline__ float exponent2(const float4& r1, float dx, float dy)
