@@ -39,6 +39,33 @@ def borderline_tile_mask(proj) -> np.ndarray:
     return np.repeat(np.repeat(mt, tile, 0), tile, 1)[:H, :W]
 
 
+def borderline_pixel_mask(proj, pix, margin: float = 1e-3) -> np.ndarray:
+    """Sampled pixels [M, 2] of (x, y) that a rect-borderline Gaussian can
+    change: in a tile of its envelope rect outside its core rect, with
+    alpha = opacity e^g there at or above the 1/255 cut-off (less a relative
+    margin).  Where alpha is below the cut-off the Gaussian is skipped whether
+    or not the tile lists it, so the pixel is the same on both sides."""
+    tile = proj["tile"]
+    px, py = pix[:, 0].astype(np.int64), pix[:, 1].astype(np.int64)
+    tx, ty = px // tile, py // tile
+    out = np.zeros(len(px), bool)
+    for i in np.nonzero(proj["borderline"])[0]:
+        e, c = proj["envelope"][i], proj["core"][i]
+        if e[2] < e[0]:
+            continue
+        sel = (tx >= e[0]) & (tx <= e[2]) & (ty >= e[1]) & (ty <= e[3]) & ~out
+        if c[2] >= c[0]:
+            sel &= ~((tx >= c[0]) & (tx <= c[2]) & (ty >= c[1]) & (ty <= c[3]))
+        if not sel.any():
+            continue
+        a, b, cc = proj["conic"][i]
+        dx = px[sel] - proj["mean2d"][i, 0]
+        dy = py[sel] - proj["mean2d"][i, 1]
+        g = -0.5 * (a * dx * dx + 2.0 * b * dx * dy + cc * dy * dy)
+        out[np.nonzero(sel)[0]] = proj["opacity"][i] * np.exp(g) >= (1.0 - margin) / 255.0
+    return out
+
+
 def compare_render(C_gpu, G_gpu, ref, exclude=None, tol_c=TOL_C, tol_g=TOL_G):
     """C_gpu [3,H,W], G_gpu [3,3,H,W] or None; ref: oracle.render(..., variants=True).
     Returns (n_fail, n_checked, n_excluded, worst)."""
