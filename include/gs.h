@@ -236,6 +236,55 @@ gs_status gs_upscale_to(gs_ctx* ctx, const float* C, const float* grads, int32_t
 gs_status gs_upscale_bicubic(gs_ctx* ctx, const float* C, int32_t W, int32_t H, int32_t W2, int32_t H2, float a,
                              float* out);
 
+/* ---- Learned residual on the spline (an extension beside the paper's method:
+ * the paper upscales with the spline alone, Sec. 5, and argues against learned
+ * upscalers, Sec. 2).  A per-output-pixel MLP 50 -> 64 -> 64 -> 3 with ReLU
+ * reads the 48 values the spline reads -- f[12 k + 3 q + c] = quantity q (C,
+ * dC/dx, dC/dy, d2C/dxdy) of channel c at corner k ((i, j), (i+1, j),
+ * (i, j+1), (i+1, j+1)) of the pixel's cell -- and f[48] = t, f[49] = u, the
+ * local coordinates of its sample point, and adds its output to the spline.
+ *
+ * params: GS_MLP_PARAMS FP32 values, device memory, row-major in the order
+ * W1 [64][50], b1 [64], W2 [64][64], b2 [64], W3 [3][64], b3 [3]; the
+ * matrices are used as BF16 (round to nearest even), the biases as FP32, and
+ * every product is accumulated in FP32 (tensor cores for the two hidden
+ * layers).  Training uses the mean squared error over samples and channels,
+ * L = sum (spline + r - target)^2 / (3 M), and Adam. */
+#define GS_MLP_IN 50
+#define GS_MLP_HIDDEN 64
+#define GS_MLP_PARAMS 7619
+#define GS_MLP_ROW 64   /* BF16 values per feature row of gs_mlp_samples (50 used) */
+
+/* Spline plus residual at any output size (the sizes of gs_upscale_to), the
+ * MLP fused into the upscale pass.  params == NULL: the spline alone
+ * (gs_upscale_to).  out [3][H2][W2].  Asynchronous; a bounded device wait that
+ * expires is reported by gs_synchronize (GS_ERR_TIMEOUT). */
+gs_status gs_upscale_mlp(gs_ctx* ctx, const float* C, const float* grads, int32_t W, int32_t H, int32_t W2,
+                         int32_t H2, const float* params, float* out);
+
+/* Training samples of the residual at M output pixels (device int32 [M][2] of
+ * (X, Y) in the W2 x H2 output): features [M][GS_MLP_ROW] as BF16 bit
+ * patterns (slots 50..63 zero), the spline value base [M][3] and, when
+ * target_image [3][H2][W2] and target are given, target [M][3] = the image at
+ * the pixel.  All device memory.  A pixel outside the output is written as
+ * zeros and reported by gs_synchronize (GS_ERR_DEVICE_CHECK). */
+gs_status gs_mlp_samples(gs_ctx* ctx, const float* C, const float* grads, int32_t W, int32_t H, int32_t W2,
+                         int32_t H2, const int32_t* pixels, int64_t M, const float* target_image,
+                         uint16_t* features, float* base, float* target);
+
+/* Loss and gradient over M samples: grads [GS_MLP_PARAMS] = dL/dparams
+ * (overwritten; the gradient of the BF16-rounded matrices, applied to the FP32
+ * values), *loss = L (device float, overwritten; may be NULL).  Asynchronous. */
+gs_status gs_mlp_gradient(gs_ctx* ctx, const float* params, const uint16_t* features, const float* base,
+                          const float* target, int64_t M, float* grads, float* loss);
+
+/* One Adam step (Kingma and Ba, 2015, with bias correction) at step >= 1:
+ * m = beta1 m + (1 - beta1) g, v = beta2 v + (1 - beta2) g^2,
+ * params -= lr (m / (1 - beta1^step)) / (sqrt(v / (1 - beta2^step)) + eps).
+ * All arrays device FP32 [GS_MLP_PARAMS]; m and v start at zero. */
+gs_status gs_mlp_adam(gs_ctx* ctx, float* params, float* m, float* v, const float* grads, int32_t step, float lr,
+                      float beta1, float beta2, float eps);
+
 /* ---- Reverse mode (training with differentiable upscaling; supplement
  * "Backward Pass").  All gradients are of one scalar loss L; upstream arrays
  * hold dL/d(output).  Asynchronous on the context's stream. */

@@ -91,12 +91,21 @@ def features(C, grads, W2: int, H2: int, pixels=None) -> np.ndarray:
     return f
 
 
-def forward(theta, f):
-    """MLP residual r [M, 3] of features f [M, 50], with the intermediates."""
+def forward(theta, f, quantize=None):
+    """MLP residual r [M, 3] of features f [M, 50], with the intermediates.
+
+    ``quantize`` (e.g. ``bf16_round``), when given, is applied where a lower-
+    precision evaluation stores an operand in a narrower type: to the features
+    and to h1 before the second layer.  That rounding is a quantisation decision
+    (the code of the narrow value), taken here on this definition's values."""
     p = unpack(theta)
     f = np.asarray(f, np.float64)
+    if quantize is not None:
+        f = quantize(f)
     z1 = f @ p["W1"].T + p["b1"]
     h1 = np.maximum(z1, 0.0)
+    if quantize is not None:
+        h1 = quantize(h1)
     z2 = h1 @ p["W2"].T + p["b2"]
     h2 = np.maximum(z2, 0.0)
     r = h2 @ p["W3"].T + p["b3"]
@@ -121,18 +130,25 @@ def loss(theta, f, base, target) -> float:
     return float(np.sum(e * e) / e.size)
 
 
-def gradient(theta, f, base, target):
-    """dL/dtheta (flat, the order of ``pack``) by reverse-mode chain rule, and L."""
+def gradient(theta, f, base, target, masks=None, quantize=None):
+    """dL/dtheta (flat, the order of ``pack``) by reverse-mode chain rule, and L.
+
+    The ReLU derivative is 1 where z > 0, else 0.  ``masks`` = (z1 > 0, z2 > 0)
+    as boolean [M, 64] arrays replaces those decisions when given, and
+    ``quantize`` is applied as in ``forward`` and to d2 and d1 before they are
+    multiplied (the points where a lower-precision evaluation narrows them)."""
     p = unpack(theta)
-    f = np.asarray(f, np.float64)
-    r, s = forward(theta, f)
+    q = (lambda a: a) if quantize is None else quantize
+    f = q(np.asarray(f, np.float64))
+    r, s = forward(theta, f, quantize)
+    m1, m2 = (s["z1"] > 0, s["z2"] > 0) if masks is None else masks
     e = np.asarray(base, np.float64) + r - np.asarray(target, np.float64)
     d3 = 2.0 * e / e.size                        # dL/dr            [M, 3]
     g = {"W3": d3.T @ s["h2"], "b3": d3.sum(0)}
-    d2 = (d3 @ p["W3"]) * (s["z2"] > 0)          # dL/dz2           [M, 64]
+    d2 = q((d3 @ p["W3"]) * m2)                  # dL/dz2           [M, 64]
     g["W2"] = d2.T @ s["h1"]
     g["b2"] = d2.sum(0)
-    d1 = (d2 @ p["W2"]) * (s["z1"] > 0)          # dL/dz1           [M, 64]
+    d1 = q((d2 @ p["W2"]) * m1)                  # dL/dz1           [M, 64]
     g["W1"] = d1.T @ f
     g["b1"] = d1.sum(0)
     return pack(g), float(np.sum(e * e) / e.size)

@@ -32,6 +32,10 @@ GS_MODE_3DGS = 0
 GS_MODE_EXACT = 1
 MODES = {"3dgs": GS_MODE_3DGS, "exact": GS_MODE_EXACT}
 GS_FLAG_NO_HOST_WAIT = 1
+GS_MLP_IN = 50
+GS_MLP_HIDDEN = 64
+GS_MLP_PARAMS = 7619
+GS_MLP_ROW = 64
 
 
 class GsGaussians(ct.Structure):
@@ -92,6 +96,11 @@ _SIGS = {
     "gs_backward": ([_P, _P, ct.c_int32, ct.POINTER(GsGaussianGrads)], ct.c_int),
     "gs_render_with_grads_noalloc": ([ct.POINTER(GsGaussians), ct.POINTER(GsCamera), ct.c_int32, ct.c_int32,
                                       ct.POINTER(GsOptions), _P, _P, _P], ct.c_int),
+    "gs_upscale_mlp": ([_P, _P, _P, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32, _P, _P], ct.c_int),
+    "gs_mlp_samples": ([_P, _P, _P, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32, _P, ct.c_int64, _P, _P, _P, _P],
+                       ct.c_int),
+    "gs_mlp_gradient": ([_P, _P, _P, _P, _P, ct.c_int64, _P, _P], ct.c_int),
+    "gs_mlp_adam": ([_P, _P, _P, _P, _P, ct.c_int32, ct.c_float, ct.c_float, ct.c_float, ct.c_float], ct.c_int),
 }
 
 
@@ -395,6 +404,53 @@ class Context:
         _chk(lib.gs_upscale_bicubic(self.h, C.data_ptr(), W, H, W2, H2, float(a), o.data_ptr()), self.h,
              "gs_upscale_bicubic")
         return o
+
+    def upscale_mlp(self, C, grads, W2: int, H2: int, params=None, out=None):
+        """Spline plus the learned residual (params: FP32 [GS_MLP_PARAMS] on the
+        device, or None for the spline alone) at any size W2 x H2."""
+        H, W = int(C.shape[-2]), int(C.shape[-1])
+        assert C.is_contiguous() and grads.is_contiguous()
+        if params is not None:
+            assert params.is_contiguous() and params.numel() == GS_MLP_PARAMS
+        o = out if out is not None else self._empty(3, H2, W2)
+        _chk(lib.gs_upscale_mlp(self.h, C.data_ptr(), grads.data_ptr(), W, H, W2, H2,
+                                None if params is None else params.data_ptr(), o.data_ptr()), self.h,
+             "gs_upscale_mlp")
+        return o
+
+    def mlp_samples(self, C, grads, W2: int, H2: int, pixels, target_image=None, out=None):
+        """Training samples at output pixels (int32 [M, 2] of (X, Y) on the device):
+        (features int16 [M, GS_MLP_ROW] holding BF16 bit patterns, spline [M, 3],
+        target [M, 3] or None)."""
+        torch = _torch()
+        H, W = int(C.shape[-2]), int(C.shape[-1])
+        assert pixels.dtype == torch.int32 and pixels.is_contiguous()
+        M = int(pixels.shape[0])
+        if out is None:
+            feat = torch.empty(M, GS_MLP_ROW, dtype=torch.int16, device="cuda")
+            base = self._empty(M, 3)
+            tgt = self._empty(M, 3) if target_image is not None else None
+        else:
+            feat, base, tgt = out
+        _chk(lib.gs_mlp_samples(self.h, C.data_ptr(), grads.data_ptr(), W, H, W2, H2, pixels.data_ptr(), M,
+                                None if target_image is None else target_image.data_ptr(), feat.data_ptr(),
+                                base.data_ptr(), None if tgt is None else tgt.data_ptr()), self.h, "gs_mlp_samples")
+        return feat, base, tgt
+
+    def mlp_gradient(self, params, feat, base, target, out=None):
+        """(dL/dparams [GS_MLP_PARAMS], L as a device scalar) of the mean squared
+        error over the samples."""
+        torch = _torch()
+        M = int(feat.shape[0])
+        g, L = out if out is not None else (self._empty(GS_MLP_PARAMS), self._empty(1))
+        _chk(lib.gs_mlp_gradient(self.h, params.data_ptr(), feat.data_ptr(), base.data_ptr(), target.data_ptr(), M,
+                                 g.data_ptr(), None if L is None else L.data_ptr()), self.h, "gs_mlp_gradient")
+        return g, L
+
+    def mlp_adam(self, params, m, v, grads, step: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+                 eps: float = 1e-8):
+        _chk(lib.gs_mlp_adam(self.h, params.data_ptr(), m.data_ptr(), v.data_ptr(), grads.data_ptr(), int(step),
+                             float(lr), float(beta1), float(beta2), float(eps)), self.h, "gs_mlp_adam")
 
     def upscale_backward_to(self, dout, W: int, H: int, out=None):
         """Adjoint of upscale_to: dL/d(out) [3, H2, W2] -> (dL/dC, dL/dgrads)."""

@@ -602,6 +602,67 @@ gs_status gs_upscale_to(gs_ctx* c, const float* C, const float* grads, int32_t W
     return GS_OK;
 }
 
+gs_status gs_upscale_mlp(gs_ctx* c, const float* C, const float* grads, int32_t W, int32_t H, int32_t W2, int32_t H2,
+                         const float* params, float* out)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    LaunchTally tally(c);
+    if (!C || !grads || !out) return fail(c, GS_ERR_INVALID_ARG, "NULL image pointer");
+    gs_status st = check_sizes(c, W, H, W2, H2, 2);
+    if (st != GS_OK) return st;
+    if (!params) {
+        GS_CUDA(c, launch_upscale_to(c->stream, C, grads, W, H, W2, H2, out));
+        return GS_OK;
+    }
+    GS_CUDA(c, launch_mlp_upscale(c->stream, C, grads, W, H, W2, H2, params, out, as<int>(c->errword)));
+    return GS_OK;
+}
+
+gs_status gs_mlp_samples(gs_ctx* c, const float* C, const float* grads, int32_t W, int32_t H, int32_t W2, int32_t H2,
+                         const int32_t* pixels, int64_t M, const float* target_image, uint16_t* features, float* base,
+                         float* target)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    LaunchTally tally(c);
+    if (M < 0) return fail(c, GS_ERR_INVALID_ARG, "M < 0");
+    if (M == 0) return GS_OK;
+    if (!C || !grads || !pixels || !features || !base) return fail(c, GS_ERR_INVALID_ARG, "NULL pointer");
+    if ((target_image == nullptr) != (target == nullptr))
+        return fail(c, GS_ERR_INVALID_ARG, "target_image and target go together");
+    if (reinterpret_cast<uintptr_t>(features) % 16) return fail(c, GS_ERR_INVALID_ARG, "features not 16-byte aligned");
+    gs_status st = check_sizes(c, W, H, W2, H2, 2);
+    if (st != GS_OK) return st;
+    GS_CUDA(c, launch_mlp_samples(c->stream, C, grads, W, H, W2, H2, pixels, M, target_image, features, base, target,
+                                  as<int>(c->errword)));
+    return GS_OK;
+}
+
+gs_status gs_mlp_gradient(gs_ctx* c, const float* params, const uint16_t* features, const float* base,
+                          const float* target, int64_t M, float* grads, float* loss)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    LaunchTally tally(c);
+    if (M < 0) return fail(c, GS_ERR_INVALID_ARG, "M < 0");
+    if (!params || !grads || (M > 0 && (!features || !base || !target)))
+        return fail(c, GS_ERR_INVALID_ARG, "NULL pointer");
+    if (reinterpret_cast<uintptr_t>(features) % 16) return fail(c, GS_ERR_INVALID_ARG, "features not 16-byte aligned");
+    GS_CUDA(c, launch_mlp_grad(c->stream, params, features, base, target, M, grads, loss, as<int>(c->errword)));
+    return GS_OK;
+}
+
+gs_status gs_mlp_adam(gs_ctx* c, float* params, float* m, float* v, const float* grads, int32_t step, float lr,
+                      float beta1, float beta2, float eps)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    LaunchTally tally(c);
+    if (!params || !m || !v || !grads) return fail(c, GS_ERR_INVALID_ARG, "NULL pointer");
+    if (step < 1) return fail(c, GS_ERR_INVALID_ARG, "step must be >= 1");
+    if (!(beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f && eps > 0.f && lr >= 0.f))
+        return fail(c, GS_ERR_INVALID_ARG, "need 0 <= beta < 1, eps > 0, lr >= 0");
+    GS_CUDA(c, launch_mlp_adam(c->stream, params, m, v, grads, step, lr, beta1, beta2, eps));
+    return GS_OK;
+}
+
 gs_status gs_upscale_backward_to(gs_ctx* c, const float* dL_dout, int32_t W, int32_t H, int32_t W2, int32_t H2,
                                  float* dL_dC, float* dL_dgrads)
 {

@@ -306,4 +306,19 @@ cudaError_t launch_blend_stats(cudaStream_t s, int mode, const BlendArgs& a, uns
 cudaError_t launch_upscale(cudaStream_t s, const float* C, const float* grads, int W, int H, int factor,
                            float* out);
 
+// Learned residual on the spline (parameters: GS_MLP_PARAMS FP32 values, W1 b1 W2 b2 W3 b3)
+// spline + MLP residual at any output size W2 x H2 (tensor-core inference fused into the upscale)
+cudaError_t launch_mlp_upscale(cudaStream_t s, const float* C, const float* G, int W, int H, int W2, int H2,
+                               const float* params, float* out, int* err);
+// training samples at output pixels [M][2]: BF16 feature rows [M][64], spline [M][3], target [M][3]
+cudaError_t launch_mlp_samples(cudaStream_t s, const float* C, const float* G, int W, int H, int W2, int H2,
+                               const int* pixels, long long M, const float* target_img, uint16_t* feat, float* base,
+                               float* target, int* err);
+// MSE loss over M samples and its gradient (grads and loss overwritten)
+cudaError_t launch_mlp_grad(cudaStream_t s, const float* params, const uint16_t* feat, const float* base,
+                            const float* target, long long M, float* grads, float* loss, int* err);
+// one Adam step (step >= 1) on params with moments m, v
+cudaError_t launch_mlp_adam(cudaStream_t s, float* params, float* m, float* v, const float* g, int step, float lr,
+                            float beta1, float beta2, float eps);
+
 }  // namespace gs

@@ -26,6 +26,7 @@
 // evaluates each output with 12 vector shared loads and 48 FMAs.  HBM-bound:
 // 48 B per low-res pixel in, 12 B per output pixel out.
 #include "gs_internal.cuh"
+#include "spline_common.cuh"
 
 namespace gs {
 namespace {
@@ -37,29 +38,6 @@ constexpr int kMaxFactor = 16;
 // footprint of a 64 x 16 output tile for W2 >= W: at most 63 + 2 x 15 + 2 cells
 constexpr int kFootW = kOutW + 2;
 constexpr int kFootH = kOutH + 2;
-
-// floor(num / den) for den > 0
-__device__ __forceinline__ long long floor_div(long long num, long long den)
-{
-    return num >= 0 ? num / den : -((den - 1 - num) / den);
-}
-
-// cell and local coordinate of output pixel X (clamped to [0, W - 2])
-__device__ __forceinline__ void cell_of(int X, int W, int W2, int& i, float& t)
-{
-    const long long num = (2ll * X + 1) * W - W2, den = 2ll * W2;
-    long long q = floor_div(num, den);
-    q = q < 0 ? 0 : (q > W - 2 ? W - 2 : q);
-    i = (int)q;
-    t = (float)(num - den * q) / (float)den;
-}
-
-__device__ __forceinline__ float4 hermite(float t)
-{
-    const float t2 = t * t;
-    const float omt = 1.f - t;
-    return make_float4((1.f + 2.f * t) * omt * omt, t2 * (3.f - 2.f * t), t * omt * omt, t2 * (t - 1.f));
-}
 
 // footprint bound of a 64 x 16 output tile: ceil(63 W / W2) + 2 columns,
 // ceil(15 H / H2) + 2 rows

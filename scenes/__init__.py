@@ -170,3 +170,36 @@ def subset(scene: dict, idx) -> dict:
 
 def num_gaussians(scene: dict) -> int:
     return int(scene["means"].shape[0])
+
+
+def mixture_scene_device(n: int, seed: int = 0, device: str = "cuda", components: int = 200,
+                         sh_degree: int = 3, aspect=(16.0, 9.0), fov_x_deg: float = 60.0,
+                         log_scale_mean: float = -4.0, log_scale_std: float = 0.7,
+                         opacity_logit_std: float = 1.5) -> dict:
+    """The recipe of ``mixture_scene`` drawn with torch's generator on the device
+    (another random stream than the numpy one; for generating many training
+    scenes quickly).  Values are torch float32 tensors on ``device``."""
+    import torch
+    g = torch.Generator(device=device).manual_seed(int(seed))
+    kw = dict(device=device, generator=g)
+    t = math.tan(math.radians(fov_x_deg) / 2.0)
+    zc = 3.0 + 7.0 * torch.rand(components, **kw)
+    xc = (torch.rand(components, **kw) - 0.5) * zc * t * (aspect[0] / aspect[1])
+    yc = (torch.rand(components, **kw) - 0.5) * zc * t
+    centres = torch.stack([xc, yc, zc], 1)
+    # Dirichlet(1) weights = normalised Exp(1) draws
+    w = -torch.log(torch.rand(components, **kw).clamp_min(1e-12))
+    comp = torch.multinomial(w / w.sum(), n, replacement=True, generator=g)
+    sig = torch.exp(math.log(0.4) + 0.5 * torch.randn(components, 3, **kw))
+    R, _ = torch.linalg.qr(torch.randn(components, 3, 3, **kw))
+    local = torch.randn(n, 3, **kw) * sig[comp]
+    means = centres[comp] + torch.einsum("nij,nj->ni", R[comp], local)
+    q = torch.randn(n, 4, **kw)
+    q = q / q.norm(dim=1, keepdim=True)
+    k = (sh_degree + 1) ** 2
+    sh = 0.2 * torch.randn(n, k, 3, **kw)
+    sh[:, 0, :] = (torch.rand(n, 3, **kw) - 0.5) / _Y00
+    return dict(means=means.float().contiguous(),
+                log_scales=(log_scale_mean + log_scale_std * torch.randn(n, 3, **kw)).contiguous(),
+                quats=q.contiguous(), opacity_logits=(opacity_logit_std * torch.randn(n, **kw)).contiguous(),
+                sh=sh.contiguous(), sh_degree=int(sh_degree))
