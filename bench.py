@@ -58,7 +58,10 @@ def _args():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gs", choices=["gs", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile", default=None, choices=["main", "direct", "backward"],
+    ap.add_argument("--mlp-pairs", type=int, default=2000,
+                    help="training pairs (480x270 with derivatives, 1920x1080 direct) of the learned residual")
+    ap.add_argument("--mlp-steps", type=int, default=3000, help="Adam steps of the learned residual")
+    ap.add_argument("--profile", default=None, choices=["main", "direct", "backward", "mlp"],
                     help="run only warm-up + steps of the 2x path (main) or of the direct 1920x1080 "
                          "render (direct) and print stage times; the case ncu captures use")
     return ap.parse_args()
@@ -480,6 +483,8 @@ def run_gs(args):
 
         # batched multi-view rendering (stereo pairs), batched vs one view at a time
         views = views_leg(torch, gs, scenes, stream) if world == 1 else None
+        learned = (mlp_leg(torch, gs, scenes, stream, dev, _peaks()[0], args.mlp_pairs, args.mlp_steps)
+                   if world == 1 and args.mlp_pairs > 0 else None)
 
         # end to end through the public API: pinned host scene in, image out
         # Every step uploads its scene (354 MB) from pinned host memory and reads
@@ -595,6 +600,7 @@ def run_gs(args):
         "psnr_db": {"2x_960x540": psnr2, "4x_480x270": psnr4, "vs": "direct 1920x1080 render, clipped to [0,1]"},
         "path_4x": {"mpix_s": OUT_W * OUT_H / 1e3 / ms_4x, "ms": ms_4x},
         "multi_view": views,
+        "learned_residual": learned,
         "comparisons": {
             "bicubic_2x": {"what": "plain 960x540 render + cubic convolution (a = -0.75) to 1920x1080",
                            "mpix_s": OUT_W * OUT_H / 1e3 / ms_bic, "ms": ms_bic, "psnr_db": psnr_bic},
@@ -654,6 +660,116 @@ def _traffic_from_profiles():
     if h.hexdigest()[:16] != d.get("sources_sha256_16"):
         return None
     return int(d["dram_bytes_per_launch"])
+
+
+MLP_W, MLP_H, MLP_F = 480, 270, 4          # training pairs: 480x270 -> 1920x1080
+MLP_SAMPLES_PER_PAIR = 4096
+MLP_BATCH = 16384
+MLP_PARAMS_FLOP = 2 * (50 * 64 + 64 * 64 + 64 * 3)   # algorithmic FLOP per output pixel of the network
+
+
+def _device_scene(gs, scenes, n, seed, log_scale_mean=-4.0):
+    sc = scenes.mixture_scene_device(n, seed=seed, log_scale_mean=log_scale_mean)
+    return gs.DeviceScene({"sh_degree": sc["sh_degree"]}, tensors={k: v for k, v in sc.items() if k != "sh_degree"})
+
+
+def mlp_leg(torch, gs, scenes, stream, dev, peaks, pairs, steps, reps=20):
+    """The learned residual: trained on the GPU by the library's kernels on
+    `pairs` seeded mixture scenes (1.5M Gaussians each, drawn on the device,
+    the mean log-scale of each scene uniform in [-4, -3] so that the Gaussians'
+    pixel sizes at 480x270 cover those of the 960x540 benchmark scene),
+    rendered at 480x270 with derivatives and at 1920x1080 directly; then its
+    inference fused into the 4x upscale of the benchmark scene's 960x540 render
+    to 3840x2160, against the spline alone, PSNR against a direct 3840x2160
+    render."""
+    from paper_2503_14171_gb300 import residual
+    ctx = gs.Context(stream=stream)
+    cam_t = scenes.pinhole_camera(MLP_W, MLP_H)
+    cam_th = scenes.scaled_camera(cam_t, MLP_F)
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        gen = torch.Generator(device="cuda").manual_seed(0)
+        scale_means = np.random.default_rng(7).uniform(-4.0, -3.0, pairs + 4)
+        sets = []
+        for k in range(pairs):
+            d = _device_scene(gs, scenes, N_GAUSS, 100_000 + k, scale_means[k])
+            C, G = ctx.render_with_grads(d, cam_t, MLP_W, MLP_H)
+            D = ctx.render(d, cam_th, MLP_W * MLP_F, MLP_H * MLP_F)
+            sets.append(residual.draw_samples(ctx, C, G, D, MLP_SAMPLES_PER_PAIR, gen))
+            del d
+        samples = residual.SampleSet.cat(sets)
+        del sets
+        torch.cuda.synchronize()
+        t_data = time.perf_counter() - t0
+        model = residual.ResidualMLP(ctx, seed=0)
+        t0 = time.perf_counter()
+        losses = residual.train(model, samples, steps=steps, batch=MLP_BATCH, lr=2e-3, seed=1)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        # one training step timed on the device (gradient + Adam on one batch)
+        batch = samples.slice(0, MLP_BATCH)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(3):
+            ctx.mlp_gradient(model.params, batch.feat, batch.base, batch.target, out=(model.grads, model.loss))
+        a.record(stream)
+        for _ in range(reps):
+            ctx.mlp_gradient(model.params, batch.feat, batch.base, batch.target, out=(model.grads, model.loss))
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms_grad = a.elapsed_time(b) / reps
+        # inference on the benchmark scene: 960x540 -> 3840x2160
+        W2, H2 = LOW_W * 4, LOW_H * 4
+        cam = scenes.pinhole_camera(LOW_W, LOW_H)
+        C, G = ctx.render_with_grads(dev, cam, LOW_W, LOW_H)
+        out_mlp = torch.empty(3, H2, W2, device="cuda")
+        out_spl = torch.empty(3, H2, W2, device="cuda")
+
+        def timed(fn):
+            for _ in range(3):
+                fn()
+            a.record(stream)
+            for _ in range(reps):
+                fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / reps
+
+        ms_mlp = timed(lambda: ctx.upscale_mlp(C, G, W2, H2, params=model.params, out=out_mlp))
+        ms_spl = timed(lambda: ctx.upscale_mlp(C, G, W2, H2, out=out_spl))
+        direct = ctx.render(dev, scenes.scaled_camera(cam, 4), W2, H2)
+        torch.cuda.synchronize()
+        p_mlp, p_spl = residual.psnr(out_mlp, direct), residual.psnr(out_spl, direct)
+        # held-out training-resolution pairs: PSNR gain at 480x270 -> 1920x1080
+        gains = []
+        for k in range(4):
+            d = _device_scene(gs, scenes, N_GAUSS, 900_000 + k, scale_means[pairs + k])
+            C2, G2 = ctx.render_with_grads(d, cam_t, MLP_W, MLP_H)
+            D2 = ctx.render(d, cam_th, MLP_W * MLP_F, MLP_H * MLP_F)
+            gains.append(residual.psnr(model.upscale(C2, G2, MLP_W * MLP_F, MLP_H * MLP_F), D2)
+                         - residual.psnr(ctx.upscale_mlp(C2, G2, MLP_W * MLP_F, MLP_H * MLP_F), D2))
+            del d
+    ctx.synchronize()
+    ctx.close()
+    flop = W2 * H2 * MLP_PARAMS_FLOP
+    tflops = flop / (ms_mlp * 1e-3) / 1e12
+    lo = losses[:20].mean().item()
+    hi = losses[-20:].mean().item()
+    return {
+        "what": "per-pixel residual MLP 50-64-64-3 on the spline's 48 corner values and (t, u), BF16 operands, "
+                "FP32 accumulators in tensor memory (tcgen05), fused into the upscale",
+        "train": {"pairs": pairs, "samples": len(samples), "steps": steps, "batch": MLP_BATCH,
+                  "pair_res": [MLP_W, MLP_H, MLP_W * MLP_F, MLP_H * MLP_F], "gaussians_per_scene": N_GAUSS,
+                  "scene_log_scale_mean": "U[-4, -3] per pair",
+                  "data_s": t_data, "train_s": t_train, "loss_first20": lo, "loss_last20": hi,
+                  "grad_step_ms": ms_grad, "heldout_psnr_gain_db": gains},
+        "infer_4x": {"in": [LOW_W, LOW_H], "out": [W2, H2], "ms": ms_mlp, "mpix_s": W2 * H2 / 1e3 / ms_mlp,
+                     "spline_only_ms": ms_spl, "spline_only_mpix_s": W2 * H2 / 1e3 / ms_spl,
+                     "psnr_db": p_mlp, "spline_only_psnr_db": p_spl, "vs": "direct 3840x2160 render"},
+        "roofline": {"bound": "tensor", "kernel": "k_mlp_upscale", "achieved": tflops,
+                     "peak": peaks.get("bf16_tflops"), "unit": "TFLOP/s",
+                     "frac": tflops / peaks.get("bf16_tflops", 1949.0),
+                     "flop_per_pixel": MLP_PARAMS_FLOP},
+    }
 
 
 def stereo_views(seed=0, pairs=8, lo=(512, 512), hi=(1104, 1032), ipd=0.064):
@@ -772,7 +888,24 @@ def run_profile(args):
     def backward_step():
         ctx.backward(dout, FACTOR, out=grads)
 
-    fn = {"main": main_step, "direct": direct_step, "backward": backward_step}[args.profile]
+    # the learned residual's fused 4x upscale (960x540 -> 3840x2160) with
+    # seeded untrained-scale weights: the kernel's work does not depend on them
+    mlp_out = None
+    mlp_params = None
+
+    def mlp_step():
+        ctx.upscale_mlp(C, G, LOW_W * 4, LOW_H * 4, params=mlp_params, out=mlp_out)
+
+    fn = {"main": main_step, "direct": direct_step, "backward": backward_step, "mlp": mlp_step}[args.profile]
+    if args.profile == "mlp":
+        from paper_2503_14171_gb300 import residual
+        with torch.cuda.stream(stream):
+            main_step()
+            mlp_out = torch.empty(3, LOW_H * 4, LOW_W * 4, device="cuda")
+            p = residual.init_params(0)
+            p[-3 - 192:-3] = np.random.default_rng(1).normal(0, 0.05, 192)    # a non-zero output layer
+            mlp_params = torch.as_tensor(p).cuda()
+            torch.cuda.synchronize()
     if args.profile == "backward":
         with torch.cuda.stream(stream):
             main_step()

@@ -157,27 +157,66 @@ __device__ __forceinline__ void mma_k64(uint32_t d, uint32_t a, uint32_t b, uint
 
 // ------------------------------------------------------------------ inference
 
+// A tile is 32 x 4 output pixels: thread tid takes pixel (tid % 32, tid / 32),
+// so warp w owns output row w of the tile and accumulator lanes 32 w .. 32 w +
+// 31.  The tile's low-res footprint (at most 33 x 5 pixels for W2 >= W,
+// H2 >= H: the cells of 32 consecutive columns span at most 31 cells) is staged
+// in shared memory with coalesced loads, each low-res pixel as three float4
+// holding its 12 values (C, C_x, C_y, C_xy) x (r, g, b) -- the feature order
+// of one corner.  Cell indices and Hermite weights of the tile's 32 columns
+// and 4 rows are computed once per tile.
+constexpr int kTileW = 32, kTileH = 4;
+constexpr int kFootW = kTileW + 1, kFootH = kTileH + 1;
+static_assert(kTileW * kTileH == kRows, "one tile per MMA");
+
 struct InferSmem {
-    uint8_t a1[kRows * 128];   // features of the tile's samples (A of layer 1)
-    uint8_t a2[kRows * 128];   // h1 (A of layer 2)
+    uint8_t a[kRows * 128];          // A operand: features, then h1
     uint8_t w1[kHid * 128];
     uint8_t w2[kHid * 128];
-    float w3[kOut * kHid];
-    float b1[kHid], b2[kHid], b3[4];
+    float4 foot[kFootH * kFootW * 3];
+    float4 w3b2[kHid];               // (W3[0][k], W3[1][k], W3[2][k], b2[k]), W3 as BF16 values
+    float4 b1[kHid / 4];
+    float4 hx[kTileW], hy[kTileH];   // Hermite weights of the columns / rows
+    float tx[kTileW], ty[kTileH];    // local coordinates t, u
+    int cx[kTileW], cy[kTileH];      // absolute cell indices
+    float b3[4];
     uint64_t bar;
     uint32_t tmem;
 };
 
-constexpr uint32_t kInferCols = 128;   // D1: columns 0..63, D2: 64..127
+constexpr uint32_t kInferCols = 64;   // D1 and D2 share columns 0..63
 
-__global__ void __launch_bounds__(kThreads) k_mlp_upscale(const float* __restrict__ C, const float* __restrict__ G,
-                                                          int W, int H, int W2, int H2, const float* __restrict__ P,
-                                                          float* __restrict__ out, int* __restrict__ err)
+// element e (0..11) of a corner's three float4
+__device__ __forceinline__ float corner_value(const float4 (&v)[3], int e)
+{
+    const float4 q = v[e >> 2];
+    switch (e & 3) {
+    case 0: return q.x;
+    case 1: return q.y;
+    case 2: return q.z;
+    default: return q.w;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 5) k_mlp_upscale(const float* __restrict__ C, const float* __restrict__ G,
+                                                             int W, int H, int W2, int H2,
+                                                             const float* __restrict__ P, float* __restrict__ out,
+                                                             int* __restrict__ err)
 {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     InferSmem& s = *reinterpret_cast<InferSmem*>(smem_raw);
-    const int tid = threadIdx.x, warp = tid >> 5;
-    stage_weights(P, s.w1, s.w2, nullptr, s.w3, s.b1, s.b2, s.b3);
+    const int tid = threadIdx.x, warp = tid >> 5, lx = tid & 31, ly = tid >> 5;
+    for (int e = tid; e < kHid * 64; e += kThreads) {
+        const int n = e >> 6, k = e & 63;
+        st_bf16(s.w1, kmaj(n, k, kSbo64), k < kIn ? P[oW1 + n * kIn + k] : 0.f);
+        st_bf16(s.w2, kmaj(n, k, kSbo64), P[oW2 + n * kHid + k]);
+    }
+    if (tid < kHid) {
+        s.w3b2[tid] = make_float4(bf16_round(P[oW3 + tid]), bf16_round(P[oW3 + kHid + tid]),
+                                  bf16_round(P[oW3 + 2 * kHid + tid]), P[oB2 + tid]);
+        reinterpret_cast<float*>(s.b1)[tid] = P[oB1 + tid];
+    }
+    if (tid < kOut) s.b3[tid] = P[oB3 + tid];
     if (tid == 0) {
         mbar_init(&s.bar, 1);
         mbar_init_fence();
@@ -192,67 +231,130 @@ __global__ void __launch_bounds__(kThreads) k_mlp_upscale(const float* __restric
     fence_after_sync();
     const uint32_t tmem = s.tmem;
     const uint32_t lane = (uint32_t)(warp * 32) << 16;
-    const uint32_t a1 = smem_u32(s.a1), a2 = smem_u32(s.a2), w1 = smem_u32(s.w1), w2 = smem_u32(s.w2);
+    const uint32_t sa = smem_u32(s.a), w1 = smem_u32(s.w1), w2 = smem_u32(s.w2);
     constexpr uint32_t idesc = idesc_bf16(kRows, kHid);
-    const long long npix = (long long)W2 * H2;
-    const long long ntiles = (npix + kRows - 1) / kRows;
+    const int tiles_x = (W2 + kTileW - 1) / kTileW;
+    const long long ntiles = (long long)tiles_x * ((H2 + kTileH - 1) / kTileH);
+    const size_t plane = (size_t)W * H, plane2 = (size_t)W2 * H2;
     uint32_t phase = 0;
     bool ok = true;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const long long p = tile * kRows + tid;
-        const bool active = p < npix;
-        int X = 0, Y = 0;
-        float sp[3] = {0.f, 0.f, 0.f};
+        const int tyi = (int)(tile / tiles_x);
+        const int X0 = (int)(tile - (long long)tyi * tiles_x) * kTileW, Y0 = tyi * kTileH;
+        // cells of the tile's columns and rows (clamped to the last pixel)
+        if (tid < kTileW) {
+            int ci;
+            float t;
+            cell_of(min(X0 + tid, W2 - 1), W, W2, ci, t);
+            s.cx[tid] = ci;
+            s.tx[tid] = t;
+            s.hx[tid] = hermite(t);
+        } else if (tid < kTileW + kTileH) {
+            const int r = tid - kTileW;
+            int cj;
+            float u;
+            cell_of(min(Y0 + r, H2 - 1), H, H2, cj, u);
+            s.cy[r] = cj;
+            s.ty[r] = u;
+            s.hy[r] = hermite(u);
+        }
+        __syncthreads();
+        const int i0 = s.cx[0], j0 = s.cy[0];
+        const int fw = s.cx[kTileW - 1] + 2 - i0, fh = s.cy[kTileH - 1] + 2 - j0;   // <= kFootW x kFootH
+        for (int e = tid; e < fw * fh; e += kThreads) {
+            const int fy = e / fw, fx = e - fy * fw;
+            const size_t o = (size_t)(j0 + fy) * W + i0 + fx;
+            float4* d = s.foot + 3 * (fy * kFootW + fx);
+            d[0] = make_float4(__ldg(C + o), __ldg(C + plane + o), __ldg(C + 2 * plane + o), __ldg(G + o));
+            d[1] = make_float4(__ldg(G + plane + o), __ldg(G + 2 * plane + o), __ldg(G + 3 * plane + o),
+                               __ldg(G + 4 * plane + o));
+            d[2] = make_float4(__ldg(G + 5 * plane + o), __ldg(G + 6 * plane + o), __ldg(G + 7 * plane + o),
+                               __ldg(G + 8 * plane + o));
+        }
+        __syncthreads();
+        // this pixel: spline value and BF16 features (row tid of A)
+        const int X = X0 + lx, Y = Y0 + ly;
+        float sp0 = 0.f, sp1 = 0.f, sp2 = 0.f;
         {
-            float f[48], t = 0.f, u = 0.f;
-            if (active) {
-                Y = (int)(p / W2);
-                X = (int)(p - (long long)Y * W2);
-                pixel_inputs(C, G, W, H, W2, H2, X, Y, f, t, u, sp);
-            } else {
+            const int li = s.cx[lx] - i0, lj = s.cy[ly] - j0;
+            const float4 hx = s.hx[lx], hy = s.hy[ly];
+            float4 v[4][3];
 #pragma unroll
-                for (int k = 0; k < 48; ++k) f[k] = 0.f;
+            for (int k = 0; k < 4; ++k) {
+                const float4* src = s.foot + 3 * ((lj + (k >> 1)) * kFootW + li + (k & 1));
+                v[k][0] = src[0];
+                v[k][1] = src[1];
+                v[k][2] = src[2];
+                const float Hx = (k & 1) ? hx.y : hx.x, Gx = (k & 1) ? hx.w : hx.z;
+                const float Hy = (k >> 1) ? hy.y : hy.x, Gy = (k >> 1) ? hy.w : hy.z;
+                const float wv = Hx * Hy, wdx = Gx * Hy, wdy = Hx * Gy, wdxy = Gx * Gy;
+                sp0 = fmaf(wv, v[k][0].x, sp0);
+                sp1 = fmaf(wv, v[k][0].y, sp1);
+                sp2 = fmaf(wv, v[k][0].z, sp2);
+                sp0 = fmaf(wdx, v[k][0].w, sp0);
+                sp1 = fmaf(wdx, v[k][1].x, sp1);
+                sp2 = fmaf(wdx, v[k][1].y, sp2);
+                sp0 = fmaf(wdy, v[k][1].z, sp0);
+                sp1 = fmaf(wdy, v[k][1].w, sp1);
+                sp2 = fmaf(wdy, v[k][2].x, sp2);
+                sp0 = fmaf(wdxy, v[k][2].y, sp0);
+                sp1 = fmaf(wdxy, v[k][2].z, sp1);
+                sp2 = fmaf(wdxy, v[k][2].w, sp2);
             }
-            uint4 q[8];
-            feature_chunks(f, t, u, q);
-            store_row(s.a1, tid, q);
+            // feature f = 12 k + e is element e of corner k; chunk c holds f = 8c .. 8c + 7
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                uint32_t w4[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int f = 8 * c + 2 * j;
+                    w4[j] = pack_bf16x2(corner_value(v[f / 12], f % 12), corner_value(v[(f + 1) / 12], (f + 1) % 12));
+                }
+                *reinterpret_cast<uint4*>(s.a + kmaj(tid, 8 * c, kSbo64)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+            }
+            *reinterpret_cast<uint4*>(s.a + kmaj(tid, 48, kSbo64)) =
+                make_uint4(pack_bf16x2(s.tx[lx], s.ty[ly]), 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(s.a + kmaj(tid, 56, kSbo64)) = make_uint4(0u, 0u, 0u, 0u);
         }
         fence_async_smem();
         fence_before_sync();
         __syncthreads();
         if (tid == 0) {
             fence_after_sync();
-            mma_k64(tmem, a1, w1, idesc);
+            mma_k64(tmem, sa, w1, idesc);
             mma_commit(&s.bar);
         }
         ok = __syncthreads_and(mbar_wait(&s.bar, phase, kWaitLimit));
         phase ^= 1u;
         if (!ok) break;
         fence_after_sync();
-        // layer 1 epilogue: h1 = relu(z1 + b1) as the BF16 row of a2
-        {
-            uint4 q[8];
+        // layer 1 epilogue: h1 = relu(z1 + b1) as the BF16 row of A (the MMA
+        // that read the features is complete)
 #pragma unroll
-            for (int g = 0; g < 4; ++g) {
-                float z[16];
-                tmem_ld16(tmem + lane + 16 * g, z);
-                tmem_wait_ld();
+        for (int g = 0; g < 4; ++g) {
+            float z[16];
+            tmem_ld16(tmem + lane + 16 * g, z);
+            tmem_wait_ld();
 #pragma unroll
-                for (int k = 0; k < 16; ++k) z[k] = fmaxf(z[k] + s.b1[16 * g + k], 0.f);
-#pragma unroll
-                for (int h = 0; h < 2; ++h)
-                    q[2 * g + h] = make_uint4(pack_bf16x2(z[8 * h], z[8 * h + 1]), pack_bf16x2(z[8 * h + 2], z[8 * h + 3]),
-                                              pack_bf16x2(z[8 * h + 4], z[8 * h + 5]),
-                                              pack_bf16x2(z[8 * h + 6], z[8 * h + 7]));
+            for (int k4 = 0; k4 < 4; ++k4) {
+                const float4 b = s.b1[4 * g + k4];
+                z[4 * k4] = fmaxf(z[4 * k4] + b.x, 0.f);
+                z[4 * k4 + 1] = fmaxf(z[4 * k4 + 1] + b.y, 0.f);
+                z[4 * k4 + 2] = fmaxf(z[4 * k4 + 2] + b.z, 0.f);
+                z[4 * k4 + 3] = fmaxf(z[4 * k4 + 3] + b.w, 0.f);
             }
-            store_row(s.a2, tid, q);
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                *reinterpret_cast<uint4*>(s.a + kmaj(tid, 16 * g + 8 * h, kSbo64)) =
+                    make_uint4(pack_bf16x2(z[8 * h], z[8 * h + 1]), pack_bf16x2(z[8 * h + 2], z[8 * h + 3]),
+                               pack_bf16x2(z[8 * h + 4], z[8 * h + 5]), pack_bf16x2(z[8 * h + 6], z[8 * h + 7]));
         }
         fence_async_smem();
         fence_before_sync();
         __syncthreads();
         if (tid == 0) {
             fence_after_sync();
-            mma_k64(tmem + kHid, a2, w2, idesc);
+            mma_k64(tmem, sa, w2, idesc);      // every thread has read D1
             mma_commit(&s.bar);
         }
         ok = __syncthreads_and(mbar_wait(&s.bar, phase, kWaitLimit));
@@ -264,22 +366,22 @@ __global__ void __launch_bounds__(kThreads) k_mlp_upscale(const float* __restric
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
             float z[16];
-            tmem_ld16(tmem + lane + kHid + 16 * g, z);
+            tmem_ld16(tmem + lane + 16 * g, z);
             tmem_wait_ld();
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
-                const int n = 16 * g + k;
-                const float h = fmaxf(z[k] + s.b2[n], 0.f);
-                r0 = fmaf(s.w3[n], h, r0);
-                r1 = fmaf(s.w3[kHid + n], h, r1);
-                r2 = fmaf(s.w3[2 * kHid + n], h, r2);
+                const float4 w = s.w3b2[16 * g + k];
+                const float h = fmaxf(z[k] + w.w, 0.f);
+                r0 = fmaf(w.x, h, r0);
+                r1 = fmaf(w.y, h, r1);
+                r2 = fmaf(w.z, h, r2);
             }
         }
-        if (active) {
-            const size_t o = (size_t)Y * W2 + X, plane2 = (size_t)npix;
-            out[o] = sp[0] + r0;
-            out[plane2 + o] = sp[1] + r1;
-            out[2 * plane2 + o] = sp[2] + r2;
+        if (X < W2 && Y < H2) {
+            const size_t o = (size_t)Y * W2 + X;
+            out[o] = sp0 + r0;
+            out[plane2 + o] = sp1 + r1;
+            out[2 * plane2 + o] = sp2 + r2;
         }
         fence_before_sync();
     }
@@ -646,10 +748,10 @@ cudaError_t launch_mlp_upscale(cudaStream_t s, const float* C, const float* G, i
     const size_t smem = sizeof(InferSmem);
     cudaError_t e = cudaFuncSetAttribute(k_mlp_upscale, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const long long ntiles = ((long long)W2 * H2 + kRows - 1) / kRows;
+    const long long ntiles = (long long)((W2 + kTileW - 1) / kTileW) * ((H2 + kTileH - 1) / kTileH);
     if (ntiles == 0) return cudaSuccess;
-    // four CTAs per SM: 4 x 128 tensor-memory columns, 4 x ~50 KB shared memory
-    const long long grid = std::min<long long>(ntiles, 4ll * sm_count());
+    // five CTAs per SM: 5 x 64 tensor-memory columns, 5 x ~42 KB shared memory
+    const long long grid = std::min<long long>(ntiles, 5ll * sm_count());
     k_mlp_upscale<<<(unsigned)grid, kThreads, smem, s>>>(C, G, W, H, W2, H2, params, out, err);
     note_launch();
     return cudaGetLastError();

@@ -191,7 +191,12 @@ def mixture_scene_device(n: int, seed: int = 0, device: str = "cuda", components
     w = -torch.log(torch.rand(components, **kw).clamp_min(1e-12))
     comp = torch.multinomial(w / w.sum(), n, replacement=True, generator=g)
     sig = torch.exp(math.log(0.4) + 0.5 * torch.randn(components, 3, **kw))
-    R, _ = torch.linalg.qr(torch.randn(components, 3, 3, **kw))
+    # random component axes: the rotation of a uniformly random unit quaternion
+    qc = torch.randn(components, 4, **kw)
+    w, x, y, z = (qc / qc.norm(dim=1, keepdim=True)).unbind(1)
+    R = torch.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
+                     2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                     2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], 1).view(components, 3, 3)
     local = torch.randn(n, 3, **kw) * sig[comp]
     means = centres[comp] + torch.einsum("nij,nj->ni", R[comp], local)
     q = torch.randn(n, 4, **kw)
