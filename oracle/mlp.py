@@ -95,9 +95,10 @@ def forward(theta, f, quantize=None):
     """MLP residual r [M, 3] of features f [M, 50], with the intermediates.
 
     ``quantize`` (e.g. ``bf16_round``), when given, is applied where a lower-
-    precision evaluation stores an operand in a narrower type: to the features
-    and to h1 before the second layer.  That rounding is a quantisation decision
-    (the code of the narrow value), taken here on this definition's values."""
+    precision evaluation stores an operand in a narrower type: to the features,
+    to h1 before the second layer and to h2 before the output layer.  That
+    rounding is a quantisation decision (the code of the narrow value), taken
+    here on this definition's values."""
     p = unpack(theta)
     f = np.asarray(f, np.float64)
     if quantize is not None:
@@ -108,6 +109,8 @@ def forward(theta, f, quantize=None):
         h1 = quantize(h1)
     z2 = h1 @ p["W2"].T + p["b2"]
     h2 = np.maximum(z2, 0.0)
+    if quantize is not None:
+        h2 = quantize(h2)
     r = h2 @ p["W3"].T + p["b3"]
     return r, dict(z1=z1, h1=h1, z2=z2, h2=h2)
 

@@ -10,6 +10,8 @@
 // Parameters: one FP32 vector W1 [64][50], b1 [64], W2 [64][64], b2 [64],
 // W3 [3][64], b3 [3] (7619 values).  The matrices enter the tensor core as
 // BF16 (round to nearest even), the biases stay FP32; accumulation is FP32.
+// Activations enter each product as BF16: the features, h1 and h2 (and, in the
+// reverse mode, d2 and d1).
 //
 // Kernels (tcgen05, one CTA of 128 threads per 128 samples at a time, a
 // persistent grid; see umma.cuh for the operand layout):
@@ -17,13 +19,15 @@
 //                   gather the 48 corner values (once, for both the spline and
 //                   the features), evaluate the spline, stage the BF16
 //                   features as the A operand, two MMAs (M 128, N 64, K 64)
-//                   with ReLU epilogues from tensor memory, the last layer
-//                   (64 -> 3) on the FP32 cores, write spline + residual.
+//                   and a third (N 16, the 64 -> 3 output layer) with ReLU
+//                   epilogues from tensor memory, write spline + residual.
 //   k_mlp_samples   training samples: features (BF16 rows of 64), spline value
 //                   and target at given output pixels.
 //   k_mlp_grad      forward and reverse mode of the MSE loss over M samples:
 //                   h1 = relu(W1 f + b1) and h2 = relu(W2 h1 + b2) as in
-//                   inference; d3 = 2 e / (3 M); d2 = (W3^T d3) [z2 > 0] on the
+//                   inference (h2 narrowed to BF16 for the output layer, which
+//                   runs on the FP32 cores here); d3 = 2 e / (3 M);
+//                   d2 = (W3^T d3) [z2 > 0] on the
 //                   FP32 cores; d1 = (W2^T d2) [z1 > 0] as an MMA against W2^T;
 //                   the weight gradients of both hidden layers in one MMA per
 //                   tile, P Q^T with P = [d2^T ; d1^T] (128 units x 128
@@ -173,9 +177,9 @@ struct InferSmem {
     uint8_t a[kRows * 128];          // A operand: features, then h1
     uint8_t w1[kHid * 128];
     uint8_t w2[kHid * 128];
+    uint8_t w3[16 * 128];            // W3 as a B operand: N = 16 rows (3 used), K = 64
     float4 foot[kFootH * kFootW * 3];
-    float4 w3b2[kHid];               // (W3[0][k], W3[1][k], W3[2][k], b2[k]), W3 as BF16 values
-    float4 b1[kHid / 4];
+    float4 b1[kHid / 4], b2[kHid / 4];
     float4 hx[kTileW], hy[kTileH];   // Hermite weights of the columns / rows
     float tx[kTileW], ty[kTileH];    // local coordinates t, u
     int cx[kTileW], cy[kTileH];      // absolute cell indices
@@ -184,7 +188,7 @@ struct InferSmem {
     uint32_t tmem;
 };
 
-constexpr uint32_t kInferCols = 64;   // D1 and D2 share columns 0..63
+constexpr uint32_t kInferCols = 64;   // D1, D2 and D3 share columns 0..63
 
 // element e (0..11) of a corner's three float4
 __device__ __forceinline__ float corner_value(const float4 (&v)[3], int e)
@@ -211,10 +215,13 @@ __global__ void __launch_bounds__(kThreads, 5) k_mlp_upscale(const float* __rest
         st_bf16(s.w1, kmaj(n, k, kSbo64), k < kIn ? P[oW1 + n * kIn + k] : 0.f);
         st_bf16(s.w2, kmaj(n, k, kSbo64), P[oW2 + n * kHid + k]);
     }
+    for (int e = tid; e < 16 * 64; e += kThreads) {
+        const int n = e >> 6, k = e & 63;
+        st_bf16(s.w3, kmaj(n, k, kSbo64), n < kOut ? P[oW3 + n * kHid + k] : 0.f);
+    }
     if (tid < kHid) {
-        s.w3b2[tid] = make_float4(bf16_round(P[oW3 + tid]), bf16_round(P[oW3 + kHid + tid]),
-                                  bf16_round(P[oW3 + 2 * kHid + tid]), P[oB2 + tid]);
         reinterpret_cast<float*>(s.b1)[tid] = P[oB1 + tid];
+        reinterpret_cast<float*>(s.b2)[tid] = P[oB2 + tid];
     }
     if (tid < kOut) s.b3[tid] = P[oB3 + tid];
     if (tid == 0) {
@@ -231,8 +238,9 @@ __global__ void __launch_bounds__(kThreads, 5) k_mlp_upscale(const float* __rest
     fence_after_sync();
     const uint32_t tmem = s.tmem;
     const uint32_t lane = (uint32_t)(warp * 32) << 16;
-    const uint32_t sa = smem_u32(s.a), w1 = smem_u32(s.w1), w2 = smem_u32(s.w2);
+    const uint32_t sa = smem_u32(s.a), w1 = smem_u32(s.w1), w2 = smem_u32(s.w2), w3 = smem_u32(s.w3);
     constexpr uint32_t idesc = idesc_bf16(kRows, kHid);
+    constexpr uint32_t idesc3 = idesc_bf16(kRows, 16);
     const int tiles_x = (W2 + kTileW - 1) / kTileW;
     const long long ntiles = (long long)tiles_x * ((H2 + kTileH - 1) / kTileH);
     const size_t plane = (size_t)W * H, plane2 = (size_t)W2 * H2;
@@ -361,21 +369,47 @@ __global__ void __launch_bounds__(kThreads, 5) k_mlp_upscale(const float* __rest
         phase ^= 1u;
         if (!ok) break;
         fence_after_sync();
-        // layer 2 epilogue and the last layer: r = W3 relu(z2 + b2) + b3
-        float r0 = s.b3[0], r1 = s.b3[1], r2 = s.b3[2];
+        // layer 2 epilogue: h2 = relu(z2 + b2) as the BF16 row of A (the MMA
+        // that read h1 is complete)
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
             float z[16];
             tmem_ld16(tmem + lane + 16 * g, z);
             tmem_wait_ld();
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const float4 w = s.w3b2[16 * g + k];
-                const float h = fmaxf(z[k] + w.w, 0.f);
-                r0 = fmaf(w.x, h, r0);
-                r1 = fmaf(w.y, h, r1);
-                r2 = fmaf(w.z, h, r2);
+            for (int k4 = 0; k4 < 4; ++k4) {
+                const float4 b = s.b2[4 * g + k4];
+                z[4 * k4] = fmaxf(z[4 * k4] + b.x, 0.f);
+                z[4 * k4 + 1] = fmaxf(z[4 * k4 + 1] + b.y, 0.f);
+                z[4 * k4 + 2] = fmaxf(z[4 * k4 + 2] + b.z, 0.f);
+                z[4 * k4 + 3] = fmaxf(z[4 * k4 + 3] + b.w, 0.f);
             }
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                *reinterpret_cast<uint4*>(s.a + kmaj(tid, 16 * g + 8 * h, kSbo64)) =
+                    make_uint4(pack_bf16x2(z[8 * h], z[8 * h + 1]), pack_bf16x2(z[8 * h + 2], z[8 * h + 3]),
+                               pack_bf16x2(z[8 * h + 4], z[8 * h + 5]), pack_bf16x2(z[8 * h + 6], z[8 * h + 7]));
+        }
+        fence_async_smem();
+        fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            fence_after_sync();
+            mma_k64(tmem, sa, w3, idesc3);     // the output layer, N = 16 (3 used)
+            mma_commit(&s.bar);
+        }
+        ok = __syncthreads_and(mbar_wait(&s.bar, phase, kWaitLimit));
+        phase ^= 1u;
+        if (!ok) break;
+        fence_after_sync();
+        float r0, r1, r2;
+        {
+            float z[16];
+            tmem_ld16(tmem + lane, z);
+            tmem_wait_ld();
+            r0 = z[0] + s.b3[0];
+            r1 = z[1] + s.b3[1];
+            r2 = z[2] + s.b3[2];
         }
         if (X < W2 && Y < H2) {
             const size_t o = (size_t)Y * W2 + X;
@@ -587,7 +621,7 @@ __global__ void __launch_bounds__(kThreads) k_mlp_grad(const float* __restrict__
                     const int n = 16 * g + k;
                     const float zz = z[k] + s.b2[n];
                     if (zz > 0.f) mask2[n >> 5] |= 1u << (n & 31);
-                    const float h = fmaxf(zz, 0.f);
+                    const float h = bf16_round(fmaxf(zz, 0.f));   // as the output layer reads it
                     s.h2[tid][n] = h;
                     r0 = fmaf(s.w3[n], h, r0);
                     r1 = fmaf(s.w3[kHid + n], h, r1);

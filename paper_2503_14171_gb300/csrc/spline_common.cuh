@@ -15,12 +15,20 @@ __device__ __forceinline__ long long floor_div(long long num, long long den)
     return num >= 0 ? num / den : -((den - 1 - num) / den);
 }
 
-// cell and local coordinate of output pixel X (clamped to [0, W - 2])
+// cell and local coordinate of output pixel X (clamped to [0, W - 2]); a
+// negative numerator clamps to cell 0, and a quotient of 31-bit operands takes
+// the 32-bit division (the same exact floor)
 __device__ __forceinline__ void cell_of(int X, int W, int W2, int& i, float& t)
 {
     const long long num = (2ll * X + 1) * W - W2, den = 2ll * W2;
-    long long q = floor_div(num, den);
-    q = q < 0 ? 0 : (q > W - 2 ? W - 2 : q);
+    long long q;
+    if (num < 0)
+        q = 0;
+    else if (num <= 0x7FFFFFFFll && den <= 0x7FFFFFFFll)
+        q = (long long)((unsigned)num / (unsigned)den);
+    else
+        q = floor_div(num, den);
+    q = q > W - 2 ? W - 2 : q;
     i = (int)q;
     t = (float)(num - den * q) / (float)den;
 }

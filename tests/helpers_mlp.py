@@ -1,8 +1,8 @@
 """Comparing the tensor-core MLP kernels with the FP64 oracle (oracle.mlp).
 
 The kernels narrow operands to BF16 (8 significant bits) at fixed points: the
-matrices, the features, h1 before the second layer, d2 and d1 before the
-reverse-mode products.  Each narrowing is a quantisation decision, so the
+matrices, the features, h1 before the second layer, h2 before the output
+layer, d2 and d1 before the reverse-mode products.  Each narrowing is a quantisation decision, so the
 reference takes it in the kernels' precision: oracle.mlp evaluated with
 ``quantize = bf16_round`` on the BF16 values of the matrices.  What remains
 between kernel and reference is FP32 accumulation, bounded as follows:
@@ -68,9 +68,11 @@ def forward_reference(theta_b, f):
     h1_pre = np.maximum(s["z1"], 0.0)
     eh1 = flip_step(h1_pre, e1)
     e2 = eh1 @ A2.T + 66 * G * (s["h1"] @ A2.T + np.abs(p["b2"]))
-    e3 = e2 @ A3.T + 66 * G * ((s["h2"] + e2) @ A3.T + np.abs(p["b3"]))
+    h2_pre = np.maximum(s["z2"], 0.0)
+    eh2 = flip_step(h2_pre, e2)
+    e3 = eh2 @ A3.T + 66 * G * (s["h2"] @ A3.T + np.abs(p["b3"]))
     keep = np.all(np.abs(s["z1"]) > 2 * e1, axis=1) & np.all(np.abs(s["z2"]) > 2 * e2, axis=1)
-    return dict(r=r, e3=e3, keep=keep, e1=e1, e2=e2, eh1=eh1, **s)
+    return dict(r=r, e3=e3, keep=keep, e1=e1, e2=e2, eh1=eh1, eh2=eh2, **s)
 
 
 def gradient_reference(theta_b, f, base, target):
@@ -100,11 +102,11 @@ def gradient_reference(theta_b, f, base, target):
     ed1q = flip_step(d1, ed1)
     d1q = q(d1)
     eh1 = fw["eh1"]
-    e2 = fw["e2"]
+    eh2 = fw["eh2"]
     fa = np.abs(np.asarray(f, np.float64))
     acc = LAMBDA * np.sqrt(M) * G          # the sums over samples
     bound = {
-        "W3": ed3.T @ (h2 + e2) + np.abs(d3).T @ e2 + acc * (np.abs(d3).T @ h2),
+        "W3": ed3.T @ (h2 + eh2) + np.abs(d3).T @ eh2 + acc * (np.abs(d3).T @ h2),
         "b3": ed3.sum(0) + acc * np.abs(d3).sum(0),
         "W2": ed2q.T @ (h1 + eh1) + np.abs(d2q).T @ eh1 + acc * (np.abs(d2q).T @ h1),
         "b2": ed2q.sum(0) + acc * np.abs(d2q).sum(0),

@@ -1,5 +1,6 @@
 """The comparison rules of helpers_mlp hold for an emulation of the kernels'
-precision in numpy (BF16 narrowing where the kernels narrow, FP32 sums in
+precision in numpy (BF16 narrowing where the kernels narrow: features, h1, h2,
+d2, d1; FP32 sums in
 another order), and they are tight enough to catch plausible kernel mistakes
 (a dropped bias, a transposed W2, a feature slot off by one)."""
 import numpy as np
@@ -17,7 +18,7 @@ def _emulate(theta, f, base=None, target=None, transpose_w2=False, drop_b2=False
     z1 = (fb @ bf(p["W1"]).T).astype(np.float32) + p["b1"]
     h1 = bf(np.maximum(z1, 0))
     z2 = (h1 @ bf(p["W2"]).T).astype(np.float32) + (0 if drop_b2 else p["b2"])
-    h2 = np.maximum(z2, 0)
+    h2 = bf(np.maximum(z2, 0))
     r = (h2 @ bf(p["W3"]).T).astype(np.float32) + p["b3"]
     out = dict(r=r, z1=z1, z2=z2)
     if base is not None:
