@@ -339,23 +339,19 @@ __global__ void __launch_bounds__(kThreads, 5) k_mlp_upscale(const float* __rest
         // layer 1 epilogue: h1 = relu(z1 + b1) as the BF16 row of A (the MMA
         // that read the features is complete)
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            float z[16];
-            tmem_ld16(tmem + lane + 16 * g, z);
+        for (int g = 0; g < 4; g += 2) {      // two loads in flight per wait
+            float z[2][16];
+            tmem_ld16(tmem + lane + 16 * g, z[0]);
+            tmem_ld16(tmem + lane + 16 * g + 16, z[1]);
             tmem_wait_ld();
 #pragma unroll
-            for (int k4 = 0; k4 < 4; ++k4) {
-                const float4 b = s.b1[4 * g + k4];
-                z[4 * k4] = fmaxf(z[4 * k4] + b.x, 0.f);
-                z[4 * k4 + 1] = fmaxf(z[4 * k4 + 1] + b.y, 0.f);
-                z[4 * k4 + 2] = fmaxf(z[4 * k4 + 2] + b.z, 0.f);
-                z[4 * k4 + 3] = fmaxf(z[4 * k4 + 3] + b.w, 0.f);
+            for (int h = 0; h < 2; ++h) {
+                uint32_t w[8];
+                bias_relu_bf16(z[h], s.b1 + 4 * (g + h), w);
+                *reinterpret_cast<uint4*>(s.a + kmaj(tid, 16 * (g + h), kSbo64)) = make_uint4(w[0], w[1], w[2], w[3]);
+                *reinterpret_cast<uint4*>(s.a + kmaj(tid, 16 * (g + h) + 8, kSbo64)) =
+                    make_uint4(w[4], w[5], w[6], w[7]);
             }
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-                *reinterpret_cast<uint4*>(s.a + kmaj(tid, 16 * g + 8 * h, kSbo64)) =
-                    make_uint4(pack_bf16x2(z[8 * h], z[8 * h + 1]), pack_bf16x2(z[8 * h + 2], z[8 * h + 3]),
-                               pack_bf16x2(z[8 * h + 4], z[8 * h + 5]), pack_bf16x2(z[8 * h + 6], z[8 * h + 7]));
         }
         fence_async_smem();
         fence_before_sync();
@@ -372,23 +368,19 @@ __global__ void __launch_bounds__(kThreads, 5) k_mlp_upscale(const float* __rest
         // layer 2 epilogue: h2 = relu(z2 + b2) as the BF16 row of A (the MMA
         // that read h1 is complete)
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            float z[16];
-            tmem_ld16(tmem + lane + 16 * g, z);
+        for (int g = 0; g < 4; g += 2) {      // two loads in flight per wait
+            float z[2][16];
+            tmem_ld16(tmem + lane + 16 * g, z[0]);
+            tmem_ld16(tmem + lane + 16 * g + 16, z[1]);
             tmem_wait_ld();
 #pragma unroll
-            for (int k4 = 0; k4 < 4; ++k4) {
-                const float4 b = s.b2[4 * g + k4];
-                z[4 * k4] = fmaxf(z[4 * k4] + b.x, 0.f);
-                z[4 * k4 + 1] = fmaxf(z[4 * k4 + 1] + b.y, 0.f);
-                z[4 * k4 + 2] = fmaxf(z[4 * k4 + 2] + b.z, 0.f);
-                z[4 * k4 + 3] = fmaxf(z[4 * k4 + 3] + b.w, 0.f);
+            for (int h = 0; h < 2; ++h) {
+                uint32_t w[8];
+                bias_relu_bf16(z[h], s.b2 + 4 * (g + h), w);
+                *reinterpret_cast<uint4*>(s.a + kmaj(tid, 16 * (g + h), kSbo64)) = make_uint4(w[0], w[1], w[2], w[3]);
+                *reinterpret_cast<uint4*>(s.a + kmaj(tid, 16 * (g + h) + 8, kSbo64)) =
+                    make_uint4(w[4], w[5], w[6], w[7]);
             }
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-                *reinterpret_cast<uint4*>(s.a + kmaj(tid, 16 * g + 8 * h, kSbo64)) =
-                    make_uint4(pack_bf16x2(z[8 * h], z[8 * h + 1]), pack_bf16x2(z[8 * h + 2], z[8 * h + 3]),
-                               pack_bf16x2(z[8 * h + 4], z[8 * h + 5]), pack_bf16x2(z[8 * h + 6], z[8 * h + 7]));
         }
         fence_async_smem();
         fence_before_sync();

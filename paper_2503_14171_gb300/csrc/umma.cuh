@@ -172,5 +172,40 @@ __device__ __forceinline__ float bf16_round(float x)
     return __uint_as_float(pack_bf16x2(x, 0.f) << 16);
 }
 
+// relu then round to nearest even, two values in one conversion
+__device__ __forceinline__ uint32_t pack_relu_bf16x2(float lo, float hi)
+{
+    uint32_t r;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
+// (a.x + b.x, a.y + b.y), each rounded to nearest, in one packed FP32 add
+__device__ __forceinline__ float2 add_f32x2(float ax, float ay, float bx, float by)
+{
+    float2 r;
+    asm("{\n\t.reg .b64 x, y, z;\n\t"
+        "mov.b64 x, {%2, %3};\n\t"
+        "mov.b64 y, {%4, %5};\n\t"
+        "add.rn.f32x2 z, x, y;\n\t"
+        "mov.b64 {%0, %1}, z;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(ax), "f"(ay), "f"(bx), "f"(by));
+    return r;
+}
+
+// bias + relu + BF16 of 16 accumulator columns: 8 packed words
+__device__ __forceinline__ void bias_relu_bf16(const float (&z)[16], const float4* b, uint32_t (&w)[8])
+{
+#pragma unroll
+    for (int k4 = 0; k4 < 4; ++k4) {
+        const float4 bb = b[k4];
+        const float2 u0 = add_f32x2(z[4 * k4], z[4 * k4 + 1], bb.x, bb.y);
+        const float2 u1 = add_f32x2(z[4 * k4 + 2], z[4 * k4 + 3], bb.z, bb.w);
+        w[2 * k4] = pack_relu_bf16x2(u0.x, u0.y);
+        w[2 * k4 + 1] = pack_relu_bf16x2(u1.x, u1.y);
+    }
+}
+
 }  // namespace umma
 }  // namespace gs
