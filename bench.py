@@ -792,8 +792,10 @@ def stereo_views(seed=0, pairs=8, lo=(512, 512), hi=(1104, 1032), ipd=0.064):
 
 def views_leg(torch, gs, scenes, stream, n_list=(300_000, 800_000, 2_000_000), reps=20):
     """Batched multi-view rendering (16 stereo views, each eye rendered at half
-    size with derivatives and upscaled 2x) against the same views one at a
-    time; both recorded as CUDA graphs.  Output megapixels per second."""
+    size with derivatives and upscaled 2x; one projection, one blend and one
+    upscale launch for all views, the blend's launch shape from the autotuner)
+    against the same views one at a time; both recorded as CUDA graphs.  Output
+    megapixels per second."""
     camdefs, eyes = stereo_views()
     V = len(eyes)
     lows = [(W // 2, H // 2) for W, H in eyes]
@@ -833,6 +835,9 @@ def views_leg(torch, gs, scenes, stream, n_list=(300_000, 800_000, 2_000_000), r
             with torch.cuda.stream(stream):
                 body()
                 torch.cuda.synchronize()
+                if mode == "batched":
+                    # launch shape of the batched blend: the project's autotuner on this batch
+                    tune_ms, tune_best = ctx.autotune_views(dev, cams, lows, [2] * V, outs, reps=5)
                 g = torch.cuda.CUDAGraph()
                 with torch.cuda.graph(g, stream=stream):
                     body()
@@ -852,7 +857,11 @@ def views_leg(torch, gs, scenes, stream, n_list=(300_000, 800_000, 2_000_000), r
         res["scenes"][str(n)] = {"batched_ms": timings["batched"], "per_view_ms": timings["per_view"],
                                  "batched_mpix_s": out_mpix / timings["batched"] * 1e3,
                                  "per_view_mpix_s": out_mpix / timings["per_view"] * 1e3,
-                                 "speedup": timings["per_view"] / timings["batched"]}
+                                 "speedup": timings["per_view"] / timings["batched"],
+                                 "autotune_ms": [round(t, 4) for t in tune_ms],
+                                 "autotune_best": {"config": tune_best, "warp_map": tune_best % 2,
+                                                   "schedule": ["tile order", "heaviest first",
+                                                                "persistent"][tune_best // 2]}}
         del dev
         torch.cuda.empty_cache()
     return res

@@ -156,16 +156,19 @@ gs_status gs_set_options(gs_ctx* ctx, const gs_options* opt);
 gs_status gs_reserve(gs_ctx* ctx, int64_t n, int32_t W, int32_t H, int64_t super_pairs);
 
 /* gs_reserve plus the per-view buffers of gs_render_views for up to V views
+ * (super_pairs is then the capacity of each view's pair buffers)
  * (1 <= V <= 32) of up to n Gaussians; W, H, super_pairs bound every view. */
 gs_status gs_reserve_views(gs_ctx* ctx, int64_t n, int32_t V, int32_t W, int32_t H, int64_t super_pairs);
 
 /* Several views of one Gaussian set in one batch (e.g. the stereo pairs of a
  * VR headset, which the paper names as a use of cheap upscaling): one launch
  * projects every view (each Gaussian's inputs, SH coefficients included, are
- * read once for all views), then each view is depth-sorted, binned, blended
- * with derivatives into out_C[v] [3][H_v][W_v] and out_grads[v]
- * [3][3][H_v][W_v], and, where out_up != NULL and out_up[v] != NULL, upscaled
- * by factors[v] into out_up[v].  View v uses cams[v], Ws[v] x Hs[v]; each view
+ * read once for all views), then each view is depth-sorted and binned into
+ * buffers of its own; one launch blends every tile of every view with
+ * derivatives into out_C[v] [3][H_v][W_v] and out_grads[v] [3][3][H_v][W_v]
+ * (launch shape from gs_views_config / gs_autotune_views), and one launch
+ * upscales, where out_up != NULL and out_up[v] != NULL, by factors[v] into
+ * out_up[v].  View v uses cams[v], Ws[v] x Hs[v]; each view
  * equals a single-view gs_render_with_grads of the same camera bit for bit.
  * Requires GS_FLAG_NO_HOST_WAIT and gs_reserve_views; makes no host-blocking
  * call (capturable in a CUDA graph); a view beyond the reserved pairs renders
@@ -176,6 +179,25 @@ gs_status gs_reserve_views(gs_ctx* ctx, int64_t n, int32_t V, int32_t W, int32_t
 gs_status gs_render_views(gs_ctx* ctx, const gs_gaussians* g, int32_t V, const gs_camera* cams, const int32_t* Ws,
                           const int32_t* Hs, float* const* out_C, float* const* out_grads, const int32_t* factors,
                           float* const* out_up);
+
+/* Tuning of gs_render_views (the launch shapes of its batched blend; the
+ * images do not depend on them, bit for bit).  warp_map: the pixels of each
+ * warp of a 16 x 16 tile, 0 = an 8 x 4 block, 1 = a 16 x 2 strip.  schedule:
+ * 0 = one block per tile in tile order, 1 = one block per tile, the heaviest
+ * tiles of the previous batch first, 2 = resident blocks taking tiles from a
+ * counter.  Default (0, 1). */
+#define GS_VIEWS_CONFIGS 6   /* configuration k: warp_map = k % 2, schedule = k / 2 */
+gs_status gs_views_config(gs_ctx* ctx, int32_t warp_map, int32_t schedule);
+
+/* Autotuner: renders the batch of gs_render_views (same arguments) once
+ * untimed and `reps` times timed (CUDA events on the context's stream) in each
+ * of the GS_VIEWS_CONFIGS configurations, keeps the fastest in the context and
+ * returns the mean milliseconds per batch of each configuration in ms[k] (host
+ * float[GS_VIEWS_CONFIGS], may be NULL) and the chosen k in *best (may be
+ * NULL).  Synchronises; not for use inside a CUDA graph capture. */
+gs_status gs_autotune_views(gs_ctx* ctx, const gs_gaussians* g, int32_t V, const gs_camera* cams, const int32_t* Ws,
+                            const int32_t* Hs, float* const* out_C, float* const* out_grads, const int32_t* factors,
+                            float* const* out_up, int32_t reps, float* ms, int32_t* best);
 
 /* Projection and tile binning for a W x H image (Sec. 4: EWA projection
  * Sigma' = J W Sigma W^T J^T + 0.3 I, front-to-back order).  Per Gaussian: view

@@ -32,6 +32,7 @@ GS_MODE_3DGS = 0
 GS_MODE_EXACT = 1
 MODES = {"3dgs": GS_MODE_3DGS, "exact": GS_MODE_EXACT}
 GS_FLAG_NO_HOST_WAIT = 1
+GS_VIEWS_CONFIGS = 6
 GS_MLP_IN = 50
 GS_MLP_HIDDEN = 64
 GS_MLP_PARAMS = 7619
@@ -73,6 +74,10 @@ _SIGS = {
     "gs_render_views": ([_P, ct.POINTER(GsGaussians), ct.c_int32, ct.POINTER(GsCamera), ct.POINTER(ct.c_int32),
                          ct.POINTER(ct.c_int32), ct.POINTER(_P), ct.POINTER(_P), ct.POINTER(ct.c_int32),
                          ct.POINTER(_P)], ct.c_int),
+    "gs_views_config": ([_P, ct.c_int32, ct.c_int32], ct.c_int),
+    "gs_autotune_views": ([_P, ct.POINTER(GsGaussians), ct.c_int32, ct.POINTER(GsCamera), ct.POINTER(ct.c_int32),
+                           ct.POINTER(ct.c_int32), ct.POINTER(_P), ct.POINTER(_P), ct.POINTER(ct.c_int32),
+                           ct.POINTER(_P), ct.c_int32, ct.POINTER(ct.c_float), ct.POINTER(ct.c_int32)], ct.c_int),
     "gs_project": ([_P, ct.POINTER(GsGaussians), ct.POINTER(GsCamera), ct.c_int32, ct.c_int32], ct.c_int),
     "gs_render_binned": ([_P, _P, _P], ct.c_int),
     "gs_render_with_grads": ([_P, ct.POINTER(GsGaussians), ct.POINTER(GsCamera), ct.c_int32, ct.c_int32, _P, _P],
@@ -330,6 +335,13 @@ class Context:
                 if factors is not None:
                     o.append(self._empty(3, H * factors[v], W * factors[v]))
                 outs.append(o)
+        _chk(lib.gs_render_views(self.h, ct.byref(scene.struct), V, *self._views_args(cams, sizes, factors, outs)),
+             self.h, "gs_render_views")
+        return outs
+
+    @staticmethod
+    def _views_args(cams, sizes, factors, outs):
+        V = len(cams)
         cam_arr = (GsCamera * V)(*[make_camera(c) for c in cams])
         Ws = (ct.c_int32 * V)(*[int(w) for w, _ in sizes])
         Hs = (ct.c_int32 * V)(*[int(h) for _, h in sizes])
@@ -337,9 +349,21 @@ class Context:
         pG = (_P * V)(*[o[1].data_ptr() for o in outs])
         fac = (ct.c_int32 * V)(*[int(f) for f in factors]) if factors is not None else None
         pU = (_P * V)(*[o[2].data_ptr() for o in outs]) if factors is not None else None
-        _chk(lib.gs_render_views(self.h, ct.byref(scene.struct), V, cam_arr, Ws, Hs, pC, pG, fac, pU), self.h,
-             "gs_render_views")
-        return outs
+        return cam_arr, Ws, Hs, pC, pG, fac, pU
+
+    def views_config(self, warp_map: int, schedule: int):
+        """Launch shape of the batched blend of render_views (see gs_views_config)."""
+        _chk(lib.gs_views_config(self.h, int(warp_map), int(schedule)), self.h, "gs_views_config")
+
+    def autotune_views(self, scene: DeviceScene, cams: list, sizes: list, factors, outs, reps: int = 5):
+        """Time every launch shape of the batched blend on this batch, keep the
+        fastest; returns (ms per configuration, chosen configuration)."""
+        ms = (ct.c_float * GS_VIEWS_CONFIGS)()
+        best = ct.c_int32()
+        _chk(lib.gs_autotune_views(self.h, ct.byref(scene.struct), len(cams),
+                                   *self._views_args(cams, sizes, factors, outs), int(reps), ms, ct.byref(best)),
+             self.h, "gs_autotune_views")
+        return list(ms), int(best.value)
 
     def set_options(self, mode=None, bg=None, max_pairs=None):
         if mode is not None:

@@ -500,7 +500,7 @@ gs_status gs_destroy(gs_ctx* c)
                       &c->sort_counter, &c->sranges, &c->tile_count, &c->tile_start, &c->state, &c->count,
                       &c->errword, &c->grad2d, &c->up_planes, &c->pair_check, &c->tile_work, &c->tile_order,
                       &c->vrec0, &c->vrec1, &c->vrec2, &c->vrect, &c->vsupers, &c->vkey, &c->vtotals,
-                      &c->views_dev};
+                      &c->views_dev, &c->vpairs0, &c->vpairs1, &c->vsranges, &c->vwork, &c->vorder, &c->vqueue};
     for (DevBuf* b : bufs) release(*b);
     if (c->h_scalar) cudaFreeHost(c->h_scalar);
     if (c->totals_ready) cudaEventDestroy(c->totals_ready);
@@ -869,8 +869,15 @@ gs_status reserve_impl(gs_ctx* c, int64_t n, int32_t V, int32_t W, int32_t H, in
             (st = ensure(c, c->vrec2, sizeof(float4) * vn)) || (st = ensure(c, c->vrect, sizeof(ushort4) * vn)) ||
             (st = ensure(c, c->vsupers, sizeof(uint32_t) * vn)) || (st = ensure(c, c->vkey, sizeof(uint32_t) * vn)) ||
             (st = ensure(c, c->vtotals, sizeof(unsigned long long) * 2 * kTotalSlots * (size_t)V)) ||
-            (st = ensure(c, c->views_dev, sizeof(ViewDesc) * kMaxViews)))
+            (st = ensure(c, c->views_dev, sizeof(ViewDesc) * kMaxViews)) ||
+            (st = ensure(c, c->vpairs0, sizeof(uint64_t) * (size_t)super_pairs * V)) ||
+            (st = ensure(c, c->vpairs1, sizeof(uint64_t) * (size_t)super_pairs * V)) ||
+            (st = ensure(c, c->vsranges, sizeof(uint2) * (size_t)Ts * V)) ||
+            (st = ensure(c, c->vwork, sizeof(uint32_t) * (size_t)T * V)) ||
+            (st = ensure(c, c->vorder, sizeof(uint32_t) * (size_t)T * V)) ||
+            (st = ensure(c, c->vqueue, sizeof(uint32_t))))
             return st;
+        GS_CUDA(c, cudaMemsetAsync(c->vwork.p, 0, sizeof(uint32_t) * (size_t)T * V, c->stream));
     }
     GS_CUDA(c, cudaStreamSynchronize(c->stream));
     c->res_views = V;
@@ -947,14 +954,21 @@ gs_status gs_render_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_
     vo.totals = vtot;
     GS_CUDA(c, launch_project_views(s, *g, as<ViewDesc>(c->views_dev), V, c->opt.mode, vo));
 
-    // then each view: depth order, emission, pair check and sort, blend (and upscale)
+    // then each view: depth order, emission, pair check and sort into its own
+    // pair and range buffers; then the blends of all views in one launch and
+    // the upscales of all views in one launch
     const uint32_t ds_cap = n > 1 ? depth_sort_capacity(c->device) : 0u;
     const bool persistent = n > 1 && n <= ds_cap && n <= kDsMaxN;
     const size_t G = ds_cap / kDsMaxSlice;
     const uint32_t cap = (uint32_t)c->res_pairs;
     const int64_t limit = c->opt.max_pairs > 0 ? std::min<int64_t>(c->opt.max_pairs, kMaxPairs) : kMaxPairs;
-    uint64_t* pairs[2] = {as<uint64_t>(c->pairs[0]), as<uint64_t>(c->pairs[1])};
     PairCheckOut* chk = as<PairCheckOut>(c->pair_check);
+    BlendViews bv;
+    bv.V = V;
+    bv.start[0] = 0;
+    UpscaleViews uv;
+    uv.V = 0;
+    uv.start[0] = 0;
     for (int v = 0; v < V; ++v) {
         const ViewDesc& d = batch.v[v];
         const int stiles_x = (d.tiles_x + kSuper - 1) / kSuper, stiles_y = (d.tiles_y + kSuper - 1) / kSuper;
@@ -965,6 +979,8 @@ gs_status gs_render_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_
         uint32_t* keys_v = as<uint32_t>(c->vkey) + off;
         uint32_t* supers_v = as<uint32_t>(c->vsupers) + off;
         const ushort4* rect_v = as<ushort4>(c->vrect) + off;
+        uint64_t* pairs[2] = {as<uint64_t>(c->vpairs0) + (size_t)v * cap, as<uint64_t>(c->vpairs1) + (size_t)v * cap};
+        uint2* sranges_v = as<uint2>(c->vsranges) + (size_t)v * c->res_supers;
         uint32_t* keys[2] = {as<uint32_t>(c->dkey[0]), as<uint32_t>(c->dkey[1])};
         uint32_t* ids[2] = {as<uint32_t>(c->did[0]), as<uint32_t>(c->did[1])};
         GS_CUDA(c, cudaMemsetAsync(c->super_counts.p, 0, sizeof(uint32_t) * kCountCopies * Ts, s));
@@ -995,7 +1011,7 @@ gs_status gs_render_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_
         GS_CUDA(c, launch_emit_pairs(s, ids[sorted], as<uint32_t>(c->offsets), rect_v, n, stiles_x, pairs[0],
                                      as<uint32_t>(c->super_counts), Ts, cap));
         GS_CUDA(c, launch_supers_to_hist(s, as<uint32_t>(c->super_counts), Ts, spasses, as<uint32_t>(c->sort_hist),
-                                         as<uint2>(c->sranges),
+                                         sranges_v,
                                          PairCheckIn{vtot + (size_t)v * 2 * kTotalSlots, cap,
                                                      (unsigned long long)limit},
                                          chk, as<int>(c->errword)));
@@ -1004,14 +1020,14 @@ gs_status gs_render_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_
             GS_CUDA(c, radix_sort_u64_keys(s, pairs, cap, 32, 32 + sbits, as<uint32_t>(c->sort_hist),
                                            as<uint32_t>(c->sort_status), as<uint32_t>(c->sort_counter),
                                            as<int>(c->errword), &psorted, true, &chk->count, false));
-        BlendArgs a;
+        BlendArgs& a = bv.a[v];
         a.W = d.W;
         a.H = d.H;
         a.tiles_x = d.tiles_x;
         a.tiles_y = d.tiles_y;
         a.stiles_x = stiles_x;
         a.n = n;
-        a.sranges = as<uint2>(c->sranges);
+        a.sranges = sranges_v;
         a.pair_words = reinterpret_cast<const uint32_t*>(pairs[psorted]);
         a.rect = rect_v;
         a.rec = Records{as<float4>(c->vrec0) + off, as<float4>(c->vrec1) + off, as<float4>(c->vrec2) + off};
@@ -1022,12 +1038,89 @@ gs_status gs_render_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_
         a.count = nullptr;
         a.order = nullptr;
         a.work = nullptr;
-        GS_CUDA(c, launch_blend(s, true, c->opt.mode, a));
-        if (out_up && out_up[v])
-            GS_CUDA(c, launch_upscale(s, out_C[v], out_grads[v], d.W, d.H, factors[v], out_up[v]));
+        bv.start[v + 1] = bv.start[v] + d.tiles_x * d.tiles_y;
+        if (out_up && out_up[v]) {
+            UpscaleView& u = uv.v[uv.V];
+            u.C = out_C[v];
+            u.G = out_grads[v];
+            u.W = d.W;
+            u.H = d.H;
+            u.W2 = d.W * factors[v];
+            u.H2 = d.H * factors[v];
+            u.out = out_up[v];
+            uv.start[uv.V + 1] = uv.start[uv.V] + upscale_tiles(u.W2, u.H2);
+            ++uv.V;
+        }
     }
+    const int total = bv.start[V];
+    bv.work = as<uint32_t>(c->vwork);
+    bv.queue = as<uint32_t>(c->vqueue);
+    bv.order = nullptr;
+    if (c->views_sched == 1) {   // heaviest tiles of the last batch first
+        GS_CUDA(c, launch_tile_order(s, as<uint32_t>(c->vwork), (uint32_t)total, as<uint32_t>(c->vorder)));
+        bv.order = as<uint32_t>(c->vorder);
+    }
+    GS_CUDA(c, launch_blend_views(s, c->opt.mode, bv, c->views_map, c->views_sched == 2));
+    if (uv.V > 0) GS_CUDA(c, launch_upscale_views(s, uv));
     c->totals_known = false;
     return GS_OK;
+}
+
+gs_status gs_views_config(gs_ctx* c, int32_t warp_map, int32_t schedule)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (warp_map < 0 || warp_map > 1 || schedule < 0 || schedule > 2)
+        return fail(c, GS_ERR_INVALID_ARG, "warp_map in {0, 1}, schedule in {0, 1, 2}");
+    c->views_map = warp_map;
+    c->views_sched = schedule;
+    return GS_OK;
+}
+
+gs_status gs_autotune_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_camera* cams, const int32_t* Ws,
+                            const int32_t* Hs, float* const* out_C, float* const* out_grads, const int32_t* factors,
+                            float* const* out_up, int32_t reps, float* ms, int32_t* best)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (reps < 1) return fail(c, GS_ERR_INVALID_ARG, "reps must be >= 1");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    GS_CUDA(c, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(c, GS_ERR_CUDA, "cudaEventCreate failed");
+    }
+    float best_ms = 0.f;
+    int best_k = -1;
+    gs_status st = GS_OK;
+    for (int k = 0; k < GS_VIEWS_CONFIGS && st == GS_OK; ++k) {
+        c->views_map = k & 1;
+        c->views_sched = k >> 1;
+        // one untimed batch: first use of the variant, and tile durations for schedule 1
+        st = gs_render_views(c, g, V, cams, Ws, Hs, out_C, out_grads, factors, out_up);
+        if (st != GS_OK) break;
+        if (cudaEventRecord(e0, c->stream) != cudaSuccess) { st = fail(c, GS_ERR_CUDA, "event"); break; }
+        for (int r = 0; r < reps && st == GS_OK; ++r)
+            st = gs_render_views(c, g, V, cams, Ws, Hs, out_C, out_grads, factors, out_up);
+        if (st != GS_OK) break;
+        float t = 0.f;
+        if (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
+            st = fail(c, GS_ERR_CUDA, "event timing failed");
+            break;
+        }
+        t /= (float)reps;
+        if (ms) ms[k] = t;
+        if (best_k < 0 || t < best_ms) {
+            best_ms = t;
+            best_k = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != GS_OK) return st;
+    c->views_map = best_k & 1;
+    c->views_sched = best_k >> 1;
+    if (best) *best = best_k;
+    return read_device_error(c);
 }
 
 gs_status gs_read_projected(gs_ctx* c, float* mean2d, float* conic, float* rgb, float* opacity, float* depth,

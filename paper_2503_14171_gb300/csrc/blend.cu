@@ -28,6 +28,8 @@
 //   C += c w, C_x += c w_x, C_y += c w_y, C_xy += c w_xy
 //   T *= (1 - alpha), T_x -= w_x, T_y -= w_y, T_xy -= w_xy
 // (identical to B_i, A_i and their derivatives in the supplement, T = 1 - A).
+#include <algorithm>
+
 #include "blend_common.cuh"
 
 namespace gs {
@@ -123,25 +125,27 @@ __device__ __forceinline__ void store(const BlendArgs& a, const PixelState& p, i
     if (a.count) a.count[pix] = p.last;
 }
 
-// STATS: count the (pixel, Gaussian) pairs evaluated (every list entry a pixel
-// passes before it stops, the oracle's count) and blended, instead of writing
-// images (used once, outside timed regions, to size the FLOP count).
-template <bool GRADS, int MODE, bool STATS = false>
-__global__ void __launch_bounds__(kThreads) k_blend(BlendArgs a, unsigned long long* __restrict__ stats = nullptr)
+// One tile of a blend.  STATS: count the (pixel, Gaussian) pairs evaluated
+// (every list entry a pixel passes before it stops, the oracle's count) and
+// blended, instead of writing images (used once, outside timed regions, to
+// size the FLOP count).  MAP: the pixels of each warp, 0 = an 8 x 4 block
+// (two blocks across, four down: a compact block makes the lanes of a warp
+// agree more often on whether a Gaussian reaches them), 1 = a 16 x 2 strip.
+// work_slot, when given, receives the tile's duration (clock64 / 16).
+template <bool GRADS, int MODE, bool STATS, int MAP>
+__device__ __forceinline__ void blend_tile(const BlendArgs& a, int tile, unsigned long long* __restrict__ stats,
+                                           uint32_t* work_slot)
 {
     __shared__ float4 s_r0[kStage];
     __shared__ float4 s_r1[kStage];
     __shared__ float4 s_r2[kStage];
     __shared__ int s_wcnt[kWarps];
 
-    const int tile = a.order ? (int)a.order[blockIdx.x] : (int)blockIdx.x;
     const long long t_start = clock64();
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // each warp covers an 8 x 4 block of the tile (two blocks across, four
-    // down): a compact block makes the lanes of a warp agree more often on
-    // whether a Gaussian reaches them
-    const int lx = ((warp & 1) << 3) | (lane & 7), ly = ((warp >> 1) << 2) | (lane >> 3);
+    const int lx = MAP == 0 ? ((warp & 1) << 3) | (lane & 7) : lane & 15;
+    const int ly = MAP == 0 ? ((warp >> 1) << 2) | (lane >> 3) : (warp << 1) | (lane >> 4);
     const int x = tx * kTile + lx, y = ty * kTile + ly;
     const float px = (float)x, py = (float)y;
     const uint32_t lanemask_lt = (1u << lane) - 1u;
@@ -218,14 +222,53 @@ __global__ void __launch_bounds__(kThreads) k_blend(BlendArgs a, unsigned long l
         }
         return;
     }
-    if (a.work && threadIdx.x == 0) a.work[tile] = (uint32_t)min((clock64() - t_start) >> 4, 0xFFFFFFFFll);
+    if (work_slot && threadIdx.x == 0) *work_slot = (uint32_t)min((clock64() - t_start) >> 4, 0xFFFFFFFFll);
     if (x < a.W && y < a.H) store<GRADS>(a, p, x, y);
+}
+
+template <bool GRADS, int MODE, bool STATS = false>
+__global__ void __launch_bounds__(kThreads, 4) k_blend(BlendArgs a, unsigned long long* __restrict__ stats = nullptr)
+{
+    const int tile = a.order ? (int)a.order[blockIdx.x] : (int)blockIdx.x;
+    blend_tile<GRADS, MODE, STATS, 0>(a, tile, stats, a.work ? a.work + tile : nullptr);
+}
+
+// The tiles of every view of a batch in one launch: job j is global tile
+// order[j] (or j), the tiles of view v being start[v] .. start[v + 1] - 1.
+// PERSIST: a grid of resident blocks takes jobs from a counter in turn;
+// otherwise one block per job.
+template <bool GRADS, int MODE, int MAP, bool PERSIST>
+__global__ void __launch_bounds__(kThreads, 4) k_blend_views(const __grid_constant__ BlendViews b)
+{
+    __shared__ int s_job;
+    const int total = b.start[b.V];
+    for (int j = PERSIST ? -1 : (int)blockIdx.x;;) {
+        if (PERSIST) {
+            __syncthreads();          // the previous tile's shared state is no longer read
+            if (threadIdx.x == 0) s_job = (int)atomicAdd(b.queue, 1u);
+            __syncthreads();
+            j = s_job;
+            if (j >= total) break;
+        }
+        const int g = b.order ? (int)b.order[j] : j;
+        int v = 0;
+        while (v + 1 < b.V && g >= b.start[v + 1]) ++v;
+        blend_tile<GRADS, MODE, false, MAP>(b.a[v], g - b.start[v], nullptr, b.work ? b.work + g : nullptr);
+        if (!PERSIST) break;
+    }
 }
 
 template <bool GRADS, int MODE>
 cudaError_t launch_t(cudaStream_t s, const BlendArgs& a)
 {
     k_blend<GRADS, MODE><<<a.tiles_x * a.tiles_y, kThreads, 0, s>>>(a); note_launch();
+    return cudaGetLastError();
+}
+
+template <int MODE, int MAP, bool PERSIST>
+cudaError_t launch_views_t(cudaStream_t s, const BlendViews& b, int grid)
+{
+    k_blend_views<true, MODE, MAP, PERSIST><<<grid, kThreads, 0, s>>>(b); note_launch();
     return cudaGetLastError();
 }
 
@@ -240,6 +283,39 @@ cudaError_t launch_blend_stats(cudaStream_t s, int mode, const BlendArgs& a, uns
         k_blend<true, GS_MODE_3DGS, true><<<tiles, kThreads, 0, s>>>(a, stats);
     note_launch();
     return cudaGetLastError();
+}
+
+cudaError_t launch_blend_views(cudaStream_t s, int mode, const BlendViews& b, int map, bool persistent)
+{
+    const int total = b.start[b.V];
+    if (total <= 0) return cudaSuccess;
+    int grid = total;
+    if (persistent) {
+        // resident blocks: as many as fit (blocks per SM by the occupancy calculator)
+        int dev = 0, sms = 1, per_sm = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (mode == GS_MODE_EXACT)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, map ? k_blend_views<true, GS_MODE_EXACT, 1, true>
+                                                                       : k_blend_views<true, GS_MODE_EXACT, 0, true>,
+                                                          kThreads, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, map ? k_blend_views<true, GS_MODE_3DGS, 1, true>
+                                                                       : k_blend_views<true, GS_MODE_3DGS, 0, true>,
+                                                          kThreads, 0);
+        grid = std::min(total, std::max(1, sms * std::max(1, per_sm)));
+        cudaError_t e = cudaMemsetAsync(b.queue, 0, sizeof(uint32_t), s);
+        if (e != cudaSuccess) return e;
+    }
+    if (mode == GS_MODE_EXACT) {
+        if (persistent) return map ? launch_views_t<GS_MODE_EXACT, 1, true>(s, b, grid)
+                                   : launch_views_t<GS_MODE_EXACT, 0, true>(s, b, grid);
+        return map ? launch_views_t<GS_MODE_EXACT, 1, false>(s, b, grid)
+                   : launch_views_t<GS_MODE_EXACT, 0, false>(s, b, grid);
+    }
+    if (persistent) return map ? launch_views_t<GS_MODE_3DGS, 1, true>(s, b, grid)
+                               : launch_views_t<GS_MODE_3DGS, 0, true>(s, b, grid);
+    return map ? launch_views_t<GS_MODE_3DGS, 1, false>(s, b, grid) : launch_views_t<GS_MODE_3DGS, 0, false>(s, b, grid);
 }
 
 cudaError_t launch_blend(cudaStream_t s, bool grads, int mode, const BlendArgs& a)

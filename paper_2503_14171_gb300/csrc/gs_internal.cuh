@@ -156,6 +156,12 @@ struct gs_ctx {
     gs::DevBuf vsupers, vkey;           // uint32[V][n]
     gs::DevBuf vtotals;                 // uint64[V][2 kTotalSlots]
     gs::DevBuf views_dev;               // gs::ViewDesc[kMaxViews]
+    gs::DevBuf vpairs0, vpairs1;        // uint64[V][res_pairs]: each view's pairs (sort ping-pong)
+    gs::DevBuf vsranges;                // uint2[V][res_supers]
+    gs::DevBuf vwork, vorder;           // uint32[V * res_tiles]: tile durations / order of the batch
+    gs::DevBuf vqueue;                  // uint32 job counter of the persistent batched blend
+    int views_map = 0;                  // batched blend: 0 = 8 x 4 warp blocks, 1 = 16 x 2
+    int views_sched = 1;                // 0 = tile order, 1 = heaviest first (last batch), 2 = persistent
     bool totals_known = true;           // P, Ps valid on the host
     gs::DevBuf up_planes;               // float[12][H][W] upstream planes of gs_backward
     unsigned long long* h_scalar = nullptr;   // pinned host scalar for the pair count
@@ -286,6 +292,22 @@ cudaError_t launch_unpack_projected(cudaStream_t s, Records rec, const int* radi
                                     float* opacity, float* depth, int32_t* radius_out, int32_t* tiles_out);
 
 cudaError_t launch_blend(cudaStream_t s, bool grads, int mode, const BlendArgs& a);
+
+// The derivative blends of a batch of views in one launch: view v's tiles are
+// global tiles start[v] .. start[v + 1] - 1 (its args' order/work unused); jobs
+// in the order `order` (optional), durations into `work` (optional).
+constexpr int kMaxBatchViews = 32;
+struct BlendViews {
+    BlendArgs a[kMaxBatchViews];
+    int start[kMaxBatchViews + 1];
+    int V;
+    const uint32_t* order;
+    uint32_t* work;
+    uint32_t* queue;   // job counter of the persistent variant
+};
+// map: the warp's pixels (0: 8 x 4 block, 1: 16 x 2 strip); persistent: resident
+// blocks taking tiles from a counter instead of one block per tile
+cudaError_t launch_blend_views(cudaStream_t s, int mode, const BlendViews& b, int map, bool persistent);
 // adjoint of the derivative blend (grad2d accumulated; zero it first)
 cudaError_t launch_blend_backward(cudaStream_t s, int mode, const BlendBwdArgs& a);
 // adjoint of the projection: grad2d [n][9] -> gradients of the inputs (overwritten)
@@ -305,6 +327,23 @@ cudaError_t launch_blend_stats(cudaStream_t s, int mode, const BlendArgs& a, uns
 
 cudaError_t launch_upscale(cudaStream_t s, const float* C, const float* grads, int W, int H, int factor,
                            float* out);
+
+// The spline upscales of a batch of views in one launch (view v's 64 x 16
+// output tiles are blocks start[v] .. start[v + 1] - 1; upscale_tiles gives
+// each view's count)
+struct UpscaleView {
+    const float* C;
+    const float* G;
+    int W, H, W2, H2;
+    float* out;
+};
+struct UpscaleViews {
+    UpscaleView v[kMaxBatchViews];
+    int start[kMaxBatchViews + 1];
+    int V;
+};
+int upscale_tiles(int W2, int H2);
+cudaError_t launch_upscale_views(cudaStream_t s, const UpscaleViews& b);
 
 // Learned residual on the spline (parameters: GS_MLP_PARAMS FP32 values, W1 b1 W2 b2 W3 b3)
 // spline + MLP residual at any output size W2 x H2 (tensor-core inference fused into the upscale)

@@ -41,20 +41,19 @@ constexpr int kFootH = kOutH + 2;
 
 // footprint bound of a 64 x 16 output tile: ceil(63 W / W2) + 2 columns,
 // ceil(15 H / H2) + 2 rows
-int foot_w(int W, int W2) { return std::min(kFootW, (int)((63ll * W + W2 - 1) / W2) + 2); }
-int foot_h(int H, int H2) { return std::min(kFootH, (int)((15ll * H + H2 - 1) / H2) + 2); }
+__host__ __device__ int foot_w(int W, int W2) { return min(kFootW, (int)((63ll * W + W2 - 1) / W2) + 2); }
+__host__ __device__ int foot_h(int H, int H2) { return min(kFootH, (int)((15ll * H + H2 - 1) / H2) + 2); }
 
-__global__ void __launch_bounds__(kThreadsX * kThreadsY) k_upscale(const float* __restrict__ Cimg,
-                                                                   const float* __restrict__ G, int W, int H,
-                                                                   int W2, int H2, int pitch,
-                                                                   float* __restrict__ out)
+// The 64 x 16 output tile at (X0, Y0) (one block)
+__device__ __forceinline__ void upscale_tile(const float* __restrict__ Cimg, const float* __restrict__ G, int W,
+                                             int H, int W2, int H2, int pitch, float* __restrict__ out, int X0,
+                                             int Y0)
 {
     // per low-res pixel of the footprint, its 12 values packed in 3 float4: [fy][fx][3]
     extern __shared__ float4 sm[];
     __shared__ float4 s_wx[kOutW];             // basis weights (h00, h01, h10, h11) per output column
     __shared__ float4 s_wy[kOutH];
     __shared__ int s_cx[kOutW], s_cy[kOutH];   // cell index relative to the footprint origin
-    const int X0 = blockIdx.x * kOutW, Y0 = blockIdx.y * kOutH;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * kThreadsX + tx;
 
@@ -144,6 +143,28 @@ __global__ void __launch_bounds__(kThreadsX * kThreadsY) k_upscale(const float* 
             out[2 * oplane + o] = bch;
         }
     }
+}
+
+__global__ void __launch_bounds__(kThreadsX * kThreadsY) k_upscale(const float* __restrict__ Cimg,
+                                                                   const float* __restrict__ G, int W, int H,
+                                                                   int W2, int H2, int pitch,
+                                                                   float* __restrict__ out)
+{
+    upscale_tile(Cimg, G, W, H, W2, H2, pitch, out, blockIdx.x * kOutW, blockIdx.y * kOutH);
+}
+
+// The upscales of a batch of views in one launch: block b takes tile b - start[v]
+// of view v (row-major over its tiles_x tiles per row).
+__global__ void __launch_bounds__(kThreadsX * kThreadsY) k_upscale_views(const __grid_constant__ UpscaleViews b)
+{
+    const int g = blockIdx.x;
+    int v = 0;
+    while (v + 1 < b.V && g >= b.start[v + 1]) ++v;
+    const UpscaleView& u = b.v[v];
+    const int t = g - b.start[v];
+    const int tiles_x = (u.W2 + kOutW - 1) / kOutW;
+    const int by = t / tiles_x, bx = t - by * tiles_x;
+    upscale_tile(u.C, u.G, u.W, u.H, u.W2, u.H2, foot_w(u.W, u.W2), u.out, bx * kOutW, by * kOutH);
 }
 
 // Adjoint of k_upscale.  The output is linear in the low-res values, so
@@ -357,6 +378,32 @@ cudaError_t launch_upscale_to(cudaStream_t s, const float* C, const float* grads
     const size_t smem = 3 * sizeof(float4) * pitch * foot_h(H, H2);
     k_upscale<<<grid, dim3(kThreadsX, kThreadsY), smem, s>>>(C, grads, W, H, W2, H2, pitch, out); note_launch();
     return cudaGetLastError();
+}
+
+cudaError_t launch_upscale_views(cudaStream_t s, const UpscaleViews& b)
+{
+    const int total = b.start[b.V];
+    if (total <= 0) return cudaSuccess;
+    size_t smem = 0;
+    for (int v = 0; v < b.V; ++v) {
+        const UpscaleView& u = b.v[v];
+        if (!sizes_ok(u.W, u.H, u.W2, u.H2, 2)) return cudaErrorInvalidValue;
+        smem = std::max(smem, 3 * sizeof(float4) * foot_w(u.W, u.W2) * foot_h(u.H, u.H2));
+    }
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_upscale_views, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(3 * sizeof(float4) * kFootW * kFootH));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_upscale_views<<<total, dim3(kThreadsX, kThreadsY), smem, s>>>(b); note_launch();
+    return cudaGetLastError();
+}
+
+int upscale_tiles(int W2, int H2)
+{
+    return ((W2 + kOutW - 1) / kOutW) * ((H2 + kOutH - 1) / kOutH);
 }
 
 cudaError_t launch_upscale(cudaStream_t s, const float* C, const float* grads, int W, int H, int factor, float* out)

@@ -1,7 +1,9 @@
 """Batched views (gs_render_views): every view of a batch -- stereo pairs of
-different sizes, one projection launch for all -- equals the single-view render
-of the same camera bit for bit, upscales included; the batch replays from a
-CUDA graph; and the reservation rules hold."""
+different sizes, one projection launch, one blend launch and one upscale
+launch for all -- equals the single-view render of the same camera bit for
+bit, upscales included, in every launch shape of the batched blend; the
+autotuner picks the fastest shape; the batch replays from a CUDA graph; and
+the reservation rules hold."""
 import numpy as np
 import pytest
 
@@ -57,7 +59,43 @@ def test_views_equal_single_view(gs, sh):
     _check(gs, scene, cams, szs, factors, outs, bg)
 
 
-def test_views_graph_replay(gs):
+@pytest.mark.parametrize("config", range(6))
+def test_views_every_launch_shape(gs, config):
+    """Each launch shape of the batched blend (warp map x schedule) gives the
+    single-view images bit for bit; twice, so that the heaviest-first schedule
+    runs on recorded tile durations."""
+    scene = gs.DeviceScene(scenes.random_scene(n=12000, seed=36, sh_degree=2, xy_range=1.3, log_scale_mean=-3.3))
+    cams, szs = stereo_batch([(150, 110), (77, 45)])
+    factors = [2, 2, 3, 3]
+    with gs.Context(no_host_wait=True) as ctx:
+        ctx.reserve_views(scene.n, len(cams), 150, 110, 600000)
+        ctx.views_config(config % 2, config // 2)
+        outs = ctx.render_views(scene, cams, szs, factors)
+        outs = ctx.render_views(scene, cams, szs, factors, outs=outs)
+        ctx.synchronize()
+    _check(gs, scene, cams, szs, factors, outs, (0.0, 0.0, 0.0))
+
+
+def test_views_autotune(gs):
+    scene = gs.DeviceScene(scenes.random_scene(n=10000, seed=37, sh_degree=1))
+    cams, szs = stereo_batch([(128, 96), (96, 64)])
+    factors = [2] * 4
+    with gs.Context(no_host_wait=True) as ctx:
+        ctx.reserve_views(scene.n, len(cams), 128, 96, 500000)
+        outs = ctx.render_views(scene, cams, szs, factors)
+        ms, best = ctx.autotune_views(scene, cams, szs, factors, outs, reps=3)
+        assert len(ms) == gs.GS_VIEWS_CONFIGS and all(t > 0 for t in ms)
+        assert 0 <= best < gs.GS_VIEWS_CONFIGS and ms[best] == min(ms)
+        outs = ctx.render_views(scene, cams, szs, factors, outs=outs)   # with the chosen shape
+        ctx.synchronize()
+        with pytest.raises(gs.GSError) as e:
+            ctx.views_config(2, 0)
+        assert e.value.status == gs.GS_ERR_INVALID_ARG
+    _check(gs, scene, cams, szs, factors, outs, (0.0, 0.0, 0.0))
+
+
+@pytest.mark.parametrize("schedule", [1, 2])
+def test_views_graph_replay(gs, schedule):
     import torch
     scene = gs.DeviceScene(scenes.random_scene(n=6000, seed=32, sh_degree=1))
     cams, szs = stereo_batch([(80, 60), (112, 80)])
@@ -65,6 +103,7 @@ def test_views_graph_replay(gs):
     stream = torch.cuda.Stream()
     with gs.Context(stream=stream, no_host_wait=True) as ctx:
         ctx.reserve_views(scene.n, 4, 112, 80, 300000)
+        ctx.views_config(0, schedule)
         with torch.cuda.stream(stream):
             outs = ctx.render_views(scene, cams, szs, factors)
         torch.cuda.synchronize()
