@@ -498,7 +498,7 @@ gs_status gs_destroy(gs_ctx* c)
                       &c->pairs[1],
                       &c->sort_hist, &c->sort_status,
                       &c->sort_counter, &c->sranges, &c->tile_count, &c->tile_start, &c->state, &c->count,
-                      &c->errword, &c->grad2d, &c->up_planes, &c->pair_check, &c->tile_work, &c->tile_order,
+                      &c->errword, &c->grad2d, &c->pair_check, &c->tile_work, &c->tile_order,
                       &c->vrec0, &c->vrec1, &c->vrec2, &c->vrect, &c->vsupers, &c->vkey, &c->vtotals,
                       &c->views_dev, &c->vpairs0, &c->vpairs1, &c->vsranges, &c->vwork, &c->vorder, &c->vqueue};
     for (DevBuf* b : bufs) release(*b);
@@ -704,9 +704,10 @@ gs_status gs_upscale_backward(gs_ctx* c, const float* dL_dout, int32_t W, int32_
 
 namespace {
 
-gs_status do_render_backward(gs_ctx* c, const float* dC, const float* dG, float* grad2d)
+gs_status do_render_backward(gs_ctx* c, const float* dC, const float* dG, float* grad2d, const float* dout = nullptr,
+                             int factor = 0)
 {
-    if (!dC || !grad2d) return fail(c, GS_ERR_INVALID_ARG, "dL_dC and grad2d are required");
+    if ((!dC && !dout) || !grad2d) return fail(c, GS_ERR_INVALID_ARG, "dL_dC and grad2d are required");
     if (!c->have_proj || !c->have_state || !c->state_grads)
         return fail(c, GS_ERR_NOT_READY, "no derivative blend since the last projection");
     if (c->n > 0) GS_CUDA(c, cudaMemsetAsync(grad2d, 0, sizeof(float) * 9 * (size_t)c->n, c->stream));
@@ -725,6 +726,9 @@ gs_status do_render_backward(gs_ctx* c, const float* dC, const float* dG, float*
     a.count = as<int>(c->count);
     a.dC = dC;
     a.dG = dG;
+    a.dout = dout;
+    a.W2 = c->W * factor;
+    a.H2 = c->H * factor;
     a.grad2d = grad2d;
     a.err = as<int>(c->errword);
     // the forward blend's tile order of this frame (heaviest first)
@@ -769,15 +773,10 @@ gs_status gs_backward(gs_ctx* c, const float* dL_dout, int32_t factor, const gs_
         return fail(c, GS_ERR_NOT_READY, "no derivative blend since the last projection");
     if (c->W < 2 || c->H < 2) return fail(c, GS_ERR_INVALID_ARG, "upscale needs W, H >= 2");
     if (factor < 1 || factor > 16) return fail(c, GS_ERR_INVALID_ARG, "factor must be in 1..16");
-    const size_t plane = (size_t)c->W * c->H;
     gs_status st;
-    if ((st = ensure(c, c->up_planes, sizeof(float) * 12 * plane)) ||
-        (st = ensure(c, c->grad2d, sizeof(float) * 9 * (size_t)std::max<int64_t>(c->n, 1))))
-        return st;
-    float* dC = as<float>(c->up_planes);
-    float* dG = dC + 3 * plane;
-    GS_CUDA(c, launch_upscale_backward(c->stream, dL_dout, c->W, c->H, factor, dC, dG));
-    if ((st = do_render_backward(c, dC, dG, as<float>(c->grad2d))) != GS_OK) return st;
+    if ((st = ensure(c, c->grad2d, sizeof(float) * 9 * (size_t)std::max<int64_t>(c->n, 1)))) return st;
+    // the upscale's adjoint fused into the blend's: no low-res upstream planes
+    if ((st = do_render_backward(c, nullptr, nullptr, as<float>(c->grad2d), dL_dout, factor)) != GS_OK) return st;
     return do_project_backward(c, as<float>(c->grad2d), out);
 }
 
@@ -860,7 +859,7 @@ gs_status reserve_impl(gs_ctx* c, int64_t n, int32_t V, int32_t W, int32_t H, in
         (st = ensure(c, c->state, sizeof(float4) * pix)) || (st = ensure(c, c->count, sizeof(int) * pix)) ||
         (st = ensure(c, c->tile_count, sizeof(uint32_t) * T)) || (st = ensure(c, c->tile_start, sizeof(uint32_t) * T)) ||
         (st = ensure(c, c->tile_work, sizeof(uint32_t) * T)) || (st = ensure(c, c->tile_order, sizeof(uint32_t) * T)) ||
-        (st = ensure(c, c->grad2d, sizeof(float) * 9 * un)) || (st = ensure(c, c->up_planes, sizeof(float) * 12 * pix)) ||
+        (st = ensure(c, c->grad2d, sizeof(float) * 9 * un)) ||
         (st = ensure(c, c->pair_check, sizeof(PairCheckOut))))
         return st;
     if (V > 0) {

@@ -44,7 +44,13 @@
 // rounds, each recounted from a stored segment start.  Per list entry the block
 // reduces the pixels' 9 gradients (a transposed warp sum, then shared-memory
 // atomics) and adds one set per tile and Gaussian to global memory.
+//
+// The upstream gradient is either given per low-res pixel (dL/dC and dL/d of
+// the derivative planes) or, fused, as the gradient of the upscaled image: each
+// pixel then gathers its own upstream values through the upscale's adjoint
+// before the walk, and the low-res planes never exist in memory.
 #include "blend_common.cuh"
+#include "spline_common.cuh"
 
 namespace gs {
 namespace {
@@ -188,13 +194,25 @@ __global__ void __launch_bounds__(kThreads) k_blend_bwd(BlendBwdArgs a)
         p.last = a.count[pix];
         const float4 st = a.state[pix];
         p.T = st.x; p.Tx = st.y; p.Ty = st.z; p.Txy = st.w;
+        if (a.dout) {   // the upscale's adjoint at this pixel, fused
+            float acc[3][4];
+            upscale_adjoint_at(a.dout, a.W, a.H, a.W2, a.H2, x, y, acc);
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            p.uC[ch] = a.dC[ch * plane + pix];
-            if (a.dG) {
-                p.uX[ch] = a.dG[(0 * 3 + ch) * plane + pix];
-                p.uY[ch] = a.dG[(1 * 3 + ch) * plane + pix];
-                p.uZ[ch] = a.dG[(2 * 3 + ch) * plane + pix];
+            for (int ch = 0; ch < 3; ++ch) {
+                p.uC[ch] = acc[ch][0];
+                p.uX[ch] = acc[ch][1];
+                p.uY[ch] = acc[ch][2];
+                p.uZ[ch] = acc[ch][3];
+            }
+        } else {
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                p.uC[ch] = a.dC[ch * plane + pix];
+                if (a.dG) {
+                    p.uX[ch] = a.dG[(0 * 3 + ch) * plane + pix];
+                    p.uY[ch] = a.dG[(1 * 3 + ch) * plane + pix];
+                    p.uZ[ch] = a.dG[(2 * 3 + ch) * plane + pix];
+                }
             }
         }
     }

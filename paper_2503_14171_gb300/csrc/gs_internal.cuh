@@ -91,6 +91,10 @@ struct BlendBwdArgs {
     const int* count;              // [W*H] list position after the last blended Gaussian
     const float* dC;               // [3][H][W]
     const float* dG;               // [3 (x, y, xy)][3][H][W]
+    // instead of dC / dG (when not null): the upstream gradient of the upscaled
+    // image [3][H2][W2], taken through the upscale's adjoint per pixel
+    const float* dout;
+    int W2, H2;
     float* grad2d;                 // [n][9]
     int* err;
     const uint32_t* order;         // optional: tiles in this order (the forward's, heaviest first)
@@ -163,7 +167,6 @@ struct gs_ctx {
     int views_map = 0;                  // batched blend: 0 = 8 x 4 warp blocks, 1 = 16 x 2
     int views_sched = 1;                // 0 = tile order, 1 = heaviest first (last batch), 2 = persistent
     bool totals_known = true;           // P, Ps valid on the host
-    gs::DevBuf up_planes;               // float[12][H][W] upstream planes of gs_backward
     unsigned long long* h_scalar = nullptr;   // pinned host scalar for the pair count
     int sorted_ids_buf = 0;             // which did[] holds the depth-sorted ids
     int sorted_pairs_buf = 0;           // which pairs[] holds the sorted pairs

@@ -165,6 +165,27 @@ def test_backward_chain_exact(gs, ora):
         assert bad == 0, (key, bad, worst)
 
 
+@pytest.mark.parametrize("mode,s", [("3dgs", 2), ("3dgs", 3), ("exact", 2)])
+def test_fused_backward_equals_chain(gs, mode, s):
+    """gs_backward takes the upscale's adjoint inside the blend's; it equals the
+    separate calls (upscale adjoint -> planes -> blend adjoint -> projection
+    adjoint) up to the order of the float atomics that sum over tiles."""
+    import torch
+    n, W, H = 3000, 77, 45
+    scene = gs.DeviceScene(scenes.random_scene(n=n, seed=19, sh_degree=3))
+    cam = scenes.pinhole_camera(W, H)
+    dout = torch.randn(3, H * s, W * s, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+    with gs.Context(mode=mode, bg=(0.2, 0.1, 0.4)) as ctx:
+        ctx.render_with_grads(scene, cam, W, H)
+        fused = {k: v.cpu().numpy() for k, v in ctx.backward(dout, s).items()}
+        dC, dG = ctx.upscale_backward(dout, W, H, s)
+        g2d = ctx.render_backward(dC, dG)
+        chain = {k: v.cpu().numpy() for k, v in ctx.project_backward(g2d).items()}
+        ctx.synchronize()
+    for k in fused:
+        np.testing.assert_allclose(fused[k], chain[k], rtol=1e-5, atol=1e-6 * (np.abs(chain[k]).max() + 1e-12))
+
+
 def test_autograd_matches_backward(gs):
     """torch.autograd through render_upscale equals gs_backward on the same upstream."""
     import torch
