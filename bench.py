@@ -784,31 +784,13 @@ def mlp_leg(torch, gs, scenes, stream, dev, peaks, pairs, steps, reps=20):
     }
 
 
-def stereo_views(seed=0, pairs=8, lo=(512, 512), hi=(1104, 1032), ipd=0.064):
-    """16 views = 8 stereo pairs; per-eye sizes log-uniform between lo and hi
-    (rounded to even), eyes 64 mm apart around the origin, looking down +z."""
-    import scenes
-    rng = np.random.default_rng(seed)
-    cams, eyes = [], []
-    for k in range(pairs):
-        W = int(round(np.exp(rng.uniform(np.log(lo[0]), np.log(hi[0]))) / 2)) * 2
-        H = int(round(np.exp(rng.uniform(np.log(lo[1]), np.log(hi[1]))) / 2)) * 2
-        yaw = rng.uniform(-0.05, 0.05)
-        for side in (-0.5, 0.5):
-            eye = (side * ipd, 0.0, 0.0)
-            target = (side * ipd + 6.0 * np.sin(yaw), 0.0, 6.0 * np.cos(yaw))
-            eyes.append((W, H))
-            cams.append((eye, target))
-    return cams, eyes
-
-
 def views_leg(torch, gs, scenes, stream, n_list=(300_000, 800_000, 2_000_000), reps=20):
     """Batched multi-view rendering (16 stereo views, each eye rendered at half
     size with derivatives and upscaled 2x; one projection, one blend and one
     upscale launch for all views, the blend's launch shape from the autotuner)
     against the same views one at a time; both recorded as CUDA graphs.  Output
     megapixels per second."""
-    camdefs, eyes = stereo_views()
+    camdefs, eyes = scenes.stereo_views()
     V = len(eyes)
     lows = [(W // 2, H // 2) for W, H in eyes]
     cams = [scenes.pinhole_camera(w, h, viewmat=scenes.look_at_viewmat(e, t)) for (w, h), (e, t) in zip(lows, camdefs)]

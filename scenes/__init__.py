@@ -208,3 +208,22 @@ def mixture_scene_device(n: int, seed: int = 0, device: str = "cuda", components
                 log_scales=(log_scale_mean + log_scale_std * torch.randn(n, 3, **kw)).contiguous(),
                 quats=q.contiguous(), opacity_logits=(opacity_logit_std * torch.randn(n, **kw)).contiguous(),
                 sh=sh.contiguous(), sh_degree=int(sh_degree))
+
+
+def stereo_views(seed: int = 0, pairs: int = 8, lo=(512, 512), hi=(1104, 1032), ipd: float = 0.064):
+    """The batching workload's 16 views: 8 stereo pairs whose per-eye sizes are
+    log-uniform between lo and hi (rounded to even), eyes 64 mm apart around the
+    origin, each pair yawed by U[-0.05, 0.05] rad, looking down +z.  Returns
+    ([(eye, target)] per view, [(W, H)] per view)."""
+    rng = np.random.default_rng(seed)
+    cams, eyes = [], []
+    for _ in range(pairs):
+        W = int(round(np.exp(rng.uniform(np.log(lo[0]), np.log(hi[0]))) / 2)) * 2
+        H = int(round(np.exp(rng.uniform(np.log(lo[1]), np.log(hi[1]))) / 2)) * 2
+        yaw = rng.uniform(-0.05, 0.05)
+        for side in (-0.5, 0.5):
+            eye = (side * ipd, 0.0, 0.0)
+            target = (side * ipd + 6.0 * np.sin(yaw), 0.0, 6.0 * np.cos(yaw))
+            eyes.append((W, H))
+            cams.append((eye, target))
+    return cams, eyes

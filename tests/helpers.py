@@ -66,6 +66,39 @@ def borderline_pixel_mask(proj, pix, margin: float = 1e-3) -> np.ndarray:
     return out
 
 
+def depth_order_ambiguous(proj, bins, pix, rel: float = 6e-7, overlap: float = 1e-5) -> np.ndarray:
+    """Sampled pixels [M, 2] of (x, y) whose front-to-back order is not unique
+    under FP32 depths: among the tile-list Gaussians that reach the pixel at or
+    above the 1/255 cut-off (less a relative margin), two adjacent in the
+    oracle's order have depths within rel of each other (an FP32 camera-space
+    z, a three-term dot product plus a translation, is within a few units in
+    the last place, relative 2^-24 each, of the FP64 one), both before the
+    pixel's transmittance falls below 1e-4, and overlapping enough for their
+    order to matter (T alpha_i alpha_j above `overlap`: swapping two layers
+    changes the blend by T alpha_i alpha_j (c_i - c_j)).  The identity rotation
+    keeps the FP32 depths exact."""
+    tile, tiles_x = proj["tile"], proj["tiles_x"]
+    out = np.zeros(len(pix), bool)
+    for m, (x, y) in enumerate(np.asarray(pix, np.int64)):
+        s, e = bins["ranges"][(y // tile) * tiles_x + x // tile]
+        ids = bins["vals"][s:e].astype(np.int64)
+        if len(ids) < 2:
+            continue
+        dx = x - proj["mean2d"][ids, 0]
+        dy = y - proj["mean2d"][ids, 1]
+        a, b, c = proj["conic"][ids].T
+        alpha = proj["opacity"][ids] * np.exp(-0.5 * (a * dx * dx + 2.0 * b * dx * dy + c * dy * dy))
+        live = alpha >= (1.0 - 1e-3) / 255.0
+        d, al = proj["depth"][ids][live], np.minimum(alpha[live], 0.99)
+        if len(d) < 2:
+            continue
+        T = np.concatenate([[1.0], np.cumprod(1.0 - al)[:-1]])     # transmittance before each layer
+        reach = T > 1e-4 * (1.0 - 1e-3)
+        close = np.abs(np.diff(d)) <= rel * np.abs(d[1:])
+        out[m] = bool(np.any(close & reach[:-1] & (T[:-1] * al[:-1] * al[1:] > overlap)))
+    return out
+
+
 def compare_render(C_gpu, G_gpu, ref, exclude=None, tol_c=TOL_C, tol_g=TOL_G):
     """C_gpu [3,H,W], G_gpu [3,3,H,W] or None; ref: oracle.render(..., variants=True).
     Returns (n_fail, n_checked, n_excluded, worst)."""
