@@ -135,7 +135,10 @@ const char* gs_last_error(const gs_ctx* ctx);
 /* Create a context on the current CUDA device.  stream: a cudaStream_t (NULL =
  * the legacy default stream).  opt may be NULL (tile 16, 3DGS mode, black
  * background, no pair limit).  *out receives the context; free it with
- * gs_destroy. */
+ * gs_destroy.  The projection's depth sort runs, up to about 10k Gaussians per
+ * SM, as one cooperative grid of one block per SM that expects the GPU to
+ * itself: do not run the frames of two contexts concurrently on different
+ * streams (their bounded grid barriers would report GS_ERR_TIMEOUT). */
 gs_status gs_create(gs_ctx** out, void* stream, const gs_options* opt);
 
 /* Release the context and its scratch memory (synchronises its stream). */
