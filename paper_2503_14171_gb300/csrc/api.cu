@@ -335,13 +335,14 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
         return st;
     uint64_t* pairs[2] = {as<uint64_t>(c->pairs[0]), as<uint64_t>(c->pairs[1])};
     GS_CUDA(c, launch_emit_pairs(c->stream, ids, as<uint32_t>(c->offsets), as<ushort4>(c->rect), n, stiles_x, pairs[0],
-                                 counted ? as<uint32_t>(c->super_counts) : nullptr, (uint32_t)Ts));
+                                 counted ? as<uint32_t>(c->super_counts) : nullptr, (uint32_t)Ts, Ps));
     int psorted = 0;
     if (counted) {
         // digit histograms of the super-tile passes and the super-tile ranges,
-        // both from the per-super-tile counts
+        // both from the per-super-tile counts (checked against the buffers)
         GS_CUDA(c, launch_supers_to_hist(c->stream, as<uint32_t>(c->super_counts), (uint32_t)Ts, spasses,
-                                         as<uint32_t>(c->sort_hist), as<uint2>(c->sranges)));
+                                         as<uint32_t>(c->sort_hist), as<uint2>(c->sranges),
+                                         PairCheckIn{nullptr, Ps ? Ps : 1u, 0}, nullptr, as<int>(c->errword)));
         if (Ps > 1 && Ts > 1)
             GS_CUDA(c, radix_sort_u64_keys(c->stream, pairs, Ps, 32, 32 + sbits, as<uint32_t>(c->sort_hist),
                                            as<uint32_t>(c->sort_status), as<uint32_t>(c->sort_counter),

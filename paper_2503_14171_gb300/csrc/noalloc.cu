@@ -210,8 +210,9 @@ extern "C" gs_status gs_render_with_grads_noalloc(const gs_gaussians* g, const g
     const int spasses = radix_passes(32, 32 + sbits);
     NA_CUDA(cudaMemsetAsync(scounts, 0, sizeof(uint32_t) * kCountCopies * Ts, s));
     NA_CUDA(launch_emit_pairs(s, ids[sorted], offsets, at<ushort4>(base, kOffRect), n, stiles_x, pairs[0], scounts,
-                              Ts));
-    NA_CUDA(launch_supers_to_hist(s, scounts, Ts, spasses, hist, sranges));
+                              Ts, Ps));
+    NA_CUDA(launch_supers_to_hist(s, scounts, Ts, spasses, hist, sranges, PairCheckIn{nullptr, Ps ? Ps : 1u, 0},
+                                  nullptr, err));
     int psorted = 0;
     if (Ps > 1 && Ts > 1)
         NA_CUDA(radix_sort_u64_keys(s, pairs, Ps, 32, 32 + sbits, hist, at<uint32_t>(base, kOffStatus),

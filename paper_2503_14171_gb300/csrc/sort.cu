@@ -467,7 +467,12 @@ __global__ void __launch_bounds__(kThreads) k_supers_to_hist(uint32_t* __restric
         for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p][(t >> (p * kRadixBits)) & (kRadix - 1)], c);
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (out) {
+    // the emitted pairs must fit the pair buffers (in.cap; 0: unchecked): a
+    // frame beyond the reservation (out != NULL) is reported as a capacity
+    // overflow, a count above the exactly sized buffers as a failed check
+    // (only after an expired bounded wait upstream); either way the ranges are
+    // left empty, so no later kernel reads beyond the buffers
+    if (out || in.cap) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
         if (lane == 0) s_sum[warp] = mine;
@@ -475,12 +480,15 @@ __global__ void __launch_bounds__(kThreads) k_supers_to_hist(uint32_t* __restric
         if (threadIdx.x == 0) {
             unsigned long long ps = 0, p = 0;
             for (int w = 0; w < kWarps; ++w) ps += s_sum[w];
-            for (int k = 0; k < kTotalSlots; ++k) p += in.slots[2 * k + 1];
-            const bool ok = ps <= in.cap && p <= in.max_pairs;
-            out->needed = ps;
-            out->tile_pairs = p;
-            out->count = ok ? (uint32_t)ps : 0u;
-            if (!ok) atomicExch(err, kDevCapacity);
+            bool ok = ps <= in.cap;
+            if (out) {
+                for (int k = 0; k < kTotalSlots; ++k) p += in.slots[2 * k + 1];
+                ok = ok && p <= in.max_pairs;
+                out->needed = ps;
+                out->tile_pairs = p;
+                out->count = ok ? (uint32_t)ps : 0u;
+            }
+            if (!ok && err) atomicExch(err, out ? kDevCapacity : kDevCheck);
             s_ok = ok;
         }
         __syncthreads();
