@@ -178,15 +178,15 @@ struct InferSmem {
     uint8_t w1[kHid * 128];
     uint8_t w2[kHid * 128];
     uint8_t w3[16 * 128];            // W3 as a B operand: N = 16 rows (3 used), K = 64
-    float4 foot[kFootH * kFootW * 3];
     float4 b1[kHid / 4], b2[kHid / 4];
-    float4 hx[kTileW], hy[kTileH];   // Hermite weights of the columns / rows
     float tx[kTileW], ty[kTileH];    // local coordinates t, u
     int cx[kTileW], cy[kTileH];      // absolute cell indices
     float b3[4];
     uint64_t bar;
     uint32_t tmem;
 };
+// followed in dynamic shared memory by the footprint: fpw x fph low-res pixels
+// (fpw = ceil(31 W / W2) + 2 <= 33, fph = ceil(3 H / H2) + 2 <= 5), three float4 each
 
 constexpr uint32_t kInferCols = 64;   // D1, D2 and D3 share columns 0..63
 
@@ -202,13 +202,14 @@ __device__ __forceinline__ float corner_value(const float4 (&v)[3], int e)
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 5) k_mlp_upscale(const float* __restrict__ C, const float* __restrict__ G,
-                                                             int W, int H, int W2, int H2,
+__global__ void __launch_bounds__(kThreads, 6) k_mlp_upscale(const float* __restrict__ C, const float* __restrict__ G,
+                                                             int W, int H, int W2, int H2, int fpw,
                                                              const float* __restrict__ P, float* __restrict__ out,
                                                              int* __restrict__ err)
 {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     InferSmem& s = *reinterpret_cast<InferSmem*>(smem_raw);
+    float4* const foot = reinterpret_cast<float4*>(smem_raw + sizeof(InferSmem));
     const int tid = threadIdx.x, warp = tid >> 5, lx = tid & 31, ly = tid >> 5;
     for (int e = tid; e < kHid * 64; e += kThreads) {
         const int n = e >> 6, k = e & 63;
@@ -256,7 +257,6 @@ __global__ void __launch_bounds__(kThreads, 5) k_mlp_upscale(const float* __rest
             cell_of(min(X0 + tid, W2 - 1), W, W2, ci, t);
             s.cx[tid] = ci;
             s.tx[tid] = t;
-            s.hx[tid] = hermite(t);
         } else if (tid < kTileW + kTileH) {
             const int r = tid - kTileW;
             int cj;
@@ -264,15 +264,14 @@ __global__ void __launch_bounds__(kThreads, 5) k_mlp_upscale(const float* __rest
             cell_of(min(Y0 + r, H2 - 1), H, H2, cj, u);
             s.cy[r] = cj;
             s.ty[r] = u;
-            s.hy[r] = hermite(u);
         }
         __syncthreads();
         const int i0 = s.cx[0], j0 = s.cy[0];
-        const int fw = s.cx[kTileW - 1] + 2 - i0, fh = s.cy[kTileH - 1] + 2 - j0;   // <= kFootW x kFootH
+        const int fw = s.cx[kTileW - 1] + 2 - i0, fh = s.cy[kTileH - 1] + 2 - j0;   // <= fpw x fph
         for (int e = tid; e < fw * fh; e += kThreads) {
             const int fy = e / fw, fx = e - fy * fw;
             const size_t o = (size_t)(j0 + fy) * W + i0 + fx;
-            float4* d = s.foot + 3 * (fy * kFootW + fx);
+            float4* d = foot + 3 * (fy * fpw + fx);
             d[0] = make_float4(__ldg(C + o), __ldg(C + plane + o), __ldg(C + 2 * plane + o), __ldg(G + o));
             d[1] = make_float4(__ldg(G + plane + o), __ldg(G + 2 * plane + o), __ldg(G + 3 * plane + o),
                                __ldg(G + 4 * plane + o));
@@ -285,11 +284,11 @@ __global__ void __launch_bounds__(kThreads, 5) k_mlp_upscale(const float* __rest
         float sp0 = 0.f, sp1 = 0.f, sp2 = 0.f;
         {
             const int li = s.cx[lx] - i0, lj = s.cy[ly] - j0;
-            const float4 hx = s.hx[lx], hy = s.hy[ly];
+            const float4 hx = hermite(s.tx[lx]), hy = hermite(s.ty[ly]);
             float4 v[4][3];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const float4* src = s.foot + 3 * ((lj + (k >> 1)) * kFootW + li + (k & 1));
+                const float4* src = foot + 3 * ((lj + (k >> 1)) * fpw + li + (k & 1));
                 v[k][0] = src[0];
                 v[k][1] = src[1];
                 v[k][2] = src[2];
@@ -771,14 +770,23 @@ int sm_count()
 cudaError_t launch_mlp_upscale(cudaStream_t s, const float* C, const float* G, int W, int H, int W2, int H2,
                                const float* params, float* out, int* err)
 {
-    const size_t smem = sizeof(InferSmem);
+    // footprint bound of a 32 x 4 tile: ceil(31 W / W2) + 2 columns, ceil(3 H / H2) + 2 rows
+    const int fpw = std::min(kFootW, (int)((31ll * W + W2 - 1) / W2) + 2);
+    const int fph = std::min(kFootH, (int)((3ll * H + H2 - 1) / H2) + 2);
+    const size_t smem = sizeof(InferSmem) + 3 * sizeof(float4) * (size_t)fpw * fph;
     cudaError_t e = cudaFuncSetAttribute(k_mlp_upscale, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const long long ntiles = (long long)((W2 + kTileW - 1) / kTileW) * ((H2 + kTileH - 1) / kTileH);
     if (ntiles == 0) return cudaSuccess;
-    // five CTAs per SM: 5 x 64 tensor-memory columns, 5 x ~42 KB shared memory
-    const long long grid = std::min<long long>(ntiles, 5ll * sm_count());
-    k_mlp_upscale<<<(unsigned)grid, kThreads, smem, s>>>(C, G, W, H, W2, H2, params, out, err);
+    // persistent: as many CTAs as fit on an SM (six at 4x with 37 KB of shared
+    // memory each, five at 2x and below), never more than the 512 tensor-memory
+    // columns hold (8 x 64)
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_upscale, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    per_sm = std::max(1, std::min(per_sm, 512 / (int)kInferCols));
+    const long long grid = std::min<long long>(ntiles, (long long)per_sm * sm_count());
+    k_mlp_upscale<<<(unsigned)grid, kThreads, smem, s>>>(C, G, W, H, W2, H2, fpw, params, out, err);
     note_launch();
     return cudaGetLastError();
 }
