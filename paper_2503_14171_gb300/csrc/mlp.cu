@@ -780,7 +780,12 @@ cudaError_t launch_mlp_upscale(cudaStream_t s, const float* C, const float* G, i
     if (ntiles == 0) return cudaSuccess;
     // persistent: as many CTAs as fit on an SM (six at 4x with 37 KB of shared
     // memory each, five at 2x and below), never more than the 512 tensor-memory
-    // columns hold (8 x 64)
+    // columns hold (8 x 64).  The kernel asks for the largest shared-memory
+    // carveout: the occupancy calculator otherwise assumes a smaller default
+    // carveout than the one the driver picks at launch, and reports one CTA.
+    e = cudaFuncSetAttribute(k_mlp_upscale, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_upscale, kThreads, smem);
     if (e != cudaSuccess) return e;

@@ -18,153 +18,175 @@
 // rounding; outside [0, 1] only in the border half-cells, where the edge patch
 // is extrapolated).
 //
-// Launch: one 256-thread block per 64 x 16 tile of output pixels, 2 x 2 outputs
-// per thread.  The block computes the cell index and the four basis weights of
-// its 64 columns and 16 rows once (shared tables), stages the low-res footprint
-// of the tile -- each pixel's 12 values (C, C_x, C_y, C_xy for three channels)
-// packed as three float4 -- in shared memory with coalesced loads, and then
-// evaluates each output with 12 vector shared loads and 48 FMAs.  HBM-bound:
-// 48 B per low-res pixel in, 12 B per output pixel out.
+// Separable evaluation.  Grouping the sum by the patch row b,
+//   p = sum_b H_b(u) A_b + G_b(u) B_b,
+//   A_b = sum_a H_a(t) f(a,b) + G_a(t) f_x(a,b),  B_b = sum_a H_a(t) f_y(a,b) + G_a(t) f_xy(a,b),
+// where A_b and B_b depend only on the output column (through i and t) and the
+// low-res row.  A thread owns one output column and a run of consecutive output
+// rows; for factors >= 1 their cell rows step by 0 or 1, so each low-res row's
+// (A, B) is formed once (8 FMAs per channel) and every output then costs 4 FMAs
+// per channel.
+//
+// Launch: one 256-thread block per 64 x 32 tile of output pixels: 64 columns x
+// 4 runs of 8 rows, a warp = 32 columns of one run (coalesced stores).  The
+// block computes the cell index and the basis weights of its 64 columns and 32
+// rows once (shared tables) and stages the low-res footprint of the tile -- each
+// pixel's 12 values (C, C_x, C_y, C_xy for three channels) packed as three
+// float4 -- in shared memory with coalesced loads.  48 B per low-res pixel in,
+// 12 B per output pixel out.
 #include "gs_internal.cuh"
 #include "spline_common.cuh"
 
 namespace gs {
 namespace {
 
-constexpr int kThreadsX = 32, kThreadsY = 8;
-constexpr int kOutW = 2 * kThreadsX;    // 64
-constexpr int kOutH = 2 * kThreadsY;    // 16
 constexpr int kMaxFactor = 16;
-// footprint of a 64 x 16 output tile for W2 >= W: at most 63 + 2 x 15 + 2 cells
-constexpr int kFootW = kOutW + 2;
-constexpr int kFootH = kOutH + 2;
+// spline tiles
+constexpr int kSplCols = 64, kSplRuns = 4, kSplRun = 8;
+constexpr int kSplThreads = kSplCols * kSplRuns;   // 256
+constexpr int kSplW = kSplCols;                    // 64
+constexpr int kSplH = kSplRuns * kSplRun;          // 32
+// footprint of a 64 x 32 output tile for W2 >= W: at most 63 + 2 x 31 + 2 cells
+constexpr int kFootW = kSplW + 1;
+constexpr int kFootH = kSplH + 1;
 
-// footprint bound of a 64 x 16 output tile: ceil(63 W / W2) + 2 columns,
-// ceil(15 H / H2) + 2 rows
+// footprint bound of a 64 x 32 output tile: ceil(63 W / W2) + 2 columns,
+// ceil(31 H / H2) + 2 rows
 __host__ __device__ int foot_w(int W, int W2) { return min(kFootW, (int)((63ll * W + W2 - 1) / W2) + 2); }
-__host__ __device__ int foot_h(int H, int H2) { return min(kFootH, (int)((15ll * H + H2 - 1) / H2) + 2); }
+__host__ __device__ int foot_h(int H, int H2) { return min(kFootH, (int)((31ll * H + H2 - 1) / H2) + 2); }
 
-// The 64 x 16 output tile at (X0, Y0) (one block)
+// (A, B) of the three channels at footprint row r for the column with cell li
+// and x weights w = (h00, h01, h10, h11)
+__device__ __forceinline__ void spline_row(const float4* __restrict__ foot, int pitch, int r, int li, float4 w,
+                                           float (&A)[3], float (&B)[3])
+{
+    const float4* v = foot + 3 * (r * pitch + li);
+    const float4 a0 = v[0], a1 = v[1], a2 = v[2];   // corner a = 0: (C rgb, Cx r) (Cx gb, Cy rg) (Cy b, Cxy rgb)
+    const float4 b0 = v[3], b1 = v[4], b2 = v[5];   // corner a = 1
+    A[0] = fmaf(w.x, a0.x, fmaf(w.y, b0.x, fmaf(w.z, a0.w, w.w * b0.w)));
+    A[1] = fmaf(w.x, a0.y, fmaf(w.y, b0.y, fmaf(w.z, a1.x, w.w * b1.x)));
+    A[2] = fmaf(w.x, a0.z, fmaf(w.y, b0.z, fmaf(w.z, a1.y, w.w * b1.y)));
+    B[0] = fmaf(w.x, a1.z, fmaf(w.y, b1.z, fmaf(w.z, a2.y, w.w * b2.y)));
+    B[1] = fmaf(w.x, a1.w, fmaf(w.y, b1.w, fmaf(w.z, a2.z, w.w * b2.z)));
+    B[2] = fmaf(w.x, a2.x, fmaf(w.y, b2.x, fmaf(w.z, a2.w, w.w * b2.w)));
+}
+
+// The 64 x 32 output tile at (X0, Y0) (one block of kSplThreads)
 __device__ __forceinline__ void upscale_tile(const float* __restrict__ Cimg, const float* __restrict__ G, int W,
                                              int H, int W2, int H2, int pitch, float* __restrict__ out, int X0,
                                              int Y0)
 {
     // per low-res pixel of the footprint, its 12 values packed in 3 float4: [fy][fx][3]
     extern __shared__ float4 sm[];
-    __shared__ float4 s_wx[kOutW];             // basis weights (h00, h01, h10, h11) per output column
-    __shared__ float4 s_wy[kOutH];
-    __shared__ int s_cx[kOutW], s_cy[kOutH];   // cell index relative to the footprint origin
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int tid = ty * kThreadsX + tx;
+    __shared__ float4 s_wx[kSplW];   // basis weights (h00, h01, h10, h11) per output column
+    __shared__ float4 s_wy[kSplH];
+    __shared__ int s_cx[kSplW], s_cy[kSplH];   // cell index (absolute until the footprint origin is known)
+    const int tid = threadIdx.x;
+    const int col = tid & (kSplCols - 1), run = tid / kSplCols;
 
-    int i0, j0, itmp, jtmp;
-    float ttmp;
-    cell_of(X0, W, W2, i0, ttmp);
-    cell_of(Y0, H, H2, j0, ttmp);
-    cell_of(min(X0 + kOutW - 1, W2 - 1), W, W2, itmp, ttmp);
-    cell_of(min(Y0 + kOutH - 1, H2 - 1), H, H2, jtmp, ttmp);
-    const int fw = itmp + 2 - i0, fh = jtmp + 2 - j0;   // <= pitch x foot_h(H, H2)
-
-    if (tid < kOutW) {
+    if (tid < kSplW) {
         int ci;
         float t;
         cell_of(min(X0 + tid, W2 - 1), W, W2, ci, t);
-        s_cx[tid] = ci - i0;
+        s_cx[tid] = ci;
         s_wx[tid] = hermite(t);
-    } else if (tid < kOutW + kOutH) {
-        const int r = tid - kOutW;
+    } else if (tid < kSplW + kSplH) {
+        const int r = tid - kSplW;
         int cj;
         float u;
         cell_of(min(Y0 + r, H2 - 1), H, H2, cj, u);
-        s_cy[r] = cj - j0;
+        s_cy[r] = cj;
         s_wy[r] = hermite(u);
     }
-    // footprint: 12 planes, each a coalesced row-major fh x fw window
+    __syncthreads();
+    const int i0 = s_cx[0], j0 = s_cy[0];
+    const int fw = s_cx[kSplW - 1] + 2 - i0, fh = s_cy[kSplH - 1] + 2 - j0;   // <= pitch x foot_h(H, H2)
+
+    // footprint: pixel p of the row-major fh x fw window is loaded by thread
+    // p mod 256 (coalesced in each of the 12 planes); two rounds of loads in
+    // flight before the first store
     const size_t plane = (size_t)W * H;
-    for (int fy = ty; fy < fh; fy += kThreadsY) {
-        const size_t row = (size_t)(j0 + fy) * W + i0;
-        for (int fx = tx; fx < fw; fx += kThreadsX) {
-            const float* c = Cimg + row + fx;
-            const float* g = G + row + fx;
-            float4* d = sm + 3 * (fy * pitch + fx);
-            d[0] = make_float4(c[0], c[plane], c[2 * plane], g[0]);
-            d[1] = make_float4(g[plane], g[2 * plane], g[3 * plane], g[4 * plane]);
-            d[2] = make_float4(g[5 * plane], g[6 * plane], g[7 * plane], g[8 * plane]);
+    const int np = fw * fh;
+    for (int p0 = 0; p0 < np; p0 += 2 * kSplThreads) {
+        float v[2][12];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int p = p0 + r * kSplThreads + tid;
+            if (p < np) {
+                const int fy = p / fw, fx = p - fy * fw;
+                const size_t o = (size_t)(j0 + fy) * W + i0 + fx;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) v[r][k] = __ldg(Cimg + k * plane + o);
+#pragma unroll
+                for (int k = 0; k < 9; ++k) v[r][3 + k] = __ldg(G + k * plane + o);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int p = p0 + r * kSplThreads + tid;
+            if (p < np) {
+                const int fy = p / fw, fx = p - fy * fw;
+                float4* d = sm + 3 * (fy * pitch + fx);
+                d[0] = make_float4(v[r][0], v[r][1], v[r][2], v[r][3]);
+                d[1] = make_float4(v[r][4], v[r][5], v[r][6], v[r][7]);
+                d[2] = make_float4(v[r][8], v[r][9], v[r][10], v[r][11]);
+            }
         }
     }
     __syncthreads();
 
+    const int X = X0 + col;
+    const int y0 = run * kSplRun;
+    if (X >= W2 || Y0 + y0 >= H2) return;   // no barrier follows
+    const float4 wx = s_wx[col];
+    const int li = s_cx[col] - i0;
+    // rows cur and cur + 1 of the run's current cell (relative to the footprint)
+    int cur = s_cy[y0] - j0;
+    float A0[3], B0[3], A1[3], B1[3];
+    spline_row(sm, pitch, cur, li, wx, A0, B0);
+    spline_row(sm, pitch, cur + 1, li, wx, A1, B1);
     const size_t oplane = (size_t)W2 * H2;
+    float* o = out + (size_t)(Y0 + y0) * W2 + X;
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
-        const int oy = ty + b * kThreadsY;
-        const int Y = Y0 + oy;
-        if (Y >= H2) continue;
-        const float4 wy = s_wy[oy];
-        const int lj = s_cy[oy];
+    for (int k = 0; k < kSplRun; ++k) {
+        if (Y0 + y0 + k >= H2) break;
+        const int lj = s_cy[y0 + k] - j0;
+        if (lj != cur) {   // the next cell row (cells of consecutive rows step by at most one)
+            cur = lj;
 #pragma unroll
-        for (int a = 0; a < 2; ++a) {
-            const int ox = tx + a * kThreadsX;
-            const int X = X0 + ox;
-            if (X >= W2) continue;
-            const float4 wx = s_wx[ox];
-            const int li = s_cx[ox];
-            // corner (p, q), p, q in {0, 1}: value weight Hx_p Hy_q, d/dx weight Gx_p Hy_q,
-            // d/dy weight Hx_p Gy_q, d2/dxdy weight Gx_p Gy_q
-            float r = 0.f, gch = 0.f, bch = 0.f;
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-#pragma unroll
-                for (int p = 0; p < 2; ++p) {
-                    const float hx = p ? wx.y : wx.x, gx = p ? wx.w : wx.z;
-                    const float hy = q ? wy.y : wy.x, gy = q ? wy.w : wy.z;
-                    const float wv = hx * hy, wdx = gx * hy, wdy = hx * gy, wdxy = gx * gy;
-                    const float4* v = sm + 3 * ((lj + q) * pitch + li + p);
-                    const float4 v0 = v[0];   // C r, C g, C b, Cx r
-                    const float4 v1 = v[1];   // Cx g, Cx b, Cy r, Cy g
-                    const float4 v2 = v[2];   // Cy b, Cxy r, Cxy g, Cxy b
-                    r = fmaf(wv, v0.x, r);
-                    gch = fmaf(wv, v0.y, gch);
-                    bch = fmaf(wv, v0.z, bch);
-                    r = fmaf(wdx, v0.w, r);
-                    gch = fmaf(wdx, v1.x, gch);
-                    bch = fmaf(wdx, v1.y, bch);
-                    r = fmaf(wdy, v1.z, r);
-                    gch = fmaf(wdy, v1.w, gch);
-                    bch = fmaf(wdy, v2.x, bch);
-                    r = fmaf(wdxy, v2.y, r);
-                    gch = fmaf(wdxy, v2.z, gch);
-                    bch = fmaf(wdxy, v2.w, bch);
-                }
+            for (int c = 0; c < 3; ++c) {
+                A0[c] = A1[c];
+                B0[c] = B1[c];
             }
-            const size_t o = (size_t)Y * W2 + X;
-            out[o] = r;
-            out[oplane + o] = gch;
-            out[2 * oplane + o] = bch;
+            spline_row(sm, pitch, cur + 1, li, wx, A1, B1);
         }
+        const float4 wy = s_wy[y0 + k];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            o[c * oplane] = fmaf(wy.x, A0[c], fmaf(wy.y, A1[c], fmaf(wy.z, B0[c], wy.w * B1[c])));
+        o += W2;
     }
 }
 
-__global__ void __launch_bounds__(kThreadsX * kThreadsY) k_upscale(const float* __restrict__ Cimg,
-                                                                   const float* __restrict__ G, int W, int H,
-                                                                   int W2, int H2, int pitch,
-                                                                   float* __restrict__ out)
+__global__ void __launch_bounds__(kSplThreads) k_upscale(const float* __restrict__ Cimg, const float* __restrict__ G,
+                                                         int W, int H, int W2, int H2, int pitch,
+                                                         float* __restrict__ out)
 {
-    upscale_tile(Cimg, G, W, H, W2, H2, pitch, out, blockIdx.x * kOutW, blockIdx.y * kOutH);
+    upscale_tile(Cimg, G, W, H, W2, H2, pitch, out, blockIdx.x * kSplW, blockIdx.y * kSplH);
 }
 
 // The upscales of a batch of views in one launch: block b takes tile b - start[v]
 // of view v (row-major over its tiles_x tiles per row).
-__global__ void __launch_bounds__(kThreadsX * kThreadsY) k_upscale_views(const __grid_constant__ UpscaleViews b)
+__global__ void __launch_bounds__(kSplThreads) k_upscale_views(const __grid_constant__ UpscaleViews b)
 {
     const int g = blockIdx.x;
     int v = 0;
     while (v + 1 < b.V && g >= b.start[v + 1]) ++v;
     const UpscaleView& u = b.v[v];
     const int t = g - b.start[v];
-    const int tiles_x = (u.W2 + kOutW - 1) / kOutW;
+    const int tiles_x = (u.W2 + kSplW - 1) / kSplW;
     const int by = t / tiles_x, bx = t - by * tiles_x;
-    upscale_tile(u.C, u.G, u.W, u.H, u.W2, u.H2, foot_w(u.W, u.W2), u.out, bx * kOutW, by * kOutH);
+    upscale_tile(u.C, u.G, u.W, u.H, u.W2, u.H2, foot_w(u.W, u.W2), u.out, bx * kSplW, by * kSplH);
 }
 
 // Adjoint of k_upscale (upscale_adjoint_at in spline_common.cuh): one thread
@@ -215,6 +237,10 @@ __device__ __forceinline__ void taps_of(int X, int W, int W2, float a, int& firs
     w = make_float4(keys(1.f + t, a), keys(t, a), keys(1.f - t, a), keys(2.f - t, a));
 }
 
+// bicubic tiles: one 32 x 8-thread block per 64 x 16 outputs, 2 x 2 per thread
+constexpr int kThreadsX = 32, kThreadsY = 8;
+constexpr int kOutW = 2 * kThreadsX;   // 64
+constexpr int kOutH = 2 * kThreadsY;   // 16
 constexpr int kBicFootW = kOutW + 3;   // 63 + 4 taps for W2 >= W
 constexpr int kBicFootH = kOutH + 3;
 
@@ -316,7 +342,7 @@ cudaError_t launch_upscale_to(cudaStream_t s, const float* C, const float* grads
                               float* out)
 {
     if (!sizes_ok(W, H, W2, H2, 2)) return cudaErrorInvalidValue;
-    dim3 grid((W2 + kOutW - 1) / kOutW, (H2 + kOutH - 1) / kOutH);
+    dim3 grid((W2 + kSplW - 1) / kSplW, (H2 + kSplH - 1) / kSplH);
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_upscale, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -326,7 +352,7 @@ cudaError_t launch_upscale_to(cudaStream_t s, const float* C, const float* grads
     }
     const int pitch = foot_w(W, W2);
     const size_t smem = 3 * sizeof(float4) * pitch * foot_h(H, H2);
-    k_upscale<<<grid, dim3(kThreadsX, kThreadsY), smem, s>>>(C, grads, W, H, W2, H2, pitch, out); note_launch();
+    k_upscale<<<grid, kSplThreads, smem, s>>>(C, grads, W, H, W2, H2, pitch, out); note_launch();
     return cudaGetLastError();
 }
 
@@ -347,13 +373,13 @@ cudaError_t launch_upscale_views(cudaStream_t s, const UpscaleViews& b)
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_upscale_views<<<total, dim3(kThreadsX, kThreadsY), smem, s>>>(b); note_launch();
+    k_upscale_views<<<total, kSplThreads, smem, s>>>(b); note_launch();
     return cudaGetLastError();
 }
 
 int upscale_tiles(int W2, int H2)
 {
-    return ((W2 + kOutW - 1) / kOutW) * ((H2 + kOutH - 1) / kOutH);
+    return ((W2 + kSplW - 1) / kSplW) * ((H2 + kSplH - 1) / kSplH);
 }
 
 cudaError_t launch_upscale(cudaStream_t s, const float* C, const float* grads, int W, int H, int factor, float* out)
