@@ -272,22 +272,6 @@ cudaError_t launch_views_t(cudaStream_t s, const BlendViews& b, int grid)
     return cudaGetLastError();
 }
 
-// Blocks of the persistent batched blend resident per SM.  The kernel asks for
-// the largest shared-memory carveout: the occupancy calculator otherwise
-// assumes a smaller default carveout than the one the driver picks at launch,
-// and reports fewer resident blocks than run.
-template <int MODE, int MAP>
-cudaError_t resident_per_sm(int& per_sm)
-{
-    auto* k = k_blend_views<true, MODE, MAP, true>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                         (int)cudaSharedmemCarveoutMaxShared);
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, 0);
-    per_sm = std::max(1, per_sm);
-    return e;
-}
-
 }  // namespace
 
 cudaError_t launch_blend_stats(cudaStream_t s, int mode, const BlendArgs& a, unsigned long long* stats)
@@ -307,16 +291,20 @@ cudaError_t launch_blend_views(cudaStream_t s, int mode, const BlendViews& b, in
     if (total <= 0) return cudaSuccess;
     int grid = total;
     if (persistent) {
-        int per_sm = 0;
-        cudaError_t e = mode == GS_MODE_EXACT
-                            ? (map ? resident_per_sm<GS_MODE_EXACT, 1>(per_sm) : resident_per_sm<GS_MODE_EXACT, 0>(per_sm))
-                            : (map ? resident_per_sm<GS_MODE_3DGS, 1>(per_sm) : resident_per_sm<GS_MODE_3DGS, 0>(per_sm));
-        if (e != cudaSuccess) return e;
-        int dev = 0, sms = 1;
+        // resident blocks: as many as fit (blocks per SM by the occupancy calculator)
+        int dev = 0, sms = 1, per_sm = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        grid = std::min(total, std::max(1, sms * per_sm));
-        e = cudaMemsetAsync(b.queue, 0, sizeof(uint32_t), s);
+        if (mode == GS_MODE_EXACT)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, map ? k_blend_views<true, GS_MODE_EXACT, 1, true>
+                                                                       : k_blend_views<true, GS_MODE_EXACT, 0, true>,
+                                                          kThreads, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, map ? k_blend_views<true, GS_MODE_3DGS, 1, true>
+                                                                       : k_blend_views<true, GS_MODE_3DGS, 0, true>,
+                                                          kThreads, 0);
+        grid = std::min(total, std::max(1, sms * std::max(1, per_sm)));
+        cudaError_t e = cudaMemsetAsync(b.queue, 0, sizeof(uint32_t), s);
         if (e != cudaSuccess) return e;
     }
     if (mode == GS_MODE_EXACT) {

@@ -765,6 +765,38 @@ int sm_count()
 
 }  // namespace
 
+// CTAs of a tensor-memory kernel resident per SM: the limits of its registers,
+// shared memory (with the largest carveout), threads and blocks per SM, and of
+// the 512 tensor-memory columns.  (The runtime's occupancy calculator reports
+// one CTA per SM for any kernel that allocates tensor memory.)
+template <typename Kernel>
+cudaError_t resident_ctas(Kernel k, int threads, size_t smem, uint32_t tmem_cols, int& per_sm)
+{
+    int dev = 0, smem_sm = 0, reserved = 0, regs_sm = 0, threads_sm = 0, blocks_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&threads_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&blocks_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k);
+    if (e != cudaSuccess) return e;
+    // shared memory is allocated in 128-byte units; registers per warp in units
+    // of 8 per thread, and a warp's registers come from one of the 4 sub-partitions
+    const size_t per_cta_smem = (smem + fa.sharedSizeBytes + (size_t)reserved + 127) / 128 * 128;
+    const int warps = (threads + 31) / 32;
+    const int regs_warp = (fa.numRegs + 7) / 8 * 8 * 32;
+    const int warps_by_regs = regs_warp > 0 ? 4 * ((regs_sm / 4) / regs_warp) : 64;
+    int n = (int)std::min<size_t>((size_t)smem_sm / per_cta_smem, 64);
+    n = std::min(n, warps_by_regs / warps);
+    n = std::min(n, threads_sm / (warps * 32));
+    n = std::min(n, blocks_sm);
+    n = std::min(n, (int)(512 / tmem_cols));
+    per_sm = std::max(1, n);
+    return cudaSuccess;
+}
+
 // ------------------------------------------------------------------ launchers
 
 cudaError_t launch_mlp_upscale(cudaStream_t s, const float* C, const float* G, int W, int H, int W2, int H2,
@@ -779,17 +811,14 @@ cudaError_t launch_mlp_upscale(cudaStream_t s, const float* C, const float* G, i
     const long long ntiles = (long long)((W2 + kTileW - 1) / kTileW) * ((H2 + kTileH - 1) / kTileH);
     if (ntiles == 0) return cudaSuccess;
     // persistent: as many CTAs as fit on an SM (six at 4x with 37 KB of shared
-    // memory each, five at 2x and below), never more than the 512 tensor-memory
-    // columns hold (8 x 64).  The kernel asks for the largest shared-memory
-    // carveout: the occupancy calculator otherwise assumes a smaller default
-    // carveout than the one the driver picks at launch, and reports one CTA.
+    // memory each, five at 2x and below); the largest shared-memory carveout
+    // makes that many resident
     e = cudaFuncSetAttribute(k_mlp_upscale, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_upscale, kThreads, smem);
+    int per_sm = 1;
+    e = resident_ctas(k_mlp_upscale, kThreads, smem, kInferCols, per_sm);
     if (e != cudaSuccess) return e;
-    per_sm = std::max(1, std::min(per_sm, 512 / (int)kInferCols));
     const long long grid = std::min<long long>(ntiles, (long long)per_sm * sm_count());
     k_mlp_upscale<<<(unsigned)grid, kThreads, smem, s>>>(C, G, W, H, W2, H2, fpw, params, out, err);
     note_launch();
