@@ -92,7 +92,6 @@ T* as(DevBuf& b)
     return reinterpret_cast<T*>(b.p);
 }
 
-constexpr size_t kRadixDigits = 256;
 
 int bits_for(uint32_t v)   // number of bits to represent values < v (v >= 1)
 {
@@ -221,12 +220,10 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
     const int spasses = radix_passes(32, 32 + sbits);
     ZeroList zl{};
     if (persistent) {
-        if ((st = ensure(c, c->ds_scratch, G * kRadixDigits * 4 + G * 8 + 64 + 4 * kRadixDigits * 4))) return st;
+        if ((st = ensure(c, c->ds_scratch, ds_scratch_bytes(G)))) return st;
         unsigned char* base = as<unsigned char>(c->ds_scratch);
-        zl.p[zl.count] = reinterpret_cast<uint32_t*>(base + G * kRadixDigits * 4 + G * 8);   // barrier
-        zl.words[zl.count++] = 2;
-        zl.p[zl.count] = reinterpret_cast<uint32_t*>(base + G * kRadixDigits * 4 + G * 8 + 64);   // digit totals
-        zl.words[zl.count++] = 4 * kRadixDigits;
+        zl.p[zl.count] = reinterpret_cast<uint32_t*>(base + ds_zero_offset(G));   // barrier and totals
+        zl.words[zl.count++] = ds_zero_words();
     }
     if (counted) {
         zl.p[zl.count] = as<uint32_t>(c->super_counts);
@@ -262,10 +259,10 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
         uint32_t* keys[2] = {as<uint32_t>(c->dkey[0]), as<uint32_t>(c->dkey[1])};
         uint32_t* vals[2] = {as<uint32_t>(c->did[0]), as<uint32_t>(c->did[1])};
         GS_CUDA(c, launch_depth_sort_scan(c->stream, c->device, keys[0], keys, vals, as<uint32_t>(c->supers_touched), n,
-                                          as<uint32_t>(c->offsets), reinterpret_cast<uint32_t*>(base),
-                                          reinterpret_cast<unsigned long long*>(base + G * kRadixDigits * 4),
-                                          reinterpret_cast<unsigned int*>(base + G * kRadixDigits * 4 + G * 8),
-                                          reinterpret_cast<uint32_t*>(base + G * kRadixDigits * 4 + G * 8 + 64),
+                                          as<uint32_t>(c->offsets), reinterpret_cast<uint32_t*>(base + ds_cnt_offset(G)),
+                                          reinterpret_cast<uint32_t*>(base + ds_csum_offset(G)),
+                                          reinterpret_cast<unsigned int*>(base + ds_bar_offset(G)),
+                                          reinterpret_cast<uint32_t*>(base + ds_tot_offset(G)),
                                           as<int>(c->errword), &sorted, true));
     } else {
         if (n > 1) {
@@ -854,7 +851,7 @@ gs_status reserve_impl(gs_ctx* c, int64_t n, int32_t V, int32_t W, int32_t H, in
                      sizeof(uint32_t) * std::max(radix_status_words((uint32_t)super_pairs, 32, 32 + sbits),
                                                  radix_status_words(nn, 0, 32)))) ||
         (st = ensure(c, c->sort_counter, sizeof(uint32_t) * 8)) ||
-        (st = ensure(c, c->ds_scratch, G * kRadixDigits * 4 + G * 8 + 64 + 4 * kRadixDigits * 4)) ||
+        (st = ensure(c, c->ds_scratch, ds_scratch_bytes(G))) ||
         (st = ensure(c, c->pairs[0], sizeof(uint64_t) * (size_t)super_pairs)) ||
         (st = ensure(c, c->pairs[1], sizeof(uint64_t) * (size_t)super_pairs)) ||
         (st = ensure(c, c->state, sizeof(float4) * pix)) || (st = ensure(c, c->count, sizeof(int) * pix)) ||
@@ -988,10 +985,10 @@ gs_status gs_render_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_
         if (persistent) {
             unsigned char* base = as<unsigned char>(c->ds_scratch);
             GS_CUDA(c, launch_depth_sort_scan(s, c->device, keys_v, keys, ids, supers_v, n, as<uint32_t>(c->offsets),
-                                              reinterpret_cast<uint32_t*>(base),
-                                              reinterpret_cast<unsigned long long*>(base + G * kRadixDigits * 4),
-                                              reinterpret_cast<unsigned int*>(base + G * kRadixDigits * 4 + G * 8),
-                                              reinterpret_cast<uint32_t*>(base + G * kRadixDigits * 4 + G * 8 + 64),
+                                              reinterpret_cast<uint32_t*>(base + ds_cnt_offset(G)),
+                                              reinterpret_cast<uint32_t*>(base + ds_csum_offset(G)),
+                                              reinterpret_cast<unsigned int*>(base + ds_bar_offset(G)),
+                                              reinterpret_cast<uint32_t*>(base + ds_tot_offset(G)),
                                               as<int>(c->errword), &sorted, false));
         } else {
             unsigned long long* scan_tot = as<unsigned long long>(c->scan_totals) + 2 * kTotalSlots;

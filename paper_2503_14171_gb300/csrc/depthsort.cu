@@ -9,10 +9,16 @@
 //   ballot per digit bit and per-warp running counters (stable), reorder it by
 //   digit in shared memory, publish the block's digit counts (and add them to
 //   the digit totals), grid barrier, derive the global offset of each of the
-//   block's digit runs, write the runs out (coalesced), grid barrier;
-//   then the exclusive scan of supers_touched[id] in the sorted order (block
-//   sums, grid barrier, block prefixes), which gives each Gaussian's first
-//   pair slot.
+//   block's digit runs, write the runs out (coalesced), grid barrier.
+// The exclusive scan of supers_touched[id] in the sorted order (each
+// Gaussian's first pair slot) rides on the last pass: a Gaussian's slot is
+// the pair count of every Gaussian before it in the final order, i.e. of the
+// lower digits (all blocks), of the same digit in earlier blocks, and of its
+// own digit run before it.  So the last pass also scans the pair counts of
+// its reordered slice and publishes their per-digit sums beside the digit
+// counts; after its one grid barrier each block derives its runs' pair-slot
+// bases exactly as it derives their positions, and writes the offsets with
+// the ids (no barrier after it).
 // This replaces a histogram kernel, four one-sweep passes and a scan kernel
 // (seven launches whose time is dominated by latency at this size) with one.
 //
@@ -31,6 +37,7 @@ constexpr int kDsRadix = 256;
 constexpr int kDsPasses = 4;
 constexpr long kGridSpinLimit = 1L << 22;
 constexpr int kDsPer = kDsMaxSlice / kDsThreads;   // slice elements per thread
+static_assert(kDsTotWords == (kDsPasses + 1) * kDsRadix, "digit totals of every pass, then the pair-count totals");
 // The pair count of each Gaussian rides along with its id through the passes:
 // id in the low kIdBits bits, min(count, kCntEsc) above; kCntEsc means "look
 // the count up" (rare: a Gaussian over 2047 super-tiles).
@@ -47,8 +54,8 @@ struct DsArgs {
     const uint32_t* counts;      // [n] pair count per Gaussian (by id)
     uint32_t* offsets;           // [n + 1] exclusive scan in depth order
     uint32_t* cnt;               // [grid][256] per-block digit counts
-    uint32_t* tot;               // [4][256] digit totals per pass (zeroed)
-    unsigned long long* bsum;    // [grid] per-block count sums
+    uint32_t* csum;              // [grid][256] per-block digit sums of the pair counts (last pass)
+    uint32_t* tot;               // [5][256] digit totals per pass, then the pair-count totals (zeroed)
     unsigned int* bar;           // [2] barrier counter and generation (zeroed)
     int* err;
     uint32_t n;
@@ -102,10 +109,16 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
     uint32_t* s_off = reinterpret_cast<uint32_t*>(s_wcnt + kDsWarps * kDsRadix);   // [256]
     uint32_t* s_boff = s_off + kDsRadix;                              // [256] block-local digit starts
     uint32_t* s_wtot = s_boff + kDsRadix;                             // [kDsWarps]
+    // last pass only (s_rank is free once the slice is reordered): pair-count
+    // scan value at each digit run's start, and each run's first pair slot
+    // minus that value
+    uint32_t* s_cbase = reinterpret_cast<uint32_t*>(s_rank);          // [256]
+    uint32_t* s_obase = s_cbase + kDsRadix;                           // [256]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt = (1u << lane) - 1u;
 
     for (int pass = 0; pass < kDsPasses; ++pass) {
+        const bool last = pass == kDsPasses - 1;
         const int shift = pass * 8;
         // ping-pong buffers chosen by condition (a run-time index into the
         // parameter struct would copy it to local memory)
@@ -202,20 +215,82 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
             s_key2[lp] = key;
             s_id2[lp] = s_id[j];
         }
+        if (last) {
+            // pair counts of the reordered slice, their exclusive scan (in
+            // s_key, free now): thread t takes a contiguous run of E positions
+            __syncthreads();
+            const uint32_t E = (m + kDsThreads - 1) / kDsThreads;
+            const uint32_t t0 = min(m, tid * E), t1 = min(m, t0 + E);
+            uint32_t sum = 0;
+            for (uint32_t j = t0; j < t1; ++j) {
+                const uint32_t v = s_id2[j];
+                uint32_t c = v >> kIdBits;
+                if (c == kCntEsc) {   // escaped: look the count up
+                    const uint32_t id = v & kIdMask;
+                    c = id < n ? a.counts[id] : 0u;
+                }
+                s_key[j] = c;
+                sum += c;
+            }
+            uint32_t x = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31) s_wtot[warp] = x;
+            __syncthreads();
+            uint32_t wb = 0, btot = 0;
+            for (int w = 0; w < kDsWarps; ++w) {
+                const uint32_t t = s_wtot[w];
+                wb += w < warp ? t : 0u;
+                btot += t;
+            }
+            uint32_t run = wb + x - sum;
+            for (uint32_t j = t0; j < t1; ++j) {
+                const uint32_t c = s_key[j];
+                s_key[j] = run;
+                run += c;
+            }
+            __syncthreads();
+            // per digit: the pair counts of its run (published, and added to
+            // the digit's total) and the scan value at the run's start
+            if (tid < kDsRadix) {
+                const uint32_t r0 = s_boff[tid], r1 = tid + 1 < kDsRadix ? s_boff[tid + 1] : m;
+                const uint32_t v0 = r0 < m ? s_key[r0] : btot, v1 = r1 < m ? s_key[r1] : btot;
+                a.csum[(size_t)blockIdx.x * kDsRadix + tid] = v1 - v0;
+                if (v1 != v0) atomicAdd(&a.tot[kDsPasses * kDsRadix + tid], v1 - v0);
+                s_cbase[tid] = v0;
+            }
+        }
         grid_barrier(a.bar, a.err);
         // global start of this block's run of each digit:
         // exclusive digit total + this digit's count in earlier blocks, the
         // latter summed by 4 groups of 256 threads (every 4th earlier block each)
         {
-            uint32_t* s_part = reinterpret_cast<uint32_t*>(s_wcnt);   // [4][256]; s_wcnt is free here
+            uint32_t* s_part = reinterpret_cast<uint32_t*>(s_wcnt);   // [2][4][256]; s_wcnt is free here
             const uint32_t d = tid & (kDsRadix - 1), g = tid / kDsRadix;
-            uint32_t p0 = 0, p1 = 0;
+            uint32_t p0 = 0, p1 = 0, q0 = 0, q1 = 0;
             uint32_t b = g;
-            for (; b + 4 < blockIdx.x; b += 8) {
-                p0 += __ldcg(a.cnt + (size_t)b * kDsRadix + d);
-                p1 += __ldcg(a.cnt + (size_t)(b + 4) * kDsRadix + d);
+            if (last) {   // the digit counts and the pair-count sums
+                for (; b + 4 < blockIdx.x; b += 8) {
+                    p0 += __ldcg(a.cnt + (size_t)b * kDsRadix + d);
+                    p1 += __ldcg(a.cnt + (size_t)(b + 4) * kDsRadix + d);
+                    q0 += __ldcg(a.csum + (size_t)b * kDsRadix + d);
+                    q1 += __ldcg(a.csum + (size_t)(b + 4) * kDsRadix + d);
+                }
+                if (b < blockIdx.x) {
+                    p0 += __ldcg(a.cnt + (size_t)b * kDsRadix + d);
+                    q0 += __ldcg(a.csum + (size_t)b * kDsRadix + d);
+                }
+                s_part[4 * kDsRadix + g * kDsRadix + d] = q0 + q1;
+            } else {
+                for (; b + 4 < blockIdx.x; b += 8) {
+                    p0 += __ldcg(a.cnt + (size_t)b * kDsRadix + d);
+                    p1 += __ldcg(a.cnt + (size_t)(b + 4) * kDsRadix + d);
+                }
+                if (b < blockIdx.x) p0 += __ldcg(a.cnt + (size_t)b * kDsRadix + d);
             }
-            if (b < blockIdx.x) p0 += __ldcg(a.cnt + (size_t)b * kDsRadix + d);
             s_part[g * kDsRadix + d] = p0 + p1;
         }
         __syncthreads();
@@ -232,12 +307,37 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
             }
             if (lane == 31) s_wtot[warp] = x;
             s_off[tid] = pre + x - tot - s_boff[tid];   // completed below with earlier warps' totals
+            if (last) {
+                // first pair slot of this block's run of digit tid, minus the
+                // run's start in the slice's pair-count scan
+                const uint32_t cpre = s_part[4 * kDsRadix + tid] + s_part[5 * kDsRadix + tid] +
+                                      s_part[6 * kDsRadix + tid] + s_part[7 * kDsRadix + tid];
+                const uint32_t ctot = __ldcg(a.tot + kDsPasses * kDsRadix + tid);
+                uint32_t xc = ctot;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, xc, o);
+                    if (lane >= o) xc += y;
+                }
+                if (lane == 31) s_wtot[kDsRadix / 32 + warp] = xc;
+                s_obase[tid] = cpre + xc - ctot - s_cbase[tid];   // completed below likewise
+            }
         }
         __syncthreads();
         if (tid < kDsRadix) {
             uint32_t wb = 0;
             for (int w = 0; w < warp; ++w) wb += s_wtot[w];
             s_off[tid] += wb;
+            if (last) {
+                uint32_t wc = 0, all = 0;
+                for (int w = 0; w < kDsRadix / 32; ++w) {
+                    const uint32_t t = s_wtot[kDsRadix / 32 + w];
+                    wc += w < warp ? t : 0u;
+                    all += t;
+                }
+                s_obase[tid] += wc;
+                if (blockIdx.x == 0 && tid == 0) a.offsets[n] = all;   // the pair total
+            }
         }
         __syncthreads();
         // write the digit runs out: consecutive threads, consecutive addresses
@@ -246,99 +346,19 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
             const uint32_t pos = s_off[(key >> shift) & 0xFFu] + j;
             if (pos < n) {
                 const uint32_t v = s_id2[j];
-                if (pass + 1 < kDsPasses) {
+                if (!last) {
                     dst_key[pos] = key;
                     dst_id[pos] = v;
-                } else {   // last pass: plain ids, and the counts in sorted order in the free key buffer
+                } else {   // last pass: plain ids and their first pair slots
                     dst_id[pos] = v & kIdMask;
-                    dst_key[pos] = v >> kIdBits;
+                    a.offsets[pos] = s_obase[(key >> shift) & 0xFFu] + s_key[j];
                 }
             }
         }
-        grid_barrier(a.bar, a.err);
+        if (!last) grid_barrier(a.bar, a.err);
     }
-
-    // exclusive scan of counts[id] over the sorted slice.  Stage the sorted ids
-    // and their gathered counts in shared memory (independent loads), then
-    // thread t scans a contiguous run of E = ceil(m / 1024) positions.
-    const uint32_t* sorted = ((kDsPasses - 1) & 1) ? a.ids[1] : a.ids[0];
-    const uint32_t* sorted_cnt = ((kDsPasses - 1) & 1) ? a.keys[1] : a.keys[0];
-    uint32_t* s_cnt = s_key;   // reuse
-    {
-        uint32_t rc[kDsPer];
-#pragma unroll
-        for (int k = 0; k < kDsPer; ++k) {
-            const uint32_t j = tid + k * kDsThreads;
-            rc[k] = j < m ? __ldcg(sorted_cnt + lo + j) : 0u;
-        }
-#pragma unroll
-        for (int k = 0; k < kDsPer; ++k) {
-            const uint32_t j = tid + k * kDsThreads;
-            if (j < m) {
-                uint32_t c = rc[k];
-                if (c == kCntEsc) {   // escaped: look the count up
-                    const uint32_t id = __ldcg(sorted + lo + j);
-                    c = id < n ? a.counts[id] : 0u;
-                }
-                s_cnt[j] = c;
-            }
-        }
-    }
-    __syncthreads();
-    const uint32_t E = (m + kDsThreads - 1) / kDsThreads;
-    const uint32_t t0 = min(m, tid * E), t1 = min(m, t0 + E);
-    unsigned long long sum = 0;
-    for (uint32_t j = t0; j < t1; ++j) sum += s_cnt[j];
-    unsigned long long x = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    __shared__ unsigned long long s_w64[kDsWarps];
-    if (lane == 31) s_w64[warp] = x;
-    __syncthreads();
-    unsigned long long wb = 0, btot = 0;
-    for (int w = 0; w < kDsWarps; ++w) {
-        const unsigned long long t = s_w64[w];
-        wb += w < warp ? t : 0ull;
-        btot += t;
-    }
-    if (tid == 0) a.bsum[blockIdx.x] = btot;
-    // block-local exclusive prefixes, in place (s_id is free again)
-    uint32_t run = (uint32_t)(wb + x - sum);
-    for (uint32_t j = t0; j < t1; ++j) {
-        const uint32_t c = s_cnt[j];
-        s_id[j] = run;
-        run += c;
-    }
-    grid_barrier(a.bar, a.err);
-    // one warp reads the block sums (lane-strided) and broadcasts the prefix:
-    // every thread reading them would hammer the same few L2 lines
-    if (warp == 0) {
-        unsigned long long bpre = 0, all = 0;
-        for (uint32_t b = lane; b < G; b += 32) {
-            const unsigned long long v = __ldcg(a.bsum + b);
-            bpre += b < blockIdx.x ? v : 0ull;
-            all += v;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            bpre += __shfl_xor_sync(0xffffffffu, bpre, o);
-            all += __shfl_xor_sync(0xffffffffu, all, o);
-        }
-        if (lane == 0) {
-            s_w64[0] = bpre;
-            s_w64[1] = all;
-        }
-    }
-    __syncthreads();
-    const uint32_t bp = (uint32_t)s_w64[0];
-    const unsigned long long all = s_w64[1];
-#pragma unroll 4
-    for (uint32_t j = tid; j < m; j += kDsThreads) a.offsets[lo + j] = bp + s_id[j];
-    if (blockIdx.x == G - 1 && tid == 0) a.offsets[n] = (uint32_t)all;
 }
+
 
 int ds_grid(int device)
 {
@@ -370,7 +390,7 @@ uint32_t depth_sort_capacity(int device)
 
 cudaError_t launch_depth_sort_scan(cudaStream_t s, int device, const uint32_t* keys_in, uint32_t* keys[2],
                                    uint32_t* ids[2], const uint32_t* counts, uint32_t n, uint32_t* offsets,
-                                   uint32_t* cnt_scratch, unsigned long long* bsum_scratch, unsigned int* bar,
+                                   uint32_t* cnt_scratch, uint32_t* csum_scratch, unsigned int* bar,
                                    uint32_t* tot_scratch, int* err, int* out_idx, bool pre_zeroed)
 {
     const int G = ds_grid(device);
@@ -381,7 +401,7 @@ cudaError_t launch_depth_sort_scan(cudaStream_t s, int device, const uint32_t* k
     cudaError_t e = cudaSuccess;
     if (!pre_zeroed) {
         if ((e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), s)) != cudaSuccess) return e;
-        if ((e = cudaMemsetAsync(tot_scratch, 0, sizeof(uint32_t) * kDsPasses * kDsRadix, s)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(tot_scratch, 0, sizeof(uint32_t) * kDsTotWords, s)) != cudaSuccess) return e;
     }
     DsArgs a;
     a.keys_in = keys_in;
@@ -393,7 +413,7 @@ cudaError_t launch_depth_sort_scan(cudaStream_t s, int device, const uint32_t* k
     a.offsets = offsets;
     a.cnt = cnt_scratch;
     a.tot = tot_scratch;
-    a.bsum = bsum_scratch;
+    a.csum = csum_scratch;
     a.bar = bar;
     a.err = err;
     a.n = n;

@@ -275,9 +275,22 @@ constexpr uint32_t kDsMaxSlice = 10240;
 constexpr uint32_t kDsMaxN = (1u << 21) - 1u;   // ids share a 32-bit word with the pair counts
 size_t depth_sort_smem_bytes();
 uint32_t depth_sort_capacity(int device);
+// Scratch of a grid of up to G blocks, carved from one buffer of
+// ds_scratch_bytes(G): per-block digit counts and pair-count sums ([G][256]
+// words each), the grid barrier (64 bytes) and the totals (kDsTotWords words);
+// the barrier and the totals (ds_zero_words() words from ds_zero_offset(G),
+// contiguous) must be zero at launch unless the launcher clears them.
+constexpr uint32_t kDsTotWords = 5 * 256;
+constexpr size_t ds_cnt_offset(size_t) { return 0; }
+constexpr size_t ds_csum_offset(size_t G) { return G * 256 * 4; }
+constexpr size_t ds_bar_offset(size_t G) { return 2 * G * 256 * 4; }
+constexpr size_t ds_tot_offset(size_t G) { return ds_bar_offset(G) + 64; }
+constexpr size_t ds_scratch_bytes(size_t G) { return ds_tot_offset(G) + 4 * (size_t)kDsTotWords; }
+constexpr size_t ds_zero_offset(size_t G) { return ds_bar_offset(G); }
+constexpr uint32_t ds_zero_words() { return 16 + kDsTotWords; }
 cudaError_t launch_depth_sort_scan(cudaStream_t s, int device, const uint32_t* keys_in, uint32_t* keys[2],
                                    uint32_t* ids[2], const uint32_t* counts, uint32_t n, uint32_t* offsets,
-                                   uint32_t* cnt_scratch, unsigned long long* bsum_scratch, unsigned int* bar,
+                                   uint32_t* cnt_scratch, uint32_t* csum_scratch, unsigned int* bar,
                                    uint32_t* tot_scratch, int* err, int* out_idx, bool pre_zeroed = false);
 
 // pairs at offsets >= cap are counted but not written (the capacity check of

@@ -51,11 +51,9 @@ constexpr size_t kOffId0 = kOffKey1 + align256(4ull * kNaMaxGaussians);
 constexpr size_t kOffId1 = kOffId0 + align256(4ull * kNaMaxGaussians);
 constexpr size_t kOffOffsets = kOffId1 + align256(4ull * kNaMaxGaussians);
 constexpr size_t kOffTotals = kOffOffsets + align256(4ull * (kNaMaxGaussians + 1));
-constexpr size_t kOffDsCnt = kOffTotals + align256(8ull * (2 * kTotalSlots + 4));
-constexpr size_t kOffDsSum = kOffDsCnt + align256(4ull * 256 * kNaMaxBlocks);
-constexpr size_t kOffDsBar = kOffDsSum + align256(8ull * kNaMaxBlocks);
-constexpr size_t kOffDsTot = kOffDsBar + 256;
-constexpr size_t kOffSCounts = kOffDsTot + align256(4ull * 4 * 256);
+constexpr size_t kOffDs = kOffTotals + align256(8ull * (2 * kTotalSlots + 4));   // the persistent depth sort's scratch
+constexpr size_t kOffDsSum = kOffDs + align256(ds_scratch_bytes(kNaMaxBlocks));   // the fallback scan's partials
+constexpr size_t kOffSCounts = kOffDsSum + align256(8ull * kNaMaxBlocks);
 constexpr size_t kOffSRanges = kOffSCounts + align256(4ull * kCountCopies * kNaMaxSupers);
 constexpr size_t kOffHist = kOffSRanges + align256(8ull * kNaMaxSupers);
 constexpr size_t kOffStatus = kOffHist + align256(4ull * 8 * 256);
@@ -189,10 +187,12 @@ extern "C" gs_status gs_render_with_grads_noalloc(const gs_gaussians* g, const g
     int sorted = 0;
     const uint32_t ds_cap = n > 1 ? depth_sort_capacity(dev) : 0u;
     if (n > 1 && n <= ds_cap && n <= kDsMaxN && ds_cap / kDsMaxSlice <= kNaMaxBlocks) {
+        const size_t G = ds_cap / kDsMaxSlice;
         NA_CUDA(launch_depth_sort_scan(s, dev, keys[0], keys, ids, at<uint32_t>(base, kOffSupers), n, offsets,
-                                       at<uint32_t>(base, kOffDsCnt), at<unsigned long long>(base, kOffDsSum),
-                                       at<unsigned int>(base, kOffDsBar), at<uint32_t>(base, kOffDsTot), err,
-                                       &sorted));
+                                       at<uint32_t>(base, kOffDs + ds_cnt_offset(G)),
+                                       at<uint32_t>(base, kOffDs + ds_csum_offset(G)),
+                                       at<unsigned int>(base, kOffDs + ds_bar_offset(G)),
+                                       at<uint32_t>(base, kOffDs + ds_tot_offset(G)), err, &sorted));
     } else {
         if (n > 1)
             NA_CUDA(radix_sort_u32_pairs(s, keys, ids, n, 0, 32, at<uint32_t>(base, kOffHist),
