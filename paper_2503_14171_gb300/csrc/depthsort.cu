@@ -3,13 +3,23 @@
 //
 // For up to kDsMaxSlice Gaussians per SM the whole sort runs as a single
 // cooperative kernel, one 1024-thread block per SM, each block owning a
-// contiguous slice of the sequence:
-//   4 stable LSD passes over the 8-bit digits of the FP32 depth bits (ids in
-//   ascending order ride along): load the slice, rank it by digit with one
-//   ballot per digit bit and per-warp running counters (stable), reorder it by
-//   digit in shared memory, publish the block's digit counts (and add them to
-//   the digit totals), grid barrier, derive the global offset of each of the
-//   block's digit runs, write the runs out (coalesced), grid barrier.
+// contiguous slice of the sequence.
+//
+// Key range.  Every visible depth is a positive FP32 value, and the order of
+// positive FP32 values is that of their bit patterns, so subtracting the
+// smallest visible key keeps the order; the keys of the Gaussians that emit no
+// pair (0xFFFFFFFF) go last.  Once the slice is loaded, each block publishes
+// the range of its visible keys, and after one grid barrier every block knows
+// the whole range: when it spans fewer than 2^27 - 1 values (16 binades, a
+// depth ratio up to 65536) the biased keys fit 27 bits and three passes of 9
+// bits sort them, otherwise four.
+//
+// Each pass is a stable LSD pass over a 9-bit digit (ids in ascending order
+// ride along): stage the slice, rank it by digit with one ballot per digit bit
+// and per-warp running counters (stable), reorder it by digit in shared
+// memory, publish the block's digit counts (and add them to the digit
+// totals), grid barrier, derive the global offset of each of the block's digit
+// runs, write the runs out (coalesced), grid barrier.
 // The exclusive scan of supers_touched[id] in the sorted order (each
 // Gaussian's first pair slot) rides on the last pass: a Gaussian's slot is
 // the pair count of every Gaussian before it in the final order, i.e. of the
@@ -18,7 +28,8 @@
 // its reordered slice and publishes their per-digit sums beside the digit
 // counts; after its one grid barrier each block derives its runs' pair-slot
 // bases exactly as it derives their positions, and writes the offsets with
-// the ids (no barrier after it).
+// the ids (no barrier after it).  The passes alternate between the two
+// buffers so that the last one always writes ids[1].
 // This replaces a histogram kernel, four one-sweep passes and a scan kernel
 // (seven launches whose time is dominated by latency at this size) with one.
 //
@@ -33,11 +44,15 @@ namespace {
 
 constexpr int kDsThreads = 1024;
 constexpr int kDsWarps = kDsThreads / 32;
-constexpr int kDsRadix = 256;
-constexpr int kDsPasses = 4;
+constexpr int kDsBits = 9;
+constexpr int kDsRadix = 1 << kDsBits;
+constexpr int kDsMaxPasses = 4;                    // 36 bits: any 32-bit key
+constexpr uint32_t kCulled = 0xFFFFFFFFu;          // key of a Gaussian that emits no pair
+constexpr uint32_t kCulled3 = (1u << (3 * kDsBits)) - 1u;   // its biased key when three passes suffice
 constexpr long kGridSpinLimit = 1L << 22;
 constexpr int kDsPer = kDsMaxSlice / kDsThreads;   // slice elements per thread
-static_assert(kDsTotWords == (kDsPasses + 1) * kDsRadix, "digit totals of every pass, then the pair-count totals");
+static_assert(kDsTotWords == (kDsMaxPasses + 1) * kDsRadix, "digit totals of every pass, then the pair-count totals");
+static_assert(kDsRadix == kDsRadixWords, "the scratch layout's digit count");
 // The pair count of each Gaussian rides along with its id through the passes:
 // id in the low kIdBits bits, min(count, kCntEsc) above; kCntEsc means "look
 // the count up" (rare: a Gaussian over 2047 super-tiles).
@@ -53,9 +68,10 @@ struct DsArgs {
     uint32_t* ids[2];
     const uint32_t* counts;      // [n] pair count per Gaussian (by id)
     uint32_t* offsets;           // [n + 1] exclusive scan in depth order
-    uint32_t* cnt;               // [grid][256] per-block digit counts
-    uint32_t* csum;              // [grid][256] per-block digit sums of the pair counts (last pass)
-    uint32_t* tot;               // [5][256] digit totals per pass, then the pair-count totals (zeroed)
+    uint32_t* cnt;               // [grid][512] per-block digit counts
+    uint32_t* csum;              // [grid][512] per-block digit sums of the pair counts (last pass);
+                                 // words 0, 1 of a block's row first carry its key range
+    uint32_t* tot;               // [5][512] digit totals per pass, then the pair-count totals (zeroed)
     unsigned int* bar;           // [2] barrier counter and generation (zeroed)
     int* err;
     uint32_t n;
@@ -99,50 +115,108 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
     const uint32_t hi = min(n, lo + slice);
     const uint32_t m = hi > lo ? hi - lo : 0u;
     const uint32_t cw = (m + kDsWarps - 1) / kDsWarps;   // elements per warp chunk
+    constexpr uint32_t R = kDsRadix;
 
     uint32_t* s_key = reinterpret_cast<uint32_t*>(smem);
     uint32_t* s_id = s_key + kDsMaxSlice;
     uint32_t* s_key2 = s_id + kDsMaxSlice;                            // slice reordered by digit
     uint32_t* s_id2 = s_key2 + kDsMaxSlice;
     uint16_t* s_rank = reinterpret_cast<uint16_t*>(s_id2 + kDsMaxSlice);
-    uint16_t* s_wcnt = s_rank + kDsMaxSlice;                          // [kDsWarps][256]
-    uint32_t* s_off = reinterpret_cast<uint32_t*>(s_wcnt + kDsWarps * kDsRadix);   // [256]
-    uint32_t* s_boff = s_off + kDsRadix;                              // [256] block-local digit starts
-    uint32_t* s_wtot = s_boff + kDsRadix;                             // [kDsWarps]
+    uint16_t* s_wcnt = s_rank + kDsMaxSlice;                          // [kDsWarps][R]
+    uint32_t* s_off = reinterpret_cast<uint32_t*>(s_wcnt + kDsWarps * R);   // [R]
+    uint32_t* s_boff = s_off + R;                                     // [R] block-local digit starts
+    uint32_t* s_wtot = s_boff + R;                                    // [kDsWarps]
     // last pass only (s_rank is free once the slice is reordered): pair-count
     // scan value at each digit run's start, and each run's first pair slot
     // minus that value
-    uint32_t* s_cbase = reinterpret_cast<uint32_t*>(s_rank);          // [256]
-    uint32_t* s_obase = s_cbase + kDsRadix;                           // [256]
+    uint32_t* s_cbase = reinterpret_cast<uint32_t*>(s_rank);          // [R]
+    uint32_t* s_obase = s_cbase + R;                                  // [R]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt = (1u << lane) - 1u;
 
-    for (int pass = 0; pass < kDsPasses; ++pass) {
-        const bool last = pass == kDsPasses - 1;
-        const int shift = pass * 8;
+    // ---- the slice's keys and the range of the visible ones ----
+    uint32_t rk[kDsPer];
+    {
+        uint32_t kmin = kCulled, kmax = 0u;
+#pragma unroll
+        for (int k = 0; k < kDsPer; ++k) {
+            const uint32_t j = tid + k * kDsThreads;
+            rk[k] = kCulled;
+            if (j < m) rk[k] = __ldcg(a.keys_in + lo + j);
+            if (rk[k] != kCulled) {
+                kmin = min(kmin, rk[k]);
+                kmax = max(kmax, rk[k]);
+            }
+        }
+        kmin = __reduce_min_sync(0xffffffffu, kmin);
+        kmax = __reduce_max_sync(0xffffffffu, kmax);
+        if (lane == 0) {
+            s_off[warp] = kmin;
+            s_off[kDsWarps + warp] = kmax;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < kDsWarps; ++w) {
+                kmin = min(kmin, s_off[w]);
+                kmax = max(kmax, s_off[kDsWarps + w]);
+            }
+            a.csum[(size_t)blockIdx.x * R] = kmin;
+            a.csum[(size_t)blockIdx.x * R + 1] = kmax;
+        }
+    }
+    grid_barrier(a.bar, a.err);
+    if (warp == 0) {
+        uint32_t kmin = kCulled, kmax = 0u;
+        for (uint32_t b = lane; b < G; b += 32) {
+            kmin = min(kmin, __ldcg(a.csum + (size_t)b * R));
+            kmax = max(kmax, __ldcg(a.csum + (size_t)b * R + 1));
+        }
+        kmin = __reduce_min_sync(0xffffffffu, kmin);
+        kmax = __reduce_max_sync(0xffffffffu, kmax);
+        if (lane == 0) {
+            s_wtot[0] = kmin;
+            s_wtot[1] = kmax;
+        }
+    }
+    __syncthreads();
+    const bool any = s_wtot[0] <= s_wtot[1];
+    const uint32_t bias = any ? s_wtot[0] : 0u;
+    const int P = (any ? s_wtot[1] - s_wtot[0] : 0u) < kCulled3 ? 3 : 4;
+    const uint32_t culled = P == 3 ? kCulled3 : kCulled - bias;   // above every biased visible key
+    __syncthreads();   // s_wtot is reused below
+#pragma unroll
+    for (int k = 0; k < kDsPer; ++k) {
+        const uint32_t j = tid + k * kDsThreads;
+        if (j < m) {
+            s_key[j] = rk[k] == kCulled ? culled : rk[k] - bias;
+            const uint32_t c = a.counts[lo + j];
+            s_id[j] = (lo + j) | ((c < kCntEsc ? c : kCntEsc) << kIdBits);
+        }
+    }
+
+    for (int pass = 0; pass < P; ++pass) {
+        const bool last = pass == P - 1;
+        const int shift = pass * kDsBits;
         // ping-pong buffers chosen by condition (a run-time index into the
-        // parameter struct would copy it to local memory)
-        const bool odd = pass & 1;
-        const uint32_t* src_key = pass == 0 ? a.keys_in : (odd ? a.keys[0] : a.keys[1]);
-        const uint32_t* src_id = pass == 0 ? nullptr : (odd ? a.ids[0] : a.ids[1]);
-        uint32_t* dst_key = odd ? a.keys[1] : a.keys[0];
-        uint32_t* dst_id = odd ? a.ids[1] : a.ids[0];
-        for (int i = tid; i < kDsWarps * kDsRadix; i += kDsThreads) s_wcnt[i] = 0;
-        // stage the slice in shared memory: coalesced loads (L2, the previous
-        // pass's scatter by other blocks), all of a thread's loads in flight at once
-        {
-            uint32_t rk[kDsPer], ri[kDsPer];
+        // parameter struct would copy it to local memory); the last pass
+        // writes buffer 1
+        const bool to1 = ((pass + P) & 1) != 0;
+        const uint32_t* src_key = to1 ? a.keys[0] : a.keys[1];
+        const uint32_t* src_id = to1 ? a.ids[0] : a.ids[1];
+        uint32_t* dst_key = to1 ? a.keys[1] : a.keys[0];
+        uint32_t* dst_id = to1 ? a.ids[1] : a.ids[0];
+        for (int i = tid; i < kDsWarps * (int)R; i += kDsThreads) s_wcnt[i] = 0;
+        // stage the slice in shared memory (the first pass has it already):
+        // coalesced loads (L2, the previous pass's scatter by other blocks),
+        // all of a thread's loads in flight at once
+        if (pass > 0) {
+            uint32_t ri[kDsPer];
 #pragma unroll
             for (int k = 0; k < kDsPer; ++k) {
                 const uint32_t j = tid + k * kDsThreads;
                 if (j < m) {
                     rk[k] = __ldcg(src_key + lo + j);
-                    if (pass == 0) {
-                        const uint32_t c = a.counts[lo + j];
-                        ri[k] = (lo + j) | ((c < kCntEsc ? c : kCntEsc) << kIdBits);
-                    } else {
-                        ri[k] = __ldcg(src_id + lo + j);
-                    }
+                    ri[k] = __ldcg(src_id + lo + j);
                 }
             }
 #pragma unroll
@@ -160,37 +234,37 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
         for (uint32_t base = wlo; base < whi; base += 32) {
             const uint32_t j = base + lane;
             const bool valid = j < whi;
-            const uint32_t d = valid ? (s_key[j] >> shift) & 0xFFu : 0u;
+            const uint32_t d = valid ? (s_key[j] >> shift) & (R - 1) : 0u;
             // lanes holding the same digit: one ballot per digit bit (a match
             // instruction's cost grows with the distinct digits in the warp)
             uint32_t peers = __ballot_sync(0xffffffffu, valid);
 #pragma unroll
-            for (int b = 0; b < 8; ++b) {
+            for (int b = 0; b < kDsBits; ++b) {
                 const bool bit = (d >> b) & 1u;
                 const uint32_t bal = __ballot_sync(0xffffffffu, bit);
                 peers &= bit ? bal : ~bal;
             }
             uint32_t prev = 0;
-            if (valid) prev = s_wcnt[warp * kDsRadix + d];
+            if (valid) prev = s_wcnt[warp * R + d];
             __syncwarp();
             if (valid) {
                 s_rank[j] = (uint16_t)(prev + __popc(peers & lt));
-                if (lane == 31 - __clz(peers)) s_wcnt[warp * kDsRadix + d] = (uint16_t)(prev + __popc(peers));
+                if (lane == 31 - __clz(peers)) s_wcnt[warp * R + d] = (uint16_t)(prev + __popc(peers));
             }
             __syncwarp();
         }
         __syncthreads();
         // per digit: exclusive prefix over warps, the block's count (published,
         // and added to the digit total), and the block-local start of the digit
-        if (tid < kDsRadix) {
+        if (tid < (int)R) {
             uint32_t run = 0;
             for (int w = 0; w < kDsWarps; ++w) {
-                const uint32_t c = s_wcnt[w * kDsRadix + tid];
-                s_wcnt[w * kDsRadix + tid] = (uint16_t)run;
+                const uint32_t c = s_wcnt[w * R + tid];
+                s_wcnt[w * R + tid] = (uint16_t)run;
                 run += c;
             }
-            a.cnt[(size_t)blockIdx.x * kDsRadix + tid] = run;
-            if (run) atomicAdd(&a.tot[pass * kDsRadix + tid], run);
+            a.cnt[(size_t)blockIdx.x * R + tid] = run;
+            if (run) atomicAdd(&a.tot[pass * R + tid], run);
             uint32_t x = run;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -201,7 +275,7 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
             s_boff[tid] = x - run;
         }
         __syncthreads();
-        if (tid < kDsRadix) {
+        if (tid < (int)R) {
             uint32_t wb = 0;
             for (int w = 0; w < warp; ++w) wb += s_wtot[w];
             s_boff[tid] += wb;
@@ -210,8 +284,8 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
         // reorder the slice by digit (stable) in shared memory
         for (uint32_t j = tid; j < m; j += kDsThreads) {
             const uint32_t key = s_key[j];
-            const uint32_t d = (key >> shift) & 0xFFu;
-            const uint32_t lp = s_boff[d] + s_wcnt[(j / cw) * kDsRadix + d] + s_rank[j];
+            const uint32_t d = (key >> shift) & (R - 1);
+            const uint32_t lp = s_boff[d] + s_wcnt[(j / cw) * R + d] + s_rank[j];
             s_key2[lp] = key;
             s_id2[lp] = s_id[j];
         }
@@ -255,50 +329,49 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
             __syncthreads();
             // per digit: the pair counts of its run (published, and added to
             // the digit's total) and the scan value at the run's start
-            if (tid < kDsRadix) {
-                const uint32_t r0 = s_boff[tid], r1 = tid + 1 < kDsRadix ? s_boff[tid + 1] : m;
+            if (tid < (int)R) {
+                const uint32_t r0 = s_boff[tid], r1 = tid + 1 < (int)R ? s_boff[tid + 1] : m;
                 const uint32_t v0 = r0 < m ? s_key[r0] : btot, v1 = r1 < m ? s_key[r1] : btot;
-                a.csum[(size_t)blockIdx.x * kDsRadix + tid] = v1 - v0;
-                if (v1 != v0) atomicAdd(&a.tot[kDsPasses * kDsRadix + tid], v1 - v0);
+                a.csum[(size_t)blockIdx.x * R + tid] = v1 - v0;
+                if (v1 != v0) atomicAdd(&a.tot[kDsMaxPasses * R + tid], v1 - v0);
                 s_cbase[tid] = v0;
             }
         }
         grid_barrier(a.bar, a.err);
         // global start of this block's run of each digit:
         // exclusive digit total + this digit's count in earlier blocks, the
-        // latter summed by 4 groups of 256 threads (every 4th earlier block each)
+        // latter summed by 2 groups of 512 threads (every other earlier block each)
         {
-            uint32_t* s_part = reinterpret_cast<uint32_t*>(s_wcnt);   // [2][4][256]; s_wcnt is free here
-            const uint32_t d = tid & (kDsRadix - 1), g = tid / kDsRadix;
+            uint32_t* s_part = reinterpret_cast<uint32_t*>(s_wcnt);   // [2][2][R]; s_wcnt is free here
+            const uint32_t d = tid & (R - 1), g = tid / R;
             uint32_t p0 = 0, p1 = 0, q0 = 0, q1 = 0;
             uint32_t b = g;
             if (last) {   // the digit counts and the pair-count sums
-                for (; b + 4 < blockIdx.x; b += 8) {
-                    p0 += __ldcg(a.cnt + (size_t)b * kDsRadix + d);
-                    p1 += __ldcg(a.cnt + (size_t)(b + 4) * kDsRadix + d);
-                    q0 += __ldcg(a.csum + (size_t)b * kDsRadix + d);
-                    q1 += __ldcg(a.csum + (size_t)(b + 4) * kDsRadix + d);
+                for (; b + 2 < blockIdx.x; b += 4) {
+                    p0 += __ldcg(a.cnt + (size_t)b * R + d);
+                    p1 += __ldcg(a.cnt + (size_t)(b + 2) * R + d);
+                    q0 += __ldcg(a.csum + (size_t)b * R + d);
+                    q1 += __ldcg(a.csum + (size_t)(b + 2) * R + d);
                 }
                 if (b < blockIdx.x) {
-                    p0 += __ldcg(a.cnt + (size_t)b * kDsRadix + d);
-                    q0 += __ldcg(a.csum + (size_t)b * kDsRadix + d);
+                    p0 += __ldcg(a.cnt + (size_t)b * R + d);
+                    q0 += __ldcg(a.csum + (size_t)b * R + d);
                 }
-                s_part[4 * kDsRadix + g * kDsRadix + d] = q0 + q1;
+                s_part[2 * R + g * R + d] = q0 + q1;
             } else {
-                for (; b + 4 < blockIdx.x; b += 8) {
-                    p0 += __ldcg(a.cnt + (size_t)b * kDsRadix + d);
-                    p1 += __ldcg(a.cnt + (size_t)(b + 4) * kDsRadix + d);
+                for (; b + 2 < blockIdx.x; b += 4) {
+                    p0 += __ldcg(a.cnt + (size_t)b * R + d);
+                    p1 += __ldcg(a.cnt + (size_t)(b + 2) * R + d);
                 }
-                if (b < blockIdx.x) p0 += __ldcg(a.cnt + (size_t)b * kDsRadix + d);
+                if (b < blockIdx.x) p0 += __ldcg(a.cnt + (size_t)b * R + d);
             }
-            s_part[g * kDsRadix + d] = p0 + p1;
+            s_part[g * R + d] = p0 + p1;
         }
         __syncthreads();
-        if (tid < kDsRadix) {
+        if (tid < (int)R) {
             const uint32_t* s_part = reinterpret_cast<const uint32_t*>(s_wcnt);
-            const uint32_t tot = __ldcg(a.tot + pass * kDsRadix + tid);
-            const uint32_t pre = s_part[tid] + s_part[kDsRadix + tid] + s_part[2 * kDsRadix + tid] +
-                                 s_part[3 * kDsRadix + tid];
+            const uint32_t tot = __ldcg(a.tot + pass * R + tid);
+            const uint32_t pre = s_part[tid] + s_part[R + tid];
             uint32_t x = tot;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -310,28 +383,27 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
             if (last) {
                 // first pair slot of this block's run of digit tid, minus the
                 // run's start in the slice's pair-count scan
-                const uint32_t cpre = s_part[4 * kDsRadix + tid] + s_part[5 * kDsRadix + tid] +
-                                      s_part[6 * kDsRadix + tid] + s_part[7 * kDsRadix + tid];
-                const uint32_t ctot = __ldcg(a.tot + kDsPasses * kDsRadix + tid);
+                const uint32_t cpre = s_part[2 * R + tid] + s_part[3 * R + tid];
+                const uint32_t ctot = __ldcg(a.tot + kDsMaxPasses * R + tid);
                 uint32_t xc = ctot;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
                     const uint32_t y = __shfl_up_sync(0xffffffffu, xc, o);
                     if (lane >= o) xc += y;
                 }
-                if (lane == 31) s_wtot[kDsRadix / 32 + warp] = xc;
+                if (lane == 31) s_wtot[R / 32 + warp] = xc;
                 s_obase[tid] = cpre + xc - ctot - s_cbase[tid];   // completed below likewise
             }
         }
         __syncthreads();
-        if (tid < kDsRadix) {
+        if (tid < (int)R) {
             uint32_t wb = 0;
             for (int w = 0; w < warp; ++w) wb += s_wtot[w];
             s_off[tid] += wb;
             if (last) {
                 uint32_t wc = 0, all = 0;
-                for (int w = 0; w < kDsRadix / 32; ++w) {
-                    const uint32_t t = s_wtot[kDsRadix / 32 + w];
+                for (int w = 0; w < (int)R / 32; ++w) {
+                    const uint32_t t = s_wtot[R / 32 + w];
                     wc += w < warp ? t : 0u;
                     all += t;
                 }
@@ -343,7 +415,8 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
         // write the digit runs out: consecutive threads, consecutive addresses
         for (uint32_t j = tid; j < m; j += kDsThreads) {
             const uint32_t key = s_key2[j];
-            const uint32_t pos = s_off[(key >> shift) & 0xFFu] + j;
+            const uint32_t d = (key >> shift) & (R - 1);
+            const uint32_t pos = s_off[d] + j;
             if (pos < n) {
                 const uint32_t v = s_id2[j];
                 if (!last) {
@@ -351,14 +424,13 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
                     dst_id[pos] = v;
                 } else {   // last pass: plain ids and their first pair slots
                     dst_id[pos] = v & kIdMask;
-                    a.offsets[pos] = s_obase[(key >> shift) & 0xFFu] + s_key[j];
+                    a.offsets[pos] = s_obase[d] + s_key[j];
                 }
             }
         }
         if (!last) grid_barrier(a.bar, a.err);
     }
 }
-
 
 int ds_grid(int device)
 {
@@ -432,7 +504,7 @@ cudaError_t launch_depth_sort_scan(cudaStream_t s, int device, const uint32_t* k
     cfg.numAttrs = 1;
     e = cudaLaunchKernelEx(&cfg, k_depth_sort_scan, a);
     note_launch();
-    *out_idx = (kDsPasses - 1) & 1;
+    *out_idx = 1;   // the last pass writes ids[1]
     return e;
 }
 

@@ -276,14 +276,15 @@ constexpr uint32_t kDsMaxN = (1u << 21) - 1u;   // ids share a 32-bit word with 
 size_t depth_sort_smem_bytes();
 uint32_t depth_sort_capacity(int device);
 // Scratch of a grid of up to G blocks, carved from one buffer of
-// ds_scratch_bytes(G): per-block digit counts and pair-count sums ([G][256]
+// ds_scratch_bytes(G): per-block digit counts and pair-count sums ([G][512]
 // words each), the grid barrier (64 bytes) and the totals (kDsTotWords words);
 // the barrier and the totals (ds_zero_words() words from ds_zero_offset(G),
 // contiguous) must be zero at launch unless the launcher clears them.
-constexpr uint32_t kDsTotWords = 5 * 256;
+constexpr uint32_t kDsRadixWords = 512;
+constexpr uint32_t kDsTotWords = 5 * kDsRadixWords;
 constexpr size_t ds_cnt_offset(size_t) { return 0; }
-constexpr size_t ds_csum_offset(size_t G) { return G * 256 * 4; }
-constexpr size_t ds_bar_offset(size_t G) { return 2 * G * 256 * 4; }
+constexpr size_t ds_csum_offset(size_t G) { return G * kDsRadixWords * 4; }
+constexpr size_t ds_bar_offset(size_t G) { return 2 * G * kDsRadixWords * 4; }
 constexpr size_t ds_tot_offset(size_t G) { return ds_bar_offset(G) + 64; }
 constexpr size_t ds_scratch_bytes(size_t G) { return ds_tot_offset(G) + 4 * (size_t)kDsTotWords; }
 constexpr size_t ds_zero_offset(size_t G) { return ds_bar_offset(G); }

@@ -91,6 +91,44 @@ def test_bins_bit_exact(gs, ora, name, kw, camkind, W, H):
         assert np.all(t[s:e] == tile)
 
 
+def _wide_depth_scene(n=6000, seed=21, z=(0.02, 3000.0)):
+    """Depths log-uniform over a ratio of 150,000 (beyond the 2^27 FP32 steps
+    that three 9-bit radix passes cover), positions and scales in proportion
+    to depth so that every depth is on screen at a similar pixel size."""
+    scene = scenes.random_scene(n=n, seed=seed)
+    rng = np.random.default_rng(seed + 1)
+    d = np.exp(rng.uniform(np.log(z[0]), np.log(z[1]), n))
+    scene["means"][:, 2] = d
+    scene["means"][:, :2] *= (0.5 * d)[:, None]
+    scene["log_scales"] += np.log(0.6 * d).astype(np.float32)[:, None]
+    return scene
+
+
+@pytest.mark.parametrize("z", [(0.02, 3000.0), (0.5, 8.0)])
+def test_bins_bit_exact_over_depth_ranges(gs, ora, z):
+    """The depth sort biases the FP32 depth bits by the smallest visible one and
+    takes three 9-bit passes when the visible keys span fewer than 2^27 - 1
+    values, four otherwise: both cases against the oracle's bins, bit for bit."""
+    W, H = 96, 64
+    scene = _wide_depth_scene(z=z)
+    cam = scenes.pinhole_camera(W, H, znear=0.01)
+    proj = ora.project(scene, cam, W, H)
+    vis = proj["tiles_touched"] > 0
+    bits = proj["depth"][vis].astype(np.float32).view(np.uint32).astype(np.int64)
+    span = int(bits.max() - bits.min())
+    assert (span >= (1 << 27) - 1) == (z[1] / z[0] > 65536)   # the case this parameter is meant to hit
+    ref = ora.bin_pairs(proj)
+    with gs.Context() as ctx:
+        ctx.project(gs.DeviceScene(scene), cam, W, H)
+        keys, vals, ranges = (t.cpu().numpy() for t in ctx.read_bins())
+    drop = np.nonzero(proj["borderline"])[0].astype(np.uint32)
+    gk, gv = pairs_without(keys.view(np.uint64), vals.view(np.uint32), drop)
+    rk, rv = pairs_without(ref["keys"], ref["vals"], drop)
+    assert len(rk) > 1000
+    assert np.array_equal(gk, rk)
+    assert np.array_equal(gv, rv)
+
+
 @pytest.mark.parametrize("name,kw,camkind,W,H", CASES)
 @pytest.mark.parametrize("bg", [(0.0, 0.0, 0.0), (0.2, 0.5, 0.9)])
 def test_render_with_grads(gs, ora, name, kw, camkind, W, H, bg):
