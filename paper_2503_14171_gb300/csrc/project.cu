@@ -224,6 +224,45 @@ __device__ __forceinline__ void view_records(const ViewProj& v, float mx3, float
 
 constexpr int kProjThreads = 128;
 
+// Copy the SH coefficients of a warp's cnt Gaussians (contiguous, KF floats
+// each) into s[gi][k].  From a 16-byte aligned source every lane first issues
+// all of its 16-byte loads, then scatters them into the padded rows; otherwise
+// (or for the last few floats) scalar coalesced loads.
+template <int KF, int PITCH>
+__device__ __forceinline__ void stage_sh(float (*s)[PITCH], const float* __restrict__ src, int cnt, int lane)
+{
+    const int tot = cnt * KF;
+    int done = 0;
+    if ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+        constexpr int kPer = (32 * KF / 4 + 31) / 32;   // float4 per lane for a full warp
+        const int tot4 = tot >> 2;
+        const float4* src4 = reinterpret_cast<const float4*>(src);
+        float4 v[kPer];
+#pragma unroll
+        for (int r = 0; r < kPer; ++r) {
+            const int q = lane + 32 * r;
+            if (q < tot4) v[r] = __ldcs(src4 + q);
+        }
+#pragma unroll
+        for (int r = 0; r < kPer; ++r) {
+            const int q = lane + 32 * r;
+            if (q < tot4) {
+                const float e[4] = {v[r].x, v[r].y, v[r].z, v[r].w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int f = 4 * q + c, gi = f / KF;
+                    s[gi][f - gi * KF] = e[c];
+                }
+            }
+        }
+        done = 4 * tot4;
+    }
+    for (int f = done + lane; f < tot; f += 32) {
+        const int gi = f / KF;
+        s[gi][f - gi * KF] = src[f];
+    }
+}
+
 // DEG: SH degree 0..3, or -1 for direct RGB colours.  Each warp first copies the
 // SH coefficients of its 32 Gaussians (contiguous, (DEG+1)^2 * 3 floats each)
 // into shared memory with coalesced loads; the row pitch is padded to an odd
@@ -254,14 +293,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
     if (DEG >= 0) {
         const int wbase = blockIdx.x * blockDim.x + warp * 32;
         const int cnt = min(32, n - wbase);
-        if (cnt > 0) {
-            const float* src = sh + (size_t)wbase * KF;
-            const int tot = cnt * KF;
-            for (int q = lane; q < tot; q += 32) {
-                const int gi = q / KF;
-                s_sh[warp][gi][q - gi * KF] = src[q];
-            }
-        }
+        if (cnt > 0) stage_sh<KF, PITCH>(s_sh[warp], sh + (size_t)wbase * KF, cnt, lane);
         __syncwarp();
     }
     // every lane runs to the warp reduction below; the tail of the last warp
@@ -344,14 +376,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project_views(
     if (DEG >= 0) {
         const int wbase = blockIdx.x * blockDim.x + warp * 32;
         const int cnt = min(32, n - wbase);
-        if (cnt > 0) {
-            const float* src = sh + (size_t)wbase * KF;
-            const int tot = cnt * KF;
-            for (int q = lane; q < tot; q += 32) {
-                const int gi = q / KF;
-                s_sh[warp][gi][q - gi * KF] = src[q];
-            }
-        }
+        if (cnt > 0) stage_sh<KF, PITCH>(s_sh[warp], sh + (size_t)wbase * KF, cnt, lane);
         __syncwarp();
     }
     const bool inrange = i < n;
@@ -469,13 +494,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project_bwd(
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int wbase = blockIdx.x * blockDim.x + warp * 32;
     const int wcnt = min(32, n - wbase);
-    if (DEG >= 0 && wcnt > 0) {
-        const float* src = sh + (size_t)wbase * KF;
-        for (int q = lane; q < wcnt * KF; q += 32) {
-            const int gi = q / KF;
-            s_sh[warp][gi][q - gi * KF] = src[q];
-        }
-    }
+    if (DEG >= 0 && wcnt > 0) stage_sh<KF, PITCH>(s_sh[warp], sh + (size_t)wbase * KF, wcnt, lane);
     __syncwarp();
     const bool inrange = i < n;
     float gshv[DEG >= 0 ? KF : 1];
