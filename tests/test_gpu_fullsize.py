@@ -230,16 +230,15 @@ def test_full_upscale_2x_sampled(ora, low):
     _check_upscale(ora, low["C"], low["G"], low["out"], pix, OUT_W, OUT_H)
 
 
-def test_full_backward_sampled(gs, ora, scene, low):
-    """gs_backward for dL/d(output) non-zero on 300 seeded output pixels,
+def _check_backward_sampled(ora, scene, n, cam, proj, bins, ctx, upstream, seed):
+    """gs_backward for an upstream gradient that is non-zero only on 300
+    seeded output pixels (upstream(hx, hy, rng) gives its [3, k] values there),
     against upscale adjoint -> blend adjoint on the low-res pixels they read
     -> projection adjoint of the Gaussians those pixels blend.  Output pixels
-    whose cell corners hold a pixel the forward check
-    excludes (near-threshold decisions, a rect-borderline Gaussian above the
-    cut-off) are dropped."""
+    whose cell corners hold a pixel the forward check excludes (near-threshold
+    decisions, a rect-borderline Gaussian above the cut-off) are dropped."""
     import torch
-    proj, bins, ctx = low["proj"], low["bins"], low["ctx"]
-    rng = np.random.default_rng(5)
+    rng = np.random.default_rng(seed)
     hx, hy = rng.integers(0, OUT_W, 300), rng.integers(0, OUT_H, 300)
     # the cell (i, j) = clamp(floor(x), 0, W - 2) of x = (X + 0.5) / 2 - 0.5 and its corners
     cx = np.clip(np.floor((hx + 0.5) / 2 - 0.5).astype(np.int64), 0, LOW_W - 2)
@@ -254,7 +253,7 @@ def test_full_backward_sampled(gs, ora, scene, low):
     keep = ~np.any(bad_lo[ny, nx], axis=1)
     assert keep.mean() > 0.7
     dout = np.zeros((3, OUT_H, OUT_W), np.float32)
-    dout[:, hy[keep], hx[keep]] = rng.normal(size=(3, int(keep.sum()))).astype(np.float32)
+    dout[:, hy[keep], hx[keep]] = upstream(hx[keep], hy[keep], rng)
 
     dC, dG = ora.upscale_adjoint(dout.astype(np.float64), LOW_W, LOW_H)
     live = np.any(dC != 0, axis=0) | np.any(dG.reshape(9, LOW_H, LOW_W) != 0, axis=0)
@@ -266,25 +265,86 @@ def test_full_backward_sampled(gs, ora, scene, low):
     hit = np.nonzero(np.any(g2d != 0, axis=1))[0]
     assert len(hit) > 100
     sub = {k: (v[hit] if isinstance(v, np.ndarray) else v) for k, v in scene.items()}
-    want = ora.project_adjoint(sub, low["cam"], LOW_W, LOW_H, g2d[hit])
+    want = ora.project_adjoint(sub, cam, LOW_W, LOW_H, g2d[hit])
 
     got = ctx.backward(torch.as_tensor(dout).cuda(), 2)
     torch.cuda.synchronize()
     ctx.synchronize()
-    got = {k: v.cpu().numpy().reshape(N, -1) for k, v in got.items()}
+    got = {k: v.cpu().numpy().reshape(n, -1) for k, v in got.items()}
     # a colour clamped at max(0, .) has a one-sided derivative FP32 may take the other way
     fine = ~np.any(np.abs(proj["rgb"][hit]) < 1e-5, axis=1)
-    rest = np.ones(N, bool)
+    rest = np.ones(n, bool)
     rest[hit] = False
     for key, w in want.items():
         w = w.reshape(len(hit), -1)
         g = got[key][hit]
+        # the derivative tolerance: 1e-3 max(|ref|, rms of the parameter's column)
         rms = np.sqrt(np.mean(w ** 2, axis=0, keepdims=True)) + 1e-30
-        tol = 5e-4 * np.abs(w) + 5e-4 * rms
-        bad = (np.abs(g - w) > tol) & fine[:, None]
-        assert not bad.any(), (key, int(bad.sum()), float(np.max(np.abs(g - w) / tol)))
+        tol = 1e-3 * np.maximum(np.abs(w), rms)
+        r = np.where(fine[:, None], np.abs(g - w) / tol, 0.0)
+        worst = np.unravel_index(np.argmax(r), r.shape)
+        assert r.max() <= 1.0, (key, int((r > 1).sum()), float(r.max()), float(w[worst]), float(g[worst]),
+                                float(rms[0, worst[1]]))
         # Gaussians no live pixel blends receive nothing
         assert np.all(np.abs(got[key][rest]) <= 5e-4 * rms), key
+
+
+def test_full_backward_sampled(ora, scene, low):
+    """The reverse mode of the 2x step for a seeded normal upstream gradient on
+    300 output pixels (the benchmark's scene)."""
+    _check_backward_sampled(ora, scene, N, low["cam"], low["proj"], low["bins"], low["ctx"],
+                            lambda hx, hy, rng: rng.normal(size=(3, len(hx))).astype(np.float32), seed=5)
+
+
+def test_differentiation_workload_1m_sampled(gs, ora):
+    """The differentiation workload: the mixture scene's generator with 1M
+    Gaussians, 960x540 render with derivatives -> 2x upscale -> the loss
+    L = 0.8 mean|out - t| + 0.2 mean((out - t)^2) against a seeded target t
+    (offset so that no residual sits at the L1 kink), taken over 300 seeded
+    output pixels; its upstream gradient (0.8 sign(r) + 0.4 r) / m goes
+    through gs_backward in the benchmark's launch configuration and is checked
+    against the oracle's adjoint chain as above."""
+    import torch
+    n = 1_000_000
+    scene1 = scenes.mixture_scene(n, seed=0)
+    cam = scenes.pinhole_camera(LOW_W, LOW_H)
+    proj = ora.project(scene1, cam, LOW_W, LOW_H)
+    bins = ora.bin_pairs(proj)
+    dev1 = gs.DeviceScene(scene1)
+    C = torch.empty(3, LOW_H, LOW_W, device="cuda")
+    G = torch.empty(3, 3, LOW_H, LOW_W, device="cuda")
+    out = torch.empty(3, OUT_H, OUT_W, device="cuda")
+
+    def body(gc):
+        gc.project(dev1, cam, LOW_W, LOW_H)
+        gc.render_binned(grads=True, out_C=C, out_grads=G)
+        gc.upscale(C, G, 2, out=out)
+
+    stream = torch.cuda.Stream()
+    ctx = gs.Context(stream=stream, no_host_wait=True)
+    ctx.reserve(n, LOW_W, LOW_H, bins["P"] + bins["P"] // 10 + 4096)
+    try:
+        with torch.cuda.stream(stream):
+            body(ctx)
+            torch.cuda.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=stream):
+                body(ctx)
+            graph.replay()
+        torch.cuda.synchronize()
+        ctx.synchronize()
+        o = out.cpu().numpy()
+        target = o + 0.05 + 0.1 * np.abs(np.random.default_rng(11).standard_normal(o.shape)).astype(np.float32)
+
+        def upstream(hx, hy, rng):
+            r = (o[:, hy, hx] - target[:, hy, hx]).astype(np.float64)
+            assert np.all(np.abs(r) > 1e-2)
+            m = r.size
+            return ((0.8 * np.sign(r) + 0.4 * r) / m).astype(np.float32)
+
+        _check_backward_sampled(ora, scene1, n, cam, proj, bins, ctx, upstream, seed=13)
+    finally:
+        ctx.close()
 
 
 # ---------------------------------------------------------------- 480x270 -> 4x
