@@ -64,7 +64,7 @@ __device__ __forceinline__ bool blend_pair(PixelState& p, float g2, float dx, fl
                                            const float4& r1, const float4& c, int idx)
 {
     if (MODE == GS_MODE_3DGS && g2 < r1.w) return false;   // sigma e^g < 1/255 for sure
-    float alpha = c.w * exp2f(g2);
+    float alpha = c.w * pow2(g2);
     bool clamped = false;
     if (MODE == GS_MODE_3DGS) {
         if (alpha < (1.f / 255.f)) return false;

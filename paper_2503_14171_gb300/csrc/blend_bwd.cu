@@ -75,7 +75,7 @@ __device__ __forceinline__ bool bwd_entry(BwdPixel& p, const float4& r0, const f
     const float dx = p.px - r0.x, dy = p.py - r0.y;
     const float g2 = exponent2(r1, dx, dy);
     if (MODE == GS_MODE_3DGS && g2 < r1.w) return false;
-    float alpha = c.w * exp2f(g2);
+    float alpha = c.w * pow2(g2);
     bool clamped = false;
     if (MODE == GS_MODE_3DGS) {
         if (alpha < (1.f / 255.f)) return false;

@@ -30,6 +30,18 @@ __device__ __forceinline__ bool pair_hit(const uint32_t* __restrict__ pair_words
     return id < n && ((w.y >> (16 + bit)) & 1u);
 }
 
+// 2^x by the hardware's base-2 exponential (PTX ex2.approx.ftz.f32: about
+// 2^-22 relative error; results below 2^-126 flush to zero -- in 3DGS mode no
+// blended pair comes near that (alpha >= 1/255), in exact mode such a pair
+// adds less than 1e-38).  The blend and its adjoint both take it, so the
+// adjoint re-takes the forward's decisions on the same values.
+__device__ __forceinline__ float pow2(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Exponent of a (pixel, Gaussian) pair in base 2: r1 = (A2, B2, C2, threshold)
 // with g2 = A2 dx^2 + B2 dx dy + C2 dy^2 = g log2(e).
 __device__ __forceinline__ float exponent2(const float4& r1, float dx, float dy)
