@@ -498,7 +498,8 @@ gs_status gs_destroy(gs_ctx* c)
                       &c->sort_counter, &c->sranges, &c->tile_count, &c->tile_start, &c->state, &c->count,
                       &c->errword, &c->grad2d, &c->pair_check, &c->tile_work, &c->tile_order,
                       &c->vrec0, &c->vrec1, &c->vrec2, &c->vrect, &c->vsupers, &c->vkey, &c->vtotals,
-                      &c->views_dev, &c->vpairs0, &c->vpairs1, &c->vsranges, &c->vwork, &c->vorder, &c->vqueue};
+                      &c->views_dev, &c->vpairs0, &c->vpairs1, &c->vsranges, &c->vwork, &c->vorder, &c->vqueue,
+                      &c->vsortv};
     for (DevBuf* b : bufs) release(*b);
     if (c->h_scalar) cudaFreeHost(c->h_scalar);
     if (c->totals_ready) cudaEventDestroy(c->totals_ready);
@@ -862,13 +863,27 @@ gs_status reserve_impl(gs_ctx* c, int64_t n, int32_t V, int32_t W, int32_t H, in
         return st;
     if (V > 0) {
         const size_t vn = un * (size_t)V;
+        if (vn >= 0xFFFFFFFFull)
+            return fail(c, GS_ERR_CAPACITY, "%d views of %lld Gaussians exceed 2^32 entries", V, (long long)n);
+        const int vbits = bits_for((uint32_t)V);
+        // the batched depth sort: (view, depth) keys in the two pair buffers
+        // (free until the views' pairs are emitted), values in vkey and vsortv
+        const size_t per_view = std::max<size_t>((size_t)super_pairs, un);
+        if ((st = ensure(c, c->vsortv, sizeof(uint32_t) * vn)) ||
+            (st = ensure(c, c->offsets, sizeof(uint32_t) * (vn + 1))) ||
+            (st = ensure(c, c->scan_partials, sizeof(unsigned long long) * scan_partials_count((uint32_t)vn))) ||
+            (st = ensure(c, c->sort_status, sizeof(uint32_t) * std::max({radix_status_words((uint32_t)vn, 0, 32 + vbits),
+                                                                          radix_status_words(nn, 0, 32),
+                                                                          radix_status_words((uint32_t)super_pairs, 32,
+                                                                                             32 + sbits)}))))
+            return st;
         if ((st = ensure(c, c->vrec0, sizeof(float4) * vn)) || (st = ensure(c, c->vrec1, sizeof(float4) * vn)) ||
             (st = ensure(c, c->vrec2, sizeof(float4) * vn)) || (st = ensure(c, c->vrect, sizeof(ushort4) * vn)) ||
             (st = ensure(c, c->vsupers, sizeof(uint32_t) * vn)) || (st = ensure(c, c->vkey, sizeof(uint32_t) * vn)) ||
             (st = ensure(c, c->vtotals, sizeof(unsigned long long) * 2 * kTotalSlots * (size_t)V)) ||
             (st = ensure(c, c->views_dev, sizeof(ViewDesc) * kMaxViews)) ||
-            (st = ensure(c, c->vpairs0, sizeof(uint64_t) * (size_t)super_pairs * V)) ||
-            (st = ensure(c, c->vpairs1, sizeof(uint64_t) * (size_t)super_pairs * V)) ||
+            (st = ensure(c, c->vpairs0, sizeof(uint64_t) * per_view * V)) ||
+            (st = ensure(c, c->vpairs1, sizeof(uint64_t) * per_view * V)) ||
             (st = ensure(c, c->vsranges, sizeof(uint2) * (size_t)Ts * V)) ||
             (st = ensure(c, c->vwork, sizeof(uint32_t) * (size_t)T * V)) ||
             (st = ensure(c, c->vorder, sizeof(uint32_t) * (size_t)T * V)) ||
@@ -958,6 +973,30 @@ gs_status gs_render_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_
     const bool persistent = n > 1 && n <= ds_cap && n <= kDsMaxN;
     const size_t G = ds_cap / kDsMaxSlice;
     const uint32_t cap = (uint32_t)c->res_pairs;
+    // Several views (or views beyond the persistent sort's capacity): the depth
+    // keys of every view sorted together, the view as the top digit, so that
+    // each view's Gaussians come out contiguous and in their own depth order
+    // (the sort is stable and starts in id order), then one pair-offset scan
+    // over the whole order.  A single view within capacity keeps the
+    // persistent sort.
+    const bool batched = V > 1 || !persistent;
+    const uint32_t* vsorted = nullptr;   // v n + i in (view, depth, id) order
+    if (batched) {
+        const uint32_t total = (uint32_t)((uint64_t)V * n);
+        uint64_t* k64[2] = {as<uint64_t>(c->vpairs0), as<uint64_t>(c->vpairs1)};
+        uint32_t* v32[2] = {as<uint32_t>(c->vkey), as<uint32_t>(c->vsortv)};
+        GS_CUDA(c, launch_view_keys(s, as<uint32_t>(c->vkey), n, total, k64[0], v32[0]));
+        int vs = 0;
+        if (total > 1)
+            GS_CUDA(c, radix_sort_u64_pairs(s, k64, v32, total, 0, 32 + bits_for((uint32_t)V),
+                                            as<uint32_t>(c->sort_hist), as<uint32_t>(c->sort_status),
+                                            as<uint32_t>(c->sort_counter), as<int>(c->errword), &vs));
+        vsorted = v32[vs];
+        unsigned long long* scan_tot = as<unsigned long long>(c->scan_totals) + 2 * kTotalSlots;
+        GS_CUDA(c, launch_scan_gathered(s, as<uint32_t>(c->vsupers), nullptr, vsorted, total, as<uint32_t>(c->offsets),
+                                        as<unsigned long long>(c->scan_partials),
+                                        reinterpret_cast<uint32_t*>(scan_tot + 2), scan_tot, as<int>(c->errword)));
+    }
     const int64_t limit = c->opt.max_pairs > 0 ? std::min<int64_t>(c->opt.max_pairs, kMaxPairs) : kMaxPairs;
     PairCheckOut* chk = as<PairCheckOut>(c->pair_check);
     BlendViews bv;
@@ -981,8 +1020,11 @@ gs_status gs_render_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_
         uint32_t* keys[2] = {as<uint32_t>(c->dkey[0]), as<uint32_t>(c->dkey[1])};
         uint32_t* ids[2] = {as<uint32_t>(c->did[0]), as<uint32_t>(c->did[1])};
         GS_CUDA(c, cudaMemsetAsync(c->super_counts.p, 0, sizeof(uint32_t) * kCountCopies * Ts, s));
-        int sorted = 0;
-        if (persistent) {
+        if (batched) {   // this view's stretch of the batched order and offsets
+            GS_CUDA(c, launch_emit_pairs(s, vsorted + off, as<uint32_t>(c->offsets) + off, rect_v, n, stiles_x,
+                                         pairs[0], as<uint32_t>(c->super_counts), Ts, cap, (uint32_t)off, true));
+        } else {
+            int sorted = 0;
             unsigned char* base = as<unsigned char>(c->ds_scratch);
             GS_CUDA(c, launch_depth_sort_scan(s, c->device, keys_v, keys, ids, supers_v, n, as<uint32_t>(c->offsets),
                                               reinterpret_cast<uint32_t*>(base + ds_cnt_offset(G)),
@@ -990,23 +1032,9 @@ gs_status gs_render_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_
                                               reinterpret_cast<unsigned int*>(base + ds_bar_offset(G)),
                                               reinterpret_cast<uint32_t*>(base + ds_tot_offset(G)),
                                               as<int>(c->errword), &sorted, false));
-        } else {
-            unsigned long long* scan_tot = as<unsigned long long>(c->scan_totals) + 2 * kTotalSlots;
-            if (n > 1) {
-                GS_CUDA(c, cudaMemcpyAsync(keys[0], keys_v, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
-                GS_CUDA(c, launch_iota(s, ids[0], n));
-                GS_CUDA(c, radix_sort_u32_pairs(s, keys, ids, n, 0, 32, as<uint32_t>(c->sort_hist),
-                                                as<uint32_t>(c->sort_status), as<uint32_t>(c->sort_counter),
-                                                as<int>(c->errword), &sorted));
-            } else {
-                GS_CUDA(c, launch_iota(s, ids[0], n));
-            }
-            GS_CUDA(c, launch_scan_gathered(s, supers_v, nullptr, ids[sorted], n, as<uint32_t>(c->offsets),
-                                            as<unsigned long long>(c->scan_partials),
-                                            reinterpret_cast<uint32_t*>(scan_tot + 2), scan_tot, as<int>(c->errword)));
+            GS_CUDA(c, launch_emit_pairs(s, ids[sorted], as<uint32_t>(c->offsets), rect_v, n, stiles_x, pairs[0],
+                                         as<uint32_t>(c->super_counts), Ts, cap));
         }
-        GS_CUDA(c, launch_emit_pairs(s, ids[sorted], as<uint32_t>(c->offsets), rect_v, n, stiles_x, pairs[0],
-                                     as<uint32_t>(c->super_counts), Ts, cap));
         GS_CUDA(c, launch_supers_to_hist(s, as<uint32_t>(c->super_counts), Ts, spasses, as<uint32_t>(c->sort_hist),
                                          sranges_v,
                                          PairCheckIn{vtot + (size_t)v * 2 * kTotalSlots, cap,

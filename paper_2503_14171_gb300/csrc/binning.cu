@@ -23,7 +23,7 @@ template <bool COUNT>
 __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ ids, const uint32_t* __restrict__ offsets,
                                               const ushort4* __restrict__ rect, uint32_t n, int stiles_x,
                                               uint64_t* __restrict__ pairs, uint32_t* __restrict__ counts,
-                                              uint32_t Ts, uint32_t cap)
+                                              uint32_t Ts, uint32_t cap, uint32_t id_base, bool rebase)
 {
     __shared__ uint32_t s_cnt[COUNT ? kMaxSupersForCounts : 1];
     if (COUNT) {
@@ -32,9 +32,10 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ ids, 
     }
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < n) {
-        uint32_t off = offsets[k];
-        const uint32_t end = offsets[k + 1];
-        const uint32_t id = ids[k];
+        const uint32_t base = rebase ? offsets[0] : 0u;
+        uint32_t off = offsets[k] - base;
+        const uint32_t end = offsets[k + 1] - base;
+        const uint32_t id = ids[k] - id_base;
         if (off < end && id < n) {   // id >= n only after an expired bounded wait in the sort
             const ushort4 r = rect[id];
             const int sx0 = r.x / kSuper, sx1 = r.z / kSuper, sy0 = r.y / kSuper, sy1 = r.w / kSuper;
@@ -223,13 +224,16 @@ cudaError_t launch_tile_order(cudaStream_t s, const uint32_t* work, uint32_t T, 
 }
 
 cudaError_t launch_emit_pairs(cudaStream_t s, const uint32_t* ids, const uint32_t* offsets, const ushort4* rect,
-                              uint32_t n, int stiles_x, uint64_t* pairs, uint32_t* counts, uint32_t Ts, uint32_t cap)
+                              uint32_t n, int stiles_x, uint64_t* pairs, uint32_t* counts, uint32_t Ts, uint32_t cap,
+                              uint32_t id_base, bool rebase)
 {
     if (n == 0) return cudaSuccess;
     if (counts && Ts <= (uint32_t)kMaxSupersForCounts)
-        k_emit<true><<<(n + 255) / 256, 256, 0, s>>>(ids, offsets, rect, n, stiles_x, pairs, counts, Ts, cap);
+        k_emit<true><<<(n + 255) / 256, 256, 0, s>>>(ids, offsets, rect, n, stiles_x, pairs, counts, Ts, cap, id_base,
+                                                     rebase);
     else
-        k_emit<false><<<(n + 255) / 256, 256, 0, s>>>(ids, offsets, rect, n, stiles_x, pairs, nullptr, 0, cap);
+        k_emit<false><<<(n + 255) / 256, 256, 0, s>>>(ids, offsets, rect, n, stiles_x, pairs, nullptr, 0, cap, id_base,
+                                                      rebase);
     note_launch();
     return cudaGetLastError();
 }

@@ -158,6 +158,7 @@ struct gs_ctx {
     gs::DevBuf vrec0, vrec1, vrec2;     // float4[V][n]
     gs::DevBuf vrect;                   // ushort4[V][n]
     gs::DevBuf vsupers, vkey;           // uint32[V][n]
+    gs::DevBuf vsortv;                  // uint32[V][n]: the batched depth sort's second value buffer
     gs::DevBuf vtotals;                 // uint64[V][2 kTotalSlots]
     gs::DevBuf views_dev;               // gs::ViewDesc[kMaxViews]
     gs::DevBuf vpairs0, vpairs1;        // uint64[V][res_pairs]: each view's pairs (sort ping-pong)
@@ -233,6 +234,14 @@ cudaError_t radix_sort_u32_pairs(cudaStream_t s, uint32_t* keys[2], uint32_t* va
 // (from launch_supers_to_hist), so the sort skips its histogram kernels.
 // n_dev (optional, needs hist_ready): the key count is min(n, *n_dev), read on
 // the device; n is then the capacity the launch is sized for.
+// (uint64 key, uint32 value) pairs, stable, over bits [bit_lo, bit_hi)
+cudaError_t radix_sort_u64_pairs(cudaStream_t s, uint64_t* keys[2], uint32_t* vals[2], uint32_t n, int bit_lo,
+                                 int bit_hi, uint32_t* hist, uint32_t* status, uint32_t* counters, int* err,
+                                 int* out_idx);
+// keys[g] = view << 32 | vkey[g] and vals[g] = g for g = v n + i < total (the
+// depth keys of a batch of views, sorted together with the view as the top digit)
+cudaError_t launch_view_keys(cudaStream_t s, const uint32_t* vkey, uint32_t n, uint32_t total, uint64_t* keys,
+                             uint32_t* vals);
 cudaError_t radix_sort_u64_keys(cudaStream_t s, uint64_t* keys[2], uint32_t n, int bit_lo, int bit_hi,
                                 uint32_t* hist, uint32_t* status, uint32_t* counters, int* err,
                                 int* out_idx, bool hist_ready, const uint32_t* n_dev = nullptr,
@@ -296,9 +305,12 @@ cudaError_t launch_depth_sort_scan(cudaStream_t s, int device, const uint32_t* k
 
 // pairs at offsets >= cap are counted but not written (the capacity check of
 // launch_supers_to_hist then rejects the frame)
+// id_base, rebase: the ids and offsets of one view within a batch sorted
+// together (ids[k] - id_base is the view's own id; its pairs start at slot
+// offsets[k] - offsets[0] of its pair buffer)
 cudaError_t launch_emit_pairs(cudaStream_t s, const uint32_t* ids, const uint32_t* offsets, const ushort4* rect,
                               uint32_t n, int stiles_x, uint64_t* pairs, uint32_t* counts, uint32_t Ts,
-                              uint32_t cap = 0xFFFFFFFFu);
+                              uint32_t cap = 0xFFFFFFFFu, uint32_t id_base = 0, bool rebase = false);
 cudaError_t launch_ranges(cudaStream_t s, const uint64_t* pairs, uint32_t P, uint32_t T, uint2* ranges);
 // per-tile lists from the super-tile lists: counts, starts, ranges and (optionally) keys/vals
 cudaError_t launch_tile_lists(cudaStream_t s, const uint64_t* spairs, const uint2* sranges, const ushort4* rect,

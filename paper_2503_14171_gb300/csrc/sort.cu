@@ -44,7 +44,7 @@ __device__ __forceinline__ uint32_t digit_of(K key, int shift)
 // Histogram of every pass's digit over all keys, in per-warp shared-memory
 // sub-histograms (a key shared by a whole warp, e.g. the exponent byte of a
 // depth, costs one 32-way serialised atomic instead of block-wide contention).
-constexpr int kHistPasses = 4;
+constexpr int kHistPasses = 5;   // up to 40 bits (the (view, depth) keys of a batch of views)
 template <typename K>
 __global__ void __launch_bounds__(kThreads) k_radix_hist(const K* __restrict__ keys, uint32_t n, int bit_lo,
                                                          int passes, uint32_t* __restrict__ hist)
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kThreads) k_radix_hist(const K* __restrict__ k
             if (p < passes) atomicAdd(&s_hist[warp][p][digit_of(key, bit_lo + p * kRadixBits)], 1u);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < passes * kRadix; i += kThreads) {
+    for (int i = threadIdx.x; i < min(passes, kHistPasses) * kRadix; i += kThreads) {
         uint32_t v = 0;
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) v += (&s_hist[w][0][0])[i];
@@ -263,6 +263,7 @@ cudaError_t radix_sort_impl(cudaStream_t s, K* keys[2], uint32_t* vals[2], uint3
         if ((e = cudaMemsetAsync(counters, 0, sizeof(uint32_t) * passes, s)) != cudaSuccess) return e;
     }
     if (!hist_ready) {
+        if (passes > kHistPasses) return cudaErrorInvalidValue;   // the histogram kernel holds kHistPasses passes
         if ((e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * passes * kRadix, s)) != cudaSuccess) return e;
         const uint32_t hb = (n + kThreads * 8 - 1) / (kThreads * 8);
         const int hist_blocks = (int)(hb < 152u * 8u ? hb : 152u * 8u);
@@ -422,6 +423,35 @@ cudaError_t radix_sort_u32_pairs(cudaStream_t s, uint32_t* keys[2], uint32_t* va
 {
     return radix_sort_impl<uint32_t, true>(s, keys, vals, n, bit_lo, bit_hi, hist, status, counters, err, out_idx,
                                            false, nullptr);
+}
+
+cudaError_t radix_sort_u64_pairs(cudaStream_t s, uint64_t* keys[2], uint32_t* vals[2], uint32_t n, int bit_lo,
+                                 int bit_hi, uint32_t* hist, uint32_t* status, uint32_t* counters, int* err,
+                                 int* out_idx)
+{
+    return radix_sort_impl<uint64_t, true>(s, keys, vals, n, bit_lo, bit_hi, hist, status, counters, err, out_idx,
+                                           false, nullptr);
+}
+
+namespace {
+// key g = (view << 32 | depth key of Gaussian i in view v), value g, for g = v n + i
+__global__ void __launch_bounds__(256) k_view_keys(const uint32_t* __restrict__ vkey, uint32_t n, uint32_t total,
+                                                   uint64_t* __restrict__ keys, uint32_t* __restrict__ vals)
+{
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    const uint32_t k = vkey[g];
+    keys[g] = ((uint64_t)(g / n) << 32) | k;
+    vals[g] = g;
+}
+}  // namespace
+
+cudaError_t launch_view_keys(cudaStream_t s, const uint32_t* vkey, uint32_t n, uint32_t total, uint64_t* keys,
+                             uint32_t* vals)
+{
+    if (total == 0 || n == 0) return cudaSuccess;
+    k_view_keys<<<(total + 255) / 256, 256, 0, s>>>(vkey, n, total, keys, vals); note_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t radix_sort_u64_keys(cudaStream_t s, uint64_t* keys[2], uint32_t n, int bit_lo, int bit_hi,
