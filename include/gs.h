@@ -166,8 +166,9 @@ gs_status gs_reserve_views(gs_ctx* ctx, int64_t n, int32_t V, int32_t W, int32_t
 /* Several views of one Gaussian set in one batch (e.g. the stereo pairs of a
  * VR headset, which the paper names as a use of cheap upscaling): one launch
  * projects every view (each Gaussian's inputs, SH coefficients included, are
- * read once for all views), then each view is depth-sorted and binned into
- * buffers of its own; one launch blends every tile of every view with
+ * read once for all views), one sort puts every view's Gaussians in depth
+ * order (the view as the top digit), each view is binned into buffers of its
+ * own; one launch blends every tile of every view with
  * derivatives into out_C[v] [3][H_v][W_v] and out_grads[v] [3][3][H_v][W_v]
  * (launch shape from gs_views_config / gs_autotune_views), and one launch
  * upscales, where out_up != NULL and out_up[v] != NULL, by factors[v] into
