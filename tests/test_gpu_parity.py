@@ -307,3 +307,32 @@ def test_blend_work_counts_match_oracle(gs, ora):
         n_eval, n_acc = ctx.blend_stats()
     assert abs(n_eval - ref["n_eval"]) <= 2e-3 * ref["n_eval"]
     assert abs(n_acc - ref["n_acc"]) <= 2e-3 * ref["n_acc"]
+
+
+@pytest.mark.parametrize("shift", [1, 2, 3])
+def test_projection_of_unaligned_sh(gs, shift):
+    """SH coefficients starting off a 16-byte boundary (a view into a larger
+    buffer) take the projection's scalar staging path; the projected records,
+    bins and image equal those of the aligned copy bit for bit."""
+    import torch
+    scene = scenes.random_scene(n=3000, seed=41, sh_degree=3, xy_range=1.2)
+    W, H = 80, 56
+    cam = scenes.pinhole_camera(W, H)
+    aligned = gs.DeviceScene(scene)
+    sh = np.ascontiguousarray(scene["sh"], np.float32).reshape(-1)
+    buf = torch.zeros(sh.size + 4, dtype=torch.float32, device="cuda")
+    buf[shift:shift + sh.size] = torch.as_tensor(sh).cuda()
+    tensors = dict(aligned.t)
+    tensors["sh"] = buf[shift:shift + sh.size].view(scene["sh"].shape)
+    assert tensors["sh"].data_ptr() % 16 != 0
+    shifted = gs.DeviceScene(scene, tensors=tensors)
+    res = []
+    for dev in (aligned, shifted):
+        with gs.Context() as ctx:
+            C, G = ctx.render_with_grads(dev, cam, W, H)
+            pr = {k: v.cpu().numpy() for k, v in ctx.read_projected().items()}
+            res.append((C.cpu().numpy(), G.cpu().numpy(), pr))
+    (C0, G0, p0), (C1, G1, p1) = res
+    assert np.array_equal(C0, C1) and np.array_equal(G0, G1)
+    for k in p0:
+        assert np.array_equal(p0[k], p1[k]), k

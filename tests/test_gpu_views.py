@@ -157,3 +157,25 @@ def test_views_beyond_persistent_sort(gs):
     _check(gs, scene, cams, szs, [2, 2], outs, (0.0, 0.0, 0.0))
     del outs
     torch.cuda.empty_cache()
+
+
+def test_views_at_the_view_limit(gs):
+    """32 views (the limit: five view bits above the 32 depth bits of the
+    batched sort's keys) of a small scene at small and ragged sizes, and a
+    single view (which keeps the persistent depth sort): each equals its
+    single-view render bit for bit."""
+    scene = gs.DeviceScene(scenes.random_scene(n=3000, seed=38, sh_degree=1, xy_range=1.1))
+    sizes = [(16 + 3 * k, 12 + 2 * k) for k in range(16)]
+    cams, szs = stereo_batch(sizes)
+    assert len(cams) == 32
+    factors = [1 + (v % 3) for v in range(32)]
+    with gs.Context(no_host_wait=True) as ctx:
+        ctx.reserve_views(scene.n, 32, max(w for w, _ in szs), max(h for _, h in szs), 200000)
+        outs = ctx.render_views(scene, cams, szs, factors)
+        ctx.synchronize()
+    _check(gs, scene, cams, szs, factors, outs, (0.0, 0.0, 0.0))
+    with gs.Context(no_host_wait=True) as ctx:
+        ctx.reserve_views(scene.n, 1, 64, 48, 200000)
+        one = ctx.render_views(scene, cams[:1], [(64, 48)], [2])
+        ctx.synchronize()
+    _check(gs, scene, cams[:1], [(64, 48)], [2], one, (0.0, 0.0, 0.0))
