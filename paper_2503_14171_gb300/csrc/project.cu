@@ -228,6 +228,33 @@ constexpr int kProjThreads = 128;
 // each) into s[gi][k].  From a 16-byte aligned source every lane first issues
 // all of its 16-byte loads, then scatters them into the padded rows; otherwise
 // (or for the last few floats) scalar coalesced loads.
+// The reverse: write s[gi][k] of a warp's cnt Gaussians to dst (contiguous,
+// KF floats each), 16-byte stores where dst is 16-byte aligned.
+template <int KF, int PITCH>
+__device__ __forceinline__ void unstage_sh(float* __restrict__ dst, const float (*s)[PITCH], int cnt, int lane)
+{
+    const int tot = cnt * KF;
+    int done = 0;
+    if ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
+        const int tot4 = tot >> 2;
+        float4* dst4 = reinterpret_cast<float4*>(dst);
+        for (int q = lane; q < tot4; q += 32) {
+            float e[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int f = 4 * q + c, gi = f / KF;
+                e[c] = s[gi][f - gi * KF];
+            }
+            dst4[q] = make_float4(e[0], e[1], e[2], e[3]);
+        }
+        done = 4 * tot4;
+    }
+    for (int f = done + lane; f < tot; f += 32) {
+        const int gi = f / KF;
+        dst[f] = s[gi][f - gi * KF];
+    }
+}
+
 template <int KF, int PITCH>
 __device__ __forceinline__ void stage_sh(float (*s)[PITCH], const float* __restrict__ src, int cnt, int lane)
 {
@@ -674,13 +701,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project_bwd(
             for (int k = 0; k < (DEG >= 0 ? KF : 1); ++k) s_sh[warp][lane][k] = gshv[k];
         }
         __syncwarp();
-        if (wcnt > 0) {
-            float* dst = g_sh + (size_t)wbase * KF;
-            for (int q = lane; q < wcnt * KF; q += 32) {
-                const int gi = q / KF;
-                dst[q] = s_sh[warp][gi][q - gi * KF];
-            }
-        }
+        if (wcnt > 0) unstage_sh<KF, PITCH>(g_sh + (size_t)wbase * KF, s_sh[warp], wcnt, lane);
     }
 }
 
