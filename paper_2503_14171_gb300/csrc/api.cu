@@ -93,6 +93,26 @@ T* as(DevBuf& b)
 }
 
 
+// The next blend's tile order, computed beside the projection's histogram
+// kernel when the recorded durations belong to this tile layout (else the
+// blend computes it, after resetting the history).
+struct OrderJob {
+    const uint32_t* work = nullptr;
+    uint32_t T = 0;
+    uint32_t* order = nullptr;
+};
+OrderJob order_job(gs_ctx* c, uint32_t T)
+{
+    OrderJob j;
+    if (T > 0 && c->work_tiles == (int64_t)T && c->tile_work.cap >= sizeof(uint32_t) * T &&
+        c->tile_order.cap >= sizeof(uint32_t) * T) {
+        j.work = as<uint32_t>(c->tile_work);
+        j.T = T;
+        j.order = as<uint32_t>(c->tile_order);
+    }
+    return j;
+}
+
 int bits_for(uint32_t v)   // number of bits to represent values < v (v >= 1)
 {
     int b = 0;
@@ -172,6 +192,7 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
     if (!(cam->fx > 0.f) || !(cam->fy > 0.f)) return fail(c, GS_ERR_INVALID_ARG, "fx, fy must be > 0");
     c->have_proj = false;
     c->have_state = false;
+    c->order_ready = false;
     const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
     const int stiles_x = (tiles_x + kSuper - 1) / kSuper, stiles_y = (tiles_y + kSuper - 1) / kSuper;
     const int64_t T = (int64_t)tiles_x * tiles_y;
@@ -289,10 +310,12 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
         PairCheckOut* chk = as<PairCheckOut>(c->pair_check);
         GS_CUDA(c, launch_emit_pairs(c->stream, ids, as<uint32_t>(c->offsets), as<ushort4>(c->rect), n, stiles_x,
                                      pairs[0], as<uint32_t>(c->super_counts), (uint32_t)Ts, cap));
+        const OrderJob job = order_job(c, (uint32_t)(tiles_x * tiles_y));
         GS_CUDA(c, launch_supers_to_hist(c->stream, as<uint32_t>(c->super_counts), (uint32_t)Ts, spasses,
                                          as<uint32_t>(c->sort_hist), as<uint2>(c->sranges),
                                          PairCheckIn{totals, cap, (unsigned long long)limit}, chk,
-                                         as<int>(c->errword)));
+                                         as<int>(c->errword), job.work, job.T, job.order));
+        c->order_ready = job.order != nullptr;
         int psorted = 0;
         if (Ts > 1 && cap > 1)
             GS_CUDA(c, radix_sort_u64_keys(c->stream, pairs, cap, 32, 32 + sbits, as<uint32_t>(c->sort_hist),
@@ -337,9 +360,12 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
     if (counted) {
         // digit histograms of the super-tile passes and the super-tile ranges,
         // both from the per-super-tile counts (checked against the buffers)
+        const OrderJob job = order_job(c, (uint32_t)(tiles_x * tiles_y));
         GS_CUDA(c, launch_supers_to_hist(c->stream, as<uint32_t>(c->super_counts), (uint32_t)Ts, spasses,
                                          as<uint32_t>(c->sort_hist), as<uint2>(c->sranges),
-                                         PairCheckIn{nullptr, Ps ? Ps : 1u, 0}, nullptr, as<int>(c->errword)));
+                                         PairCheckIn{nullptr, Ps ? Ps : 1u, 0}, nullptr, as<int>(c->errword),
+                                         job.work, job.T, job.order));
+        c->order_ready = job.order != nullptr;
         if (Ps > 1 && Ts > 1)
             GS_CUDA(c, radix_sort_u64_keys(c->stream, pairs, Ps, 32, 32 + sbits, as<uint32_t>(c->sort_hist),
                                            as<uint32_t>(c->sort_status), as<uint32_t>(c->sort_counter),
@@ -406,7 +432,9 @@ gs_status do_blend(gs_ctx* c, float* out_C, float* out_grads)
         GS_CUDA(c, cudaMemsetAsync(c->tile_work.p, 0, sizeof(uint32_t) * T, c->stream));
         c->work_tiles = T;
     }
-    GS_CUDA(c, launch_tile_order(c->stream, as<uint32_t>(c->tile_work), T, as<uint32_t>(c->tile_order)));
+    if (!c->order_ready)   // else the projection's histogram launch computed it
+        GS_CUDA(c, launch_tile_order(c->stream, as<uint32_t>(c->tile_work), T, as<uint32_t>(c->tile_order)));
+    c->order_ready = false;
     BlendArgs a = blend_args(c, out_C, out_grads);
     a.order = as<uint32_t>(c->tile_order);
     a.work = as<uint32_t>(c->tile_work);
@@ -524,6 +552,7 @@ gs_status gs_set_options(gs_ctx* c, const gs_options* opt)
     c->opt = *opt;
     c->have_proj = false;
     c->have_state = false;
+    c->order_ready = false;
     return GS_OK;
 }
 
@@ -953,6 +982,7 @@ gs_status gs_render_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_
     }
     c->have_proj = false;
     c->have_state = false;
+    c->order_ready = false;
     cudaStream_t s = c->stream;
     // all views projected in one launch
     unsigned long long* vtot = as<unsigned long long>(c->vtotals);

@@ -141,6 +141,7 @@ struct gs_ctx {
     gs::DevBuf tile_count, tile_start;  // uint32[tiles] (per-tile list materialisation)
     gs::DevBuf tile_work, tile_order;   // uint32[tiles]: last frame's block durations, this frame's order
     int64_t work_tiles = -1;            // tile count the recorded durations belong to
+    bool order_ready = false;           // the projection computed the next blend's tile order
     gs::DevBuf state;                   // float4[W*H]
     gs::DevBuf count;                   // int32[W*H]
     gs::DevBuf errword;                 // int32
@@ -230,11 +231,7 @@ cudaError_t launch_project(cudaStream_t s, const gs_gaussians& g, const CameraPa
 cudaError_t radix_sort_u32_pairs(cudaStream_t s, uint32_t* keys[2], uint32_t* vals[2], uint32_t n,
                                  int bit_lo, int bit_hi, uint32_t* hist, uint32_t* status,
                                  uint32_t* counters, int* err, int* out_idx);
-// hist_ready: hist already holds the exclusive digit histograms of every pass
-// (from launch_supers_to_hist), so the sort skips its histogram kernels.
-// n_dev (optional, needs hist_ready): the key count is min(n, *n_dev), read on
-// the device; n is then the capacity the launch is sized for.
-// (uint64 key, uint32 value) pairs, stable, over bits [bit_lo, bit_hi)
+// (uint64 key, uint32 value) pairs likewise (at most 40 bits)
 cudaError_t radix_sort_u64_pairs(cudaStream_t s, uint64_t* keys[2], uint32_t* vals[2], uint32_t n, int bit_lo,
                                  int bit_hi, uint32_t* hist, uint32_t* status, uint32_t* counters, int* err,
                                  int* out_idx);
@@ -242,6 +239,11 @@ cudaError_t radix_sort_u64_pairs(cudaStream_t s, uint64_t* keys[2], uint32_t* va
 // depth keys of a batch of views, sorted together with the view as the top digit)
 cudaError_t launch_view_keys(cudaStream_t s, const uint32_t* vkey, uint32_t n, uint32_t total, uint64_t* keys,
                              uint32_t* vals);
+// uint64 keys alone.  hist_ready: hist already holds the exclusive digit
+// histograms of every pass (from launch_supers_to_hist), so the sort skips its
+// histogram kernels.  n_dev (optional, needs hist_ready): the key count is
+// min(n, *n_dev), read on the device; n is then the capacity the launch is
+// sized for.
 cudaError_t radix_sort_u64_keys(cudaStream_t s, uint64_t* keys[2], uint32_t n, int bit_lo, int bit_hi,
                                 uint32_t* hist, uint32_t* status, uint32_t* counters, int* err,
                                 int* out_idx, bool hist_ready, const uint32_t* n_dev = nullptr,
@@ -261,9 +263,14 @@ struct PairCheckOut {
     unsigned long long needed, tile_pairs;
     uint32_t count;
 };
+// order_work / order_T / order (optional): in a second block of the same
+// launch, the next blend's tile order from the recorded durations (as
+// launch_tile_order).
 cudaError_t launch_supers_to_hist(cudaStream_t s, uint32_t* counts, uint32_t Ts, int passes, uint32_t* hist,
                                   uint2* ranges, PairCheckIn in = PairCheckIn{nullptr, 0, 0},
-                                  PairCheckOut* out = nullptr, int* err = nullptr);
+                                  PairCheckOut* out = nullptr, int* err = nullptr,
+                                  const uint32_t* order_work = nullptr, uint32_t order_T = 0,
+                                  uint32_t* order = nullptr);
 size_t radix_status_words(uint32_t n, int bit_lo, int bit_hi);
 int radix_passes(int bit_lo, int bit_hi);
 

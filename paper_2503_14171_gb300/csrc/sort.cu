@@ -9,6 +9,7 @@
 // records kDevTimeout in the context's error word and proceeds (its output is
 // then undefined, the GPU is never hung).
 #include "gs_internal.cuh"
+#include "tile_order.cuh"
 
 namespace gs {
 namespace {
@@ -479,8 +480,14 @@ cudaError_t radix_sort_u64_keys(cudaStream_t s, uint64_t* keys[2], uint32_t n, i
 __global__ void __launch_bounds__(kThreads) k_supers_to_hist(uint32_t* __restrict__ counts, uint32_t Ts,
                                                              int passes, uint32_t* __restrict__ hist,
                                                              uint2* __restrict__ ranges, PairCheckIn in,
-                                                             PairCheckOut* out, int* __restrict__ err)
+                                                             PairCheckOut* out, int* __restrict__ err,
+                                                             const uint32_t* __restrict__ order_work,
+                                                             uint32_t order_T, uint32_t* __restrict__ order)
 {
+    if (blockIdx.x == 1) {   // beside it, independent of it: the next blend's tile order
+        tile_order_block(order_work, order_T, order);
+        return;
+    }
     __shared__ uint32_t s_hist[kHistPasses][kRadix];
     __shared__ uint32_t s_warp[kWarps];
     __shared__ unsigned long long s_sum[kWarps];
@@ -569,9 +576,12 @@ __global__ void __launch_bounds__(kThreads) k_supers_to_hist(uint32_t* __restric
 }
 
 cudaError_t launch_supers_to_hist(cudaStream_t s, uint32_t* counts, uint32_t Ts, int passes, uint32_t* hist,
-                                  uint2* ranges, PairCheckIn in, PairCheckOut* out, int* err)
+                                  uint2* ranges, PairCheckIn in, PairCheckOut* out, int* err,
+                                  const uint32_t* order_work, uint32_t order_T, uint32_t* order)
 {
-    k_supers_to_hist<<<1, kThreads, 0, s>>>(counts, Ts, passes, hist, ranges, in, out, err); note_launch();
+    const int blocks = order && order_work && order_T > 0 ? 2 : 1;
+    k_supers_to_hist<<<blocks, kThreads, 0, s>>>(counts, Ts, passes, hist, ranges, in, out, err, order_work, order_T,
+                                                 order); note_launch();
     return cudaGetLastError();
 }
 
