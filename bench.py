@@ -687,6 +687,22 @@ def run_gs(args):
     return 0
 
 
+def _blend_sources_hash():
+    """16 hex digits of sha256 over what defines the blend kernel: blend.cu,
+    blend_common.cuh and the BlendArgs struct of gs_internal.cuh."""
+    import hashlib
+    import re
+    csrc = os.path.join(ROOT, "paper_2503_14171_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in ("blend.cu", "blend_common.cuh"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    with open(os.path.join(csrc, "gs_internal.cuh")) as f:
+        m = re.search(r"struct BlendArgs \{.*?\n\};", f.read(), re.S)
+    h.update(m.group(0).encode() if m else b"")
+    return h.hexdigest()[:16]
+
+
 def _traffic_from_profiles():
     """DRAM bytes per blend launch from the committed ncu summary, or None when
     the blend's sources changed since that capture."""
@@ -700,11 +716,7 @@ def _traffic_from_profiles():
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 d[k.strip()] = v.strip()
-    h = hashlib.sha256()
-    for name in ("blend.cu", "blend_common.cuh", "gs_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2503_14171_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
-    if h.hexdigest()[:16] != d.get("sources_sha256_16"):
+    if _blend_sources_hash() != d.get("sources_sha256_16"):
         return None
     return int(d["dram_bytes_per_launch"])
 
