@@ -61,7 +61,8 @@ def _args():
     ap.add_argument("--mlp-pairs", type=int, default=2000,
                     help="training pairs (480x270 with derivatives, 1920x1080 direct) of the learned residual")
     ap.add_argument("--mlp-steps", type=int, default=3000, help="Adam steps of the learned residual")
-    ap.add_argument("--profile", default=None, choices=["main", "direct", "backward", "mlp"],
+    ap.add_argument("--profile", default=None,
+                    choices=["main", "direct", "backward", "mlp", "mlp_train", "views", "bicubic", "upscale_bwd"],
                     help="run only warm-up + steps of the 2x path (main) or of the direct 1920x1080 "
                          "render (direct) and print stage times; the case ncu captures use")
     return ap.parse_args()
@@ -902,7 +903,9 @@ def views_leg(torch, gs, scenes, stream, n_list=(300_000, 800_000, 2_000_000), r
                                  "autotune_ms": [round(t, 4) for t in tune_ms],
                                  "autotune_best": {"config": tune_best, "warp_map": tune_best % 2,
                                                    "schedule": ["tile order", "heaviest first",
-                                                                "persistent"][tune_best // 2]}}
+                                                                "persistent",
+                                                                "views in order, heaviest first within"
+                                                                ][tune_best // 2]}}
         del dev
         torch.cuda.empty_cache()
     return res
@@ -946,7 +949,65 @@ def run_profile(args):
     def mlp_step():
         ctx.upscale_mlp(C, G, LOW_W * 4, LOW_H * 4, params=mlp_params, out=mlp_out)
 
-    fn = {"main": main_step, "direct": direct_step, "backward": backward_step, "mlp": mlp_step}[args.profile]
+    # one Adam step of the learned residual (samples drawn once from the 2x
+    # render against the direct render: the same scene, 16,384 samples)
+    model = None
+    batch = None
+
+    def mlp_train_step():
+        model.step(batch, 1e-3)
+
+    # the batched views (16 stereo views of a 300k-Gaussian scene, half-size
+    # renders with derivatives, 2x upscales; one projection, blend and upscale
+    # launch)
+    views = {}
+
+    def views_step():
+        views["ctx"].render_views(views["dev"], views["cams"], views["lows"], [2] * len(views["cams"]),
+                                  outs=views["outs"])
+
+    # the bicubic comparator on the plain 960x540 render, and the upscale's adjoint
+    bic_out = None
+
+    def bicubic_step():
+        ctx.render(dev, cam, LOW_W, LOW_H, out_C=C)
+        ctx.upscale_bicubic(C, OUT_W, OUT_H, out=bic_out)
+
+    up_dout = None
+    up_grads = None
+
+    def upscale_bwd_step():
+        ctx.upscale_backward(up_dout, LOW_W, LOW_H, FACTOR, out=up_grads)
+
+    fn = {"main": main_step, "direct": direct_step, "backward": backward_step, "mlp": mlp_step,
+          "mlp_train": mlp_train_step, "views": views_step, "bicubic": bicubic_step,
+          "upscale_bwd": upscale_bwd_step}[args.profile]
+    if args.profile == "mlp_train":
+        from paper_2503_14171_gb300 import residual
+        with torch.cuda.stream(stream):
+            main_step()
+            direct = torch.empty(3, OUT_H, OUT_W, device="cuda")
+            ctx.render(dev, cam_hi, OUT_W, OUT_H, out_C=direct)
+            main_step()
+            batch = residual.draw_samples(ctx, C, G, direct, MLP_BATCH, torch.Generator("cuda").manual_seed(0))
+            model = residual.ResidualMLP(ctx, seed=0)
+            torch.cuda.synchronize()
+    if args.profile == "views":
+        camdefs, eyes = scenes.stereo_views()
+        lows = [(w // 2, h // 2) for w, h in eyes]
+        vcams = [scenes.pinhole_camera(w, h, viewmat=scenes.look_at_viewmat(e, t))
+                 for (w, h), (e, t) in zip(lows, camdefs)]
+        vdev = gs.DeviceScene(scenes.mixture_scene(300_000, seed=1))
+        vctx = gs.Context(stream=stream, no_host_wait=True)
+        vctx.reserve_views(300_000, len(vcams), max(w for w, _ in lows), max(h for _, h in lows), 2_000_000)
+        views.update(ctx=vctx, dev=vdev, cams=vcams, lows=lows,
+                     outs=[[torch.empty(3, h, w, device="cuda"), torch.empty(3, 3, h, w, device="cuda"),
+                            torch.empty(3, 2 * h, 2 * w, device="cuda")] for w, h in lows])
+    if args.profile == "bicubic":
+        bic_out = torch.empty(3, OUT_H, OUT_W, device="cuda")
+    if args.profile == "upscale_bwd":
+        up_dout = torch.randn(3, OUT_H, OUT_W, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+        up_grads = (torch.empty(3, LOW_H, LOW_W, device="cuda"), torch.empty(3, 3, LOW_H, LOW_W, device="cuda"))
     if args.profile == "mlp":
         from paper_2503_14171_gb300 import residual
         with torch.cuda.stream(stream):
@@ -972,8 +1033,14 @@ def run_profile(args):
             fn()
         b.record(stream)
         torch.cuda.synchronize()
+    try:
+        pairs = ctx.pair_count()
+    except gs.GSError:   # no projection in this profile
+        pairs = None
     print(json.dumps({"profile": args.profile, "ms_per_step": a.elapsed_time(b) / args.steps,
-                      "pairs": ctx.pair_count(), "launches": ctx.launch_count()}), flush=True)
+                      "pairs": pairs, "launches": ctx.launch_count()}), flush=True)
+    if views:
+        views["ctx"].close()
     ctx.close()
     return 0
 

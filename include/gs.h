@@ -189,8 +189,10 @@ gs_status gs_render_views(gs_ctx* ctx, const gs_gaussians* g, int32_t V, const g
  * warp of a 16 x 16 tile, 0 = an 8 x 4 block, 1 = a 16 x 2 strip.  schedule:
  * 0 = one block per tile in tile order, 1 = one block per tile, the heaviest
  * tiles of the previous batch first, 2 = resident blocks taking tiles from a
- * counter.  Default (0, 1). */
-#define GS_VIEWS_CONFIGS 6   /* configuration k: warp_map = k % 2, schedule = k / 2 */
+ * counter, 3 = one block per tile, the views in order and each view's heaviest
+ * tiles of the previous batch first (each view's Gaussian records stay in L2
+ * while its tiles run).  Default (0, 1). */
+#define GS_VIEWS_CONFIGS 8   /* configuration k: warp_map = k % 2, schedule = k / 2 */
 gs_status gs_views_config(gs_ctx* ctx, int32_t warp_map, int32_t schedule);
 
 /* Autotuner: renders the batch of gs_render_views (same arguments) once

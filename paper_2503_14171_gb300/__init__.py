@@ -32,7 +32,7 @@ GS_MODE_3DGS = 0
 GS_MODE_EXACT = 1
 MODES = {"3dgs": GS_MODE_3DGS, "exact": GS_MODE_EXACT}
 GS_FLAG_NO_HOST_WAIT = 1
-GS_VIEWS_CONFIGS = 6
+GS_VIEWS_CONFIGS = 8
 GS_MLP_IN = 50
 GS_MLP_HIDDEN = 64
 GS_MLP_PARAMS = 7619

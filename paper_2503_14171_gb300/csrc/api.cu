@@ -1114,6 +1114,9 @@ gs_status gs_render_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_
     if (c->views_sched == 1) {   // heaviest tiles of the last batch first
         GS_CUDA(c, launch_tile_order(s, as<uint32_t>(c->vwork), (uint32_t)total, as<uint32_t>(c->vorder)));
         bv.order = as<uint32_t>(c->vorder);
+    } else if (c->views_sched == 3) {   // the views in order, each view's heaviest tiles first
+        GS_CUDA(c, launch_tile_order_views(s, as<uint32_t>(c->vwork), bv.start, V, as<uint32_t>(c->vorder)));
+        bv.order = as<uint32_t>(c->vorder);
     }
     GS_CUDA(c, launch_blend_views(s, c->opt.mode, bv, c->views_map, c->views_sched == 2));
     if (uv.V > 0) GS_CUDA(c, launch_upscale_views(s, uv));
@@ -1124,8 +1127,8 @@ gs_status gs_render_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_
 gs_status gs_views_config(gs_ctx* c, int32_t warp_map, int32_t schedule)
 {
     if (!c) return GS_ERR_INVALID_ARG;
-    if (warp_map < 0 || warp_map > 1 || schedule < 0 || schedule > 2)
-        return fail(c, GS_ERR_INVALID_ARG, "warp_map in {0, 1}, schedule in {0, 1, 2}");
+    if (warp_map < 0 || warp_map > 1 || schedule < 0 || schedule > 3)
+        return fail(c, GS_ERR_INVALID_ARG, "warp_map in {0, 1}, schedule in {0, 1, 2, 3}");
     c->views_map = warp_map;
     c->views_sched = schedule;
     return GS_OK;
@@ -1149,7 +1152,7 @@ gs_status gs_autotune_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const g
     for (int k = 0; k < GS_VIEWS_CONFIGS && st == GS_OK; ++k) {
         c->views_map = k & 1;
         c->views_sched = k >> 1;
-        // one untimed batch: first use of the variant, and tile durations for schedule 1
+        // one untimed batch: first use of the variant, and tile durations for schedules 1 and 3
         st = gs_render_views(c, g, V, cams, Ws, Hs, out_C, out_grads, factors, out_up);
         if (st != GS_OK) break;
         if (cudaEventRecord(e0, c->stream) != cudaSuccess) { st = fail(c, GS_ERR_CUDA, "event"); break; }

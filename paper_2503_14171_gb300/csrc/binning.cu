@@ -158,6 +158,21 @@ __global__ void __launch_bounds__(1024) k_tile_starts(const uint32_t* __restrict
     }
 }
 
+// One block per view of a batch: view v's tiles (start[v] .. start[v + 1] - 1
+// of the batch) heaviest first, in its own stretch of the order, so that the
+// blend takes the views one after another.
+struct ViewStarts {
+    int start[kMaxViews + 1];
+};
+__global__ void __launch_bounds__(1024) k_tile_order_views(const uint32_t* __restrict__ work,
+                                                            const __grid_constant__ ViewStarts vs,
+                                                            uint32_t* __restrict__ order)
+{
+    const int v = blockIdx.x;
+    const uint32_t b = (uint32_t)vs.start[v], T = (uint32_t)(vs.start[v + 1] - vs.start[v]);
+    tile_order_block(work + b, T, order + b, b);
+}
+
 // One block: the tiles heaviest first (tile_order.cuh).
 __global__ void __launch_bounds__(1024) k_tile_order(const uint32_t* __restrict__ work, uint32_t T,
                                                       uint32_t* __restrict__ order)
@@ -177,6 +192,15 @@ cudaError_t launch_iota(cudaStream_t s, uint32_t* ids, uint32_t n)
 {
     if (n == 0) return cudaSuccess;
     k_iota<<<(n + 255) / 256, 256, 0, s>>>(ids, n); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_order_views(cudaStream_t s, const uint32_t* work, const int* start, int V, uint32_t* order)
+{
+    if (V < 1 || V > kMaxViews) return cudaErrorInvalidValue;
+    ViewStarts vs{};
+    for (int v = 0; v <= V; ++v) vs.start[v] = start[v];
+    k_tile_order_views<<<V, 1024, 0, s>>>(work, vs, order); note_launch();
     return cudaGetLastError();
 }
 

@@ -73,6 +73,9 @@ struct BlendArgs {
 
 // Order tiles by the recorded work of the previous frame, heaviest first
 // (coarse: 4 buckets per octave of the recorded duration).
+// The tiles of a batch of views (view v: start[v] .. start[v + 1] - 1), each
+// view's heaviest first, the views in order.
+cudaError_t launch_tile_order_views(cudaStream_t s, const uint32_t* work, const int* start, int V, uint32_t* order);
 cudaError_t launch_tile_order(cudaStream_t s, const uint32_t* work, uint32_t T, uint32_t* order);
 
 // Adjoint of the blend: the forward's binning (super-tile lists filtered per

@@ -10,8 +10,9 @@ namespace gs {
 constexpr int kOrderBuckets = 128;
 static_assert(kOrderBuckets % 32 == 0, "buckets are scanned by one warp, a whole number per lane");
 
+// order[0 .. T) receives base + the tile indices 0 .. T - 1, heaviest first
 __device__ __forceinline__ void tile_order_block(const uint32_t* __restrict__ work, uint32_t T,
-                                                 uint32_t* __restrict__ order)
+                                                 uint32_t* __restrict__ order, uint32_t base = 0)
 {
     __shared__ uint32_t s_cnt[kOrderBuckets];
     for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) s_cnt[b] = 0;
@@ -45,7 +46,7 @@ __device__ __forceinline__ void tile_order_block(const uint32_t* __restrict__ wo
         }
     }
     __syncthreads();
-    for (uint32_t t = threadIdx.x; t < T; t += blockDim.x) order[atomicAdd(&s_cnt[bucket(work[t])], 1u)] = t;
+    for (uint32_t t = threadIdx.x; t < T; t += blockDim.x) order[atomicAdd(&s_cnt[bucket(work[t])], 1u)] = base + t;
 }
 
 }  // namespace gs

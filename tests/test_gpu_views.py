@@ -59,7 +59,7 @@ def test_views_equal_single_view(gs, sh):
     _check(gs, scene, cams, szs, factors, outs, bg)
 
 
-@pytest.mark.parametrize("config", range(6))
+@pytest.mark.parametrize("config", range(8))
 def test_views_every_launch_shape(gs, config):
     """Each launch shape of the batched blend (warp map x schedule) gives the
     single-view images bit for bit; twice, so that the heaviest-first schedule
@@ -90,11 +90,13 @@ def test_views_autotune(gs):
         ctx.synchronize()
         with pytest.raises(gs.GSError) as e:
             ctx.views_config(2, 0)
+        with pytest.raises(gs.GSError):
+            ctx.views_config(0, 4)
         assert e.value.status == gs.GS_ERR_INVALID_ARG
     _check(gs, scene, cams, szs, factors, outs, (0.0, 0.0, 0.0))
 
 
-@pytest.mark.parametrize("schedule", [1, 2])
+@pytest.mark.parametrize("schedule", [1, 2, 3])
 def test_views_graph_replay(gs, schedule):
     import torch
     scene = gs.DeviceScene(scenes.random_scene(n=6000, seed=32, sh_degree=1))
