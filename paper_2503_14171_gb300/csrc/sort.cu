@@ -20,7 +20,7 @@ constexpr int kThreads = 256;              // one thread per digit in the digit 
 constexpr int kWarps = kThreads / 32;
 constexpr int kItems = 8;                  // keys per thread
 constexpr int kTileKeys = kThreads * kItems;
-constexpr int kMaxPasses = 8;
+constexpr int kMaxPasses = 8;              // the callers' histogram ([8][256]) and counter ([8]) buffers
 constexpr uint32_t kFlagAgg = 1u << 30;    // status word: 2-bit flag | 30-bit count
 constexpr uint32_t kFlagInc = 2u << 30;
 constexpr uint32_t kValueMask = (1u << 30) - 1;
@@ -256,6 +256,7 @@ cudaError_t radix_sort_impl(cudaStream_t s, K* keys[2], uint32_t* vals[2], uint3
     *out_idx = 0;
     if (n <= 1 || bit_hi <= bit_lo) return cudaSuccess;
     const int passes = (bit_hi - bit_lo + kRadixBits - 1) / kRadixBits;
+    if (passes > kMaxPasses) return cudaErrorInvalidValue;
     const uint32_t tiles = (n + kTileKeys - 1) / kTileKeys;
     cudaError_t e;
     if (!pre_zeroed) {
