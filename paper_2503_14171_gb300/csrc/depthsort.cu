@@ -77,30 +77,35 @@ struct DsArgs {
     uint32_t n;
 };
 
-// Grid-wide barrier for a cooperative launch (all blocks resident).
+// Grid-wide barrier for a cooperative launch (all blocks resident).  Thread 0
+// of each block arrives with an acquire-release add at GPU scope (it releases
+// the block's writes, ordered before it by the CTA barrier, and acquires those
+// of the blocks that arrived earlier); the last to arrive resets the count and
+// publishes the next generation with a release add; the others poll the
+// generation with acquire loads.
 __device__ __forceinline__ void grid_barrier(unsigned int* bar, int* err)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned int* vgen = bar + 1;
-        const unsigned int gen = *vgen;
-        __threadfence();
-        const unsigned int arrived = atomicAdd(bar, 1u);
+        unsigned int gen, arrived;
+        asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(gen) : "l"(bar + 1) : "memory");
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(bar) : "memory");
         if (arrived == gridDim.x - 1) {
-            bar[0] = 0u;
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
+            asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(bar) : "memory");
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar + 1) : "memory");
         } else {
             long spins = 0;
-            while (*vgen == gen) {
+            unsigned int g;
+            do {
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(bar + 1) : "memory");
+                if (g != gen) break;
                 if (++spins > kGridSpinLimit) {
                     atomicExch(err, kDevTimeout);
                     break;
                 }
-                __nanosleep(64);
-            }
+                __nanosleep(32);
+            } while (true);
         }
-        __threadfence();
     }
     __syncthreads();
 }
