@@ -247,6 +247,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_mlp_upscale(const float* __rest
     const size_t plane = (size_t)W * H, plane2 = (size_t)W2 * H2;
     uint32_t phase = 0;
     bool ok = true;
+    bool late = false;   // this thread's wait for an MMA ran out (the block leaves at its next barrier)
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int tyi = (int)(tile / tiles_x);
         const int X0 = (int)(tile - (long long)tyi * tiles_x) * kTileW, Y0 = tyi * kTileH;
@@ -265,7 +266,10 @@ __global__ void __launch_bounds__(kThreads, 6) k_mlp_upscale(const float* __rest
             s.cy[r] = cj;
             s.ty[r] = u;
         }
-        __syncthreads();
+        if (__syncthreads_or(late)) {
+            ok = false;
+            break;
+        }
         const int i0 = s.cx[0], j0 = s.cy[0];
         const int fw = s.cx[kTileW - 1] + 2 - i0, fh = s.cy[kTileH - 1] + 2 - j0;   // <= fpw x fph
         for (int e = tid; e < fw * fh; e += kThreads) {
@@ -331,9 +335,8 @@ __global__ void __launch_bounds__(kThreads, 6) k_mlp_upscale(const float* __rest
             mma_k64(tmem, sa, w1, idesc);
             mma_commit(&s.bar);
         }
-        ok = __syncthreads_and(mbar_wait(&s.bar, phase, kWaitLimit));
+        late |= !mbar_wait(&s.bar, phase, kWaitLimit);   // each thread reads only its own accumulator lane
         phase ^= 1u;
-        if (!ok) break;
         fence_after_sync();
         // layer 1 epilogue: h1 = relu(z1 + b1) as the BF16 row of A (the MMA
         // that read the features is complete)
@@ -354,15 +357,17 @@ __global__ void __launch_bounds__(kThreads, 6) k_mlp_upscale(const float* __rest
         }
         fence_async_smem();
         fence_before_sync();
-        __syncthreads();
+        if (__syncthreads_or(late)) {
+            ok = false;
+            break;
+        }
         if (tid == 0) {
             fence_after_sync();
             mma_k64(tmem, sa, w2, idesc);      // every thread has read D1
             mma_commit(&s.bar);
         }
-        ok = __syncthreads_and(mbar_wait(&s.bar, phase, kWaitLimit));
+        late |= !mbar_wait(&s.bar, phase, kWaitLimit);   // each thread reads only its own accumulator lane
         phase ^= 1u;
-        if (!ok) break;
         fence_after_sync();
         // layer 2 epilogue: h2 = relu(z2 + b2) as the BF16 row of A (the MMA
         // that read h1 is complete)
@@ -383,15 +388,17 @@ __global__ void __launch_bounds__(kThreads, 6) k_mlp_upscale(const float* __rest
         }
         fence_async_smem();
         fence_before_sync();
-        __syncthreads();
+        if (__syncthreads_or(late)) {
+            ok = false;
+            break;
+        }
         if (tid == 0) {
             fence_after_sync();
             mma_k64(tmem, sa, w3, idesc3);     // the output layer, N = 16 (3 used)
             mma_commit(&s.bar);
         }
-        ok = __syncthreads_and(mbar_wait(&s.bar, phase, kWaitLimit));
+        late |= !mbar_wait(&s.bar, phase, kWaitLimit);   // each thread reads only its own accumulator lane
         phase ^= 1u;
-        if (!ok) break;
         fence_after_sync();
         float r0, r1, r2;
         {
@@ -410,6 +417,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_mlp_upscale(const float* __rest
         }
         fence_before_sync();
     }
+    ok = !__syncthreads_or(late || !ok);   // a wait in the last tile may have run out
     if (!ok && tid == 0) atomicExch(err, kDevTimeout);
     __syncthreads();
     fence_after_sync();
