@@ -227,7 +227,7 @@ __device__ __forceinline__ void blend_tile(const BlendArgs& a, int tile, unsigne
 }
 
 template <bool GRADS, int MODE, bool STATS = false>
-__global__ void __launch_bounds__(kThreads, 4) k_blend(BlendArgs a, unsigned long long* __restrict__ stats = nullptr)
+__global__ void __launch_bounds__(kThreads, 5) k_blend(BlendArgs a, unsigned long long* __restrict__ stats = nullptr)
 {
     const int tile = a.order ? (int)a.order[blockIdx.x] : (int)blockIdx.x;
     blend_tile<GRADS, MODE, STATS, 0>(a, tile, stats, a.work ? a.work + tile : nullptr);
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend(BlendArgs a, unsigned lon
 // PERSIST: a grid of resident blocks takes jobs from a counter in turn;
 // otherwise one block per job.
 template <bool GRADS, int MODE, int MAP, bool PERSIST>
-__global__ void __launch_bounds__(kThreads, 4) k_blend_views(const __grid_constant__ BlendViews b)
+__global__ void __launch_bounds__(kThreads, 5) k_blend_views(const __grid_constant__ BlendViews b)
 {
     __shared__ int s_job;
     const int total = b.start[b.V];
