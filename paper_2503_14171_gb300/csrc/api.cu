@@ -94,8 +94,10 @@ T* as(DevBuf& b)
 
 
 // The next blend's tile order, computed beside the projection's histogram
-// kernel when the recorded durations belong to this tile layout (else the
-// blend computes it, after resetting the history).
+// kernel (a 256-thread block) when the recorded durations belong to this tile
+// layout and the tiles are few enough for that block (else the blend launches
+// its own 1024-thread ordering: 8160 tiles of a 1920 x 1080 frame took the
+// shared launch from 7.6 to 20.3 us).
 struct OrderJob {
     const uint32_t* work = nullptr;
     uint32_t T = 0;
@@ -104,7 +106,8 @@ struct OrderJob {
 OrderJob order_job(gs_ctx* c, uint32_t T)
 {
     OrderJob j;
-    if (T > 0 && c->work_tiles == (int64_t)T && c->tile_work.cap >= sizeof(uint32_t) * T &&
+    constexpr uint32_t kMaxSharedOrderTiles = 4096;
+    if (T > 0 && T <= kMaxSharedOrderTiles && c->work_tiles == (int64_t)T && c->tile_work.cap >= sizeof(uint32_t) * T &&
         c->tile_order.cap >= sizeof(uint32_t) * T) {
         j.work = as<uint32_t>(c->tile_work);
         j.T = T;

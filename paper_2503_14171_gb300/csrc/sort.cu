@@ -102,7 +102,7 @@ struct OnesweepSmem {
 };
 
 template <typename K, bool HAS_VAL>
-__global__ void __launch_bounds__(kThreads) k_onesweep(const K* __restrict__ keys_in, K* __restrict__ keys_out,
+__global__ void __launch_bounds__(kThreads, 4) k_onesweep(const K* __restrict__ keys_in, K* __restrict__ keys_out,
                                                        const uint32_t* __restrict__ vals_in,
                                                        uint32_t* __restrict__ vals_out, uint32_t n, int shift,
                                                        const uint32_t* __restrict__ digit_base,
