@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import scenes
-from helpers import (TOL_UP, borderline_tile_mask, compare_render, pairs_without)
+from helpers import (TOL_UP, borderline_tile_mask, compare_pixels, compare_render, gpu_rows, pairs_without)
 
 pytestmark = pytest.mark.gpu
 
@@ -336,3 +336,29 @@ def test_projection_of_unaligned_sh(gs, shift):
     assert np.array_equal(C0, C1) and np.array_equal(G0, G1)
     for k in p0:
         assert np.array_equal(p0[k], p1[k]), k
+
+
+def test_exact_mode_escaped_pair_counts(gs, ora):
+    """A frame of 2050 super-tiles in exact mode: every Gaussian touches every
+    super-tile, so its pair count (2050) exceeds the 11 bits that ride with
+    its id through the depth sort and is looked up.  The bins equal the
+    oracle's bit for bit, and sampled pixels match."""
+    W, H = 3200, 2624
+    scene = scenes.random_scene(40, seed=24, xy_range=0.6)
+    cam = scenes.pinhole_camera(W, H)
+    proj = ora.project(scene, cam, W, H, mode=ora.MODE_EXACT)
+    vis = proj["tiles_touched"] > 0
+    assert vis.sum() > 20
+    ref_bins = ora.bin_pairs(proj)
+    rng = np.random.default_rng(3)
+    pix = np.stack([rng.integers(0, W, 800), rng.integers(0, H, 800)], 1)
+    ref = ora.render(proj, ref_bins, pixels=pix, variants=True)
+    with gs.Context(mode="exact") as ctx:
+        dev = gs.DeviceScene(scene)
+        C, G = ctx.render_with_grads(dev, cam, W, H)
+        keys, vals, _ = (t.cpu().numpy() for t in ctx.read_bins())
+        rows = gpu_rows(C, G, pix)
+    assert np.array_equal(keys.view(np.uint64), ref_bins["keys"])
+    assert np.array_equal(vals.view(np.uint32), ref_bins["vals"])
+    fail, checked, excluded = compare_pixels(rows, ref)
+    assert fail == 0 and checked == len(pix), (fail, checked, excluded)
