@@ -362,3 +362,28 @@ def test_exact_mode_escaped_pair_counts(gs, ora):
     assert np.array_equal(vals.view(np.uint32), ref_bins["vals"])
     fail, checked, excluded = compare_pixels(rows, ref)
     assert fail == 0 and checked == len(pix), (fail, checked, excluded)
+
+
+def test_invalid_gaussians_are_culled(gs):
+    """Gaussians with a NaN mean, NaN log-scales, a NaN opacity logit or a zero
+    quaternion are culled: the render (with derivatives) equals, bit for bit,
+    the render of the scene without them, and the pair count is theirs less."""
+    scene = scenes.random_scene(n=2000, seed=26, sh_degree=2, xy_range=1.1)
+    bad = scenes.random_scene(n=2000, seed=26, sh_degree=2, xy_range=1.1)
+    bad["means"][0:10, 0] = np.nan
+    bad["log_scales"][10:20, 1] = np.nan
+    bad["opacity_logits"][20:30] = np.nan
+    bad["quats"][30:40] = 0.0
+    keep = np.ones(2000, bool)
+    keep[:40] = False
+    good = {k: (v[keep] if isinstance(v, np.ndarray) and v.shape[:1] == (2000,) else v) for k, v in scene.items()}
+    W, H = 96, 80
+    cam = scenes.pinhole_camera(W, H)
+    out = []
+    for sc in (bad, good):
+        with gs.Context() as ctx:
+            C, G = ctx.render_with_grads(gs.DeviceScene(sc), cam, W, H)
+            out.append((C.cpu().numpy(), G.cpu().numpy(), ctx.pair_count()))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2]
