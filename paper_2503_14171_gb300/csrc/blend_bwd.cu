@@ -159,8 +159,11 @@ __device__ __forceinline__ void warp_sum9_to_shared(float v[9], int lane, float*
     if (lane == 0) atomicAdd(&acc[8], t8);
 }
 
+// Four blocks per SM: the register cap of 64 costs the 3DGS instantiation 20 B
+// of spills, and the fourth block's warps hide more of the gather and
+// barrier latency than the spills add.
 template <int MODE>
-__global__ void __launch_bounds__(kThreads) k_blend_bwd(BlendBwdArgs a)
+__global__ void __launch_bounds__(kThreads, 4) k_blend_bwd(BlendBwdArgs a)
 {
     __shared__ float4 s_r0[kCand];
     __shared__ float4 s_r1[kCand];
