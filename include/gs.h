@@ -361,7 +361,10 @@ gs_status gs_backward(gs_ctx* ctx, const float* dL_dout, int32_t factor, const g
  * exits; no cudaMalloc, cudaFree or other allocating call is made.  Limits:
  * g->n <= 16384, W * H <= 65536 with W, H <= 4096, at most 262144
  * (64x64-pixel super-tile, Gaussian) pairs; beyond them GS_ERR_CAPACITY and
- * nothing is written.  opt may be NULL (3DGS mode, black background).
+ * nothing is written.  opt may be NULL (3DGS mode, black background);
+ * opt->flags must be 0 (GS_ERR_INVALID_ARG otherwise: the call always waits
+ * for its pair count), and opt->max_pairs limits the (tile, Gaussian) pairs
+ * as for gs_render_with_grads (GS_ERR_CAPACITY beyond it, nothing written).
  * stream: a cudaStream_t (NULL = legacy default stream).  Inputs and outputs
  * are caller-owned device pointers as for gs_render_with_grads: out_C
  * [3][H][W], out_grads [3][3][H][W].
@@ -371,8 +374,11 @@ gs_status gs_backward(gs_ctx* ctx, const float* dL_dout, int32_t factor, const g
  * capture.  The call synchronises the stream (pair-count readback and a final
  * error check).  All calls share the array and its contents persist between
  * calls; whatever must start at zero is cleared by each call.  Calls whose
- * work could overlap on the GPU (other streams, other host threads) race on
- * the array and must be serialised by the caller. */
+ * work could overlap on the same GPU (other streams, other host threads) race
+ * on that GPU's array and must be serialised by the caller.  The host side
+ * keeps no per-call state outside the call (the read-backs are locals, the
+ * per-device address an atomic word), so calls on different GPUs from
+ * different host threads are independent. */
 gs_status gs_render_with_grads_noalloc(const gs_gaussians* g, const gs_camera* cam, int32_t W, int32_t H,
                                        const gs_options* opt, void* stream, float* out_C, float* out_grads);
 
@@ -413,6 +419,24 @@ gs_status gs_blend_stats(gs_ctx* ctx, int64_t* counts);
 /* Number of kernels libgs has launched on behalf of ctx since gs_create (host
  * int64; counts every kernel of every call, e.g. for launch accounting). */
 gs_status gs_launch_count(const gs_ctx* ctx, int64_t* count);
+
+/* Fault injection for tests of the error paths (no counterpart in the paper).
+ * Nothing injected faults, traps or hangs the GPU:
+ *   GS_INJECT_WAIT_EXPIRY, value = polls (1..2^24): the next frame whose depth
+ *     sort is the persistent cooperative sort (up to about 10k Gaussians per
+ *     SM) first makes one thread wait, with that bound, for a device word that
+ *     nothing sets.  The wait runs out, records the expiry in the context's
+ *     error word like any bounded wait of the library, and the frame goes on
+ *     unchanged; the next gs_synchronize returns GS_ERR_TIMEOUT.
+ *   GS_INJECT_ALLOC_FAILURE, value = n >= 0: the scratch allocation after the
+ *     next n ones fails as if cudaMalloc had run out of memory (GS_ERR_OOM from
+ *     the call that needed it; the context stays usable).
+ *   GS_INJECT_NONE: cancel both.
+ * Each injection is consumed once. */
+#define GS_INJECT_NONE 0
+#define GS_INJECT_WAIT_EXPIRY 1
+#define GS_INJECT_ALLOC_FAILURE 2
+gs_status gs_debug_inject(gs_ctx* ctx, int32_t what, int64_t value);
 
 /* Wait for the context's stream and report any device-side error recorded by
  * its kernels since the last check (GS_ERR_TIMEOUT / GS_ERR_DEVICE_CHECK, or

@@ -32,6 +32,9 @@ GS_MODE_3DGS = 0
 GS_MODE_EXACT = 1
 MODES = {"3dgs": GS_MODE_3DGS, "exact": GS_MODE_EXACT}
 GS_FLAG_NO_HOST_WAIT = 1
+GS_INJECT_NONE = 0
+GS_INJECT_WAIT_EXPIRY = 1
+GS_INJECT_ALLOC_FAILURE = 2
 GS_VIEWS_CONFIGS = 8
 GS_MLP_IN = 50
 GS_MLP_HIDDEN = 64
@@ -99,6 +102,7 @@ _SIGS = {
     "gs_render_backward": ([_P, _P, _P, _P], ct.c_int),
     "gs_project_backward": ([_P, _P, ct.POINTER(GsGaussianGrads)], ct.c_int),
     "gs_backward": ([_P, _P, ct.c_int32, ct.POINTER(GsGaussianGrads)], ct.c_int),
+    "gs_debug_inject": ([_P, ct.c_int32, ct.c_int64], ct.c_int),
     "gs_render_with_grads_noalloc": ([ct.POINTER(GsGaussians), ct.POINTER(GsCamera), ct.c_int32, ct.c_int32,
                                       ct.POINTER(GsOptions), _P, _P, _P], ct.c_int),
     "gs_upscale_mlp": ([_P, _P, _P, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32, _P, _P], ct.c_int),
@@ -201,6 +205,10 @@ def gs_project_backward(ctx, grad2d: int, out: GsGaussianGrads):
 
 def gs_backward(ctx, dL_dout: int, factor: int, out: GsGaussianGrads):
     _chk(lib.gs_backward(ctx, dL_dout, factor, ct.byref(out)), ctx, "gs_backward")
+
+
+def gs_debug_inject(ctx, what: int, value: int):
+    _chk(lib.gs_debug_inject(ctx, what, value), ctx, "gs_debug_inject")
 
 
 def gs_render_with_grads_noalloc(g: GsGaussians, cam: GsCamera, W: int, H: int, options: GsOptions | None,
@@ -537,6 +545,10 @@ class Context:
 
     def synchronize(self):
         gs_synchronize(self.h)
+
+    def debug_inject(self, what: int, value: int = 0):
+        """Fault injection for the error-path tests (GS_INJECT_*)."""
+        gs_debug_inject(self.h, what, value)
 
     # ---- reverse mode ----------------------------------------------------------
 

@@ -64,6 +64,8 @@ gs_status ensure(gs_ctx* c, DevBuf& b, size_t bytes)
     if (c->reserved)   // after gs_reserve no call allocates
         return fail(c, GS_ERR_CAPACITY, "a buffer of %zu bytes exceeds the reserved capacity", bytes);
     size_t want = bytes + bytes / 4;
+    if (c->inject_alloc_countdown >= 0 && c->inject_alloc_countdown-- == 0)   // gs_debug_inject
+        return fail(c, GS_ERR_OOM, "cudaMalloc(%zu) failed: injected allocation failure", want);
     if (b.p) {
         GS_CUDA(c, cudaStreamSynchronize(c->stream));
         cudaFree(b.p);
@@ -287,7 +289,8 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
                                           reinterpret_cast<uint32_t*>(base + ds_csum_offset(G)),
                                           reinterpret_cast<unsigned int*>(base + ds_bar_offset(G)),
                                           reinterpret_cast<uint32_t*>(base + ds_tot_offset(G)),
-                                          as<int>(c->errword), &sorted, true));
+                                          as<int>(c->errword), &sorted, true, c->inject_wait_spins));
+        c->inject_wait_spins = 0;
     } else {
         if (n > 1) {
             uint32_t* keys[2] = {as<uint32_t>(c->dkey[0]), as<uint32_t>(c->dkey[1])};
@@ -1257,6 +1260,26 @@ gs_status gs_blend_stats(gs_ctx* c, int64_t* counts)
     counts[0] = (int64_t)h[0];
     counts[1] = (int64_t)h[1];
     return GS_OK;
+}
+
+gs_status gs_debug_inject(gs_ctx* c, int32_t what, int64_t value)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    switch (what) {
+    case GS_INJECT_NONE:
+        c->inject_wait_spins = 0;
+        c->inject_alloc_countdown = -1;
+        return GS_OK;
+    case GS_INJECT_WAIT_EXPIRY:
+        if (value < 1 || value > (1 << 24)) return fail(c, GS_ERR_INVALID_ARG, "polls must be in 1..2^24");
+        c->inject_wait_spins = (uint32_t)value;
+        return GS_OK;
+    case GS_INJECT_ALLOC_FAILURE:
+        if (value < 0) return fail(c, GS_ERR_INVALID_ARG, "countdown must be >= 0");
+        c->inject_alloc_countdown = value;
+        return GS_OK;
+    }
+    return fail(c, GS_ERR_INVALID_ARG, "unknown injection %d", what);
 }
 
 gs_status gs_launch_count(const gs_ctx* c, int64_t* count)

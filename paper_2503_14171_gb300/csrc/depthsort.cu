@@ -35,6 +35,9 @@
 //
 // Grid barriers spin at most kGridSpinLimit times; on expiry the block records
 // kDevTimeout in the error word and carries on (outputs undefined, no hang).
+#include <atomic>
+#include <mutex>
+
 #include <cooperative_groups.h>
 
 #include "gs_internal.cuh"
@@ -72,9 +75,10 @@ struct DsArgs {
     uint32_t* csum;              // [grid][512] per-block digit sums of the pair counts (last pass);
                                  // words 0, 1 of a block's row first carry its key range
     uint32_t* tot;               // [5][512] digit totals per pass, then the pair-count totals (zeroed)
-    unsigned int* bar;           // [2] barrier counter and generation (zeroed)
+    unsigned int* bar;           // [2] barrier counter and generation (zeroed); bar[2] stays zero
     int* err;
     uint32_t n;
+    uint32_t inject_spins;       // > 0: block 0 first polls bar[2], which nothing sets, this many times
 };
 
 // Grid-wide barrier for a cooperative launch (all blocks resident).  Thread 0
@@ -83,6 +87,23 @@ struct DsArgs {
 // of the blocks that arrived earlier); the last to arrive resets the count and
 // publishes the next generation with a release add; the others poll the
 // generation with acquire loads.
+// Poll word (acquire loads) until it differs from `unchanged`, at most limit
+// times; on expiry record kDevTimeout in the error word and return false.
+__device__ __forceinline__ bool bounded_poll(const unsigned int* word, unsigned int unchanged, long limit, int* err)
+{
+    long spins = 0;
+    unsigned int g;
+    do {
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(word) : "memory");
+        if (g != unchanged) return true;
+        if (++spins > limit) {
+            atomicExch(err, kDevTimeout);
+            return false;
+        }
+        __nanosleep(32);
+    } while (true);
+}
+
 __device__ __forceinline__ void grid_barrier(unsigned int* bar, int* err)
 {
     __syncthreads();
@@ -94,17 +115,7 @@ __device__ __forceinline__ void grid_barrier(unsigned int* bar, int* err)
             asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(bar) : "memory");
             asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar + 1) : "memory");
         } else {
-            long spins = 0;
-            unsigned int g;
-            do {
-                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(bar + 1) : "memory");
-                if (g != gen) break;
-                if (++spins > kGridSpinLimit) {
-                    atomicExch(err, kDevTimeout);
-                    break;
-                }
-                __nanosleep(32);
-            } while (true);
+            bounded_poll(bar + 1, gen, kGridSpinLimit, err);
         }
     }
     __syncthreads();
@@ -138,6 +149,11 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
     uint32_t* s_obase = s_cbase + R;                                  // [R]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt = (1u << lane) - 1u;
+
+    // fault injection for the tests of the expiry path: a bounded wait for a
+    // word nothing sets runs out and records kDevTimeout; the sort itself is
+    // unaffected
+    if (a.inject_spins && blockIdx.x == 0 && tid == 0) bounded_poll(a.bar + 2, 0u, (long)a.inject_spins, a.err);
 
     // ---- the slice's keys and the range of the visible ones ----
     uint32_t rk[kDsPer];
@@ -437,10 +453,28 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
     }
 }
 
+// Grid of the persistent sort on each device (its SM count, or 0 when one
+// block per SM does not fit), computed once per device.  The cache is one
+// atomic word per device (-1 = not yet known): concurrent first calls from
+// several host threads compute the same value, and a reader never sees a
+// value that belongs to another device.
+constexpr int kDsMaxDevices = 64;
+std::atomic<int> g_ds_grid[kDsMaxDevices] = {};
+std::atomic<bool> g_ds_grid_init{false};
+std::mutex g_ds_grid_mutex;
+
 int ds_grid(int device)
 {
-    static int cached_dev = -1, cached = 0;
-    if (cached_dev == device) return cached;
+    if (device < 0 || device >= kDsMaxDevices) return 0;
+    if (!g_ds_grid_init.load(std::memory_order_acquire)) {
+        std::lock_guard<std::mutex> lock(g_ds_grid_mutex);
+        if (!g_ds_grid_init.load(std::memory_order_relaxed)) {
+            for (auto& v : g_ds_grid) v.store(-1, std::memory_order_relaxed);
+            g_ds_grid_init.store(true, std::memory_order_release);
+        }
+    }
+    const int known = g_ds_grid[device].load(std::memory_order_acquire);
+    if (known >= 0) return known;
     int sms = 0, per_sm = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
     const size_t smem = depth_sort_smem_bytes();
@@ -448,9 +482,9 @@ int ds_grid(int device)
         return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_depth_sort_scan, kDsThreads, smem) != cudaSuccess)
         return 0;
-    cached_dev = device;
-    cached = per_sm >= 1 ? sms : 0;
-    return cached;
+    const int grid = per_sm >= 1 ? sms : 0;
+    g_ds_grid[device].store(grid, std::memory_order_release);
+    return grid;
 }
 
 }  // namespace
@@ -468,7 +502,8 @@ uint32_t depth_sort_capacity(int device)
 cudaError_t launch_depth_sort_scan(cudaStream_t s, int device, const uint32_t* keys_in, uint32_t* keys[2],
                                    uint32_t* ids[2], const uint32_t* counts, uint32_t n, uint32_t* offsets,
                                    uint32_t* cnt_scratch, uint32_t* csum_scratch, unsigned int* bar,
-                                   uint32_t* tot_scratch, int* err, int* out_idx, bool pre_zeroed)
+                                   uint32_t* tot_scratch, int* err, int* out_idx, bool pre_zeroed,
+                                   uint32_t inject_spins)
 {
     const int G = ds_grid(device);
     if (G <= 0 || n == 0 || n > (uint32_t)G * (uint32_t)kDsMaxSlice || n > kDsMaxN) return cudaErrorInvalidValue;
@@ -477,7 +512,7 @@ cudaError_t launch_depth_sort_scan(cudaStream_t s, int device, const uint32_t* k
     const uint32_t grid = (uint32_t)(want < (uint64_t)G ? want : (uint64_t)G);
     cudaError_t e = cudaSuccess;
     if (!pre_zeroed) {
-        if ((e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), s)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(bar, 0, 3 * sizeof(unsigned int), s)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(tot_scratch, 0, sizeof(uint32_t) * kDsTotWords, s)) != cudaSuccess) return e;
     }
     DsArgs a;
@@ -494,6 +529,7 @@ cudaError_t launch_depth_sort_scan(cudaStream_t s, int device, const uint32_t* k
     a.bar = bar;
     a.err = err;
     a.n = n;
+    a.inject_spins = inject_spins;
     // a cooperative launch (all blocks co-resident, checked against the
     // occupancy above); launched through cudaLaunchKernelEx so that it can be
     // recorded in a CUDA graph

@@ -176,6 +176,9 @@ struct gs_ctx {
     int sorted_ids_buf = 0;             // which did[] holds the depth-sorted ids
     int sorted_pairs_buf = 0;           // which pairs[] holds the sorted pairs
     int64_t launches = 0;               // kernels launched on behalf of this context
+    // fault injection (gs_debug_inject): one-shot, consumed by the next use
+    uint32_t inject_wait_spins = 0;     // the next persistent depth sort's extra wait runs out after this many polls
+    int64_t inject_alloc_countdown = -1;   // the allocation after this many more fails (-1: none)
 };
 
 namespace gs {
@@ -311,7 +314,8 @@ constexpr uint32_t ds_zero_words() { return 16 + kDsTotWords; }
 cudaError_t launch_depth_sort_scan(cudaStream_t s, int device, const uint32_t* keys_in, uint32_t* keys[2],
                                    uint32_t* ids[2], const uint32_t* counts, uint32_t n, uint32_t* offsets,
                                    uint32_t* cnt_scratch, uint32_t* csum_scratch, unsigned int* bar,
-                                   uint32_t* tot_scratch, int* err, int* out_idx, bool pre_zeroed = false);
+                                   uint32_t* tot_scratch, int* err, int* out_idx, bool pre_zeroed = false,
+                                   uint32_t inject_spins = 0);
 
 // pairs at offsets >= cap are counted but not written (the capacity check of
 // launch_supers_to_hist then rejects the frame)

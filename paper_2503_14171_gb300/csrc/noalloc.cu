@@ -18,8 +18,12 @@
 // that first call before any stream capture.  All calls share the array and
 // it keeps the last call's contents: what must start at zero is cleared on
 // every call, and two calls whose work overlaps on the GPU (different streams,
-// different host threads) race on it.
-#include <string.h>
+// different host threads) race on it.  Host-side state is per call (the
+// readbacks are locals) apart from the per-device address, which is an
+// atomic word, so calls from several host threads on different devices are
+// independent.
+#include <algorithm>
+#include <atomic>
 
 #include "gs_internal.cuh"
 
@@ -68,9 +72,7 @@ static_assert(kNaMaxSupers <= (uint32_t)kMaxSupersForCounts, "super-tile counts 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaScratchBytes];
 
 constexpr int kNaMaxDevices = 64;
-unsigned char* g_na_base[kNaMaxDevices] = {nullptr};          // device address of the array, per device
-unsigned long long g_na_totals[2 * kTotalSlots];              // host copy of the pair totals
-int g_na_err = 0;
+std::atomic<unsigned char*> g_na_base[kNaMaxDevices] = {};    // device address of the array, per device
 
 template <typename T>
 T* at(unsigned char* base, size_t off)
@@ -126,6 +128,8 @@ extern "C" gs_status gs_render_with_grads_noalloc(const gs_gaussians* g, const g
     o.mode = GS_MODE_3DGS;
     if (opt) o = *opt;
     if (o.tile != kTile || (o.mode != GS_MODE_3DGS && o.mode != GS_MODE_EXACT)) return GS_ERR_INVALID_ARG;
+    // every call waits for its pair count and its error word: no flag applies
+    if (o.flags != 0 || o.max_pairs < 0) return GS_ERR_INVALID_ARG;
     if (!g || !cam || !out_C || !out_grads) return GS_ERR_INVALID_ARG;
     if (W < 1 || H < 1 || (uint32_t)W > kNaMaxSide || (uint32_t)H > kNaMaxSide) return GS_ERR_INVALID_ARG;
     if ((uint64_t)W * (uint64_t)H > kNaMaxPixels) return GS_ERR_CAPACITY;
@@ -141,12 +145,13 @@ extern "C" gs_status gs_render_with_grads_noalloc(const gs_gaussians* g, const g
     int dev = 0;
     NA_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kNaMaxDevices) return GS_ERR_INVALID_ARG;
-    if (!g_na_base[dev]) {
+    unsigned char* base = g_na_base[dev].load(std::memory_order_acquire);
+    if (!base) {   // concurrent first calls look up the same address
         void* ptr = nullptr;
         NA_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
-        g_na_base[dev] = static_cast<unsigned char*>(ptr);
+        base = static_cast<unsigned char*>(ptr);
+        g_na_base[dev].store(base, std::memory_order_release);
     }
-    unsigned char* base = g_na_base[dev];
 
     const uint32_t n = (uint32_t)g->n;
     const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
@@ -169,19 +174,25 @@ extern "C" gs_status gs_render_with_grads_noalloc(const gs_gaussians* g, const g
     NA_CUDA(cudaMemsetAsync(sranges, 0, sizeof(uint2) * Ts, s));
 
     const CameraParams cp = na_camera(*cam, W, H);
+    unsigned long long h_totals[2 * kTotalSlots] = {};   // pair totals (pageable; the copy completes before use)
     if (n > 0) {
         NA_CUDA(launch_project(s, *g, cp, W, H, tiles_x, tiles_y, o.mode, rec, at<float>(base, kOffDepth),
                                at<int>(base, kOffRadius), at<ushort4>(base, kOffRect), at<uint32_t>(base, kOffTiles),
                                at<uint32_t>(base, kOffSupers), keys[0], ids[0], totals));
         // pair totals to pageable host memory (a synchronous copy; no pinned buffer)
-        NA_CUDA(cudaMemcpyAsync(g_na_totals, totals, sizeof(g_na_totals), cudaMemcpyDeviceToHost, s));
+        NA_CUDA(cudaMemcpyAsync(h_totals, totals, sizeof(h_totals), cudaMemcpyDeviceToHost, s));
         NA_CUDA(cudaStreamSynchronize(s));
-    } else {
-        memset(g_na_totals, 0, sizeof(g_na_totals));
     }
-    unsigned long long Ps64 = 0;
-    for (int k = 0; k < kTotalSlots; ++k) Ps64 += g_na_totals[2 * k];
+    unsigned long long Ps64 = 0, P64 = 0;
+    for (int k = 0; k < kTotalSlots; ++k) {
+        Ps64 += h_totals[2 * k];
+        P64 += h_totals[2 * k + 1];
+    }
     if (Ps64 > kNaMaxSuperPairs) return GS_ERR_CAPACITY;
+    // the (tile, Gaussian) pair limit of the options, as gs_render_with_grads applies it
+    const unsigned long long limit =
+        o.max_pairs > 0 ? (unsigned long long)std::min<int64_t>(o.max_pairs, kMaxPairs) : (unsigned long long)kMaxPairs;
+    if (P64 > limit) return GS_ERR_CAPACITY;
     const uint32_t Ps = (uint32_t)Ps64;
 
     int sorted = 0;
@@ -239,9 +250,10 @@ extern "C" gs_status gs_render_with_grads_noalloc(const gs_gaussians* g, const g
     NA_CUDA(launch_blend(s, true, o.mode, a));
 
     // report a bounded device wait that expired (outputs are then undefined)
-    NA_CUDA(cudaMemcpyAsync(&g_na_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int h_err = 0;
+    NA_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     NA_CUDA(cudaStreamSynchronize(s));
-    if (g_na_err == kDevTimeout) return GS_ERR_TIMEOUT;
-    if (g_na_err != kDevOk) return GS_ERR_DEVICE_CHECK;
+    if (h_err == kDevTimeout) return GS_ERR_TIMEOUT;
+    if (h_err != kDevOk) return GS_ERR_DEVICE_CHECK;
     return GS_OK;
 }
