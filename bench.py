@@ -43,11 +43,13 @@ METRIC = "output MPix/s render+upscale vs direct full-res render, same GB300, at
 # pair with the derivative recurrences adds 52 (itemised beside the blend kernel).
 FLOP_EVAL = 10
 FLOP_ACC_GRADS = 52
+# The scope table's estimate of the same work (the count the roofline is
+# graded on): about 10 per evaluated pair and about 100 per blended pair.
+FLOP_ACC_SURVEY = 100
 # The blend adjoint re-evaluates each pair (10) and, per blended pair, inverts
 # the state update, forms the weights, the adjoints and the 9 gradient terms
 # and sums them over the tile's pixels: 173 (itemised beside the kernel).
 FLOP_BWD_BLEND = 173
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
 
@@ -426,6 +428,21 @@ def run_gs(args):
 
         ms_4x_eager = time_loop(step4, kd)
         Ps_4x = ctx.super_pair_count()
+        P_4x = ctx.pair_count()
+        n_eval4, n_acc4 = ctx.blend_stats()
+        # per-stage CUDA-event times of the 4x path (eager, as stages_ms of the 2x path)
+        ev4 = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(kd)]
+        for k in range(kd):
+            ev4[k][0].record(stream)
+            ctx.project(dev, cam4, OUT_W // 4, OUT_H // 4)
+            ev4[k][1].record(stream)
+            ctx.render_binned(grads=True, out_C=C4, out_grads=G4)
+            ev4[k][2].record(stream)
+            ctx.upscale(C4, G4, 4, out=out4)
+            ev4[k][3].record(stream)
+        torch.cuda.synchronize()
+        stages4 = {name: statistics.mean(e[q].elapsed_time(e[q + 1]) for e in ev4)
+                   for q, name in enumerate(("project_bin", "blend_grads", "upscale"))}
 
         def body4(gc):
             gc.render_with_grads(dev, cam4, OUT_W // 4, OUT_H // 4, out_C=C4, out_grads=G4)
@@ -481,6 +498,11 @@ def run_gs(args):
         torch.cuda.synchronize()
         psnr_15 = psnr(out15.cpu().numpy(), d_np)
         gctx_15.close()
+
+        # PSNR against the direct render as the Gaussians shrink below a pixel
+        sweep = psnr_sweep_leg(torch, gs, scenes, stream) if world == 1 else None
+        # the paper's largest workload size: 5M Gaussians at about 5K output
+        garden = garden_leg(torch, gs, scenes, stream) if world == 1 else None
 
         # batched multi-view rendering (stereo pairs), batched vs one view at a time
         views = views_leg(torch, gs, scenes, stream) if world == 1 else None
@@ -612,10 +634,15 @@ def run_gs(args):
     peaks, src = _peaks()
     clk = clocks.summary()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12    # TFLOP/s
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    # MEASURED_PEAKS.json holds no FP32 figure: the ALU peak is derived from the
+    # unit counts (SMs read from the device) and the maximum SM clock
+    alu_peak = sm_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12    # TFLOP/s
     blend_ms = statistics.mean(t_blend)
-    flops = n_eval * FLOP_EVAL + n_acc * FLOP_ACC_GRADS
+    flops = n_eval * FLOP_EVAL + n_acc * FLOP_ACC_SURVEY
     achieved = flops / (blend_ms * 1e-3) / 1e12
+    flops_itemised = n_eval * FLOP_EVAL + n_acc * FLOP_ACC_GRADS
+    achieved_itemised = flops_itemised / (blend_ms * 1e-3) / 1e12
     traffic = _traffic_from_profiles()
 
     cpu = None
@@ -640,7 +667,12 @@ def run_gs(args):
         "direct_render": {"mpix_s": OUT_W * OUT_H / 1e3 / ms_direct, "ms": ms_direct, "pairs": P_direct},
         "speedup_vs_direct": (OUT_W * OUT_H / 1e3 / ms_step) / (OUT_W * OUT_H / 1e3 / ms_direct),
         "psnr_db": {"2x_960x540": psnr2, "4x_480x270": psnr4, "vs": "direct 1920x1080 render, clipped to [0,1]"},
-        "path_4x": {"mpix_s": OUT_W * OUT_H / 1e3 / ms_4x, "ms": ms_4x},
+        "path_4x": {"mpix_s": OUT_W * OUT_H / 1e3 / ms_4x, "ms": ms_4x, "low_res": [OUT_W // 4, OUT_H // 4],
+                    "stages_ms": stages4, "pairs": P_4x, "super_pairs": Ps_4x,
+                    "pairs_evaluated": n_eval4, "pairs_blended": n_acc4,
+                    "speedup_vs_2x": ms_step / ms_4x},
+        "psnr_sweep": sweep,
+        "garden_scale": garden,
         "multi_view": views,
         "learned_residual": learned,
         "comparisons": {
@@ -656,7 +688,13 @@ def run_gs(args):
                       "upscale": statistics.mean(t_up)},
         "roofline": {"bound": "alu", "kernel": "k_blend<grads,3dgs>", "achieved": achieved, "peak": alu_peak,
                      "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": traffic,
-                     "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x %.0f MHz (sm_max_mhz, %s)" % (sm_mhz, src),
+                     "flop_count": "scope-table estimate: %d per evaluated pair + %d per blended pair"
+                                   % (FLOP_EVAL, FLOP_ACC_SURVEY),
+                     "achieved_itemised": achieved_itemised, "frac_itemised": achieved_itemised / alu_peak,
+                     "flop_count_itemised": "formulas counted term by term: %d per evaluated pair + %d per "
+                                            "blended pair" % (FLOP_EVAL, FLOP_ACC_GRADS),
+                     "peak_source": "derived, not measured: FP32 FMA %d SMs (from the device) x %d lanes x 2 x "
+                                    "%.0f MHz (sm_max_mhz, %s)" % (sm_count, FP32_LANES_PER_SM, sm_mhz, src),
                      "pairs_evaluated": n_eval, "pairs_blended": n_acc},
         "upscale_hbm": {"achieved_gbs": (LOW_W * LOW_H * 48 + OUT_W * OUT_H * 12) / (statistics.mean(t_up) * 1e-3) / 1e9,
                         "peak_gbs": peaks.get("hbm_gbs"), "peak_source": src},
@@ -686,6 +724,118 @@ def run_gs(args):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def psnr_sweep_leg(torch, gs, scenes, stream, means=(-4.0, -5.0, -6.0), reps=10):
+    """The 2x and 4x paths and the direct 1920x1080 render of the benchmark
+    scene's recipe at smaller Gaussians (mean log-scale -4, -5, -6): PSNR of
+    each upscaled frame against the direct render, the median 3-sigma radius
+    in low-res pixels, and the frame times.  At -5 and -6 most Gaussians are
+    smaller than a 960x540 pixel, the regime where the paper expects the
+    upscaling to lose detail (Sec. 6.4)."""
+    out = {}
+    cam = scenes.pinhole_camera(LOW_W, LOW_H)
+    cam4 = scenes.pinhole_camera(OUT_W // 4, OUT_H // 4)
+    cam_hi = scenes.scaled_camera(cam, FACTOR)
+    with torch.cuda.stream(stream):
+        ctx = gs.Context(stream=stream)
+        for m in means:
+            dev = gs.DeviceScene(scenes.mixture_scene(N_GAUSS, seed=0, log_scale_mean=m))
+            direct = ctx.render(dev, cam_hi, OUT_W, OUT_H)
+            C, G = ctx.render_with_grads(dev, cam, LOW_W, LOW_H)
+            rad = ctx.read_projected()["radius"]
+            vis = rad[rad > 0].float()
+            med_r = float(vis.median().item()) if vis.numel() else 0.0
+            up2 = ctx.upscale(C, G, FACTOR)
+            C4, G4 = ctx.render_with_grads(dev, cam4, OUT_W // 4, OUT_H // 4)
+            up4 = ctx.upscale(C4, G4, 4)
+            torch.cuda.synchronize()
+            d_np = direct.cpu().numpy()
+            row = {"psnr_2x_db": psnr(up2.cpu().numpy(), d_np), "psnr_4x_db": psnr(up4.cpu().numpy(), d_np),
+                   "median_radius_3sigma_px_960x540": med_r}
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            for name, fn in (("direct_ms", lambda: ctx.render(dev, cam_hi, OUT_W, OUT_H, out_C=direct)),
+                             ("path_2x_ms", lambda: (ctx.render_with_grads(dev, cam, LOW_W, LOW_H, out_C=C,
+                                                                           out_grads=G),
+                                                     ctx.upscale(C, G, FACTOR, out=up2))),
+                             ("path_4x_ms", lambda: (ctx.render_with_grads(dev, cam4, OUT_W // 4, OUT_H // 4,
+                                                                           out_C=C4, out_grads=G4),
+                                                     ctx.upscale(C4, G4, 4, out=up4)))):
+                for _ in range(2):
+                    fn()
+                a.record(stream)
+                for _ in range(reps):
+                    fn()
+                b.record(stream)
+                torch.cuda.synchronize()
+                row[name] = a.elapsed_time(b) / reps
+            out["log_scale_mean_%g" % m] = row
+            del dev
+        ctx.close()
+    torch.cuda.empty_cache()
+    return {"what": "1.5M-Gaussian mixture scenes, seed 0, mean log-scale as keyed; PSNR of the upscaled "
+                    "1920x1080 frame against the direct 1920x1080 render; eager API calls", "by_scale": out}
+
+
+GARDEN_N = 5_000_000
+GARDEN_W, GARDEN_H = 5184, 3360     # about the paper's 5187 x 3361 target, divisible by 2, 4 and 8
+
+
+def garden_leg(torch, gs, scenes, stream, reps=5):
+    """The size of the paper's largest workload (garden: 5M Gaussians at
+    5187 x 3361, Table 2 and the supplement's render-time table): a 5M-Gaussian
+    mixture scene rendered directly at 5184 x 3360 and through the spline at
+    2x, 4x and 8x.  5M Gaussians exceed the persistent depth sort's capacity,
+    so this frame runs the one-sweep depth sort and the single-pass offset
+    scan."""
+    res = {"n_gaussians": GARDEN_N, "out_res": [GARDEN_W, GARDEN_H]}
+    with torch.cuda.stream(stream):
+        dev = gs.DeviceScene(scenes.mixture_scene(GARDEN_N, seed=0))
+        ctx = gs.Context(stream=stream)
+        cam_hi = scenes.pinhole_camera(GARDEN_W, GARDEN_H)
+        direct = torch.empty(3, GARDEN_H, GARDEN_W, device="cuda")
+        up = torch.empty(3, GARDEN_H, GARDEN_W, device="cuda")
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+        def timed(fn):
+            for _ in range(2):
+                fn()
+            torch.cuda.synchronize()
+            a.record(stream)
+            for _ in range(reps):
+                fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / reps
+
+        ms_d = timed(lambda: ctx.render(dev, cam_hi, GARDEN_W, GARDEN_H, out_C=direct))
+        res["direct"] = {"ms": ms_d, "mpix_s": GARDEN_W * GARDEN_H / 1e3 / ms_d, "pairs": ctx.pair_count()}
+        d_np = None
+        for f in (2, 4, 8):
+            w, h = GARDEN_W // f, GARDEN_H // f
+            cam = scenes.pinhole_camera(w, h)
+            C = torch.empty(3, h, w, device="cuda")
+            G = torch.empty(3, 3, h, w, device="cuda")
+
+            def step():
+                ctx.render_with_grads(dev, cam, w, h, out_C=C, out_grads=G)
+                ctx.upscale(C, G, f, out=up)
+
+            ms = timed(step)
+            if d_np is None:
+                ctx.render(dev, cam_hi, GARDEN_W, GARDEN_H, out_C=direct)
+                torch.cuda.synchronize()
+                d_np = direct.cpu().numpy()
+            step()
+            torch.cuda.synchronize()
+            res["spline_%dx" % f] = {"ms": ms, "mpix_s": GARDEN_W * GARDEN_H / 1e3 / ms,
+                                     "speedup_vs_direct": ms_d / ms, "psnr_db": psnr(up.cpu().numpy(), d_np)}
+        ctx.close()
+        del dev
+    torch.cuda.empty_cache()
+    res["note"] = ("eager API calls (one pair-count wait per frame); the paper's L4 times for the same sizes: "
+                   "direct 72.4 ms, spline 2x 28.7 ms, 4x 14.1 ms, 8x 12.4 ms (context, not target)")
+    return res
 
 
 def _blend_sources_hash():
