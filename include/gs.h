@@ -151,7 +151,7 @@ gs_status gs_set_stream(gs_ctx* ctx, void* stream);
 gs_status gs_set_options(gs_ctx* ctx, const gs_options* opt);
 
 /* Allocate every scratch buffer for frames of up to n Gaussians, W x H pixels
- * and super_pairs (64x64-pixel super-tile, Gaussian) pairs, and fix those
+ * and super_pairs (super-tile, Gaussian) pairs, and fix those
  * capacities.  Needed before frames with GS_FLAG_NO_HOST_WAIT; afterwards no
  * call of this context allocates: a frame beyond n, W or H returns
  * GS_ERR_CAPACITY at once, one beyond super_pairs as described for the flag.
@@ -360,7 +360,7 @@ gs_status gs_backward(gs_ctx* ctx, const float* dL_dout, int32_t factor, const g
  * about 6.6 MB that each GPU loading the library holds until the process
  * exits; no cudaMalloc, cudaFree or other allocating call is made.  Limits:
  * g->n <= 16384, W * H <= 65536 with W, H <= 4096, at most 262144
- * (64x64-pixel super-tile, Gaussian) pairs; beyond them GS_ERR_CAPACITY and
+ * (super-tile, Gaussian) pairs; beyond them GS_ERR_CAPACITY and
  * nothing is written.  opt may be NULL (3DGS mode, black background);
  * opt->flags must be 0 (GS_ERR_INVALID_ARG otherwise: the call always waits
  * for its pair count), and opt->max_pairs limits the (tile, Gaussian) pairs
@@ -387,7 +387,9 @@ gs_status gs_render_with_grads_noalloc(const gs_gaussians* g, const gs_camera* c
  * the frame produced (also when it exceeded the reservation). */
 gs_status gs_pair_count(gs_ctx* ctx, int64_t* P);
 
-/* Number of (64x64-pixel super-tile, Gaussian) pairs of the last gs_project:
+/* Number of (super-tile, Gaussian) pairs of the last gs_project (a super-tile
+ * is ks x ks tiles of 16 x 16 pixels, ks the smallest of 1, 2, 4 for which the
+ * frame has at most 256 super-tiles, else 4; 4 in GS_MODE_EXACT):
  * the pair buffers' size (and the super_pairs a gs_reserve for such frames
  * needs).  Waits as gs_pair_count does. */
 gs_status gs_super_pair_count(gs_ctx* ctx, int64_t* Ps);
@@ -409,6 +411,11 @@ gs_status gs_read_bins(gs_ctx* ctx, uint64_t* keys, uint32_t* vals, uint32_t* ra
  * T_N = 1 - A_N and its d/dx, d/dy, d2/dxdy; count [H][W] (int32) = 1 + the list
  * position of the last Gaussian blended (0 = none).  Either may be NULL. */
 gs_status gs_read_state(gs_ctx* ctx, float* state, int32_t* count);
+
+/* Duration of each tile's block in the last blend, in units of 16 SM clock
+ * cycles: work [tiles_y][tiles_x] (device uint32; the next frame's blend takes
+ * the tiles heaviest first by these).  For load-balance inspection. */
+gs_status gs_read_tile_work(gs_ctx* ctx, uint32_t* work);
 
 /* Work counts of a blend of the last gs_project's binning (3DGS or exact mode
  * as configured): counts[0] = (pixel, Gaussian) pairs evaluated, counts[1] =

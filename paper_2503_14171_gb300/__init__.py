@@ -103,6 +103,7 @@ _SIGS = {
     "gs_project_backward": ([_P, _P, ct.POINTER(GsGaussianGrads)], ct.c_int),
     "gs_backward": ([_P, _P, ct.c_int32, ct.POINTER(GsGaussianGrads)], ct.c_int),
     "gs_debug_inject": ([_P, ct.c_int32, ct.c_int64], ct.c_int),
+    "gs_read_tile_work": ([_P, _P], ct.c_int),
     "gs_render_with_grads_noalloc": ([ct.POINTER(GsGaussians), ct.POINTER(GsCamera), ct.c_int32, ct.c_int32,
                                       ct.POINTER(GsOptions), _P, _P, _P], ct.c_int),
     "gs_upscale_mlp": ([_P, _P, _P, ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32, _P, _P], ct.c_int),
@@ -531,6 +532,14 @@ class Context:
         count = self._empty(self.H, self.W, dtype=torch.int32)
         _chk(lib.gs_read_state(self.h, state.data_ptr(), count.data_ptr()), self.h, "gs_read_state")
         return state, count
+
+    def read_tile_work(self):
+        """Per-tile block durations of the last blend (units of 16 SM cycles), [tiles_y, tiles_x]."""
+        torch = _torch()
+        tx, ty = (self.W + 15) // 16, (self.H + 15) // 16
+        out = torch.empty(ty, tx, dtype=torch.int32, device="cuda")
+        _chk(lib.gs_read_tile_work(self.h, out.data_ptr()), self.h, "gs_read_tile_work")
+        return out
 
     def blend_stats(self):
         """(pairs evaluated, pairs blended) of the current binning."""

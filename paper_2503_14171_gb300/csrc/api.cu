@@ -199,7 +199,8 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
     c->have_state = false;
     c->order_ready = false;
     const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
-    const int stiles_x = (tiles_x + kSuper - 1) / kSuper, stiles_y = (tiles_y + kSuper - 1) / kSuper;
+    const int ks = super_side(tiles_x, tiles_y, c->opt.mode);
+    const int stiles_x = (tiles_x + ks - 1) / ks, stiles_y = (tiles_y + ks - 1) / ks;
     const int64_t T = (int64_t)tiles_x * tiles_y;
     const int64_t Ts = (int64_t)stiles_x * stiles_y;
     if (T > 0x7FFFFFFF) return fail(c, GS_ERR_INVALID_ARG, "too many tiles");
@@ -266,7 +267,7 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
         zl.words[zl.count++] = (uint32_t)spasses;
     }
     GS_CUDA(c, cudaMemsetAsync(totals, 0, 2 * kTotalSlots * sizeof(unsigned long long), c->stream));
-    GS_CUDA(c, launch_project(c->stream, *g, cp, W, H, tiles_x, tiles_y, c->opt.mode, rec, as<float>(c->depth),
+    GS_CUDA(c, launch_project(c->stream, *g, cp, W, H, tiles_x, tiles_y, ks, c->opt.mode, rec, as<float>(c->depth),
                               as<int>(c->radius), as<ushort4>(c->rect), as<uint32_t>(c->tiles_touched),
                               as<uint32_t>(c->supers_touched), as<uint32_t>(c->dkey[0]), as<uint32_t>(c->did[0]),
                               totals, &zl));
@@ -314,7 +315,7 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
         const uint32_t cap = (uint32_t)c->res_pairs;
         uint64_t* pairs[2] = {as<uint64_t>(c->pairs[0]), as<uint64_t>(c->pairs[1])};
         PairCheckOut* chk = as<PairCheckOut>(c->pair_check);
-        GS_CUDA(c, launch_emit_pairs(c->stream, ids, as<uint32_t>(c->offsets), as<ushort4>(c->rect), n, stiles_x,
+        GS_CUDA(c, launch_emit_pairs(c->stream, ids, as<uint32_t>(c->offsets), as<ushort4>(c->rect), n, ks, stiles_x,
                                      pairs[0], as<uint32_t>(c->super_counts), (uint32_t)Ts, cap));
         const OrderJob job = order_job(c, (uint32_t)(tiles_x * tiles_y));
         GS_CUDA(c, launch_supers_to_hist(c->stream, as<uint32_t>(c->super_counts), (uint32_t)Ts, spasses,
@@ -331,6 +332,7 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
         c->n = n;
         c->W = W;
         c->H = H;
+        c->ks = ks;
         c->tiles_x = tiles_x;
         c->tiles_y = tiles_y;
         c->stiles_x = stiles_x;
@@ -360,8 +362,8 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
                                                                     radix_status_words(n, 0, 32)))))
         return st;
     uint64_t* pairs[2] = {as<uint64_t>(c->pairs[0]), as<uint64_t>(c->pairs[1])};
-    GS_CUDA(c, launch_emit_pairs(c->stream, ids, as<uint32_t>(c->offsets), as<ushort4>(c->rect), n, stiles_x, pairs[0],
-                                 counted ? as<uint32_t>(c->super_counts) : nullptr, (uint32_t)Ts, Ps));
+    GS_CUDA(c, launch_emit_pairs(c->stream, ids, as<uint32_t>(c->offsets), as<ushort4>(c->rect), n, ks, stiles_x,
+                                 pairs[0], counted ? as<uint32_t>(c->super_counts) : nullptr, (uint32_t)Ts, Ps));
     int psorted = 0;
     if (counted) {
         // digit histograms of the super-tile passes and the super-tile ranges,
@@ -389,6 +391,7 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
     c->n = n;
     c->W = W;
     c->H = H;
+    c->ks = ks;
     c->tiles_x = tiles_x;
     c->tiles_y = tiles_y;
     c->stiles_x = stiles_x;
@@ -408,6 +411,7 @@ BlendArgs blend_args(gs_ctx* c, float* out_C, float* out_grads)
     a.tiles_x = c->tiles_x;
     a.tiles_y = c->tiles_y;
     a.stiles_x = c->stiles_x;
+    a.ks = c->ks;
     a.n = (uint32_t)c->n;
     a.sranges = as<uint2>(c->sranges);
     a.pair_words = reinterpret_cast<const uint32_t*>(c->pairs[c->sorted_pairs_buf].p);
@@ -750,6 +754,7 @@ gs_status do_render_backward(gs_ctx* c, const float* dC, const float* dG, float*
     a.H = c->H;
     a.tiles_x = c->tiles_x;
     a.stiles_x = c->stiles_x;
+    a.ks = c->ks;
     a.n = (uint32_t)c->n;
     a.sranges = as<uint2>(c->sranges);
     a.pair_words = reinterpret_cast<const uint32_t*>(c->pairs[c->sorted_pairs_buf].p);
@@ -860,8 +865,11 @@ gs_status reserve_impl(gs_ctx* c, int64_t n, int32_t V, int32_t W, int32_t H, in
         V > kMaxViews)
         return fail(c, GS_ERR_INVALID_ARG, "bad reserve sizes");
     const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
-    const int stiles_x = (tiles_x + kSuper - 1) / kSuper, stiles_y = (tiles_y + kSuper - 1) / kSuper;
-    const int64_t T = (int64_t)tiles_x * tiles_y, Ts = (int64_t)stiles_x * stiles_y;
+    const int stiles_x = (tiles_x + kSuperMax - 1) / kSuperMax, stiles_y = (tiles_y + kSuperMax - 1) / kSuperMax;
+    const int64_t T = (int64_t)tiles_x * tiles_y;
+    // every frame up to W x H: the largest super-tiles give at most Ts4 of them,
+    // smaller ones (chosen only when they fit one sort pass) at most 256
+    const int64_t Ts = std::max<int64_t>((int64_t)stiles_x * stiles_y, std::min<int64_t>(kSuperOnePass, T));
     if (Ts > kMaxSupersForCounts)
         return fail(c, GS_ERR_INVALID_ARG, "%lld super-tiles exceed %d", (long long)Ts, kMaxSupersForCounts);
     const size_t un = (size_t)std::max<int64_t>(n, 1), pix = (size_t)W * H;
@@ -973,7 +981,8 @@ gs_status gs_render_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_
             return fail(c, GS_ERR_INVALID_ARG, "bad view %d", v);
         const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
         const int64_t T = (int64_t)tiles_x * tiles_y;
-        const int64_t Ts = (int64_t)((tiles_x + kSuper - 1) / kSuper) * ((tiles_y + kSuper - 1) / kSuper);
+        const int ks = super_side(tiles_x, tiles_y, c->opt.mode);
+        const int64_t Ts = (int64_t)((tiles_x + ks - 1) / ks) * ((tiles_y + ks - 1) / ks);
         if (T > c->res_tiles || Ts > c->res_supers || (int64_t)W * H > c->res_pixels)
             return fail(c, GS_ERR_CAPACITY, "view %d (%d x %d) exceeds the reserved sizes", v, W, H);
         if (out_up && out_up[v]) {
@@ -985,6 +994,7 @@ gs_status gs_render_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_
         batch.v[v].H = H;
         batch.v[v].tiles_x = tiles_x;
         batch.v[v].tiles_y = tiles_y;
+        batch.v[v].ks = ks;
     }
     c->have_proj = false;
     c->have_state = false;
@@ -1043,7 +1053,7 @@ gs_status gs_render_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_
     uv.start[0] = 0;
     for (int v = 0; v < V; ++v) {
         const ViewDesc& d = batch.v[v];
-        const int stiles_x = (d.tiles_x + kSuper - 1) / kSuper, stiles_y = (d.tiles_y + kSuper - 1) / kSuper;
+        const int stiles_x = (d.tiles_x + d.ks - 1) / d.ks, stiles_y = (d.tiles_y + d.ks - 1) / d.ks;
         const uint32_t Ts = (uint32_t)(stiles_x * stiles_y);
         const int sbits = bits_for(Ts);
         const int spasses = radix_passes(32, 32 + sbits);
@@ -1057,7 +1067,7 @@ gs_status gs_render_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_
         uint32_t* ids[2] = {as<uint32_t>(c->did[0]), as<uint32_t>(c->did[1])};
         GS_CUDA(c, cudaMemsetAsync(c->super_counts.p, 0, sizeof(uint32_t) * kCountCopies * Ts, s));
         if (batched) {   // this view's stretch of the batched order and offsets
-            GS_CUDA(c, launch_emit_pairs(s, vsorted + off, as<uint32_t>(c->offsets) + off, rect_v, n, stiles_x,
+            GS_CUDA(c, launch_emit_pairs(s, vsorted + off, as<uint32_t>(c->offsets) + off, rect_v, n, d.ks, stiles_x,
                                          pairs[0], as<uint32_t>(c->super_counts), Ts, cap, (uint32_t)off, true));
         } else {
             int sorted = 0;
@@ -1068,8 +1078,8 @@ gs_status gs_render_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_
                                               reinterpret_cast<unsigned int*>(base + ds_bar_offset(G)),
                                               reinterpret_cast<uint32_t*>(base + ds_tot_offset(G)),
                                               as<int>(c->errword), &sorted, false));
-            GS_CUDA(c, launch_emit_pairs(s, ids[sorted], as<uint32_t>(c->offsets), rect_v, n, stiles_x, pairs[0],
-                                         as<uint32_t>(c->super_counts), Ts, cap));
+            GS_CUDA(c, launch_emit_pairs(s, ids[sorted], as<uint32_t>(c->offsets), rect_v, n, d.ks, stiles_x,
+                                         pairs[0], as<uint32_t>(c->super_counts), Ts, cap));
         }
         GS_CUDA(c, launch_supers_to_hist(s, as<uint32_t>(c->super_counts), Ts, spasses, as<uint32_t>(c->sort_hist),
                                          sranges_v,
@@ -1087,6 +1097,7 @@ gs_status gs_render_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_
         a.tiles_x = d.tiles_x;
         a.tiles_y = d.tiles_y;
         a.stiles_x = stiles_x;
+        a.ks = d.ks;
         a.n = n;
         a.sranges = sranges_v;
         a.pair_words = reinterpret_cast<const uint32_t*>(pairs[psorted]);
@@ -1214,7 +1225,7 @@ gs_status gs_read_bins(gs_ctx* c, uint64_t* keys, uint32_t* vals, uint32_t* rang
         return st;
     GS_CUDA(c, launch_tile_lists(c->stream, as<uint64_t>(c->pairs[c->sorted_pairs_buf]), as<uint2>(c->sranges),
                                  as<ushort4>(c->rect), as<float>(c->depth), (uint32_t)c->n, c->tiles_x, c->tiles_y,
-                                 c->stiles_x, as<uint32_t>(c->tile_count), as<uint32_t>(c->tile_start), keys, vals,
+                                 c->ks, c->stiles_x, as<uint32_t>(c->tile_count), as<uint32_t>(c->tile_start), keys, vals,
                                  reinterpret_cast<uint2*>(ranges)));
     return GS_OK;
 }
@@ -1233,6 +1244,15 @@ gs_status gs_read_state(gs_ctx* c, float* state, int32_t* count)
                                          sizeof(float), npix, cudaMemcpyDeviceToDevice, c->stream));
     }
     if (count) GS_CUDA(c, cudaMemcpyAsync(count, c->count.p, sizeof(int) * npix, cudaMemcpyDeviceToDevice, c->stream));
+    return GS_OK;
+}
+
+gs_status gs_read_tile_work(gs_ctx* c, uint32_t* work)
+{
+    if (!c || !work) return GS_ERR_INVALID_ARG;
+    if (!c->have_state) return fail(c, GS_ERR_NOT_READY, "no blend state");
+    const size_t T = (size_t)c->tiles_x * c->tiles_y;
+    GS_CUDA(c, cudaMemcpyAsync(work, c->tile_work.p, sizeof(uint32_t) * T, cudaMemcpyDeviceToDevice, c->stream));
     return GS_OK;
 }
 

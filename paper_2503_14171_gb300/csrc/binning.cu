@@ -2,13 +2,14 @@
 //
 // Gaussians are first sorted by the FP32 bits of their view depth (a stable
 // radix sort of n keys, ids ascending).  Each Gaussian then emits
-// (tile mask << 48 | super-tile << 32 | id) for every 64x64-pixel super-tile
-// (4x4 tiles) its tile rect touches, in depth order; the mask marks which of
-// the super-tile's 16 tiles the rect covers.  A stable radix sort on the
-// super-tile bits alone yields per-super-tile lists ordered by (depth, id).
-// The blend filters a super-tile's list by the masks, which reproduces every
-// tile's own front-to-back list exactly while sorting 3-5x fewer pairs than
-// per-tile binning (and 8 B instead of 12 B per pair and pass).
+// (tile mask << 48 | super-tile << 32 | id) for every super-tile of ks x ks
+// tiles (ks = 1, 2 or 4, chosen per frame by super_side) its tile rect
+// touches, in depth order; the mask marks which of the super-tile's ks^2 tiles
+// the rect covers.  A stable radix sort on the super-tile bits alone yields
+// per-super-tile lists ordered by (depth, id).  The blend filters a
+// super-tile's list by the masks, which reproduces every tile's own
+// front-to-back list exactly while sorting up to 3-5x fewer pairs than
+// per-tile binning at ks = 4 (and 8 B instead of 12 B per pair and pass).
 //
 // The per-tile lists themselves (keys tile << 32 | depth bits, ids, ranges)
 // are materialised only on request (gs_read_bins), by the same filter.
@@ -22,7 +23,7 @@ namespace {
 // atomic per touched super-tile and block).
 template <bool COUNT>
 __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ ids, const uint32_t* __restrict__ offsets,
-                                              const ushort4* __restrict__ rect, uint32_t n, int stiles_x,
+                                              const ushort4* __restrict__ rect, uint32_t n, int ks, int stiles_x,
                                               uint64_t* __restrict__ pairs, uint32_t* __restrict__ counts,
                                               uint32_t Ts, uint32_t cap, uint32_t id_base, bool rebase)
 {
@@ -39,15 +40,15 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ ids, 
         const uint32_t id = ids[k] - id_base;
         if (off < end && id < n) {   // id >= n only after an expired bounded wait in the sort
             const ushort4 r = rect[id];
-            const int sx0 = r.x / kSuper, sx1 = r.z / kSuper, sy0 = r.y / kSuper, sy1 = r.w / kSuper;
+            const int sx0 = r.x / ks, sx1 = r.z / ks, sy0 = r.y / ks, sy1 = r.w / ks;
             for (int sy = sy0; sy <= sy1; ++sy) {
-                // rows of the super-tile's 4 x 4 tiles inside the rect
-                const int ly0 = max((int)r.y - sy * kSuper, 0), ly1 = min((int)r.w - sy * kSuper, kSuper - 1);
+                // rows of the super-tile's ks x ks tiles inside the rect
+                const int ly0 = max((int)r.y - sy * ks, 0), ly1 = min((int)r.w - sy * ks, ks - 1);
                 for (int sx = sx0; sx <= sx1 && off < end; ++sx) {
-                    const int lx0 = max((int)r.x - sx * kSuper, 0), lx1 = min((int)r.z - sx * kSuper, kSuper - 1);
+                    const int lx0 = max((int)r.x - sx * ks, 0), lx1 = min((int)r.z - sx * ks, ks - 1);
                     const uint32_t cols = ((2u << lx1) - 1u) & ~((1u << lx0) - 1u);
                     uint32_t mask = 0;
-                    for (int ly = ly0; ly <= ly1; ++ly) mask |= cols << (kSuper * ly);
+                    for (int ly = ly0; ly <= ly1; ++ly) mask |= cols << (ks * ly);
                     const uint32_t s = (uint32_t)(sy * stiles_x + sx);
                     if (off < cap) pairs[off] = ((uint64_t)mask << 48) | ((uint64_t)s << 32) | id;
                     ++off;
@@ -89,14 +90,15 @@ __device__ __forceinline__ bool covers(ushort4 r, int tx, int ty)
 template <bool WRITE>
 __global__ void __launch_bounds__(256) k_tile_lists(const uint64_t* __restrict__ spairs, const uint2* __restrict__ sranges,
                                                     const ushort4* __restrict__ rect, const float* __restrict__ depth,
-                                                    uint32_t n, int tiles_x, int stiles_x, uint32_t* __restrict__ count,
+                                                    uint32_t n, int tiles_x, int ks, int stiles_x,
+                                                    uint32_t* __restrict__ count,
                                                     const uint32_t* __restrict__ tile_start, uint64_t* __restrict__ keys,
                                                     uint32_t* __restrict__ vals)
 {
     __shared__ int s_wcnt[8];
     const int t = blockIdx.x;
     const int tx = t % tiles_x, ty = t / tiles_x;
-    const uint2 sr = sranges[(ty / kSuper) * stiles_x + tx / kSuper];
+    const uint2 sr = sranges[(ty / ks) * stiles_x + tx / ks];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t base = WRITE ? tile_start[t] : 0u;
     for (uint32_t c0 = sr.x; c0 < sr.y; c0 += 256) {
@@ -212,16 +214,16 @@ cudaError_t launch_tile_order(cudaStream_t s, const uint32_t* work, uint32_t T, 
 }
 
 cudaError_t launch_emit_pairs(cudaStream_t s, const uint32_t* ids, const uint32_t* offsets, const ushort4* rect,
-                              uint32_t n, int stiles_x, uint64_t* pairs, uint32_t* counts, uint32_t Ts, uint32_t cap,
-                              uint32_t id_base, bool rebase)
+                              uint32_t n, int ks, int stiles_x, uint64_t* pairs, uint32_t* counts, uint32_t Ts,
+                              uint32_t cap, uint32_t id_base, bool rebase)
 {
     if (n == 0) return cudaSuccess;
     if (counts && Ts <= (uint32_t)kMaxSupersForCounts)
-        k_emit<true><<<(n + 255) / 256, 256, 0, s>>>(ids, offsets, rect, n, stiles_x, pairs, counts, Ts, cap, id_base,
-                                                     rebase);
+        k_emit<true><<<(n + 255) / 256, 256, 0, s>>>(ids, offsets, rect, n, ks, stiles_x, pairs, counts, Ts, cap,
+                                                     id_base, rebase);
     else
-        k_emit<false><<<(n + 255) / 256, 256, 0, s>>>(ids, offsets, rect, n, stiles_x, pairs, nullptr, 0, cap, id_base,
-                                                      rebase);
+        k_emit<false><<<(n + 255) / 256, 256, 0, s>>>(ids, offsets, rect, n, ks, stiles_x, pairs, nullptr, 0, cap,
+                                                      id_base, rebase);
     note_launch();
     return cudaGetLastError();
 }
@@ -234,16 +236,16 @@ cudaError_t launch_ranges(cudaStream_t s, const uint64_t* pairs, uint32_t P, uin
 }
 
 cudaError_t launch_tile_lists(cudaStream_t s, const uint64_t* spairs, const uint2* sranges, const ushort4* rect,
-                              const float* depth, uint32_t n, int tiles_x, int tiles_y, int stiles_x,
+                              const float* depth, uint32_t n, int tiles_x, int tiles_y, int ks, int stiles_x,
                               uint32_t* count, uint32_t* start, uint64_t* keys, uint32_t* vals, uint2* ranges)
 {
     const int T = tiles_x * tiles_y;
-    k_tile_lists<false><<<T, 256, 0, s>>>(spairs, sranges, rect, depth, n, tiles_x, stiles_x, count, nullptr, nullptr,
-                                          nullptr); note_launch();
+    k_tile_lists<false><<<T, 256, 0, s>>>(spairs, sranges, rect, depth, n, tiles_x, ks, stiles_x, count, nullptr,
+                                          nullptr, nullptr); note_launch();
     k_tile_starts<<<1, 1024, 0, s>>>(count, (uint32_t)T, start, ranges); note_launch();
     if (keys || vals) {
-        k_tile_lists<true><<<T, 256, 0, s>>>(spairs, sranges, rect, depth, n, tiles_x, stiles_x, count, start, keys,
-                                             vals); note_launch();
+        k_tile_lists<true><<<T, 256, 0, s>>>(spairs, sranges, rect, depth, n, tiles_x, ks, stiles_x, count, start,
+                                             keys, vals); note_launch();
     }
     return cudaGetLastError();
 }

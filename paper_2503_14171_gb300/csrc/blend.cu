@@ -4,8 +4,8 @@
 //
 // One 256-thread block per 16x16 tile, one pixel per thread (each warp an 8x4
 // block of pixels).  Binning is done
-// per 64x64 super-tile (4x4 tiles): the block walks its super-tile's
-// depth-ordered list 256 candidates at a time,
+// per super-tile of ks x ks tiles (ks = 1, 2 or 4 per frame): the block walks
+// its super-tile's depth-ordered list 256 candidates at a time,
 // keeps the Gaussians whose pair marks this tile (an order-preserving
 // block compaction, so the kept sequence is exactly the tile's own
 // front-to-back list) and stages their records in shared memory until at
@@ -150,7 +150,7 @@ __device__ __forceinline__ void blend_tile(const BlendArgs& a, int tile, unsigne
     const float px = (float)x, py = (float)y;
     const uint32_t lanemask_lt = (1u << lane) - 1u;
 
-    const int S = (ty / kSuper) * a.stiles_x + (tx / kSuper);
+    const int S = (ty / a.ks) * a.stiles_x + (tx / a.ks);
     const uint2 sr = a.sranges[S];
     const int total = (int)(sr.y - sr.x);
 
@@ -160,7 +160,7 @@ __device__ __forceinline__ void blend_tile(const BlendArgs& a, int tile, unsigne
     int list_base = 0;   // position of the batch's first record in the tile's list
 
     // candidate of the first round
-    const int tbit = (ty & (kSuper - 1)) * kSuper + (tx & (kSuper - 1));   // this tile in the pair masks
+    const int tbit = (ty & (a.ks - 1)) * a.ks + (tx & (a.ks - 1));   // this tile in the pair masks
     uint32_t cid = 0xFFFFFFFFu;
     bool chit = false;
     if ((int)threadIdx.x < total) chit = pair_hit(a.pair_words, sr.x + threadIdx.x, a.n, tbit, cid);

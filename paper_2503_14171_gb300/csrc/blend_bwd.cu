@@ -237,10 +237,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_bwd(BlendBwdArgs a)
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) M = max(M, s_max[w]);
 
-    const int S = (ty / kSuper) * a.stiles_x + (tx / kSuper);
+    const int S = (ty / a.ks) * a.stiles_x + (tx / a.ks);
     const uint2 sr = a.sranges[S];
     const int total = (int)(sr.y - sr.x);
-    const int tbit = (ty & (kSuper - 1)) * kSuper + (tx & (kSuper - 1));   // this tile in the pair masks
+    const int tbit = (ty & (a.ks - 1)) * a.ks + (tx & (a.ks - 1));   // this tile in the pair masks
 
     // pass 1: the tile's list position at the start of each round of candidates
     int filt = 0, R = 0;

@@ -19,8 +19,8 @@ __device__ __forceinline__ bool covers(ushort4 r, int tx, int ty)
 }
 
 // A (super-tile, Gaussian) pair is mask << 48 | super-tile << 32 | id, with
-// bit 4 ly + lx of the 16-bit mask set when the Gaussian's tile rect covers
-// tile (lx, ly) of the super-tile's 4 x 4 tiles.  pair_hit reads pair k (one
+// bit ks ly + lx of the mask set when the Gaussian's tile rect covers tile
+// (lx, ly) of the super-tile's ks x ks tiles (ks = 1, 2 or 4).  pair_hit reads pair k (one
 // coalesced 8-byte load) and tests the calling tile's bit.
 __device__ __forceinline__ bool pair_hit(const uint32_t* __restrict__ pair_words, size_t k, uint32_t n, int bit,
                                          uint32_t& id)

@@ -10,7 +10,23 @@ namespace gs {
 
 constexpr int kTile = 16;                 // tile side in pixels (16 x 16 = 256 pixels)
 constexpr int kTilePixels = kTile * kTile;
-constexpr int kSuper = 4;                 // super-tile side in tiles (64 x 64 pixels)
+// Tile binning works per super-tile of ks x ks tiles (ks = 1, 2 or 4: a pair
+// carries a ks^2-bit mask of the tiles it covers).  super_side picks ks per
+// frame: the smallest side whose super-tile count fits one 8-bit pass of the
+// pair sort, else the largest.  Small super-tiles keep the blend's filtered
+// walk short (a block scans its super-tile's whole list); at larger images the
+// extra pairs and sort passes of small super-tiles cost more than they save.
+// In exact mode every Gaussian is in every tile, so smaller super-tiles would
+// only multiply the pairs: the largest side is used.
+constexpr int kSuperMax = 4;
+constexpr int kSuperOnePass = 256;        // super-tiles one 8-bit radix pass orders
+inline int super_side(int tiles_x, int tiles_y, int mode)
+{
+    if (mode == GS_MODE_EXACT) return kSuperMax;
+    for (int ks = 1; ks < kSuperMax; ks *= 2)
+        if ((int64_t)((tiles_x + ks - 1) / ks) * ((tiles_y + ks - 1) / ks) <= kSuperOnePass) return ks;
+    return kSuperMax;
+}
 
 // Device error word values (written by bounded waits / device checks).
 constexpr int kDevOk = 0;
@@ -55,6 +71,7 @@ struct DevBuf {
 // Arguments of the blend kernel.
 struct BlendArgs {
     int W, H, tiles_x, tiles_y, stiles_x;
+    int ks;                        // super-tile side in tiles
     uint32_t n;
     const uint2* sranges;          // [super-tiles] list ranges
     const uint32_t* pair_words;    // sorted (super << 32 | id) pairs viewed as 32-bit words
@@ -84,6 +101,7 @@ cudaError_t launch_tile_order(cudaStream_t s, const uint32_t* work, uint32_t T, 
 // opacity, r, g, b), accumulated.
 struct BlendBwdArgs {
     int W, H, tiles_x, stiles_x;
+    int ks;                        // super-tile side in tiles
     uint32_t n;
     const uint2* sranges;          // [super-tiles] list ranges
     const uint32_t* pair_words;    // sorted (super << 32 | id) pairs viewed as 32-bit words
@@ -116,6 +134,7 @@ struct gs_ctx {
     bool have_state = false;
     int64_t n = 0;
     int W = 0, H = 0, tiles_x = 0, tiles_y = 0, stiles_x = 0, stiles_y = 0;
+    int ks = gs::kSuperMax;             // super-tile side of the last projection
     int64_t P = 0;                      // (tile, Gaussian) pairs
     int64_t Ps = 0;                     // (super-tile, Gaussian) pairs
 
@@ -194,6 +213,7 @@ inline void note_launch() { ++launch_counter(); }
 struct ViewDesc {
     CameraParams cam;
     int W, H, tiles_x, tiles_y;
+    int ks;   // super-tile side in tiles
 };
 // Per-view outputs of the batched projection, view v at offset v * n (totals:
 // 2 kTotalSlots per view).
@@ -226,7 +246,7 @@ struct ZeroList {
 };
 
 cudaError_t launch_project(cudaStream_t s, const gs_gaussians& g, const CameraParams& cam, int W, int H,
-                           int tiles_x, int tiles_y, int mode, Records rec, float* depth, int* radius,
+                           int tiles_x, int tiles_y, int ks, int mode, Records rec, float* depth, int* radius,
                            ushort4* rect, uint32_t* tiles_touched, uint32_t* supers_touched, uint32_t* depth_key,
                            uint32_t* ids, unsigned long long* totals,
                            const ZeroList* zero = nullptr);
@@ -323,12 +343,12 @@ cudaError_t launch_depth_sort_scan(cudaStream_t s, int device, const uint32_t* k
 // together (ids[k] - id_base is the view's own id; its pairs start at slot
 // offsets[k] - offsets[0] of its pair buffer)
 cudaError_t launch_emit_pairs(cudaStream_t s, const uint32_t* ids, const uint32_t* offsets, const ushort4* rect,
-                              uint32_t n, int stiles_x, uint64_t* pairs, uint32_t* counts, uint32_t Ts,
+                              uint32_t n, int ks, int stiles_x, uint64_t* pairs, uint32_t* counts, uint32_t Ts,
                               uint32_t cap = 0xFFFFFFFFu, uint32_t id_base = 0, bool rebase = false);
 cudaError_t launch_ranges(cudaStream_t s, const uint64_t* pairs, uint32_t P, uint32_t T, uint2* ranges);
 // per-tile lists from the super-tile lists: counts, starts, ranges and (optionally) keys/vals
 cudaError_t launch_tile_lists(cudaStream_t s, const uint64_t* spairs, const uint2* sranges, const ushort4* rect,
-                              const float* depth, uint32_t n, int tiles_x, int tiles_y, int stiles_x,
+                              const float* depth, uint32_t n, int tiles_x, int tiles_y, int ks, int stiles_x,
                               uint32_t* count, uint32_t* start, uint64_t* keys, uint32_t* vals, uint2* ranges);
 cudaError_t launch_unpack_projected(cudaStream_t s, Records rec, const int* radius, const uint32_t* tiles_touched,
                                     const float* depth_in, uint32_t n, float* mean2d, float* conic, float* rgb,

@@ -155,7 +155,8 @@ extern "C" gs_status gs_render_with_grads_noalloc(const gs_gaussians* g, const g
 
     const uint32_t n = (uint32_t)g->n;
     const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
-    const int stiles_x = (tiles_x + kSuper - 1) / kSuper, stiles_y = (tiles_y + kSuper - 1) / kSuper;
+    const int ks = super_side(tiles_x, tiles_y, o.mode);
+    const int stiles_x = (tiles_x + ks - 1) / ks, stiles_y = (tiles_y + ks - 1) / ks;
     const uint32_t Ts = (uint32_t)(stiles_x * stiles_y);
     if (Ts > kNaMaxSupers) return GS_ERR_CAPACITY;
 
@@ -176,7 +177,7 @@ extern "C" gs_status gs_render_with_grads_noalloc(const gs_gaussians* g, const g
     const CameraParams cp = na_camera(*cam, W, H);
     unsigned long long h_totals[2 * kTotalSlots] = {};   // pair totals (pageable; the copy completes before use)
     if (n > 0) {
-        NA_CUDA(launch_project(s, *g, cp, W, H, tiles_x, tiles_y, o.mode, rec, at<float>(base, kOffDepth),
+        NA_CUDA(launch_project(s, *g, cp, W, H, tiles_x, tiles_y, ks, o.mode, rec, at<float>(base, kOffDepth),
                                at<int>(base, kOffRadius), at<ushort4>(base, kOffRect), at<uint32_t>(base, kOffTiles),
                                at<uint32_t>(base, kOffSupers), keys[0], ids[0], totals));
         // pair totals to pageable host memory (a synchronous copy; no pinned buffer)
@@ -220,8 +221,8 @@ extern "C" gs_status gs_render_with_grads_noalloc(const gs_gaussians* g, const g
     const int sbits = bits_for_na(Ts);
     const int spasses = radix_passes(32, 32 + sbits);
     NA_CUDA(cudaMemsetAsync(scounts, 0, sizeof(uint32_t) * kCountCopies * Ts, s));
-    NA_CUDA(launch_emit_pairs(s, ids[sorted], offsets, at<ushort4>(base, kOffRect), n, stiles_x, pairs[0], scounts,
-                              Ts, Ps));
+    NA_CUDA(launch_emit_pairs(s, ids[sorted], offsets, at<ushort4>(base, kOffRect), n, ks, stiles_x, pairs[0],
+                              scounts, Ts, Ps));
     NA_CUDA(launch_supers_to_hist(s, scounts, Ts, spasses, hist, sranges, PairCheckIn{nullptr, Ps ? Ps : 1u, 0},
                                   nullptr, err));
     int psorted = 0;
@@ -235,6 +236,7 @@ extern "C" gs_status gs_render_with_grads_noalloc(const gs_gaussians* g, const g
     a.tiles_x = tiles_x;
     a.tiles_y = tiles_y;
     a.stiles_x = stiles_x;
+    a.ks = ks;
     a.n = n;
     a.sranges = sranges;
     a.pair_words = reinterpret_cast<const uint32_t*>(pairs[psorted]);

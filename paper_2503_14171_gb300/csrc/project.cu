@@ -111,7 +111,7 @@ struct ViewProj {
 
 __device__ __forceinline__ ViewProj project_view(float mx3, float my3, float mz3, const float S[6], bool ok, float L,
                                                  const CameraParams& cam, int W, int H, int tiles_x, int tiles_y,
-                                                 int mode)
+                                                 int ks, int mode)
 {
     ViewProj o;
     const float S00 = S[0], S01 = S[1], S02 = S[2], S11 = S[3], S12 = S[4], S22 = S[5];
@@ -189,7 +189,7 @@ __device__ __forceinline__ ViewProj project_view(float mx3, float my3, float mz3
     o.rad = rad;
     o.rc = rc;
     o.ntiles = ntiles;
-    o.nsup = ntiles ? (uint32_t)((rc.z / kSuper - rc.x / kSuper + 1) * (rc.w / kSuper - rc.y / kSuper + 1)) : 0u;
+    o.nsup = ntiles ? (uint32_t)((rc.z / ks - rc.x / ks + 1) * (rc.w / ks - rc.y / ks + 1)) : 0u;
     o.vis = vis;
     return o;
 }
@@ -298,7 +298,7 @@ template <int DEG>
 __global__ void __launch_bounds__(kProjThreads) k_project(
     int n, const float* __restrict__ means, const float* __restrict__ log_scales,
     const float* __restrict__ quats, const float* __restrict__ op_logits, const float* __restrict__ sh,
-    const float* __restrict__ rgb_in, CameraParams cam, int W, int H, int tiles_x, int tiles_y,
+    const float* __restrict__ rgb_in, CameraParams cam, int W, int H, int tiles_x, int tiles_y, int ks,
     int mode, Records rec, float* __restrict__ depth_out, int* __restrict__ radius_out,
     ushort4* __restrict__ rect_out, uint32_t* __restrict__ tiles_out, uint32_t* __restrict__ supers_out,
     uint32_t* __restrict__ depth_key, uint32_t* __restrict__ ids, unsigned long long* __restrict__ totals,
@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
     cov3d(quats, log_scales, ii, S, qok);
     const float op = 1.f / (1.f + expf(-op_logits[ii]));
     const float L = logf(255.f * op);
-    const ViewProj v = project_view(mx3, my3, mz3, S, qok && inrange, L, cam, W, H, tiles_x, tiles_y, mode);
+    const ViewProj v = project_view(mx3, my3, mz3, S, qok && inrange, L, cam, W, H, tiles_x, tiles_y, ks, mode);
     // frame totals of (super-tile, Gaussian) and (tile, Gaussian) pairs: they do
     // not depend on the depth order, so they are summed here -- per block, then
     // into one of kTotalSlots slot pairs (spreading the atomics), summed on the host
@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project_views(
     for (int vi = 0; vi < V; ++vi) {
         const ViewDesc d = views[vi];
         const ViewProj v = project_view(mx3, my3, mz3, S, qok && inrange, L, d.cam, d.W, d.H, d.tiles_x, d.tiles_y,
-                                        mode);
+                                        d.ks, mode);
         unsigned long long wsum = v.nsup, wt = v.ntiles;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -725,7 +725,7 @@ __global__ void k_unpack(Records rec, const int* __restrict__ radius, const uint
 }  // namespace
 
 cudaError_t launch_project(cudaStream_t s, const gs_gaussians& g, const CameraParams& cam, int W, int H,
-                           int tiles_x, int tiles_y, int mode, Records rec, float* depth, int* radius, ushort4* rect,
+                           int tiles_x, int tiles_y, int ks, int mode, Records rec, float* depth, int* radius, ushort4* rect,
                            uint32_t* tiles_touched, uint32_t* supers_touched, uint32_t* depth_key, uint32_t* ids,
                            unsigned long long* totals,
                            const ZeroList* zero)
@@ -744,7 +744,7 @@ cudaError_t launch_project(cudaStream_t s, const gs_gaussians& g, const CameraPa
     if (zero) zl = *zero;
 #define GS_PROJECT(D)                                                                                              \
     k_project<D><<<blocks, kProjThreads, 0, s>>>(n, g.means, g.log_scales, g.quats, g.opacity_logits, g.sh, g.rgb, \
-                                                 cam, W, H, tiles_x, tiles_y, mode, rec, depth, radius, rect,      \
+                                                 cam, W, H, tiles_x, tiles_y, ks, mode, rec, depth, radius, rect,  \
                                                  tiles_touched, supers_touched, depth_key, ids, totals, zl)
     switch (deg) {
     case 0: GS_PROJECT(0); break;
