@@ -64,7 +64,8 @@ def _args():
                     help="training pairs (480x270 with derivatives, 1920x1080 direct) of the learned residual")
     ap.add_argument("--mlp-steps", type=int, default=3000, help="Adam steps of the learned residual")
     ap.add_argument("--profile", default=None,
-                    choices=["main", "direct", "backward", "mlp", "mlp_train", "views", "bicubic", "upscale_bwd"],
+                    choices=["main", "main4", "direct", "backward", "mlp", "mlp_train", "views", "bicubic",
+                             "upscale_bwd"],
                     help="run only warm-up + steps of the 2x path (main) or of the direct 1920x1080 "
                          "render (direct) and print stage times; the case ncu captures use")
     return ap.parse_args()
@@ -1085,6 +1086,16 @@ def run_profile(args):
     def direct_step():
         ctx.render(dev, cam_hi, OUT_W, OUT_H, out_C=out)
 
+    # the 4x path: 480x270 render with derivatives, 4x upscale to 1920x1080
+    cam4 = scenes.pinhole_camera(OUT_W // 4, OUT_H // 4)
+    C4 = torch.empty(3, OUT_H // 4, OUT_W // 4, device="cuda")
+    G4 = torch.empty(3, 3, OUT_H // 4, OUT_W // 4, device="cuda")
+
+    def main4_step():
+        ctx.project(dev, cam4, OUT_W // 4, OUT_H // 4)
+        ctx.render_binned(grads=True, out_C=C4, out_grads=G4)
+        ctx.upscale(C4, G4, 4, out=out)
+
     dout = None
     grads = None
 
@@ -1129,7 +1140,7 @@ def run_profile(args):
     def upscale_bwd_step():
         ctx.upscale_backward(up_dout, LOW_W, LOW_H, FACTOR, out=up_grads)
 
-    fn = {"main": main_step, "direct": direct_step, "backward": backward_step, "mlp": mlp_step,
+    fn = {"main": main_step, "main4": main4_step, "direct": direct_step, "backward": backward_step, "mlp": mlp_step,
           "mlp_train": mlp_train_step, "views": views_step, "bicubic": bicubic_step,
           "upscale_bwd": upscale_bwd_step}[args.profile]
     if args.profile == "mlp_train":
