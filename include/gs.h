@@ -158,42 +158,60 @@ gs_status gs_set_options(gs_ctx* ctx, const gs_options* opt);
  * Synchronises the stream.  W x H <= 4096 super-tiles (e.g. 4096 x 4096). */
 gs_status gs_reserve(gs_ctx* ctx, int64_t n, int32_t W, int32_t H, int64_t super_pairs);
 
-/* gs_reserve plus the per-view buffers of gs_render_views for up to V views
- * (super_pairs is then the capacity of each view's pair buffers)
- * (1 <= V <= 32) of up to n Gaussians; W, H, super_pairs bound every view. */
+/* gs_reserve plus the per-view buffers of gs_render_views and
+ * gs_render_views_scenes for up to V views (1 <= V <= 32), each of up to n
+ * Gaussians (for a batch over several Gaussian sets: the largest set); W, H
+ * and super_pairs (the capacity of each view's pair buffers) bound every
+ * view. */
 gs_status gs_reserve_views(gs_ctx* ctx, int64_t n, int32_t V, int32_t W, int32_t H, int64_t super_pairs);
 
 /* Several views of one Gaussian set in one batch (e.g. the stereo pairs of a
- * VR headset, which the paper names as a use of cheap upscaling): one launch
- * projects every view (each Gaussian's inputs, SH coefficients included, are
- * read once for all views), one sort puts every view's Gaussians in depth
- * order (the view as the top digit), each view is binned into buffers of its
- * own; one launch blends every tile of every view with
- * derivatives into out_C[v] [3][H_v][W_v] and out_grads[v] [3][3][H_v][W_v]
- * (launch shape from gs_views_config / gs_autotune_views), and one launch
- * upscales, where out_up != NULL and out_up[v] != NULL, by factors[v] into
- * out_up[v].  View v uses cams[v], Ws[v] x Hs[v]; each view
- * equals a single-view gs_render_with_grads of the same camera bit for bit.
- * Requires GS_FLAG_NO_HOST_WAIT and gs_reserve_views; makes no host-blocking
- * call (capturable in a CUDA graph); a view beyond the reserved pairs renders
- * as background with GS_ERR_CAPACITY at the next gs_synchronize.  Host arrays
- * of V entries (cams, Ws, Hs, factors) and of V device pointers (out_C,
- * out_grads, out_up).  The context's single-view results (gs_render_binned,
- * gs_read_*, gs_backward) are invalid afterwards. */
+ * VR headset, which the paper names as a use of cheap upscaling; Sec. 1):
+ * one launch projects every view (each Gaussian's inputs, SH coefficients
+ * included, are read once for all views), one sort puts every view's
+ * Gaussians in depth order (the view as the top digit), one launch emits
+ * every view's pairs into buffers of its own, one launch per pass sorts every
+ * view's pairs; one launch blends every tile of every view with derivatives
+ * into out_C[v] [3][H_v][W_v] and out_grads[v] [3][3][H_v][W_v] (launch shape
+ * from gs_views_config / gs_autotune_views), and one launch upscales, where
+ * out_up != NULL and out_up[v] != NULL, by factors[v] into out_up[v].  View v
+ * uses cams[v], Ws[v] x Hs[v]; each view equals a single-view
+ * gs_render_with_grads of the same camera bit for bit.  Requires
+ * GS_FLAG_NO_HOST_WAIT and gs_reserve_views; makes no host-blocking call
+ * (capturable in a CUDA graph); a view beyond the reserved pairs renders as
+ * background with GS_ERR_CAPACITY at the next gs_synchronize (gs_pair_count /
+ * gs_super_pair_count then give the batch's sums).  Host arrays of V entries
+ * (cams, Ws, Hs, factors) and of V device pointers (out_C, out_grads,
+ * out_up).  The context's single-view results (gs_render_binned, gs_read_*,
+ * gs_backward) are invalid afterwards. */
 gs_status gs_render_views(gs_ctx* ctx, const gs_gaussians* g, int32_t V, const gs_camera* cams, const int32_t* Ws,
                           const int32_t* Hs, float* const* out_C, float* const* out_grads, const int32_t* factors,
                           float* const* out_up);
 
-/* Tuning of gs_render_views (the launch shapes of its batched blend; the
- * images do not depend on them, bit for bit).  warp_map: the pixels of each
- * warp of a 16 x 16 tile, 0 = an 8 x 4 block, 1 = a 16 x 2 strip.  schedule:
- * 0 = one block per tile in tile order, 1 = one block per tile, the heaviest
- * tiles of the previous batch first, 2 = resident blocks taking tiles from a
- * counter, 3 = one block per tile, the views in order and each view's heaviest
- * tiles of the previous batch first (each view's Gaussian records stay in L2
- * while its tiles run).  Default (0, 1). */
-#define GS_VIEWS_CONFIGS 8   /* configuration k: warp_map = k % 2, schedule = k / 2 */
-gs_status gs_views_config(gs_ctx* ctx, int32_t warp_map, int32_t schedule);
+/* gs_render_views over several Gaussian sets of uneven size in one batch
+ * (e.g. views of different scenes, or of one scene at several levels of
+ * detail): scenes is a host array of S (1 <= S <= 32) sets, view v renders
+ * scenes[scene_of_view[v]] (host int32[V], each in 0..S-1).  One projection
+ * launch per set (over the views that use it); everything after it runs as in
+ * gs_render_views, and each view equals a single-view gs_render_with_grads of
+ * its set bit for bit.  Every set must fit the reservation's n. */
+gs_status gs_render_views_scenes(gs_ctx* ctx, const gs_gaussians* scenes, int32_t S, const int32_t* scene_of_view,
+                                 int32_t V, const gs_camera* cams, const int32_t* Ws, const int32_t* Hs,
+                                 float* const* out_C, float* const* out_grads, const int32_t* factors,
+                                 float* const* out_up);
+
+/* Tuning of the batched views (the binning and launch shapes; the images do
+ * not depend on them, bit for bit).  warp_map: the pixels of each warp of a
+ * 16 x 16 tile, 0 = an 8 x 4 block, 1 = a 16 x 2 strip.  schedule: 0 = one
+ * block per tile in tile order, 1 = one block per tile, the heaviest tiles of
+ * the previous batch first, 2 = resident blocks taking tiles from a counter,
+ * 3 = one block per tile, the views in order and each view's heaviest tiles of
+ * the previous batch first (each view's Gaussian records stay in L2 while its
+ * tiles run).  super_side: the super-tile side of every view's binning, 0 = per
+ * view by the single-frame rule (gs_super_pair_count), 4 = 4 x 4 tiles
+ * (fewer pairs, longer lists per blend block).  Default (0, 1, 0). */
+#define GS_VIEWS_CONFIGS 16   /* configuration k: warp_map = k % 2, schedule = (k / 2) % 4, super_side = 4 if k >= 8 */
+gs_status gs_views_config(gs_ctx* ctx, int32_t warp_map, int32_t schedule, int32_t super_side);
 
 /* Autotuner: renders the batch of gs_render_views (same arguments) once
  * untimed and `reps` times timed (CUDA events on the context's stream) in each
@@ -204,6 +222,12 @@ gs_status gs_views_config(gs_ctx* ctx, int32_t warp_map, int32_t schedule);
 gs_status gs_autotune_views(gs_ctx* ctx, const gs_gaussians* g, int32_t V, const gs_camera* cams, const int32_t* Ws,
                             const int32_t* Hs, float* const* out_C, float* const* out_grads, const int32_t* factors,
                             float* const* out_up, int32_t reps, float* ms, int32_t* best);
+
+/* The autotuner on a gs_render_views_scenes batch (same arguments). */
+gs_status gs_autotune_views_scenes(gs_ctx* ctx, const gs_gaussians* scenes, int32_t S, const int32_t* scene_of_view,
+                                   int32_t V, const gs_camera* cams, const int32_t* Ws, const int32_t* Hs,
+                                   float* const* out_C, float* const* out_grads, const int32_t* factors,
+                                   float* const* out_up, int32_t reps, float* ms, int32_t* best);
 
 /* Projection and tile binning for a W x H image (Sec. 4: EWA projection
  * Sigma' = J W Sigma W^T J^T + 0.3 I, front-to-back order).  Per Gaussian: view

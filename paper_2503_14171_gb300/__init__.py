@@ -35,7 +35,7 @@ GS_FLAG_NO_HOST_WAIT = 1
 GS_INJECT_NONE = 0
 GS_INJECT_WAIT_EXPIRY = 1
 GS_INJECT_ALLOC_FAILURE = 2
-GS_VIEWS_CONFIGS = 8
+GS_VIEWS_CONFIGS = 16
 GS_MLP_IN = 50
 GS_MLP_HIDDEN = 64
 GS_MLP_PARAMS = 7619
@@ -77,7 +77,14 @@ _SIGS = {
     "gs_render_views": ([_P, ct.POINTER(GsGaussians), ct.c_int32, ct.POINTER(GsCamera), ct.POINTER(ct.c_int32),
                          ct.POINTER(ct.c_int32), ct.POINTER(_P), ct.POINTER(_P), ct.POINTER(ct.c_int32),
                          ct.POINTER(_P)], ct.c_int),
-    "gs_views_config": ([_P, ct.c_int32, ct.c_int32], ct.c_int),
+    "gs_render_views_scenes": ([_P, ct.POINTER(GsGaussians), ct.c_int32, ct.POINTER(ct.c_int32), ct.c_int32,
+                                ct.POINTER(GsCamera), ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32), ct.POINTER(_P),
+                                ct.POINTER(_P), ct.POINTER(ct.c_int32), ct.POINTER(_P)], ct.c_int),
+    "gs_views_config": ([_P, ct.c_int32, ct.c_int32, ct.c_int32], ct.c_int),
+    "gs_autotune_views_scenes": ([_P, ct.POINTER(GsGaussians), ct.c_int32, ct.POINTER(ct.c_int32), ct.c_int32,
+                                  ct.POINTER(GsCamera), ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32),
+                                  ct.POINTER(_P), ct.POINTER(_P), ct.POINTER(ct.c_int32), ct.POINTER(_P), ct.c_int32,
+                                  ct.POINTER(ct.c_float), ct.POINTER(ct.c_int32)], ct.c_int),
     "gs_autotune_views": ([_P, ct.POINTER(GsGaussians), ct.c_int32, ct.POINTER(GsCamera), ct.POINTER(ct.c_int32),
                            ct.POINTER(ct.c_int32), ct.POINTER(_P), ct.POINTER(_P), ct.POINTER(ct.c_int32),
                            ct.POINTER(_P), ct.c_int32, ct.POINTER(ct.c_float), ct.POINTER(ct.c_int32)], ct.c_int),
@@ -332,21 +339,43 @@ class Context:
         _chk(lib.gs_reserve_views(self.h, int(n), int(V), int(W), int(H), int(super_pairs)), self.h,
              "gs_reserve_views")
 
-    def render_views(self, scene: DeviceScene, cams: list, sizes: list, factors=None, outs=None):
-        """Render len(cams) views (sizes: [(W, H)]) with derivatives in one batch;
-        with factors, also upscale view v by factors[v].  Returns a list of
-        (C, G) or (C, G, up) per view."""
-        V = len(cams)
-        if outs is None:
-            outs = []
-            for v, (W, H) in enumerate(sizes):
-                o = [self._empty(3, H, W), self._empty(3, 3, H, W)]
-                if factors is not None:
-                    o.append(self._empty(3, H * factors[v], W * factors[v]))
-                outs.append(o)
-        _chk(lib.gs_render_views(self.h, ct.byref(scene.struct), V, *self._views_args(cams, sizes, factors, outs)),
-             self.h, "gs_render_views")
+    def _views_outs(self, sizes, factors, outs):
+        if outs is not None:
+            return outs
+        outs = []
+        for v, (W, H) in enumerate(sizes):
+            o = [self._empty(3, H, W), self._empty(3, 3, H, W)]
+            if factors is not None:
+                o.append(self._empty(3, H * factors[v], W * factors[v]))
+            outs.append(o)
         return outs
+
+    def render_views(self, scene, cams: list, sizes: list, factors=None, outs=None, scene_of_view=None):
+        """Render len(cams) views (sizes: [(W, H)]) with derivatives in one batch;
+        with factors, also upscale view v by factors[v].  scene is one
+        DeviceScene (gs_render_views), or a list of them with scene_of_view[v]
+        naming view v's (gs_render_views_scenes).  Returns a list of (C, G) or
+        (C, G, up) per view."""
+        V = len(cams)
+        outs = self._views_outs(sizes, factors, outs)
+        if isinstance(scene, (list, tuple)):
+            sets, sov = self._scenes_args(scene, scene_of_view, V)
+            _chk(lib.gs_render_views_scenes(self.h, sets, len(scene), sov, V,
+                                            *self._views_args(cams, sizes, factors, outs)),
+                 self.h, "gs_render_views_scenes")
+        else:
+            _chk(lib.gs_render_views(self.h, ct.byref(scene.struct), V,
+                                     *self._views_args(cams, sizes, factors, outs)),
+                 self.h, "gs_render_views")
+        return outs
+
+    @staticmethod
+    def _scenes_args(scenes, scene_of_view, V):
+        if scene_of_view is None or len(scene_of_view) != V:
+            raise ValueError("a list of scenes needs scene_of_view with one entry per view")
+        sets = (GsGaussians * len(scenes))(*[s.struct for s in scenes])
+        sov = (ct.c_int32 * V)(*[int(k) for k in scene_of_view])
+        return sets, sov
 
     @staticmethod
     def _views_args(cams, sizes, factors, outs):
@@ -360,18 +389,27 @@ class Context:
         pU = (_P * V)(*[o[2].data_ptr() for o in outs]) if factors is not None else None
         return cam_arr, Ws, Hs, pC, pG, fac, pU
 
-    def views_config(self, warp_map: int, schedule: int):
-        """Launch shape of the batched blend of render_views (see gs_views_config)."""
-        _chk(lib.gs_views_config(self.h, int(warp_map), int(schedule)), self.h, "gs_views_config")
+    def views_config(self, warp_map: int, schedule: int, super_side: int = 0):
+        """Binning and launch shape of render_views batches (see gs_views_config)."""
+        _chk(lib.gs_views_config(self.h, int(warp_map), int(schedule), int(super_side)), self.h, "gs_views_config")
 
-    def autotune_views(self, scene: DeviceScene, cams: list, sizes: list, factors, outs, reps: int = 5):
-        """Time every launch shape of the batched blend on this batch, keep the
-        fastest; returns (ms per configuration, chosen configuration)."""
+    def autotune_views(self, scene, cams: list, sizes: list, factors, outs, reps: int = 5, scene_of_view=None):
+        """Time every binning and launch shape of the batched views on this
+        batch, keep the fastest; returns (ms per configuration, chosen
+        configuration).  scene as for render_views."""
         ms = (ct.c_float * GS_VIEWS_CONFIGS)()
         best = ct.c_int32()
-        _chk(lib.gs_autotune_views(self.h, ct.byref(scene.struct), len(cams),
-                                   *self._views_args(cams, sizes, factors, outs), int(reps), ms, ct.byref(best)),
-             self.h, "gs_autotune_views")
+        V = len(cams)
+        if isinstance(scene, (list, tuple)):
+            sets, sov = self._scenes_args(scene, scene_of_view, V)
+            _chk(lib.gs_autotune_views_scenes(self.h, sets, len(scene), sov, V,
+                                              *self._views_args(cams, sizes, factors, outs), int(reps), ms,
+                                              ct.byref(best)),
+                 self.h, "gs_autotune_views_scenes")
+        else:
+            _chk(lib.gs_autotune_views(self.h, ct.byref(scene.struct), V,
+                                       *self._views_args(cams, sizes, factors, outs), int(reps), ms, ct.byref(best)),
+                 self.h, "gs_autotune_views")
         return list(ms), int(best.value)
 
     def set_options(self, mode=None, bg=None, max_pairs=None):

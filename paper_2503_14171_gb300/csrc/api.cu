@@ -198,6 +198,7 @@ gs_status do_project(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, int
     c->have_proj = false;
     c->have_state = false;
     c->order_ready = false;
+    c->batch_views = 0;
     const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
     const int ks = super_side(tiles_x, tiles_y, c->opt.mode);
     const int stiles_x = (tiles_x + ks - 1) / ks, stiles_y = (tiles_y + ks - 1) / ks;
@@ -537,7 +538,7 @@ gs_status gs_destroy(gs_ctx* c)
                       &c->errword, &c->grad2d, &c->pair_check, &c->tile_work, &c->tile_order,
                       &c->vrec0, &c->vrec1, &c->vrec2, &c->vrect, &c->vsupers, &c->vkey, &c->vtotals,
                       &c->views_dev, &c->vpairs0, &c->vpairs1, &c->vsranges, &c->vwork, &c->vorder, &c->vqueue,
-                      &c->vsortv};
+                      &c->vsortv, &c->vcounts, &c->vhist, &c->vstatus};
     for (DevBuf* b : bufs) release(*b);
     if (c->h_scalar) cudaFreeHost(c->h_scalar);
     if (c->totals_ready) cudaEventDestroy(c->totals_ready);
@@ -563,6 +564,7 @@ gs_status gs_set_options(gs_ctx* c, const gs_options* opt)
     c->have_proj = false;
     c->have_state = false;
     c->order_ready = false;
+    c->batch_views = 0;
     return GS_OK;
 }
 
@@ -826,11 +828,15 @@ namespace {
 gs_status known_totals(gs_ctx* c)
 {
     if (c->totals_known) return GS_OK;
-    PairCheckOut o{};
-    GS_CUDA(c, cudaMemcpyAsync(&o, c->pair_check.p, sizeof(o), cudaMemcpyDeviceToHost, c->stream));
+    PairCheckOut o[kMaxViews] = {};
+    const int k = c->batch_views > 0 ? c->batch_views : 1;   // after a batch: the sums over its views
+    GS_CUDA(c, cudaMemcpyAsync(o, c->pair_check.p, sizeof(PairCheckOut) * k, cudaMemcpyDeviceToHost, c->stream));
     GS_CUDA(c, cudaStreamSynchronize(c->stream));
-    c->P = (int64_t)o.tile_pairs;
-    c->Ps = (int64_t)o.needed;
+    c->P = c->Ps = 0;
+    for (int v = 0; v < k; ++v) {
+        c->P += (int64_t)o[v].tile_pairs;
+        c->Ps += (int64_t)o[v].needed;
+    }
     c->totals_known = true;
     return GS_OK;
 }
@@ -840,7 +846,7 @@ gs_status known_totals(gs_ctx* c)
 gs_status gs_pair_count(gs_ctx* c, int64_t* P)
 {
     if (!c || !P) return GS_ERR_INVALID_ARG;
-    if (!c->have_proj) return GS_ERR_NOT_READY;
+    if (!c->have_proj && c->batch_views == 0) return GS_ERR_NOT_READY;
     gs_status st = known_totals(c);
     if (st != GS_OK) return st;
     *P = c->P;
@@ -850,7 +856,7 @@ gs_status gs_pair_count(gs_ctx* c, int64_t* P)
 gs_status gs_super_pair_count(gs_ctx* c, int64_t* Ps)
 {
     if (!c || !Ps) return GS_ERR_INVALID_ARG;
-    if (!c->have_proj) return GS_ERR_NOT_READY;
+    if (!c->have_proj && c->batch_views == 0) return GS_ERR_NOT_READY;
     gs_status st = known_totals(c);
     if (st != GS_OK) return st;
     *Ps = c->Ps;
@@ -930,8 +936,14 @@ gs_status reserve_impl(gs_ctx* c, int64_t n, int32_t V, int32_t W, int32_t H, in
             (st = ensure(c, c->vsranges, sizeof(uint2) * (size_t)Ts * V)) ||
             (st = ensure(c, c->vwork, sizeof(uint32_t) * (size_t)T * V)) ||
             (st = ensure(c, c->vorder, sizeof(uint32_t) * (size_t)T * V)) ||
-            (st = ensure(c, c->vqueue, sizeof(uint32_t))))
+            (st = ensure(c, c->vqueue, sizeof(uint32_t))) ||
+            (st = ensure(c, c->vcounts, sizeof(uint32_t) * kCountCopies * (size_t)Ts * V)) ||
+            (st = ensure(c, c->vhist, sizeof(uint32_t) * 8 * 256 * (size_t)V)) ||
+            (st = ensure(c, c->vstatus, sizeof(uint32_t) *
+                                            (radix_status_words((uint32_t)super_pairs, 32, 32 + sbits) + 8) * V)) ||
+            (st = ensure(c, c->pair_check, sizeof(PairCheckOut) * (size_t)V)))
             return st;
+        c->vstatus_stride = radix_status_words((uint32_t)super_pairs, 32, 32 + sbits) + 8;
         GS_CUDA(c, cudaMemsetAsync(c->vwork.p, 0, sizeof(uint32_t) * (size_t)T * V, c->stream));
     }
     GS_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -960,28 +972,53 @@ gs_status gs_reserve_views(gs_ctx* c, int64_t n, int32_t V, int32_t W, int32_t H
     return reserve_impl(c, n, V, W, H, super_pairs);
 }
 
-gs_status gs_render_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_camera* cams, const int32_t* Ws,
-                          const int32_t* Hs, float* const* out_C, float* const* out_grads, const int32_t* factors,
-                          float* const* out_up)
+namespace {
+
+// A batch of views over one or several Gaussian sets (gs_render_views,
+// gs_render_views_scenes).  Launches: per Gaussian set one projection of all
+// its views; one stable sort of every (view, depth) key of the batch; one
+// pair-offset scan; one emission; one histogram launch; one launch per pass
+// of the pair sort over every view's pairs; one blend of every tile of every
+// view; one upscale of every view.  No host wait.
+gs_status render_views_impl(gs_ctx* c, const gs_gaussians* scenes, int32_t S, const int32_t* scene_of_view, int32_t V,
+                            const gs_camera* cams, const int32_t* Ws, const int32_t* Hs, float* const* out_C,
+                            float* const* out_grads, const int32_t* factors, float* const* out_up)
 {
-    if (!c) return GS_ERR_INVALID_ARG;
-    LaunchTally tally(c);
     if (!(c->opt.flags & GS_FLAG_NO_HOST_WAIT) || !c->reserved || c->res_views < 1)
-        return fail(c, GS_ERR_NOT_READY, "gs_render_views needs GS_FLAG_NO_HOST_WAIT and gs_reserve_views");
+        return fail(c, GS_ERR_NOT_READY, "batched views need GS_FLAG_NO_HOST_WAIT and gs_reserve_views");
     if (V < 1 || V > c->res_views) return fail(c, GS_ERR_CAPACITY, "%d views, %d reserved", V, c->res_views);
+    if (!scenes || S < 1 || S > kMaxViews) return fail(c, GS_ERR_INVALID_ARG, "1 <= S <= %d Gaussian sets", kMaxViews);
     if (!cams || !Ws || !Hs || !out_C || !out_grads) return fail(c, GS_ERR_INVALID_ARG, "NULL argument");
-    gs_status st = check_gaussians(c, g);
-    if (st != GS_OK) return st;
-    const uint32_t n = (uint32_t)g->n;
-    if ((int64_t)n > c->res_n) return fail(c, GS_ERR_CAPACITY, "n %u exceeds the reserved %lld", n, (long long)c->res_n);
+    gs_status st;
+    for (int k = 0; k < S; ++k) {
+        if ((st = check_gaussians(c, &scenes[k])) != GS_OK) return st;
+        if (scenes[k].n > c->res_n)
+            return fail(c, GS_ERR_CAPACITY, "Gaussian set %d: n %lld exceeds the reserved %lld", k,
+                        (long long)scenes[k].n, (long long)c->res_n);
+    }
+    // views grouped by Gaussian set (each set's views contiguous, in view order)
     ViewBatch batch{};
+    int order[kMaxViews];
+    int set_first[kMaxViews + 1];
+    uint32_t nview[kMaxViews];
+    uint64_t total64 = 0;
+    {
+        int q = 0;
+        for (int k = 0; k < S; ++k) {
+            set_first[k] = q;
+            for (int v = 0; v < V; ++v)
+                if ((scene_of_view ? scene_of_view[v] : 0) == k) order[q++] = v;
+        }
+        set_first[S] = q;
+        if (q != V) return fail(c, GS_ERR_INVALID_ARG, "a view's Gaussian set index is outside 0..%d", S - 1);
+    }
     for (int v = 0; v < V; ++v) {
         const int W = Ws[v], H = Hs[v];
         if (W < 1 || H < 1 || !(cams[v].fx > 0.f) || !(cams[v].fy > 0.f) || !out_C[v] || !out_grads[v])
             return fail(c, GS_ERR_INVALID_ARG, "bad view %d", v);
         const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
         const int64_t T = (int64_t)tiles_x * tiles_y;
-        const int ks = super_side(tiles_x, tiles_y, c->opt.mode);
+        const int ks = c->views_ks ? c->views_ks : super_side(tiles_x, tiles_y, c->opt.mode);
         const int64_t Ts = (int64_t)((tiles_x + ks - 1) / ks) * ((tiles_y + ks - 1) / ks);
         if (T > c->res_tiles || Ts > c->res_supers || (int64_t)W * H > c->res_pixels)
             return fail(c, GS_ERR_CAPACITY, "view %d (%d x %d) exceeds the reserved sizes", v, W, H);
@@ -989,108 +1026,128 @@ gs_status gs_render_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_
             const int f = factors ? factors[v] : 0;
             if (f < 1 || f > 16 || W < 2 || H < 2) return fail(c, GS_ERR_INVALID_ARG, "bad upscale of view %d", v);
         }
-        batch.v[v].cam = make_camera(cams[v], W, H);
-        batch.v[v].W = W;
-        batch.v[v].H = H;
-        batch.v[v].tiles_x = tiles_x;
-        batch.v[v].tiles_y = tiles_y;
-        batch.v[v].ks = ks;
+        nview[v] = (uint32_t)scenes[scene_of_view ? scene_of_view[v] : 0].n;
+    }
+    // the view's entries in the batch arrays, in view order
+    uint32_t start[kMaxViews + 1];
+    for (int v = 0; v < V; ++v) {
+        start[v] = (uint32_t)total64;
+        total64 += nview[v];
+    }
+    start[V] = (uint32_t)total64;
+    if (total64 > (uint64_t)c->res_n * (uint64_t)c->res_views || total64 >= 0xFFFFFFFFull)
+        return fail(c, GS_ERR_CAPACITY, "the batch's %llu (view, Gaussian) entries exceed the reservation",
+                    (unsigned long long)total64);
+    const uint32_t total = (uint32_t)total64;
+    for (int q = 0; q < V; ++q) {   // descriptions grouped by Gaussian set
+        const int v = order[q];
+        ViewDesc& d = batch.v[q];
+        d.cam = make_camera(cams[v], Ws[v], Hs[v]);
+        d.W = Ws[v];
+        d.H = Hs[v];
+        d.tiles_x = (Ws[v] + kTile - 1) / kTile;
+        d.tiles_y = (Hs[v] + kTile - 1) / kTile;
+        d.ks = c->views_ks ? c->views_ks : super_side(d.tiles_x, d.tiles_y, c->opt.mode);
+        d.off = start[v];
+        d.vid = v;
     }
     c->have_proj = false;
     c->have_state = false;
     c->order_ready = false;
     cudaStream_t s = c->stream;
-    // all views projected in one launch
     unsigned long long* vtot = as<unsigned long long>(c->vtotals);
     GS_CUDA(c, cudaMemsetAsync(vtot, 0, sizeof(unsigned long long) * 2 * kTotalSlots * V, s));
     GS_CUDA(c, launch_set_views(s, batch, V, as<ViewDesc>(c->views_dev)));
+    // the batched depth sort's keys go to the pair buffers (free until the
+    // views' pairs are emitted), its values to vkey and vsortv
+    uint64_t* k64[2] = {as<uint64_t>(c->vpairs0), as<uint64_t>(c->vpairs1)};
+    uint32_t* v32[2] = {as<uint32_t>(c->vkey), as<uint32_t>(c->vsortv)};
     ViewOutputs vo;
     vo.rec = Records{as<float4>(c->vrec0), as<float4>(c->vrec1), as<float4>(c->vrec2)};
     vo.rect = as<ushort4>(c->vrect);
     vo.supers = as<uint32_t>(c->vsupers);
-    vo.depth_key = as<uint32_t>(c->vkey);
+    vo.key64 = k64[0];
+    vo.gidx = v32[0];
     vo.totals = vtot;
-    GS_CUDA(c, launch_project_views(s, *g, as<ViewDesc>(c->views_dev), V, c->opt.mode, vo));
-
-    // then each view: depth order, emission, pair check and sort into its own
-    // pair and range buffers; then the blends of all views in one launch and
-    // the upscales of all views in one launch
-    const uint32_t ds_cap = n > 1 ? depth_sort_capacity(c->device) : 0u;
-    const bool persistent = n > 1 && n <= ds_cap && n <= kDsMaxN;
-    const size_t G = ds_cap / kDsMaxSlice;
-    const uint32_t cap = (uint32_t)c->res_pairs;
-    // Several views (or views beyond the persistent sort's capacity): the depth
-    // keys of every view sorted together, the view as the top digit, so that
-    // each view's Gaussians come out contiguous and in their own depth order
-    // (the sort is stable and starts in id order), then one pair-offset scan
-    // over the whole order.  A single view within capacity keeps the
-    // persistent sort.
-    const bool batched = V > 1 || !persistent;
-    const uint32_t* vsorted = nullptr;   // v n + i in (view, depth, id) order
-    if (batched) {
-        const uint32_t total = (uint32_t)((uint64_t)V * n);
-        uint64_t* k64[2] = {as<uint64_t>(c->vpairs0), as<uint64_t>(c->vpairs1)};
-        uint32_t* v32[2] = {as<uint32_t>(c->vkey), as<uint32_t>(c->vsortv)};
-        GS_CUDA(c, launch_view_keys(s, as<uint32_t>(c->vkey), n, total, k64[0], v32[0]));
-        int vs = 0;
-        if (total > 1)
-            GS_CUDA(c, radix_sort_u64_pairs(s, k64, v32, total, 0, 32 + bits_for((uint32_t)V),
-                                            as<uint32_t>(c->sort_hist), as<uint32_t>(c->sort_status),
-                                            as<uint32_t>(c->sort_counter), as<int>(c->errword), &vs));
-        vsorted = v32[vs];
-        unsigned long long* scan_tot = as<unsigned long long>(c->scan_totals) + 2 * kTotalSlots;
-        GS_CUDA(c, launch_scan_gathered(s, as<uint32_t>(c->vsupers), nullptr, vsorted, total, as<uint32_t>(c->offsets),
-                                        as<unsigned long long>(c->scan_partials),
-                                        reinterpret_cast<uint32_t*>(scan_tot + 2), scan_tot, as<int>(c->errword)));
+    for (int k = 0; k < S; ++k) {   // one projection launch per Gaussian set, over its views
+        const int nv = set_first[k + 1] - set_first[k];
+        if (nv > 0)
+            GS_CUDA(c, launch_project_views(s, scenes[k], as<ViewDesc>(c->views_dev) + set_first[k], nv, c->opt.mode,
+                                            vo));
     }
+    // every view's Gaussians in its own depth order, contiguous per view (the
+    // view is the top digit of the stable sort, which starts in id order),
+    // then the super-tile pair offsets over the whole order
+    int vs = 0;
+    if (total > 1)
+        GS_CUDA(c, radix_sort_u64_pairs(s, k64, v32, total, 0, 32 + bits_for((uint32_t)V), as<uint32_t>(c->sort_hist),
+                                        as<uint32_t>(c->sort_status), as<uint32_t>(c->sort_counter),
+                                        as<int>(c->errword), &vs));
+    const uint32_t* vsorted = v32[vs];
+    unsigned long long* scan_tot = as<unsigned long long>(c->scan_totals) + 2 * kTotalSlots;
+    GS_CUDA(c, launch_scan_gathered(s, as<uint32_t>(c->vsupers), nullptr, vsorted, total, as<uint32_t>(c->offsets),
+                                    as<unsigned long long>(c->scan_partials), reinterpret_cast<uint32_t*>(scan_tot + 2),
+                                    scan_tot, as<int>(c->errword)));
+
+    // per view: its pair buffers, counts, histograms, sort state and ranges
     const int64_t limit = c->opt.max_pairs > 0 ? std::min<int64_t>(c->opt.max_pairs, kMaxPairs) : kMaxPairs;
+    const uint32_t cap = (uint32_t)c->res_pairs;
+    const size_t counts_stride = (size_t)kCountCopies * c->res_supers;
+    const size_t status_stride = c->vstatus_stride;
     PairCheckOut* chk = as<PairCheckOut>(c->pair_check);
+    EmitViews ev{};
+    HistViews hv{};
+    SortSegs sg{};
     BlendViews bv;
     bv.V = V;
     bv.start[0] = 0;
     UpscaleViews uv;
     uv.V = 0;
     uv.start[0] = 0;
+    ev.V = hv.V = sg.count = V;
+    GS_CUDA(c, cudaMemsetAsync(c->vcounts.p, 0, sizeof(uint32_t) * counts_stride * V, s));
+    GS_CUDA(c, cudaMemsetAsync(c->vstatus.p, 0, sizeof(uint32_t) * status_stride * V, s));
     for (int v = 0; v < V; ++v) {
-        const ViewDesc& d = batch.v[v];
+        const int q = [&] { for (int i = 0; i < V; ++i) if (order[i] == v) return i; return 0; }();
+        const ViewDesc& d = batch.v[q];
         const int stiles_x = (d.tiles_x + d.ks - 1) / d.ks, stiles_y = (d.tiles_y + d.ks - 1) / d.ks;
         const uint32_t Ts = (uint32_t)(stiles_x * stiles_y);
         const int sbits = bits_for(Ts);
-        const int spasses = radix_passes(32, 32 + sbits);
-        const size_t off = (size_t)v * n;
-        uint32_t* keys_v = as<uint32_t>(c->vkey) + off;
-        uint32_t* supers_v = as<uint32_t>(c->vsupers) + off;
-        const ushort4* rect_v = as<ushort4>(c->vrect) + off;
+        const int spasses = Ts > 1 ? radix_passes(32, 32 + sbits) : 0;
         uint64_t* pairs[2] = {as<uint64_t>(c->vpairs0) + (size_t)v * cap, as<uint64_t>(c->vpairs1) + (size_t)v * cap};
+        uint32_t* counts_v = as<uint32_t>(c->vcounts) + (size_t)v * counts_stride;
+        uint32_t* hist_v = as<uint32_t>(c->vhist) + (size_t)v * 8 * 256;
+        uint32_t* status_v = as<uint32_t>(c->vstatus) + (size_t)v * status_stride;
         uint2* sranges_v = as<uint2>(c->vsranges) + (size_t)v * c->res_supers;
-        uint32_t* keys[2] = {as<uint32_t>(c->dkey[0]), as<uint32_t>(c->dkey[1])};
-        uint32_t* ids[2] = {as<uint32_t>(c->did[0]), as<uint32_t>(c->did[1])};
-        GS_CUDA(c, cudaMemsetAsync(c->super_counts.p, 0, sizeof(uint32_t) * kCountCopies * Ts, s));
-        if (batched) {   // this view's stretch of the batched order and offsets
-            GS_CUDA(c, launch_emit_pairs(s, vsorted + off, as<uint32_t>(c->offsets) + off, rect_v, n, d.ks, stiles_x,
-                                         pairs[0], as<uint32_t>(c->super_counts), Ts, cap, (uint32_t)off, true));
-        } else {
-            int sorted = 0;
-            unsigned char* base = as<unsigned char>(c->ds_scratch);
-            GS_CUDA(c, launch_depth_sort_scan(s, c->device, keys_v, keys, ids, supers_v, n, as<uint32_t>(c->offsets),
-                                              reinterpret_cast<uint32_t*>(base + ds_cnt_offset(G)),
-                                              reinterpret_cast<uint32_t*>(base + ds_csum_offset(G)),
-                                              reinterpret_cast<unsigned int*>(base + ds_bar_offset(G)),
-                                              reinterpret_cast<uint32_t*>(base + ds_tot_offset(G)),
-                                              as<int>(c->errword), &sorted, false));
-            GS_CUDA(c, launch_emit_pairs(s, ids[sorted], as<uint32_t>(c->offsets), rect_v, n, d.ks, stiles_x,
-                                         pairs[0], as<uint32_t>(c->super_counts), Ts, cap));
-        }
-        GS_CUDA(c, launch_supers_to_hist(s, as<uint32_t>(c->super_counts), Ts, spasses, as<uint32_t>(c->sort_hist),
-                                         sranges_v,
-                                         PairCheckIn{vtot + (size_t)v * 2 * kTotalSlots, cap,
-                                                     (unsigned long long)limit},
-                                         chk, as<int>(c->errword)));
-        int psorted = 0;
-        if (Ts > 1 && cap > 1)
-            GS_CUDA(c, radix_sort_u64_keys(s, pairs, cap, 32, 32 + sbits, as<uint32_t>(c->sort_hist),
-                                           as<uint32_t>(c->sort_status), as<uint32_t>(c->sort_counter),
-                                           as<int>(c->errword), &psorted, true, &chk->count, false));
+        EmitView& e = ev.v[v];
+        e.pairs = pairs[0];
+        e.counts = counts_v;
+        e.start = start[v];
+        e.n = nview[v];
+        e.cap = cap;
+        e.Ts = Ts;
+        e.ks = d.ks;
+        e.stiles_x = stiles_x;
+        HistView& h = hv.v[v];
+        h.counts = counts_v;
+        h.Ts = Ts;
+        h.passes = spasses;
+        h.hist = hist_v;
+        h.ranges = sranges_v;
+        h.in = PairCheckIn{vtot + (size_t)v * 2 * kTotalSlots, cap, (unsigned long long)limit};
+        h.out = chk + v;
+        SortSeg& g = sg.seg[v];
+        g.keys[0] = pairs[0];
+        g.keys[1] = pairs[1];
+        g.n_dev = &chk[v].count;
+        g.cap = cap;
+        g.tiles = radix_tiles(cap);
+        g.passes = spasses;
+        g.bit_lo = 32;
+        g.hist = hist_v;
+        g.status = status_v;
+        g.counters = status_v + status_stride - 8;   // the last 8 words of the view's (zeroed) state
+        g.err = as<int>(c->errword);
         BlendArgs& a = bv.a[v];
         a.W = d.W;
         a.H = d.H;
@@ -1098,11 +1155,12 @@ gs_status gs_render_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_
         a.tiles_y = d.tiles_y;
         a.stiles_x = stiles_x;
         a.ks = d.ks;
-        a.n = n;
+        a.n = nview[v];
         a.sranges = sranges_v;
-        a.pair_words = reinterpret_cast<const uint32_t*>(pairs[psorted]);
-        a.rect = rect_v;
-        a.rec = Records{as<float4>(c->vrec0) + off, as<float4>(c->vrec1) + off, as<float4>(c->vrec2) + off};
+        a.pair_words = reinterpret_cast<const uint32_t*>(pairs[spasses & 1]);
+        a.rect = as<ushort4>(c->vrect) + start[v];
+        a.rec = Records{as<float4>(c->vrec0) + start[v], as<float4>(c->vrec1) + start[v],
+                        as<float4>(c->vrec2) + start[v]};
         a.bg = make_float3(c->opt.bg[0], c->opt.bg[1], c->opt.bg[2]);
         a.out_C = out_C[v];
         a.out_G = out_grads[v];
@@ -1124,12 +1182,15 @@ gs_status gs_render_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_
             ++uv.V;
         }
     }
-    const int total = bv.start[V];
+    GS_CUDA(c, launch_emit_views(s, ev, vsorted, as<uint32_t>(c->offsets), as<ushort4>(c->vrect), total));
+    GS_CUDA(c, launch_supers_to_hist_views(s, hv, as<int>(c->errword)));
+    GS_CUDA(c, radix_sort_u64_segs(s, sg));
+    const int tiles_total = bv.start[V];
     bv.work = as<uint32_t>(c->vwork);
     bv.queue = as<uint32_t>(c->vqueue);
     bv.order = nullptr;
     if (c->views_sched == 1) {   // heaviest tiles of the last batch first
-        GS_CUDA(c, launch_tile_order(s, as<uint32_t>(c->vwork), (uint32_t)total, as<uint32_t>(c->vorder)));
+        GS_CUDA(c, launch_tile_order(s, as<uint32_t>(c->vwork), (uint32_t)tiles_total, as<uint32_t>(c->vorder)));
         bv.order = as<uint32_t>(c->vorder);
     } else if (c->views_sched == 3) {   // the views in order, each view's heaviest tiles first
         GS_CUDA(c, launch_tile_order_views(s, as<uint32_t>(c->vwork), bv.start, V, as<uint32_t>(c->vorder)));
@@ -1138,24 +1199,53 @@ gs_status gs_render_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_
     GS_CUDA(c, launch_blend_views(s, c->opt.mode, bv, c->views_map, c->views_sched == 2));
     if (uv.V > 0) GS_CUDA(c, launch_upscale_views(s, uv));
     c->totals_known = false;
+    c->batch_views = V;
     return GS_OK;
 }
 
-gs_status gs_views_config(gs_ctx* c, int32_t warp_map, int32_t schedule)
+}  // namespace
+
+gs_status gs_render_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_camera* cams, const int32_t* Ws,
+                          const int32_t* Hs, float* const* out_C, float* const* out_grads, const int32_t* factors,
+                          float* const* out_up)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    LaunchTally tally(c);
+    if (!g) return fail(c, GS_ERR_INVALID_ARG, "gaussians == NULL");
+    return render_views_impl(c, g, 1, nullptr, V, cams, Ws, Hs, out_C, out_grads, factors, out_up);
+}
+
+gs_status gs_render_views_scenes(gs_ctx* c, const gs_gaussians* scenes, int32_t S, const int32_t* scene_of_view,
+                                 int32_t V, const gs_camera* cams, const int32_t* Ws, const int32_t* Hs,
+                                 float* const* out_C, float* const* out_grads, const int32_t* factors,
+                                 float* const* out_up)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    LaunchTally tally(c);
+    if (!scene_of_view) return fail(c, GS_ERR_INVALID_ARG, "scene_of_view == NULL");
+    return render_views_impl(c, scenes, S, scene_of_view, V, cams, Ws, Hs, out_C, out_grads, factors, out_up);
+}
+
+gs_status gs_views_config(gs_ctx* c, int32_t warp_map, int32_t schedule, int32_t super_side_tiles)
 {
     if (!c) return GS_ERR_INVALID_ARG;
     if (warp_map < 0 || warp_map > 1 || schedule < 0 || schedule > 3)
         return fail(c, GS_ERR_INVALID_ARG, "warp_map in {0, 1}, schedule in {0, 1, 2, 3}");
+    if (super_side_tiles != 0 && super_side_tiles != kSuperMax)
+        return fail(c, GS_ERR_INVALID_ARG, "super-tile side 0 (per view) or %d", kSuperMax);
     c->views_map = warp_map;
     c->views_sched = schedule;
+    c->views_ks = super_side_tiles;
     return GS_OK;
 }
 
-gs_status gs_autotune_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_camera* cams, const int32_t* Ws,
-                            const int32_t* Hs, float* const* out_C, float* const* out_grads, const int32_t* factors,
-                            float* const* out_up, int32_t reps, float* ms, int32_t* best)
+namespace {
+
+gs_status autotune_impl(gs_ctx* c, const gs_gaussians* scenes, int32_t S, const int32_t* scene_of_view, int32_t V,
+                        const gs_camera* cams, const int32_t* Ws, const int32_t* Hs, float* const* out_C,
+                        float* const* out_grads, const int32_t* factors, float* const* out_up, int32_t reps,
+                        float* ms, int32_t* best)
 {
-    if (!c) return GS_ERR_INVALID_ARG;
     if (reps < 1) return fail(c, GS_ERR_INVALID_ARG, "reps must be >= 1");
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     GS_CUDA(c, cudaEventCreate(&e0));
@@ -1168,13 +1258,14 @@ gs_status gs_autotune_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const g
     gs_status st = GS_OK;
     for (int k = 0; k < GS_VIEWS_CONFIGS && st == GS_OK; ++k) {
         c->views_map = k & 1;
-        c->views_sched = k >> 1;
+        c->views_sched = (k >> 1) & 3;
+        c->views_ks = (k >> 3) ? kSuperMax : 0;
         // one untimed batch: first use of the variant, and tile durations for schedules 1 and 3
-        st = gs_render_views(c, g, V, cams, Ws, Hs, out_C, out_grads, factors, out_up);
+        st = render_views_impl(c, scenes, S, scene_of_view, V, cams, Ws, Hs, out_C, out_grads, factors, out_up);
         if (st != GS_OK) break;
         if (cudaEventRecord(e0, c->stream) != cudaSuccess) { st = fail(c, GS_ERR_CUDA, "event"); break; }
         for (int r = 0; r < reps && st == GS_OK; ++r)
-            st = gs_render_views(c, g, V, cams, Ws, Hs, out_C, out_grads, factors, out_up);
+            st = render_views_impl(c, scenes, S, scene_of_view, V, cams, Ws, Hs, out_C, out_grads, factors, out_up);
         if (st != GS_OK) break;
         float t = 0.f;
         if (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
@@ -1193,9 +1284,32 @@ gs_status gs_autotune_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const g
     cudaEventDestroy(e1);
     if (st != GS_OK) return st;
     c->views_map = best_k & 1;
-    c->views_sched = best_k >> 1;
+    c->views_sched = (best_k >> 1) & 3;
+    c->views_ks = (best_k >> 3) ? kSuperMax : 0;
     if (best) *best = best_k;
     return read_device_error(c);
+}
+
+}  // namespace
+
+gs_status gs_autotune_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_camera* cams, const int32_t* Ws,
+                            const int32_t* Hs, float* const* out_C, float* const* out_grads, const int32_t* factors,
+                            float* const* out_up, int32_t reps, float* ms, int32_t* best)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (!g) return fail(c, GS_ERR_INVALID_ARG, "gaussians == NULL");
+    return autotune_impl(c, g, 1, nullptr, V, cams, Ws, Hs, out_C, out_grads, factors, out_up, reps, ms, best);
+}
+
+gs_status gs_autotune_views_scenes(gs_ctx* c, const gs_gaussians* scenes, int32_t S, const int32_t* scene_of_view,
+                                   int32_t V, const gs_camera* cams, const int32_t* Ws, const int32_t* Hs,
+                                   float* const* out_C, float* const* out_grads, const int32_t* factors,
+                                   float* const* out_up, int32_t reps, float* ms, int32_t* best)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (!scene_of_view) return fail(c, GS_ERR_INVALID_ARG, "scene_of_view == NULL");
+    return autotune_impl(c, scenes, S, scene_of_view, V, cams, Ws, Hs, out_C, out_grads, factors, out_up, reps, ms,
+                         best);
 }
 
 gs_status gs_read_projected(gs_ctx* c, float* mean2d, float* conic, float* rgb, float* opacity, float* depth,

@@ -67,6 +67,74 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ ids, 
     }
 }
 
+// The emission of every view of a batch in one launch.  Position k of the
+// batched (view, depth, id) order belongs to the view v whose stretch
+// [start_v, start_v + n_v) holds it; its Gaussian is sorted[k] - start_v of
+// that view, its pairs start at offsets[k] - offsets[start_v] of the view's own
+// pair buffer, and they are emitted exactly as k_emit emits a single view's
+// (same super-tile side, masks and order).  Per-super-tile counts go through
+// shared memory for the block's first view and straight to global memory for
+// the (rare) positions of a later view in the same block.
+__global__ void __launch_bounds__(256) k_emit_views(const __grid_constant__ EmitViews b,
+                                                    const uint32_t* __restrict__ sorted,
+                                                    const uint32_t* __restrict__ offsets,
+                                                    const ushort4* __restrict__ rect, uint32_t total)
+{
+    __shared__ uint32_t s_cnt[kMaxSupersForCounts];
+    const uint32_t k0 = blockIdx.x * blockDim.x;
+    int v0 = 0;
+    while (v0 + 1 < b.V && k0 >= b.v[v0 + 1].start) ++v0;
+    const EmitView& f = b.v[v0];
+    const bool shared_counts = f.Ts <= (uint32_t)kMaxSupersForCounts;
+    if (shared_counts) {
+        for (uint32_t t = threadIdx.x; t < f.Ts; t += blockDim.x) s_cnt[t] = 0;
+        __syncthreads();
+    }
+    const uint32_t k = k0 + threadIdx.x;
+    if (k < total) {
+        int v = v0;
+        while (v + 1 < b.V && k >= b.v[v + 1].start) ++v;
+        const EmitView& e = b.v[v];
+        const uint32_t base = offsets[e.start];
+        uint32_t off = offsets[k] - base;
+        const uint32_t end = offsets[k + 1] - base;
+        const uint32_t g = sorted[k];
+        const uint32_t id = g - e.start;
+        if (off < end && id < e.n) {   // id >= n only after an expired bounded wait in the sort
+            const ushort4 r = rect[g];
+            const int ks = e.ks;
+            const int sx0 = r.x / ks, sx1 = r.z / ks, sy0 = r.y / ks, sy1 = r.w / ks;
+            uint32_t* gcnt = e.counts + (size_t)(blockIdx.x % kCountCopies) * e.Ts;
+            for (int sy = sy0; sy <= sy1; ++sy) {
+                const int ly0 = max((int)r.y - sy * ks, 0), ly1 = min((int)r.w - sy * ks, ks - 1);
+                for (int sx = sx0; sx <= sx1 && off < end; ++sx) {
+                    const int lx0 = max((int)r.x - sx * ks, 0), lx1 = min((int)r.z - sx * ks, ks - 1);
+                    const uint32_t cols = ((2u << lx1) - 1u) & ~((1u << lx0) - 1u);
+                    uint32_t mask = 0;
+                    for (int ly = ly0; ly <= ly1; ++ly) mask |= cols << (ks * ly);
+                    const uint32_t st = (uint32_t)(sy * e.stiles_x + sx);
+                    if (off < e.cap) e.pairs[off] = ((uint64_t)mask << 48) | ((uint64_t)st << 32) | id;
+                    ++off;
+                    if (st < e.Ts) {
+                        if (v == v0 && shared_counts)
+                            atomicAdd(&s_cnt[st], 1u);
+                        else
+                            atomicAdd(&gcnt[st], 1u);
+                    }
+                }
+            }
+        }
+    }
+    if (shared_counts) {
+        __syncthreads();
+        uint32_t* dst = f.counts + (size_t)(blockIdx.x % kCountCopies) * f.Ts;
+        for (uint32_t t = threadIdx.x; t < f.Ts; t += blockDim.x) {
+            const uint32_t c = s_cnt[t];
+            if (c) atomicAdd(&dst[t], c);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) k_ranges(const uint64_t* __restrict__ pairs, uint32_t P, uint32_t T,
                                                 uint2* __restrict__ ranges)
 {
@@ -225,6 +293,14 @@ cudaError_t launch_emit_pairs(cudaStream_t s, const uint32_t* ids, const uint32_
         k_emit<false><<<(n + 255) / 256, 256, 0, s>>>(ids, offsets, rect, n, ks, stiles_x, pairs, nullptr, 0, cap,
                                                       id_base, rebase);
     note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emit_views(cudaStream_t s, const EmitViews& b, const uint32_t* sorted, const uint32_t* offsets,
+                              const ushort4* rect, uint32_t total)
+{
+    if (total == 0 || b.V <= 0) return cudaSuccess;
+    k_emit_views<<<(total + 255) / 256, 256, 0, s>>>(b, sorted, offsets, rect, total); note_launch();
     return cudaGetLastError();
 }
 

@@ -188,6 +188,12 @@ struct gs_ctx {
     gs::DevBuf vsranges;                // uint2[V][res_supers]
     gs::DevBuf vwork, vorder;           // uint32[V * res_tiles]: tile durations / order of the batch
     gs::DevBuf vqueue;                  // uint32 job counter of the persistent batched blend
+    gs::DevBuf vcounts;                 // uint32[V][kCountCopies][res_supers]: each view's super-tile counts
+    gs::DevBuf vhist;                   // uint32[V][8][256]: each view's pair-sort digit histograms
+    gs::DevBuf vstatus;                 // uint32[V][vstatus_stride]: each view's look-back states and counters
+    size_t vstatus_stride = 0;
+    int batch_views = 0;                // views of the last batch (0: the last frame was a single view)
+    int views_ks = 0;                   // batched views: super-tile side, 0 = per-view rule, or kSuperMax
     int views_map = 0;                  // batched blend: 0 = 8 x 4 warp blocks, 1 = 16 x 2
     int views_sched = 1;                // 0 = tile order, 1 = heaviest first (last batch), 2 = persistent
     bool totals_known = true;           // P, Ps valid on the host
@@ -213,15 +219,21 @@ inline void note_launch() { ++launch_counter(); }
 struct ViewDesc {
     CameraParams cam;
     int W, H, tiles_x, tiles_y;
-    int ks;   // super-tile side in tiles
+    int ks;         // super-tile side in tiles
+    uint32_t off;   // the view's Gaussian i is entry off + i of the batch's per-(view, Gaussian) arrays
+    int vid;        // the view's index in the batch
 };
-// Per-view outputs of the batched projection, view v at offset v * n (totals:
-// 2 kTotalSlots per view).
+// Per-view outputs of the batched projection, view v's Gaussian i at entry
+// g = off_v + i (totals: 2 kTotalSlots per view, at vid): records, rect,
+// super-tiles touched, and the batched depth sort's input, key64[g] =
+// vid << 32 | FP32 depth bits (0xFFFFFFFF for a Gaussian without tiles) and
+// gidx[g] = g.
 struct ViewOutputs {
     Records rec;
     ushort4* rect;
     uint32_t* supers;
-    uint32_t* depth_key;
+    uint64_t* key64;
+    uint32_t* gidx;
     unsigned long long* totals;
 };
 cudaError_t launch_project_views(cudaStream_t s, const gs_gaussians& g, const ViewDesc* views, int V, int mode,
@@ -261,10 +273,6 @@ cudaError_t radix_sort_u32_pairs(cudaStream_t s, uint32_t* keys[2], uint32_t* va
 cudaError_t radix_sort_u64_pairs(cudaStream_t s, uint64_t* keys[2], uint32_t* vals[2], uint32_t n, int bit_lo,
                                  int bit_hi, uint32_t* hist, uint32_t* status, uint32_t* counters, int* err,
                                  int* out_idx);
-// keys[g] = view << 32 | vkey[g] and vals[g] = g for g = v n + i < total (the
-// depth keys of a batch of views, sorted together with the view as the top digit)
-cudaError_t launch_view_keys(cudaStream_t s, const uint32_t* vkey, uint32_t n, uint32_t total, uint64_t* keys,
-                             uint32_t* vals);
 // uint64 keys alone.  hist_ready: hist already holds the exclusive digit
 // histograms of every pass (from launch_supers_to_hist), so the sort skips its
 // histogram kernels.  n_dev (optional, needs hist_ready): the key count is
@@ -299,6 +307,46 @@ cudaError_t launch_supers_to_hist(cudaStream_t s, uint32_t* counts, uint32_t Ts,
                                   uint32_t* order = nullptr);
 size_t radix_status_words(uint32_t n, int bit_lo, int bit_hi);
 int radix_passes(int bit_lo, int bit_hi);
+uint32_t radix_tiles(uint32_t n);   // one-sweep tiles of n keys
+
+// Several independent uint64 key arrays sorted in the same launches (the pair
+// lists of a batch of views): segment s sorts keys[0] of min(cap, *n_dev)
+// keys on bits [bit_lo, bit_lo + 8 passes) into keys[passes % 2], with its own
+// exclusive digit histograms hist [passes][256], look-back states status
+// [passes][tiles][256] and tile counters [passes] (both zeroed beforehand).
+constexpr int kMaxSortSegs = 32;
+struct SortSeg {
+    void* keys[2];
+    const uint32_t* n_dev;
+    uint32_t cap, tiles;   // tiles = radix_tiles(cap)
+    int passes, bit_lo;
+    const uint32_t* hist;
+    uint32_t* status;
+    uint32_t* counters;
+    int* err;
+    int first_block;       // set by the launcher
+};
+struct SortSegs {
+    SortSeg seg[kMaxSortSegs];
+    int count;
+};
+cudaError_t radix_sort_u64_segs(cudaStream_t s, SortSegs g);
+
+// k_supers_to_hist for each view of a batch in one launch (block v: view v).
+struct HistView {
+    uint32_t* counts;
+    uint32_t Ts;
+    int passes;
+    uint32_t* hist;
+    uint2* ranges;
+    PairCheckIn in;
+    PairCheckOut* out;
+};
+struct HistViews {
+    HistView v[kMaxSortSegs];
+    int V;
+};
+cudaError_t launch_supers_to_hist_views(cudaStream_t s, const HistViews& b, int* err);
 
 // exclusive scan of counts[ids[k]] over k -> offsets[k] (offsets[n] = total);
 // totals[0] = exact 64-bit total, totals[1] = 64-bit total of side[ids[k]].
@@ -345,6 +393,22 @@ cudaError_t launch_depth_sort_scan(cudaStream_t s, int device, const uint32_t* k
 cudaError_t launch_emit_pairs(cudaStream_t s, const uint32_t* ids, const uint32_t* offsets, const ushort4* rect,
                               uint32_t n, int ks, int stiles_x, uint64_t* pairs, uint32_t* counts, uint32_t Ts,
                               uint32_t cap = 0xFFFFFFFFu, uint32_t id_base = 0, bool rebase = false);
+// The emission of every view of a batch in one launch: view v owns positions
+// [start, start + n) of the batched (view, depth, id) order sorted (global
+// indices, view v's Gaussian i at start + i) and its own pair buffer (cap
+// pairs), super-tile side ks, stiles_x and counts [kCountCopies][Ts] (zeroed).
+struct EmitView {
+    uint64_t* pairs;
+    uint32_t* counts;
+    uint32_t start, n, cap, Ts;
+    int ks, stiles_x;
+};
+struct EmitViews {
+    EmitView v[kMaxSortSegs];
+    int V;
+};
+cudaError_t launch_emit_views(cudaStream_t s, const EmitViews& b, const uint32_t* sorted, const uint32_t* offsets,
+                              const ushort4* rect, uint32_t total);
 cudaError_t launch_ranges(cudaStream_t s, const uint64_t* pairs, uint32_t P, uint32_t T, uint2* ranges);
 // per-tile lists from the super-tile lists: counts, starts, ranges and (optionally) keys/vals
 cudaError_t launch_tile_lists(cudaStream_t s, const uint64_t* spairs, const uint2* sranges, const ushort4* rect,

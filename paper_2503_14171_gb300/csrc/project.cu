@@ -386,8 +386,10 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
 // as in k_project) -- computes the view-independent 3D covariance and opacity
 // once, then runs the per-view projection of k_project for every view (same
 // expressions, so a view here equals a single-view k_project bit for bit).
-// Per view v it writes the records, tile rect, super-tile count and depth key
-// at offset v * n of the outputs, and the view's pair totals into slot set v.
+// Per view it writes the records, tile rect, super-tile count and the batched
+// depth sort's key and index at entry off + i of the outputs, and the view's
+// pair totals into slot set vid.  A batch over several Gaussian sets runs one
+// launch per set, each over the views that use it.
 template <int DEG>
 __global__ void __launch_bounds__(kProjThreads) k_project_views(
     int n, const float* __restrict__ means, const float* __restrict__ log_scales,
@@ -434,17 +436,19 @@ __global__ void __launch_bounds__(kProjThreads) k_project_views(
 #pragma unroll
             for (int w = 0; w < kProjThreads / 32; ++w) b += s_tot[threadIdx.x][w];
             if (b)
-                atomicAdd(&out.totals[(size_t)vi * 2 * kTotalSlots + 2 * (blockIdx.x % kTotalSlots) + threadIdx.x], b);
+                atomicAdd(&out.totals[(size_t)d.vid * 2 * kTotalSlots + 2 * (blockIdx.x % kTotalSlots) + threadIdx.x],
+                          b);
         }
         __syncthreads();   // s_tot is reused by the next view
         if (!inrange) continue;
-        const size_t o = (size_t)vi * n + i;
+        const size_t o = (size_t)d.off + i;
         const int4 rc = v.rc;
         out.supers[o] = v.nsup;
         out.rect[o] = v.ntiles ? make_ushort4((unsigned short)rc.x, (unsigned short)rc.y, (unsigned short)rc.z,
                                               (unsigned short)rc.w)
                                : make_ushort4(1, 1, 0, 0);
-        out.depth_key[o] = v.ntiles > 0 ? __float_as_uint(v.pz) : 0xFFFFFFFFu;
+        out.key64[o] = ((uint64_t)d.vid << 32) | (v.ntiles > 0 ? __float_as_uint(v.pz) : 0xFFFFFFFFu);
+        out.gidx[o] = (uint32_t)o;
         float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
         if (v.vis)
             view_records<DEG>(v, mx3, my3, mz3, &s_sh[warp][lane][0], rgb_in + 3 * (DEG >= 0 ? 0 : i), op, L,

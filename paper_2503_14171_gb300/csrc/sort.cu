@@ -101,20 +101,17 @@ struct OnesweepSmem {
     uint32_t vals[HAS_VAL ? kTileKeys : 1];
 };
 
+// One tile of a one-sweep pass (the tile index taken from a counter in launch
+// order, so every predecessor tile is running or done).
 template <typename K, bool HAS_VAL>
-__global__ void __launch_bounds__(kThreads, 4) k_onesweep(const K* __restrict__ keys_in, K* __restrict__ keys_out,
-                                                       const uint32_t* __restrict__ vals_in,
-                                                       uint32_t* __restrict__ vals_out, uint32_t n, int shift,
-                                                       const uint32_t* __restrict__ digit_base,
-                                                       uint32_t* __restrict__ status,
-                                                       uint32_t* __restrict__ tile_counter, int* __restrict__ err,
-                                                       const uint32_t* __restrict__ n_dev)
+__device__ __forceinline__ void onesweep_tile(OnesweepSmem<K, HAS_VAL>& S, const K* __restrict__ keys_in,
+                                              K* __restrict__ keys_out, const uint32_t* __restrict__ vals_in,
+                                              uint32_t* __restrict__ vals_out, uint32_t n, int shift,
+                                              const uint32_t* __restrict__ digit_base,
+                                              uint32_t* __restrict__ status, uint32_t* __restrict__ tile_counter,
+                                              int* __restrict__ err)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto& S = *reinterpret_cast<OnesweepSmem<K, HAS_VAL>*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (n_dev) n = min(n, *n_dev);   // key count known on the device only; surplus tiles exit
-
     for (int i = tid; i < kWarps * kRadix; i += kThreads) (&S.warp_hist[0][0])[i] = 0;
     if (tid == 0) S.tile = atomicAdd(tile_counter, 1u);   // tiles are taken in launch order
     __syncthreads();
@@ -249,6 +246,44 @@ __global__ void __launch_bounds__(kThreads, 4) k_onesweep(const K* __restrict__ 
 }
 
 template <typename K, bool HAS_VAL>
+__global__ void __launch_bounds__(kThreads, 4) k_onesweep(const K* __restrict__ keys_in, K* __restrict__ keys_out,
+                                                       const uint32_t* __restrict__ vals_in,
+                                                       uint32_t* __restrict__ vals_out, uint32_t n, int shift,
+                                                       const uint32_t* __restrict__ digit_base,
+                                                       uint32_t* __restrict__ status,
+                                                       uint32_t* __restrict__ tile_counter, int* __restrict__ err,
+                                                       const uint32_t* __restrict__ n_dev)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto& S = *reinterpret_cast<OnesweepSmem<K, HAS_VAL>*>(smem_raw);
+    if (n_dev) n = min(n, *n_dev);   // key count known on the device only; surplus tiles exit
+    onesweep_tile<K, HAS_VAL>(S, keys_in, keys_out, vals_in, vals_out, n, shift, digit_base, status, tile_counter,
+                              err);
+}
+
+// One pass over several independent key arrays (the pair lists of a batch of
+// views) in one launch: blocks [first[s], first[s + 1]) serve segment s, which
+// sorts its own keys with its own digit histogram, look-back states and tile
+// counter exactly as k_onesweep sorts one array.  A segment with fewer passes
+// than the launch's pass index has no blocks.
+template <typename K>
+__global__ void __launch_bounds__(kThreads, 4) k_onesweep_segs(const __grid_constant__ SortSegs g, int pass)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto& S = *reinterpret_cast<OnesweepSmem<K, false>*>(smem_raw);
+    int sg = 0;
+    while (sg + 1 < g.count && (int)blockIdx.x >= g.seg[sg + 1].first_block) ++sg;
+    const SortSeg& q = g.seg[sg];
+    if (pass >= q.passes) return;
+    uint32_t n = q.cap;
+    if (q.n_dev) n = min(n, *q.n_dev);
+    const int cur = pass & 1;
+    onesweep_tile<K, false>(S, reinterpret_cast<const K*>(q.keys[cur]), reinterpret_cast<K*>(q.keys[cur ^ 1]),
+                            nullptr, nullptr, n, q.bit_lo + pass * kRadixBits, q.hist + pass * kRadix,
+                            q.status + (size_t)pass * q.tiles * kRadix, q.counters + pass, q.err);
+}
+
+template <typename K, bool HAS_VAL>
 cudaError_t radix_sort_impl(cudaStream_t s, K* keys[2], uint32_t* vals[2], uint32_t n, int bit_lo, int bit_hi,
                             uint32_t* hist, uint32_t* status, uint32_t* counters, int* err, int* out_idx,
                             bool hist_ready, const uint32_t* n_dev = nullptr, bool pre_zeroed = false)
@@ -273,12 +308,7 @@ cudaError_t radix_sort_impl(cudaStream_t s, K* keys[2], uint32_t* vals[2], uint3
         k_radix_hist_scan<<<passes, kThreads, 0, s>>>(hist); note_launch();
     }
     const size_t smem = sizeof(OnesweepSmem<K, HAS_VAL>);
-    static bool attr_set = false;
-    if (!attr_set) {
-        e = cudaFuncSetAttribute(k_onesweep<K, HAS_VAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static_assert(sizeof(OnesweepSmem<uint64_t, true>) <= 48 * 1024, "dynamic shared memory within the default limit");
     int cur = 0;
     for (int p = 0; p < passes; ++p) {
         const int shift = bit_lo + p * kRadixBits;
@@ -435,27 +465,6 @@ cudaError_t radix_sort_u64_pairs(cudaStream_t s, uint64_t* keys[2], uint32_t* va
                                            false, nullptr);
 }
 
-namespace {
-// key g = (view << 32 | depth key of Gaussian i in view v), value g, for g = v n + i
-__global__ void __launch_bounds__(256) k_view_keys(const uint32_t* __restrict__ vkey, uint32_t n, uint32_t total,
-                                                   uint64_t* __restrict__ keys, uint32_t* __restrict__ vals)
-{
-    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= total) return;
-    const uint32_t k = vkey[g];
-    keys[g] = ((uint64_t)(g / n) << 32) | k;
-    vals[g] = g;
-}
-}  // namespace
-
-cudaError_t launch_view_keys(cudaStream_t s, const uint32_t* vkey, uint32_t n, uint32_t total, uint64_t* keys,
-                             uint32_t* vals)
-{
-    if (total == 0 || n == 0) return cudaSuccess;
-    k_view_keys<<<(total + 255) / 256, 256, 0, s>>>(vkey, n, total, keys, vals); note_launch();
-    return cudaGetLastError();
-}
-
 cudaError_t radix_sort_u64_keys(cudaStream_t s, uint64_t* keys[2], uint32_t n, int bit_lo, int bit_hi,
                                 uint32_t* hist, uint32_t* status, uint32_t* counters, int* err, int* out_idx,
                                 bool hist_ready, const uint32_t* n_dev, bool pre_zeroed)
@@ -478,17 +487,10 @@ cudaError_t radix_sort_u64_keys(cudaStream_t s, uint64_t* keys[2], uint32_t n, i
 // range is left empty (the blend then sees no Gaussians), out->count = 0 so
 // the sort does nothing, and the error word reports the overflow;
 // out->needed / out->tile_pairs keep the frame's totals for the host.
-__global__ void __launch_bounds__(kThreads) k_supers_to_hist(uint32_t* __restrict__ counts, uint32_t Ts,
-                                                             int passes, uint32_t* __restrict__ hist,
-                                                             uint2* __restrict__ ranges, PairCheckIn in,
-                                                             PairCheckOut* out, int* __restrict__ err,
-                                                             const uint32_t* __restrict__ order_work,
-                                                             uint32_t order_T, uint32_t* __restrict__ order)
+__device__ __forceinline__ void supers_to_hist_block(uint32_t* __restrict__ counts, uint32_t Ts, int passes,
+                                                     uint32_t* __restrict__ hist, uint2* __restrict__ ranges,
+                                                     const PairCheckIn& in, PairCheckOut* out, int* __restrict__ err)
 {
-    if (blockIdx.x == 1) {   // beside it, independent of it: the next blend's tile order
-        tile_order_block(order_work, order_T, order);
-        return;
-    }
     __shared__ uint32_t s_hist[kHistPasses][kRadix];
     __shared__ uint32_t s_warp[kWarps];
     __shared__ unsigned long long s_sum[kWarps];
@@ -574,6 +576,63 @@ __global__ void __launch_bounds__(kThreads) k_supers_to_hist(uint32_t* __restric
         carry += tot;
         __syncthreads();
     }
+}
+
+__global__ void __launch_bounds__(kThreads) k_supers_to_hist(uint32_t* __restrict__ counts, uint32_t Ts,
+                                                             int passes, uint32_t* __restrict__ hist,
+                                                             uint2* __restrict__ ranges, PairCheckIn in,
+                                                             PairCheckOut* out, int* __restrict__ err,
+                                                             const uint32_t* __restrict__ order_work,
+                                                             uint32_t order_T, uint32_t* __restrict__ order)
+{
+    if (blockIdx.x == 1) {   // beside it, independent of it: the next blend's tile order
+        tile_order_block(order_work, order_T, order);
+        return;
+    }
+    supers_to_hist_block(counts, Ts, passes, hist, ranges, in, out, err);
+}
+
+// The per-view counts of a batch of views: block v folds view v's counts into
+// its histograms, ranges and pair check, as k_supers_to_hist does for a frame.
+__global__ void __launch_bounds__(kThreads) k_supers_to_hist_views(const __grid_constant__ HistViews b,
+                                                                   int* __restrict__ err)
+{
+    const HistView& h = b.v[blockIdx.x];
+    supers_to_hist_block(h.counts, h.Ts, h.passes, h.hist, h.ranges, h.in, h.out, err);
+}
+
+cudaError_t launch_supers_to_hist_views(cudaStream_t s, const HistViews& b, int* err)
+{
+    if (b.V <= 0) return cudaSuccess;
+    k_supers_to_hist_views<<<b.V, kThreads, 0, s>>>(b, err); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t radix_sort_u64_segs(cudaStream_t s, SortSegs g)
+{
+    int max_passes = 0;
+    for (int k = 0; k < g.count; ++k) {
+        if (g.seg[k].passes > kMaxPasses) return cudaErrorInvalidValue;
+        max_passes = max_passes > g.seg[k].passes ? max_passes : g.seg[k].passes;
+    }
+    const size_t smem = sizeof(OnesweepSmem<uint64_t, false>);
+    for (int p = 0; p < max_passes; ++p) {
+        int blocks = 0;
+        for (int k = 0; k < g.count; ++k) {
+            g.seg[k].first_block = blocks;
+            if (p < g.seg[k].passes) blocks += (int)g.seg[k].tiles;
+        }
+        if (blocks == 0) continue;
+        k_onesweep_segs<uint64_t><<<blocks, kThreads, smem, s>>>(g, p); note_launch();
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+uint32_t radix_tiles(uint32_t n)
+{
+    return (n + kTileKeys - 1) / kTileKeys;
 }
 
 cudaError_t launch_supers_to_hist(cudaStream_t s, uint32_t* counts, uint32_t Ts, int passes, uint32_t* hist,
