@@ -983,82 +983,100 @@ def mlp_leg(torch, gs, scenes, stream, dev, peaks, pairs, steps, reps=20):
     }
 
 
-def views_leg(torch, gs, scenes, stream, n_list=(300_000, 800_000, 2_000_000), reps=20):
-    """Batched multi-view rendering (16 stereo views, each eye rendered at half
-    size with derivatives and upscaled 2x; one projection, one blend and one
-    upscale launch for all views, the blend's launch shape from the autotuner)
-    against the same views one at a time; both recorded as CUDA graphs.  Output
-    megapixels per second."""
+VIEW_SETS = (300_000, 800_000, 2_000_000)
+
+
+def _view_sets_and_cams(scenes):
+    """The batching workload: 8 stereo pairs of uneven per-eye sizes (512x512
+    to 1104x1032, each eye rendered at half size with derivatives and upscaled
+    2x), pair k drawing on Gaussian set k mod 3 of the 300k, 800k and 2M
+    mixture scenes."""
     camdefs, eyes = scenes.stereo_views()
-    V = len(eyes)
     lows = [(W // 2, H // 2) for W, H in eyes]
     cams = [scenes.pinhole_camera(w, h, viewmat=scenes.look_at_viewmat(e, t)) for (w, h), (e, t) in zip(lows, camdefs)]
+    scene_of_view = [(v // 2) % len(VIEW_SETS) for v in range(len(eyes))]
+    return eyes, lows, cams, scene_of_view
+
+
+def views_leg(torch, gs, scenes, stream, reps=20):
+    """Batched multi-view rendering (16 stereo views over three Gaussian sets
+    of uneven size; one projection launch per set, one sort, emission and
+    histogram launch and one launch per sort pass for all views, one blend and
+    one upscale launch; binning and launch shape from the autotuner) against
+    the same views one at a time; both recorded as CUDA graphs.  Output
+    megapixels per second."""
+    eyes, lows, cams, sov = _view_sets_and_cams(scenes)
+    V = len(eyes)
     out_mpix = sum(W * H for W, H in eyes) / 1e6
-    res = {"views": V, "eye_sizes": eyes, "scenes": {}}
-    for n in n_list:
-        scene = scenes.mixture_scene(n, seed=1)
-        dev = gs.DeviceScene(scene)
-        Wm, Hm = max(w for w, _ in lows), max(h for _, h in lows)
-        # super-tile pairs of the largest view bound the reservation (with headroom)
-        ps = 0
-        with gs.Context(stream=stream) as probe:
-            with torch.cuda.stream(stream):
-                for (w, h), cam in zip(lows, cams):
-                    probe.project(dev, cam, w, h)
-                    ps = max(ps, probe.super_pair_count())
-        cap = ps + ps // 4 + 4096
-        timings = {}
-        for mode in ("batched", "per_view"):
-            ctx = gs.Context(stream=stream, no_host_wait=True)
+    devs = [gs.DeviceScene(scenes.mixture_scene(n, seed=1)) for n in VIEW_SETS]
+    Wm, Hm = max(w for w, _ in lows), max(h for _, h in lows)
+    # super-tile pairs of the largest view bound the reservation (with headroom)
+    ps = 0
+    with gs.Context(stream=stream) as probe:
+        with torch.cuda.stream(stream):
+            for (w, h), cam, k in zip(lows, cams, sov):
+                probe.project(devs[k], cam, w, h)
+                ps = max(ps, probe.super_pair_count())
+    cap = ps + ps // 4 + 4096
+    res = {"views": V, "eye_sizes": eyes, "render_sizes": lows, "gaussian_sets": list(VIEW_SETS),
+           "set_of_view": sov, "entries": sum(VIEW_SETS[k] for k in sov)}
+    timings = {}
+    tune = None
+    for mode in ("batched", "per_view"):
+        ctx = gs.Context(stream=stream, no_host_wait=True)
+        if mode == "batched":
+            ctx.reserve_views(max(VIEW_SETS), V, Wm, Hm, cap)
+        else:
+            ctx.reserve(max(VIEW_SETS), Wm, Hm, cap)
+        outs = [[torch.empty(3, h, w, device="cuda"), torch.empty(3, 3, h, w, device="cuda"),
+                 torch.empty(3, 2 * h, 2 * w, device="cuda")] for w, h in lows]
+
+        def body():
             if mode == "batched":
-                ctx.reserve_views(n, V, Wm, Hm, cap)
+                ctx.render_views(devs, cams, lows, [2] * V, outs=outs, scene_of_view=sov)
             else:
-                ctx.reserve(n, Wm, Hm, cap)
-            outs = [[torch.empty(3, h, w, device="cuda"), torch.empty(3, 3, h, w, device="cuda"),
-                     torch.empty(3, 2 * h, 2 * w, device="cuda")] for w, h in lows]
+                for (w, h), cam, o, k in zip(lows, cams, outs, sov):
+                    ctx.render_with_grads(devs[k], cam, w, h, out_C=o[0], out_grads=o[1])
+                    ctx.upscale(o[0], o[1], 2, out=o[2])
 
-            def body():
-                if mode == "batched":
-                    ctx.render_views(dev, cams, lows, [2] * V, outs=outs)
-                else:
-                    for (w, h), cam, o in zip(lows, cams, outs):
-                        ctx.render_with_grads(dev, cam, w, h, out_C=o[0], out_grads=o[1])
-                        ctx.upscale(o[0], o[1], 2, out=o[2])
-
-            with torch.cuda.stream(stream):
+        with torch.cuda.stream(stream):
+            body()
+            torch.cuda.synchronize()
+            if mode == "batched":
+                # binning and launch shape: the project's autotuner on this batch
+                tune = ctx.autotune_views(devs, cams, lows, [2] * V, outs, reps=5, scene_of_view=sov)
+            l0 = ctx.launch_count()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
                 body()
-                torch.cuda.synchronize()
-                if mode == "batched":
-                    # launch shape of the batched blend: the project's autotuner on this batch
-                    tune_ms, tune_best = ctx.autotune_views(dev, cams, lows, [2] * V, outs, reps=5)
-                g = torch.cuda.CUDAGraph()
-                with torch.cuda.graph(g, stream=stream):
-                    body()
-                for _ in range(3):
-                    g.replay()
-                torch.cuda.synchronize()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                for _ in range(reps):
-                    g.replay()
-                b.record(stream)
-                torch.cuda.synchronize()
-            ctx.synchronize()
-            timings[mode] = a.elapsed_time(b) / reps
-            del g
-            ctx.close()
-        res["scenes"][str(n)] = {"batched_ms": timings["batched"], "per_view_ms": timings["per_view"],
-                                 "batched_mpix_s": out_mpix / timings["batched"] * 1e3,
-                                 "per_view_mpix_s": out_mpix / timings["per_view"] * 1e3,
-                                 "speedup": timings["per_view"] / timings["batched"],
-                                 "autotune_ms": [round(t, 4) for t in tune_ms],
-                                 "autotune_best": {"config": tune_best, "warp_map": tune_best % 2,
-                                                   "schedule": ["tile order", "heaviest first",
-                                                                "persistent",
-                                                                "views in order, heaviest first within"
-                                                                ][tune_best // 2]}}
-        del dev
-        torch.cuda.empty_cache()
+            launches = ctx.launch_count() - l0
+            for _ in range(3):
+                g.replay()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                g.replay()
+            b.record(stream)
+            torch.cuda.synchronize()
+        ctx.synchronize()
+        timings[mode] = (a.elapsed_time(b) / reps, launches)
+        del g
+        ctx.close()
+    tune_ms, best = tune
+    res.update({"batched_ms": timings["batched"][0], "per_view_ms": timings["per_view"][0],
+                "batched_launches": timings["batched"][1], "per_view_launches": timings["per_view"][1],
+                "batched_mpix_s": out_mpix / timings["batched"][0] * 1e3,
+                "per_view_mpix_s": out_mpix / timings["per_view"][0] * 1e3,
+                "speedup": timings["per_view"][0] / timings["batched"][0],
+                "autotune_ms": [round(t, 4) for t in tune_ms],
+                "autotune_best": {"config": best, "warp_map": ["8x4 block", "16x2 strip"][best % 2],
+                                  "schedule": ["tile order", "heaviest first", "persistent",
+                                               "views in order, heaviest first within"][(best // 2) % 4],
+                                  "super_side": "4x4 tiles" if best >= 8 else "per view (smallest side with "
+                                                                              "<= 256 super-tiles)"}})
+    del devs
+    torch.cuda.empty_cache()
     return res
 
 
@@ -1118,14 +1136,13 @@ def run_profile(args):
     def mlp_train_step():
         model.step(batch, 1e-3)
 
-    # the batched views (16 stereo views of a 300k-Gaussian scene, half-size
-    # renders with derivatives, 2x upscales; one projection, blend and upscale
-    # launch)
+    # the batched views (16 stereo views over the 300k, 800k and 2M sets,
+    # half-size renders with derivatives, 2x upscales)
     views = {}
 
     def views_step():
         views["ctx"].render_views(views["dev"], views["cams"], views["lows"], [2] * len(views["cams"]),
-                                  outs=views["outs"])
+                                  outs=views["outs"], scene_of_view=views["sov"])
 
     # the bicubic comparator on the plain 960x540 render, and the upscale's adjoint
     bic_out = None
@@ -1154,14 +1171,11 @@ def run_profile(args):
             model = residual.ResidualMLP(ctx, seed=0)
             torch.cuda.synchronize()
     if args.profile == "views":
-        camdefs, eyes = scenes.stereo_views()
-        lows = [(w // 2, h // 2) for w, h in eyes]
-        vcams = [scenes.pinhole_camera(w, h, viewmat=scenes.look_at_viewmat(e, t))
-                 for (w, h), (e, t) in zip(lows, camdefs)]
-        vdev = gs.DeviceScene(scenes.mixture_scene(300_000, seed=1))
+        eyes, lows, vcams, sov = _view_sets_and_cams(scenes)
+        vdevs = [gs.DeviceScene(scenes.mixture_scene(n, seed=1)) for n in VIEW_SETS]
         vctx = gs.Context(stream=stream, no_host_wait=True)
-        vctx.reserve_views(300_000, len(vcams), max(w for w, _ in lows), max(h for _, h in lows), 2_000_000)
-        views.update(ctx=vctx, dev=vdev, cams=vcams, lows=lows,
+        vctx.reserve_views(max(VIEW_SETS), len(vcams), max(w for w, _ in lows), max(h for _, h in lows), 5_000_000)
+        views.update(ctx=vctx, dev=vdevs, sov=sov, cams=vcams, lows=lows,
                      outs=[[torch.empty(3, h, w, device="cuda"), torch.empty(3, 3, h, w, device="cuda"),
                             torch.empty(3, 2 * h, 2 * w, device="cuda")] for w, h in lows])
     if args.profile == "bicubic":

@@ -538,7 +538,7 @@ gs_status gs_destroy(gs_ctx* c)
                       &c->errword, &c->grad2d, &c->pair_check, &c->tile_work, &c->tile_order,
                       &c->vrec0, &c->vrec1, &c->vrec2, &c->vrect, &c->vsupers, &c->vkey, &c->vtotals,
                       &c->views_dev, &c->vpairs0, &c->vpairs1, &c->vsranges, &c->vwork, &c->vorder, &c->vqueue,
-                      &c->vsortv, &c->vcounts, &c->vhist, &c->vstatus};
+                      &c->vsortv, &c->vcounts, &c->vhist, &c->vstatus, &c->vdhist, &c->vdstatus};
     for (DevBuf* b : bufs) release(*b);
     if (c->h_scalar) cudaFreeHost(c->h_scalar);
     if (c->totals_ready) cudaEventDestroy(c->totals_ready);
@@ -914,17 +914,18 @@ gs_status reserve_impl(gs_ctx* c, int64_t n, int32_t V, int32_t W, int32_t H, in
         const size_t vn = un * (size_t)V;
         if (vn >= 0xFFFFFFFFull)
             return fail(c, GS_ERR_CAPACITY, "%d views of %lld Gaussians exceed 2^32 entries", V, (long long)n);
-        const int vbits = bits_for((uint32_t)V);
-        // the batched depth sort: (view, depth) keys in the two pair buffers
-        // (free until the views' pairs are emitted), values in vkey and vsortv
+        // the views' depth sorts: 32-bit keys, both ping-pong halves in the
+        // first pair buffer (free until the views' pairs are emitted), values
+        // in vkey and vsortv
         const size_t per_view = std::max<size_t>((size_t)super_pairs, un);
         if ((st = ensure(c, c->vsortv, sizeof(uint32_t) * vn)) ||
+            (st = ensure(c, c->vdhist, sizeof(uint32_t) * 4 * 256 * (size_t)V)) ||
+            (st = ensure(c, c->vdstatus, sizeof(uint32_t) * (radix_status_words(nn, 0, 32) + 8) * V)) ||
             (st = ensure(c, c->offsets, sizeof(uint32_t) * (vn + 1))) ||
             (st = ensure(c, c->scan_partials, sizeof(unsigned long long) * scan_partials_count((uint32_t)vn))) ||
-            (st = ensure(c, c->sort_status, sizeof(uint32_t) * std::max({radix_status_words((uint32_t)vn, 0, 32 + vbits),
-                                                                          radix_status_words(nn, 0, 32),
-                                                                          radix_status_words((uint32_t)super_pairs, 32,
-                                                                                             32 + sbits)}))))
+            (st = ensure(c, c->sort_status, sizeof(uint32_t) * std::max(radix_status_words(nn, 0, 32),
+                                                                         radix_status_words((uint32_t)super_pairs, 32,
+                                                                                            32 + sbits)))))
             return st;
         if ((st = ensure(c, c->vrec0, sizeof(float4) * vn)) || (st = ensure(c, c->vrec1, sizeof(float4) * vn)) ||
             (st = ensure(c, c->vrec2, sizeof(float4) * vn)) || (st = ensure(c, c->vrect, sizeof(ushort4) * vn)) ||
@@ -944,6 +945,7 @@ gs_status reserve_impl(gs_ctx* c, int64_t n, int32_t V, int32_t W, int32_t H, in
             (st = ensure(c, c->pair_check, sizeof(PairCheckOut) * (size_t)V)))
             return st;
         c->vstatus_stride = radix_status_words((uint32_t)super_pairs, 32, 32 + sbits) + 8;
+        c->vdstatus_stride = radix_status_words(nn, 0, 32) + 8;
         GS_CUDA(c, cudaMemsetAsync(c->vwork.p, 0, sizeof(uint32_t) * (size_t)T * V, c->stream));
     }
     GS_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -1058,15 +1060,16 @@ gs_status render_views_impl(gs_ctx* c, const gs_gaussians* scenes, int32_t S, co
     unsigned long long* vtot = as<unsigned long long>(c->vtotals);
     GS_CUDA(c, cudaMemsetAsync(vtot, 0, sizeof(unsigned long long) * 2 * kTotalSlots * V, s));
     GS_CUDA(c, launch_set_views(s, batch, V, as<ViewDesc>(c->views_dev)));
-    // the batched depth sort's keys go to the pair buffers (free until the
-    // views' pairs are emitted), its values to vkey and vsortv
-    uint64_t* k64[2] = {as<uint64_t>(c->vpairs0), as<uint64_t>(c->vpairs1)};
+    // the views' depth sorts: keys in the first pair buffer (free until the
+    // views' pairs are emitted), values (batch entries) in vkey and vsortv
+    const size_t vcap = (size_t)c->res_n * c->res_views;
+    uint32_t* k32[2] = {as<uint32_t>(c->vpairs0), as<uint32_t>(c->vpairs0) + vcap};
     uint32_t* v32[2] = {as<uint32_t>(c->vkey), as<uint32_t>(c->vsortv)};
     ViewOutputs vo;
     vo.rec = Records{as<float4>(c->vrec0), as<float4>(c->vrec1), as<float4>(c->vrec2)};
     vo.rect = as<ushort4>(c->vrect);
     vo.supers = as<uint32_t>(c->vsupers);
-    vo.key64 = k64[0];
+    vo.depth_key = k32[0];
     vo.gidx = v32[0];
     vo.totals = vtot;
     for (int k = 0; k < S; ++k) {   // one projection launch per Gaussian set, over its views
@@ -1075,15 +1078,35 @@ gs_status render_views_impl(gs_ctx* c, const gs_gaussians* scenes, int32_t S, co
             GS_CUDA(c, launch_project_views(s, scenes[k], as<ViewDesc>(c->views_dev) + set_first[k], nv, c->opt.mode,
                                             vo));
     }
-    // every view's Gaussians in its own depth order, contiguous per view (the
-    // view is the top digit of the stable sort, which starts in id order),
-    // then the super-tile pair offsets over the whole order
-    int vs = 0;
-    if (total > 1)
-        GS_CUDA(c, radix_sort_u64_pairs(s, k64, v32, total, 0, 32 + bits_for((uint32_t)V), as<uint32_t>(c->sort_hist),
-                                        as<uint32_t>(c->sort_status), as<uint32_t>(c->sort_counter),
-                                        as<int>(c->errword), &vs));
-    const uint32_t* vsorted = v32[vs];
+    // every view's Gaussians in its own depth order (each view's stretch of
+    // the batch sorted as a segment of its own: a stable sort of the 32-bit
+    // depth keys, which start in id order), then the super-tile pair offsets
+    // over the whole order
+    {
+        SortSegs ds{};
+        ds.count = V;
+        const size_t dstride = c->vdstatus_stride;
+        GS_CUDA(c, cudaMemsetAsync(c->vdhist.p, 0, sizeof(uint32_t) * 4 * 256 * V, s));
+        GS_CUDA(c, cudaMemsetAsync(c->vdstatus.p, 0, sizeof(uint32_t) * dstride * V, s));
+        for (int v = 0; v < V; ++v) {
+            SortSeg& q = ds.seg[v];
+            for (int b = 0; b < 2; ++b) {
+                q.keys[b] = k32[b] + start[v];
+                q.vals[b] = v32[b] + start[v];
+            }
+            q.n_dev = nullptr;
+            q.cap = nview[v];
+            q.tiles = radix_tiles(nview[v]);
+            q.passes = 4;   // even: the sorted entries land in v32[0]
+            q.bit_lo = 0;
+            q.hist = as<uint32_t>(c->vdhist) + (size_t)v * 4 * 256;
+            q.status = as<uint32_t>(c->vdstatus) + (size_t)v * dstride;
+            q.counters = q.status + dstride - 8;
+            q.err = as<int>(c->errword);
+        }
+        GS_CUDA(c, radix_sort_u32_pairs_segs(s, ds));
+    }
+    const uint32_t* vsorted = v32[0];
     unsigned long long* scan_tot = as<unsigned long long>(c->scan_totals) + 2 * kTotalSlots;
     GS_CUDA(c, launch_scan_gathered(s, as<uint32_t>(c->vsupers), nullptr, vsorted, total, as<uint32_t>(c->offsets),
                                     as<unsigned long long>(c->scan_partials), reinterpret_cast<uint32_t*>(scan_tot + 2),

@@ -192,6 +192,9 @@ struct gs_ctx {
     gs::DevBuf vhist;                   // uint32[V][8][256]: each view's pair-sort digit histograms
     gs::DevBuf vstatus;                 // uint32[V][vstatus_stride]: each view's look-back states and counters
     size_t vstatus_stride = 0;
+    gs::DevBuf vdhist;                  // uint32[V][4][256]: each view's depth-sort digit histograms
+    gs::DevBuf vdstatus;                // uint32[V][vdstatus_stride]: each view's depth-sort states and counters
+    size_t vdstatus_stride = 0;
     int batch_views = 0;                // views of the last batch (0: the last frame was a single view)
     int views_ks = 0;                   // batched views: super-tile side, 0 = per-view rule, or kSuperMax
     int views_map = 0;                  // batched blend: 0 = 8 x 4 warp blocks, 1 = 16 x 2
@@ -225,14 +228,14 @@ struct ViewDesc {
 };
 // Per-view outputs of the batched projection, view v's Gaussian i at entry
 // g = off_v + i (totals: 2 kTotalSlots per view, at vid): records, rect,
-// super-tiles touched, and the batched depth sort's input, key64[g] =
-// vid << 32 | FP32 depth bits (0xFFFFFFFF for a Gaussian without tiles) and
-// gidx[g] = g.
+// super-tiles touched, and the input of the views' depth sorts,
+// depth_key[g] = FP32 depth bits (0xFFFFFFFF for a Gaussian without tiles)
+// and gidx[g] = g.
 struct ViewOutputs {
     Records rec;
     ushort4* rect;
     uint32_t* supers;
-    uint64_t* key64;
+    uint32_t* depth_key;
     uint32_t* gidx;
     unsigned long long* totals;
 };
@@ -309,14 +312,16 @@ size_t radix_status_words(uint32_t n, int bit_lo, int bit_hi);
 int radix_passes(int bit_lo, int bit_hi);
 uint32_t radix_tiles(uint32_t n);   // one-sweep tiles of n keys
 
-// Several independent uint64 key arrays sorted in the same launches (the pair
-// lists of a batch of views): segment s sorts keys[0] of min(cap, *n_dev)
-// keys on bits [bit_lo, bit_lo + 8 passes) into keys[passes % 2], with its own
-// exclusive digit histograms hist [passes][256], look-back states status
-// [passes][tiles][256] and tile counters [passes] (both zeroed beforehand).
+// Several independent key arrays sorted in the same launches (the pair lists
+// of a batch of views; each view's depth keys): segment s sorts keys[0] (and
+// vals[0]) of min(cap, *n_dev) keys on bits [bit_lo, bit_lo + 8 passes) into
+// keys[passes % 2] (vals[passes % 2]), with its own exclusive digit
+// histograms hist [passes][256], look-back states status [passes][tiles][256]
+// and tile counters [passes] (both zeroed beforehand).
 constexpr int kMaxSortSegs = 32;
 struct SortSeg {
     void* keys[2];
+    uint32_t* vals[2];
     const uint32_t* n_dev;
     uint32_t cap, tiles;   // tiles = radix_tiles(cap)
     int passes, bit_lo;
@@ -330,7 +335,10 @@ struct SortSegs {
     SortSeg seg[kMaxSortSegs];
     int count;
 };
-cudaError_t radix_sort_u64_segs(cudaStream_t s, SortSegs g);
+cudaError_t radix_sort_u64_segs(cudaStream_t s, SortSegs g);   // uint64 keys alone, hist given
+// uint32 keys with uint32 values, at most 4 passes, cap = the segment's count
+// (n_dev null); the digit histograms are computed here (hist zeroed beforehand)
+cudaError_t radix_sort_u32_pairs_segs(cudaStream_t s, SortSegs g);
 
 // k_supers_to_hist for each view of a batch in one launch (block v: view v).
 struct HistView {

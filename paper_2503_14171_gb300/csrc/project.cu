@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project_views(
         out.rect[o] = v.ntiles ? make_ushort4((unsigned short)rc.x, (unsigned short)rc.y, (unsigned short)rc.z,
                                               (unsigned short)rc.w)
                                : make_ushort4(1, 1, 0, 0);
-        out.key64[o] = ((uint64_t)d.vid << 32) | (v.ntiles > 0 ? __float_as_uint(v.pz) : 0xFFFFFFFFu);
+        out.depth_key[o] = v.ntiles > 0 ? __float_as_uint(v.pz) : 0xFFFFFFFFu;
         out.gidx[o] = (uint32_t)o;
         float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
         if (v.vis)

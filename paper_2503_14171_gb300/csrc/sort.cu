@@ -266,11 +266,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_onesweep(const K* __restrict__ 
 // sorts its own keys with its own digit histogram, look-back states and tile
 // counter exactly as k_onesweep sorts one array.  A segment with fewer passes
 // than the launch's pass index has no blocks.
-template <typename K>
+template <typename K, bool HAS_VAL>
 __global__ void __launch_bounds__(kThreads, 4) k_onesweep_segs(const __grid_constant__ SortSegs g, int pass)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto& S = *reinterpret_cast<OnesweepSmem<K, false>*>(smem_raw);
+    auto& S = *reinterpret_cast<OnesweepSmem<K, HAS_VAL>*>(smem_raw);
     int sg = 0;
     while (sg + 1 < g.count && (int)blockIdx.x >= g.seg[sg + 1].first_block) ++sg;
     const SortSeg& q = g.seg[sg];
@@ -278,9 +278,66 @@ __global__ void __launch_bounds__(kThreads, 4) k_onesweep_segs(const __grid_cons
     uint32_t n = q.cap;
     if (q.n_dev) n = min(n, *q.n_dev);
     const int cur = pass & 1;
-    onesweep_tile<K, false>(S, reinterpret_cast<const K*>(q.keys[cur]), reinterpret_cast<K*>(q.keys[cur ^ 1]),
-                            nullptr, nullptr, n, q.bit_lo + pass * kRadixBits, q.hist + pass * kRadix,
-                            q.status + (size_t)pass * q.tiles * kRadix, q.counters + pass, q.err);
+    onesweep_tile<K, HAS_VAL>(S, reinterpret_cast<const K*>(q.keys[cur]), reinterpret_cast<K*>(q.keys[cur ^ 1]),
+                              HAS_VAL ? q.vals[cur] : nullptr, HAS_VAL ? q.vals[cur ^ 1] : nullptr, n,
+                              q.bit_lo + pass * kRadixBits, q.hist + pass * kRadix,
+                              q.status + (size_t)pass * q.tiles * kRadix, q.counters + pass, q.err);
+}
+
+// Digit histograms of every pass of each segment (blocks [first[s], first[s +
+// 1]) count segment s's keys), accumulated into the segments' zeroed
+// histograms; then one block per (segment, pass) turns them into exclusive
+// prefixes.
+constexpr int kSegHistItems = 16;   // keys per thread of the histogram blocks
+__global__ void __launch_bounds__(kThreads) k_radix_hist_segs(const __grid_constant__ SortSegs g)
+{
+    __shared__ uint32_t s_hist[4][kRadix];
+    int sg = 0;
+    while (sg + 1 < g.count && (int)blockIdx.x >= g.seg[sg + 1].first_block) ++sg;
+    const SortSeg& q = g.seg[sg];
+    const int passes = min(q.passes, 4);
+    for (int i = threadIdx.x; i < 4 * kRadix; i += kThreads) (&s_hist[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t n = q.cap;
+    const uint32_t base = (blockIdx.x - q.first_block) * (uint32_t)(kThreads * kSegHistItems);
+    const uint32_t* keys = reinterpret_cast<const uint32_t*>(q.keys[0]);
+#pragma unroll 4
+    for (int k = 0; k < kSegHistItems; ++k) {
+        const uint32_t i = base + k * kThreads + threadIdx.x;
+        if (i < n) {
+            const uint32_t key = keys[i];
+            for (int p = 0; p < passes; ++p)
+                atomicAdd(&s_hist[p][(key >> (q.bit_lo + p * kRadixBits)) & (kRadix - 1)], 1u);
+        }
+    }
+    __syncthreads();
+    uint32_t* h = const_cast<uint32_t*>(q.hist);
+    for (int i = threadIdx.x; i < passes * kRadix; i += kThreads) {
+        const uint32_t v = (&s_hist[0][0])[i];
+        if (v) atomicAdd(&h[i], v);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_radix_hist_scan_segs(const __grid_constant__ SortSegs g)
+{
+    const int sg = blockIdx.x / 4, p = blockIdx.x % 4;
+    const SortSeg& q = g.seg[sg];
+    if (p >= q.passes) return;
+    __shared__ uint32_t s_warp[kWarps];
+    uint32_t* h = const_cast<uint32_t*>(q.hist) + p * kRadix;
+    const uint32_t v = h[threadIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    uint32_t b = 0;
+    for (int w = 0; w < warp; ++w) b += s_warp[w];
+    h[threadIdx.x] = b + x - v;
 }
 
 template <typename K, bool HAS_VAL>
@@ -608,14 +665,15 @@ cudaError_t launch_supers_to_hist_views(cudaStream_t s, const HistViews& b, int*
     return cudaGetLastError();
 }
 
-cudaError_t radix_sort_u64_segs(cudaStream_t s, SortSegs g)
+template <typename K, bool HAS_VAL>
+cudaError_t radix_sort_segs_impl(cudaStream_t s, SortSegs g)
 {
     int max_passes = 0;
     for (int k = 0; k < g.count; ++k) {
         if (g.seg[k].passes > kMaxPasses) return cudaErrorInvalidValue;
         max_passes = max_passes > g.seg[k].passes ? max_passes : g.seg[k].passes;
     }
-    const size_t smem = sizeof(OnesweepSmem<uint64_t, false>);
+    const size_t smem = sizeof(OnesweepSmem<K, HAS_VAL>);
     for (int p = 0; p < max_passes; ++p) {
         int blocks = 0;
         for (int k = 0; k < g.count; ++k) {
@@ -623,11 +681,33 @@ cudaError_t radix_sort_u64_segs(cudaStream_t s, SortSegs g)
             if (p < g.seg[k].passes) blocks += (int)g.seg[k].tiles;
         }
         if (blocks == 0) continue;
-        k_onesweep_segs<uint64_t><<<blocks, kThreads, smem, s>>>(g, p); note_launch();
+        k_onesweep_segs<K, HAS_VAL><<<blocks, kThreads, smem, s>>>(g, p); note_launch();
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t radix_sort_u64_segs(cudaStream_t s, SortSegs g)
+{
+    return radix_sort_segs_impl<uint64_t, false>(s, g);
+}
+
+cudaError_t radix_sort_u32_pairs_segs(cudaStream_t s, SortSegs g)
+{
+    int blocks = 0;
+    for (int k = 0; k < g.count; ++k) {
+        if (g.seg[k].passes > 4 || g.seg[k].n_dev) return cudaErrorInvalidValue;   // host-known counts, <= 32 bits
+        g.seg[k].first_block = blocks;
+        blocks += (int)((g.seg[k].cap + kThreads * kSegHistItems - 1) / (kThreads * kSegHistItems));
+    }
+    if (blocks > 0) {
+        k_radix_hist_segs<<<blocks, kThreads, 0, s>>>(g); note_launch();
+        k_radix_hist_scan_segs<<<4 * g.count, kThreads, 0, s>>>(g); note_launch();
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return radix_sort_segs_impl<uint32_t, true>(s, g);
 }
 
 uint32_t radix_tiles(uint32_t n)
