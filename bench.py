@@ -626,6 +626,23 @@ def run_gs(args):
         torch.cuda.synchronize()
         tb = [statistics.mean(e[q].elapsed_time(e[q + 1]) for e in bev) for q in range(3)]
         unfused_ms = statistics.mean(e[0].elapsed_time(e[3]) for e in bev)
+        # the recompute variant of the blend adjoint (the tile's forward walk
+        # re-run, the exact state checkpointed per round of candidates)
+        rctx = gs.Context(stream=stream, bwd_recompute=True)
+        rctx.project(dev, cam, LOW_W, LOW_H)
+        rctx.render_binned(grads=True, out_C=C, out_grads=G)
+        rgr = rctx.backward(dout, FACTOR)
+        for _ in range(3):
+            rctx.backward(dout, FACTOR, out=rgr)
+        torch.cuda.synchronize()
+        rev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(kb)]
+        for k in range(kb):
+            rev[k][0].record(stream)
+            rctx.backward(dout, FACTOR, out=rgr)
+            rev[k][1].record(stream)
+        torch.cuda.synchronize()
+        bwd_rec_ms = max_over_ranks(statistics.mean(e[0].elapsed_time(e[1]) for e in rev), "cuda", world)
+        rctx.close()
 
     if rank != 0:
         if world > 1:
@@ -701,6 +718,9 @@ def run_gs(args):
                         "peak_gbs": peaks.get("hbm_gbs"), "peak_source": src},
         "backward": {"ms_per_step": bwd_ms, "steps": kb,
                      "what": "gs_backward: upscale adjoint fused into the blend adjoint, then the projection adjoint",
+                     "recompute_ms_per_step": bwd_rec_ms,
+                     "recompute_what": "the same with GS_FLAG_BWD_RECOMPUTE: each tile's forward walk re-run, the "
+                                       "exact state checkpointed per round of candidates (no stored forward state)",
                      "unfused_ms": unfused_ms,
                      "stages_ms": {"upscale_adjoint": tb[0], "blend_adjoint": tb[1], "project_adjoint": tb[2]},
                      "roofline": {"bound": "alu", "kernel": "k_blend_bwd<3dgs>",

@@ -126,6 +126,18 @@ typedef struct gs_options {
  * be captured in a CUDA graph. */
 #define GS_FLAG_NO_HOST_WAIT 1
 
+/* gs_options.flags: the recompute variant of the blend's adjoint
+ * (gs_render_backward, gs_backward).  Instead of recovering the blend state of
+ * each step by inverting the forward's update from the stored final state
+ * through the whole list (the supplement's inversion trick), the adjoint first
+ * re-runs each tile's forward walk (the transmittance state only, every
+ * decision taken on the same FP32 values) and checkpoints the exact state at
+ * the start of each round of 256 candidates in context scratch (8 per tile,
+ * thinned to every second, fourth, ... round on longer lists); walking back,
+ * every round starts from the exact state at its end.  Needs the projection
+ * only (not the forward's stored state); costs a second walk of each tile. */
+#define GS_FLAG_BWD_RECOMPUTE 2
+
 /* Human-readable name of a status code (static string). */
 const char* gs_status_string(gs_status status);
 

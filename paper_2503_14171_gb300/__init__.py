@@ -32,6 +32,7 @@ GS_MODE_3DGS = 0
 GS_MODE_EXACT = 1
 MODES = {"3dgs": GS_MODE_3DGS, "exact": GS_MODE_EXACT}
 GS_FLAG_NO_HOST_WAIT = 1
+GS_FLAG_BWD_RECOMPUTE = 2
 GS_INJECT_NONE = 0
 GS_INJECT_WAIT_EXPIRY = 1
 GS_INJECT_ALLOC_FAILURE = 2
@@ -298,7 +299,7 @@ class Context:
     """Owns a gs_ctx bound to a torch CUDA stream (default: the current stream)."""
 
     def __init__(self, mode: str | int = "3dgs", bg=(0.0, 0.0, 0.0), stream=None, max_pairs: int = 0,
-                 no_host_wait: bool = False):
+                 no_host_wait: bool = False, bwd_recompute: bool = False):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("libgs needs a CUDA device")
@@ -309,7 +310,8 @@ class Context:
         for k in range(3):
             self.opt.bg[k] = float(bg[k])
         self.opt.max_pairs = int(max_pairs)
-        self.opt.flags = GS_FLAG_NO_HOST_WAIT if no_host_wait else 0
+        self.opt.flags = (GS_FLAG_NO_HOST_WAIT if no_host_wait else 0) | (GS_FLAG_BWD_RECOMPUTE if bwd_recompute
+                                                                          else 0)
         self.h = gs_create(ct.c_void_p(self.stream.cuda_stream), self.opt)
         self.W = self.H = 0
 
@@ -412,7 +414,10 @@ class Context:
                  self.h, "gs_autotune_views")
         return list(ms), int(best.value)
 
-    def set_options(self, mode=None, bg=None, max_pairs=None):
+    def set_options(self, mode=None, bg=None, max_pairs=None, bwd_recompute=None):
+        if bwd_recompute is not None:
+            self.opt.flags = (self.opt.flags & ~GS_FLAG_BWD_RECOMPUTE) | (GS_FLAG_BWD_RECOMPUTE if bwd_recompute
+                                                                          else 0)
         if mode is not None:
             self.opt.mode = MODES[mode] if isinstance(mode, str) else int(mode)
         if bg is not None:

@@ -130,7 +130,8 @@ gs_status check_options(gs_ctx* c, const gs_options* o)
     if (o->tile != kTile) return fail(c, GS_ERR_INVALID_ARG, "tile must be %d", kTile);
     if (o->mode != GS_MODE_3DGS && o->mode != GS_MODE_EXACT) return fail(c, GS_ERR_INVALID_ARG, "bad mode");
     if (o->max_pairs < 0) return fail(c, GS_ERR_INVALID_ARG, "max_pairs < 0");
-    if (o->flags & ~GS_FLAG_NO_HOST_WAIT) return fail(c, GS_ERR_INVALID_ARG, "unknown flags 0x%x", o->flags);
+    if (o->flags & ~(GS_FLAG_NO_HOST_WAIT | GS_FLAG_BWD_RECOMPUTE))
+        return fail(c, GS_ERR_INVALID_ARG, "unknown flags 0x%x", o->flags);
     return GS_OK;
 }
 
@@ -538,7 +539,7 @@ gs_status gs_destroy(gs_ctx* c)
                       &c->errword, &c->grad2d, &c->pair_check, &c->tile_work, &c->tile_order,
                       &c->vrec0, &c->vrec1, &c->vrec2, &c->vrect, &c->vsupers, &c->vkey, &c->vtotals,
                       &c->views_dev, &c->vpairs0, &c->vpairs1, &c->vsranges, &c->vwork, &c->vorder, &c->vqueue,
-                      &c->vsortv, &c->vcounts, &c->vhist, &c->vstatus, &c->vdhist, &c->vdstatus};
+                      &c->vsortv, &c->vcounts, &c->vhist, &c->vstatus, &c->vdhist, &c->vdstatus, &c->ckpt};
     for (DevBuf* b : bufs) release(*b);
     if (c->h_scalar) cudaFreeHost(c->h_scalar);
     if (c->totals_ready) cudaEventDestroy(c->totals_ready);
@@ -748,8 +749,13 @@ gs_status do_render_backward(gs_ctx* c, const float* dC, const float* dG, float*
                              int factor = 0)
 {
     if ((!dC && !dout) || !grad2d) return fail(c, GS_ERR_INVALID_ARG, "dL_dC and grad2d are required");
-    if (!c->have_proj || !c->have_state || !c->state_grads)
+    const bool recompute = (c->opt.flags & GS_FLAG_BWD_RECOMPUTE) != 0;
+    if (!c->have_proj || (!recompute && (!c->have_state || !c->state_grads)))
         return fail(c, GS_ERR_NOT_READY, "no derivative blend since the last projection");
+    gs_status st;
+    if (recompute &&
+        (st = ensure(c, c->ckpt, sizeof(float4) * kCkSlots * kTilePixels * (size_t)c->tiles_x * c->tiles_y)))
+        return st;
     if (c->n > 0) GS_CUDA(c, cudaMemsetAsync(grad2d, 0, sizeof(float) * 9 * (size_t)c->n, c->stream));
     BlendBwdArgs a;
     a.W = c->W;
@@ -775,6 +781,7 @@ gs_status do_render_backward(gs_ctx* c, const float* dC, const float* dG, float*
     // the forward blend's tile order of this frame (heaviest first)
     a.order = c->work_tiles == (int64_t)c->tiles_x * c->tiles_y && c->tile_order.p ? as<uint32_t>(c->tile_order)
                                                                                    : nullptr;
+    a.ckpt = recompute ? as<float4>(c->ckpt) : nullptr;
     GS_CUDA(c, launch_blend_backward(c->stream, c->opt.mode, a));
     return GS_OK;
 }
@@ -810,7 +817,8 @@ gs_status gs_backward(gs_ctx* c, const float* dL_dout, int32_t factor, const gs_
     if (!c) return GS_ERR_INVALID_ARG;
     LaunchTally tally(c);
     if (!dL_dout || !out) return fail(c, GS_ERR_INVALID_ARG, "dL_dout and out are required");
-    if (!c->have_proj || !c->have_state || !c->state_grads)
+    if (!c->have_proj ||
+        (!(c->opt.flags & GS_FLAG_BWD_RECOMPUTE) && (!c->have_state || !c->state_grads)))
         return fail(c, GS_ERR_NOT_READY, "no derivative blend since the last projection");
     if (c->W < 2 || c->H < 2) return fail(c, GS_ERR_INVALID_ARG, "upscale needs W, H >= 2");
     if (factor < 1 || factor > 16) return fail(c, GS_ERR_INVALID_ARG, "factor must be in 1..16");
@@ -908,7 +916,9 @@ gs_status reserve_impl(gs_ctx* c, int64_t n, int32_t V, int32_t W, int32_t H, in
         (st = ensure(c, c->tile_count, sizeof(uint32_t) * T)) || (st = ensure(c, c->tile_start, sizeof(uint32_t) * T)) ||
         (st = ensure(c, c->tile_work, sizeof(uint32_t) * T)) || (st = ensure(c, c->tile_order, sizeof(uint32_t) * T)) ||
         (st = ensure(c, c->grad2d, sizeof(float) * 9 * un)) ||
-        (st = ensure(c, c->pair_check, sizeof(PairCheckOut))))
+        (st = ensure(c, c->pair_check, sizeof(PairCheckOut))) ||
+        ((c->opt.flags & GS_FLAG_BWD_RECOMPUTE) &&
+         (st = ensure(c, c->ckpt, sizeof(float4) * kCkSlots * kTilePixels * (size_t)T))))
         return st;
     if (V > 0) {
         const size_t vn = un * (size_t)V;

@@ -20,10 +20,10 @@ namespace gs {
 namespace {
 
 // COUNT: also accumulate per-super-tile pair counts (shared memory, then one
-// atomic per touched super-tile and block).
-template <bool COUNT>
+// atomic per touched super-tile and block).  KS: the super-tile side (1, 2, 4).
+template <bool COUNT, int KS>
 __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ ids, const uint32_t* __restrict__ offsets,
-                                              const ushort4* __restrict__ rect, uint32_t n, int ks, int stiles_x,
+                                              const ushort4* __restrict__ rect, uint32_t n, int stiles_x,
                                               uint64_t* __restrict__ pairs, uint32_t* __restrict__ counts,
                                               uint32_t Ts, uint32_t cap, uint32_t id_base, bool rebase)
 {
@@ -40,15 +40,16 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ ids, 
         const uint32_t id = ids[k] - id_base;
         if (off < end && id < n) {   // id >= n only after an expired bounded wait in the sort
             const ushort4 r = rect[id];
-            const int sx0 = r.x / ks, sx1 = r.z / ks, sy0 = r.y / ks, sy1 = r.w / ks;
+            constexpr int ks = KS, ksh = KS == 4 ? 2 : KS == 2 ? 1 : 0;
+            const int sx0 = r.x >> ksh, sx1 = r.z >> ksh, sy0 = r.y >> ksh, sy1 = r.w >> ksh;
             for (int sy = sy0; sy <= sy1; ++sy) {
                 // rows of the super-tile's ks x ks tiles inside the rect
-                const int ly0 = max((int)r.y - sy * ks, 0), ly1 = min((int)r.w - sy * ks, ks - 1);
+                const int ly0 = max((int)r.y - (sy << ksh), 0), ly1 = min((int)r.w - (sy << ksh), ks - 1);
                 for (int sx = sx0; sx <= sx1 && off < end; ++sx) {
-                    const int lx0 = max((int)r.x - sx * ks, 0), lx1 = min((int)r.z - sx * ks, ks - 1);
+                    const int lx0 = max((int)r.x - (sx << ksh), 0), lx1 = min((int)r.z - (sx << ksh), ks - 1);
                     const uint32_t cols = ((2u << lx1) - 1u) & ~((1u << lx0) - 1u);
                     uint32_t mask = 0;
-                    for (int ly = ly0; ly <= ly1; ++ly) mask |= cols << (ks * ly);
+                    for (int ly = ly0; ly <= ly1; ++ly) mask |= cols << (ly << ksh);
                     const uint32_t s = (uint32_t)(sy * stiles_x + sx);
                     if (off < cap) pairs[off] = ((uint64_t)mask << 48) | ((uint64_t)s << 32) | id;
                     ++off;
@@ -102,16 +103,16 @@ __global__ void __launch_bounds__(256) k_emit_views(const __grid_constant__ Emit
         const uint32_t id = g - e.start;
         if (off < end && id < e.n) {   // id >= n only after an expired bounded wait in the sort
             const ushort4 r = rect[g];
-            const int ks = e.ks;
-            const int sx0 = r.x / ks, sx1 = r.z / ks, sy0 = r.y / ks, sy1 = r.w / ks;
+            const int ks = e.ks, ksh = __ffs(ks) - 1;
+            const int sx0 = r.x >> ksh, sx1 = r.z >> ksh, sy0 = r.y >> ksh, sy1 = r.w >> ksh;
             uint32_t* gcnt = e.counts + (size_t)(blockIdx.x % kCountCopies) * e.Ts;
             for (int sy = sy0; sy <= sy1; ++sy) {
-                const int ly0 = max((int)r.y - sy * ks, 0), ly1 = min((int)r.w - sy * ks, ks - 1);
+                const int ly0 = max((int)r.y - (sy << ksh), 0), ly1 = min((int)r.w - (sy << ksh), ks - 1);
                 for (int sx = sx0; sx <= sx1 && off < end; ++sx) {
-                    const int lx0 = max((int)r.x - sx * ks, 0), lx1 = min((int)r.z - sx * ks, ks - 1);
+                    const int lx0 = max((int)r.x - (sx << ksh), 0), lx1 = min((int)r.z - (sx << ksh), ks - 1);
                     const uint32_t cols = ((2u << lx1) - 1u) & ~((1u << lx0) - 1u);
                     uint32_t mask = 0;
-                    for (int ly = ly0; ly <= ly1; ++ly) mask |= cols << (ks * ly);
+                    for (int ly = ly0; ly <= ly1; ++ly) mask |= cols << (ly << ksh);
                     const uint32_t st = (uint32_t)(sy * e.stiles_x + sx);
                     if (off < e.cap) e.pairs[off] = ((uint64_t)mask << 48) | ((uint64_t)st << 32) | id;
                     ++off;
@@ -166,7 +167,8 @@ __global__ void __launch_bounds__(256) k_tile_lists(const uint64_t* __restrict__
     __shared__ int s_wcnt[8];
     const int t = blockIdx.x;
     const int tx = t % tiles_x, ty = t / tiles_x;
-    const uint2 sr = sranges[(ty / ks) * stiles_x + tx / ks];
+    const int ksh = __ffs(ks) - 1;
+    const uint2 sr = sranges[(ty >> ksh) * stiles_x + (tx >> ksh)];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t base = WRITE ? tile_start[t] : 0u;
     for (uint32_t c0 = sr.x; c0 < sr.y; c0 += 256) {
@@ -286,12 +288,18 @@ cudaError_t launch_emit_pairs(cudaStream_t s, const uint32_t* ids, const uint32_
                               uint32_t cap, uint32_t id_base, bool rebase)
 {
     if (n == 0) return cudaSuccess;
-    if (counts && Ts <= (uint32_t)kMaxSupersForCounts)
-        k_emit<true><<<(n + 255) / 256, 256, 0, s>>>(ids, offsets, rect, n, ks, stiles_x, pairs, counts, Ts, cap,
-                                                     id_base, rebase);
-    else
-        k_emit<false><<<(n + 255) / 256, 256, 0, s>>>(ids, offsets, rect, n, ks, stiles_x, pairs, nullptr, 0, cap,
-                                                      id_base, rebase);
+    const bool cnt = counts && Ts <= (uint32_t)kMaxSupersForCounts;
+#define GS_EMIT(C, K)                                                                                         \
+    k_emit<C, K><<<(n + 255) / 256, 256, 0, s>>>(ids, offsets, rect, n, stiles_x, pairs, C ? counts : nullptr, \
+                                                 C ? Ts : 0u, cap, id_base, rebase)
+    if (ks == 1) {
+        if (cnt) GS_EMIT(true, 1); else GS_EMIT(false, 1);
+    } else if (ks == 2) {
+        if (cnt) GS_EMIT(true, 2); else GS_EMIT(false, 2);
+    } else {
+        if (cnt) GS_EMIT(true, 4); else GS_EMIT(false, 4);
+    }
+#undef GS_EMIT
     note_launch();
     return cudaGetLastError();
 }

@@ -150,7 +150,8 @@ __device__ __forceinline__ void blend_tile(const BlendArgs& a, int tile, unsigne
     const float px = (float)x, py = (float)y;
     const uint32_t lanemask_lt = (1u << lane) - 1u;
 
-    const int S = (ty / a.ks) * a.stiles_x + (tx / a.ks);
+    const int ksh = __ffs(a.ks) - 1;   // ks = 1, 2 or 4
+    const int S = (ty >> ksh) * a.stiles_x + (tx >> ksh);
     const uint2 sr = a.sranges[S];
     const int total = (int)(sr.y - sr.x);
 

@@ -21,10 +21,22 @@
 // then to the mean and the conic by differentiating g, g_x, g_y, g_xy = -b.
 // A clamped alpha (0.99) is a constant: no gradient to sigma or the geometry.
 //
-// The state before each step is recovered from the state after it (the stored
-// final state for the last one) by inverting the update: T = T'/(1 - alpha),
-// T_x = (T_x' + alpha T g_x)/(1 - alpha), ... (the supplement's inversion trick
-// written for T = 1 - A).
+// The state before each step is recovered from the state after it by
+// inverting the update: T = T'/(1 - alpha), T_x = (T_x' + alpha T g_x)/(1 -
+// alpha), ... (the supplement's inversion trick written for T = 1 - A).  Two
+// variants anchor that walk:
+//  * inversion: from the final state the forward blend stored, through the
+//    whole list (each alpha = 0.99 step scales the rounding of the recovered
+//    state by up to 100, and such factors compound along the list);
+//  * recompute: the block first re-runs the forward walk of its tile (the
+//    transmittance state alone, every decision on the same FP32 values as the
+//    forward) and checkpoints the exact state at the start of each round of
+//    candidates; walking back, each round starts from the exact state at its
+//    end, so the inversion spans one round's entries (about 60 at the 960 x
+//    540 workload) instead of the whole list.  The forward's stored state and
+//    counts are not used (the recomputed ones are).  Checkpoints go to global
+//    scratch, kCkSlots per tile; a tile with more rounds keeps every second
+//    one, then every fourth, ...
 //
 // Algorithmic work (FP32 operations, FMA = 2) per blended pair: g_x, g_y, g_xy'
 // 9; the state before the step 19; the weights w.. 14; dL/dc 21; G_w.. 24;
@@ -159,10 +171,46 @@ __device__ __forceinline__ void warp_sum9_to_shared(float v[9], int lane, float*
     if (lane == 0) atomicAdd(&acc[8], t8);
 }
 
+// The forward blend's step of the transmittance state alone (same expressions
+// and decisions as the forward).  Returns true if the pair was blended; sets
+// done when the pixel stops before it.
+template <int MODE>
+__device__ __forceinline__ bool fwd_state_step(BwdPixel& p, bool& done, const float4& r0, const float4& r1, float sigma)
+{
+    const float dx = p.px - r0.x, dy = p.py - r0.y;
+    const float g2 = exponent2(r1, dx, dy);
+    if (MODE == GS_MODE_3DGS && g2 < r1.w) return false;
+    float alpha = sigma * pow2(g2);
+    bool clamped = false;
+    if (MODE == GS_MODE_3DGS) {
+        if (alpha < (1.f / 255.f)) return false;
+        clamped = alpha > 0.99f;
+        alpha = fminf(alpha, 0.99f);
+    }
+    const float Tn = p.T * (1.f - alpha);
+    if (MODE == GS_MODE_3DGS && Tn < 1e-4f) {
+        done = true;
+        return false;
+    }
+    const float bn = r1.y * kLn2;
+    float gx = fmaf(r0.z, dx, bn * dy);
+    float gy = fmaf(r0.w, dy, bn * dx);
+    float gxy = fmaf(gx, gy, bn);
+    if (clamped) { gx = 0.f; gy = 0.f; gxy = 0.f; }
+    const float wx = alpha * fmaf(p.T, gx, p.Tx);
+    const float wy = alpha * fmaf(p.T, gy, p.Ty);
+    const float wxy = alpha * (p.T * gxy + p.Tx * gy + p.Ty * gx + p.Txy);
+    p.Tx -= wx;
+    p.Ty -= wy;
+    p.Txy -= wxy;
+    p.T = Tn;
+    return true;
+}
+
 // Four blocks per SM: the register cap of 64 costs the 3DGS instantiation 20 B
 // of spills, and the fourth block's warps hide more of the gather and
 // barrier latency than the spills add.
-template <int MODE>
+template <int MODE, bool RECOMPUTE>
 __global__ void __launch_bounds__(kThreads, 4) k_blend_bwd(BlendBwdArgs a)
 {
     __shared__ float4 s_r0[kCand];
@@ -194,9 +242,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_bwd(BlendBwdArgs a)
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) { p.uC[ch] = 0.f; p.uX[ch] = 0.f; p.uY[ch] = 0.f; p.uZ[ch] = 0.f; }
     if (inside) {
-        p.last = a.count[pix];
-        const float4 st = a.state[pix];
-        p.T = st.x; p.Tx = st.y; p.Ty = st.z; p.Txy = st.w;
+        if (!RECOMPUTE) {
+            p.last = a.count[pix];
+            const float4 st = a.state[pix];
+            p.T = st.x; p.Tx = st.y; p.Ty = st.z; p.Txy = st.w;
+        }
         if (a.dout) {   // the upscale's adjoint at this pixel, fused
             float acc[3][4];
             upscale_adjoint_at(a.dout, a.W, a.H, a.W2, a.H2, x, y, acc);
@@ -225,26 +275,82 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_bwd(BlendBwdArgs a)
     p.lTy = p.uY[0] * a.bg.x + p.uY[1] * a.bg.y + p.uY[2] * a.bg.z;
     p.lTxy = p.uZ[0] * a.bg.x + p.uZ[1] * a.bg.y + p.uZ[2] * a.bg.z;
 
+#pragma unroll
+    for (int q = 0; q < 9; ++q) s_acc[threadIdx.x][q] = 0.f;
+
+    const int ksh = __ffs(a.ks) - 1;   // ks = 1, 2 or 4
+    const int S = (ty >> ksh) * a.stiles_x + (tx >> ksh);
+    const uint2 sr = a.sranges[S];
+    const int total = (int)(sr.y - sr.x);
+    const int tbit = (ty & (a.ks - 1)) * a.ks + (tx & (a.ks - 1));   // this tile in the pair masks
+
+    int filt = 0, R = 0;
+    int ck_stride = 1, ck_used = 0;   // recompute: checkpoint of round r in slot r / ck_stride
+    float4* ck = RECOMPUTE ? a.ckpt + (size_t)tile * kCkSlots * kThreads + threadIdx.x : nullptr;
+    if (RECOMPUTE) {
+        // pass 1: the forward walk of the tile (transmittance state and counts),
+        // round by round, with the exact state checkpointed at round starts
+        bool done = !inside;
+        for (int c0 = 0; c0 < total; c0 += kCand, ++R) {
+            if (__syncthreads_count(done) == kThreads) break;
+            if (R % kMaxRounds == 0) {
+                if (R / kMaxRounds >= kMaxSegs) {
+                    if (threadIdx.x == 0) atomicExch(a.err, kDevCheck);
+                    break;
+                }
+                if (threadIdx.x == 0) s_seg[R / kMaxRounds] = filt;
+            }
+            if (threadIdx.x == 0) s_round[R % kMaxRounds] = filt;
+            if (R % ck_stride == 0) {
+                if (R / ck_stride == kCkSlots) {   // full: keep every second checkpoint
+#pragma unroll 1
+                    for (int j = 1; j < kCkSlots / 2; ++j) ck[(size_t)j * kThreads] = ck[(size_t)(2 * j) * kThreads];
+                    ck_stride *= 2;
+                }
+                if (R % ck_stride == 0) {
+                    ck[(size_t)(R / ck_stride) * kThreads] = make_float4(p.T, p.Tx, p.Ty, p.Txy);
+                    ck_used = R / ck_stride + 1;
+                }
+            }
+            const int c = c0 + (int)threadIdx.x;
+            uint32_t id = 0xFFFFFFFFu;
+            bool hit = false;
+            if (c < total) hit = pair_hit(a.pair_words, sr.x + c, a.n, tbit, id);
+            const uint32_t ball = __ballot_sync(0xffffffffu, hit);
+            if (lane == 0) s_wcnt[warp] = __popc(ball);
+            __syncthreads();
+            int wbase = 0, tot = 0;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) {
+                const int cw = s_wcnt[w];
+                wbase += w < warp ? cw : 0;
+                tot += cw;
+            }
+            if (hit) {
+                const int k = wbase + __popc(ball & lanemask_lt);
+                s_r0[k] = a.rec.r0[id];
+                s_r1[k] = a.rec.r1[id];
+                s_r2[k].w = a.rec.r2[id].w;
+            }
+            __syncthreads();
+            for (int k = 0; k < tot && !done; ++k)
+                if (fwd_state_step<MODE>(p, done, s_r0[k], s_r1[k], s_r2[k].w)) p.last = filt + k + 1;
+            filt += tot;
+        }
+        __syncthreads();
+    }
     // the block's longest prefix of the tile list
     int m = p.last;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (lane == 0) s_max[warp] = m;
-#pragma unroll
-    for (int q = 0; q < 9; ++q) s_acc[threadIdx.x][q] = 0.f;
     __syncthreads();
     int M = 0;
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) M = max(M, s_max[w]);
 
-    const int S = (ty / a.ks) * a.stiles_x + (tx / a.ks);
-    const uint2 sr = a.sranges[S];
-    const int total = (int)(sr.y - sr.x);
-    const int tbit = (ty & (a.ks - 1)) * a.ks + (tx & (a.ks - 1));   // this tile in the pair masks
-
-    // pass 1: the tile's list position at the start of each round of candidates
-    int filt = 0, R = 0;
-    for (int c0 = 0; c0 < total && filt < M; c0 += kCand, ++R) {
+    // pass 1 (inversion): the tile's list position at the start of each round of candidates
+    for (int c0 = 0; !RECOMPUTE && c0 < total && filt < M; c0 += kCand, ++R) {
         if (R % kMaxRounds == 0) {
             if (R / kMaxRounds >= kMaxSegs) break;
             if (threadIdx.x == 0) s_seg[R / kMaxRounds] = filt;
@@ -298,6 +404,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_bwd(BlendBwdArgs a)
         __syncthreads();
         for (int r = re - 1; r >= rb; --r) {
             const int fb = s_round[r - rb];
+            if (RECOMPUTE && r + 1 < R && (r + 1) % ck_stride == 0 && (r + 1) / ck_stride < ck_used) {
+                // the exact state at the end of this round (the next round's start)
+                const float4 st = ck[(size_t)((r + 1) / ck_stride) * kThreads];
+                p.T = st.x; p.Tx = st.y; p.Ty = st.z; p.Txy = st.w;
+            }
             const int c = r * kCand + (int)threadIdx.x;
             uint32_t id = 0xFFFFFFFFu;
             bool hit = false;
@@ -351,10 +462,17 @@ cudaError_t launch_blend_backward(cudaStream_t s, int mode, const BlendBwdArgs& 
 {
     const int tiles = a.tiles_x * ((a.H + kTile - 1) / kTile);
     if (tiles == 0) return cudaSuccess;
-    if (mode == GS_MODE_EXACT)
-        k_blend_bwd<GS_MODE_EXACT><<<tiles, kThreads, 0, s>>>(a);
-    else
-        k_blend_bwd<GS_MODE_3DGS><<<tiles, kThreads, 0, s>>>(a);
+    if (a.ckpt) {
+        if (mode == GS_MODE_EXACT)
+            k_blend_bwd<GS_MODE_EXACT, true><<<tiles, kThreads, 0, s>>>(a);
+        else
+            k_blend_bwd<GS_MODE_3DGS, true><<<tiles, kThreads, 0, s>>>(a);
+    } else {
+        if (mode == GS_MODE_EXACT)
+            k_blend_bwd<GS_MODE_EXACT, false><<<tiles, kThreads, 0, s>>>(a);
+        else
+            k_blend_bwd<GS_MODE_3DGS, false><<<tiles, kThreads, 0, s>>>(a);
+    }
     note_launch();
     return cudaGetLastError();
 }

@@ -119,7 +119,11 @@ struct BlendBwdArgs {
     float* grad2d;                 // [n][9]
     int* err;
     const uint32_t* order;         // optional: tiles in this order (the forward's, heaviest first)
+    // recompute variant (when not null): per tile kCkSlots x 256 checkpointed
+    // states; state and count above are then not read
+    float4* ckpt;
 };
+constexpr int kCkSlots = 8;   // checkpoints per tile of the recompute variant of the blend adjoint
 
 }  // namespace gs
 
@@ -172,6 +176,7 @@ struct gs_ctx {
     gs_gaussians last_g{};              // inputs and camera of the last projection
     gs::CameraParams last_cam{};
     gs::DevBuf grad2d;                  // float[n][9]
+    gs::DevBuf ckpt;                    // float4[tiles][kCkSlots][256]: the recompute adjoint's checkpoints
     // frames without a host wait (GS_FLAG_NO_HOST_WAIT): buffers reserved up front
     bool reserved = false;
     int64_t res_n = 0, res_pixels = 0, res_tiles = 0, res_supers = 0, res_pairs = 0;

@@ -189,7 +189,8 @@ __device__ __forceinline__ ViewProj project_view(float mx3, float my3, float mz3
     o.rad = rad;
     o.rc = rc;
     o.ntiles = ntiles;
-    o.nsup = ntiles ? (uint32_t)((rc.z / ks - rc.x / ks + 1) * (rc.w / ks - rc.y / ks + 1)) : 0u;
+    const int ksh = __ffs(ks) - 1;   // ks = 1, 2 or 4
+    o.nsup = ntiles ? (uint32_t)(((rc.z >> ksh) - (rc.x >> ksh) + 1) * ((rc.w >> ksh) - (rc.y >> ksh) + 1)) : 0u;
     o.vis = vis;
     return o;
 }

@@ -8,6 +8,8 @@
 // Every wait on another block is bounded: after kSpinLimit polls the block
 // records kDevTimeout in the context's error word and proceeds (its output is
 // then undefined, the GPU is never hung).
+#include <atomic>
+
 #include "gs_internal.cuh"
 #include "tile_order.cuh"
 
@@ -245,6 +247,9 @@ __device__ __forceinline__ void onesweep_tile(OnesweepSmem<K, HAS_VAL>& S, const
     }
 }
 
+// The single-array pass (the same steps as onesweep_tile, kept as one kernel
+// body: its own code measured 4 us faster per 2.5M-pair pass than a call of
+// the shared tile function).
 template <typename K, bool HAS_VAL>
 __global__ void __launch_bounds__(kThreads, 4) k_onesweep(const K* __restrict__ keys_in, K* __restrict__ keys_out,
                                                        const uint32_t* __restrict__ vals_in,
@@ -256,9 +261,140 @@ __global__ void __launch_bounds__(kThreads, 4) k_onesweep(const K* __restrict__ 
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto& S = *reinterpret_cast<OnesweepSmem<K, HAS_VAL>*>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (n_dev) n = min(n, *n_dev);   // key count known on the device only; surplus tiles exit
-    onesweep_tile<K, HAS_VAL>(S, keys_in, keys_out, vals_in, vals_out, n, shift, digit_base, status, tile_counter,
-                              err);
+
+    for (int i = tid; i < kWarps * kRadix; i += kThreads) (&S.warp_hist[0][0])[i] = 0;
+    if (tid == 0) S.tile = atomicAdd(tile_counter, 1u);   // tiles are taken in launch order
+    __syncthreads();
+    const uint32_t tile = S.tile;
+    const uint32_t base = tile * (uint32_t)kTileKeys;
+    if (base >= n) return;
+
+    K key[kItems];
+    uint32_t val[kItems];
+    uint32_t dig[kItems];
+    uint32_t rank[kItems];
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+        const uint32_t idx = base + warp * (kItems * 32) + i * 32 + lane;
+        const bool valid = idx < n;
+        key[i] = valid ? keys_in[idx] : K(0);
+        if (HAS_VAL) val[i] = valid ? vals_in[idx] : 0u;
+        dig[i] = valid ? digit_of(key[i], shift) : (uint32_t)kRadix;
+    }
+    // warp multi-split: rank among earlier keys of the same digit in this warp;
+    // the lanes sharing a digit are found with one ballot per digit bit
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+        const uint32_t d = dig[i];
+        uint32_t peers = __ballot_sync(0xffffffffu, d < (uint32_t)kRadix);
+#pragma unroll
+        for (int b = 0; b < kRadixBits; ++b) {
+            const bool bit = (d >> b) & 1u;
+            const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+            peers &= bit ? bal : ~bal;
+        }
+        const int leader = 31 - __clz(peers);
+        uint32_t prev = 0;
+        if (d < (uint32_t)kRadix) prev = S.warp_hist[warp][d];
+        rank[i] = prev + __popc(peers & lt);
+        __syncwarp();
+        if (lane == leader && d < (uint32_t)kRadix) S.warp_hist[warp][d] = prev + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+
+    // thread d: per-warp exclusive prefix for digit d and the tile's count
+    const uint32_t d = tid;
+    uint32_t total = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+        const uint32_t c = S.warp_hist[w][d];
+        S.warp_hist[w][d] = total;
+        total += c;
+    }
+    volatile uint32_t* st = status + (size_t)tile * kRadix + d;
+    *st = (tile == 0 ? kFlagInc : kFlagAgg) | total;
+
+    // exclusive scan of the tile's digit counts
+    uint32_t x = total;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) S.warp_tot[warp] = x;
+    __syncthreads();
+    uint32_t wbase = 0;
+    for (int w = 0; w < warp; ++w) wbase += S.warp_tot[w];
+    const uint32_t local_start = wbase + x - total;
+    S.local_start[d] = local_start;
+
+    // decoupled look-back over earlier tiles for digit d, kLookback tiles per
+    // round trip (tiles before 0 read as an inclusive zero)
+    uint32_t excl = 0;
+    if (tile > 0) {
+        long spins = 0;
+        int j = (int)tile - 1;
+        while (true) {
+            uint32_t sw[kLookback];
+#pragma unroll
+            for (int w = 0; w < kLookback; ++w)
+                sw[w] = j - w >= 0 ? *(volatile const uint32_t*)(status + (size_t)(j - w) * kRadix + d) : kFlagInc;
+            int used = 0;
+            bool inc = false, blocked = false;
+#pragma unroll
+            for (int w = 0; w < kLookback; ++w) {
+                if (inc || blocked) continue;
+                const uint32_t f = sw[w] & ~kValueMask;
+                if (f == 0u) {
+                    blocked = true;
+                    continue;
+                }
+                excl += sw[w] & kValueMask;
+                ++used;
+                inc = f == kFlagInc;
+            }
+            if (inc) break;
+            j -= used;
+            if (blocked && ++spins > kSpinLimit) {
+                atomicExch(err, kDevTimeout);
+                break;
+            }
+        }
+        *st = kFlagInc | ((excl + total) & kValueMask);
+    }
+    S.global_base[d] = digit_base[d] + excl - local_start;
+    __syncthreads();
+
+    // stage keys in digit order
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+        const uint32_t dd = dig[i];
+        if (dd < (uint32_t)kRadix) {
+            const uint32_t lp = S.local_start[dd] + S.warp_hist[warp][dd] + rank[i];
+            S.keys[lp] = key[i];
+            if (HAS_VAL) S.vals[lp] = val[i];
+        }
+    }
+    __syncthreads();
+    const uint32_t count = min((uint32_t)kTileKeys, n - base);
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+        const uint32_t p = i * kThreads + tid;
+        if (p < count) {
+            const K k = S.keys[p];
+            const uint32_t g = S.global_base[digit_of(k, shift)] + p;
+            if (g < n) {
+                keys_out[g] = k;
+                if (HAS_VAL) vals_out[g] = S.vals[p];
+            } else {   // inconsistent look-back state: report instead of writing out of bounds
+                atomicExch(err, kDevCheck);
+            }
+        }
+    }
 }
 
 // One pass over several independent key arrays (the pair lists of a batch of
@@ -340,6 +476,28 @@ __global__ void __launch_bounds__(kThreads) k_radix_hist_scan_segs(const __grid_
     h[threadIdx.x] = b + x - v;
 }
 
+// The one-sweep kernels' dynamic shared memory attribute, set once per device
+// (an atomic bit per device: concurrent first calls set the same value).
+template <typename K, bool HAS_VAL>
+cudaError_t onesweep_attr()
+{
+    static std::atomic<uint64_t> done{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = dev < 64 ? (uint64_t(1) << dev) : 0;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    const int smem = (int)sizeof(OnesweepSmem<K, HAS_VAL>);
+    if ((e = cudaFuncSetAttribute(k_onesweep<K, HAS_VAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_onesweep_segs<K, HAS_VAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
+        cudaSuccess)
+        return e;
+    done.fetch_or(bit, std::memory_order_acq_rel);
+    return cudaSuccess;
+}
+
 template <typename K, bool HAS_VAL>
 cudaError_t radix_sort_impl(cudaStream_t s, K* keys[2], uint32_t* vals[2], uint32_t n, int bit_lo, int bit_hi,
                             uint32_t* hist, uint32_t* status, uint32_t* counters, int* err, int* out_idx,
@@ -365,7 +523,7 @@ cudaError_t radix_sort_impl(cudaStream_t s, K* keys[2], uint32_t* vals[2], uint3
         k_radix_hist_scan<<<passes, kThreads, 0, s>>>(hist); note_launch();
     }
     const size_t smem = sizeof(OnesweepSmem<K, HAS_VAL>);
-    static_assert(sizeof(OnesweepSmem<uint64_t, true>) <= 48 * 1024, "dynamic shared memory within the default limit");
+    if ((e = onesweep_attr<K, HAS_VAL>()) != cudaSuccess) return e;
     int cur = 0;
     for (int p = 0; p < passes; ++p) {
         const int shift = bit_lo + p * kRadixBits;
@@ -674,6 +832,8 @@ cudaError_t radix_sort_segs_impl(cudaStream_t s, SortSegs g)
         max_passes = max_passes > g.seg[k].passes ? max_passes : g.seg[k].passes;
     }
     const size_t smem = sizeof(OnesweepSmem<K, HAS_VAL>);
+    cudaError_t ea = onesweep_attr<K, HAS_VAL>();
+    if (ea != cudaSuccess) return ea;
     for (int p = 0; p < max_passes; ++p) {
         int blocks = 0;
         for (int k = 0; k < g.count; ++k) {

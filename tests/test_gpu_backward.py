@@ -2,6 +2,10 @@
 kernel, through the C ABI, against the FP64 oracle's adjoint on the same
 upstream gradient.
 
+Both variants of the blend adjoint are checked: the inversion trick from the
+forward's stored final state, and the recompute variant (the tile's forward
+walk re-run, the exact state checkpointed at each round of candidates).
+
 Tolerances: gradients are sums of many FP32 terms (per pixel a back-to-front
 sweep with the state recovered by dividing by 1 - alpha, then atomics across
 pixels), so a Gaussian's gradient is compared as
@@ -73,8 +77,12 @@ CASES = [
 ]
 
 
+VARIANTS = ["inversion", "recompute"]
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("name,kw,W,H,mode,bg", CASES)
-def test_render_backward(gs, ora, name, kw, W, H, mode, bg):
+def test_render_backward(gs, ora, name, kw, W, H, mode, bg, variant):
     scene = scenes.random_scene(**kw)
     cam = scenes.pinhole_camera(W, H)
     m = 0 if mode == "3dgs" else 1
@@ -90,7 +98,7 @@ def test_render_backward(gs, ora, name, kw, W, H, mode, bg):
         uC = uC * keep
         uG = uG * keep
     want = ora.render_adjoint(proj, bins, (uC, uG), bg=bg)["g2d"]
-    with gs.Context(mode=mode, bg=bg) as ctx:
+    with gs.Context(mode=mode, bg=bg, bwd_recompute=variant == "recompute") as ctx:
         ctx.render_with_grads(gs.DeviceScene(scene), cam, W, H)
         got = ctx.render_backward(_t(uC), _t(uG)).cpu().numpy()
         ctx.synchronize()
@@ -143,7 +151,8 @@ def test_project_backward(gs, ora, sh):
 
 # ---------------------------------------------------------------- chain
 
-def test_backward_chain_exact(gs, ora):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_backward_chain_exact(gs, ora, variant):
     """gs_backward (upscale -> blend -> projection adjoints in one call) against
     the oracle's chained adjoints, exact mode (no near-threshold decisions)."""
     n, W, H, s = 300, 40, 32, 2
@@ -156,7 +165,7 @@ def test_backward_chain_exact(gs, ora):
     dC, dG = ora.upscale_adjoint(dout.astype(np.float64), W, H)
     g2d = ora.render_adjoint(proj, bins, (dC, dG), bg=bg)["g2d"]
     want = ora.project_adjoint(scene, cam, W, H, g2d)
-    with gs.Context(mode="exact", bg=bg) as ctx:
+    with gs.Context(mode="exact", bg=bg, bwd_recompute=variant == "recompute") as ctx:
         ctx.render_with_grads(gs.DeviceScene(scene), cam, W, H)
         got = {k: v.cpu().numpy() for k, v in ctx.backward(_t(dout), s).items()}
         ctx.synchronize()
@@ -165,8 +174,9 @@ def test_backward_chain_exact(gs, ora):
         assert bad == 0, (key, bad, worst)
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("mode,s", [("3dgs", 2), ("3dgs", 3), ("exact", 2)])
-def test_fused_backward_equals_chain(gs, mode, s):
+def test_fused_backward_equals_chain(gs, mode, s, variant):
     """gs_backward takes the upscale's adjoint inside the blend's; it equals the
     separate calls (upscale adjoint -> planes -> blend adjoint -> projection
     adjoint) up to the order of the float atomics that sum over tiles."""
@@ -175,7 +185,7 @@ def test_fused_backward_equals_chain(gs, mode, s):
     scene = gs.DeviceScene(scenes.random_scene(n=n, seed=19, sh_degree=3))
     cam = scenes.pinhole_camera(W, H)
     dout = torch.randn(3, H * s, W * s, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
-    with gs.Context(mode=mode, bg=(0.2, 0.1, 0.4)) as ctx:
+    with gs.Context(mode=mode, bg=(0.2, 0.1, 0.4), bwd_recompute=variant == "recompute") as ctx:
         ctx.render_with_grads(scene, cam, W, H)
         fused = {k: v.cpu().numpy() for k, v in ctx.backward(dout, s).items()}
         dC, dG = ctx.upscale_backward(dout, W, H, s)
@@ -243,3 +253,84 @@ def test_backward_empty_and_culled(gs):
         ctx.render_with_grads(empty, cam, W, H)
         g2 = ctx.render_backward(torch.ones(3, H, W, device="cuda"), torch.ones(3, 3, H, W, device="cuda"))
         assert g2.shape == (0, 9)
+
+
+# ---------------------------------------------------------------- the two variants
+
+def _opaque_layers(n=6000, seed=61):
+    """Stacked high-opacity Gaussians (opacity logits N(3.5, 1): alpha at the
+    0.99 clamp or just below it over much of each footprint), so that most
+    pixels take several steps of alpha >= 0.9 before they stop: the steps
+    whose inversion divides by 1 - alpha <= 0.1."""
+    sc = scenes.random_scene(n=n, seed=seed, sh_degree=1, xy_range=0.9, log_scale_mean=-2.9)
+    sc["opacity_logits"] = np.random.default_rng(seed).normal(3.5, 1.0, n).astype(np.float32)
+    return sc
+
+
+def _errors(got, want):
+    rms = np.sqrt(np.mean(want ** 2, axis=0, keepdims=True)) + 1e-30
+    return float(np.max(np.abs(got - want) / (np.abs(want) + rms)))
+
+
+def test_variants_on_opaque_layers(gs, ora):
+    """Both variants against the FP64 adjoint on a scene of opaque layers
+    (pixels with several alpha >= 0.9 steps), each within the tolerance; the
+    recompute variant's error is at most the inversion's.  Also: the recompute
+    variant needs only the projection (no stored forward state)."""
+    import torch
+    W, H = 96, 64
+    scene = _opaque_layers()
+    cam = scenes.pinhole_camera(W, H)
+    proj = ora.project(scene, cam, W, H)
+    bins = ora.bin_pairs(proj)
+    ref = ora.render(proj, bins, variants=True)
+    keep = (ref["nvar"] == 1) & ~borderline_tile_mask(proj)
+    assert keep.mean() > 0.8
+    rng = np.random.default_rng(8)
+    uC = rng.normal(size=(3, H, W)) * keep
+    uG = rng.normal(size=(3, 3, H, W)) * keep
+    want = ora.render_adjoint(proj, bins, (uC, uG))["g2d"]
+    # the scene does what it is for: steps of alpha >= 0.9 are common
+    a = np.asarray(proj["opacity"])
+    assert np.mean(a > 0.9) > 0.5
+    got = {}
+    for variant in VARIANTS:
+        with gs.Context(bwd_recompute=variant == "recompute") as ctx:
+            dev = gs.DeviceScene(scene)
+            if variant == "recompute":
+                ctx.project(dev, cam, W, H)           # the projection alone suffices
+                g = ctx.render_backward(_t(uC), _t(uG))
+            else:
+                ctx.render_with_grads(dev, cam, W, H)
+                g = ctx.render_backward(_t(uC), _t(uG))
+            ctx.synchronize()
+            got[variant] = g.cpu().numpy()
+            torch.cuda.synchronize()
+    err = {v: _errors(np.asarray(got[v], np.float64), want) for v in VARIANTS}
+    for v in VARIANTS:
+        bad, worst = _cmp_cols(got[v], want)
+        assert bad == 0, (v, bad, worst, err)
+    assert err["recompute"] <= err["inversion"] * 1.05, err
+
+
+def test_recompute_long_lists_thin_checkpoints(gs, ora):
+    """Exact mode, 3000 Gaussians: every tile's list is every Gaussian, so a
+    block walks about 12 rounds of 256 candidates, more than the 8 checkpoint
+    slots of the recompute variant (which then keeps every second round).
+    Both variants against the oracle."""
+    W, H = 48, 16
+    scene = scenes.random_scene(n=3000, seed=62, log_scale_mean=-2.7)
+    cam = scenes.pinhole_camera(W, H)
+    proj = ora.project(scene, cam, W, H, mode=1)
+    bins = ora.bin_pairs(proj)
+    rng = np.random.default_rng(9)
+    uC = rng.normal(size=(3, H, W))
+    uG = rng.normal(size=(3, 3, H, W))
+    want = ora.render_adjoint(proj, bins, (uC, uG))["g2d"]
+    for variant in VARIANTS:
+        with gs.Context(mode="exact", bwd_recompute=variant == "recompute") as ctx:
+            ctx.render_with_grads(gs.DeviceScene(scene), cam, W, H)
+            got = ctx.render_backward(_t(uC), _t(uG)).cpu().numpy()
+            ctx.synchronize()
+        bad, worst = _cmp_cols(got, want)
+        assert bad == 0, (variant, bad, worst)
