@@ -246,6 +246,60 @@ def test_tight_tile_sets_keep_the_image(ora, seed):
     np.testing.assert_array_equal(a["state"][:4], b["state"][:4])
 
 
+def _square_rects(proj):
+    """The 3DGS renderer's tile sets: the tiles holding a pixel centre (i, j)
+    with |i - mean_x| <= r and |j - mean_y| <= r, r = the radius
+    ceil(3 sqrt(lambda_max)), clipped to the image."""
+    W, H, tile = proj["W"], proj["H"], proj["tile"]
+    r = np.asarray(proj["radius"], np.float64)
+    mx, my = np.asarray(proj["mean2d"], np.float64).T
+    x0, x1 = np.ceil(mx - r), np.floor(mx + r)
+    y0, y1 = np.ceil(my - r), np.floor(my + r)
+    ok = (r > 0) & (x1 >= 0) & (x0 <= W - 1) & (y1 >= 0) & (y0 <= H - 1) & (x0 <= x1) & (y0 <= y1)
+    rect = np.stack([np.clip(x0, 0, W - 1) // tile, np.clip(y0, 0, H - 1) // tile,
+                     np.clip(x1, 0, W - 1) // tile, np.clip(y1, 0, H - 1) // tile], 1).astype(np.int32)
+    rect[~ok] = np.array([0, 0, -1, -1], np.int32)
+    touched = np.where(ok, (rect[:, 2] - rect[:, 0] + 1) * (rect[:, 3] - rect[:, 1] + 1), 0).astype(np.int64)
+    return rect, touched
+
+
+@pytest.mark.slow
+def test_tight_tile_sets_keep_the_image_dense_opaque(ora):
+    """At the benchmark scene's density (about 3 Gaussians per pixel: 18,000
+    over 96 x 64) with mostly opaque Gaussians (opacity logits N(1, 1), sigma
+    above 0.35 for 84 % of them).  For such Gaussians the alpha >= 1/255
+    ellipse reaches past the 3-sigma square, so the square (the 3DGS renderer's
+    own truncation, which every-tile binning would not apply) is the
+    reference: cutting it to the alpha >= 1/255 box drops only pairs the
+    cut-off rejects, and the image is bit-identical to the square's."""
+    W, H = 96, 64
+    scene = scenes.random_scene(18000, seed=7, sh_degree=1, xy_range=1.0, log_scale_mean=-3.3)
+    scene["opacity_logits"] = np.random.default_rng(7).normal(1.0, 1.0, 18000).astype(np.float32)
+    sig = 1.0 / (1.0 + np.exp(-scene["opacity_logits"].astype(np.float64)))
+    assert np.mean(sig > 0.35) > 0.8
+    cam = _rotated_camera(W, H)
+    proj = ora.project(scene, cam, W, H)
+    square = dict(proj)
+    square["rect"], square["tiles_touched"] = _square_rects(proj)
+    tight = ora.bin_pairs(proj)
+    full = ora.bin_pairs(square)
+    assert tight["P"] < 0.9 * full["P"]          # the cut removes pairs inside the squares (15 % here)
+    a = ora.render(proj, tight)
+    b = ora.render(square, full)
+    np.testing.assert_array_equal(a["C"], b["C"])
+    np.testing.assert_array_equal(a["grads"], b["grads"])
+    np.testing.assert_array_equal(a["state"][:4], b["state"][:4])
+    # and the square does truncate here: binning every Gaussian into every
+    # tile changes the image (alpha >= 1/255 beyond 3 sigma)
+    every = dict(proj)
+    vis = proj["radius"] > 0
+    every["rect"] = np.where(vis[:, None], np.array([0, 0, every["tiles_x"] - 1, every["tiles_y"] - 1]),
+                             np.array([0, 0, -1, -1])).astype(np.int32)
+    every["tiles_touched"] = np.where(vis, every["tiles_x"] * every["tiles_y"], 0).astype(np.int64)
+    c = ora.render(every, ora.bin_pairs(every))
+    assert not np.array_equal(a["C"], c["C"])
+
+
 def test_borderline_flags_are_rare(ora):
     W, H = 64, 64
     scene = scenes.random_scene(1000, seed=0)
