@@ -64,8 +64,8 @@ def _args():
                     help="training pairs (480x270 with derivatives, 1920x1080 direct) of the learned residual")
     ap.add_argument("--mlp-steps", type=int, default=3000, help="Adam steps of the learned residual")
     ap.add_argument("--profile", default=None,
-                    choices=["main", "main4", "direct", "backward", "mlp", "mlp_train", "views", "bicubic",
-                             "upscale_bwd"],
+                    choices=["main", "main4", "direct", "backward", "backward_recompute", "mlp", "mlp_train",
+                             "views", "bicubic", "upscale_bwd", "garden2x"],
                     help="run only warm-up + steps of the 2x path (main) or of the direct 1920x1080 "
                          "render (direct) and print stage times; the case ncu captures use")
     return ap.parse_args()
@@ -1140,6 +1140,15 @@ def run_profile(args):
     def backward_step():
         ctx.backward(dout, FACTOR, out=grads)
 
+    # the 5M-Gaussian frame at the paper's garden size, spline 2x (2592x1680
+    # render with derivatives -> 5184x3360): the one-sweep depth sort path
+    garden = {}
+
+    def garden_step():
+        ctx.render_with_grads(garden["dev"], garden["cam"], GARDEN_W // 2, GARDEN_H // 2, out_C=garden["C"],
+                              out_grads=garden["G"])
+        ctx.upscale(garden["C"], garden["G"], 2, out=garden["out"])
+
     # the learned residual's fused 4x upscale (960x540 -> 3840x2160) with
     # seeded untrained-scale weights: the kernel's work does not depend on them
     mlp_out = None
@@ -1177,7 +1186,8 @@ def run_profile(args):
     def upscale_bwd_step():
         ctx.upscale_backward(up_dout, LOW_W, LOW_H, FACTOR, out=up_grads)
 
-    fn = {"main": main_step, "main4": main4_step, "direct": direct_step, "backward": backward_step, "mlp": mlp_step,
+    fn = {"main": main_step, "main4": main4_step, "direct": direct_step, "backward": backward_step,
+          "backward_recompute": backward_step, "garden2x": garden_step, "mlp": mlp_step,
           "mlp_train": mlp_train_step, "views": views_step, "bicubic": bicubic_step,
           "upscale_bwd": upscale_bwd_step}[args.profile]
     if args.profile == "mlp_train":
@@ -1212,7 +1222,15 @@ def run_profile(args):
             p[-3 - 192:-3] = np.random.default_rng(1).normal(0, 0.05, 192)    # a non-zero output layer
             mlp_params = torch.as_tensor(p).cuda()
             torch.cuda.synchronize()
-    if args.profile == "backward":
+    if args.profile == "garden2x":
+        garden.update(dev=gs.DeviceScene(scenes.mixture_scene(GARDEN_N, seed=0)),
+                      cam=scenes.pinhole_camera(GARDEN_W // 2, GARDEN_H // 2),
+                      C=torch.empty(3, GARDEN_H // 2, GARDEN_W // 2, device="cuda"),
+                      G=torch.empty(3, 3, GARDEN_H // 2, GARDEN_W // 2, device="cuda"),
+                      out=torch.empty(3, GARDEN_H, GARDEN_W, device="cuda"))
+    if args.profile == "backward_recompute":
+        ctx.set_options(bwd_recompute=True)
+    if args.profile in ("backward", "backward_recompute"):
         with torch.cuda.stream(stream):
             main_step()
             dout = torch.randn(3, OUT_H, OUT_W, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
