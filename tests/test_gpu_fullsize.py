@@ -422,40 +422,45 @@ def test_full_learned_residual_sampled(gs, ora, low):
     assert np.abs(ref["r"]).mean() > 1e-3
 
 
-# ---------------------------------------------------------------- batched views (16 stereo views, 2M)
+# ---------------------------------------------------------------- batched views (16 stereo views, 3 sets)
+
+VIEW_SETS = (300_000, 800_000, 2_000_000)
+
 
 def test_full_batched_views(gs, ora):
     """The batching workload as the benchmark runs it: 16 stereo views (eyes of
-    512x512 to 1104x1032 rendered at half size with derivatives, 2x upscales)
-    of the 2M-Gaussian mixture scene, autotuned, captured in a CUDA graph and
-    replayed.  Every view equals its single-view render bit for bit, and two
-    views (the largest and the smallest) match the oracle on sampled pixels."""
+    512x512 to 1104x1032 rendered at half size with derivatives, 2x upscales),
+    stereo pair k drawing on Gaussian set k mod 3 of the 300k, 800k and 2M
+    mixture scenes, autotuned, captured in a CUDA graph and replayed.  Every
+    view equals its single-view render bit for bit, and two views (the
+    largest and the smallest) match the oracle on sampled pixels."""
     import torch
     camdefs, eyes = scenes.stereo_views()
     V = len(eyes)
     lows = [(w // 2, h // 2) for w, h in eyes]
     cams = [scenes.pinhole_camera(w, h, viewmat=scenes.look_at_viewmat(e, t)) for (w, h), (e, t) in zip(lows, camdefs)]
-    scene = scenes.mixture_scene(2_000_000, seed=1)
-    dev = gs.DeviceScene(scene)
+    sov = [(v // 2) % len(VIEW_SETS) for v in range(V)]
+    sets = [scenes.mixture_scene(n, seed=1) for n in VIEW_SETS]
+    devs = [gs.DeviceScene(sc) for sc in sets]
     Wm, Hm = max(w for w, _ in lows), max(h for _, h in lows)
     stream = torch.cuda.Stream()
     ps = 0
     with gs.Context(stream=stream) as probe:
         with torch.cuda.stream(stream):
-            for (w, h), cam in zip(lows, cams):
-                probe.project(dev, cam, w, h)
+            for (w, h), cam, k in zip(lows, cams, sov):
+                probe.project(devs[k], cam, w, h)
                 ps = max(ps, probe.super_pair_count())
     with gs.Context(stream=stream, no_host_wait=True) as ctx:
-        ctx.reserve_views(dev.n, V, Wm, Hm, ps + ps // 4 + 4096)
+        ctx.reserve_views(max(VIEW_SETS), V, Wm, Hm, ps + ps // 4 + 4096)
         outs = [[torch.empty(3, h, w, device="cuda"), torch.empty(3, 3, h, w, device="cuda"),
                  torch.empty(3, 2 * h, 2 * w, device="cuda")] for w, h in lows]
         with torch.cuda.stream(stream):
-            ctx.render_views(dev, cams, lows, [2] * V, outs=outs)
+            ctx.render_views(devs, cams, lows, [2] * V, outs=outs, scene_of_view=sov)
             torch.cuda.synchronize()
-            ms, best = ctx.autotune_views(dev, cams, lows, [2] * V, outs, reps=2)
+            ms, best = ctx.autotune_views(devs, cams, lows, [2] * V, outs, reps=2, scene_of_view=sov)
             graph = torch.cuda.CUDAGraph()
             with torch.cuda.graph(graph, stream=stream):
-                ctx.render_views(dev, cams, lows, [2] * V, outs=outs)
+                ctx.render_views(devs, cams, lows, [2] * V, outs=outs, scene_of_view=sov)
             for o in outs:
                 for t in o:
                     t.zero_()
@@ -466,7 +471,7 @@ def test_full_batched_views(gs, ora):
         got = [[t.cpu().numpy() for t in o] for o in outs]
     with gs.Context() as ref:
         for v, ((w, h), cam) in enumerate(zip(lows, cams)):
-            C, G = ref.render_with_grads(dev, cam, w, h)
+            C, G = ref.render_with_grads(devs[sov[v]], cam, w, h)
             up = ref.upscale(C, G, 2).cpu().numpy()
             assert np.array_equal(got[v][0], C.cpu().numpy()), v
             assert np.array_equal(got[v][1], G.cpu().numpy()), v
@@ -474,9 +479,9 @@ def test_full_batched_views(gs, ora):
     areas = [w * h for w, h in lows]
     for v in (int(np.argmax(areas)), int(np.argmin(areas))):
         (w, h), cam = lows[v], cams[v]
-        proj = ora.project(scene, cam, w, h)
+        proj = ora.project(sets[sov[v]], cam, w, h)
         bins = ora.bin_pairs(proj)
         _check_low(ora, torch.as_tensor(got[v][0]), torch.as_tensor(got[v][1]), proj, bins,
                    _low_pixels(w, h, 2500, seed=20 + v), rotated=True)
-    del dev
+    del devs
     torch.cuda.empty_cache()

@@ -328,3 +328,26 @@ def test_mixed_sets_rules(gs):
         outs = ctx.render_views(devs[:2], cams, szs, factors, scene_of_view=ok)
         ctx.synchronize()
     _check_mixed(gs, devs, cams, szs, ok, factors, outs, (0.0, 0.0, 0.0))
+
+
+def test_mixed_sets_with_an_empty_set(gs):
+    """A set of no Gaussians beside a non-empty one: its views are background
+    only, the others unchanged; and a single view through the several-sets
+    call equals its single-view render."""
+    empty = gs.DeviceScene(scenes.random_scene(n=0, seed=0))
+    full = gs.DeviceScene(scenes.random_scene(n=2500, seed=44, sh_degree=2))
+    cams, szs = translated_stereo([(64, 48), (40, 30)])
+    sov = [0, 1, 1, 0]
+    factors = [2, 2, 3, 3]
+    bg = (0.3, 0.2, 0.1)
+    with gs.Context(bg=bg, no_host_wait=True) as ctx:
+        ctx.reserve_views(full.n, len(cams), 64, 48, 100000)
+        outs = ctx.render_views([empty, full], cams, szs, factors, scene_of_view=sov)
+        one = ctx.render_views([empty, full], cams[1:2], szs[1:2], [2], scene_of_view=[1])
+        ctx.synchronize()
+    _check_mixed(gs, [empty, full], cams, szs, sov, factors, outs, bg)
+    _check_mixed(gs, [empty, full], cams[1:2], szs[1:2], [1], [2], one, bg)
+    for v in (0, 3):
+        C = outs[v][0].cpu().numpy()
+        assert np.allclose(C, np.array(bg, np.float32)[:, None, None])
+        assert not outs[v][1].cpu().numpy().any()
