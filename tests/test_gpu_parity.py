@@ -91,6 +91,44 @@ def test_bins_bit_exact(gs, ora, name, kw, camkind, W, H):
         assert np.all(t[s:e] == tile)
 
 
+@pytest.mark.parametrize("W,H,side", [(256, 256, 1), (512, 288, 2), (1024, 576, 4), (1040, 600, 4)])
+def test_bins_bit_exact_every_super_side(gs, ora, W, H, side):
+    """The per-frame super-tile side (1, 2 or 4 tiles: the smallest with at
+    most 256 super-tiles) at sizes that pick each: the per-tile lists equal
+    the oracle's bit for bit, the super-tile pair count is the one that side
+    gives, and sampled pixels of the derivative render match the oracle."""
+    scene = scenes.random_scene(n=30000, seed=27, sh_degree=1, xy_range=1.2, log_scale_mean=-3.8)
+    cam = scenes.pinhole_camera(W, H)
+    proj = ora.project(scene, cam, W, H)
+    ref = ora.bin_pairs(proj)
+    tx, ty = (W + 15) // 16, (H + 15) // 16
+    assert side == next(k for k in (1, 2, 4) if ((tx + k - 1) // k) * ((ty + k - 1) // k) <= 256 or k == 4)
+    # super-tile pairs the side gives, from the oracle's rects
+    rc = np.asarray(proj["rect"], np.int64)
+    live = rc[:, 2] >= rc[:, 0]
+    want_ps = int(np.sum(((rc[live, 2] // side) - (rc[live, 0] // side) + 1) *
+                         ((rc[live, 3] // side) - (rc[live, 1] // side) + 1)))
+    rng = np.random.default_rng(W)
+    pix = np.stack([rng.integers(0, W, 600), rng.integers(0, H, 600)], 1)
+    with gs.Context() as ctx:
+        dev = gs.DeviceScene(scene)
+        C, G = ctx.render_with_grads(dev, cam, W, H)
+        keys, vals, _ = (t.cpu().numpy() for t in ctx.read_bins())
+        ps = ctx.super_pair_count()
+        rows = gpu_rows(C, G, pix)
+    drop = np.nonzero(proj["borderline"])[0].astype(np.uint32)
+    gk, gv = pairs_without(keys.view(np.uint64), vals.view(np.uint32), drop)
+    rk, rv = pairs_without(ref["keys"], ref["vals"], drop)
+    assert len(rk) > 10000
+    assert np.array_equal(gk, rk) and np.array_equal(gv, rv)
+    if len(drop) == 0:
+        assert ps == want_ps
+    out = ora.render(proj, ref, pixels=pix, variants=True)
+    excl = borderline_tile_mask(proj)[pix[:, 1], pix[:, 0]]
+    fail, checked, _ = compare_pixels(rows, out, exclude=excl)
+    assert fail == 0 and checked > 0.9 * len(pix), (fail, checked)
+
+
 def _wide_depth_scene(n=6000, seed=21, z=(0.02, 3000.0)):
     """Depths log-uniform over a ratio of 150,000 (beyond the 2^27 FP32 steps
     that three 9-bit radix passes cover), positions and scales in proportion
