@@ -7,19 +7,21 @@
 //
 // Key range.  Every visible depth is a positive FP32 value, and the order of
 // positive FP32 values is that of their bit patterns, so subtracting the
-// smallest visible key keeps the order; the keys of the Gaussians that emit no
-// pair (0xFFFFFFFF) go last.  Once the slice is loaded, each block publishes
+// smallest visible key keeps the order.  The Gaussians that emit no pair (key
+// 0xFFFFFFFF) go last in id order: each takes the biased key span + 1 + id,
+// above every visible one.  Once the slice is loaded, each block publishes
 // the range of its visible keys, and after one grid barrier every block knows
-// the whole range: when it spans fewer than 2^27 - 1 values (16 binades, a
-// depth ratio up to 65536) the biased keys fit 27 bits and three passes of 9
-// bits sort them, otherwise four.
+// the whole range: when span + n fits 27 bits (up to 16 binades of depth,
+// less the Gaussian count) three passes of 9 bits sort the biased keys,
+// otherwise four.
 //
 // Each pass is a stable LSD pass over a 9-bit digit (ids in ascending order
-// ride along): stage the slice, rank it by digit with one ballot per digit bit
-// and per-warp running counters (stable), reorder it by digit in shared
-// memory, publish the block's digit counts (and add them to the digit
-// totals), grid barrier, derive the global offset of each of the block's digit
-// runs, write the runs out (coalesced), grid barrier.
+// ride along): stage the slice, rank it by digit (stable: per-warp lane-mask
+// tables built with shared-memory atomics, per-warp running counters),
+// reorder it by digit in shared memory, publish the
+// block's digit counts (and add them to the digit totals), grid barrier,
+// derive the global offset of each of the block's digit runs, write the runs
+// out (coalesced), grid barrier.
 // The exclusive scan of supers_touched[id] in the sorted order (each
 // Gaussian's first pair slot) rides on the last pass: a Gaussian's slot is
 // the pair count of every Gaussian before it in the final order, i.e. of the
@@ -51,9 +53,9 @@ constexpr int kDsBits = 9;
 constexpr int kDsRadix = 1 << kDsBits;
 constexpr int kDsMaxPasses = 4;                    // 36 bits: any 32-bit key
 constexpr uint32_t kCulled = 0xFFFFFFFFu;          // key of a Gaussian that emits no pair
-constexpr uint32_t kCulled3 = (1u << (3 * kDsBits)) - 1u;   // its biased key when three passes suffice
 constexpr long kGridSpinLimit = 1L << 22;
 constexpr int kDsPer = kDsMaxSlice / kDsThreads;   // slice elements per thread
+static_assert(kDsWarps * kDsRadix <= 2 * kDsMaxSlice, "the rank's lane-mask tables fit in s_key2 / s_id2");
 static_assert(kDsTotWords == (kDsMaxPasses + 1) * kDsRadix, "digit totals of every pass, then the pair-count totals");
 static_assert(kDsRadix == kDsRadixWords, "the scratch layout's digit count");
 // The pair count of each Gaussian rides along with its id through the passes:
@@ -75,18 +77,12 @@ struct DsArgs {
     uint32_t* csum;              // [grid][512] per-block digit sums of the pair counts (last pass);
                                  // words 0, 1 of a block's row first carry its key range
     uint32_t* tot;               // [5][512] digit totals per pass, then the pair-count totals (zeroed)
-    unsigned int* bar;           // [2] barrier counter and generation (zeroed); bar[2] stays zero
+    unsigned int* bar;           // [0] arrival counter of the grid barrier (zeroed); bar[2] stays zero
     int* err;
     uint32_t n;
     uint32_t inject_spins;       // > 0: block 0 first polls bar[2], which nothing sets, this many times
 };
 
-// Grid-wide barrier for a cooperative launch (all blocks resident).  Thread 0
-// of each block arrives with an acquire-release add at GPU scope (it releases
-// the block's writes, ordered before it by the CTA barrier, and acquires those
-// of the blocks that arrived earlier); the last to arrive resets the count and
-// publishes the next generation with a release add; the others poll the
-// generation with acquire loads.
 // Poll word (acquire loads) until it differs from `unchanged`, at most limit
 // times; on expiry record kDevTimeout in the error word and return false.
 __device__ __forceinline__ bool bounded_poll(const unsigned int* word, unsigned int unchanged, long limit, int* err)
@@ -104,19 +100,32 @@ __device__ __forceinline__ bool bounded_poll(const unsigned int* word, unsigned 
     } while (true);
 }
 
-__device__ __forceinline__ void grid_barrier(unsigned int* bar, int* err)
+// Grid-wide barrier for a cooperative launch (all blocks resident): an
+// arrival counter that only grows during the launch (zeroed before it), so
+// that the k-th barrier is passed once it reaches k * gridDim.x.  Thread 0 of
+// each block arrives with a release add at GPU scope (releasing the block's
+// writes, ordered before it by the CTA barrier) and polls the counter with
+// acquire loads.  The adds form one chain of read-modify-writes, so the load
+// that reads the last arrival's value acquires the writes released by every
+// earlier arrival.  One round trip to L2 per barrier, where a reset counter
+// and a separate generation word take two.
+__device__ __forceinline__ void grid_barrier(unsigned int* bar, unsigned int& target, int* err)
 {
     __syncthreads();
+    target += gridDim.x;
     if (threadIdx.x == 0) {
-        unsigned int gen, arrived;
-        asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(gen) : "l"(bar + 1) : "memory");
-        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(bar) : "memory");
-        if (arrived == gridDim.x - 1) {
-            asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(bar) : "memory");
-            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar + 1) : "memory");
-        } else {
-            bounded_poll(bar + 1, gen, kGridSpinLimit, err);
-        }
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+        long spins = 0;
+        unsigned int c;
+        do {
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(c) : "l"(bar) : "memory");
+            if ((int)(c - target) >= 0) break;
+            if (++spins > kGridSpinLimit) {
+                atomicExch(err, kDevTimeout);
+                break;
+            }
+            __nanosleep(32);
+        } while (true);
     }
     __syncthreads();
 }
@@ -137,16 +146,14 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
     uint32_t* s_id = s_key + kDsMaxSlice;
     uint32_t* s_key2 = s_id + kDsMaxSlice;                            // slice reordered by digit
     uint32_t* s_id2 = s_key2 + kDsMaxSlice;
-    uint16_t* s_rank = reinterpret_cast<uint16_t*>(s_id2 + kDsMaxSlice);
-    uint16_t* s_wcnt = s_rank + kDsMaxSlice;                          // [kDsWarps][R]
+    uint16_t* s_wcnt = reinterpret_cast<uint16_t*>(s_id2 + kDsMaxSlice);   // [kDsWarps][R]
     uint32_t* s_off = reinterpret_cast<uint32_t*>(s_wcnt + kDsWarps * R);   // [R]
     uint32_t* s_boff = s_off + R;                                     // [R] block-local digit starts
-    uint32_t* s_wtot = s_boff + R;                                    // [kDsWarps]
-    // last pass only (s_rank is free once the slice is reordered): pair-count
-    // scan value at each digit run's start, and each run's first pair slot
-    // minus that value
-    uint32_t* s_cbase = reinterpret_cast<uint32_t*>(s_rank);          // [R]
+    // last pass only: pair-count scan value at each digit run's start, and
+    // each run's first pair slot minus that value
+    uint32_t* s_cbase = s_boff + R;                                   // [R]
     uint32_t* s_obase = s_cbase + R;                                  // [R]
+    uint32_t* s_wtot = s_obase + R;                                   // [kDsWarps]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt = (1u << lane) - 1u;
 
@@ -155,15 +162,20 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
     // unaffected
     if (a.inject_spins && blockIdx.x == 0 && tid == 0) bounded_poll(a.bar + 2, 0u, (long)a.inject_spins, a.err);
 
-    // ---- the slice's keys and the range of the visible ones ----
-    uint32_t rk[kDsPer];
+    unsigned int bar_target = 0;   // the grid barrier's arrival count to wait for
+    // ---- the slice's keys (and pair counts) and the range of the visible keys ----
+    uint32_t rk[kDsPer], rc[kDsPer];
     {
         uint32_t kmin = kCulled, kmax = 0u;
 #pragma unroll
         for (int k = 0; k < kDsPer; ++k) {
             const uint32_t j = tid + k * kDsThreads;
             rk[k] = kCulled;
-            if (j < m) rk[k] = __ldcg(a.keys_in + lo + j);
+            rc[k] = 0u;
+            if (j < m) {
+                rk[k] = __ldcg(a.keys_in + lo + j);
+                rc[k] = __ldcg(a.counts + lo + j);
+            }
             if (rk[k] != kCulled) {
                 kmin = min(kmin, rk[k]);
                 kmax = max(kmax, rk[k]);
@@ -185,7 +197,7 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
             a.csum[(size_t)blockIdx.x * R + 1] = kmax;
         }
     }
-    grid_barrier(a.bar, a.err);
+    grid_barrier(a.bar, bar_target, a.err);
     if (warp == 0) {
         uint32_t kmin = kCulled, kmax = 0u;
         for (uint32_t b = lane; b < G; b += 32) {
@@ -202,16 +214,18 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
     __syncthreads();
     const bool any = s_wtot[0] <= s_wtot[1];
     const uint32_t bias = any ? s_wtot[0] : 0u;
-    const int P = (any ? s_wtot[1] - s_wtot[0] : 0u) < kCulled3 ? 3 : 4;
-    const uint32_t culled = P == 3 ? kCulled3 : kCulled - bias;   // above every biased visible key
+    // a Gaussian that emits no pair takes the key cbase + id: above every
+    // biased visible key and in id order, as equal keys would sort, but
+    // distinct (equal digits in a warp make the ranking's atomics collide)
+    const uint32_t cbase = any ? s_wtot[1] - s_wtot[0] + 1u : 0u;
+    const int P = (uint64_t)cbase + n - 1u < (1ull << (3 * kDsBits)) ? 3 : 4;
     __syncthreads();   // s_wtot is reused below
 #pragma unroll
     for (int k = 0; k < kDsPer; ++k) {
         const uint32_t j = tid + k * kDsThreads;
         if (j < m) {
-            s_key[j] = rk[k] == kCulled ? culled : rk[k] - bias;
-            const uint32_t c = a.counts[lo + j];
-            s_id[j] = (lo + j) | ((c < kCntEsc ? c : kCntEsc) << kIdBits);
+            s_key[j] = rk[k] == kCulled ? cbase + lo + j : rk[k] - bias;
+            s_id[j] = (lo + j) | ((rc[k] < kCntEsc ? rc[k] : kCntEsc) << kIdBits);
         }
     }
 
@@ -226,7 +240,9 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
         const uint32_t* src_id = to1 ? a.ids[0] : a.ids[1];
         uint32_t* dst_key = to1 ? a.keys[1] : a.keys[0];
         uint32_t* dst_id = to1 ? a.ids[1] : a.ids[0];
-        for (int i = tid; i < kDsWarps * (int)R; i += kDsThreads) s_wcnt[i] = 0;
+        for (int i = tid; i < kDsWarps * (int)R / 8; i += kDsThreads) reinterpret_cast<uint4*>(s_wcnt)[i] = make_uint4(0, 0, 0, 0);
+        for (int i = tid; i < kDsWarps * (int)R / 4; i += kDsThreads)   // the rank's lane-mask tables
+            reinterpret_cast<uint4*>(s_key2)[i] = make_uint4(0, 0, 0, 0);
         // stage the slice in shared memory (the first pass has it already):
         // coalesced loads (L2, the previous pass's scatter by other blocks),
         // all of a thread's loads in flight at once
@@ -250,29 +266,42 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
             }
         }
         __syncthreads();
-        // stable ranking: warp w ranks its chunk [w cw, (w+1) cw) 32 elements at a time
+        // stable ranking: warp w ranks its chunk [w cw, (w+1) cw), at most
+        // kDsPer groups of 32 (cw <= kDsMaxSlice / 32), in order.  The lanes
+        // of a group that hold the same digit are found through a per-warp
+        // table of lane masks, one word per digit (in s_key2 / s_id2, free
+        // until the reorder, zeroed above): each lane ORs its bit into its
+        // digit's word and reads the word back.  (Warp votes cost one ballot
+        // per digit bit and a match instruction's cost grows with the
+        // distinct digits in the warp; both run far below the shared-memory
+        // atomics' rate.)  The highest lane of each digit then reads the
+        // warp's running count of the digit, passes it to its peers, writes
+        // it back advanced and clears the digit's word.  Each lane keeps its
+        // digit and rank in dr (digit | rank << 16) for the reorder below.
         const uint32_t wlo = warp * cw, whi = min(m, wlo + cw);
-        for (uint32_t base = wlo; base < whi; base += 32) {
-            const uint32_t j = base + lane;
-            const bool valid = j < whi;
-            const uint32_t d = valid ? (s_key[j] >> shift) & (R - 1) : 0u;
-            // lanes holding the same digit: one ballot per digit bit (a match
-            // instruction's cost grows with the distinct digits in the warp)
-            uint32_t peers = __ballot_sync(0xffffffffu, valid);
+        uint32_t* s_mask = s_key2 + warp * R;
+        uint32_t dr[kDsPer];
 #pragma unroll
-            for (int b = 0; b < kDsBits; ++b) {
-                const bool bit = (d >> b) & 1u;
-                const uint32_t bal = __ballot_sync(0xffffffffu, bit);
-                peers &= bit ? bal : ~bal;
+        for (int g = 0; g < kDsPer; ++g) {
+            if (wlo + g * 32 < whi) {   // warp-uniform
+                const uint32_t j = wlo + g * 32 + lane;
+                const bool valid = j < whi;
+                const uint32_t d = valid ? (s_key[j] >> shift) & (R - 1) : 0u;
+                if (valid) atomicOr(s_mask + d, 1u << lane);
+                __syncwarp();
+                const uint32_t peers = valid ? s_mask[d] : (1u << lane);   // an idle lane leads itself
+                __syncwarp();   // every lane has read its word before the leaders clear it
+                const int leader = 31 - __clz(peers);
+                uint32_t prev = 0;
+                if (valid && lane == leader) {
+                    prev = s_wcnt[warp * R + d];
+                    s_wcnt[warp * R + d] = (uint16_t)(prev + __popc(peers));
+                    s_mask[d] = 0u;
+                }
+                prev = __shfl_sync(0xffffffffu, prev, leader);
+                dr[g] = d | ((prev + __popc(peers & lt)) << 16);
+                __syncwarp();   // the next group's lanes see the cleared words and the new counts
             }
-            uint32_t prev = 0;
-            if (valid) prev = s_wcnt[warp * R + d];
-            __syncwarp();
-            if (valid) {
-                s_rank[j] = (uint16_t)(prev + __popc(peers & lt));
-                if (lane == 31 - __clz(peers)) s_wcnt[warp * R + d] = (uint16_t)(prev + __popc(peers));
-            }
-            __syncwarp();
         }
         __syncthreads();
         // per digit: exclusive prefix over warps, the block's count (published,
@@ -302,13 +331,17 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
             s_boff[tid] += wb;
         }
         __syncthreads();
-        // reorder the slice by digit (stable) in shared memory
-        for (uint32_t j = tid; j < m; j += kDsThreads) {
-            const uint32_t key = s_key[j];
-            const uint32_t d = (key >> shift) & (R - 1);
-            const uint32_t lp = s_boff[d] + s_wcnt[(j / cw) * R + d] + s_rank[j];
-            s_key2[lp] = key;
-            s_id2[lp] = s_id[j];
+        // reorder the slice by digit (stable) in shared memory, each lane
+        // moving the elements it ranked
+#pragma unroll
+        for (int g = 0; g < kDsPer; ++g) {
+            const uint32_t j = wlo + g * 32 + lane;
+            if (j < whi) {
+                const uint32_t d = dr[g] & 0xFFFFu;
+                const uint32_t lp = s_boff[d] + s_wcnt[warp * R + d] + (dr[g] >> 16);
+                s_key2[lp] = s_key[j];
+                s_id2[lp] = s_id[j];
+            }
         }
         if (last) {
             // pair counts of the reordered slice, their exclusive scan (in
@@ -358,41 +391,60 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
                 s_cbase[tid] = v0;
             }
         }
-        grid_barrier(a.bar, a.err);
+        grid_barrier(a.bar, bar_target, a.err);
         // global start of this block's run of each digit:
-        // exclusive digit total + this digit's count in earlier blocks, the
-        // latter summed by 2 groups of 512 threads (every other earlier block each)
+        // exclusive digit total + this digit's count in earlier blocks.  The
+        // latter is summed with 16-byte loads: thread t takes digits
+        // 4 (t mod 128) .. 4 (t mod 128) + 3 of the earlier blocks b = t / 128
+        // (mod 8), four rows' loads in flight, into s_part[8][R] (and the
+        // pair-count sums of the last pass into s_part[8 + 8][R]: s_wcnt is
+        // free here and holds exactly these 16 R words).
         {
-            uint32_t* s_part = reinterpret_cast<uint32_t*>(s_wcnt);   // [2][2][R]; s_wcnt is free here
-            const uint32_t d = tid & (R - 1), g = tid / R;
-            uint32_t p0 = 0, p1 = 0, q0 = 0, q1 = 0;
-            uint32_t b = g;
-            if (last) {   // the digit counts and the pair-count sums
-                for (; b + 2 < blockIdx.x; b += 4) {
-                    p0 += __ldcg(a.cnt + (size_t)b * R + d);
-                    p1 += __ldcg(a.cnt + (size_t)(b + 2) * R + d);
-                    q0 += __ldcg(a.csum + (size_t)b * R + d);
-                    q1 += __ldcg(a.csum + (size_t)(b + 2) * R + d);
+            uint32_t* s_part = reinterpret_cast<uint32_t*>(s_wcnt);
+            const uint32_t q = tid & 127, g = tid >> 7;
+            const uint4* cnt4 = reinterpret_cast<const uint4*>(a.cnt) + q;
+            const uint4* csum4 = reinterpret_cast<const uint4*>(a.csum) + q;
+            constexpr uint32_t RQ = R / 4;   // 16-byte words per row
+            uint4 p = make_uint4(0, 0, 0, 0);
+            {
+                uint32_t b = g;
+                for (; b + 24 < blockIdx.x; b += 32) {
+                    uint4 v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) v[u] = __ldcg(cnt4 + (size_t)(b + 8 * u) * RQ);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) { p.x += v[u].x; p.y += v[u].y; p.z += v[u].z; p.w += v[u].w; }
                 }
-                if (b < blockIdx.x) {
-                    p0 += __ldcg(a.cnt + (size_t)b * R + d);
-                    q0 += __ldcg(a.csum + (size_t)b * R + d);
+                for (; b < blockIdx.x; b += 8) {
+                    const uint4 v = __ldcg(cnt4 + (size_t)b * RQ);
+                    p.x += v.x; p.y += v.y; p.z += v.z; p.w += v.w;
                 }
-                s_part[2 * R + g * R + d] = q0 + q1;
-            } else {
-                for (; b + 2 < blockIdx.x; b += 4) {
-                    p0 += __ldcg(a.cnt + (size_t)b * R + d);
-                    p1 += __ldcg(a.cnt + (size_t)(b + 2) * R + d);
-                }
-                if (b < blockIdx.x) p0 += __ldcg(a.cnt + (size_t)b * R + d);
             }
-            s_part[g * R + d] = p0 + p1;
+            reinterpret_cast<uint4*>(s_part + g * R)[q] = p;
+            if (last) {
+                uint4 c = make_uint4(0, 0, 0, 0);
+                uint32_t b = g;
+                for (; b + 24 < blockIdx.x; b += 32) {
+                    uint4 v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) v[u] = __ldcg(csum4 + (size_t)(b + 8 * u) * RQ);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) { c.x += v[u].x; c.y += v[u].y; c.z += v[u].z; c.w += v[u].w; }
+                }
+                for (; b < blockIdx.x; b += 8) {
+                    const uint4 v = __ldcg(csum4 + (size_t)b * RQ);
+                    c.x += v.x; c.y += v.y; c.z += v.z; c.w += v.w;
+                }
+                reinterpret_cast<uint4*>(s_part + (8 + g) * R)[q] = c;
+            }
         }
         __syncthreads();
         if (tid < (int)R) {
             const uint32_t* s_part = reinterpret_cast<const uint32_t*>(s_wcnt);
             const uint32_t tot = __ldcg(a.tot + pass * R + tid);
-            const uint32_t pre = s_part[tid] + s_part[R + tid];
+            uint32_t pre = 0;
+#pragma unroll
+            for (int g = 0; g < 8; ++g) pre += s_part[g * R + tid];
             uint32_t x = tot;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -404,7 +456,9 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
             if (last) {
                 // first pair slot of this block's run of digit tid, minus the
                 // run's start in the slice's pair-count scan
-                const uint32_t cpre = s_part[2 * R + tid] + s_part[3 * R + tid];
+                uint32_t cpre = 0;
+#pragma unroll
+                for (int g = 8; g < 16; ++g) cpre += s_part[g * R + tid];
                 const uint32_t ctot = __ldcg(a.tot + kDsMaxPasses * R + tid);
                 uint32_t xc = ctot;
 #pragma unroll
@@ -449,7 +503,7 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
                 }
             }
         }
-        if (!last) grid_barrier(a.bar, a.err);
+        if (!last) grid_barrier(a.bar, bar_target, a.err);
     }
 }
 
@@ -491,7 +545,7 @@ int ds_grid(int device)
 
 size_t depth_sort_smem_bytes()
 {
-    return (size_t)kDsMaxSlice * (4 * 4 + 2) + (size_t)kDsWarps * kDsRadix * 2 + 2 * kDsRadix * 4 + kDsWarps * 4;
+    return (size_t)kDsMaxSlice * 4 * 4 + (size_t)kDsWarps * kDsRadix * 2 + 4 * kDsRadix * 4 + kDsWarps * 4;
 }
 
 uint32_t depth_sort_capacity(int device)

@@ -145,8 +145,9 @@ def _wide_depth_scene(n=6000, seed=21, z=(0.02, 3000.0)):
 @pytest.mark.parametrize("z", [(0.02, 3000.0), (0.5, 8.0)])
 def test_bins_bit_exact_over_depth_ranges(gs, ora, z):
     """The depth sort biases the FP32 depth bits by the smallest visible one and
-    takes three 9-bit passes when the visible keys span fewer than 2^27 - 1
-    values, four otherwise: both cases against the oracle's bins, bit for bit."""
+    takes three 9-bit passes when the visible keys' span plus the Gaussian
+    count fits 27 bits, four otherwise: both cases against the oracle's bins,
+    bit for bit."""
     W, H = 96, 64
     scene = _wide_depth_scene(z=z)
     cam = scenes.pinhole_camera(W, H, znear=0.01)
@@ -154,7 +155,8 @@ def test_bins_bit_exact_over_depth_ranges(gs, ora, z):
     vis = proj["tiles_touched"] > 0
     bits = proj["depth"][vis].astype(np.float32).view(np.uint32).astype(np.int64)
     span = int(bits.max() - bits.min())
-    assert (span >= (1 << 27) - 1) == (z[1] / z[0] > 65536)   # the case this parameter is meant to hit
+    n = len(proj["depth"])
+    assert (span + n >= (1 << 27)) == (z[1] / z[0] > 65536)   # the case this parameter is meant to hit
     ref = ora.bin_pairs(proj)
     with gs.Context() as ctx:
         ctx.project(gs.DeviceScene(scene), cam, W, H)
