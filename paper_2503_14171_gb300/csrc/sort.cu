@@ -44,6 +44,34 @@ __device__ __forceinline__ uint32_t digit_of(K key, int shift)
     return (uint32_t)(key >> shift) & (kRadix - 1);
 }
 
+// Stable rank of this lane's key among the keys of its digit that the warp has
+// ranked so far (warp multi-split).  The lanes holding the same digit are
+// found through the warp's table of lane masks (one word per digit, zero
+// between calls): each lane ORs its bit into its digit's word and reads the
+// word back.  (One warp ballot per digit bit, or a match instruction, costs
+// far more issue time on this part than these shared-memory atomics.)  The
+// highest lane of each digit reads the warp's running count of the digit,
+// passes it to its peers, writes it back advanced and clears the word.
+// valid = false (a slot past the end): returns 0 and touches nothing.
+__device__ __forceinline__ uint32_t warp_rank(uint32_t* __restrict__ mask, uint32_t* __restrict__ count, uint32_t d,
+                                              bool valid, int lane, uint32_t lt)
+{
+    if (valid) atomicOr(mask + d, 1u << lane);
+    __syncwarp();
+    const uint32_t peers = valid ? mask[d] : (1u << lane);   // an idle lane leads itself
+    __syncwarp();   // every lane has read its word before the leaders clear it
+    const int leader = 31 - __clz(peers);
+    uint32_t prev = 0;
+    if (valid && lane == leader) {
+        prev = count[d];
+        count[d] = prev + __popc(peers);
+        mask[d] = 0u;
+    }
+    prev = __shfl_sync(0xffffffffu, prev, leader);
+    __syncwarp();   // the next call's lanes see the cleared words and the new counts
+    return prev + __popc(peers & lt);
+}
+
 // Histogram of every pass's digit over all keys, in per-warp shared-memory
 // sub-histograms (a key shared by a whole warp, e.g. the exponent byte of a
 // depth, costs one 32-way serialised atomic instead of block-wide contention).
@@ -99,7 +127,10 @@ struct OnesweepSmem {
     uint32_t global_base[kRadix];         // output index of the tile's first key of each digit, minus local_start
     uint32_t warp_tot[kWarps];
     uint32_t tile;
-    K keys[kTileKeys];
+    union {
+        K keys[kTileKeys];                // the tile in digit order
+        uint32_t mask[kWarps][kRadix];    // before that, the ranking's per-warp lane-mask tables
+    };
     uint32_t vals[HAS_VAL ? kTileKeys : 1];
 };
 
@@ -114,7 +145,10 @@ __device__ __forceinline__ void onesweep_tile(OnesweepSmem<K, HAS_VAL>& S, const
                                               int* __restrict__ err)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < kWarps * kRadix; i += kThreads) (&S.warp_hist[0][0])[i] = 0;
+    for (int i = tid; i < kWarps * kRadix; i += kThreads) {
+        (&S.warp_hist[0][0])[i] = 0;
+        (&S.mask[0][0])[i] = 0;
+    }
     if (tid == 0) S.tile = atomicAdd(tile_counter, 1u);   // tiles are taken in launch order
     __syncthreads();
     const uint32_t tile = S.tile;
@@ -133,27 +167,11 @@ __device__ __forceinline__ void onesweep_tile(OnesweepSmem<K, HAS_VAL>& S, const
         if (HAS_VAL) val[i] = valid ? vals_in[idx] : 0u;
         dig[i] = valid ? digit_of(key[i], shift) : (uint32_t)kRadix;
     }
-    // warp multi-split: rank among earlier keys of the same digit in this warp;
-    // the lanes sharing a digit are found with one ballot per digit bit
+    // warp multi-split: rank among earlier keys of the same digit in this warp
     const uint32_t lt = lanemask_lt();
 #pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        const uint32_t d = dig[i];
-        uint32_t peers = __ballot_sync(0xffffffffu, d < (uint32_t)kRadix);
-#pragma unroll
-        for (int b = 0; b < kRadixBits; ++b) {
-            const bool bit = (d >> b) & 1u;
-            const uint32_t bal = __ballot_sync(0xffffffffu, bit);
-            peers &= bit ? bal : ~bal;
-        }
-        const int leader = 31 - __clz(peers);
-        uint32_t prev = 0;
-        if (d < (uint32_t)kRadix) prev = S.warp_hist[warp][d];
-        rank[i] = prev + __popc(peers & lt);
-        __syncwarp();
-        if (lane == leader && d < (uint32_t)kRadix) S.warp_hist[warp][d] = prev + __popc(peers);
-        __syncwarp();
-    }
+    for (int i = 0; i < kItems; ++i)
+        rank[i] = warp_rank(S.mask[warp], S.warp_hist[warp], dig[i], dig[i] < (uint32_t)kRadix, lane, lt);
     __syncthreads();
 
     // thread d: per-warp exclusive prefix for digit d and the tile's count
@@ -264,7 +282,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_onesweep(const K* __restrict__ 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (n_dev) n = min(n, *n_dev);   // key count known on the device only; surplus tiles exit
 
-    for (int i = tid; i < kWarps * kRadix; i += kThreads) (&S.warp_hist[0][0])[i] = 0;
+    for (int i = tid; i < kWarps * kRadix; i += kThreads) {
+        (&S.warp_hist[0][0])[i] = 0;
+        (&S.mask[0][0])[i] = 0;
+    }
     if (tid == 0) S.tile = atomicAdd(tile_counter, 1u);   // tiles are taken in launch order
     __syncthreads();
     const uint32_t tile = S.tile;
@@ -283,27 +304,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_onesweep(const K* __restrict__ 
         if (HAS_VAL) val[i] = valid ? vals_in[idx] : 0u;
         dig[i] = valid ? digit_of(key[i], shift) : (uint32_t)kRadix;
     }
-    // warp multi-split: rank among earlier keys of the same digit in this warp;
-    // the lanes sharing a digit are found with one ballot per digit bit
+    // warp multi-split: rank among earlier keys of the same digit in this warp
     const uint32_t lt = lanemask_lt();
 #pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        const uint32_t d = dig[i];
-        uint32_t peers = __ballot_sync(0xffffffffu, d < (uint32_t)kRadix);
-#pragma unroll
-        for (int b = 0; b < kRadixBits; ++b) {
-            const bool bit = (d >> b) & 1u;
-            const uint32_t bal = __ballot_sync(0xffffffffu, bit);
-            peers &= bit ? bal : ~bal;
-        }
-        const int leader = 31 - __clz(peers);
-        uint32_t prev = 0;
-        if (d < (uint32_t)kRadix) prev = S.warp_hist[warp][d];
-        rank[i] = prev + __popc(peers & lt);
-        __syncwarp();
-        if (lane == leader && d < (uint32_t)kRadix) S.warp_hist[warp][d] = prev + __popc(peers);
-        __syncwarp();
-    }
+    for (int i = 0; i < kItems; ++i)
+        rank[i] = warp_rank(S.mask[warp], S.warp_hist[warp], dig[i], dig[i] < (uint32_t)kRadix, lane, lt);
     __syncthreads();
 
     // thread d: per-warp exclusive prefix for digit d and the tile's count
