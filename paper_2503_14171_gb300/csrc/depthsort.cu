@@ -243,6 +243,7 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
         for (int i = tid; i < kDsWarps * (int)R / 8; i += kDsThreads) reinterpret_cast<uint4*>(s_wcnt)[i] = make_uint4(0, 0, 0, 0);
         for (int i = tid; i < kDsWarps * (int)R / 4; i += kDsThreads)   // the rank's lane-mask tables
             reinterpret_cast<uint4*>(s_key2)[i] = make_uint4(0, 0, 0, 0);
+        if (last && tid < (int)R) s_off[tid] = 0u;   // the last pass's per-digit pair-count sums
         // stage the slice in shared memory (the first pass has it already):
         // coalesced loads (L2, the previous pass's scatter by other blocks),
         // all of a thread's loads in flight at once
@@ -303,9 +304,27 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
                 __syncwarp();   // the next group's lanes see the cleared words and the new counts
             }
         }
+        // the last pass: each digit's sum of the pair counts of the block's
+        // keys (s_off holds them until the barrier; a sum needs no order)
+        if (last) {
+#pragma unroll
+            for (int g = 0; g < kDsPer; ++g) {
+                const uint32_t j = wlo + g * 32 + lane;
+                if (j < whi) {
+                    const uint32_t v = s_id[j];
+                    uint32_t c = v >> kIdBits;
+                    if (c == kCntEsc) {   // escaped: look the count up
+                        const uint32_t id = v & kIdMask;
+                        c = id < n ? a.counts[id] : 0u;
+                    }
+                    if (c) atomicAdd(&s_off[dr[g] & 0xFFFFu], c);
+                }
+            }
+        }
         __syncthreads();
         // per digit: exclusive prefix over warps, the block's count (published,
-        // and added to the digit total), and the block-local start of the digit
+        // and added to the digit total), the last pass's pair-count sum
+        // (likewise), and the block-local start of the digit
         if (tid < (int)R) {
             uint32_t run = 0;
             for (int w = 0; w < kDsWarps; ++w) {
@@ -315,6 +334,11 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
             }
             a.cnt[(size_t)blockIdx.x * R + tid] = run;
             if (run) atomicAdd(&a.tot[pass * R + tid], run);
+            if (last) {
+                const uint32_t cs = s_off[tid];
+                a.csum[(size_t)blockIdx.x * R + tid] = cs;
+                if (cs) atomicAdd(&a.tot[kDsMaxPasses * R + tid], cs);
+            }
             uint32_t x = run;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -331,22 +355,94 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
             s_boff[tid] += wb;
         }
         __syncthreads();
-        // reorder the slice by digit (stable) in shared memory, each lane
-        // moving the elements it ranked
+        // each element's position in the block's digit-ordered slice (stable),
+        // kept in dr: the reorder itself waits until after the barrier, where
+        // it overlaps the loads of the cross-block prefix
 #pragma unroll
         for (int g = 0; g < kDsPer; ++g) {
             const uint32_t j = wlo + g * 32 + lane;
             if (j < whi) {
                 const uint32_t d = dr[g] & 0xFFFFu;
-                const uint32_t lp = s_boff[d] + s_wcnt[warp * R + d] + (dr[g] >> 16);
-                s_key2[lp] = s_key[j];
-                s_id2[lp] = s_id[j];
+                dr[g] = s_boff[d] + s_wcnt[warp * R + d] + (dr[g] >> 16);
             }
         }
+        grid_barrier(a.bar, bar_target, a.err);
+        // global start of this block's run of each digit:
+        // exclusive digit total + this digit's count in earlier blocks.  The
+        // latter is summed with 16-byte loads: thread t takes digits
+        // 4 (t mod 128) .. 4 (t mod 128) + 3 of the earlier blocks b = t / 128
+        // (mod 8), four rows' loads in flight, into s_part[8][R] (and the
+        // pair-count sums of the last pass into s_part[8 + 8][R]: s_wcnt is
+        // free here and holds exactly these 16 R words).  The digit totals and
+        // the first four rows are requested before the reorder.
+        uint32_t tot = 0, ctot = 0;
+        if (tid < (int)R) {
+            tot = __ldcg(a.tot + pass * R + tid);
+            if (last) ctot = __ldcg(a.tot + kDsMaxPasses * R + tid);
+        }
+        {
+            uint32_t* s_part = reinterpret_cast<uint32_t*>(s_wcnt);
+            const uint32_t q = tid & 127, g = tid >> 7;
+            const uint4* cnt4 = reinterpret_cast<const uint4*>(a.cnt) + q;
+            const uint4* csum4 = reinterpret_cast<const uint4*>(a.csum) + q;
+            constexpr uint32_t RQ = R / 4;   // 16-byte words per row
+            uint4 p = make_uint4(0, 0, 0, 0);
+            {
+                uint4 v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const uint32_t b = g + 8 * u;
+                    v[u] = b < blockIdx.x ? __ldcg(cnt4 + (size_t)b * RQ) : make_uint4(0, 0, 0, 0);
+                }
+                // reorder the slice by digit in shared memory, each lane
+                // moving the elements it ranked
+#pragma unroll
+                for (int k = 0; k < kDsPer; ++k) {
+                    const uint32_t j = wlo + k * 32 + lane;
+                    if (j < whi) {
+                        s_key2[dr[k]] = s_key[j];
+                        s_id2[dr[k]] = s_id[j];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) { p.x += v[u].x; p.y += v[u].y; p.z += v[u].z; p.w += v[u].w; }
+            }
+            {
+                uint32_t b = g + 32;
+                for (; b + 24 < blockIdx.x; b += 32) {
+                    uint4 v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) v[u] = __ldcg(cnt4 + (size_t)(b + 8 * u) * RQ);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) { p.x += v[u].x; p.y += v[u].y; p.z += v[u].z; p.w += v[u].w; }
+                }
+                for (; b < blockIdx.x; b += 8) {
+                    const uint4 v = __ldcg(cnt4 + (size_t)b * RQ);
+                    p.x += v.x; p.y += v.y; p.z += v.z; p.w += v.w;
+                }
+            }
+            reinterpret_cast<uint4*>(s_part + g * R)[q] = p;
+            if (last) {
+                uint4 c = make_uint4(0, 0, 0, 0);
+                uint32_t b = g;
+                for (; b + 24 < blockIdx.x; b += 32) {
+                    uint4 v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) v[u] = __ldcg(csum4 + (size_t)(b + 8 * u) * RQ);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) { c.x += v[u].x; c.y += v[u].y; c.z += v[u].z; c.w += v[u].w; }
+                }
+                for (; b < blockIdx.x; b += 8) {
+                    const uint4 v = __ldcg(csum4 + (size_t)b * RQ);
+                    c.x += v.x; c.y += v.y; c.z += v.z; c.w += v.w;
+                }
+                reinterpret_cast<uint4*>(s_part + (8 + g) * R)[q] = c;
+            }
+        }
+        __syncthreads();
         if (last) {
             // pair counts of the reordered slice, their exclusive scan (in
             // s_key, free now): thread t takes a contiguous run of E positions
-            __syncthreads();
             const uint32_t E = (m + kDsThreads - 1) / kDsThreads;
             const uint32_t t0 = min(m, tid * E), t1 = min(m, t0 + E);
             uint32_t sum = 0;
@@ -381,67 +477,15 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
                 run += c;
             }
             __syncthreads();
-            // per digit: the pair counts of its run (published, and added to
-            // the digit's total) and the scan value at the run's start
+            // per digit: the scan value at the run's start
             if (tid < (int)R) {
-                const uint32_t r0 = s_boff[tid], r1 = tid + 1 < (int)R ? s_boff[tid + 1] : m;
-                const uint32_t v0 = r0 < m ? s_key[r0] : btot, v1 = r1 < m ? s_key[r1] : btot;
-                a.csum[(size_t)blockIdx.x * R + tid] = v1 - v0;
-                if (v1 != v0) atomicAdd(&a.tot[kDsMaxPasses * R + tid], v1 - v0);
-                s_cbase[tid] = v0;
+                const uint32_t r0 = s_boff[tid];
+                s_cbase[tid] = r0 < m ? s_key[r0] : btot;
             }
+            __syncthreads();   // s_wtot is reused below
         }
-        grid_barrier(a.bar, bar_target, a.err);
-        // global start of this block's run of each digit:
-        // exclusive digit total + this digit's count in earlier blocks.  The
-        // latter is summed with 16-byte loads: thread t takes digits
-        // 4 (t mod 128) .. 4 (t mod 128) + 3 of the earlier blocks b = t / 128
-        // (mod 8), four rows' loads in flight, into s_part[8][R] (and the
-        // pair-count sums of the last pass into s_part[8 + 8][R]: s_wcnt is
-        // free here and holds exactly these 16 R words).
-        {
-            uint32_t* s_part = reinterpret_cast<uint32_t*>(s_wcnt);
-            const uint32_t q = tid & 127, g = tid >> 7;
-            const uint4* cnt4 = reinterpret_cast<const uint4*>(a.cnt) + q;
-            const uint4* csum4 = reinterpret_cast<const uint4*>(a.csum) + q;
-            constexpr uint32_t RQ = R / 4;   // 16-byte words per row
-            uint4 p = make_uint4(0, 0, 0, 0);
-            {
-                uint32_t b = g;
-                for (; b + 24 < blockIdx.x; b += 32) {
-                    uint4 v[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) v[u] = __ldcg(cnt4 + (size_t)(b + 8 * u) * RQ);
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) { p.x += v[u].x; p.y += v[u].y; p.z += v[u].z; p.w += v[u].w; }
-                }
-                for (; b < blockIdx.x; b += 8) {
-                    const uint4 v = __ldcg(cnt4 + (size_t)b * RQ);
-                    p.x += v.x; p.y += v.y; p.z += v.z; p.w += v.w;
-                }
-            }
-            reinterpret_cast<uint4*>(s_part + g * R)[q] = p;
-            if (last) {
-                uint4 c = make_uint4(0, 0, 0, 0);
-                uint32_t b = g;
-                for (; b + 24 < blockIdx.x; b += 32) {
-                    uint4 v[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) v[u] = __ldcg(csum4 + (size_t)(b + 8 * u) * RQ);
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) { c.x += v[u].x; c.y += v[u].y; c.z += v[u].z; c.w += v[u].w; }
-                }
-                for (; b < blockIdx.x; b += 8) {
-                    const uint4 v = __ldcg(csum4 + (size_t)b * RQ);
-                    c.x += v.x; c.y += v.y; c.z += v.z; c.w += v.w;
-                }
-                reinterpret_cast<uint4*>(s_part + (8 + g) * R)[q] = c;
-            }
-        }
-        __syncthreads();
         if (tid < (int)R) {
             const uint32_t* s_part = reinterpret_cast<const uint32_t*>(s_wcnt);
-            const uint32_t tot = __ldcg(a.tot + pass * R + tid);
             uint32_t pre = 0;
 #pragma unroll
             for (int g = 0; g < 8; ++g) pre += s_part[g * R + tid];
@@ -459,7 +503,6 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
                 uint32_t cpre = 0;
 #pragma unroll
                 for (int g = 8; g < 16; ++g) cpre += s_part[g * R + tid];
-                const uint32_t ctot = __ldcg(a.tot + kDsMaxPasses * R + tid);
                 uint32_t xc = ctot;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {

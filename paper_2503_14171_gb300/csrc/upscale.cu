@@ -34,6 +34,8 @@
 // pixel's 12 values (C, C_x, C_y, C_xy for three channels) packed as three
 // float4 -- in shared memory with coalesced loads.  48 B per low-res pixel in,
 // 12 B per output pixel out.
+#include <atomic>
+
 #include "gs_internal.cuh"
 #include "spline_common.cuh"
 
@@ -336,6 +338,26 @@ bool sizes_ok(int W, int H, int W2, int H2, int min_side)
            (long long)H2 <= (long long)kMaxFactor * H;
 }
 
+// The upscale kernels' dynamic shared memory limit (the largest footprint, at
+// factor 1), set once per device: an atomic bit per device, so concurrent
+// first calls from several host threads set the same value.
+template <typename F>
+cudaError_t upscale_attr(F kernel, std::atomic<uint64_t>& done)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = dev < 64 ? (uint64_t(1) << dev) : 0;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(3 * sizeof(float4) * kFootW * kFootH))) != cudaSuccess)
+        return e;
+    done.fetch_or(bit, std::memory_order_acq_rel);
+    return cudaSuccess;
+}
+std::atomic<uint64_t> g_upscale_attr{0};
+std::atomic<uint64_t> g_upscale_views_attr{0};
+
 }  // namespace
 
 cudaError_t launch_upscale_to(cudaStream_t s, const float* C, const float* grads, int W, int H, int W2, int H2,
@@ -343,13 +365,8 @@ cudaError_t launch_upscale_to(cudaStream_t s, const float* C, const float* grads
 {
     if (!sizes_ok(W, H, W2, H2, 2)) return cudaErrorInvalidValue;
     dim3 grid((W2 + kSplW - 1) / kSplW, (H2 + kSplH - 1) / kSplH);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_upscale, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(3 * sizeof(float4) * kFootW * kFootH));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    cudaError_t e = upscale_attr(k_upscale, g_upscale_attr);
+    if (e != cudaSuccess) return e;
     const int pitch = foot_w(W, W2);
     const size_t smem = 3 * sizeof(float4) * pitch * foot_h(H, H2);
     k_upscale<<<grid, kSplThreads, smem, s>>>(C, grads, W, H, W2, H2, pitch, out); note_launch();
@@ -366,13 +383,8 @@ cudaError_t launch_upscale_views(cudaStream_t s, const UpscaleViews& b)
         if (!sizes_ok(u.W, u.H, u.W2, u.H2, 2)) return cudaErrorInvalidValue;
         smem = std::max(smem, 3 * sizeof(float4) * foot_w(u.W, u.W2) * foot_h(u.H, u.H2));
     }
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_upscale_views, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(3 * sizeof(float4) * kFootW * kFootH));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    cudaError_t e = upscale_attr(k_upscale_views, g_upscale_views_attr);
+    if (e != cudaSuccess) return e;
     k_upscale_views<<<total, kSplThreads, smem, s>>>(b); note_launch();
     return cudaGetLastError();
 }
