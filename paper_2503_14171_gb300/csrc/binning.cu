@@ -19,6 +19,14 @@
 namespace gs {
 namespace {
 
+// One thread per position of the depth order loads its Gaussian (sorted id,
+// first pair slot, pair count, rect); the warp then emits the pairs of its 32
+// Gaussians together, 32 at a time: lane l takes pair p = base + l of the
+// warp's run, finds the Gaussian that owns it (a binary search over the
+// lanes' run starts by shuffles), and forms the pair from that Gaussian's
+// rect.  A Gaussian's pairs keep the per-Gaussian order (super-tile rows,
+// then columns); a lane no longer loops over a large Gaussian's pairs while
+// the rest of its warp idles.
 // COUNT: also accumulate per-super-tile pair counts (shared memory, then one
 // atomic per touched super-tile and block).  KS: the super-tile side (1, 2, 4).
 template <bool COUNT, int KS>
@@ -32,30 +40,71 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ ids, 
         for (uint32_t t = threadIdx.x; t < Ts; t += blockDim.x) s_cnt[t] = 0;
         __syncthreads();
     }
+    constexpr int ks = KS, ksh = KS == 4 ? 2 : KS == 2 ? 1 : 0;
+    const int lane = threadIdx.x & 31;
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    // this lane's Gaussian: pair count c (0 when it has none or k >= n),
+    // first slot off, its super-tile columns nsx, first super-tile (sx0, sy0)
+    uint32_t c = 0, off = 0, id = 0, r01 = 0, r23 = 0;
     if (k < n) {
         const uint32_t base = rebase ? offsets[0] : 0u;
-        uint32_t off = offsets[k] - base;
+        off = offsets[k] - base;
         const uint32_t end = offsets[k + 1] - base;
-        const uint32_t id = ids[k] - id_base;
+        id = ids[k] - id_base;
         if (off < end && id < n) {   // id >= n only after an expired bounded wait in the sort
             const ushort4 r = rect[id];
-            constexpr int ks = KS, ksh = KS == 4 ? 2 : KS == 2 ? 1 : 0;
-            const int sx0 = r.x >> ksh, sx1 = r.z >> ksh, sy0 = r.y >> ksh, sy1 = r.w >> ksh;
-            for (int sy = sy0; sy <= sy1; ++sy) {
-                // rows of the super-tile's ks x ks tiles inside the rect
-                const int ly0 = max((int)r.y - (sy << ksh), 0), ly1 = min((int)r.w - (sy << ksh), ks - 1);
-                for (int sx = sx0; sx <= sx1 && off < end; ++sx) {
-                    const int lx0 = max((int)r.x - (sx << ksh), 0), lx1 = min((int)r.z - (sx << ksh), ks - 1);
-                    const uint32_t cols = ((2u << lx1) - 1u) & ~((1u << lx0) - 1u);
-                    uint32_t mask = 0;
-                    for (int ly = ly0; ly <= ly1; ++ly) mask |= cols << (ly << ksh);
-                    const uint32_t s = (uint32_t)(sy * stiles_x + sx);
-                    if (off < cap) pairs[off] = ((uint64_t)mask << 48) | ((uint64_t)s << 32) | id;
-                    ++off;
-                    if (COUNT && s < Ts) atomicAdd(&s_cnt[s], 1u);
-                }
-            }
+            r01 = (uint32_t)r.x | ((uint32_t)r.y << 16);
+            r23 = (uint32_t)r.z | ((uint32_t)r.w << 16);
+            c = end - off;
+        }
+    }
+    // run start of each lane's pairs within the warp (exclusive scan) and the total
+    uint32_t st = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, st, o);
+        if (lane >= o) st += y;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, st, 31);
+    st -= c;
+    for (uint32_t pb = 0; pb < total; pb += 32) {
+        const uint32_t p = pb + lane;
+        // owner: the largest lane whose run starts at or before p (lanes
+        // without pairs share their start with the next lane, so the largest
+        // such lane owns p whenever p < total)
+        int L = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint32_t sc = __shfl_sync(0xffffffffu, st, L + step);
+            if (sc <= p) L += step;
+        }
+        const uint32_t q = p - __shfl_sync(0xffffffffu, st, L);
+        const uint32_t o_off = __shfl_sync(0xffffffffu, off, L);
+        const uint32_t o_id = __shfl_sync(0xffffffffu, id, L);
+        const uint32_t o01 = __shfl_sync(0xffffffffu, r01, L);
+        const uint32_t o23 = __shfl_sync(0xffffffffu, r23, L);
+        if (p < total) {
+            const int rx = (int)(o01 & 0xFFFFu), ry = (int)(o01 >> 16);
+            const int rz = (int)(o23 & 0xFFFFu), rw = (int)(o23 >> 16);
+            const int sx0 = rx >> ksh, sy0 = ry >> ksh;
+            const uint32_t nsx = (uint32_t)((rz >> ksh) - sx0 + 1);
+            // q = (sy - sy0) nsx + (sx - sx0): below 2^21 the FP32 quotient
+            // (q + 1/2) / nsx is within 2^-22 (q + 1/2) / nsx of its value, which
+            // lies at least 1 / (2 nsx) from an integer, so it floors exactly
+            const uint32_t dy = q < (1u << 21) ? (uint32_t)(((float)q + 0.5f) * __frcp_rn((float)nsx)) : q / nsx;
+            const int sy = sy0 + (int)dy, sx = sx0 + (int)(q - dy * nsx);
+            // rows and columns of the super-tile's ks x ks tiles inside the rect
+            const int ly0 = max(ry - (sy << ksh), 0), ly1 = min(rw - (sy << ksh), ks - 1);
+            const int lx0 = max(rx - (sx << ksh), 0), lx1 = min(rz - (sx << ksh), ks - 1);
+            const uint32_t cols = ((2u << lx1) - 1u) & ~((1u << lx0) - 1u);
+            uint32_t mask = 0;
+#pragma unroll
+            for (int ly = 0; ly < ks; ++ly)
+                if (ly >= ly0 && ly <= ly1) mask |= cols << (ly << ksh);
+            const uint32_t s = (uint32_t)(sy * stiles_x + sx);
+            const uint32_t slot = o_off + q;
+            if (slot < cap) pairs[slot] = ((uint64_t)mask << 48) | ((uint64_t)s << 32) | o_id;
+            if (COUNT && s < Ts) atomicAdd(&s_cnt[s], 1u);
         }
     }
     if (COUNT) {
