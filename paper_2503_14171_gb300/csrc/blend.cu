@@ -37,6 +37,17 @@ namespace {
 
 constexpr int kStage = 2 * kCand;        // staged records per batch (>= kCand before blending)
 
+// Records the walk takes together, and the launch bound (blocks per SM) that
+// leaves the registers for them: with derivatives 3 records at 4 blocks/SM
+// (64 registers), without 2 at 5 (48).  Measured per (records, blocks/SM),
+// derivative blend at 960x540 / 480x270 and plain blend at 1920x1080, in µs:
+// (1, 5) 176 / 121 / 340; (2, 4) 164-174 / 96-100 / 313-334; (3, 4) 166 / 98 /
+// 320; (3, 3) 182 / 92 / 320; (4, 3) 182 / 92 / 320; (2, 5) 180 / 113 / 313.
+template <bool GRADS>
+__host__ __device__ constexpr int blend_unroll() { return GRADS ? 3 : 2; }
+template <bool GRADS>
+__host__ __device__ constexpr int blend_min_blocks() { return GRADS ? 4 : 5; }
+
 struct PixelState {
     float T, Tx, Ty, Txy;
     float C0, C1, C2, X0, X1, X2, Y0, Y1, Y2, Z0, Z1, Z2;
@@ -71,7 +82,10 @@ __device__ __forceinline__ bool blend_pair(PixelState& p, float g2, float dx, fl
         clamped = alpha > 0.99f;
         alpha = fminf(alpha, 0.99f);
     }
-    const float Tn = p.T * (1.f - alpha);
+    // every multiply-add below is spelled out (fmaf, or an intrinsic that is
+    // never fused): the walk's unrolled copies of this function then round
+    // alike wherever the compiler places them
+    const float Tn = p.T * __fsub_rn(1.f, alpha);
     if (MODE == GS_MODE_3DGS && Tn < 1e-4f) {
         p.done = true;
         return false;
@@ -88,13 +102,13 @@ __device__ __forceinline__ bool blend_pair(PixelState& p, float g2, float dx, fl
         if (clamped) { gx = 0.f; gy = 0.f; gxy = 0.f; }
         const float wx = alpha * fmaf(p.T, gx, p.Tx);
         const float wy = alpha * fmaf(p.T, gy, p.Ty);
-        const float wxy = alpha * (p.T * gxy + p.Tx * gy + p.Ty * gx + p.Txy);
+        const float wxy = alpha * fmaf(p.T, gxy, fmaf(p.Tx, gy, fmaf(p.Ty, gx, p.Txy)));
         p.X0 = fmaf(c.x, wx, p.X0); p.X1 = fmaf(c.y, wx, p.X1); p.X2 = fmaf(c.z, wx, p.X2);
         p.Y0 = fmaf(c.x, wy, p.Y0); p.Y1 = fmaf(c.y, wy, p.Y1); p.Y2 = fmaf(c.z, wy, p.Y2);
         p.Z0 = fmaf(c.x, wxy, p.Z0); p.Z1 = fmaf(c.y, wxy, p.Z1); p.Z2 = fmaf(c.z, wxy, p.Z2);
-        p.Tx -= wx;
-        p.Ty -= wy;
-        p.Txy -= wxy;
+        p.Tx = __fsub_rn(p.Tx, wx);
+        p.Ty = __fsub_rn(p.Ty, wy);
+        p.Txy = __fsub_rn(p.Txy, wxy);
     }
     p.T = Tn;
     p.last = idx + 1;
@@ -136,6 +150,10 @@ template <bool GRADS, int MODE, bool STATS, int MAP>
 __device__ __forceinline__ void blend_tile(const BlendArgs& a, int tile, unsigned long long* __restrict__ stats,
                                            uint32_t* work_slot)
 {
+    // records taken together by the walk below: their loads and exponents are
+    // formed before any of them is applied (they do not depend on the pixel's
+    // state), which leaves the walk's dependency chain the state update alone
+    constexpr int U = blend_unroll<GRADS>();
     __shared__ float4 s_r0[kStage];
     __shared__ float4 s_r1[kStage];
     __shared__ float4 s_r2[kStage];
@@ -198,7 +216,29 @@ __device__ __forceinline__ void blend_tile(const BlendArgs& a, int tile, unsigne
             if (cn < total) chit = pair_hit(a.pair_words, sr.x + cn, a.n, tbit, cid);
             __syncthreads();   // s_wcnt is reused by the next round; staged records are visible
         }
-        for (int k = 0; k < staged && !p.done; ++k) {
+        int k = 0;
+        for (; k + U - 1 < staged && !p.done; k += U) {
+            float4 q0[U], q1[U];
+            float qdx[U], qdy[U], qg2[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                q0[u] = s_r0[k + u];
+                q1[u] = s_r1[k + u];
+                qdx[u] = px - q0[u].x;
+                qdy[u] = py - q0[u].y;
+                qg2[u] = exponent2(q1[u], qdx[u], qdy[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (u > 0 && p.done) break;
+                if (STATS) ++n_eval;
+                if (MODE == GS_MODE_3DGS && qg2[u] < q1[u].w) continue;
+                const float4 c = s_r2[k + u];
+                if (blend_pair<GRADS, MODE>(p, qg2[u], qdx[u], qdy[u], q0[u], q1[u], c, list_base + k + u) && STATS)
+                    ++n_acc;
+            }
+        }
+        for (; k < staged && !p.done; ++k) {   // the batch's last records, one at a time
             const float4 r0 = s_r0[k];
             const float4 r1 = s_r1[k];
             const float dx = px - r0.x, dy = py - r0.y;
@@ -228,7 +268,8 @@ __device__ __forceinline__ void blend_tile(const BlendArgs& a, int tile, unsigne
 }
 
 template <bool GRADS, int MODE, bool STATS = false>
-__global__ void __launch_bounds__(kThreads, 5) k_blend(BlendArgs a, unsigned long long* __restrict__ stats = nullptr)
+__global__ void __launch_bounds__(kThreads, blend_min_blocks<GRADS>()) k_blend(BlendArgs a,
+                                                                             unsigned long long* __restrict__ stats = nullptr)
 {
     const int tile = a.order ? (int)a.order[blockIdx.x] : (int)blockIdx.x;
     blend_tile<GRADS, MODE, STATS, 0>(a, tile, stats, a.work ? a.work + tile : nullptr);
@@ -239,7 +280,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_blend(BlendArgs a, unsigned lon
 // PERSIST: a grid of resident blocks takes jobs from a counter in turn;
 // otherwise one block per job.
 template <bool GRADS, int MODE, int MAP, bool PERSIST>
-__global__ void __launch_bounds__(kThreads, 5) k_blend_views(const __grid_constant__ BlendViews b)
+__global__ void __launch_bounds__(kThreads, blend_min_blocks<GRADS>()) k_blend_views(const __grid_constant__ BlendViews b)
 {
     __shared__ int s_job;
     const int total = b.start[b.V];

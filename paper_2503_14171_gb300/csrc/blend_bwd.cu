@@ -100,7 +100,7 @@ __device__ __forceinline__ bool bwd_entry(BwdPixel& p, const float4& r0, const f
     float gxy = fmaf(gx, gy, bn);
     if (clamped) { gx = 0.f; gy = 0.f; gxy = 0.f; }
     // state before the step
-    const float iom = __fdividef(1.f, 1.f - alpha);
+    const float iom = __fdividef(1.f, __fsub_rn(1.f, alpha));
     const float T0 = p.T * iom;
     const float Tx0 = fmaf(alpha * T0, gx, p.Tx) * iom;
     const float Ty0 = fmaf(alpha * T0, gy, p.Ty) * iom;
@@ -187,7 +187,7 @@ __device__ __forceinline__ bool fwd_state_step(BwdPixel& p, bool& done, const fl
         clamped = alpha > 0.99f;
         alpha = fminf(alpha, 0.99f);
     }
-    const float Tn = p.T * (1.f - alpha);
+    const float Tn = p.T * __fsub_rn(1.f, alpha);   // as the forward's blend_pair
     if (MODE == GS_MODE_3DGS && Tn < 1e-4f) {
         done = true;
         return false;
@@ -199,10 +199,10 @@ __device__ __forceinline__ bool fwd_state_step(BwdPixel& p, bool& done, const fl
     if (clamped) { gx = 0.f; gy = 0.f; gxy = 0.f; }
     const float wx = alpha * fmaf(p.T, gx, p.Tx);
     const float wy = alpha * fmaf(p.T, gy, p.Ty);
-    const float wxy = alpha * (p.T * gxy + p.Tx * gy + p.Ty * gx + p.Txy);
-    p.Tx -= wx;
-    p.Ty -= wy;
-    p.Txy -= wxy;
+    const float wxy = alpha * fmaf(p.T, gxy, fmaf(p.Tx, gy, fmaf(p.Ty, gx, p.Txy)));
+    p.Tx = __fsub_rn(p.Tx, wx);
+    p.Ty = __fsub_rn(p.Ty, wy);
+    p.Txy = __fsub_rn(p.Txy, wxy);
     p.T = Tn;
     return true;
 }
