@@ -39,14 +39,17 @@ constexpr int kStage = 2 * kCand;        // staged records per batch (>= kCand b
 
 // Records the walk takes together, and the launch bound (blocks per SM) that
 // leaves the registers for them: with derivatives 3 records at 4 blocks/SM
-// (64 registers), without 2 at 5 (48).  Measured per (records, blocks/SM),
-// derivative blend at 960x540 / 480x270 and plain blend at 1920x1080, in µs:
-// (1, 5) 176 / 121 / 340; (2, 4) 164-174 / 96-100 / 313-334; (3, 4) 166 / 98 /
-// 320; (3, 3) 182 / 92 / 320; (4, 3) 182 / 92 / 320; (2, 5) 180 / 113 / 313.
-template <bool GRADS>
-__host__ __device__ constexpr int blend_unroll() { return GRADS ? 3 : 2; }
-template <bool GRADS>
-__host__ __device__ constexpr int blend_min_blocks() { return GRADS ? 4 : 5; }
+// (64 registers), without 2 at 5 (48); WIDE (frames of at most 4 tiles per
+// SM, one wave of blocks): 4 records at 3 blocks/SM.  Measured per (records,
+// blocks/SM), derivative blend at 960x540 / 640x360 / 480x270 / 320x180 and
+// plain blend at 1920x1080, in µs: (1, 5) 176 / - / 121 / - / 340; (2, 4)
+// 164-174 / - / 96-100 / - / 313-334; (3, 4) 164-170 / 106-109 / 96-100 / 86-90 /
+// 320; (3, 3) 180 / 104 / 92 / 88 / 320; (4, 3) 180 / 104 / 92 / 86 / 320;
+// (2, 5) 180 / - / 113 / - / 313.
+template <bool GRADS, bool WIDE = false>
+__host__ __device__ constexpr int blend_unroll() { return WIDE ? 4 : GRADS ? 3 : 2; }
+template <bool GRADS, bool WIDE = false>
+__host__ __device__ constexpr int blend_min_blocks() { return WIDE ? 3 : GRADS ? 4 : 5; }
 
 struct PixelState {
     float T, Tx, Ty, Txy;
@@ -146,14 +149,14 @@ __device__ __forceinline__ void store(const BlendArgs& a, const PixelState& p, i
 // (two blocks across, four down: a compact block makes the lanes of a warp
 // agree more often on whether a Gaussian reaches them), 1 = a 16 x 2 strip.
 // work_slot, when given, receives the tile's duration (clock64 / 16).
-template <bool GRADS, int MODE, bool STATS, int MAP>
+template <bool GRADS, int MODE, bool STATS, int MAP, int U>
 __device__ __forceinline__ void blend_tile(const BlendArgs& a, int tile, unsigned long long* __restrict__ stats,
                                            uint32_t* work_slot)
 {
-    // records taken together by the walk below: their loads and exponents are
-    // formed before any of them is applied (they do not depend on the pixel's
-    // state), which leaves the walk's dependency chain the state update alone
-    constexpr int U = blend_unroll<GRADS>();
+    // U records taken together by the walk below: their loads and exponents
+    // are formed before any of them is applied (they do not depend on the
+    // pixel's state), which leaves the walk's dependency chain the state
+    // update alone
     __shared__ float4 s_r0[kStage];
     __shared__ float4 s_r1[kStage];
     __shared__ float4 s_r2[kStage];
@@ -267,12 +270,12 @@ __device__ __forceinline__ void blend_tile(const BlendArgs& a, int tile, unsigne
     if (x < a.W && y < a.H) store<GRADS>(a, p, x, y);
 }
 
-template <bool GRADS, int MODE, bool STATS = false>
-__global__ void __launch_bounds__(kThreads, blend_min_blocks<GRADS>()) k_blend(BlendArgs a,
-                                                                             unsigned long long* __restrict__ stats = nullptr)
+template <bool GRADS, int MODE, bool STATS = false, bool WIDE = false>
+__global__ void __launch_bounds__(kThreads, blend_min_blocks<GRADS, WIDE>())
+    k_blend(BlendArgs a, unsigned long long* __restrict__ stats = nullptr)
 {
     const int tile = a.order ? (int)a.order[blockIdx.x] : (int)blockIdx.x;
-    blend_tile<GRADS, MODE, STATS, 0>(a, tile, stats, a.work ? a.work + tile : nullptr);
+    blend_tile<GRADS, MODE, STATS, 0, blend_unroll<GRADS, WIDE>()>(a, tile, stats, a.work ? a.work + tile : nullptr);
 }
 
 // The tiles of every view of a batch in one launch: job j is global tile
@@ -295,7 +298,8 @@ __global__ void __launch_bounds__(kThreads, blend_min_blocks<GRADS>()) k_blend_v
         const int g = b.order ? (int)b.order[j] : j;
         int v = 0;
         while (v + 1 < b.V && g >= b.start[v + 1]) ++v;
-        blend_tile<GRADS, MODE, false, MAP>(b.a[v], g - b.start[v], nullptr, b.work ? b.work + g : nullptr);
+        blend_tile<GRADS, MODE, false, MAP, blend_unroll<GRADS>()>(b.a[v], g - b.start[v], nullptr,
+                                                                 b.work ? b.work + g : nullptr);
         if (!PERSIST) break;
     }
 }
@@ -303,7 +307,19 @@ __global__ void __launch_bounds__(kThreads, blend_min_blocks<GRADS>()) k_blend_v
 template <bool GRADS, int MODE>
 cudaError_t launch_t(cudaStream_t s, const BlendArgs& a)
 {
-    k_blend<GRADS, MODE><<<a.tiles_x * a.tiles_y, kThreads, 0, s>>>(a); note_launch();
+    const int T = a.tiles_x * a.tiles_y;
+    bool wide = false;
+    if (GRADS) {   // one wave of blocks at 4 per SM: the WIDE shape
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+            wide = T <= 4 * sms;
+    }
+    if (wide)
+        k_blend<GRADS, MODE, false, GRADS><<<T, kThreads, 0, s>>>(a);
+    else
+        k_blend<GRADS, MODE><<<T, kThreads, 0, s>>>(a);
+    note_launch();
     return cudaGetLastError();
 }
 
