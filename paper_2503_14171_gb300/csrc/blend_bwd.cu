@@ -78,64 +78,97 @@ struct BwdPixel {
     float uC[3], uX[3], uY[3], uZ[3];
 };
 
-// One list entry for one pixel: returns the pixel's 9 gradient terms in v
-// (zero if the pair was not blended) and steps the state and its adjoint back.
+// The part of one list entry's step that does not depend on the pixel's
+// state: the pair's offset, exponent, decisions, alpha and its slopes, and the
+// upstream gradients dotted with the colour.  The walk forms it for a group of
+// entries before applying them (bwd_apply) one after the other.
+struct BwdPrep {
+    float dx, dy, alpha, gx, gy, gxy, bn, iom, ax, ay, axy;
+    float dC, dX, dY, dZ;   // u . c of the four upstream gradient groups
+    float sigma, ca, cc;
+    bool keep, clamped;
+};
+
 template <int MODE>
-__device__ __forceinline__ bool bwd_entry(BwdPixel& p, const float4& r0, const float4& r1, const float4& c,
-                                          float v[9])
+__device__ __forceinline__ void bwd_prep(const BwdPixel& p, const float4& r0, const float4& r1, const float4& c,
+                                         bool listed, BwdPrep& q)
 {
-    const float dx = p.px - r0.x, dy = p.py - r0.y;
-    const float g2 = exponent2(r1, dx, dy);
-    if (MODE == GS_MODE_3DGS && g2 < r1.w) return false;
-    float alpha = c.w * pow2(g2);
-    bool clamped = false;
-    if (MODE == GS_MODE_3DGS) {
-        if (alpha < (1.f / 255.f)) return false;
-        clamped = alpha > 0.99f;
-        alpha = fminf(alpha, 0.99f);
+    q.dx = p.px - r0.x;
+    q.dy = p.py - r0.y;
+    const float g2 = exponent2(r1, q.dx, q.dy);
+    q.keep = listed && !(MODE == GS_MODE_3DGS && g2 < r1.w);
+    q.clamped = false;
+    q.alpha = 0.f;
+    if (q.keep) {
+        float alpha = c.w * pow2(g2);
+        if (MODE == GS_MODE_3DGS) {
+            if (alpha < (1.f / 255.f)) q.keep = false;
+            q.clamped = alpha > 0.99f;
+            alpha = fminf(alpha, 0.99f);
+        }
+        q.alpha = alpha;
     }
-    const float bn = r1.y * kLn2;   // -b
-    float gx = fmaf(r0.z, dx, bn * dy);
-    float gy = fmaf(r0.w, dy, bn * dx);
-    float gxy = fmaf(gx, gy, bn);
-    if (clamped) { gx = 0.f; gy = 0.f; gxy = 0.f; }
-    // state before the step
-    const float iom = __fdividef(1.f, __fsub_rn(1.f, alpha));
+    q.bn = r1.y * kLn2;   // -b
+    q.gx = fmaf(r0.z, q.dx, q.bn * q.dy);
+    q.gy = fmaf(r0.w, q.dy, q.bn * q.dx);
+    q.gxy = fmaf(q.gx, q.gy, q.bn);
+    if (q.clamped) { q.gx = 0.f; q.gy = 0.f; q.gxy = 0.f; }
+    q.iom = __fdividef(1.f, __fsub_rn(1.f, q.alpha));
+    q.ax = q.alpha * q.gx;
+    q.ay = q.alpha * q.gy;
+    q.axy = q.alpha * q.gxy;
+    q.dC = fmaf(p.uC[2], c.z, fmaf(p.uC[1], c.y, p.uC[0] * c.x));
+    q.dX = fmaf(p.uX[2], c.z, fmaf(p.uX[1], c.y, p.uX[0] * c.x));
+    q.dY = fmaf(p.uY[2], c.z, fmaf(p.uY[1], c.y, p.uY[0] * c.x));
+    q.dZ = fmaf(p.uZ[2], c.z, fmaf(p.uZ[1], c.y, p.uZ[0] * c.x));
+    q.sigma = c.w;
+    q.ca = -r0.z;
+    q.cc = -r0.w;
+}
+
+// The state-dependent rest of one list entry's step for one pixel: the
+// pixel's 9 gradient terms in v and the state and its adjoint stepped back;
+// false (v untouched) for an entry the forward did not blend.
+__device__ __forceinline__ bool bwd_apply(BwdPixel& p, const BwdPrep& q, float v[9])
+{
+    if (!q.keep) return false;
+    const float alpha = q.alpha, gx = q.gx, gy = q.gy, gxy = q.gxy, iom = q.iom;
     const float T0 = p.T * iom;
     const float Tx0 = fmaf(alpha * T0, gx, p.Tx) * iom;
     const float Ty0 = fmaf(alpha * T0, gy, p.Ty) * iom;
-    const float Txy0 = fmaf(alpha, T0 * gxy + Tx0 * gy + Ty0 * gx, p.Txy) * iom;
+    const float Txy0 = fmaf(alpha, fmaf(T0, gxy, fmaf(Tx0, gy, Ty0 * gx)), p.Txy) * iom;
     const float w = alpha * T0;
     const float wx = alpha * fmaf(T0, gx, Tx0);
     const float wy = alpha * fmaf(T0, gy, Ty0);
-    const float wxy = alpha * (T0 * gxy + Tx0 * gy + Ty0 * gx + Txy0);
+    const float wxy = alpha * fmaf(T0, gxy, fmaf(Tx0, gy, fmaf(Ty0, gx, Txy0)));
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) v[6 + ch] = p.uC[ch] * w + p.uX[ch] * wx + p.uY[ch] * wy + p.uZ[ch] * wxy;
-    const float Gw = p.uC[0] * c.x + p.uC[1] * c.y + p.uC[2] * c.z - p.lT;
-    const float Gwx = p.uX[0] * c.x + p.uX[1] * c.y + p.uX[2] * c.z - p.lTx;
-    const float Gwy = p.uY[0] * c.x + p.uY[1] * c.y + p.uY[2] * c.z - p.lTy;
-    const float Gwxy = p.uZ[0] * c.x + p.uZ[1] * c.y + p.uZ[2] * c.z - p.lTxy;
-    const float ax = alpha * gx, ay = alpha * gy, axy = alpha * gxy;
-    p.lT += Gw * alpha + Gwx * ax + Gwy * ay + Gwxy * axy;
-    p.lTx += Gwx * alpha + Gwxy * ay;
-    p.lTy += Gwy * alpha + Gwxy * ax;
-    p.lTxy += Gwxy * alpha;
-    if (!clamped) {
-        const float Ga = Gw * T0 + Gwx * Tx0 + Gwy * Ty0 + Gwxy * Txy0;
-        const float Gax = Gwx * T0 + Gwxy * Ty0;
-        const float Gay = Gwy * T0 + Gwxy * Tx0;
+    for (int ch = 0; ch < 3; ++ch)
+        v[6 + ch] = fmaf(p.uZ[ch], wxy, fmaf(p.uY[ch], wy, fmaf(p.uX[ch], wx, p.uC[ch] * w)));
+    const float Gw = __fsub_rn(q.dC, p.lT);
+    const float Gwx = __fsub_rn(q.dX, p.lTx);
+    const float Gwy = __fsub_rn(q.dY, p.lTy);
+    const float Gwxy = __fsub_rn(q.dZ, p.lTxy);
+    p.lT = __fadd_rn(p.lT, fmaf(Gwxy, q.axy, fmaf(Gwy, q.ay, fmaf(Gwx, q.ax, Gw * alpha))));
+    p.lTx = __fadd_rn(p.lTx, fmaf(Gwxy, q.ay, Gwx * alpha));
+    p.lTy = __fadd_rn(p.lTy, fmaf(Gwxy, q.ax, Gwy * alpha));
+    p.lTxy = fmaf(Gwxy, alpha, p.lTxy);
+    if (!q.clamped) {
+        const float Ga = fmaf(Gwxy, Txy0, fmaf(Gwy, Ty0, fmaf(Gwx, Tx0, Gw * T0)));
+        const float Gax = fmaf(Gwxy, Ty0, Gwx * T0);
+        const float Gay = fmaf(Gwxy, Tx0, Gwy * T0);
         const float Gaxy = Gwxy * T0;
-        const float dg = alpha * (Ga + Gax * gx + Gay * gy + Gaxy * gxy);
+        const float dg = alpha * fmaf(Gaxy, gxy, fmaf(Gay, gy, fmaf(Gax, gx, Ga)));
         const float dgx = alpha * fmaf(Gaxy, gy, Gax);
         const float dgy = alpha * fmaf(Gaxy, gx, Gay);
         const float dgxy = alpha * Gaxy;
-        const float ca = -r0.z, cb = -bn, cc = -r0.w;
-        v[0] = -dg * gx + ca * dgx + cb * dgy;
-        v[1] = -dg * gy + cb * dgx + cc * dgy;
-        v[2] = -0.5f * dx * dx * dg - dx * dgx;
-        v[3] = -dx * dy * dg - dy * dgx - dx * dgy - dgxy;
-        v[4] = -0.5f * dy * dy * dg - dy * dgy;
-        v[5] = __fdividef(dg, c.w);
+        const float cb = -q.bn;
+        const float dx = q.dx, dy = q.dy;
+        v[0] = fmaf(cb, dgy, fmaf(q.ca, dgx, -dg * gx));
+        v[1] = fmaf(q.cc, dgy, fmaf(cb, dgx, -dg * gy));
+        v[2] = fmaf(-0.5f * dx * dx, dg, -dx * dgx);
+        v[3] = __fsub_rn(fmaf(-dx * dy, dg, fmaf(-dy, dgx, -dx * dgy)), dgxy);
+        v[4] = fmaf(-0.5f * dy * dy, dg, -dy * dgy);
+        v[5] = __fdividef(dg, q.sigma);
     }
     p.T = T0; p.Tx = Tx0; p.Ty = Ty0; p.Txy = Txy0;
     return true;
@@ -172,13 +205,13 @@ __device__ __forceinline__ void warp_sum9_to_shared(float v[9], int lane, float*
 }
 
 // The forward blend's step of the transmittance state alone (same expressions
-// and decisions as the forward).  Returns true if the pair was blended; sets
-// done when the pixel stops before it.
+// and decisions as the forward), given the pair's offset (dx, dy) and
+// exponent g2.  Returns true if the pair was blended; sets done when the
+// pixel stops before it.
 template <int MODE>
-__device__ __forceinline__ bool fwd_state_step(BwdPixel& p, bool& done, const float4& r0, const float4& r1, float sigma)
+__device__ __forceinline__ bool fwd_state_step(BwdPixel& p, bool& done, float dx, float dy, float g2,
+                                               const float4& r0, const float4& r1, float sigma)
 {
-    const float dx = p.px - r0.x, dy = p.py - r0.y;
-    const float g2 = exponent2(r1, dx, dy);
     if (MODE == GS_MODE_3DGS && g2 < r1.w) return false;
     float alpha = sigma * pow2(g2);
     bool clamped = false;
@@ -333,8 +366,33 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_bwd(BlendBwdArgs a)
                 s_r2[k].w = a.rec.r2[id].w;
             }
             __syncthreads();
-            for (int k = 0; k < tot && !done; ++k)
-                if (fwd_state_step<MODE>(p, done, s_r0[k], s_r1[k], s_r2[k].w)) p.last = filt + k + 1;
+            // in groups of 3, as the forward walks: the records' offsets and
+            // exponents first, then the state steps in order
+            int k = 0;
+            for (; k + 2 < tot && !done; k += 3) {
+                float4 q0[3], q1[3];
+                float qdx[3], qdy[3], qg2[3], qs[3];
+#pragma unroll
+                for (int u = 0; u < 3; ++u) {
+                    q0[u] = s_r0[k + u];
+                    q1[u] = s_r1[k + u];
+                    qs[u] = s_r2[k + u].w;
+                    qdx[u] = p.px - q0[u].x;
+                    qdy[u] = p.py - q0[u].y;
+                    qg2[u] = exponent2(q1[u], qdx[u], qdy[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < 3; ++u) {
+                    if (u > 0 && done) break;
+                    if (fwd_state_step<MODE>(p, done, qdx[u], qdy[u], qg2[u], q0[u], q1[u], qs[u]))
+                        p.last = filt + k + u + 1;
+                }
+            }
+            for (; k < tot && !done; ++k) {
+                const float4 r0 = s_r0[k], r1 = s_r1[k];
+                const float dx = p.px - r0.x, dy = p.py - r0.y;
+                if (fwd_state_step<MODE>(p, done, dx, dy, exponent2(r1, dx, dy), r0, r1, s_r2[k].w)) p.last = filt + k + 1;
+            }
             filt += tot;
         }
         __syncthreads();
@@ -434,13 +492,37 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_bwd(BlendBwdArgs a)
                 }
             }
             __syncthreads();
-            for (int k = cnt - 1; k >= 0; --k) {
+            // entries in groups of two: both prepared (state-independent part)
+            // before either is applied, which leaves the state's step the
+            // loop-carried chain
+            int k = cnt - 1;
+            for (; k >= 1; k -= 2) {
+                BwdPrep qa, qb;
+                bwd_prep<MODE>(p, s_r0[k], s_r1[k], s_r2[k], fb + k < p.last, qa);
+                bwd_prep<MODE>(p, s_r0[k - 1], s_r1[k - 1], s_r2[k - 1], fb + k - 1 < p.last, qb);
+                {
+                    float v[9];
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) v[q] = 0.f;
+                    const bool contrib = bwd_apply(p, qa, v);
+                    if (__any_sync(0xffffffffu, contrib)) warp_sum9_to_shared(v, lane, s_acc[k]);
+                }
+                {
+                    float v[9];
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) v[q] = 0.f;
+                    const bool contrib = bwd_apply(p, qb, v);
+                    if (__any_sync(0xffffffffu, contrib)) warp_sum9_to_shared(v, lane, s_acc[k - 1]);
+                }
+            }
+            if (k == 0) {
+                BwdPrep q0;
+                bwd_prep<MODE>(p, s_r0[0], s_r1[0], s_r2[0], fb < p.last, q0);
                 float v[9];
 #pragma unroll
                 for (int q = 0; q < 9; ++q) v[q] = 0.f;
-                bool contrib = false;
-                if (fb + k < p.last) contrib = bwd_entry<MODE>(p, s_r0[k], s_r1[k], s_r2[k], v);
-                if (__ballot_sync(0xffffffffu, contrib)) warp_sum9_to_shared(v, lane, s_acc[k]);
+                const bool contrib = bwd_apply(p, q0, v);
+                if (__any_sync(0xffffffffu, contrib)) warp_sum9_to_shared(v, lane, s_acc[0]);
             }
             __syncthreads();
             if ((int)threadIdx.x < cnt) {
