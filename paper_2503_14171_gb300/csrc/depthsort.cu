@@ -531,18 +531,24 @@ __global__ void __launch_bounds__(kDsThreads, 1) k_depth_sort_scan(DsArgs a)
         }
         __syncthreads();
         // write the digit runs out: consecutive threads, consecutive addresses
-        for (uint32_t j = tid; j < m; j += kDsThreads) {
-            const uint32_t key = s_key2[j];
-            const uint32_t d = (key >> shift) & (R - 1);
-            const uint32_t pos = s_off[d] + j;
-            if (pos < n) {
-                const uint32_t v = s_id2[j];
-                if (!last) {
-                    dst_key[pos] = key;
-                    dst_id[pos] = v;
-                } else {   // last pass: plain ids and their first pair slots
-                    dst_id[pos] = v & kIdMask;
-                    a.offsets[pos] = s_obase[d] + s_key[j];
+        // (unrolled over the thread's kDsPer elements, so that their shared
+        // loads issue back to back)
+#pragma unroll
+        for (int k = 0; k < kDsPer; ++k) {
+            const uint32_t j = tid + k * kDsThreads;
+            if (j < m) {
+                const uint32_t key = s_key2[j];
+                const uint32_t d = (key >> shift) & (R - 1);
+                const uint32_t pos = s_off[d] + j;
+                if (pos < n) {
+                    const uint32_t v = s_id2[j];
+                    if (!last) {
+                        dst_key[pos] = key;
+                        dst_id[pos] = v;
+                    } else {   // last pass: plain ids and their first pair slots
+                        dst_id[pos] = v & kIdMask;
+                        a.offsets[pos] = s_obase[d] + s_key[j];
+                    }
                 }
             }
         }
