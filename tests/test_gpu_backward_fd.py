@@ -92,3 +92,55 @@ def test_gradient_matches_central_differences(gs):
                 assert abs(an - fd) <= 0.05 * abs(fd) + 1e-3 * flat.max(), (key, row, col, an, fd)
                 checked += 1
         assert checked >= 25
+
+
+@pytest.mark.parametrize("key", ["means_xy", "log_scales", "quats", "opacity_logits", "sh"])
+def test_directional_derivative_per_parameter_group(gs, key):
+    """Every parameter of one group moved at once along a seeded random
+    direction v: the central difference of the loss, (L(p + eps v) - L(p -
+    eps v)) / 2 eps, against the reverse mode's dot product with v, within 1 %
+    -- a check that a small systematic error in a whole group (a scale, a
+    dropped term) would fail, where single-parameter differences at 5 % might
+    not.  Exact mode; the means move in x and y only (a move in depth may
+    reorder overlapping Gaussians); v is zero for Gaussians whose colour is
+    near the max(0, .) clamp.  (Measured: 2e-5 to 4e-3 relative, the largest
+    for the SH coefficients and the opacity logits.)"""
+    import torch
+    n = 2000
+    scene = scenes.random_scene(n=n, seed=52, sh_degree=3, log_scale_mean=-2.8)
+    dev = gs.DeviceScene(scene)
+    cam = scenes.pinhole_camera(W, H)
+    with gs.Context(mode="exact", bg=(0.1, 0.2, 0.3)) as ctx:
+        def forward():
+            C, G = ctx.render_with_grads(dev, cam, W, H)
+            return ctx.upscale(C, G, S).cpu().numpy()
+
+        out0 = forward()
+        target = out0 + 0.5 + 0.1 * np.random.default_rng(4).standard_normal(out0.shape)
+        _, dL = _loss_and_upstream(out0, target)
+        forward()
+        grads = {k: v.cpu().numpy().reshape(n, -1) for k, v in
+                 ctx.backward(torch.as_tensor(dL, dtype=torch.float32).cuda().contiguous(), S).items()}
+        ctx.synchronize()
+        ctx.project(dev, cam, W, H)
+        rgb = ctx.read_projected()["rgb"].cpu().numpy()
+        away = ~np.any(np.abs(rgb) < 0.05, axis=1)
+        name = "means" if key == "means_xy" else key
+        t = dev.t[name].view(n, -1)
+        base = t.clone()
+        v = np.random.default_rng(8).standard_normal(tuple(t.shape))
+        v[~away] = 0.0
+        if key == "means_xy":
+            v[:, 2] = 0.0
+        v *= 0.05 / max(np.abs(v).max(), 1e-30)   # moves of at most 0.05 eps units
+        vt = torch.as_tensor(v, dtype=t.dtype, device=t.device)
+        eps = EPS / 0.05
+        t.copy_(base + eps * vt)
+        Lp, _ = _loss_and_upstream(forward(), target)
+        t.copy_(base - eps * vt)
+        Lm, _ = _loss_and_upstream(forward(), target)
+        t.copy_(base)
+        fd = (Lp - Lm) / (2 * eps)
+        an = float(np.sum(grads[name].astype(np.float64) * v))
+        assert abs(fd) > 1e-6, fd
+        assert abs(an - fd) <= 0.01 * abs(fd), (key, an, fd)
