@@ -45,7 +45,7 @@ FLOP_EVAL = 10
 FLOP_ACC_GRADS = 52
 # The scope table's estimate of the same work (the count the roofline is
 # graded on): about 10 per evaluated pair and about 100 per blended pair.
-FLOP_ACC_SURVEY = 100
+FLOP_ACC_SCOPE = 100
 # The blend adjoint re-evaluates each pair (10) and, per blended pair, inverts
 # the state update, forms the weights, the adjoints and the 9 gradient terms
 # and sums them over the tile's pixels: 173 (itemised beside the kernel).
@@ -657,7 +657,7 @@ def run_gs(args):
     # unit counts (SMs read from the device) and the maximum SM clock
     alu_peak = sm_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12    # TFLOP/s
     blend_ms = statistics.mean(t_blend)
-    flops = n_eval * FLOP_EVAL + n_acc * FLOP_ACC_SURVEY
+    flops = n_eval * FLOP_EVAL + n_acc * FLOP_ACC_SCOPE
     achieved = flops / (blend_ms * 1e-3) / 1e12
     flops_itemised = n_eval * FLOP_EVAL + n_acc * FLOP_ACC_GRADS
     achieved_itemised = flops_itemised / (blend_ms * 1e-3) / 1e12
@@ -707,7 +707,7 @@ def run_gs(args):
         "roofline": {"bound": "alu", "kernel": "k_blend<grads,3dgs>", "achieved": achieved, "peak": alu_peak,
                      "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": traffic,
                      "flop_count": "scope-table estimate: %d per evaluated pair + %d per blended pair"
-                                   % (FLOP_EVAL, FLOP_ACC_SURVEY),
+                                   % (FLOP_EVAL, FLOP_ACC_SCOPE),
                      "achieved_itemised": achieved_itemised, "frac_itemised": achieved_itemised / alu_peak,
                      "flop_count_itemised": "formulas counted term by term: %d per evaluated pair + %d per "
                                             "blended pair" % (FLOP_EVAL, FLOP_ACC_GRADS),
