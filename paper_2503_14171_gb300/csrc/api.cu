@@ -1082,6 +1082,7 @@ gs_status render_views_impl(gs_ctx* c, const gs_gaussians* scenes, int32_t S, co
     vo.depth_key = k32[0];
     vo.gidx = v32[0];
     vo.totals = vtot;
+    vo.pack_counts = total <= kPackedIdxMask;   // entries in the low 24 bits, the pair count above
     for (int k = 0; k < S; ++k) {   // one projection launch per Gaussian set, over its views
         const int nv = set_first[k + 1] - set_first[k];
         if (nv > 0)
@@ -1120,7 +1121,7 @@ gs_status render_views_impl(gs_ctx* c, const gs_gaussians* scenes, int32_t S, co
     unsigned long long* scan_tot = as<unsigned long long>(c->scan_totals) + 2 * kTotalSlots;
     GS_CUDA(c, launch_scan_gathered(s, as<uint32_t>(c->vsupers), nullptr, vsorted, total, as<uint32_t>(c->offsets),
                                     as<unsigned long long>(c->scan_partials), reinterpret_cast<uint32_t*>(scan_tot + 2),
-                                    scan_tot, as<int>(c->errword)));
+                                    scan_tot, as<int>(c->errword), vo.pack_counts));
 
     // per view: its pair buffers, counts, histograms, sort state and ranges
     const int64_t limit = c->opt.max_pairs > 0 ? std::min<int64_t>(c->opt.max_pairs, kMaxPairs) : kMaxPairs;
@@ -1215,7 +1216,8 @@ gs_status render_views_impl(gs_ctx* c, const gs_gaussians* scenes, int32_t S, co
             ++uv.V;
         }
     }
-    GS_CUDA(c, launch_emit_views(s, ev, vsorted, as<uint32_t>(c->offsets), as<ushort4>(c->vrect), total));
+    GS_CUDA(c, launch_emit_views(s, ev, vsorted, as<uint32_t>(c->offsets), as<ushort4>(c->vrect), total,
+                                 vo.pack_counts));
     GS_CUDA(c, launch_supers_to_hist_views(s, hv, as<int>(c->errword)));
     GS_CUDA(c, radix_sort_u64_segs(s, sg));
     const int tiles_total = bv.start[V];

@@ -128,7 +128,8 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ ids, 
 __global__ void __launch_bounds__(256) k_emit_views(const __grid_constant__ EmitViews b,
                                                     const uint32_t* __restrict__ sorted,
                                                     const uint32_t* __restrict__ offsets,
-                                                    const ushort4* __restrict__ rect, uint32_t total)
+                                                    const ushort4* __restrict__ rect, uint32_t total,
+                                                    uint32_t idx_mask)
 {
     __shared__ uint32_t s_cnt[kMaxSupersForCounts];
     const uint32_t k0 = blockIdx.x * blockDim.x;
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(256) k_emit_views(const __grid_constant__ Emit
         const uint32_t base = offsets[e.start];
         uint32_t off = offsets[k] - base;
         const uint32_t end = offsets[k + 1] - base;
-        const uint32_t g = sorted[k];
+        const uint32_t g = sorted[k] & idx_mask;   // a packed count in the top bits is not needed here
         const uint32_t id = g - e.start;
         if (off < end && id < e.n) {   // id >= n only after an expired bounded wait in the sort
             const ushort4 r = rect[g];
@@ -354,10 +355,12 @@ cudaError_t launch_emit_pairs(cudaStream_t s, const uint32_t* ids, const uint32_
 }
 
 cudaError_t launch_emit_views(cudaStream_t s, const EmitViews& b, const uint32_t* sorted, const uint32_t* offsets,
-                              const ushort4* rect, uint32_t total)
+                              const ushort4* rect, uint32_t total, bool packed)
 {
     if (total == 0 || b.V <= 0) return cudaSuccess;
-    k_emit_views<<<(total + 255) / 256, 256, 0, s>>>(b, sorted, offsets, rect, total); note_launch();
+    k_emit_views<<<(total + 255) / 256, 256, 0, s>>>(b, sorted, offsets, rect, total,
+                                                   packed ? kPackedIdxMask : 0xFFFFFFFFu);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -235,7 +235,12 @@ struct ViewDesc {
 // g = off_v + i (totals: 2 kTotalSlots per view, at vid): records, rect,
 // super-tiles touched, and the input of the views' depth sorts,
 // depth_key[g] = FP32 depth bits (0xFFFFFFFF for a Gaussian without tiles)
-// and gidx[g] = g.
+// and gidx[g] = g, or with pack_counts (batches of fewer than 2^24 entries)
+// g | min(supers[g], 255) << 24: the pair count then travels with the entry
+// through the depth sorts (255: look it up).
+constexpr uint32_t kPackedIdxBits = 24;
+constexpr uint32_t kPackedIdxMask = (1u << kPackedIdxBits) - 1u;
+constexpr uint32_t kPackedCntEsc = 255u;
 struct ViewOutputs {
     Records rec;
     ushort4* rect;
@@ -243,6 +248,7 @@ struct ViewOutputs {
     uint32_t* depth_key;
     uint32_t* gidx;
     unsigned long long* totals;
+    bool pack_counts = false;
 };
 cudaError_t launch_project_views(cudaStream_t s, const gs_gaussians& g, const ViewDesc* views, int V, int mode,
                                  const ViewOutputs& out);
@@ -364,9 +370,11 @@ cudaError_t launch_supers_to_hist_views(cudaStream_t s, const HistViews& b, int*
 // exclusive scan of counts[ids[k]] over k -> offsets[k] (offsets[n] = total);
 // totals[0] = exact 64-bit total, totals[1] = 64-bit total of side[ids[k]].
 // scratch: scan_partials_count(n) 64-bit tile states; counter: one uint32.
+// packed: ids[k] carry their count in the top 8 bits (ViewOutputs), the entry
+// in the low 24; counts[] is read only for the escaped ones
 cudaError_t launch_scan_gathered(cudaStream_t s, const uint32_t* counts, const uint32_t* side, const uint32_t* ids,
                                  uint32_t n, uint32_t* offsets, unsigned long long* scratch, uint32_t* counter,
-                                 unsigned long long* totals, int* err);
+                                 unsigned long long* totals, int* err, bool packed = false);
 size_t scan_partials_count(uint32_t n);
 
 // counts (may be NULL): kCountCopies x Ts per-super-tile pair counts accumulated
@@ -421,7 +429,7 @@ struct EmitViews {
     int V;
 };
 cudaError_t launch_emit_views(cudaStream_t s, const EmitViews& b, const uint32_t* sorted, const uint32_t* offsets,
-                              const ushort4* rect, uint32_t total);
+                              const ushort4* rect, uint32_t total, bool packed = false);
 cudaError_t launch_ranges(cudaStream_t s, const uint64_t* pairs, uint32_t P, uint32_t T, uint2* ranges);
 // per-tile lists from the super-tile lists: counts, starts, ranges and (optionally) keys/vals
 cudaError_t launch_tile_lists(cudaStream_t s, const uint64_t* spairs, const uint2* sranges, const ushort4* rect,

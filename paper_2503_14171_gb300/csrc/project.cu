@@ -449,7 +449,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project_views(
                                               (unsigned short)rc.w)
                                : make_ushort4(1, 1, 0, 0);
         out.depth_key[o] = v.ntiles > 0 ? __float_as_uint(v.pz) : 0xFFFFFFFFu;
-        out.gidx[o] = (uint32_t)o;
+        out.gidx[o] = out.pack_counts ? (uint32_t)o | (min(v.nsup, kPackedCntEsc) << kPackedIdxBits) : (uint32_t)o;
         float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
         if (v.vis)
             view_records<DEG>(v, mx3, my3, mz3, &s_sh[warp][lane][0], rgb_in + 3 * (DEG >= 0 ? 0 : i), op, L,

@@ -552,10 +552,12 @@ cudaError_t radix_sort_impl(cudaStream_t s, K* keys[2], uint32_t* vals[2], uint3
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr int kScanRow = kScanItems + 4;   // a lane's row of offsets in shared memory, padded
 constexpr unsigned long long kScanAgg = 1ull << 62;
 constexpr unsigned long long kScanInc = 2ull << 62;
 constexpr unsigned long long kScanMask = (1ull << 62) - 1;
 
+template <bool PACKED>
 __global__ void __launch_bounds__(kScanThreads) k_scan_onepass(const uint32_t* __restrict__ counts,
                                                                const uint32_t* __restrict__ side,
                                                                const uint32_t* __restrict__ ids, uint32_t n,
@@ -566,6 +568,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_onepass(const uint32_t* _
                                                                int* __restrict__ err)
 {
     __shared__ unsigned long long s_warp[kScanThreads / 32];
+    __shared__ __align__(16) uint32_t s_out[kScanThreads / 32][32 * kScanRow];
     __shared__ unsigned long long s_prefix;
     __shared__ uint32_t s_tile;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -573,17 +576,37 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_onepass(const uint32_t* _
     __syncthreads();
     const uint32_t tile = s_tile;
     const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
-    // blocked arrangement: thread t owns positions [t*16, t*16 + 16) of the tile
+    // blocked arrangement: thread t owns positions [t*16, t*16 + 16) of the
+    // tile, loaded as four 16-byte words where the pointer allows
     const uint32_t base = tile * kScanTile + threadIdx.x * kScanItems;
     uint32_t v[kScanItems];
     unsigned long long sum = 0, sum2 = 0;
+    uint32_t w[kScanItems];
+    if (base + kScanItems <= n && (reinterpret_cast<uintptr_t>(ids) & 15u) == 0) {
+        const uint4* p4 = reinterpret_cast<const uint4*>(ids + base);
+#pragma unroll
+        for (int q = 0; q < kScanItems / 4; ++q) {
+            const uint4 t = p4[q];
+            w[4 * q] = t.x; w[4 * q + 1] = t.y; w[4 * q + 2] = t.z; w[4 * q + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i) w[i] = base + i < n ? ids[base + i] : (PACKED ? 0u : n);
+    }
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
         const uint32_t k = base + i;
-        const uint32_t id = k < n ? ids[k] : n;
-        v[i] = id < n ? counts[id] : 0u;
+        if (PACKED) {   // the count rides with the entry (escaped ones looked up)
+            const uint32_t id = w[i] & kPackedIdxMask;
+            uint32_t c = w[i] >> kPackedIdxBits;
+            if (c == kPackedCntEsc) c = id < n ? counts[id] : 0u;
+            v[i] = k < n ? c : 0u;
+        } else {
+            const uint32_t id = w[i];
+            v[i] = id < n ? counts[id] : 0u;
+            if (side != nullptr && id < n) sum2 += side[id];
+        }
         sum += v[i];
-        if (side != nullptr && id < n) sum2 += side[id];
     }
     // block scan of the per-thread sums
     unsigned long long x = sum;
@@ -647,11 +670,35 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_onepass(const uint32_t* _
     }
     __syncthreads();
     uint32_t run = (uint32_t)(s_prefix + wbase + x - sum);
+    // a warp whose 512 positions all lie below n writes them through its
+    // shared-memory rows (20-word stride: conflict-free 16-byte accesses) as
+    // 512 contiguous bytes per instruction; the ragged tail writes in place
+    const uint32_t wbase_k = tile * kScanTile + warp * 32 * kScanItems;
+    if (wbase_k + 32 * kScanItems <= n && (reinterpret_cast<uintptr_t>(offsets) & 15u) == 0) {
+        uint32_t* row = &s_out[warp][lane * kScanRow];
 #pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-        const uint32_t k = base + i;
-        if (k < n) offsets[k] = run;
-        run += v[i];
+        for (int q = 0; q < kScanItems / 4; ++q) {
+            uint4 t;
+            t.x = run; run += v[4 * q];
+            t.y = run; run += v[4 * q + 1];
+            t.z = run; run += v[4 * q + 2];
+            t.w = run; run += v[4 * q + 3];
+            *reinterpret_cast<uint4*>(row + 4 * q) = t;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < kScanItems / 4; ++j) {
+            const int e = j * 128 + lane * 4;
+            const uint4 t = *reinterpret_cast<const uint4*>(&s_out[warp][(e / kScanItems) * kScanRow + e % kScanItems]);
+            *reinterpret_cast<uint4*>(offsets + wbase_k + e) = t;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i) {
+            const uint32_t k = base + i;
+            if (k < n) offsets[k] = run;
+            run += v[i];
+        }
     }
     if (tile == ntiles - 1 && threadIdx.x == kScanThreads - 1) offsets[n] = (uint32_t)(s_prefix + tot);
 }
@@ -897,15 +944,19 @@ size_t scan_partials_count(uint32_t n)
 
 cudaError_t launch_scan_gathered(cudaStream_t s, const uint32_t* counts, const uint32_t* side, const uint32_t* ids,
                                  uint32_t n, uint32_t* offsets, unsigned long long* scratch, uint32_t* counter,
-                                 unsigned long long* totals, int* err)
+                                 unsigned long long* totals, int* err, bool packed)
 {
     const uint32_t nt = (n + kScanTile - 1) / kScanTile;
+    if (packed && (side != nullptr || n > kPackedIdxMask)) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(totals, 0, 2 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     if (n == 0) return cudaMemsetAsync(offsets, 0, sizeof(uint32_t), s);
     if ((e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * nt, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(counter, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
-    k_scan_onepass<<<nt, kScanThreads, 0, s>>>(counts, side, ids, n, offsets, scratch, counter, totals, err);
+    if (packed)
+        k_scan_onepass<true><<<nt, kScanThreads, 0, s>>>(counts, side, ids, n, offsets, scratch, counter, totals, err);
+    else
+        k_scan_onepass<false><<<nt, kScanThreads, 0, s>>>(counts, side, ids, n, offsets, scratch, counter, totals, err);
     note_launch();
     return cudaGetLastError();
 }
