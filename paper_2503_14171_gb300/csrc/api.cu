@@ -614,7 +614,7 @@ gs_status gs_upscale(gs_ctx* c, const float* C, const float* grads, int32_t W, i
     if (factor < 1 || factor > 16) return fail(c, GS_ERR_INVALID_ARG, "factor must be in 1..16");
     if ((int64_t)W * factor > (1 << 24) || (int64_t)H * factor > (1 << 24))
         return fail(c, GS_ERR_INVALID_ARG, "output too large");
-    GS_CUDA(c, launch_upscale(c->stream, C, grads, W, H, factor, out));
+    GS_CUDA(c, launch_upscale(c->stream, C, grads, W, H, factor, out, as<int>(c->errword)));
     return GS_OK;
 }
 
@@ -639,7 +639,7 @@ gs_status gs_upscale_to(gs_ctx* c, const float* C, const float* grads, int32_t W
     if (!C || !grads || !out) return fail(c, GS_ERR_INVALID_ARG, "NULL image pointer");
     gs_status st = check_sizes(c, W, H, W2, H2, 2);
     if (st != GS_OK) return st;
-    GS_CUDA(c, launch_upscale_to(c->stream, C, grads, W, H, W2, H2, out));
+    GS_CUDA(c, launch_upscale_to(c->stream, C, grads, W, H, W2, H2, out, as<int>(c->errword)));
     return GS_OK;
 }
 
@@ -652,7 +652,7 @@ gs_status gs_upscale_mlp(gs_ctx* c, const float* C, const float* grads, int32_t 
     gs_status st = check_sizes(c, W, H, W2, H2, 2);
     if (st != GS_OK) return st;
     if (!params) {
-        GS_CUDA(c, launch_upscale_to(c->stream, C, grads, W, H, W2, H2, out));
+        GS_CUDA(c, launch_upscale_to(c->stream, C, grads, W, H, W2, H2, out, as<int>(c->errword)));
         return GS_OK;
     }
     GS_CUDA(c, launch_mlp_upscale(c->stream, C, grads, W, H, W2, H2, params, out, as<int>(c->errword)));

@@ -464,9 +464,11 @@ cudaError_t launch_project_backward(cudaStream_t s, const gs_gaussians& g, const
 // adjoint of the upscale: dout [3][sH][sW] -> dC [3][H][W], dG [9][H][W] (overwritten)
 cudaError_t launch_upscale_backward(cudaStream_t s, const float* dout, int W, int H, int factor, float* dC,
                                     float* dG);
-// any output size W2 x H2 with W <= W2 <= 16 W, H <= H2 <= 16 H (fractional factors)
+// any output size W2 x H2 with W <= W2 <= 16 W, H <= H2 <= 16 H (fractional factors);
+// err (may be NULL: then the TMA-fed form is not used) records an expired
+// bounded wait of the TMA-fed form
 cudaError_t launch_upscale_to(cudaStream_t s, const float* C, const float* grads, int W, int H, int W2, int H2,
-                              float* out);
+                              float* out, int* err = nullptr);
 cudaError_t launch_upscale_backward_to(cudaStream_t s, const float* dout, int W, int H, int W2, int H2, float* dC,
                                        float* dG);
 // classical bicubic comparator (cubic convolution with Keys' parameter a) of C [3][H][W]
@@ -474,9 +476,9 @@ cudaError_t launch_bicubic(cudaStream_t s, const float* C, int W, int H, int W2,
 cudaError_t launch_blend_stats(cudaStream_t s, int mode, const BlendArgs& a, unsigned long long* stats);
 
 cudaError_t launch_upscale(cudaStream_t s, const float* C, const float* grads, int W, int H, int factor,
-                           float* out);
+                           float* out, int* err = nullptr);
 
-// The spline upscales of a batch of views in one launch (view v's 64 x 16
+// The spline upscales of a batch of views in one launch (view v's 64 x 32
 // output tiles are blocks start[v] .. start[v + 1] - 1; upscale_tiles gives
 // each view's count)
 struct UpscaleView {

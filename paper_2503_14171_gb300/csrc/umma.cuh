@@ -62,6 +62,29 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
     return false;
 }
 
+// Arrive once on the mbarrier (the producer's arrival) and raise the phase's
+// expected transaction count by `bytes`: the phase completes when the arrival
+// and that many bytes of asynchronous copies have landed.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// ---------------------------------------------------------------- TMA
+
+// One tiled 3-D box of the tensor map at element coordinates (x, y, z) into
+// shared memory (128-byte aligned), its bytes counted on the mbarrier.  The
+// map is a __grid_constant__ kernel parameter; x times the element size must
+// be a multiple of 16 bytes (the caller rounds it down).
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, int y, int z, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // ---------------------------------------------------------------- fences
 
 // generic-proxy shared-memory writes -> visible to the tensor core's reads

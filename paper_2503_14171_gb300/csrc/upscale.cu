@@ -34,10 +34,15 @@
 // pixel's 12 values (C, C_x, C_y, C_xy for three channels) packed as three
 // float4 -- in shared memory with coalesced loads.  48 B per low-res pixel in,
 // 12 B per output pixel out.
+#include <cuda.h>           // CUtensorMap (the type only; no driver library is linked)
+#include <cudaTypedefs.h>   // the encoder's signature, fetched through the runtime
+
 #include <atomic>
+#include <mutex>
 
 #include "gs_internal.cuh"
 #include "spline_common.cuh"
+#include "umma.cuh"
 
 namespace gs {
 namespace {
@@ -189,6 +194,177 @@ __global__ void __launch_bounds__(kSplThreads) k_upscale_views(const __grid_cons
     const int tiles_x = (u.W2 + kSplW - 1) / kSplW;
     const int by = t / tiles_x, bx = t - by * tiles_x;
     upscale_tile(u.C, u.G, u.W, u.H, u.W2, u.H2, foot_w(u.W, u.W2), u.out, bx * kSplW, by * kSplH);
+}
+
+// ---------------------------------------------------------------- TMA-fed persistent form
+//
+// For low-res frames whose rows are a multiple of 16 bytes (W % 4 == 0) with
+// 16-byte aligned planes, each block loops over output tiles (tile, tile +
+// grid, ...) and evaluates exactly as upscale_tile, but its footprints arrive
+// by the tensor memory accelerator: two shared-memory stages, each holding one
+// 3-D box of the C planes and one of the G planes ([plane][row][column], the
+// box's first column rounded down to a multiple of 4 as the copy requires),
+// their completion counted on the stage's mbarrier.  The footprint of the
+// tile after next is in flight while the block evaluates the current one, so
+// the staging no longer stalls the block between its load and its
+// evaluation.  Same products and sums as upscale_tile, hence the same bits.
+constexpr int kUpStages = 2;
+constexpr uint32_t kUpWaitLimit = 1u << 22;   // mbarrier polls before giving up
+
+struct UpTma {
+    int bw, bh;       // box: columns (a multiple of 4) and rows of a footprint
+    int plane;        // bw * bh floats
+    int gofs;         // offset (floats) of the G box in a stage, 128-byte aligned
+    int stage;        // floats per stage, 128-byte aligned
+};
+
+__host__ __device__ inline UpTma up_tma_layout(int W, int H, int W2, int H2)
+{
+    UpTma l;
+    // + 3: the first column rounded down to a multiple of 4; no wider or
+    // taller than the frame (W is a multiple of 4 here)
+    l.bw = min((foot_w(W, W2) + 3 + 3) & ~3, W);
+    l.bh = min(foot_h(H, H2), H);
+    l.plane = l.bw * l.bh;
+    l.gofs = (3 * l.plane + 31) & ~31;
+    l.stage = (l.gofs + 9 * l.plane + 31) & ~31;
+    return l;
+}
+
+// (A, B) as spline_row, from the planar stage: value k of column x in row r at
+// st[k * plane + r * bw + x] (k < 3: C; else G at gofs + (k - 3) * plane)
+__device__ __forceinline__ void spline_row_planar(const float* __restrict__ st, const UpTma& l, int r, int li,
+                                                  float4 w, float (&A)[3], float (&B)[3])
+{
+    const float* c = st + r * l.bw + li;
+    const float* g = c + l.gofs;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        const float* cc = c + ch * l.plane;
+        const float* gx = g + ch * l.plane;
+        const float* gy = g + (3 + ch) * l.plane;
+        const float* gxy = g + (6 + ch) * l.plane;
+        A[ch] = fmaf(w.x, cc[0], fmaf(w.y, cc[1], fmaf(w.z, gx[0], w.w * gx[1])));
+        B[ch] = fmaf(w.x, gy[0], fmaf(w.y, gy[1], fmaf(w.z, gxy[0], w.w * gxy[1])));
+    }
+}
+
+__global__ void __launch_bounds__(kSplThreads) k_upscale_tma(const __grid_constant__ CUtensorMap tmC,
+                                                             const __grid_constant__ CUtensorMap tmG, int W, int H,
+                                                             int W2, int H2, const UpTma l, float* __restrict__ out,
+                                                             int* __restrict__ err)
+{
+    extern __shared__ __align__(128) float st_raw[];   // kUpStages stages of l.stage floats, from a 128-byte boundary
+    __shared__ __align__(8) uint64_t s_full[kUpStages];
+    __shared__ float4 s_wx[kSplW];
+    __shared__ float4 s_wy[kSplH];
+    __shared__ int s_cx[kSplW], s_cy[kSplH];
+    __shared__ int s_abort;
+    const int tid = threadIdx.x;
+    const int col = tid & (kSplCols - 1), run = tid / kSplCols;
+    const int tiles_x = (W2 + kSplW - 1) / kSplW;
+    const int ntiles = tiles_x * ((H2 + kSplH - 1) / kSplH);
+    const uint32_t tx_bytes = 12u * (uint32_t)l.plane * 4u;
+    const size_t oplane = (size_t)W2 * H2;
+    float* const st_all = st_raw + ((128u - (umma::smem_u32(st_raw) & 127u)) & 127u) / 4u;
+
+    // thread 0: the copies of tile t's footprint into stage s
+    auto issue = [&](int t, int s) {
+        const int X0 = (t % tiles_x) * kSplW, Y0 = (t / tiles_x) * kSplH;
+        int i0, j0;
+        float u;
+        cell_of(X0, W, W2, i0, u);
+        cell_of(Y0, H, H2, j0, u);
+        float* dst = st_all + (size_t)s * l.stage;
+        umma::mbar_arrive_expect_tx(&s_full[s], tx_bytes);
+        umma::tma_load_3d(dst, &tmC, i0 & ~3, j0, 0, &s_full[s]);
+        umma::tma_load_3d(dst + l.gofs, &tmG, i0 & ~3, j0, 0, &s_full[s]);
+    };
+    uint32_t issued0 = 0, issued1 = 0;   // thread 0: copies issued per stage
+    if (tid == 0) {
+        umma::mbar_init(&s_full[0], 1);
+        umma::mbar_init(&s_full[1], 1);
+        umma::mbar_init_fence();
+        s_abort = 0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if ((int)blockIdx.x < ntiles) { issue(blockIdx.x, 0); ++issued0; }
+        if ((int)(blockIdx.x + gridDim.x) < ntiles) { issue(blockIdx.x + gridDim.x, 1); ++issued1; }
+    }
+
+    int it = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        const int s = it & 1;
+        const int X0 = (t % tiles_x) * kSplW, Y0 = (t / tiles_x) * kSplH;
+        if (tid < kSplW) {
+            int ci;
+            float u;
+            cell_of(min(X0 + tid, W2 - 1), W, W2, ci, u);
+            s_cx[tid] = ci;
+            s_wx[tid] = hermite(u);
+        } else if (tid < kSplW + kSplH) {
+            const int r = tid - kSplW;
+            int cj;
+            float u;
+            cell_of(min(Y0 + r, H2 - 1), H, H2, cj, u);
+            s_cy[r] = cj;
+            s_wy[r] = hermite(u);
+        }
+        __syncthreads();   // tables of tile t
+        if (!umma::mbar_wait(&s_full[s], (uint32_t)(it >> 1) & 1u, kUpWaitLimit)) {
+            s_abort = 1;
+            atomicExch(err, kDevTimeout);
+        } else {
+            const float* st = st_all + (size_t)s * l.stage;
+            const int X = X0 + col;
+            const int y0 = run * kSplRun;
+            if (X < W2 && Y0 + y0 < H2) {
+                const int i0 = s_cx[0], j0 = s_cy[0];
+                const float4 wx = s_wx[col];
+                const int li = s_cx[col] - (i0 & ~3);
+                int cur = s_cy[y0] - j0;
+                float A0[3], B0[3], A1[3], B1[3];
+                spline_row_planar(st, l, cur, li, wx, A0, B0);
+                spline_row_planar(st, l, cur + 1, li, wx, A1, B1);
+                float* o = out + (size_t)(Y0 + y0) * W2 + X;
+#pragma unroll
+                for (int k = 0; k < kSplRun; ++k) {
+                    if (Y0 + y0 + k >= H2) break;
+                    const int lj = s_cy[y0 + k] - j0;
+                    if (lj != cur) {
+                        cur = lj;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            A0[c] = A1[c];
+                            B0[c] = B1[c];
+                        }
+                        spline_row_planar(st, l, cur + 1, li, wx, A1, B1);
+                    }
+                    const float4 wy = s_wy[y0 + k];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        o[c * oplane] = fmaf(wy.x, A0[c], fmaf(wy.y, A1[c], fmaf(wy.z, B0[c], wy.w * B1[c])));
+                    o += W2;
+                }
+            }
+        }
+        __syncthreads();   // stage s and the tables read by every thread
+        if (s_abort) break;
+        if (tid == 0) {
+            const int t2 = t + kUpStages * (int)gridDim.x;
+            if (t2 < ntiles) {
+                umma::fence_async_smem();   // the stage's reads ordered before the copy that overwrites it
+                issue(t2, s);
+                if (s) ++issued1; else ++issued0;
+            }
+        }
+    }
+    // after an expired wait: let this block's copies in flight land (bounded) before it exits
+    if (s_abort && tid == 0) {
+        if (issued0) umma::mbar_wait(&s_full[0], (issued0 - 1) & 1u, kUpWaitLimit);
+        if (issued1) umma::mbar_wait(&s_full[1], (issued1 - 1) & 1u, kUpWaitLimit);
+    }
 }
 
 // Adjoint of k_upscale (upscale_adjoint_at in spline_common.cuh): one thread
@@ -360,10 +536,93 @@ std::atomic<uint64_t> g_upscale_views_attr{0};
 
 }  // namespace
 
+namespace {
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library), looked up once per process
+PFN_cuTensorMapEncodeTiled_v12000 tma_encoder()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            (void)cudaGetLastError();
+    });
+    return fn;
+}
+
+// the 3-D map of `planes` W x H FP32 planes, boxes of bw x bh x planes
+bool planes_map(CUtensorMap* m, const float* base, int W, int H, int planes, int bw, int bh)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tma_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)planes};
+    const cuuint64_t strides[2] = {(cuuint64_t)W * 4u, (cuuint64_t)W * H * 4u};
+    const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, (cuuint32_t)planes};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+std::atomic<uint64_t> g_upscale_tma_attr{0};
+constexpr size_t kUpTmaMaxSmem = 227 * 1024 - 4096;   // dynamic share beside the static tables
+
+// The TMA-fed form when the frame allows it: rows of 16-byte multiples,
+// 16-byte aligned planes, both stages within one block's shared memory.
+// Returns cudaErrorNotSupported (nothing launched) otherwise.
+cudaError_t launch_upscale_tma(cudaStream_t s, const float* C, const float* grads, int W, int H, int W2, int H2,
+                               float* out, int* err)
+{
+    if (!err || W % 4 != 0 || (reinterpret_cast<uintptr_t>(C) & 15u) || (reinterpret_cast<uintptr_t>(grads) & 15u))
+        return cudaErrorNotSupported;
+    // only where the staged form waits on more than one round of loads per
+    // block (footprints of more than 2 x 256 pixels: factors below ~2.2);
+    // with smaller footprints the staged form's single round costs less than
+    // the persistent loop's waits (4x: 12.0 vs 14.2 us at 1920x1080; 2x: 16.4 vs 14.3 us)
+    if (foot_w(W, W2) * foot_h(H, H2) <= 2 * kSplThreads) return cudaErrorNotSupported;
+    const UpTma l = up_tma_layout(W, H, W2, H2);
+    const size_t smem = (size_t)kUpStages * l.stage * sizeof(float) + 128;   // + the rounding to 128 bytes
+    if (l.bw > 256 || l.bh > 256 || smem > kUpTmaMaxSmem) return cudaErrorNotSupported;
+    CUtensorMap mC, mG;
+    if (!planes_map(&mC, C, W, H, 3, l.bw, l.bh) || !planes_map(&mG, grads, W, H, 9, l.bw, l.bh))
+        return cudaErrorNotSupported;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = dev < 64 ? (uint64_t(1) << dev) : 0;
+    if (!bit || !(g_upscale_tma_attr.load(std::memory_order_acquire) & bit)) {
+        if ((e = cudaFuncSetAttribute(k_upscale_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kUpTmaMaxSmem)) != cudaSuccess)
+            return e;
+        g_upscale_tma_attr.fetch_or(bit, std::memory_order_acq_rel);
+    }
+    int per_sm = 0, sms = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_upscale_tma, kSplThreads, smem)) != cudaSuccess)
+        return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const int ntiles = upscale_tiles(W2, H2);
+    const int grid = std::max(1, std::min(ntiles, std::max(1, per_sm) * sms));
+    k_upscale_tma<<<grid, kSplThreads, smem, s>>>(mC, mG, W, H, W2, H2, l, out, err); note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace
+
 cudaError_t launch_upscale_to(cudaStream_t s, const float* C, const float* grads, int W, int H, int W2, int H2,
-                              float* out)
+                              float* out, int* err)
 {
     if (!sizes_ok(W, H, W2, H2, 2)) return cudaErrorInvalidValue;
+    {
+        const cudaError_t e = launch_upscale_tma(s, C, grads, W, H, W2, H2, out, err);
+        if (e != cudaErrorNotSupported) return e;
+    }
     dim3 grid((W2 + kSplW - 1) / kSplW, (H2 + kSplH - 1) / kSplH);
     cudaError_t e = upscale_attr(k_upscale, g_upscale_attr);
     if (e != cudaSuccess) return e;
@@ -394,10 +653,11 @@ int upscale_tiles(int W2, int H2)
     return ((W2 + kSplW - 1) / kSplW) * ((H2 + kSplH - 1) / kSplH);
 }
 
-cudaError_t launch_upscale(cudaStream_t s, const float* C, const float* grads, int W, int H, int factor, float* out)
+cudaError_t launch_upscale(cudaStream_t s, const float* C, const float* grads, int W, int H, int factor, float* out,
+                           int* err)
 {
     if (factor < 1 || factor > kMaxFactor) return cudaErrorInvalidValue;
-    return launch_upscale_to(s, C, grads, W, H, W * factor, H * factor, out);
+    return launch_upscale_to(s, C, grads, W, H, W * factor, H * factor, out, err);
 }
 
 cudaError_t launch_upscale_backward_to(cudaStream_t s, const float* dout, int W, int H, int W2, int H2, float* dC,

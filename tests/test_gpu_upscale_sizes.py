@@ -101,3 +101,33 @@ def test_size_rules(gs):
         with pytest.raises(gs.GSError) as e:
             ctx.upscale_bicubic(_t(C), 16, 16, a=0.5)
         assert e.value.status == gs.GS_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("W,H,W2,H2", [(960, 540, 1920, 1080), (64, 32, 64, 32), (64, 64, 128, 128),
+                                       (132, 70, 264, 140), (100, 60, 150, 90), (4, 2, 5, 2), (8, 6, 8, 6),
+                                       (480, 270, 1920, 1080)])
+def test_tma_fed_equals_staged(gs, ora, W, H, W2, H2):
+    """Frames with 16-byte rows, aligned planes and footprints of more than
+    512 low-res pixels per output tile (factors up to ~2.2; the last case,
+    4x, does not qualify) take the TMA-fed persistent form; the same values
+    one float off a 16-byte boundary take the staged form.  Both evaluate the
+    same products and sums: bit-identical outputs, and the smaller frames
+    within the spline tolerance of the oracle."""
+    import torch
+    C, G = _inputs(W, H, W * 7 + H2)
+    n3, n9 = 3 * H * W, 9 * H * W
+    buf = torch.zeros(1 + n3 + n9 + 3, device="cuda")
+    Cu = buf[1:1 + n3].view(3, H, W)      # 4 bytes past a 16-byte boundary
+    Gu = buf[1 + n3:1 + n3 + n9].view(9, H, W)
+    Cu.copy_(_t(C))
+    Gu.copy_(_t(G.reshape(9, H, W)))
+    assert Cu.data_ptr() % 16 != 0
+    with gs.Context() as ctx:
+        fed = ctx.upscale_to(_t(C), _t(G), W2, H2)
+        staged = ctx.upscale_to(Cu, Gu, W2, H2)
+        ctx.synchronize()
+    assert torch.equal(fed, staged)
+    if W * H <= 140 * 80:
+        want = ora.upscale(C.astype(np.float64), G.astype(np.float64), W2, H2)
+        scale = 1.0 + max(np.abs(C).max(), np.abs(G).max())
+        assert np.abs(fed.cpu().numpy() - want).max() <= TOL_UP * scale
