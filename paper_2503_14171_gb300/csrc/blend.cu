@@ -52,20 +52,20 @@ template <bool GRADS, bool WIDE = false>
 __host__ __device__ constexpr int blend_min_blocks() { return WIDE ? 3 : GRADS ? 4 : 5; }
 
 struct PixelState {
-    float T, Tx, Ty, Txy;
-    float C0, C1, C2, X0, X1, X2, Y0, Y1, Y2, Z0, Z1, Z2;
+    float T, Txy;
+    float2 TxTy;
+    float2 C01, X01, Y01, Z01, XY2, CZ2;   // channel pairs (0, 1); channel 2 as (X2, Y2) and (C2, Z2)
     int last;
     bool done;
 };
 
 __device__ __forceinline__ void init(PixelState& p, bool inside)
 {
+    const float2 z = make_float2(0.f, 0.f);
     p.T = 1.f;
-    p.Tx = p.Ty = p.Txy = 0.f;
-    p.C0 = p.C1 = p.C2 = 0.f;
-    p.X0 = p.X1 = p.X2 = 0.f;
-    p.Y0 = p.Y1 = p.Y2 = 0.f;
-    p.Z0 = p.Z1 = p.Z2 = 0.f;
+    p.Txy = 0.f;
+    p.TxTy = z;
+    p.C01 = p.X01 = p.Y01 = p.Z01 = p.XY2 = p.CZ2 = z;
     p.last = 0;
     p.done = !inside;
 }
@@ -88,29 +88,32 @@ __device__ __forceinline__ bool blend_pair(PixelState& p, float g2, float dx, fl
     // every multiply-add below is spelled out (fmaf, or an intrinsic that is
     // never fused): the walk's unrolled copies of this function then round
     // alike wherever the compiler places them
-    const float Tn = p.T * __fsub_rn(1.f, alpha);
+    const float2 tw = mul2(make_float2(p.T, p.T), make_float2(__fsub_rn(1.f, alpha), alpha));   // (T (1 - alpha), T alpha)
+    const float Tn = tw.x;
     if (MODE == GS_MODE_3DGS && Tn < 1e-4f) {
         p.done = true;
         return false;
     }
-    const float w = alpha * p.T;
-    p.C0 = fmaf(c.x, w, p.C0);
-    p.C1 = fmaf(c.y, w, p.C1);
-    p.C2 = fmaf(c.z, w, p.C2);
+    const float w = tw.y;
+    const float2 c01 = make_float2(c.x, c.y);
+    p.C01 = fma2(c01, make_float2(w, w), p.C01);
+    if (!GRADS) p.CZ2.x = fmaf(c.z, w, p.CZ2.x);
     if (GRADS) {
         const float bn = r1.y * kLn2;                       // -b
-        float gx = fmaf(r0.z, dx, bn * dy);                 // -(a dx + b dy)
-        float gy = fmaf(r0.w, dy, bn * dx);                 // -(b dx + c dy)
+        // (g_x, g_y) = (-(a dx + b dy), -(b dx + c dy))
+        const float2 g = fma2(make_float2(r0.z, r0.w), make_float2(dx, dy), mul2(make_float2(bn, bn), make_float2(dy, dx)));
+        float gx = g.x, gy = g.y;
         float gxy = fmaf(gx, gy, bn);                       // g_x g_y + g_xy
         if (clamped) { gx = 0.f; gy = 0.f; gxy = 0.f; }
-        const float wx = alpha * fmaf(p.T, gx, p.Tx);
-        const float wy = alpha * fmaf(p.T, gy, p.Ty);
-        const float wxy = alpha * fmaf(p.T, gxy, fmaf(p.Tx, gy, fmaf(p.Ty, gx, p.Txy)));
-        p.X0 = fmaf(c.x, wx, p.X0); p.X1 = fmaf(c.y, wx, p.X1); p.X2 = fmaf(c.z, wx, p.X2);
-        p.Y0 = fmaf(c.x, wy, p.Y0); p.Y1 = fmaf(c.y, wy, p.Y1); p.Y2 = fmaf(c.z, wy, p.Y2);
-        p.Z0 = fmaf(c.x, wxy, p.Z0); p.Z1 = fmaf(c.y, wxy, p.Z1); p.Z2 = fmaf(c.z, wxy, p.Z2);
-        p.Tx = __fsub_rn(p.Tx, wx);
-        p.Ty = __fsub_rn(p.Ty, wy);
+        const float2 wxy2 = mul2(make_float2(alpha, alpha), fma2(make_float2(p.T, p.T), make_float2(gx, gy), p.TxTy));
+        const float wxy = alpha * fmaf(p.T, gxy, fmaf(p.TxTy.x, gy, fmaf(p.TxTy.y, gx, p.Txy)));
+        p.X01 = fma2(c01, make_float2(wxy2.x, wxy2.x), p.X01);
+        p.Y01 = fma2(c01, make_float2(wxy2.y, wxy2.y), p.Y01);
+        p.Z01 = fma2(c01, make_float2(wxy, wxy), p.Z01);
+        const float2 cz = make_float2(c.z, c.z);
+        p.XY2 = fma2(cz, wxy2, p.XY2);
+        p.CZ2 = fma2(cz, make_float2(w, wxy), p.CZ2);
+        p.TxTy = sub2(p.TxTy, wxy2);
         p.Txy = __fsub_rn(p.Txy, wxy);
     }
     p.T = Tn;
@@ -123,22 +126,22 @@ __device__ __forceinline__ void store(const BlendArgs& a, const PixelState& p, i
 {
     const size_t plane = (size_t)a.W * a.H;
     const size_t pix = (size_t)y * a.W + x;
-    a.out_C[pix] = fmaf(p.T, a.bg.x, p.C0);
-    a.out_C[plane + pix] = fmaf(p.T, a.bg.y, p.C1);
-    a.out_C[2 * plane + pix] = fmaf(p.T, a.bg.z, p.C2);
+    a.out_C[pix] = fmaf(p.T, a.bg.x, p.C01.x);
+    a.out_C[plane + pix] = fmaf(p.T, a.bg.y, p.C01.y);
+    a.out_C[2 * plane + pix] = fmaf(p.T, a.bg.z, p.CZ2.x);
     if (GRADS) {
         float* G = a.out_G;
-        G[pix] = fmaf(p.Tx, a.bg.x, p.X0);
-        G[plane + pix] = fmaf(p.Tx, a.bg.y, p.X1);
-        G[2 * plane + pix] = fmaf(p.Tx, a.bg.z, p.X2);
-        G[3 * plane + pix] = fmaf(p.Ty, a.bg.x, p.Y0);
-        G[4 * plane + pix] = fmaf(p.Ty, a.bg.y, p.Y1);
-        G[5 * plane + pix] = fmaf(p.Ty, a.bg.z, p.Y2);
-        G[6 * plane + pix] = fmaf(p.Txy, a.bg.x, p.Z0);
-        G[7 * plane + pix] = fmaf(p.Txy, a.bg.y, p.Z1);
-        G[8 * plane + pix] = fmaf(p.Txy, a.bg.z, p.Z2);
+        G[pix] = fmaf(p.TxTy.x, a.bg.x, p.X01.x);
+        G[plane + pix] = fmaf(p.TxTy.x, a.bg.y, p.X01.y);
+        G[2 * plane + pix] = fmaf(p.TxTy.x, a.bg.z, p.XY2.x);
+        G[3 * plane + pix] = fmaf(p.TxTy.y, a.bg.x, p.Y01.x);
+        G[4 * plane + pix] = fmaf(p.TxTy.y, a.bg.y, p.Y01.y);
+        G[5 * plane + pix] = fmaf(p.TxTy.y, a.bg.z, p.XY2.y);
+        G[6 * plane + pix] = fmaf(p.Txy, a.bg.x, p.Z01.x);
+        G[7 * plane + pix] = fmaf(p.Txy, a.bg.y, p.Z01.y);
+        G[8 * plane + pix] = fmaf(p.Txy, a.bg.z, p.CZ2.y);
     }
-    if (a.state) a.state[pix] = make_float4(p.T, p.Tx, p.Ty, p.Txy);
+    if (a.state) a.state[pix] = make_float4(p.T, p.TxTy.x, p.TxTy.y, p.Txy);
     if (a.count) a.count[pix] = p.last;
 }
 
@@ -227,8 +230,9 @@ __device__ __forceinline__ void blend_tile(const BlendArgs& a, int tile, unsigne
             for (int u = 0; u < U; ++u) {
                 q0[u] = s_r0[k + u];
                 q1[u] = s_r1[k + u];
-                qdx[u] = px - q0[u].x;
-                qdy[u] = py - q0[u].y;
+                const float2 d = sub2(make_float2(px, py), make_float2(q0[u].x, q0[u].y));
+                qdx[u] = d.x;
+                qdy[u] = d.y;
                 qg2[u] = exponent2(q1[u], qdx[u], qdy[u]);
             }
 #pragma unroll
