@@ -78,16 +78,19 @@ __device__ __forceinline__ void spline_row(const float4* __restrict__ foot, int 
     B[2] = fmaf(w.x, a2.x, fmaf(w.y, b2.x, fmaf(w.z, a2.w, w.w * b2.w)));
 }
 
-// The 64 x 32 output tile at (X0, Y0) (one block of kSplThreads)
+// The 64 x (4 RUN) output tile at (X0, Y0) (one block of kSplThreads; RUN
+// rows per thread: 8, or 16 for factors of 3 and more, whose footprints are small)
+template <int RUN = kSplRun>
 __device__ __forceinline__ void upscale_tile(const float* __restrict__ Cimg, const float* __restrict__ G, int W,
                                              int H, int W2, int H2, int pitch, float* __restrict__ out, int X0,
                                              int Y0)
 {
+    constexpr int kTH = kSplRuns * RUN;   // tile rows
     // per low-res pixel of the footprint, its 12 values packed in 3 float4: [fy][fx][3]
     extern __shared__ float4 sm[];
     __shared__ float4 s_wx[kSplW];   // basis weights (h00, h01, h10, h11) per output column
-    __shared__ float4 s_wy[kSplH];
-    __shared__ int s_cx[kSplW], s_cy[kSplH];   // cell index (absolute until the footprint origin is known)
+    __shared__ float4 s_wy[kTH];
+    __shared__ int s_cx[kSplW], s_cy[kTH];   // cell index (absolute until the footprint origin is known)
     const int tid = threadIdx.x;
     const int col = tid & (kSplCols - 1), run = tid / kSplCols;
 
@@ -97,7 +100,7 @@ __device__ __forceinline__ void upscale_tile(const float* __restrict__ Cimg, con
         cell_of(min(X0 + tid, W2 - 1), W, W2, ci, t);
         s_cx[tid] = ci;
         s_wx[tid] = hermite(t);
-    } else if (tid < kSplW + kSplH) {
+    } else if (tid < kSplW + kTH) {
         const int r = tid - kSplW;
         int cj;
         float u;
@@ -107,7 +110,7 @@ __device__ __forceinline__ void upscale_tile(const float* __restrict__ Cimg, con
     }
     __syncthreads();
     const int i0 = s_cx[0], j0 = s_cy[0];
-    const int fw = s_cx[kSplW - 1] + 2 - i0, fh = s_cy[kSplH - 1] + 2 - j0;   // <= pitch x foot_h(H, H2)
+    const int fw = s_cx[kSplW - 1] + 2 - i0, fh = s_cy[kTH - 1] + 2 - j0;   // <= pitch x foot_h(H, H2)
 
     // footprint: pixel p of the row-major fh x fw window is loaded by thread
     // p mod 256 (coalesced in each of the 12 planes); two rounds of loads in
@@ -143,7 +146,7 @@ __device__ __forceinline__ void upscale_tile(const float* __restrict__ Cimg, con
     __syncthreads();
 
     const int X = X0 + col;
-    const int y0 = run * kSplRun;
+    const int y0 = run * RUN;
     if (X >= W2 || Y0 + y0 >= H2) return;   // no barrier follows
     const float4 wx = s_wx[col];
     const int li = s_cx[col] - i0;
@@ -155,7 +158,7 @@ __device__ __forceinline__ void upscale_tile(const float* __restrict__ Cimg, con
     const size_t oplane = (size_t)W2 * H2;
     float* o = out + (size_t)(Y0 + y0) * W2 + X;
 #pragma unroll
-    for (int k = 0; k < kSplRun; ++k) {
+    for (int k = 0; k < RUN; ++k) {
         if (Y0 + y0 + k >= H2) break;
         const int lj = s_cy[y0 + k] - j0;
         if (lj != cur) {   // the next cell row (cells of consecutive rows step by at most one)
@@ -175,11 +178,12 @@ __device__ __forceinline__ void upscale_tile(const float* __restrict__ Cimg, con
     }
 }
 
+template <int RUN = kSplRun>
 __global__ void __launch_bounds__(kSplThreads) k_upscale(const float* __restrict__ Cimg, const float* __restrict__ G,
                                                          int W, int H, int W2, int H2, int pitch,
                                                          float* __restrict__ out)
 {
-    upscale_tile(Cimg, G, W, H, W2, H2, pitch, out, blockIdx.x * kSplW, blockIdx.y * kSplH);
+    upscale_tile<RUN>(Cimg, G, W, H, W2, H2, pitch, out, blockIdx.x * kSplW, blockIdx.y * (kSplRuns * RUN));
 }
 
 // The upscales of a batch of views in one launch: block b takes tile b - start[v]
@@ -623,12 +627,20 @@ cudaError_t launch_upscale_to(cudaStream_t s, const float* C, const float* grads
         const cudaError_t e = launch_upscale_tma(s, C, grads, W, H, W2, H2, out, err);
         if (e != cudaErrorNotSupported) return e;
     }
-    dim3 grid((W2 + kSplW - 1) / kSplW, (H2 + kSplH - 1) / kSplH);
-    cudaError_t e = upscale_attr(k_upscale, g_upscale_attr);
-    if (e != cudaSuccess) return e;
     const int pitch = foot_w(W, W2);
+    if (W2 >= 3 * W && H2 >= 3 * H) {   // 64 x 64 tiles: footprints of at most 23 x 23 pixels
+        constexpr int kTH = kSplRuns * 16;
+        const int fh = std::min(kTH + 1, (int)((63ll * H + H2 - 1) / H2) + 2);
+        dim3 grid((W2 + kSplW - 1) / kSplW, (H2 + kTH - 1) / kTH);
+        k_upscale<16><<<grid, kSplThreads, 3 * sizeof(float4) * pitch * fh, s>>>(C, grads, W, H, W2, H2, pitch, out);
+        note_launch();
+        return cudaGetLastError();
+    }
+    dim3 grid((W2 + kSplW - 1) / kSplW, (H2 + kSplH - 1) / kSplH);
+    cudaError_t e = upscale_attr(k_upscale<>, g_upscale_attr);
+    if (e != cudaSuccess) return e;
     const size_t smem = 3 * sizeof(float4) * pitch * foot_h(H, H2);
-    k_upscale<<<grid, kSplThreads, smem, s>>>(C, grads, W, H, W2, H2, pitch, out); note_launch();
+    k_upscale<><<<grid, kSplThreads, smem, s>>>(C, grads, W, H, W2, H2, pitch, out); note_launch();
     return cudaGetLastError();
 }
 
